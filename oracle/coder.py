@@ -1,0 +1,189 @@
+"""ctypes wrapper of the C oracle (dlic_oracle.c).  Test infrastructure only:
+the functions here restate the coding method sequentially on the CPU and are
+what the CUDA library is checked against."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dlic_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+U8P = C.POINTER(C.c_uint8)
+U32P = C.POINTER(C.c_uint32)
+F32P = C.POINTER(C.c_float)
+F64P = C.POINTER(C.c_double)
+U64P = C.POINTER(C.c_uint64)
+IP = C.POINTER(C.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (IEEE, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.or_fnv1a64.restype = C.c_uint64
+            L.or_fnv1a64.argtypes = [U8P, C.c_size_t]
+            L.or_gather.restype = None
+            L.or_gather.argtypes = [U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
+            L.or_table_from_logits.restype = C.c_int
+            L.or_table_from_logits.argtypes = [F32P, C.c_float, U32P, U32P]
+            L.or_rans_enc_step.restype = C.c_int
+            L.or_rans_enc_step.argtypes = [U64P, C.c_uint32, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                                           U32P, C.c_int]
+            L.or_rans_dec_step.restype = C.c_int
+            L.or_rans_dec_step.argtypes = [U64P, U32P, C.c_int, C.c_int, C.c_int, C.c_int, U32P,
+                                           C.c_int, IP]
+            L.or_max_encoded_bytes.restype = C.c_size_t
+            L.or_max_encoded_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+            L.or_pixel_table.restype = C.c_int
+            L.or_pixel_table.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         F32P, U32P]
+            L.or_logits.restype = C.c_int
+            L.or_logits.argtypes = [U8P, C.c_size_t, U8P, C.c_int, F32P]
+            L.or_symbol_tables.restype = C.c_int
+            L.or_symbol_tables.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, U32P, F64P]
+            L.or_encode.restype = C.c_int64
+            L.or_encode.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, U8P,
+                                    C.c_size_t]
+            L.or_decode.restype = C.c_int
+            L.or_decode.argtypes = [U8P, C.c_size_t, U8P, C.c_size_t, U8P, C.c_int, C.c_int]
+            _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _bytes(b) -> np.ndarray:
+    return np.frombuffer(bytes(b), dtype=np.uint8).copy()
+
+
+def fnv1a64(data: bytes) -> int:
+    a = _bytes(data)
+    return int(lib().or_fnv1a64(_p(a, U8P), a.size))
+
+
+def max_encoded_bytes(H: int, W: int, S: int) -> int:
+    return int(lib().or_max_encoded_bytes(H, W, S))
+
+
+def gather(img: np.ndarray, r: int, c: int) -> np.ndarray:
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    out = np.zeros(12, np.uint8)
+    lib().or_gather(_p(img, U8P), img.shape[0], img.shape[1], r, c, _p(out, U8P))
+    return out
+
+
+def table_from_logits(z, tscale: float, lut) -> np.ndarray:
+    """Cumulative table c_0..c_256 (uint32) for one logit vector."""
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    lut = np.ascontiguousarray(lut, dtype=np.uint32)
+    cum = np.zeros(257, np.uint32)
+    st = lib().or_table_from_logits(_p(z, F32P), C.c_float(tscale), _p(lut, U32P), _p(cum, U32P))
+    if st:
+        raise ValueError(f"oracle table error {st}")
+    return cum
+
+
+def rans_enc_step(x: int, f: int, c: int, Lb=16, bb=16, Mb=16):
+    xs = (C.c_uint64 * 1)(x)
+    em = (C.c_uint32 * 8)()
+    n = lib().or_rans_enc_step(xs, f, c, Lb, bb, Mb, em, 8)
+    if n < 0:
+        raise ValueError("too many renormalisation words")
+    return int(xs[0]), [int(em[i]) for i in range(n)]
+
+
+def rans_dec_step(x: int, cum, words, pos: int, Lb=16, bb=16, Mb=16):
+    cum = np.ascontiguousarray(cum, dtype=np.uint32)
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1))
+    if w.size == 0:
+        w = np.zeros(1, np.uint32)
+        nw = 0
+    else:
+        nw = w.size
+    xs = (C.c_uint64 * 1)(x)
+    ps = (C.c_int * 1)(pos)
+    s = lib().or_rans_dec_step(xs, _p(cum, U32P), cum.size - 1, Lb, bb, Mb, _p(w, U32P), nw, ps)
+    return s, int(xs[0]), int(ps[0])
+
+
+def pixel_table(blob: bytes, img: np.ndarray, r: int, c: int):
+    """(logits[256] float32, cum[257] uint32) of pixel (r, c)."""
+    b = _bytes(blob)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    z = np.zeros(256, np.float32)
+    cum = np.zeros(257, np.uint32)
+    st = lib().or_pixel_table(_p(b, U8P), b.size, _p(img, U8P), img.shape[0], img.shape[1], r, c,
+                              _p(z, F32P), _p(cum, U32P))
+    if st:
+        raise ValueError(f"oracle error {st}")
+    return z, cum
+
+
+def logits(blob: bytes, pri: np.ndarray) -> np.ndarray:
+    b = _bytes(blob)
+    pri = np.ascontiguousarray(pri, dtype=np.uint8).reshape(-1, 12)
+    z = np.zeros((pri.shape[0], 256), np.float32)
+    st = lib().or_logits(_p(b, U8P), b.size, _p(pri, U8P), pri.shape[0], _p(z, F32P))
+    if st:
+        raise ValueError(f"oracle error {st}")
+    return z
+
+
+def symbol_tables(blob: bytes, img: np.ndarray):
+    """(f | c << 16 per pixel as uint32 [H, W], ideal bits sum -log2(f/2^16))."""
+    b = _bytes(blob)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    fc = np.zeros(img.shape, np.uint32)
+    bits = (C.c_double * 1)()
+    st = lib().or_symbol_tables(_p(b, U8P), b.size, _p(img, U8P), img.shape[0], img.shape[1],
+                                _p(fc, U32P), bits)
+    if st:
+        raise ValueError(f"oracle error {st}")
+    return fc, float(bits[0])
+
+
+def encode(blob: bytes, img: np.ndarray, streams: int) -> bytes:
+    b = _bytes(blob)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    cap = max_encoded_bytes(H, W, streams)
+    out = np.zeros(cap, np.uint8)
+    n = lib().or_encode(_p(b, U8P), b.size, _p(img, U8P), H, W, streams, _p(out, U8P), cap)
+    if n < 0:
+        raise ValueError(f"oracle encode error {-n}")
+    return out[:n].tobytes()
+
+
+def decode(blob: bytes, data: bytes, H: int, W: int):
+    """(status, image): status 0 on success, 3 for a corrupt stream."""
+    b = _bytes(blob)
+    d = _bytes(data)
+    if d.size == 0:
+        d = np.zeros(1, np.uint8)
+        n = 0
+    else:
+        n = d.size
+    img = np.zeros((H, W), np.uint8)
+    st = lib().or_decode(_p(b, U8P), b.size, _p(d, U8P), n, _p(img, U8P), H, W)
+    return int(st), img

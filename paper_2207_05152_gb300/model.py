@@ -1,0 +1,153 @@
+"""Model blobs for the DLIC coder: serialisation and post-training quantisation.
+
+The density-estimation network (Sec. II-B, "Neural Network Architecture") maps
+the 12 causal priors of a pixel to 256 logits, one per 8-bit value; the
+softmax of those logits is the PDF the entropy coder uses (Eq. 1).  The coder
+needs that PDF to be bit-identical at encode and decode (Sec. II-B,
+"Preprocessor": the same matrices must enter the network on both sides), so a
+model is shipped as one little-endian byte blob that fixes every number the
+coder uses:
+
+    0    char[4] "DLM1"
+    4    u32 precision            0 = FP32 network, 1 = INT8 network
+    8    u32 n_in (12), n_h1, n_h2, n_out (256), radius (2)
+    28   f32 tscale               logit difference -> table units (64 / ln 2)
+    32   u32 lut[64]              lut[k] = round(2^23 * 2^(-k/64)), lut[0] = 2^23
+    288  layer data
+         FP32: W1 f32[h1][12], b1 f32[h1], W2 f32[h2][h1], b2 f32[h2],
+               W3 f32[256][h2], b3 f32[256]
+         INT8: W1 i8[h1][12], s1 f32[h1], o1 f32[h1],
+               W2 i8[h2][h1], s2 f32[h2], o2 f32[h2],
+               W3 i8[256][h2], s3 f32[256], o3 f32[256]
+
+The INT8 network computes, per layer, an exact integer dot product
+acc = sum_k Wq[j][k] * a_k (inputs are v - 128 for the priors and u8 hidden
+activations), then h_j = clamp(rint(fma(acc, s_j, o_j)), 0, 255) for hidden
+layers and z_j = fma(acc, s_j, o_j) for the logits.  This module holds the
+host-side model preparation only; every coding step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import struct
+
+import numpy as np
+
+MAGIC = b"DLM1"
+PREC_FP32 = 0
+PREC_INT8 = 1
+N_IN = 12
+N_OUT = 256
+RADIUS = 2
+HEADER_BYTES = 288
+TSCALE = np.float32(64.0 / np.log(2.0))
+
+
+def table_lut() -> np.ndarray:
+    """lut[k] = round(2^23 * 2^(-k/64)), k = 0..63: the fixed-point powers of
+    two the table quantisation uses to turn log2-domain logit gaps into
+    relative weights."""
+    k = np.arange(64, dtype=np.float64)
+    return np.rint(np.exp2(23.0 - k / 64.0)).astype(np.uint32)
+
+
+def _header(precision: int, h1: int, h2: int) -> bytes:
+    hdr = MAGIC + struct.pack("<6I", precision, N_IN, h1, h2, N_OUT, RADIUS)
+    hdr += struct.pack("<f", float(TSCALE))
+    hdr += table_lut().astype("<u4").tobytes()
+    assert len(hdr) == HEADER_BYTES
+    return hdr
+
+
+def _check_widths(layers):
+    if len(layers) != 3:
+        raise ValueError("the coder network has exactly three dense layers")
+    (w1, b1), (w2, b2), (w3, b3) = layers
+    h1, h2 = w1.shape[0], w2.shape[0]
+    if w1.shape != (h1, N_IN) or w2.shape != (h2, h1) or w3.shape != (N_OUT, h2):
+        raise ValueError("layer shapes must be (h1,12), (h2,h1), (256,h2)")
+    if b1.shape != (h1,) or b2.shape != (h2,) or b3.shape != (N_OUT,):
+        raise ValueError("bias shapes do not match the layers")
+    if h1 % 16 or h2 % 16 or not (16 <= h1 <= 256) or not (16 <= h2 <= 256):
+        raise ValueError("hidden widths must be multiples of 16 in [16, 256]")
+    return h1, h2
+
+
+def fp32_blob(layers) -> bytes:
+    """Blob of an FP32 network given [(W1, b1), (W2, b2), (W3, b3)]."""
+    h1, h2 = _check_widths(layers)
+    out = [_header(PREC_FP32, h1, h2)]
+    for w, b in layers:
+        out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
+        out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
+    return b"".join(out)
+
+
+def features_fp32(ctx_u8: np.ndarray) -> np.ndarray:
+    """Network input for 8-bit priors: v / 128 - 1."""
+    return ctx_u8.astype(np.float32) / np.float32(128.0) - np.float32(1.0)
+
+
+def _forward_fp32(layers, ctx_u8):
+    x = features_fp32(ctx_u8).astype(np.float64)
+    acts = []
+    for li, (w, b) in enumerate(layers):
+        x = x @ w.astype(np.float64).T + b.astype(np.float64)
+        if li < 2:
+            x = np.maximum(x, 0.0)
+            acts.append(x)
+    return acts, x
+
+
+def int8_blob(layers, calib_ctx: np.ndarray) -> bytes:
+    """Post-training quantisation of an FP32 network to the INT8 blob.
+
+    Weights: per-output-channel symmetric scale max|w| / 127, round half to
+    even, clamp to +-127.  Hidden activations: u8 with a per-layer scale
+    max(h) / 255 over the calibration contexts (u8 array [N, 12]).  Inputs:
+    v - 128 with scale 1/128."""
+    h1, h2 = _check_widths(layers)
+    acts, _ = _forward_fp32(layers, np.asarray(calib_ctx, dtype=np.uint8))
+    act_scale = [max(float(a.max()), 1e-6) / 255.0 for a in acts]
+    in_scale = [1.0 / 128.0, act_scale[0], act_scale[1]]
+    out = [_header(PREC_INT8, h1, h2)]
+    for li, (w, b) in enumerate(layers):
+        w = w.astype(np.float64)
+        b = b.astype(np.float64)
+        sw = np.abs(w).max(axis=1) / 127.0
+        sw[sw == 0] = 1.0
+        wq = np.clip(np.rint(w / sw[:, None]), -127, 127).astype(np.int8)
+        if li < 2:
+            s = sw * in_scale[li] / act_scale[li]
+            o = b / act_scale[li]
+        else:
+            s = sw * in_scale[li]
+            o = b
+        out.append(wq.tobytes())
+        out.append(s.astype("<f4").tobytes())
+        out.append(o.astype("<f4").tobytes())
+    return b"".join(out)
+
+
+def parse_blob(blob: bytes) -> dict:
+    """Split a blob into its named arrays (for inspection and training)."""
+    if blob[:4] != MAGIC:
+        raise ValueError("not a DLIC model blob")
+    prec, n_in, h1, h2, n_out, radius = struct.unpack_from("<6I", blob, 4)
+    (tscale,) = struct.unpack_from("<f", blob, 28)
+    lut = np.frombuffer(blob, dtype="<u4", count=64, offset=32)
+    d = dict(precision=prec, n_in=n_in, h1=h1, h2=h2, n_out=n_out, radius=radius,
+             tscale=tscale, lut=lut)
+    off = HEADER_BYTES
+    dims = [(h1, n_in), (h2, h1), (n_out, h2)]
+    for li, (o, i) in enumerate(dims, start=1):
+        if prec == PREC_FP32:
+            d[f"W{li}"] = np.frombuffer(blob, "<f4", o * i, off).reshape(o, i); off += 4 * o * i
+            d[f"b{li}"] = np.frombuffer(blob, "<f4", o, off); off += 4 * o
+        else:
+            d[f"Q{li}"] = np.frombuffer(blob, "i1", o * i, off).reshape(o, i); off += o * i
+            d[f"s{li}"] = np.frombuffer(blob, "<f4", o, off); off += 4 * o
+            d[f"o{li}"] = np.frombuffer(blob, "<f4", o, off); off += 4 * o
+    if off != len(blob):
+        raise ValueError("blob size does not match its header")
+    return d
+

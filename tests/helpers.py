@@ -1,0 +1,60 @@
+"""Shared test helpers: model factories and exact reference arithmetic."""
+from __future__ import annotations
+
+import struct
+from fractions import Fraction
+
+import numpy as np
+
+import synth
+from paper_2207_05152_gb300 import model as M
+
+
+def fp32_model(widths, seed=1, kind="predictive"):
+    layers = synth.predictive_mlp(widths, seed) if kind == "predictive" else synth.xavier_mlp(widths, seed)
+    return layers, M.fp32_blob(layers)
+
+
+def calib_contexts(images, count=4096, seed=77):
+    """Priors (u8 [count, 12]) of pixels drawn uniformly from the images,
+    zero-padded at the borders: calibration data for quantisation."""
+    idx, rr, cc = synth.sample_positions(images, count, seed)
+    out = np.zeros((count, 12), np.uint8)
+    dr = [-2, -2, -2, -2, -2, -1, -1, -1, -1, -1, 0, 0]
+    dc = [-2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -2, -1]
+    for n, (i, r, c) in enumerate(zip(idx, rr, cc)):
+        img = images[i]
+        H, W = img.shape
+        for k in range(12):
+            y, x = r + dr[k], c + dc[k]
+            out[n, k] = img[y, x] if 0 <= y < H and 0 <= x < W else 0
+    return out
+
+
+def int8_model(widths, images, seed=1):
+    layers = synth.predictive_mlp(widths, seed)
+    return layers, M.int8_blob(layers, calib_contexts(images))
+
+
+def f32(x) -> float:
+    return float(np.float32(x))
+
+
+def round_to_f32(q: Fraction) -> float:
+    """Correctly rounded (nearest, ties to even) float32 of an exact rational."""
+    c = np.float32(float(q))
+    best = None
+    for cand in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        d = abs(Fraction(float(cand)) - q)
+        if best is None or d < best[0] or (d == best[0] and _even(cand) and not _even(best[1])):
+            best = (d, cand)
+    return float(best[1])
+
+
+def _even(x) -> bool:
+    return (struct.unpack("<I", struct.pack("<f", float(x)))[0] & 1) == 0
+
+
+def fma32(a: float, b: float, c: float) -> float:
+    """fma in float32: a*b+c exactly, rounded once."""
+    return round_to_f32(Fraction(a) * Fraction(b) + Fraction(c))
