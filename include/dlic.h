@@ -1,0 +1,168 @@
+/*
+ * dlic.h - C ABI of the DLIC coding library (CUDA, sm_103a).
+ *
+ * DLIC (Barzen, Glazov, Geistert, Sikora, "Accelerated Deep Lossless Image
+ * Coding with Unified Parallelized GPU Coding Architecture") codes an 8-bit
+ * grayscale image pixel by pixel: a small dense network estimates the PDF of
+ * each pixel from its causal neighbours (Eq. 1, Sec. II-A), the PDF drives
+ * an rANS entropy coder (Sec. II-B "rANS"), and encoding and decoding run on
+ * the GPU as wavefronts so that every pixel whose neighbours are known is
+ * coded in parallel (Sec. II-B "Preprocessor", Fig. 1 right).  The whole
+ * coder runs on the device; the host only moves the image in and the
+ * bitstream out (Sec. II-B, last paragraph of "Preprocessor").
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are device pointers (cudaMalloc'd or equivalent) on
+ *    the current CUDA device; pointers named h_* are host pointers.  The
+ *    caller owns all of them.  The library allocates device memory only in
+ *    dlic_model_create and dlic_trainer_create and frees it in the matching
+ *    destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work on it and return without synchronising.
+ *  - Errors the host can see (bad arguments, too small buffers) are returned
+ *    at once and nothing is enqueued; dlic_last_error() then describes them.
+ *    Errors found by the device (a corrupt bitstream, a wait that timed out)
+ *    are written to the per-image d_status array of the decoding call.
+ *  - Every call is thread-safe for distinct output buffers; a model may be
+ *    shared by concurrent calls on different streams.
+ */
+#ifndef DLIC_H
+#define DLIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DLIC_API __attribute__((visibility("default")))
+#else
+#define DLIC_API
+#endif
+
+typedef enum {
+    DLIC_OK = 0,
+    DLIC_ERR_INVALID = 1,      /* bad argument or malformed model blob */
+    DLIC_ERR_CAPACITY = 2,     /* output or workspace buffer too small */
+    DLIC_ERR_CORRUPT = 3,      /* bitstream does not decode (device status) */
+    DLIC_ERR_TIMEOUT = 4,      /* a device-side wait ran out (device status) */
+    DLIC_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    DLIC_ERR_UNSUPPORTED = 6   /* valid request this build does not support */
+} dlic_status;
+
+enum { DLIC_FP32 = 0, DLIC_INT8 = 1 };
+
+typedef struct dlic_model dlic_model;
+typedef struct dlic_trainer dlic_trainer;
+
+/* One 8-bit grayscale image in device memory: row r starts at
+ * pixels + r * pitch; pitch >= width.  dlic_encode only reads the pixels,
+ * dlic_decode writes them. */
+typedef struct {
+    uint8_t *pixels;
+    int32_t height;
+    int32_t width;
+    int64_t pitch;
+} dlic_image;
+
+/* Thread-local description of the last error returned by this thread. */
+DLIC_API const char *dlic_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Models                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Creates a coder model from a model blob (host memory, little-endian):
+ *   "DLM1", u32 precision (DLIC_FP32 / DLIC_INT8), u32 12, u32 h1, u32 h2,
+ *   u32 256, u32 radius = 2, f32 tscale, u32 lut[64], then the three dense
+ *   layers (FP32: W f32[out][in] and b f32[out] per layer; INT8: W i8[out][in],
+ *   s f32[out], o f32[out] per layer).
+ * The network maps the 12 causal priors of a pixel to 256 logits (Sec. II-B,
+ * "Neural Network Architecture": dense layers, a 256-way softmax output).
+ * h1 and h2 must be multiples of 16 in [16, 256].  The blob is copied; the
+ * model owns device copies of the weights in the layouts the kernels use.
+ * The model hash (FNV-1a 64 of the blob) is written into every bitstream and
+ * checked by the decoder.  Returns DLIC_ERR_INVALID for a malformed blob. */
+DLIC_API dlic_status dlic_model_create(const void *h_blob, size_t blob_bytes, dlic_model **out);
+
+/* Frees the model's device memory.  No call using the model may still be in
+ * flight on any stream. */
+DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
+
+/* Precision tag, hidden widths and hash of a model. */
+DLIC_API dlic_status dlic_model_info(const dlic_model *model, int *precision, int *h1, int *h2,
+                            uint64_t *hash);
+
+/* ---------------------------------------------------------------------- */
+/* Encoding (Sec. II-A Fig. 2 left; Sec. II-B)                             */
+/* ---------------------------------------------------------------------- */
+
+/* Upper bound, in bytes, of the bitstream of one height x width image coded
+ * with `streams` rANS streams (clipped to the height): a 24-byte header,
+ * 4 bytes per stream, and at most one 16-bit word per pixel plus two flush
+ * words per stream. */
+DLIC_API size_t dlic_max_encoded_bytes(int height, int width, int streams);
+
+/* Stream count the library picks when the caller passes none: one stream
+ * per pixel a wave can hold, min(height, ceil(width / 3)), so that no two
+ * pixels of a wave share a stream (Sec. II-B "rANS": at most one coder
+ * instance per row). */
+DLIC_API int dlic_auto_streams(int height, int width);
+
+/* Device workspace, in bytes, that dlic_encode needs for this batch. */
+DLIC_API dlic_status dlic_encode_workspace_size(const dlic_model *model, const dlic_image *h_images, int n,
+                                       const int *h_streams, size_t *bytes);
+
+/* Encodes n images (descriptors in host memory, pixels on the device).
+ *  h_streams:     n stream counts, or NULL for dlic_auto_streams; each is
+ *                 clipped to its image height (at most one stream per row,
+ *                 Sec. II-B "rANS") and must be in [1, 65535].
+ *  d_out:         receives the n bitstreams back to back; out_capacity must
+ *                 be at least the sum of dlic_max_encoded_bytes over the
+ *                 batch (checked on the host: DLIC_ERR_CAPACITY).
+ *  d_out_offsets: n + 1 u64 byte offsets written by the device; bitstream i
+ *                 occupies [d_out_offsets[i], d_out_offsets[i + 1]).
+ *  d_workspace:   at least dlic_encode_workspace_size bytes, 256-aligned.
+ * Bitstream layout (little-endian): "DLC1", u32 height, u32 width,
+ * u8 radius (2), u8 precision, u16 S, u64 model hash, u32 words[S], then S
+ * payloads of u16 words; each payload opens with the final rANS state (high
+ * half first) and continues with the renormalisation words in the order the
+ * decoder reads them.  Row r is coded by stream r mod S; a stream's pixels
+ * are ordered by wave t = 3r + c, then by row. */
+DLIC_API dlic_status dlic_encode(const dlic_model *model, const dlic_image *h_images, int n,
+                        const int *h_streams, void *d_out, size_t out_capacity,
+                        uint64_t *d_out_offsets, void *d_workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Decoding (Sec. II-A Fig. 2 right; Sec. II-B "Preprocessor" wavefront)   */
+/* ---------------------------------------------------------------------- */
+
+/* Parses a bitstream header held in host memory (at least 24 bytes). */
+DLIC_API dlic_status dlic_read_header(const void *h_bitstream, size_t bytes, int *height, int *width,
+                             int *streams, int *precision, uint64_t *model_hash);
+
+/* Device workspace, in bytes, that dlic_decode needs for this batch. */
+DLIC_API dlic_status dlic_decode_workspace_size(const dlic_model *model, const dlic_image *h_images, int n,
+                                       size_t *bytes);
+
+/* Decodes n bitstreams held back to back in device memory d_in; bitstream i
+ * occupies bytes [h_in_offsets[i], h_in_offsets[i + 1]) (host array of
+ * n + 1 offsets, each even).  h_images[i] gives the destination buffer and
+ * the dimensions the caller expects (from dlic_read_header).  Pixels are
+ * decoded as a wavefront: wave t holds the pixels with 3r + c = t, all of
+ * whose causal priors lie on earlier waves, and each wave's pixels are
+ * predicted and decoded in parallel.  d_status (n int32, device) receives
+ * DLIC_OK or DLIC_ERR_CORRUPT per image (header mismatch, model hash
+ * mismatch, stream overrun, or a final state other than the initial one). */
+DLIC_API dlic_status dlic_decode(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,
+                        int n, const dlic_image *h_images, int32_t *d_status, void *d_workspace,
+                        size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DLIC_H */

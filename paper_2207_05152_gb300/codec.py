@@ -1,0 +1,112 @@
+"""PyTorch-facing wrapper of the C ABI: device buffers come from torch, work is
+enqueued on torch's current CUDA stream, and every coding step runs in
+libdlic.so."""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Codec:
+    """One coder model on the current CUDA device (Sec. II-B: the same model
+    and the same arithmetic at encode and decode)."""
+
+    def __init__(self, blob: bytes):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DLIC library needs a CUDA device")
+        self.blob = bytes(blob)
+        self.handle = _lib.dlic_model_create(self.blob)
+        self.precision, self.h1, self.h2, self.hash = _lib.dlic_model_info(self.handle)
+        self._ws = None
+
+    def close(self):
+        if self.handle:
+            _lib.dlic_model_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _workspace(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(256, nbytes)
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    @staticmethod
+    def _desc(imgs):
+        out = []
+        for t in imgs:
+            if t.dtype != torch.uint8 or t.dim() != 2 or not t.is_cuda:
+                raise ValueError("images must be 2-D uint8 CUDA tensors")
+            if t.stride(1) != 1:
+                raise ValueError("image rows must be contiguous")
+            out.append((t.data_ptr(), t.shape[0], t.shape[1], t.stride(0)))
+        return out
+
+    def capacity(self, shapes, streams=None) -> int:
+        streams = streams or [_lib.dlic_auto_streams(h, w) for h, w in shapes]
+        return sum(_lib.dlic_max_encoded_bytes(h, w, s) for (h, w), s in zip(shapes, streams))
+
+    def encode(self, images, streams=None, out=None, offsets=None, stream=None):
+        """Encodes a list of 2-D uint8 CUDA tensors.  Returns (bytes tensor,
+        offsets tensor of n + 1 int64 on the device)."""
+        desc = self._desc(images)
+        shapes = [(d[1], d[2]) for d in desc]
+        cap = self.capacity(shapes, streams)
+        if out is None or out.numel() < cap:
+            out = torch.empty(max(cap, 1), dtype=torch.uint8, device="cuda")
+        if offsets is None:
+            offsets = torch.empty(len(desc) + 1, dtype=torch.int64, device="cuda")
+        ws_bytes = _lib.dlic_encode_workspace_size(self.handle, desc, streams)
+        ws = self._workspace(ws_bytes)
+        _lib.dlic_encode(self.handle, desc, streams, out.data_ptr(), out.numel(), offsets.data_ptr(),
+                         ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return out, offsets
+
+    def encode_to_bytes(self, images, streams=None):
+        """Host bytes of each image's bitstream (synchronises)."""
+        out, offsets = self.encode(images, streams)
+        offs = offsets.cpu().tolist()
+        host = out[: offs[-1]].cpu().numpy().tobytes()
+        return [host[offs[i]:offs[i + 1]] for i in range(len(images))]
+
+    def decode(self, data: torch.Tensor, offsets, shapes, outs=None, status=None, stream=None):
+        """Decodes bitstreams held back to back in a uint8 CUDA tensor;
+        offsets is a host sequence of n + 1 byte offsets.  Returns (list of
+        decoded uint8 tensors, int32 status tensor on the device)."""
+        n = len(shapes)
+        if outs is None:
+            outs = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for h, w in shapes]
+        if status is None:
+            status = torch.empty(max(1, n), dtype=torch.int32, device="cuda")
+        desc = self._desc(outs)
+        ws_bytes = _lib.dlic_decode_workspace_size(self.handle, desc)
+        ws = self._workspace(ws_bytes)
+        _lib.dlic_decode(self.handle, data.data_ptr(), [int(o) for o in offsets], desc,
+                         status.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return outs, status
+
+    def decode_bytes(self, streams_bytes, shapes=None):
+        """Decodes host bitstreams; returns (list of uint8 host arrays, statuses)."""
+        if shapes is None:
+            shapes = []
+            for b in streams_bytes:
+                h = _lib.dlic_read_header(b)
+                shapes.append((h["height"], h["width"]))
+        offs = [0]
+        for b in streams_bytes:
+            offs.append(offs[-1] + len(b))
+        data = torch.frombuffer(bytearray(b"".join(streams_bytes) or b"\0"), dtype=torch.uint8).cuda()
+        outs, status = self.decode(data, offs, shapes)
+        torch.cuda.synchronize()
+        return [o.cpu().numpy() for o in outs], status[: len(shapes)].cpu().tolist()

@@ -1,0 +1,381 @@
+// C ABI of libdlic: model set-up, workspace planning and the encode / decode
+// entry points declared in include/dlic.h.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dlic {
+
+static thread_local char g_err[512] = "";
+
+dlic_status fail(dlic_status code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+dlic_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(DLIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st);
+cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
+
+cudaError_t launch_predict(const DevModel &m, const EncBatch &b, cudaStream_t st) {
+    return launch_predict_cc(m, b, st);
+}
+
+cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st) {
+    return launch_decode_cc(m, b, st);
+}
+
+static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static uint32_t le32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+static float lef32(const uint8_t *p) {
+    uint32_t u = le32(p);
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+static uint64_t fnv1a64(const uint8_t *p, size_t n) {
+    uint64_t h = 0xCBF29CE484222325ull;
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 0x100000001B3ull;
+    }
+    return h;
+}
+
+}  // namespace dlic
+
+using namespace dlic;
+
+struct dlic_model {
+    DevModel dev;
+    void *mem = nullptr;
+    int device = 0;
+};
+
+extern "C" const char *dlic_last_error(void) { return g_err; }
+
+extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_model **out) {
+    if (!h_blob || !out) return fail(DLIC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const uint8_t *b = static_cast<const uint8_t *>(h_blob);
+    if (n < 288 || memcmp(b, "DLM1", 4) != 0) return fail(DLIC_ERR_INVALID, "not a DLIC model blob");
+    const uint32_t prec = le32(b + 4), n_in = le32(b + 8), h1 = le32(b + 12), h2 = le32(b + 16),
+                   n_out = le32(b + 20), radius = le32(b + 24);
+    if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
+    if (n_in != kPriors || n_out != kSymbols || radius != 2)
+        return fail(DLIC_ERR_INVALID, "model must map 12 radius-2 priors to 256 logits");
+    if (h1 < 16 || h1 > kMaxHidden || h1 % 16 || h2 < 16 || h2 > kMaxHidden || h2 % 16)
+        return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
+    const float tscale = lef32(b + 28);
+    if (!(tscale > 0.0f)) return fail(DLIC_ERR_INVALID, "tscale must be positive");
+    uint32_t lut[64];
+    for (int k = 0; k < 64; k++) {
+        lut[k] = le32(b + 32 + 4 * k);
+        if (lut[k] > (1u << 23)) return fail(DLIC_ERR_INVALID, "lut entries must be <= 2^23");
+    }
+    if (lut[0] != (1u << 23)) return fail(DLIC_ERR_INVALID, "lut[0] must be 2^23");
+    const int din[3] = {kPriors, (int)h1, (int)h2}, dout[3] = {(int)h1, (int)h2, kSymbols};
+    size_t need = 288;
+    for (int l = 0; l < 3; l++)
+        need += prec == 0 ? 4ull * din[l] * dout[l] + 4ull * dout[l] : (size_t)din[l] * dout[l] + 8ull * dout[l];
+    if (need != n) return fail(DLIC_ERR_INVALID, "blob size %zu does not match its header (%zu)", n, need);
+
+    // Host image of the device buffer.
+    std::vector<uint8_t> host;
+    auto put = [&](const void *src, size_t bytes) {
+        size_t off = align256(host.size());
+        host.resize(off + bytes);
+        memcpy(host.data() + off, src, bytes);
+        return off;
+    };
+    DevModel d{};
+    d.precision = (int)prec;
+    d.h1 = (int)h1;
+    d.h2 = (int)h2;
+    d.tscale = tscale;
+    d.hash = fnv1a64(b, n);
+    size_t off_lut = put(lut, sizeof(lut));
+    size_t offs[16] = {0};
+    const uint8_t *p = b + 288;
+    if (prec == DLIC_FP32) {
+        for (int l = 0; l < 3; l++) {
+            std::vector<float> wt((size_t)din[l] * dout[l]), bias(dout[l]);
+            for (int j = 0; j < dout[l]; j++)
+                for (int k = 0; k < din[l]; k++) wt[(size_t)k * dout[l] + j] = lef32(p + 4 * ((size_t)j * din[l] + k));
+            p += 4ull * din[l] * dout[l];
+            for (int j = 0; j < dout[l]; j++) bias[j] = lef32(p + 4 * j);
+            p += 4ull * dout[l];
+            offs[2 * l] = put(wt.data(), wt.size() * 4);
+            offs[2 * l + 1] = put(bias.data(), bias.size() * 4);
+        }
+    } else {
+        for (int l = 0; l < 3; l++) {
+            const int k4n = (din[l] + 3) / 4;
+            std::vector<uint32_t> qt((size_t)k4n * dout[l], 0u);
+            for (int j = 0; j < dout[l]; j++)
+                for (int k = 0; k < din[l]; k++)
+                    qt[(size_t)(k / 4) * dout[l] + j] |= (uint32_t)p[(size_t)j * din[l] + k] << (8 * (k % 4));
+            p += (size_t)din[l] * dout[l];
+            std::vector<float> s(dout[l]), o(dout[l]);
+            for (int j = 0; j < dout[l]; j++) s[j] = lef32(p + 4 * j);
+            p += 4ull * dout[l];
+            for (int j = 0; j < dout[l]; j++) o[j] = lef32(p + 4 * j);
+            p += 4ull * dout[l];
+            offs[3 * l] = put(qt.data(), qt.size() * 4);
+            offs[3 * l + 1] = put(s.data(), s.size() * 4);
+            offs[3 * l + 2] = put(o.data(), o.size() * 4);
+        }
+    }
+    host.resize(align256(host.size()));
+    dlic_model *m = new dlic_model();
+    cudaGetDevice(&m->device);
+    cudaError_t e = cudaMalloc(&m->mem, host.size());
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "cudaMalloc(model)");
+    }
+    e = cudaMemcpy(m->mem, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->mem);
+        delete m;
+        return cuda_fail(e, "cudaMemcpy(model)");
+    }
+    uint8_t *base = static_cast<uint8_t *>(m->mem);
+    d.lut = reinterpret_cast<const uint32_t *>(base + off_lut);
+    if (prec == DLIC_FP32) {
+        d.w1t = reinterpret_cast<const float *>(base + offs[0]);
+        d.b1 = reinterpret_cast<const float *>(base + offs[1]);
+        d.w2t = reinterpret_cast<const float *>(base + offs[2]);
+        d.b2 = reinterpret_cast<const float *>(base + offs[3]);
+        d.w3t = reinterpret_cast<const float *>(base + offs[4]);
+        d.b3 = reinterpret_cast<const float *>(base + offs[5]);
+    } else {
+        d.q1t = reinterpret_cast<const uint32_t *>(base + offs[0]);
+        d.s1 = reinterpret_cast<const float *>(base + offs[1]);
+        d.o1 = reinterpret_cast<const float *>(base + offs[2]);
+        d.q2t = reinterpret_cast<const uint32_t *>(base + offs[3]);
+        d.s2 = reinterpret_cast<const float *>(base + offs[4]);
+        d.o2 = reinterpret_cast<const float *>(base + offs[5]);
+        d.q3t = reinterpret_cast<const uint32_t *>(base + offs[6]);
+        d.s3 = reinterpret_cast<const float *>(base + offs[7]);
+        d.o3 = reinterpret_cast<const float *>(base + offs[8]);
+    }
+    m->dev = d;
+    *out = m;
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_model_destroy(dlic_model *m) {
+    if (!m) return DLIC_OK;
+    cudaError_t e = cudaFree(m->mem);
+    delete m;
+    return e == cudaSuccess ? DLIC_OK : cuda_fail(e, "cudaFree(model)");
+}
+
+extern "C" dlic_status dlic_model_info(const dlic_model *m, int *precision, int *h1, int *h2,
+                                       uint64_t *hash) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (precision) *precision = m->dev.precision;
+    if (h1) *h1 = m->dev.h1;
+    if (h2) *h2 = m->dev.h2;
+    if (hash) *hash = m->dev.hash;
+    return DLIC_OK;
+}
+
+extern "C" size_t dlic_max_encoded_bytes(int height, int width, int streams) {
+    if (height < 1 || width < 1 || streams < 1) return 0;
+    const int S = streams < height ? streams : height;
+    return (size_t)kHeaderBytes + 4ull * S + 2ull * ((size_t)height * width + 2ull * S);
+}
+
+extern "C" int dlic_auto_streams(int height, int width) {
+    if (height < 1 || width < 1) return 0;
+    int s = (width + 2) / 3;
+    if (s > height) s = height;
+    if (s > 65535) s = 65535;
+    return s < 1 ? 1 : s;
+}
+
+static dlic_status check_images(const dlic_image *im, int n, const int *streams, bool writable) {
+    if (n < 0) return fail(DLIC_ERR_INVALID, "negative image count");
+    if (n > 0 && !im) return fail(DLIC_ERR_INVALID, "null image array");
+    for (int i = 0; i < n; i++) {
+        if (!im[i].pixels) return fail(DLIC_ERR_INVALID, "image %d: null pixels", i);
+        if (im[i].height < 1 || im[i].width < 1)
+            return fail(DLIC_ERR_INVALID, "image %d: empty image (%d x %d)", i, im[i].height, im[i].width);
+        if (im[i].height > (1 << 20) || im[i].width > (1 << 20))
+            return fail(DLIC_ERR_UNSUPPORTED, "image %d: dimension above 2^20", i);
+        if (im[i].pitch < im[i].width) return fail(DLIC_ERR_INVALID, "image %d: pitch < width", i);
+        if (streams && (streams[i] < 1 || streams[i] > 65535))
+            return fail(DLIC_ERR_INVALID, "image %d: stream count %d outside [1, 65535]", i, streams[i]);
+    }
+    (void)writable;
+    return DLIC_OK;
+}
+
+static int clip_streams(const dlic_image &im, const int *streams, int i) {
+    int s = streams ? streams[i] : dlic_auto_streams(im.height, im.width);
+    return s < im.height ? s : im.height;
+}
+
+static size_t enc_image_bytes(int H, int W, int S) {
+    const size_t N = (size_t)H * W;
+    return align256(4 * N) + align256(2 * (N + 2ull * S)) + 3 * align256(4ull * S);
+}
+
+extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
+                                                  const int *streams, size_t *bytes) {
+    if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
+    dlic_status st = check_images(im, n, streams, false);
+    if (st) return st;
+    size_t total = align256(8ull * (n + 1));
+    for (int i = 0; i < n; i++) total += enc_image_bytes(im[i].height, im[i].width, clip_streams(im[i], streams, i));
+    *bytes = total;
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, int n, const int *streams,
+                                   void *d_out, size_t out_capacity, uint64_t *d_out_offsets,
+                                   void *d_ws, size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    dlic_status st = check_images(im, n, streams, false);
+    if (st) return st;
+    if (n == 0) return DLIC_OK;
+    if (!d_out || !d_out_offsets || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(DLIC_ERR_INVALID, "workspace must be 256-byte aligned");
+    size_t need_ws = 0, need_out = 0;
+    dlic_encode_workspace_size(m, im, n, streams, &need_ws);
+    for (int i = 0; i < n; i++) need_out += dlic_max_encoded_bytes(im[i].height, im[i].width, clip_streams(im[i], streams, i));
+    if (ws_bytes < need_ws) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need_ws);
+    if (out_capacity < need_out) return fail(DLIC_ERR_CAPACITY, "output capacity %zu < %zu bytes", out_capacity, need_out);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    size_t off = align256(8ull * (n + 1));
+    uint64_t *sizes = reinterpret_cast<uint64_t *>(ws);
+    uint8_t *out = static_cast<uint8_t *>(d_out);
+    for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
+        const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
+        EncBatch *b = new EncBatch();
+        b->n = cn;
+        b->ws = ws;
+        b->sizes = sizes + c0;
+        b->chunk_start = c0;
+        int tiles = 0, total_streams = 0;
+        for (int k = 0; k < cn; k++) {
+            const dlic_image &g = im[c0 + k];
+            EncImage &e = b->img[k];
+            e.pixels = g.pixels;
+            e.pitch = g.pitch;
+            e.H = g.height;
+            e.W = g.width;
+            e.S = clip_streams(g, streams, c0 + k);
+            e.tile_begin = tiles;
+            const size_t N = (size_t)e.H * e.W;
+            tiles += (int)((N + kPredictTile - 1) / kPredictTile);
+            total_streams += e.S;
+            e.fc_off = off;
+            off += align256(4 * N);
+            e.words_off = off;
+            off += align256(2 * (N + 2ull * e.S));
+            e.cnt_off = off;
+            off += align256(4ull * e.S);
+            e.xfin_off = off;
+            off += align256(4ull * e.S);
+            e.soff_off = off;
+            off += align256(4ull * e.S);
+        }
+        b->total_tiles = tiles;
+        cudaError_t e = launch_predict(m->dev, *b, cs);
+        if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
+        if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
+        delete b;
+        if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+    }
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_read_header(const void *h_bits, size_t bytes, int *height, int *width,
+                                        int *streams, int *precision, uint64_t *hash) {
+    const uint8_t *h = static_cast<const uint8_t *>(h_bits);
+    if (!h || bytes < (size_t)kHeaderBytes || memcmp(h, "DLC1", 4) != 0 || h[12] != 2)
+        return fail(DLIC_ERR_CORRUPT, "not a DLIC bitstream");
+    if (height) *height = (int)le32(h + 4);
+    if (width) *width = (int)le32(h + 8);
+    if (precision) *precision = h[13];
+    if (streams) *streams = h[14] | (h[15] << 8);
+    if (hash) {
+        uint64_t v = 0;
+        for (int k = 0; k < 8; k++) v |= (uint64_t)h[16 + k] << (8 * k);
+        *hash = v;
+    }
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_decode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
+                                                  size_t *bytes) {
+    if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
+    dlic_status st = check_images(im, n, nullptr, true);
+    if (st) return st;
+    size_t total = 0;
+    for (int i = 0; i < n; i++) total += align256(16ull * im[i].height);
+    *bytes = total < 256 ? 256 : total;
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const uint64_t *h_in_offsets,
+                                   int n, const dlic_image *im, int32_t *d_status, void *d_ws,
+                                   size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    dlic_status st = check_images(im, n, nullptr, true);
+    if (st) return st;
+    if (n == 0) return DLIC_OK;
+    if (!d_in || !h_in_offsets || !d_status || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
+    size_t need = 0;
+    dlic_decode_workspace_size(m, im, n, &need);
+    if (ws_bytes < need) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need);
+    for (int i = 0; i < n; i++) {
+        if (h_in_offsets[i + 1] < h_in_offsets[i]) return fail(DLIC_ERR_INVALID, "offsets must not decrease");
+        if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    size_t off = 0;
+    for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
+        const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
+        DecBatch *b = new DecBatch();
+        b->n = cn;
+        b->in = static_cast<const uint8_t *>(d_in);
+        b->ws = static_cast<uint8_t *>(d_ws);
+        b->status = d_status + c0;
+        for (int k = 0; k < cn; k++) {
+            const dlic_image &g = im[c0 + k];
+            DecImage &e = b->img[k];
+            e.pixels = g.pixels;
+            e.pitch = g.pitch;
+            e.H = g.height;
+            e.W = g.width;
+            e.in_off = h_in_offsets[c0 + k];
+            e.in_bytes = h_in_offsets[c0 + k + 1] - h_in_offsets[c0 + k];
+            e.st_off = off;
+            off += align256(16ull * g.height);
+        }
+        cudaError_t e = launch_decode(m->dev, *b, cs);
+        delete b;
+        if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    }
+    return DLIC_OK;
+}

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of libdlic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/dlic.h"
+
+namespace dlic {
+
+constexpr int kPriors = 12;        // radius-2 causal window
+constexpr int kSymbols = 256;      // 8-bit alphabet
+constexpr uint32_t kRansL = 1u << 16;
+constexpr uint32_t kTotal = 1u << 16;
+constexpr uint32_t kQuantTotal = 65280u;   // 2^16 - 256: mass shared out by the PDF
+constexpr int kHeaderBytes = 24;
+constexpr int kMaxHidden = 256;
+
+// Device-side view of a model (passed to kernels by value).
+struct DevModel {
+    int precision;   // DLIC_FP32 / DLIC_INT8
+    int h1, h2;
+    float tscale;
+    const uint32_t *lut;          // 64 entries
+    // FP32 network, transposed: WkT[k * out + j] = W[j][k]
+    const float *w1t, *b1, *w2t, *b2, *w3t, *b3;
+    // INT8 network, packed 4 inputs per u32 and transposed:
+    // QkT[k4 * out + j] = bytes W[j][4*k4 .. 4*k4+3]
+    const uint32_t *q1t, *q2t, *q3t;
+    const float *s1, *o1, *s2, *o2, *s3, *o3;
+    // INT8 network as bf16 (integer-valued) in tcgen05 shared-memory layout
+    const uint16_t *tc_w;         // packed image of W1|W2|W3 operand tiles
+    uint32_t tc_w_bytes;
+    uint64_t hash;
+};
+
+// Per-image encode descriptor.
+struct EncImage {
+    const uint8_t *pixels;
+    int64_t pitch;
+    int32_t H, W, S;
+    int32_t tile_begin;           // first 128-pixel tile of this image
+    uint64_t fc_off;              // u32 (f | c << 16) per pixel, raster order
+    uint64_t words_off;           // u16 renormalisation words, per stream region
+    uint64_t cnt_off;             // u32 words per stream (incl. 2 flush words)
+    uint64_t xfin_off;            // u32 final state per stream
+    uint64_t soff_off;            // u32 payload offset of each stream (words)
+};
+
+constexpr int kMaxBatch = 192;    // images per launch (kernel-parameter space)
+constexpr int kPredictTile = 64;  // pixels per prediction CTA
+
+struct EncBatch {
+    int n;
+    int chunk_start;              // index of img[0] in the caller's batch
+    int total_tiles;
+    uint8_t *ws;                  // workspace base
+    uint64_t *sizes;              // per image bitstream bytes (in workspace)
+    EncImage img[kMaxBatch];
+};
+
+struct DecImage {
+    uint8_t *pixels;
+    int64_t pitch;
+    int32_t H, W;
+    uint64_t in_off;              // byte offset of the bitstream in d_in
+    uint64_t in_bytes;
+    uint64_t st_off;              // per-stream state (x, pos, end) in workspace
+};
+
+struct DecBatch {
+    int n;
+    const uint8_t *in;
+    uint8_t *ws;
+    int32_t *status;
+    DecImage img[kMaxBatch];
+};
+
+// Sets the thread-local error text and returns the code.
+dlic_status fail(dlic_status code, const char *fmt, ...);
+dlic_status cuda_fail(cudaError_t e, const char *what);
+
+// Kernel launchers (predict.cu, rans.cu)
+cudaError_t launch_predict(const DevModel &m, const EncBatch &b, cudaStream_t st);
+cudaError_t launch_rans_encode(const EncBatch &b, int total_streams, cudaStream_t st);
+cudaError_t launch_pack(const DevModel &m, const EncBatch &b, uint8_t *out,
+                        uint64_t *out_offsets, cudaStream_t st);
+cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st);
+
+// Number of pixels of stream s (rows s, s + S, ...) and the first word of its
+// scratch region: every earlier stream holds its pixels plus two flush words.
+__host__ __device__ inline int64_t stream_rows(int H, int S, int s) {
+    return (H - s + S - 1) / S;
+}
+__host__ __device__ inline int64_t stream_word_base(int H, int W, int S, int s) {
+    int64_t rows_before = (int64_t)(H / S) * s + (s < H % S ? s : H % S);
+    return rows_before * W + 2 * (int64_t)s;
+}
+
+}  // namespace dlic

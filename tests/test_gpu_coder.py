@@ -1,0 +1,112 @@
+"""GPU parity: the CUDA coder against the oracle, bit for bit.
+
+Bitstreams (header, word counts, every payload word) and decoded pixels must
+be identical to the oracle's for the same seeded inputs (Sec. II-B
+"Preprocessor": encoder and decoder must see the same network inputs and
+produce the same PDFs; the image is reproduced losslessly)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_2207_05152_gb300 import model as M
+from tests.helpers import calib_contexts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Codec():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_05152_gb300.codec import Codec
+    return Codec
+
+
+def _models(widths, seed, images):
+    layers = synth.predictive_mlp(widths, seed)
+    return {"fp32": M.fp32_blob(layers), "int8": M.int8_blob(layers, calib_contexts(images))}
+
+
+def _check(Codec, orc, blob, imgs, streams):
+    codec = Codec(blob)
+    got = codec.encode_to_bytes([torch.from_numpy(np.ascontiguousarray(i)).cuda() for i in imgs], streams)
+    for k, img in enumerate(imgs):
+        want = orc.encode(blob, img, streams[k] if streams else min(img.shape[0], (img.shape[1] + 2) // 3))
+        assert got[k] == want, f"image {k}: bitstream differs from the oracle"
+    dec, status = codec.decode_bytes(got)
+    assert status == [0] * len(imgs)
+    for k, img in enumerate(imgs):
+        assert np.array_equal(dec[k], img)
+    codec.close()
+    return got
+
+
+def test_cfg1_fp32_64x64_s32(Codec, orc):
+    img = synth.config_image(1)
+    blob = M.fp32_blob(synth.predictive_mlp([12, 64, 64, 256], 1))
+    _check(Codec, orc, blob, [img], [32])
+
+
+@pytest.mark.parametrize("prec", ["int8", "fp32"])
+def test_cfg2_512x512_s256(Codec, orc, prec):
+    img = synth.config_image(2)
+    blob = _models([12, 128, 128, 256], 2, [img])[prec]
+    _check(Codec, orc, blob, [img], [256])
+
+
+SHAPES = [(1, 1, 1), (1, 7, 1), (7, 1, 4), (2, 3, 2), (5, 64, 9), (16, 16, 16), (13, 40, 3),
+          (9, 50, 1), (33, 17, 32), (3, 200, 2), (70, 130, 70), (80, 250, 7)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "int8"])
+def test_edge_shapes(Codec, orc, prec):
+    imgs = [synth.value_noise_image(h, w, 7 * h + w) for h, w, _ in SHAPES]
+    blob = _models([12, 32, 48, 256], 5, [synth.voronoi_image(40, 40, 2)])[prec]
+    _check(Codec, orc, blob, imgs, [s for _, _, s in SHAPES])
+
+
+def test_auto_streams_and_batch(Codec, orc):
+    imgs = synth.batch_images(6, 31, hmin=20, hmax=90, wmin=30, wmax=160)
+    blob = _models([12, 128, 128, 256], 3, imgs[:2])["int8"]
+    _check(Codec, orc, blob, imgs, None)
+
+
+def test_pitched_image(Codec, orc):
+    img = synth.voronoi_image(40, 50, 3)
+    blob = _models([12, 64, 64, 256], 4, [img])["int8"]
+    codec = Codec(blob)
+    big = torch.zeros((40, 64), dtype=torch.uint8, device="cuda")
+    big[:, :50] = torch.from_numpy(img).cuda()
+    got = codec.encode_to_bytes([big[:, :50]], [8])[0]
+    assert got == orc.encode(blob, img, 8)
+    codec.close()
+
+
+def test_corrupt_and_capacity(Codec, orc):
+    from paper_2207_05152_gb300 import _lib
+    img = synth.value_noise_image(20, 30, 2)
+    blob = _models([12, 32, 32, 256], 6, [img])["fp32"]
+    codec = Codec(blob)
+    data = bytearray(orc.encode(blob, img, 4))
+    _, st = codec.decode_bytes([bytes(data[:-2])], [(20, 30)])
+    assert st == [_lib.DLIC_ERR_CORRUPT]
+    bad = bytearray(data)
+    bad[16] ^= 1                                   # model hash
+    _, st = codec.decode_bytes([bytes(bad)], [(20, 30)])
+    assert st == [_lib.DLIC_ERR_CORRUPT]
+    bad = bytearray(data)
+    bad[24 + 16] ^= 0x80                           # first flush word of stream 0
+    dec, st = codec.decode_bytes([bytes(bad)], [(20, 30)])
+    assert st == [_lib.DLIC_ERR_CORRUPT] or not np.array_equal(dec[0], img)
+    want_status, want_img = orc.decode(blob, bytes(bad), 20, 30)
+    assert (st[0] == 0) == (want_status == 0)
+    t = torch.from_numpy(img).cuda()
+    out = torch.empty(16, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(2, dtype=torch.int64, device="cuda")
+    ws = codec._workspace(1 << 20)
+    with pytest.raises(_lib.DlicError) as e:
+        _lib.dlic_encode(codec.handle, codec._desc([t]), [4], out.data_ptr(), out.numel(),
+                         offs.data_ptr(), ws.data_ptr(), ws.numel(), 0)
+    assert e.value.code == _lib.DLIC_ERR_CAPACITY
+    codec.close()
