@@ -1,0 +1,345 @@
+"""DLIC coding benchmark: encode + wavefront decode of a 512 x 512 8-bit
+image with the INT8 network 12 -> 128 -> 128 -> 256 and 256 rANS streams,
+bit-exact round trip, reported in Mpixel/s.
+
+One step = dlic_encode + dlic_decode of the image (every coding step of the
+path: gather, network, table, rANS encode, packing, wavefront decode).  The
+L2 cache is flushed (a 256 MiB write) before every timed step.  Extra keys
+report the plain FP32 network on the same image, the bit rate, and the
+oracle timed on the host as a baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 512
+STREAMS = 256
+WIDTHS = [12, 128, 128, 256]
+IMAGE_SEED_CFG = 2
+LAUNCHES_PER_STEP = {"encode": 5, "decode": 1}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    import numpy as np
+    import synth
+    from paper_2207_05152_gb300 import model as M
+    img = synth.config_image(IMAGE_SEED_CFG)
+    layers = synth.predictive_mlp(WIDTHS, 2)
+    # calibration contexts from a different synthetic image of the same kind
+    cal_img = synth.voronoi_image(256, 256, 4242)
+    rng = synth.Rng(4243)
+    rr = rng.integers(4096, 0, 255)
+    cc = rng.integers(4096, 0, 255)
+    pad = np.zeros((258, 260), np.uint8)
+    pad[2:, 2:258] = cal_img
+    cal = np.stack([np.concatenate([pad[r:r + 2, c:c + 5].reshape(-1), pad[r + 2, c:c + 2]])
+                    for r, c in zip(rr, cc)])
+    return img, layers, M.int8_blob(layers, cal), M.fp32_blob(layers)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and (not self.uuid or self.uuid in parts[0]):
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _gpu_uuid():
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return ""
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p["hbm_gbs"], p["bf16_tflops"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    from paper_2207_05152_gb300.codec import Codec
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g.build() if rank == 0 or ws == 1 else None
+    if ws > 1:
+        dist.barrier()
+    img, layers, blob8, blob32 = _workload()
+    N = H * W
+    dev_img = torch.from_numpy(img).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def measure(blob, steps, warmup, clocks=False):
+        codec = Codec(blob)
+        out = torch.empty(codec.capacity([(H, W)], [STREAMS]), dtype=torch.uint8, device="cuda")
+        offs = torch.empty(2, dtype=torch.int64, device="cuda")
+        dec = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        status = torch.empty(1, dtype=torch.int32, device="cuda")
+        codec.encode([dev_img], [STREAMS], out=out, offsets=offs)
+        torch.cuda.synchronize()
+        nbytes = int(offs[1].item())
+        enc_ms, dec_ms = [], []
+        sampler = ClockSampler(_gpu_uuid()) if clocks else None
+        for it in range(warmup + steps):
+            timed = it >= warmup
+            if timed and it == warmup:
+                if ws > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                if sampler:
+                    sampler.__enter__()
+                    time.sleep(0.3)
+                t_wall = time.perf_counter()
+            flush.fill_(it & 0xFF)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            codec.encode([dev_img], [STREAMS], out=out, offsets=offs)
+            e1.record(stream)
+            codec.decode(out, [0, nbytes], [(H, W)], outs=[dec], status=status)
+            e2.record(stream)
+            if timed:
+                enc_ms.append((e0, e1))
+                dec_ms.append((e1, e2))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        if ws > 1:
+            dist.barrier()
+        if sampler:
+            sampler.__exit__()
+        enc = [a.elapsed_time(b) for a, b in enc_ms]
+        dcd = [a.elapsed_time(b) for a, b in dec_ms]
+        ok = bool(torch.equal(dec, dev_img)) and int(status.item()) == 0
+        host_bits = out[:nbytes].cpu().numpy().tobytes()
+        codec.close()
+        return dict(enc=enc, dec=dcd, wall=wall, nbytes=nbytes, ok=ok, bits=host_bits,
+                    clocks=sampler.summary() if sampler else None)
+
+    r8 = measure(blob8, args.steps, args.warmup, clocks=True)
+    r32 = measure(blob32, max(2, args.steps // 3), 2)
+
+    # end to end through the public API: pinned host image in, decoded image out
+    codec = Codec(blob8)
+    h_img = torch.from_numpy(img).pin_memory()
+    h_dec = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    h_bits = torch.empty(codec.capacity([(H, W)], [STREAMS]), dtype=torch.uint8).pin_memory()
+    h_offs = torch.empty(2, dtype=torch.int64).pin_memory()
+    e2e_ms = []
+    h2d = d2h = 0
+    for it in range(args.warmup + args.steps):
+        flush.fill_(it & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_img = h_img.cuda(non_blocking=True)
+        out, offs = codec.encode([d_img], [STREAMS])
+        h_offs.copy_(offs, non_blocking=True)
+        torch.cuda.synchronize()
+        nb = int(h_offs[1])
+        h_bits[:nb].copy_(out[:nb], non_blocking=True)
+        d_bits = h_bits[:nb].cuda(non_blocking=True)
+        outs, status = codec.decode(d_bits, [0, nb], [(H, W)])
+        h_dec.copy_(outs[0], non_blocking=True)
+        st = status[:1].cpu()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+            h2d, d2h = N + nb, 16 + nb + N + 4
+        assert int(st[0]) == 0 and torch.equal(h_dec, h_img)
+    codec.close()
+
+    # max over ranks of the timed totals
+    tot8 = sum(r8["enc"]) + sum(r8["dec"])
+    t_e2e = sum(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([tot8, t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot8, t_e2e = t.tolist()
+    K = args.steps
+    value = ws * K * N / (tot8 * 1e-3) / 1e6
+    enc_mean = statistics.mean(r8["enc"])
+    dec_mean = statistics.mean(r8["dec"])
+    bpp = 8.0 * r8["nbytes"] / N
+
+    hbm_peak, bf16_peak, peak_kind = _peaks()
+    ops_per_px = 2 * (12 * 128 + 128 * 128 + 128 * 256)   # MLP multiply-adds x 2
+    dominant = "decode" if dec_mean >= enc_mean else "encode"
+    dom_ms = dec_mean if dominant == "decode" else enc_mean
+    achieved = ops_per_px * N / (dom_ms * 1e-3) / 1e12
+    line = {
+        "metric": "enc+dec Mpix/s at 512x512 (bit-exact roundtrip)",
+        "value": round(value, 3),
+        "unit": "Mpix/s",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(tot8 / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int8",
+        "data": "synthetic",
+        "config": {"workload": "cfg2: one 512x512 8-bit Voronoi image, INT8 MLP 12-128-128-256, "
+                               "256 rANS streams, encode + wavefront decode",
+                   "image": "voronoi 24 cells, seed 2000", "weights": "synthetic predictive (seed 2)",
+                   "streams": STREAMS, "l2": "flushed (256 MiB write) before every step"},
+        "enc_mpix_s": round(N / (enc_mean * 1e-3) / 1e6, 3),
+        "dec_mpix_s": round(N / (dec_mean * 1e-3) / 1e6, 3),
+        "bpp": round(bpp, 4),
+        "roundtrip_bit_exact": r8["ok"],
+        "fp32_path": {"enc_mpix_s": round(N / (statistics.mean(r32["enc"]) * 1e-3) / 1e6, 3),
+                      "dec_mpix_s": round(N / (statistics.mean(r32["dec"]) * 1e-3) / 1e6, 3),
+                      "bpp": round(8.0 * r32["nbytes"] / N, 4), "roundtrip_bit_exact": r32["ok"]},
+        "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
+                     "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
+                     "peak_source": f"bf16 burst, {peak_kind}", "traffic": None},
+        "gpu_launches": K * (LAUNCHES_PER_STEP["encode"] + LAUNCHES_PER_STEP["decode"]),
+        "clocks": r8["clocks"],
+        "e2e": {"value": round(ws * K * N / (t_e2e * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(img, blob8, r8["bits"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(img, blob, gpu_bits):
+    """The oracle as it stands, single-threaded on one host core, coding the
+    same 512 x 512 image (encode + decode)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    bits = oracle.encode(blob, img, STREAMS)
+    st, dec = oracle.decode(blob, bits, H, W)
+    dt = time.perf_counter() - t0
+    return {"value": round(H * W / dt / 1e6, 5), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": "the full 512x512 image, INT8 encode + decode (one pass)",
+            "matches_gpu_bitstream": bits == gpu_bits and st == 0}
+
+
+def run_reference(args):
+    """The oracle (plain C, one host core) on the same workload: each step is
+    a bounded sample, the encode + decode of a 192 x 192 crop of the image."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    img, layers, blob8, _ = _workload()
+    crop = img[:192, :192].copy()
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        bits = oracle.encode(blob8, crop, STREAMS)
+        st, dec = oracle.decode(blob8, bits, 192, 192)
+        dt = time.perf_counter() - t0
+        assert st == 0 and (dec == crop).all()
+        if it >= args.warmup:
+            times.append(dt)
+    K = args.steps
+    value = K * crop.size / sum(times) / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": "enc+dec Mpix/s at 512x512 (bit-exact roundtrip)",
+        "value": round(value, 5), "unit": "Mpix/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / K, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": "cfg2 sample: 192x192 crop of the 512x512 image per step, INT8 MLP "
+                               "12-128-128-256, 256 rANS streams (clipped to 192), encode + decode"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                         "sample": "192x192 crop per step"},
+        "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

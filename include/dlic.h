@@ -124,6 +124,9 @@ DLIC_API dlic_status dlic_encode_workspace_size(const dlic_model *model, const d
  *                 batch (checked on the host: DLIC_ERR_CAPACITY).
  *  d_out_offsets: n + 1 u64 byte offsets written by the device; bitstream i
  *                 occupies [d_out_offsets[i], d_out_offsets[i + 1]).
+ *  d_status:      one int32 on the device, or NULL; receives DLIC_OK, or
+ *                 DLIC_ERR_TIMEOUT if a tensor-core wait ran out (the output
+ *                 is then invalid).
  *  d_workspace:   at least dlic_encode_workspace_size bytes, 256-aligned.
  * Bitstream layout (little-endian): "DLC1", u32 height, u32 width,
  * u8 radius (2), u8 precision, u16 S, u64 model hash, u32 words[S], then S
@@ -132,9 +135,9 @@ DLIC_API dlic_status dlic_encode_workspace_size(const dlic_model *model, const d
  * decoder reads them.  Row r is coded by stream r mod S; a stream's pixels
  * are ordered by wave t = 3r + c, then by row. */
 DLIC_API dlic_status dlic_encode(const dlic_model *model, const dlic_image *h_images, int n,
-                        const int *h_streams, void *d_out, size_t out_capacity,
-                        uint64_t *d_out_offsets, void *d_workspace, size_t workspace_bytes,
-                        void *stream);
+                                 const int *h_streams, void *d_out, size_t out_capacity,
+                                 uint64_t *d_out_offsets, int32_t *d_status, void *d_workspace,
+                                 size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Decoding (Sec. II-A Fig. 2 right; Sec. II-B "Preprocessor" wavefront)   */

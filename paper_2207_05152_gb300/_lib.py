@@ -43,7 +43,7 @@ SIGNATURES = {
     "dlic_max_encoded_bytes": (_SZ, [_I, _I, _I]),
     "dlic_auto_streams": (_I, [_I, _I]),
     "dlic_encode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_I), C.POINTER(_SZ)]),
-    "dlic_encode": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _SZ, _VP]),
+    "dlic_encode": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "dlic_read_header": (_I, [_VP, _SZ, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                               C.POINTER(C.c_uint64)]),
     "dlic_decode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_SZ)]),
@@ -130,10 +130,10 @@ def dlic_encode_workspace_size(model: int, images, streams=None) -> int:
 
 
 def dlic_encode(model: int, images, streams, d_out: int, out_capacity: int, d_out_offsets: int,
-                d_ws: int, ws_bytes: int, stream: int = 0):
+                d_status: int, d_ws: int, ws_bytes: int, stream: int = 0):
     arr, n = images_array(images)
     check(lib().dlic_encode(model, arr, n, int_array(streams), d_out, out_capacity, d_out_offsets,
-                            d_ws, ws_bytes, stream or None))
+                            d_status or None, d_ws, ws_bytes, stream or None))
 
 
 def dlic_read_header(data: bytes):

@@ -57,9 +57,10 @@ class Codec:
         streams = streams or [_lib.dlic_auto_streams(h, w) for h, w in shapes]
         return sum(_lib.dlic_max_encoded_bytes(h, w, s) for (h, w), s in zip(shapes, streams))
 
-    def encode(self, images, streams=None, out=None, offsets=None, stream=None):
+    def encode(self, images, streams=None, out=None, offsets=None, status=None, stream=None):
         """Encodes a list of 2-D uint8 CUDA tensors.  Returns (bytes tensor,
-        offsets tensor of n + 1 int64 on the device)."""
+        offsets tensor of n + 1 int64 on the device); `status`, if given, is
+        a 1-element int32 CUDA tensor that receives the device status."""
         desc = self._desc(images)
         shapes = [(d[1], d[2]) for d in desc]
         cap = self.capacity(shapes, streams)
@@ -70,12 +71,16 @@ class Codec:
         ws_bytes = _lib.dlic_encode_workspace_size(self.handle, desc, streams)
         ws = self._workspace(ws_bytes)
         _lib.dlic_encode(self.handle, desc, streams, out.data_ptr(), out.numel(), offsets.data_ptr(),
-                         ws.data_ptr(), ws.numel(), _stream_handle(stream))
+                         status.data_ptr() if status is not None else 0, ws.data_ptr(), ws.numel(),
+                         _stream_handle(stream))
         return out, offsets
 
     def encode_to_bytes(self, images, streams=None):
         """Host bytes of each image's bitstream (synchronises)."""
-        out, offsets = self.encode(images, streams)
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        out, offsets = self.encode(images, streams, status=status)
+        if int(status.item()) != 0:
+            raise _lib.DlicError(int(status.item()), "device status of dlic_encode")
         offs = offsets.cpu().tolist()
         host = out[: offs[-1]].cpu().numpy().tobytes()
         return [host[offs[i]:offs[i + 1]] for i in range(len(images))]

@@ -24,12 +24,7 @@ dlic_status cuda_fail(cudaError_t e, const char *what) {
     return fail(DLIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st);
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
-
-cudaError_t launch_predict(const DevModel &m, const EncBatch &b, cudaStream_t st) {
-    return launch_predict_cc(m, b, st);
-}
 
 cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st) {
     return launch_decode_cc(m, b, st);
@@ -65,6 +60,7 @@ struct dlic_model {
     DevModel dev;
     void *mem = nullptr;
     int device = 0;
+    int num_sms = 0;
 };
 
 extern "C" const char *dlic_last_error(void) { return g_err; }
@@ -124,6 +120,18 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             offs[2 * l + 1] = put(bias.data(), bias.size() * 4);
         }
     } else {
+        const int8_t *raw[3];
+        const uint8_t *pp = p;
+        for (int l = 0; l < 3; l++) {
+            raw[l] = reinterpret_cast<const int8_t *>(pp);
+            pp += (size_t)din[l] * dout[l] + 8ull * dout[l];
+        }
+        if (h1 <= 128 && h2 <= 128) {
+            std::vector<uint16_t> img(tc_weight_bytes((int)h1, (int)h2) / 2);
+            tc_pack_weights((int)h1, (int)h2, raw[0], raw[1], raw[2], img.data());
+            offs[15] = put(img.data(), img.size() * 2);
+            d.tc_w_bytes = (uint32_t)(img.size() * 2);
+        }
         for (int l = 0; l < 3; l++) {
             const int k4n = (din[l] + 3) / 4;
             std::vector<uint32_t> qt((size_t)k4n * dout[l], 0u);
@@ -144,6 +152,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     host.resize(align256(host.size()));
     dlic_model *m = new dlic_model();
     cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (m->num_sms < 1) m->num_sms = 1;
     cudaError_t e = cudaMalloc(&m->mem, host.size());
     if (e != cudaSuccess) {
         delete m;
@@ -174,6 +184,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         d.q3t = reinterpret_cast<const uint32_t *>(base + offs[6]);
         d.s3 = reinterpret_cast<const float *>(base + offs[7]);
         d.o3 = reinterpret_cast<const float *>(base + offs[8]);
+        if (d.tc_w_bytes) d.tc_w = reinterpret_cast<const uint16_t *>(base + offs[15]);
     }
     m->dev = d;
     *out = m;
@@ -243,7 +254,7 @@ extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dli
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, streams, false);
     if (st) return st;
-    size_t total = align256(8ull * (n + 1));
+    size_t total = align256(8ull * (n + 1)) + 256;
     for (int i = 0; i < n; i++) total += enc_image_bytes(im[i].height, im[i].width, clip_streams(im[i], streams, i));
     *bytes = total;
     return DLIC_OK;
@@ -251,7 +262,7 @@ extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dli
 
 extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, int n, const int *streams,
                                    void *d_out, size_t out_capacity, uint64_t *d_out_offsets,
-                                   void *d_ws, size_t ws_bytes, void *stream) {
+                                   int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {
     if (!m) return fail(DLIC_ERR_INVALID, "null model");
     dlic_status st = check_images(im, n, streams, false);
     if (st) return st;
@@ -267,7 +278,15 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
     size_t off = align256(8ull * (n + 1));
     uint64_t *sizes = reinterpret_cast<uint64_t *>(ws);
+    int32_t *err = d_status ? d_status : reinterpret_cast<int32_t *>(ws + off);
+    off += 256;
     uint8_t *out = static_cast<uint8_t *>(d_out);
+    const bool use_tc = tc_supported(m->dev);
+    const int tile_px = use_tc ? 128 : kPredictTile;
+    {
+        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    }
     for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
         const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
         EncBatch *b = new EncBatch();
@@ -275,6 +294,7 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
         b->ws = ws;
         b->sizes = sizes + c0;
         b->chunk_start = c0;
+        b->tile_px = tile_px;
         int tiles = 0, total_streams = 0;
         for (int k = 0; k < cn; k++) {
             const dlic_image &g = im[c0 + k];
@@ -286,7 +306,7 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
             e.S = clip_streams(g, streams, c0 + k);
             e.tile_begin = tiles;
             const size_t N = (size_t)e.H * e.W;
-            tiles += (int)((N + kPredictTile - 1) / kPredictTile);
+            tiles += (int)((N + tile_px - 1) / tile_px);
             total_streams += e.S;
             e.fc_off = off;
             off += align256(4 * N);
@@ -300,7 +320,7 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
             off += align256(4ull * e.S);
         }
         b->total_tiles = tiles;
-        cudaError_t e = launch_predict(m->dev, *b, cs);
+        cudaError_t e = use_tc ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs) : launch_predict_cc(m->dev, *b, cs);
         if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
         if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
         delete b;

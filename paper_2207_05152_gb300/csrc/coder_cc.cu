@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
     int ii = 0;
     while (ii + 1 < b.n && b.img[ii + 1].tile_begin <= tile) ii++;
     const EncImage &im = b.img[ii];
-    const int64_t p = (int64_t)(tile - im.tile_begin) * kCH + tid;
+    const int64_t p = (int64_t)(tile - im.tile_begin) * kCH + tid;   // tile_px == kCH
     if (p >= (int64_t)im.H * im.W) return;
     const int r = (int)(p / im.W), c = (int)(p % im.W);
 
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
     const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
     const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
     uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
-    fc[p] = (c_hi - c_lo) | (c_lo << 16);
+    fc[stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
 }
 
 // ---------------------------------------------------------------------------

@@ -41,7 +41,7 @@ struct EncImage {
     int64_t pitch;
     int32_t H, W, S;
     int32_t tile_begin;           // first 128-pixel tile of this image
-    uint64_t fc_off;              // u32 (f | c << 16) per pixel, raster order
+    uint64_t fc_off;              // u32 (f | c << 16) per pixel, stream order
     uint64_t words_off;           // u16 renormalisation words, per stream region
     uint64_t cnt_off;             // u32 words per stream (incl. 2 flush words)
     uint64_t xfin_off;            // u32 final state per stream
@@ -49,11 +49,12 @@ struct EncImage {
 };
 
 constexpr int kMaxBatch = 192;    // images per launch (kernel-parameter space)
-constexpr int kPredictTile = 64;  // pixels per prediction CTA
+constexpr int kPredictTile = 64;  // pixels per CUDA-core prediction CTA
 
 struct EncBatch {
     int n;
     int chunk_start;              // index of img[0] in the caller's batch
+    int tile_px;                  // pixels per prediction tile
     int total_tiles;
     uint8_t *ws;                  // workspace base
     uint64_t *sizes;              // per image bitstream bytes (in workspace)
@@ -81,21 +82,59 @@ struct DecBatch {
 dlic_status fail(dlic_status code, const char *fmt, ...);
 dlic_status cuda_fail(cudaError_t e, const char *what);
 
-// Kernel launchers (predict.cu, rans.cu)
-cudaError_t launch_predict(const DevModel &m, const EncBatch &b, cudaStream_t st);
+// Kernel launchers (coder_cc.cu, coder_tc.cu, rans.cu)
+cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st);
+cudaError_t launch_predict_tc(const DevModel &m, const EncBatch &b, int *err, int num_sms, cudaStream_t st);
+bool tc_supported(const DevModel &m);
+size_t tc_weight_bytes(int h1, int h2);
+void tc_pack_weights(int h1, int h2, const int8_t *q1, const int8_t *q2, const int8_t *q3, uint16_t *out);
 cudaError_t launch_rans_encode(const EncBatch &b, int total_streams, cudaStream_t st);
 cudaError_t launch_pack(const DevModel &m, const EncBatch &b, uint8_t *out,
                         uint64_t *out_offsets, cudaStream_t st);
 cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st);
 
-// Number of pixels of stream s (rows s, s + S, ...) and the first word of its
-// scratch region: every earlier stream holds its pixels plus two flush words.
+// Rows of stream s (rows s, s + S, ...) and the first entry of its region in
+// stream-ordered per-pixel buffers: every earlier stream holds W pixels per
+// row.  Word scratch regions add the two flush words of each earlier stream.
 __host__ __device__ inline int64_t stream_rows(int H, int S, int s) {
     return (H - s + S - 1) / S;
 }
+__host__ __device__ inline int64_t stream_pix_base(int H, int W, int S, int s) {
+    const int64_t rows_before = (int64_t)(H / S) * s + (s < H % S ? s : H % S);
+    return rows_before * W;
+}
 __host__ __device__ inline int64_t stream_word_base(int H, int W, int S, int s) {
-    int64_t rows_before = (int64_t)(H / S) * s + (s < H % S ? s : H % S);
-    return rows_before * W + 2 * (int64_t)s;
+    return stream_pix_base(H, W, S, s) + 2 * (int64_t)s;
+}
+
+// Position of pixel (r, c) within its stream s = r mod S, whose pixels are
+// ordered by wave t = 3r + c, then by row.  The pixels before it are, for
+// every row r_k = s + kS of the stream, those of its columns that lie on an
+// earlier wave (clamp(t - 3 r_k, 0, W) of them), plus the pixels of earlier
+// rows of the stream on the same wave.
+__host__ __device__ inline int64_t stream_pos(int H, int W, int S, int r, int c) {
+    const int s = r % S;
+    const int64_t kr = r / S;
+    const int64_t n = stream_rows(H, S, s);
+    const int64_t D = 3LL * S;
+    const int64_t a0 = 3LL * r + c - 3LL * s;
+    int64_t k1 = 0, k2 = 0;
+    if (a0 >= W) {
+        k1 = (a0 - W) / D + 1;
+        k1 = k1 < n ? k1 : n;
+    }
+    if (a0 >= 1) {
+        k2 = (a0 - 1) / D + 1;
+        k2 = k2 < n ? k2 : n;
+    }
+    const int64_t before = (int64_t)W * k1 + (k2 - k1) * a0 - D * (k2 * (k2 - 1) / 2 - k1 * (k1 - 1) / 2);
+    const int64_t same_wave = (W - c - 1) / D;
+    return before + (kr < same_wave ? kr : same_wave);
+}
+
+// Index of pixel (r, c) in the stream-ordered per-pixel table buffer.
+__host__ __device__ inline int64_t stream_index(int H, int W, int S, int r, int c) {
+    return stream_pix_base(H, W, S, r % S) + stream_pos(H, W, S, r, c);
 }
 
 }  // namespace dlic

@@ -14,8 +14,32 @@
 
 namespace dlic {
 
-// One thread per (image, stream).  Words are written in emission order to
-// the stream's scratch region; pack reverses them.
+// One rANS step.  The quotient x / f comes from a single-precision
+// reciprocal estimate corrected to the exact value: x < f * 2^16 after
+// renormalisation, so the estimate is within one of the quotient.
+__device__ __forceinline__ uint32_t rans_put(uint32_t x, uint32_t v, uint16_t *words, uint32_t &ne) {
+    const uint32_t f = v & 0xFFFFu, c = v >> 16;
+    const float rf = __frcp_rn((float)f);
+    if (x >= (f << 16)) {
+        words[ne++] = (uint16_t)(x & 0xFFFFu);
+        x >>= 16;
+    }
+    int q = __float2int_rz(__fmul_rz(__uint2float_rz(x), rf));
+    int rem = (int)(x - (uint32_t)q * f);
+    if (rem < 0) {
+        q -= 1;
+        rem += (int)f;
+    } else if (rem >= (int)f) {
+        q += 1;
+        rem -= (int)f;
+    }
+    return ((uint32_t)q << 16) + (uint32_t)rem + c;
+}
+
+// One thread per (image, stream).  The stream's (f, c) entries are stored
+// in stream order, so the thread walks them backwards from the last symbol
+// with the next batch of loads in flight.  Words are written in emission
+// order to the stream's scratch region; pack reverses them.
 __global__ void k_rans_encode(EncBatch b, int total_streams) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total_streams) return;
@@ -27,25 +51,26 @@ __global__ void k_rans_encode(EncBatch b, int total_streams) {
     const EncImage &im = b.img[ii];
     const int s = g - first;
     const int H = im.H, W = im.W, S = im.S;
-    const uint32_t *fc = reinterpret_cast<const uint32_t *>(b.ws + im.fc_off);
+    const uint32_t *fc = reinterpret_cast<const uint32_t *>(b.ws + im.fc_off) + stream_pix_base(H, W, S, s);
     uint16_t *words = reinterpret_cast<uint16_t *>(b.ws + im.words_off) + stream_word_base(H, W, S, s);
+    const int64_t n = stream_rows(H, S, s) * W;
     uint32_t x = kRansL;
     uint32_t ne = 0;
-    const int T = 3 * (H - 1) + W;
-    for (int t = T - 1; t >= 0; t--) {
-        const int r_hi = min(H - 1, t / 3);
-        if (r_hi < s) continue;
-        const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
-        for (int r = r_hi - (r_hi - s) % S; r >= r_lo; r -= S) {
-            const uint32_t v = fc[(int64_t)r * W + (t - 3 * r)];
-            const uint32_t f = v & 0xFFFFu, c = v >> 16;
-            if (x >= (f << 16)) {
-                words[ne++] = (uint16_t)(x & 0xFFFFu);
-                x >>= 16;
-            }
-            const uint32_t q = x / f;
-            x = (q << 16) + (x - q * f) + c;
-        }
+    constexpr int B = 8;
+    uint32_t cur[B], nxt[B];
+    int64_t j = n - 1;
+#pragma unroll
+    for (int u = 0; u < B; u++) cur[u] = j - u >= 0 ? __ldg(fc + j - u) : 0u;
+    while (j >= 0) {
+        const int64_t jn = j - B;
+#pragma unroll
+        for (int u = 0; u < B; u++) nxt[u] = jn - u >= 0 ? __ldg(fc + jn - u) : 0u;
+#pragma unroll
+        for (int u = 0; u < B; u++)
+            if (j - u >= 0) x = rans_put(x, cur[u], words, ne);
+#pragma unroll
+        for (int u = 0; u < B; u++) cur[u] = nxt[u];
+        j = jn;
     }
     reinterpret_cast<uint32_t *>(b.ws + im.cnt_off)[s] = ne + 2;
     reinterpret_cast<uint32_t *>(b.ws + im.xfin_off)[s] = x;

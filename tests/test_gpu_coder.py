@@ -107,6 +107,6 @@ def test_corrupt_and_capacity(Codec, orc):
     ws = codec._workspace(1 << 20)
     with pytest.raises(_lib.DlicError) as e:
         _lib.dlic_encode(codec.handle, codec._desc([t]), [4], out.data_ptr(), out.numel(),
-                         offs.data_ptr(), ws.data_ptr(), ws.numel(), 0)
+                         offs.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0)
     assert e.value.code == _lib.DLIC_ERR_CAPACITY
     codec.close()
