@@ -25,10 +25,8 @@ dlic_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
-
-cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st) {
-    return launch_decode_cc(m, b, st);
-}
+cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
+bool tc_decode_supported(const DevModel &m);
 
 static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -373,6 +371,11 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
     }
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    {
+        cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t) * (size_t)n, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    }
+    const bool use_tc = tc_decode_supported(m->dev);
     size_t off = 0;
     for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
         const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
@@ -393,7 +396,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
             e.st_off = off;
             off += align256(16ull * g.height);
         }
-        cudaError_t e = launch_decode(m->dev, *b, cs);
+        cudaError_t e = use_tc ? launch_decode_tc(m->dev, *b, 0, m->num_sms, cs) : launch_decode_cc(m->dev, *b, cs);
         delete b;
         if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     }

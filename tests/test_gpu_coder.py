@@ -59,10 +59,14 @@ SHAPES = [(1, 1, 1), (1, 7, 1), (7, 1, 4), (2, 3, 2), (5, 64, 9), (16, 16, 16), 
           (9, 50, 1), (33, 17, 32), (3, 200, 2), (70, 130, 70), (80, 250, 7)]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "int8"])
-def test_edge_shapes(Codec, orc, prec):
+@pytest.mark.parametrize("prec,widths", [("fp32", [12, 32, 48, 256]), ("int8", [12, 32, 48, 256]),
+                                         ("int8", [12, 128, 128, 256])])
+def test_edge_shapes(Codec, orc, prec, widths):
+    # INT8 12-128-128-256 runs the tensor-core encoder and the cluster
+    # wavefront decoder; the narrower INT8 network the tensor-core encoder and
+    # the CUDA-core decoder; FP32 the CUDA-core kernels.
     imgs = [synth.value_noise_image(h, w, 7 * h + w) for h, w, _ in SHAPES]
-    blob = _models([12, 32, 48, 256], 5, [synth.voronoi_image(40, 40, 2)])[prec]
+    blob = _models(widths, 5, [synth.voronoi_image(40, 40, 2)])[prec]
     _check(Codec, orc, blob, imgs, [s for _, _, s in SHAPES])
 
 
@@ -83,10 +87,11 @@ def test_pitched_image(Codec, orc):
     codec.close()
 
 
-def test_corrupt_and_capacity(Codec, orc):
+@pytest.mark.parametrize("prec,widths", [("fp32", [12, 32, 32, 256]), ("int8", [12, 128, 128, 256])])
+def test_corrupt_and_capacity(Codec, orc, prec, widths):
     from paper_2207_05152_gb300 import _lib
     img = synth.value_noise_image(20, 30, 2)
-    blob = _models([12, 32, 32, 256], 6, [img])["fp32"]
+    blob = _models(widths, 6, [img])[prec]
     codec = Codec(blob)
     data = bytearray(orc.encode(blob, img, 4))
     _, st = codec.decode_bytes([bytes(data[:-2])], [(20, 30)])
