@@ -39,21 +39,9 @@ def _dist():
 
 
 def _workload():
-    import numpy as np
-    import synth
-    from paper_2207_05152_gb300 import model as M
-    img = synth.config_image(IMAGE_SEED_CFG)
-    layers = synth.predictive_mlp(WIDTHS, 2)
-    # calibration contexts from a different synthetic image of the same kind
-    cal_img = synth.voronoi_image(256, 256, 4242)
-    rng = synth.Rng(4243)
-    rr = rng.integers(4096, 0, 255)
-    cc = rng.integers(4096, 0, 255)
-    pad = np.zeros((258, 260), np.uint8)
-    pad[2:, 2:258] = cal_img
-    cal = np.stack([np.concatenate([pad[r:r + 2, c:c + 5].reshape(-1), pad[r + 2, c:c + 2]])
-                    for r, c in zip(rr, cc)])
-    return img, layers, M.int8_blob(layers, cal), M.fp32_blob(layers)
+    from paper_2207_05152_gb300 import workloads
+    layers, blob8, blob32 = workloads.models()
+    return workloads.cfg2_image(), layers, blob8, blob32
 
 
 class ClockSampler:

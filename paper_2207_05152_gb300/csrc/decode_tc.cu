@@ -25,13 +25,13 @@
 
 namespace dlic {
 
-constexpr int kDecThreads = 256;
+constexpr int kDecThreads = 512;
 constexpr int kDecWarps = kDecThreads / 32;
 constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
 
 struct DecTcLayout {
-    uint32_t w1, w2, w3, b1, b23, z, ring, rows, lut, st_x, st_pos, st_end, pay, total;
+    uint32_t w1, w2, w3, b1, b23, z, ring, rows, pg, lut, bf, st_x, st_pos, st_end, pay, total;
 };
 
 // Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
@@ -53,7 +53,9 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int g, int p
     L.z = take(4u * nt * kSymbols);
     L.ring = take(16u * rows);
     L.rows = take(4u * rows);
+    L.pg = take(4u * nt);
     L.lut = take(4u * 64);
+    L.bf = take(2u * 256);
     L.st_x = take(4u * g);
     L.st_pos = take(4u * g);
     L.st_end = take(4u * g);
@@ -87,24 +89,57 @@ __device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// floor(65280 * 2^32 / W) for 2^23 <= W <= 2^31, exactly: a single-precision
-// quotient (within a few units of the result) corrected with the exact
-// 64-bit remainder.
+// floor(65280 * 2^32 / W) for 2^23 <= W <= 2^31, exactly.  A reciprocal
+// estimate gives q within a few units of the quotient (q < 2^25); one
+// correction step from the exact 64-bit remainder, then a final +-1 fix-up,
+// lands on the floor.
 __device__ __forceinline__ uint32_t table_q_fast(uint32_t W) {
     const long long num = 65280LL << 32;
-    long long q = (long long)__fdiv_rn(280375465082880.0f, __uint2float_rn(W));
+    float rw;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rw) : "f"(__uint2float_rn(W)));
+    long long q = (long long)__float2uint_rz(__fmul_rz(280375465082880.0f, rw));
     long long rem = num - q * (long long)W;
+    q += (long long)__float2int_rz(__fmul_rz(__ll2float_rn(rem), rw));
+    rem = num - q * (long long)W;
 #pragma unroll 1
-    for (int k = 0; k < 16 && rem < 0; k++) {
+    for (int k = 0; k < 4 && rem < 0; k++) {
         q -= 1;
         rem += W;
     }
 #pragma unroll 1
-    for (int k = 0; k < 16 && rem >= (long long)W; k++) {
+    for (int k = 0; k < 4 && rem >= (long long)W; k++) {
         q += 1;
         rem -= W;
     }
     return (uint32_t)q;
+}
+
+// r mod S for 0 <= r < 2^24, 1 <= S <= 65535: a single-precision quotient
+// estimate (off by at most one) and an exact correction.
+__device__ __forceinline__ int fast_mod(int r, int S, float invS) {
+    int q = __float2int_rz(__fmul_rz(__int2float_rn(r), invS));
+    int m = r - q * S;
+    if (m < 0) m += S;
+    if (m >= S) m -= S;
+    return m;
+}
+
+// 8 consecutive 32-bit tensor-memory columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// Order-preserving map of a float to an unsigned integer (and back), so
+// that a warp-wide unsigned maximum finds the float maximum.
+__device__ __forceinline__ uint32_t float_key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
@@ -117,6 +152,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = prm.P, NT = prm.nt;
+    const int lgP = __ffs(P) - 1;                 // P is a power of two
     const uint32_t k = P > 1 ? cluster_rank() : 0u;
     const int img_idx = blockIdx.x / P;
     const DecImage &im = b.img[img_idx];
@@ -132,6 +168,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
         if (tid < 64) lut[tid] = m.lut[tid];
+        uint16_t *bf = reinterpret_cast<uint16_t *>(smem + L.bf);
+        if (tid < 256) bf[tid] = tc::bf16_of_int(tid - 128);
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
         for (int i = tid; i < prm.ring_rows * 4; i += kDecThreads) ring[i] = 0u;
     }
@@ -162,6 +200,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     __syncthreads();
     const int S = s_S;
     const int G = (S - (int)k + P - 1) / P;    // streams owned by this CTA: s = k + P g
+    const float invS = 1.0f / (float)(S > 0 ? S : 1);
     uint32_t *st_x = reinterpret_cast<uint32_t *>(smem + L.st_x);
     uint32_t *st_pos = reinterpret_cast<uint32_t *>(smem + L.st_pos);
     uint32_t *st_end = reinterpret_cast<uint32_t *>(smem + L.st_end);
@@ -236,7 +275,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     }
 
     const uint32_t tm = tmem_base;
-    const int q4 = warp & 3, cg = warp >> 2;                 // lane quarter, column group
+    const int q4 = warp & 3, cg = warp >> 2;                 // lane quarter, column group (0..3)
     const int unit = 32 * q4 + lane;                          // hidden / output unit of this thread
     const uint32_t tm_q = tm + ((uint32_t)(32 * q4) << 16);
     const float s1r = m.s1[unit], o1r = m.o1[unit], s2r = m.s2[unit], o2r = m.o2[unit];
@@ -252,6 +291,13 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                    sw3 = tc::smem_addr(smem + L.w3);
     const int rmask = prm.ring_rows - 1;
     uint32_t phase = 0;
+    // Operand descriptors of K step 0; K step ks starts 256 bytes further,
+    // i.e. 16 more in the descriptor's start-address field.
+    const uint64_t dw1 = tc::make_desc(sw1, 128u, 256u), db1 = tc::make_desc(sb1, 128u, 256u);
+    const uint64_t dw2 = tc::make_desc(sw2, 128u, 16u * kDecHidden);
+    const uint64_t dw3 = tc::make_desc(sw3, 128u, 16u * kDecHidden);
+    const uint64_t dw3b = tc::make_desc(sw3 + 16u * 16u * kDecHidden, 128u, 16u * kDecHidden);
+    const uint64_t db23 = tc::make_desc(sb23, 128u, 16u * kDecHidden);
 
     // Issues one layer's MMAs (thread 0), waits for them, and synchronises the
     // CTA.  After a timeout no further MMAs are issued; the wave loop still
@@ -262,22 +308,26 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         __syncthreads();
         if (tid == 0 && !s_fail) {
             tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_bf16_f32(128, NP);
             if (layer == 1) {
-                tc::mma_bf16(tm, tc::make_desc(sw1, 128u, 256u), tc::make_desc(sb1, 128u, 256u),
-                             tc::idesc_bf16_f32(128, NP), 0u);
+                tc::mma_bf16(tm, dw1, db1, idesc, 0u);
             } else if (layer == 2) {
-                for (int ks = 0; ks < kDecHidden / 16; ks++)
-                    tc::mma_bf16(tm, tc::make_desc(sw2 + 256u * ks, 128u, 16u * kDecHidden),
-                                 tc::make_desc(sb23 + 256u * ks, 128u, 16u * kDecHidden),
-                                 tc::idesc_bf16_f32(128, NP), ks > 0);
+                // two independent accumulation chains (K halves), summed in
+                // the epilogue: exact, since every partial sum is an integer
+                for (int j = 0; j < kDecHidden / 32; j++)
+                    for (int part = 0; part < 2; part++) {
+                        const int ks = part * (kDecHidden / 32) + j;
+                        tc::mma_bf16(tm + (uint32_t)(part * NP), dw2 + 16u * ks, db23 + 16u * ks, idesc, j > 0);
+                    }
             } else {
-                for (int half = 0; half < 2; half++)
-                    for (int ks = 0; ks < kDecHidden / 16; ks++)
-                        tc::mma_bf16(tm + (uint32_t)(half * NP),
-                                     tc::make_desc(sw3 + 16u * 16u * kDecHidden * half + 256u * ks, 128u,
-                                                   16u * kDecHidden),
-                                     tc::make_desc(sb23 + 256u * ks, 128u, 16u * kDecHidden),
-                                     tc::idesc_bf16_f32(128, NP), ks > 0);
+                // four chains: output half x K half
+                for (int j = 0; j < kDecHidden / 32; j++)
+                    for (int half = 0; half < 2; half++)
+                        for (int part = 0; part < 2; part++) {
+                            const int ks = part * (kDecHidden / 32) + j;
+                            tc::mma_bf16(tm + (uint32_t)((2 * half + part) * NP), (half ? dw3b : dw3) + 16u * ks,
+                                         db23 + 16u * ks, idesc, j > 0);
+                        }
             }
             tc::mma_commit(&bar);
             if (!tc::mbar_wait(&bar, phase, kDecWaitLimit)) s_fail = 1;
@@ -290,14 +340,16 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
 
     // Epilogue of a hidden layer: unit `unit`, pixel columns of this warp's
     // column group -> u8 activations as bf16 into b23 (row = pixel, k = unit).
-    auto hidden_epilogue = [&](int NP, float s, float o) {
-        for (int c0 = 16 * cg; c0 < NP; c0 += 32) {
-            uint32_t v[16];
-            tc::tmem_ld16(tm_q + (uint32_t)c0, v);
+    auto hidden_epilogue = [&](int NP, float s, float o, bool two) {
+        for (int c0 = 8 * cg; c0 < NP; c0 += 32) {
+            uint32_t v[8], v2[8];
+            tmem_ld8(tm_q + (uint32_t)c0, v);
+            if (two) tmem_ld8(tm_q + (uint32_t)(NP + c0), v2);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; e++) {
-                float h = rintf(__fmaf_rn(__uint_as_float(v[e]), s, o));
+            for (int e = 0; e < 8; e++) {
+                const float acc = two ? __fadd_rn(__uint_as_float(v[e]), __uint_as_float(v2[e])) : __uint_as_float(v[e]);
+                float h = rintf(__fmaf_rn(acc, s, o));
                 h = fminf(fmaxf(h, 0.0f), 255.0f);
                 const uint32_t mine = __float_as_uint(h) >> 16;
                 const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
@@ -308,6 +360,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     };
 
     int *rowlist = reinterpret_cast<int *>(smem + L.rows);
+    int *pixg = reinterpret_cast<int *>(smem + L.pg);
     __shared__ int s_wcnt[kDecWarps];
     const int T = 3 * (H - 1) + W;
     for (int t = 0; t < T; t++) {
@@ -315,58 +368,90 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         const int r_hi = min(H - 1, t / 3);
         // rows of this wave owned by this CTA, in increasing order
         int nk = 0;
-        for (int seg = r_lo; seg <= r_hi; seg += kDecThreads) {
-            const int r = seg + tid;
-            const bool own = r <= r_hi && ((r % S) % P) == (int)k;
-            const uint32_t bal = __ballot_sync(0xffffffffu, own);
-            if (lane == 0) s_wcnt[warp] = __popc(bal);
+        if (S % P == 0) {
+            // owned rows are exactly r = k mod P
+            const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
+            nk = r0 <= r_hi ? ((r_hi - r0) >> lgP) + 1 : 0;
+            for (int i = tid; i < nk; i += kDecThreads) rowlist[i] = r0 + (i << lgP);
             __syncthreads();
-            int before = nk, total = 0;
+        } else {
+            for (int seg = r_lo; seg <= r_hi; seg += kDecThreads) {
+                const int r = seg + tid;
+                const bool own = r <= r_hi && (fast_mod(r, S, invS) & (P - 1)) == (int)k;
+                const uint32_t bal = __ballot_sync(0xffffffffu, own);
+                if (lane == 0) s_wcnt[warp] = __popc(bal);
+                __syncthreads();
+                int before = nk, total = 0;
 #pragma unroll
-            for (int w2 = 0; w2 < kDecWarps; w2++) {
-                const int cw = s_wcnt[w2];
-                before += w2 < warp ? cw : 0;
-                total += cw;
+                for (int w2 = 0; w2 < kDecWarps; w2++) {
+                    const int cw = s_wcnt[w2];
+                    before += w2 < warp ? cw : 0;
+                    total += cw;
+                }
+                if (own) rowlist[before + __popc(bal & ((1u << lane) - 1u))] = r;
+                nk += total;
+                __syncthreads();
             }
-            if (own) rowlist[before + __popc(bal & ((1u << lane) - 1u))] = r;
-            nk += total;
-            __syncthreads();
         }
+        const bool spread = r_hi - r_lo < S;
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
-            // 1. priors of the chunk's pixels (zero rows pad the chunk to NP)
-            if (tid < NP) {
-                uint32_t w8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                if (tid < nc) {
-                    const int r = rowlist[base + tid], c = t - 3 * r;
+            // 1. priors of the chunk's pixels, four threads per pixel with
+            //    three priors each (zero rows pad the chunk to NP)
+            if (tid < 4 * NP) {
+                const int px = tid >> 2, part = tid & 3;
+                uint32_t v3[3] = {0x80u, 0x80u, 0x80u};
+                if (px < nc) {
+                    const int r = rowlist[base + px], c = t - 3 * r;
 #pragma unroll
-                    for (int q = 0; q < kPriors; q++) {
+                    for (int q3 = 0; q3 < 3; q3++) {
+                        const int q = 3 * part + q3;
                         const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
                         const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
                         const int rr = r + dr, cc = c + dc;
-                        const int v = (rr >= 0 && cc >= 0 && cc < W) ? ring[((rr & rmask) << 4) + (cc & 15)] : 0;
-                        w8[q >> 1] |= (uint32_t)tc::bf16_of_int(v - 128) << (16 * (q & 1));
+                        v3[q3] = (rr >= 0 && cc >= 0 && cc < W) ? ring[((rr & rmask) << 4) + (cc & 15)] : 0u;
                     }
                 }
-                *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset(tid, 0, 16)) = make_uint4(w8[0], w8[1], w8[2], w8[3]);
-                *reinterpret_cast<uint4 *>(b1 + tc::kmajor_offset(tid, 8, 16)) = make_uint4(w8[4], w8[5], w8[6], w8[7]);
+                const uint16_t *bf = reinterpret_cast<const uint16_t *>(smem + L.bf);
+                uint16_t *row = reinterpret_cast<uint16_t *>(b1);
+#pragma unroll
+                for (int q3 = 0; q3 < 3; q3++) {
+                    const int q = 3 * part + q3;
+                    row[tc::kmajor_offset(px, q, 16) / 2] = px < nc ? bf[v3[q3]] : (uint16_t)0;
+                }
+                if (part == 3) {
+#pragma unroll
+                    for (int q = kPriors; q < 16; q++) row[tc::kmajor_offset(px, q, 16) / 2] = 0;
+                }
+                if (part == 0 && px < nc) {
+                    // local stream of the pixel and the warp that runs its
+                    // table: by pixel when no two rows of the wave share a
+                    // stream, else by stream so that they run in row order
+                    const int r = rowlist[base + px];
+                    const int g = fast_mod(r, S, invS) >> lgP;
+                    pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
+                }
             }
             // 2. the three layers
             run_layer(1, NP);
-            hidden_epilogue(NP, s1r, o1r);
+            hidden_epilogue(NP, s1r, o1r, false);
             run_layer(2, NP);
-            hidden_epilogue(NP, s2r, o2r);
+            hidden_epilogue(NP, s2r, o2r, true);
             run_layer(3, NP);
-            for (int c0 = 16 * cg; c0 < NP; c0 += 32) {
-                uint32_t va[16], vb[16];
-                tc::tmem_ld16(tm_q + (uint32_t)c0, va);
-                tc::tmem_ld16(tm_q + (uint32_t)(NP + c0), vb);
+            for (int c0 = 8 * cg; c0 < NP; c0 += 32) {
+                uint32_t va[8], va2[8], vb[8], vb2[8];
+                tmem_ld8(tm_q + (uint32_t)c0, va);
+                tmem_ld8(tm_q + (uint32_t)(NP + c0), va2);
+                tmem_ld8(tm_q + (uint32_t)(2 * NP + c0), vb);
+                tmem_ld8(tm_q + (uint32_t)(3 * NP + c0), vb2);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    zb[(c0 + e) * kSymbols + unit] = __fmaf_rn(__uint_as_float(va[e]), s3a, o3a);
-                    zb[(c0 + e) * kSymbols + 128 + unit] = __fmaf_rn(__uint_as_float(vb[e]), s3b, o3b);
+                for (int e = 0; e < 8; e++) {
+                    const float a = __fadd_rn(__uint_as_float(va[e]), __uint_as_float(va2[e]));
+                    const float bsum = __fadd_rn(__uint_as_float(vb[e]), __uint_as_float(vb2[e]));
+                    zb[(c0 + e) * kSymbols + unit] = __fmaf_rn(a, s3a, o3a);
+                    zb[(c0 + e) * kSymbols + 128 + unit] = __fmaf_rn(bsum, s3b, o3b);
                 }
             }
             tc::fence_before_sync();
@@ -374,18 +459,18 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
             // 3. tables and rANS steps, one warp per pixel; pixels that share a
             //    stream go to the same warp (by local stream index), in row
             //    order.
-            for (int i = 0; i < nc; i++) {
+            for (int i = spread ? warp : 0; i < nc; i += spread ? kDecWarps : 1) {
+                const int pg = pixg[i];
+                if ((pg >> 24) != warp) continue;
+                const int g = pg & 0xFFFFFF;
                 const int r = rowlist[base + i], c = t - 3 * r;
-                const int g = (r % S) / P;
-                if (g % kDecWarps != warp) continue;
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
-                float mx = z[0];
+                uint32_t key = float_key(z[0]);
 #pragma unroll
-                for (int q = 1; q < 8; q++) mx = z[q] > mx ? z[q] : mx;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                for (int q = 1; q < 8; q++) key = max(key, float_key(z[q]));
+                const float mx = key_float(__reduce_max_sync(0xffffffffu, key));
                 uint32_t w[8], lsum = 0;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
@@ -406,23 +491,24 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 const uint32_t cs = 8u * lane + __umulhi(excl, Q);
                 const uint32_t ball = __ballot_sync(0xffffffffu, cs <= slot);
                 const int Lh = 31 - __clz(ball);
-                uint32_t sym = 0, f = 1, clo = 0;
-                if (lane == Lh) {
-                    uint32_t Pp = excl;
+                // c at the 9 unit boundaries of this lane; the symbol is the
+                // last unit whose lower boundary does not exceed the slot
+                uint32_t cb[9];
+                uint32_t Pp = excl;
 #pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        const uint32_t i8 = 8u * lane + q;
-                        const uint32_t lo = i8 + __umulhi(Pp, Q);
-                        const uint32_t hi = i8 == 255 ? kTotal : i8 + 1u + __umulhi(Pp + w[q], Q);
-                        if (hi > slot) {
-                            sym = i8;
-                            f = hi - lo;
-                            clo = lo;
-                            break;
-                        }
-                        Pp += w[q];
-                    }
+                for (int q = 0; q < 8; q++) {
+                    cb[q] = 8u * lane + q + __umulhi(Pp, Q);
+                    Pp += w[q];
                 }
+                cb[8] = lane == 31 ? kTotal : 8u * lane + 8u + __umulhi(Pp, Q);
+                uint32_t sym = 8u * lane, f = cb[1] - cb[0], clo = cb[0];
+#pragma unroll
+                for (int q = 1; q < 8; q++)
+                    if (cb[q] <= slot) {
+                        sym = 8u * lane + q;
+                        f = cb[q + 1] - cb[q];
+                        clo = cb[q];
+                    }
                 sym = __shfl_sync(0xffffffffu, sym, Lh);
                 f = __shfl_sync(0xffffffffu, f, Lh);
                 clo = __shfl_sync(0xffffffffu, clo, Lh);
@@ -485,7 +571,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         maxW = max(maxW, b.img[i].W);
     }
     int P = cluster;
-    if (P <= 0) P = (b.n * 8 <= num_sms) ? 8 : 1;
+    if (P <= 0) P = (b.n * 16 <= num_sms) ? 16 : (b.n * 8 <= num_sms ? 8 : 1);
     const int wave_px = min(maxH, (maxW + 2) / 3);
     const int per_cta = (wave_px + P - 1) / P + 1;
     DecTcParams prm;
@@ -496,29 +582,40 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     prm.ring_rows = rows;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
     const DecTcLayout L0 = dec_layout(prm.nt, rows, prm.max_g, 0);
-    const int budget = 227 * 1024 - 4096;
+    const int budget = 227 * 1024 - 8192;
     prm.pay_words = L0.total < (uint32_t)budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
     const DecTcLayout L = dec_layout(prm.nt, rows, prm.max_g, prm.pay_words);
     if (L.total > (uint32_t)(227 * 1024)) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
-    if (P > 8) {
-        e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
+    e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(b.n * P));
     cfg.blockDim = dim3(kDecThreads);
     cfg.dynamicSmemBytes = L.total;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)P;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // a 16-CTA cluster needs 16 free SMs in one GPC; step down if it cannot run
+    for (;;) {
+        attr[0].val.clusterDim.x = (unsigned)P;
+        cfg.gridDim = dim3((unsigned)(b.n * P));
+        int nclusters = 0;
+        if (P == 1 || (cudaOccupancyMaxActiveClusters(&nclusters, k_decode_tc, &cfg) == cudaSuccess && nclusters > 0))
+            break;
+        cudaGetLastError();
+        P >>= 1;
+        if (P < 1) return cudaErrorInvalidConfiguration;
+    }
+    if (P != prm.P) {
+        // smaller clusters hold more streams and pixels per CTA
+        return launch_decode_tc(m, b, P, num_sms, st);
+    }
     return cudaLaunchKernelEx(&cfg, k_decode_tc, m, b, prm);
 }
 

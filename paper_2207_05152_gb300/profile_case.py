@@ -1,0 +1,46 @@
+"""Runs a named workload a few times through the C ABI, for profilers.
+
+    python -m paper_2207_05152_gb300.profile_case --case cfg2 --iters 2
+    python -m paper_2207_05152_gb300.profile_case --case cfg4 --count 8 --iters 1
+
+Each iteration encodes and decodes the batch and checks the round trip.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4"])
+    ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--count", type=int, default=8)
+    ap.add_argument("--precision", default="int8", choices=["int8", "fp32"])
+    args = ap.parse_args()
+    import torch
+    from paper_2207_05152_gb300 import workloads
+    from paper_2207_05152_gb300.codec import Codec
+    _, blob8, blob32 = workloads.models()
+    imgs = [workloads.cfg2_image()] if args.case == "cfg2" else workloads.cfg4_images(args.count)
+    streams = [256] if args.case == "cfg2" else None
+    codec = Codec(blob8 if args.precision == "int8" else blob32)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    shapes = [i.shape for i in imgs]
+    for _ in range(args.iters):
+        out, offs = codec.encode(dev, streams)
+        o = offs.cpu().tolist()
+        dec, status = codec.decode(out, o, shapes)
+        torch.cuda.synchronize()
+        assert status[: len(imgs)].cpu().tolist() == [0] * len(imgs)
+        assert all(torch.equal(a, b) for a, b in zip(dec, dev))
+    print("ok", args.case, len(imgs), "images")
+
+
+if __name__ == "__main__":
+    main()
