@@ -139,6 +139,35 @@ DLIC_API dlic_status dlic_encode(const dlic_model *model, const dlic_image *h_im
                                  uint64_t *d_out_offsets, int32_t *d_status, void *d_workspace,
                                  size_t workspace_bytes, void *stream);
 
+/* Size of the fixed scratch block of dlic_encode_noalloc (16 MiB). */
+#define DLIC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* dlic_encode without a caller-provided workspace, for callers that cannot
+ * allocate device memory: a plug-in or callback inside another framework
+ * that owns every device allocation, a service whose device memory is all
+ * reserved in advance, or a loop that must avoid the device-wide
+ * synchronisation that cudaMalloc and cudaFree can cause.  The paper has no
+ * counterpart; it is a deployment convenience of this library.
+ *
+ * The call allocates nothing.  Its workspace is one block of
+ * DLIC_NOALLOC_SCRATCH_BYTES of device memory declared inside the library,
+ * which every GPU that loads the library keeps until the process exits.
+ * Arguments and results are those of dlic_encode minus the workspace pair;
+ * the output bitstreams are identical.  A batch whose workspace
+ * (dlic_encode_workspace_size) exceeds the block is rejected with
+ * DLIC_ERR_CAPACITY before anything is enqueued.
+ *  - The first call on a device looks up the block's device address with
+ *    that device current (a host-side lookup, no allocation); make that
+ *    first call before any stream capture.
+ *  - All calls share the one block and it keeps the previous call's data.
+ *    Nothing in it needs to start at zero: each call writes every word it
+ *    reads before reading it.  Calls whose work overlaps on the GPU (two
+ *    streams, two host threads) race on the block and corrupt each other's
+ *    output; serialise them. */
+DLIC_API dlic_status dlic_encode_noalloc(const dlic_model *model, const dlic_image *h_images, int n,
+                                         const int *h_streams, void *d_out, size_t out_capacity,
+                                         uint64_t *d_out_offsets, int32_t *d_status, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Decoding (Sec. II-A Fig. 2 right; Sec. II-B "Preprocessor" wavefront)   */
 /* ---------------------------------------------------------------------- */

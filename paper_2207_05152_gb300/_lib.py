@@ -44,6 +44,7 @@ SIGNATURES = {
     "dlic_auto_streams": (_I, [_I, _I]),
     "dlic_encode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_I), C.POINTER(_SZ)]),
     "dlic_encode": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
+    "dlic_encode_noalloc": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _VP]),
     "dlic_read_header": (_I, [_VP, _SZ, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                               C.POINTER(C.c_uint64)]),
     "dlic_decode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_SZ)]),
@@ -134,6 +135,16 @@ def dlic_encode(model: int, images, streams, d_out: int, out_capacity: int, d_ou
     arr, n = images_array(images)
     check(lib().dlic_encode(model, arr, n, int_array(streams), d_out, out_capacity, d_out_offsets,
                             d_status or None, d_ws, ws_bytes, stream or None))
+
+
+def dlic_encode_noalloc(model: int, images, streams, d_out: int, out_capacity: int,
+                        d_out_offsets: int, d_status: int, stream: int = 0):
+    """dlic_encode with the library's fixed scratch block as the workspace:
+    for callers that cannot allocate device memory.  Calls share the block;
+    do not let two of them overlap on the GPU."""
+    arr, n = images_array(images)
+    check(lib().dlic_encode_noalloc(model, arr, n, int_array(streams), d_out, out_capacity,
+                                    d_out_offsets, d_status or None, stream or None))
 
 
 def dlic_read_header(data: bytes):
