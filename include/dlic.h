@@ -193,6 +193,55 @@ DLIC_API dlic_status dlic_decode(const dlic_model *model, const void *d_in, cons
                         int n, const dlic_image *h_images, int32_t *d_status, void *d_workspace,
                         size_t workspace_bytes, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Training (Sec. III-A: categorical cross-entropy reported in bits)        */
+/* ---------------------------------------------------------------------- */
+
+enum { DLIC_TRAIN_BF16 = 0, DLIC_TRAIN_FP32 = 1, DLIC_TRAIN_BF16X3 = 2 };
+
+/* Number of FP32 parameters of a 12 -> h1 -> h2 -> 256 network, laid out as
+ * W1 [h1][12], b1 [h1], W2 [h2][h1], b2 [h2], W3 [256][h2], b3 [256] (the
+ * layer order of an FP32 model blob). */
+DLIC_API size_t dlic_train_param_count(int h1, int h2);
+
+/* Creates a trainer: FP32 master weights (copied from h_params, host),
+ * Adam moments (lr 1e-3, betas 0.9 / 0.999, eps 1e-8, bias-corrected) and
+ * device buffers for batches of up to max_batch contexts.  mode
+ * DLIC_TRAIN_BF16 runs every product on the tensor cores with bf16 operands
+ * and FP32 accumulation; DLIC_TRAIN_BF16X3 stores every operand as two bf16
+ * planes (x = hi + lo) and accumulates hi*hi + lo*hi + hi*lo on the tensor
+ * cores (about 16 significant bits per operand, three times the MMAs);
+ * DLIC_TRAIN_FP32 runs them in FP32 on the CUDA cores.
+ * Allocates its device memory here and frees it in dlic_trainer_destroy. */
+DLIC_API dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_batch, const float *h_params,
+                                         dlic_trainer **out);
+DLIC_API dlic_status dlic_trainer_destroy(dlic_trainer *trainer);
+
+/* Loss of a batch: d_ctx holds B x 12 u8 causal priors (the gather order of
+ * dlic_encode), d_tgt B u8 target pixels; *d_loss_bits (device float)
+ * receives mean_b -log2 softmax(z_b)[y_b]. */
+DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+                                        float *d_loss_bits, void *stream);
+
+/* Loss and its gradient with respect to every parameter (the adjoint of the
+ * forward pass, activations recomputed from the batch); d_grads (device,
+ * dlic_train_param_count floats, may be NULL) receives the gradient in the
+ * parameter layout. */
+DLIC_API dlic_status dlic_train_backward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+                                         float *d_loss_bits, float *d_grads, void *stream);
+
+/* Forward, backward and one Adam update of the master weights. */
+DLIC_API dlic_status dlic_train_step(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+                                     float *d_loss_bits, void *stream);
+
+/* Copies the FP32 master weights out of (write = 0) or into (write = 1) the
+ * trainer; d_params is a device buffer of dlic_train_param_count floats. */
+DLIC_API dlic_status dlic_trainer_params(dlic_trainer *trainer, float *d_params, int write, void *stream);
+
+/* Device status of the trainer's kernels (DLIC_OK or DLIC_ERR_TIMEOUT when a
+ * tensor-core wait ran out); synchronises with the device. */
+DLIC_API dlic_status dlic_trainer_status(dlic_trainer *trainer, int32_t *h_status);
+
 #ifdef __cplusplus
 }
 #endif

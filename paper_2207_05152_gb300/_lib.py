@@ -16,6 +16,7 @@ _lib = None
 DLIC_OK, DLIC_ERR_INVALID, DLIC_ERR_CAPACITY, DLIC_ERR_CORRUPT = 0, 1, 2, 3
 DLIC_ERR_TIMEOUT, DLIC_ERR_CUDA, DLIC_ERR_UNSUPPORTED = 4, 5, 6
 DLIC_FP32, DLIC_INT8 = 0, 1
+DLIC_TRAIN_BF16, DLIC_TRAIN_FP32, DLIC_TRAIN_BF16X3 = 0, 1, 2
 
 
 class DlicError(RuntimeError):
@@ -49,6 +50,14 @@ SIGNATURES = {
                               C.POINTER(C.c_uint64)]),
     "dlic_decode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_SZ)]),
     "dlic_decode": (_I, [_VP, _VP, C.POINTER(C.c_uint64), _I, _IMGP, _VP, _VP, _SZ, _VP]),
+    "dlic_train_param_count": (_SZ, [_I, _I]),
+    "dlic_trainer_create": (_I, [_I, _I, _I, _I, _VP, C.POINTER(_VP)]),
+    "dlic_trainer_destroy": (_I, [_VP]),
+    "dlic_train_forward": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    "dlic_train_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP]),
+    "dlic_train_step": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    "dlic_trainer_params": (_I, [_VP, _VP, _I, _VP]),
+    "dlic_trainer_status": (_I, [_VP, C.POINTER(C.c_int32)]),
 }
 
 
@@ -168,3 +177,41 @@ def dlic_decode(model: int, d_in: int, in_offsets, images, d_status: int, d_ws: 
     arr, n = images_array(images)
     check(lib().dlic_decode(model, d_in, u64_array(in_offsets), n, arr, d_status, d_ws, ws_bytes,
                             stream or None))
+
+
+def dlic_train_param_count(h1: int, h2: int) -> int:
+    return int(lib().dlic_train_param_count(h1, h2))
+
+
+def dlic_trainer_create(h1: int, h2: int, mode: int, max_batch: int, h_params) -> int:
+    """h_params: contiguous float32 numpy array of dlic_train_param_count values."""
+    h = _VP()
+    check(lib().dlic_trainer_create(h1, h2, mode, max_batch, h_params.ctypes.data, C.byref(h)))
+    return h.value
+
+
+def dlic_trainer_destroy(trainer: int):
+    check(lib().dlic_trainer_destroy(trainer))
+
+
+def dlic_train_forward(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, stream: int = 0):
+    check(lib().dlic_train_forward(trainer, d_ctx, d_tgt, B, d_loss, stream or None))
+
+
+def dlic_train_backward(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, d_grads: int,
+                        stream: int = 0):
+    check(lib().dlic_train_backward(trainer, d_ctx, d_tgt, B, d_loss, d_grads or None, stream or None))
+
+
+def dlic_train_step(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, stream: int = 0):
+    check(lib().dlic_train_step(trainer, d_ctx, d_tgt, B, d_loss, stream or None))
+
+
+def dlic_trainer_params(trainer: int, d_params: int, write: bool, stream: int = 0):
+    check(lib().dlic_trainer_params(trainer, d_params, int(bool(write)), stream or None))
+
+
+def dlic_trainer_status(trainer: int) -> int:
+    st = C.c_int32()
+    check(lib().dlic_trainer_status(trainer, C.byref(st)))
+    return st.value

@@ -1,0 +1,139 @@
+"""Training of the density network through the C ABI (dlic_train_*).
+
+The loss is the categorical cross-entropy in bits, mean_b -log2 p(y_b | ctx_b)
+(Sec. III-A reports it as "vloss in bpp").  `Trainer` owns the FP32 master
+weights and Adam state on the device; `DlicLoss` exposes the hand-written
+forward and backward kernels to torch.autograd (the gradient flows to a
+parameter-sized tensor that stands for the trainer's weights).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from . import model as M
+
+MODES = {"bf16": _lib.DLIC_TRAIN_BF16, "fp32": _lib.DLIC_TRAIN_FP32, "bf16x3": _lib.DLIC_TRAIN_BF16X3}
+_DR = np.array([-2, -2, -2, -2, -2, -1, -1, -1, -1, -1, 0, 0])
+_DC = np.array([-2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -2, -1])
+
+
+def flatten(layers) -> np.ndarray:
+    """[(W1, b1), (W2, b2), (W3, b3)] -> the trainer's parameter vector."""
+    return np.concatenate([np.asarray(a, np.float32).reshape(-1) for wb in layers for a in wb])
+
+
+def unflatten(vec, h1: int, h2: int):
+    v = np.asarray(vec, np.float32)
+    shapes = [(h1, 12), (h1,), (h2, h1), (h2,), (256, h2), (256,)]
+    out, off = [], 0
+    for s in shapes:
+        n = int(np.prod(s))
+        out.append(v[off:off + n].reshape(s))
+        off += n
+    return [(out[0], out[1]), (out[2], out[3]), (out[4], out[5])]
+
+
+def sample_contexts(images, count: int, seed: int):
+    """(ctx u8 [count, 12], tgt u8 [count]) at pixel positions drawn uniformly
+    over the images; priors outside an image are 0 (the coder's window).
+    Training-data preparation on the host; the coding path gathers on the
+    device."""
+    import synth
+    idx, rr, cc = synth.sample_positions(images, count, seed)
+    ctx = np.zeros((count, 12), np.uint8)
+    tgt = np.zeros(count, np.uint8)
+    for i, img in enumerate(images):
+        sel = np.nonzero(idx == i)[0]
+        if sel.size == 0:
+            continue
+        H, W = img.shape
+        pad = np.zeros((H + 2, W + 4), np.uint8)
+        pad[2:, 2:W + 2] = img
+        r, c = rr[sel], cc[sel]
+        ctx[sel] = pad[r[:, None] + 2 + _DR[None, :], c[:, None] + 2 + _DC[None, :]]
+        tgt[sel] = img[r, c]
+    return ctx, tgt
+
+
+class Trainer:
+    """FP32 master weights + Adam on the current CUDA device."""
+
+    def __init__(self, layers, mode: str = "bf16", max_batch: int = 65536):
+        self.h1 = layers[0][0].shape[0]
+        self.h2 = layers[1][0].shape[0]
+        self.mode = mode
+        self.nparams = _lib.dlic_train_param_count(self.h1, self.h2)
+        flat = np.ascontiguousarray(flatten(layers))
+        assert flat.size == self.nparams
+        self.handle = _lib.dlic_trainer_create(self.h1, self.h2, MODES[mode], max_batch, flat)
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def close(self):
+        if self.handle:
+            _lib.dlic_trainer_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream():
+        return int(torch.cuda.current_stream().cuda_stream)
+
+    def forward(self, ctx: torch.Tensor, tgt: torch.Tensor) -> torch.Tensor:
+        _lib.dlic_train_forward(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
+                                self.loss.data_ptr(), self._stream())
+        return self.loss
+
+    def backward(self, ctx: torch.Tensor, tgt: torch.Tensor, grads: torch.Tensor | None = None):
+        if grads is None:
+            grads = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        _lib.dlic_train_backward(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
+                                 self.loss.data_ptr(), grads.data_ptr(), self._stream())
+        return self.loss, grads
+
+    def step(self, ctx: torch.Tensor, tgt: torch.Tensor) -> torch.Tensor:
+        _lib.dlic_train_step(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
+                             self.loss.data_ptr(), self._stream())
+        return self.loss
+
+    def params(self) -> torch.Tensor:
+        out = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        _lib.dlic_trainer_params(self.handle, out.data_ptr(), False, self._stream())
+        return out
+
+    def set_params(self, flat: torch.Tensor):
+        flat = flat.contiguous().float().cuda()
+        _lib.dlic_trainer_params(self.handle, flat.data_ptr(), True, self._stream())
+
+    def layers(self):
+        return unflatten(self.params().cpu().numpy(), self.h1, self.h2)
+
+    def fp32_blob(self) -> bytes:
+        return M.fp32_blob(self.layers())
+
+    def status(self) -> int:
+        return _lib.dlic_trainer_status(self.handle)
+
+
+class DlicLoss(torch.autograd.Function):
+    """loss = DlicLoss.apply(theta, trainer, ctx, tgt): the bits loss of the
+    trainer's network; theta is a parameter-sized tensor that receives the
+    gradient (the kernels read the trainer's own master weights)."""
+
+    @staticmethod
+    def forward(fctx, theta, trainer, ctx, tgt):
+        fctx.trainer = trainer
+        fctx.save_for_backward(ctx, tgt)
+        return trainer.forward(ctx, tgt).clone().reshape(())
+
+    @staticmethod
+    def backward(fctx, g):
+        ctx, tgt = fctx.saved_tensors
+        _, grads = fctx.trainer.backward(ctx, tgt)
+        return grads * g, None, None, None

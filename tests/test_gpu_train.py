@@ -1,0 +1,131 @@
+"""GPU training step against the FP64 reference (oracle/train64.py).
+
+The loss is the categorical cross-entropy in bits (Sec. III-A, Table I).
+FP32 mode must match the FP64 gradient to FP32 accuracy; BF16 mode (bf16
+operands, FP32 accumulation) is measured against the FP64 gradient with the
+norm-wise relative error ||g - g64|| / ||g64|| per parameter tensor."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import train64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_05152_gb300 import train
+    return train
+
+
+def _data(T, n, seed, widths=(12, 256, 256, 256), kind="xavier"):
+    imgs = [synth.config_image(3, i) for i in range(2)]
+    ctx, tgt = T.sample_contexts(imgs, n, seed)
+    if kind == "xavier":
+        layers = synth.xavier_mlp(list(widths), seed)
+        rng = synth.Rng(seed + 100)
+        layers = [(w, (0.05 * rng.normal(b.size)).astype(np.float32)) for w, b in layers]
+    else:
+        layers = synth.predictive_mlp(list(widths), seed)
+    return layers, ctx, tgt
+
+
+def _rel(g, ref):
+    return float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30))
+
+
+def _grads(T, mode, layers, ctx, tgt):
+    tr = T.Trainer(layers, mode, max_batch=len(tgt))
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    loss, g = tr.backward(c, t)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    out = float(loss.item()), T.unflatten(g.cpu().numpy(), tr.h1, tr.h2)
+    tr.close()
+    return out
+
+
+@pytest.mark.parametrize("n,kind", [(2048, "xavier"), (1000, "predictive"), (1, "xavier"), (1, "predictive")])
+def test_fp32_gradient_matches_fp64(T, n, kind):
+    layers, ctx, tgt = _data(T, n, 5, kind=kind)
+    loss, g = _grads(T, "fp32", layers, ctx, tgt)
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    # FP32 rounding of logits of magnitude |z| bounds the loss error
+    _, (x, a1, h1, a2, h2, z, lse) = train64.forward(layers, ctx, tgt)
+    assert abs(loss - loss64) <= 4e-7 * np.abs(z).max() + 1e-5
+    for (gw, gb), (rw, rb) in zip(g, ref):
+        assert _rel(gw, rw) < 2e-4
+        assert _rel(gb, rb) < 2e-4
+
+
+@pytest.mark.parametrize("mode,tol", [("bf16", 3e-2), ("bf16x3", 1e-3)])
+def test_bf16_gradient_against_fp64(T, mode, tol):
+    # 2048 contexts of cfg-3-style images, 12-256-256-256, Xavier-scale
+    # weights.  Plain bf16 operands give errors of order 1e-2 (measured and
+    # reported by the benchmark); split bf16 (hi + lo planes) meets 1e-3.
+    layers, ctx, tgt = _data(T, 2048, 7)
+    loss, g = _grads(T, mode, layers, ctx, tgt)
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    errs = [(_rel(gw, rw), _rel(gb, rb)) for (gw, gb), (rw, rb) in zip(g, ref)]
+    print(mode, "loss", loss, "fp64", loss64, "norm-wise rel errors (W, b) per layer:", errs)
+    assert abs(loss - loss64) <= 1e-3 * loss64
+    for ew, eb in errs:
+        assert ew < tol and eb < tol
+
+
+def test_gradient_matches_finite_differences(T):
+    # The FP32 GPU gradient against central differences of the FP64 loss,
+    # to within 1e-3 of the tensor's largest gradient entry.
+    layers, ctx, tgt = _data(T, 512, 9, widths=(12, 32, 32, 256))
+    _, g = _grads(T, "fp32", layers, ctx, tgt)
+    rng = synth.Rng(3)
+    for layer in range(3):
+        for which in range(2):
+            arr = g[layer][which].reshape(-1)
+            scale = np.abs(arr).max()
+            for i in rng.integers(3, 0, arr.size - 1):
+                theta = np.asarray(layers[layer][which], np.float64).reshape(-1)[i]
+                h = 1e-6 * max(1.0, abs(theta))
+                fd = train64.finite_difference(layers, ctx, tgt, layer, which, int(i), h)
+                assert abs(fd - arr[i]) <= 1e-3 * scale + 1e-7
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
+def test_adam_step_and_training_progress(T, mode):
+    layers, ctx, tgt = _data(T, 4096, 11, widths=(12, 64, 64, 256))
+    layers = synth.xavier_mlp([12, 64, 64, 256], 11)
+    tr = T.Trainer(layers, mode, max_batch=4096)
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    p0 = tr.params().cpu().numpy().astype(np.float64)
+    _, g = tr.backward(c, t)
+    g = g.cpu().numpy().astype(np.float64)
+    first = float(tr.step(c, t).item())
+    p1 = tr.params().cpu().numpy().astype(np.float64)
+    want, _, _ = train64.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1)
+    assert np.allclose(p1, want, rtol=1e-5, atol=1e-6)
+    for _ in range(60):
+        last = float(tr.step(c, t).item())
+    assert tr.status() == 0
+    assert last < first - 0.5, (first, last)
+    tr.close()
+
+
+def test_autograd_function(T):
+    layers, ctx, tgt = _data(T, 256, 13, widths=(12, 32, 32, 256))
+    tr = T.Trainer(layers, "fp32", max_batch=256)
+    theta = torch.zeros(tr.nparams, device="cuda", requires_grad=True)
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    loss = T.DlicLoss.apply(theta, tr, c, t)
+    (2.0 * loss).backward()
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    flat = T.flatten([(2 * a, 2 * b) for a, b in ref])
+    assert abs(float(loss) - loss64) < 1e-4
+    assert _rel(theta.grad.cpu().numpy(), flat) < 1e-4
+    tr.close()
