@@ -109,6 +109,27 @@ def _peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+PROFILES = {"decode": ("profiles/k_decode_tc_cfg2_512x512.md", "paper_2207_05152_gb300/csrc/decode_tc.cu"),
+            "encode": ("profiles/k_encode_tc_cfg2_512x512.md", "paper_2207_05152_gb300/csrc/coder_tc.cu")}
+
+
+def _profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or
+    None when the kernel's source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        prof, src = PROFILES[kernel]
+        text = open(os.path.join(ROOT, prof)).read()
+        digest = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+        if f"sha256 prefix {digest}" not in text:
+            return None
+        m = re.search(r"traffic \(DRAM read \+ write per launch\): (\d+) bytes read, (\d+) written", text)
+        return int(m.group(1)) + int(m.group(2)) if m else None
+    except (OSError, KeyError):
+        return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -207,6 +228,8 @@ def run_ours(args):
         assert int(st[0]) == 0 and torch.equal(h_dec, h_img)
     codec.close()
 
+    train = measure_train(args)
+
     # max over ranks of the timed totals
     tot8 = sum(r8["enc"]) + sum(r8["dec"])
     t_e2e = sum(e2e_ms)
@@ -251,7 +274,8 @@ def run_ours(args):
                       "bpp": round(8.0 * r32["nbytes"] / N, 4), "roundtrip_bit_exact": r32["ok"]},
         "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
-                     "peak_source": f"bf16 burst, {peak_kind}", "traffic": None},
+                     "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
+        "train": train,
         "gpu_launches": K * (LAUNCHES_PER_STEP["encode"] + LAUNCHES_PER_STEP["decode"]),
         "clocks": r8["clocks"],
         "e2e": {"value": round(ws * K * N / (t_e2e * 1e-3) / 1e6, 3), "unit": "Mpix/s",
@@ -263,6 +287,51 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+TRAIN_BATCH = 65536
+TRAIN_WIDTHS = [12, 256, 256, 256]
+# multiply-adds x 2 per context: forward 12*256 + 256*256 + 256*256, backward
+# dh2, dh1, dW3, dW2 (256*256 each) and dW1 (256*12)
+TRAIN_FLOP_PER_CTX = 2 * (12 * 256 + 2 * 256 * 256) + 2 * (4 * 256 * 256 + 256 * 12)
+
+
+def measure_train(args):
+    """Train ctx/s of one dlic_train_step (forward, backward, Adam) at a batch
+    of 65536 contexts from 8 synthetic 512 x 512 images, 12-256-256-256."""
+    import torch
+    import synth
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.config_image(3, i) for i in range(8)]
+    ctx, tgt = T.sample_contexts(imgs, TRAIN_BATCH, 3000)
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    layers = synth.xavier_mlp(TRAIN_WIDTHS, 3)
+    out = {"workload": "cfg3: batch 65536 contexts from 8 synthetic 512x512 images, MLP 12-256-256-256, "
+                       "forward + backward + Adam", "flop_per_ctx": TRAIN_FLOP_PER_CTX}
+    stream = torch.cuda.current_stream()
+    for mode in ("bf16", "bf16x3", "fp32"):
+        tr = T.Trainer(layers, mode, max_batch=TRAIN_BATCH)
+        for _ in range(args.warmup):
+            tr.step(c, t)
+        torch.cuda.synchronize()
+        steps = args.steps if mode != "fp32" else max(3, args.steps // 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            tr.step(c, t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        loss = float(tr.loss.item())
+        assert tr.status() == 0
+        tr.close()
+        out[mode] = {"ctx_s": round(TRAIN_BATCH / (ms * 1e-3), 1), "ms_per_step": round(ms, 4),
+                     "tflops": round(TRAIN_FLOP_PER_CTX * TRAIN_BATCH / (ms * 1e-3) / 1e12, 2),
+                     "loss_bits_after": round(loss, 4)}
+    _, bf16_peak, _ = _peaks()
+    out["bf16_roofline_frac"] = round(out["bf16"]["tflops"] / bf16_peak, 4)
+    return out
 
 
 def cpu_baseline(img, blob, gpu_bits):

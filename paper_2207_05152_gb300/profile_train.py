@@ -1,0 +1,37 @@
+"""Runs a few training steps of one mode through the C ABI, for profilers.
+
+    python -m paper_2207_05152_gb300.profile_train --mode bf16 --batch 65536 --steps 2
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="bf16", choices=["bf16", "bf16x3", "fp32"])
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--steps", type=int, default=2)
+    args = ap.parse_args()
+    import torch
+    import synth
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.config_image(3, i) for i in range(8)]
+    ctx, tgt = T.sample_contexts(imgs, args.batch, 3000)
+    tr = T.Trainer(synth.xavier_mlp([12, 256, 256, 256], 3), args.mode, max_batch=args.batch)
+    c, t = torch.from_numpy(ctx).cuda(), torch.from_numpy(tgt).cuda()
+    for _ in range(args.steps):
+        tr.step(c, t)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    print("ok", args.mode, float(tr.loss.item()))
+
+
+if __name__ == "__main__":
+    main()
