@@ -31,13 +31,13 @@ constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
 
 struct DecTcLayout {
-    uint32_t w1, w2, w3, b1, b23, z, ring, rows, pg, lut, bf, st_x, st_pos, st_end, pay, total;
+    uint32_t w1, w2, w3, b1, b23, z, ring, tring, rows, pg, dsym, lut, bf, st_x, st_pos, st_end, pay, total;
 };
 
 // Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
-// the bound on the pixels of one wave), `g` owned streams and `pay_words`
-// staged payload words.
-__host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int g, int pay_words) {
+// the bound on the pixels of one wave), `tslots` tagged-ring rows, `g` owned
+// streams and `pay_words` staged payload words.
+__host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, int g, int pay_words) {
     DecTcLayout L;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes) {
@@ -52,8 +52,10 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int g, int p
     L.b23 = take(2u * nt * kDecHidden);
     L.z = take(4u * nt * kSymbols);
     L.ring = take(16u * rows);
+    L.tring = take(128u * tslots);
     L.rows = take(4u * rows);
     L.pg = take(4u * nt);
+    L.dsym = take(rows);
     L.lut = take(4u * 64);
     L.bf = take(2u * 256);
     L.st_x = take(4u * g);
@@ -68,6 +70,7 @@ struct DecTcParams {
     int P;            // CTAs per image (cluster size)
     int nt;           // pixels per chunk (multiple of 16, <= 128)
     int ring_rows;    // power of two
+    int tq;           // tagged ring: row rounds kept per neighbour (power of two)
     int max_g;        // owned streams per CTA (upper bound)
     int pay_words;    // staged payload capacity per CTA (words); 0 = read from global
 };
@@ -87,6 +90,22 @@ __device__ __forceinline__ uint32_t map_shared(uint32_t addr, uint32_t rank) {
 }
 __device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.volatile.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(tc::smem_addr(p)) : "memory");
+    return v;
+}
+
+// Tagged ring entry of pixel (r, c) with value v: a valid bit, 11 bits of the
+// row and 12 of the column, then the pixel.  A reader knows which (r, c) it
+// wants, so a single 32-bit store both delivers the value and says that it
+// has arrived: no fence or barrier is needed between CTAs.
+__device__ __forceinline__ uint32_t ring_tag(int r, int c) {
+    return 0x80000000u | ((uint32_t)(r & 0x7FF) << 20) | ((uint32_t)(c & 0xFFF) << 8);
 }
 
 // floor(65280 * 2^32 / W) for 2^23 <= W <= 2^31, exactly.  A reciprocal
@@ -147,6 +166,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok, s_S, s_err, s_fail;
+
     __shared__ uint32_t s_part[kDecThreads];
     __shared__ uint32_t s_gpart[kDecThreads];
 
@@ -158,7 +178,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     const DecImage &im = b.img[img_idx];
     const uint8_t *in = b.in + im.in_off;
     const int H = im.H, W = im.W;
-    const DecTcLayout L = dec_layout(NT, prm.ring_rows, prm.max_g, prm.pay_words);
+    const DecTcLayout L = dec_layout(NT, prm.ring_rows, 4 * prm.tq, prm.max_g, prm.pay_words);
 
     // --- set-up: weights, parameters, tensor memory, header and streams ---
     {
@@ -172,6 +192,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         if (tid < 256) bf[tid] = tc::bf16_of_int(tid - 128);
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
         for (int i = tid; i < prm.ring_rows * 4; i += kDecThreads) ring[i] = 0u;
+        uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
+        for (int i = tid; i < prm.tq * 4 * 32; i += kDecThreads) tring[i] = 0u;
     }
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, 256);
@@ -182,6 +204,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         tc::fence_mbar_init();
         s_err = 0;
         s_fail = 0;
+
         int ok = im.in_bytes >= (uint64_t)kHeaderBytes;
         int S = 0;
         if (ok) {
@@ -273,6 +296,17 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
         return;
     }
+    // When every CTA owns the rows k mod P (P divides S), a pixel's priors
+    // come from its own rows and those of CTAs k-1 and k-2, which push each
+    // decoded pixel into a tagged ring (32 columns of every row they own):
+    // CTAs then wait for the very values they read instead of for each other,
+    // and no cluster barrier runs per wave.  A CTA can run at most P - 1
+    // waves ahead of a reader, and a row's 32 ring columns outlive 24 waves.
+    const bool p2p = P >= 2 && P <= 16 && (S % P) == 0;
+    uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
+    const uint32_t tring_addr = tc::smem_addr(tring);
+    const int tqmask = prm.tq - 1;
+    if (P > 1) cluster_sync_all();   // every CTA's rings are initialised
 
     const uint32_t tm = tmem_base;
     const int q4 = warp & 3, cg = warp >> 2;                 // lane quarter, column group (0..3)
@@ -361,6 +395,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
 
     int *rowlist = reinterpret_cast<int *>(smem + L.rows);
     int *pixg = reinterpret_cast<int *>(smem + L.pg);
+    uint8_t *dsym = smem + L.dsym;   // this wave's decoded pixels, by row-list index
     __shared__ int s_wcnt[kDecWarps];
     const int T = 3 * (H - 1) + W;
     for (int t = 0; t < T; t++) {
@@ -410,7 +445,28 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
                         const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
                         const int rr = r + dr, cc = c + dc;
-                        v3[q3] = (rr >= 0 && cc >= 0 && cc < W) ? ring[((rr & rmask) << 4) + (cc & 15)] : 0u;
+                        if (rr < 0 || cc < 0 || cc >= W) {
+                            v3[q3] = 0u;
+                        } else if (p2p) {
+                            // entry (round of rr, owner distance, column mod 32)
+                            const int slot = (((rr >> lgP) & tqmask) << 2) | (((int)k - rr) & (P - 1));
+                            const uint32_t *e = tring + slot * 32 + (cc & 31);
+                            const uint32_t want = ring_tag(rr, cc);
+                            uint32_t v = ld_volatile_u32(e);
+                            if ((v & 0xFFFFFF00u) != want) {
+                                const long long t0 = clock64();
+                                do {
+                                    v = ld_volatile_u32(e);
+                                    if (clock64() - t0 > kDecWaitLimit) {
+                                        s_fail = 1;
+                                        break;
+                                    }
+                                } while ((v & 0xFFFFFF00u) != want);
+                            }
+                            v3[q3] = v & 0xFFu;
+                        } else {
+                            v3[q3] = ring[((rr & rmask) << 4) + (cc & 15)];
+                        }
                     }
                 }
                 const uint16_t *bf = reinterpret_cast<const uint16_t *>(smem + L.bf);
@@ -464,6 +520,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 if ((pg >> 24) != warp) continue;
                 const int g = pg & 0xFFFFFF;
                 const int r = rowlist[base + i], c = t - 3 * r;
+                const uint32_t x = st_x[g];
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
@@ -477,16 +534,16 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                     w[q] = table_weight(mx, z[q], m.tscale, lut);
                     lsum += w[q];
                 }
+                // the total (and from it Q) runs beside the prefix scan
+                const uint32_t Wsum = __reduce_add_sync(0xffffffffu, lsum);
+                const uint32_t Q = table_q_fast(Wsum);
                 uint32_t incl = lsum;
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
                     const uint32_t o = __shfl_up_sync(0xffffffffu, incl, off);
                     if (lane >= off) incl += o;
                 }
-                const uint32_t Wsum = __shfl_sync(0xffffffffu, incl, 31);
-                const uint32_t Q = table_q_fast(Wsum);
                 const uint32_t excl = incl - lsum;
-                const uint32_t x = st_x[g];
                 const uint32_t slot = x & 0xFFFFu;
                 const uint32_t cs = 8u * lane + __umulhi(excl, Q);
                 const uint32_t ball = __ballot_sync(0xffffffffu, cs <= slot);
@@ -524,12 +581,20 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         }
                     }
                     st_x[g] = xn;
-                    im.pixels[(int64_t)r * im.pitch + c] = (uint8_t)sym;
+                    dsym[base + i] = (uint8_t)sym;
                 }
-                if (lane < P) {
+                // the row is read by this CTA and, as rows r+1 and r+2, by the
+                // next two CTAs (every CTA when rows are not owned mod P)
+                if (p2p) {
+                    if (lane < min(3, P)) {
+                        const int slot = (((r >> lgP) & tqmask) << 2) | lane;
+                        const uint32_t a = tring_addr + 4u * (uint32_t)(slot * 32 + (c & 31));
+                        st_cluster_u32(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), ring_tag(r, c) | sym);
+                    }
+                } else if (lane < P) {
                     const uint32_t a = ring_addr + (uint32_t)(((r & rmask) << 4) + (c & 15));
                     if (P > 1)
-                        st_cluster_u8(map_shared(a, (uint32_t)lane), sym);
+                        st_cluster_u8(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), sym);
                     else
                         ring[((r & rmask) << 4) + (c & 15)] = (uint8_t)sym;
                 }
@@ -537,10 +602,17 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
             }
             __syncthreads();
         }
-        if (P > 1)
-            cluster_sync_all();
-        else
-            __syncthreads();
+        // The cluster barrier is arrived at before this wave's pixels go to the
+        // image, so its release waits only for the ring writes; the image
+        // stores complete during the next wave.
+        __syncthreads();   // every ring write of this wave precedes the barrier arrival
+        if (!p2p && P > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        for (int i = tid; i < nk; i += kDecThreads) {
+            const int r = rowlist[i];
+            im.pixels[(int64_t)r * im.pitch + (t - 3 * r)] = dsym[i];
+        }
+        __syncthreads();   // the row list is rebuilt only after every image store
+        if (!p2p && P > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     // final states must be back at the initial value with every word read
     for (int g = tid; g < G; g += kDecThreads)
@@ -580,12 +652,17 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     int rows = 1;
     while (rows < min(maxH, (maxW + 2) / 3) + 4) rows <<= 1;
     prm.ring_rows = rows;
+    int tq = 1;
+    // rows sharing a tagged-ring slot are P * tq apart: more than a wave's
+    // rows plus the reach of the window and a writer's lead
+    while (tq < (min(maxH, (maxW + 2) / 3) + P - 1) / P + 8) tq <<= 1;
+    prm.tq = tq;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
-    const DecTcLayout L0 = dec_layout(prm.nt, rows, prm.max_g, 0);
+    const DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0);
     const int budget = 227 * 1024 - 8192;
     prm.pay_words = L0.total < (uint32_t)budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
-    const DecTcLayout L = dec_layout(prm.nt, rows, prm.max_g, prm.pay_words);
+    const DecTcLayout L = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, prm.pay_words);
     if (L.total > (uint32_t)(227 * 1024)) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
