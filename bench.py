@@ -229,6 +229,7 @@ def run_ours(args):
     codec.close()
 
     train = measure_train(args)
+    batch = measure_batch(args)
 
     # max over ranks of the timed totals
     tot8 = sum(r8["enc"]) + sum(r8["dec"])
@@ -276,6 +277,7 @@ def run_ours(args):
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
         "train": train,
+        "batch": batch,
         "gpu_launches": K * (LAUNCHES_PER_STEP["encode"] + LAUNCHES_PER_STEP["decode"]),
         "clocks": r8["clocks"],
         "e2e": {"value": round(ws * K * N / (t_e2e * 1e-3) / 1e6, 3), "unit": "Mpix/s",
@@ -287,6 +289,70 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measure_batch(args):
+    """Batched coding (cfg 4): 64 synthetic images of uneven sizes (H 192..1536,
+    W 256..2048) encoded and decoded in one call each, INT8 network, automatic
+    stream counts and cluster sizes; also replayed as one CUDA graph."""
+    import torch
+    from paper_2207_05152_gb300 import workloads
+    from paper_2207_05152_gb300.codec import Codec
+    _, blob8, _ = workloads.models()
+    imgs = workloads.cfg4_images(64)
+    npx = int(sum(i.size for i in imgs))
+    codec = Codec(blob8)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    shapes = [i.shape for i in imgs]
+    out, offs = codec.encode(dev)
+    torch.cuda.synchronize()
+    o = offs.cpu().tolist()
+    decs = [torch.empty_like(d) for d in dev]
+    status = torch.zeros(len(imgs), dtype=torch.int32, device="cuda")
+    codec.decode(out, o, shapes, outs=decs, status=status)
+    torch.cuda.synchronize()
+    ok = status.cpu().tolist() == [0] * len(imgs) and all(torch.equal(a, b) for a, b in zip(decs, dev))
+    stream = torch.cuda.current_stream()
+    steps = max(2, args.steps // 3)
+    enc, dcd = [], []
+    for it in range(steps + 1):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        codec.encode(dev, out=out, offsets=offs)
+        e1.record(stream)
+        codec.decode(out, o, shapes, outs=decs, status=status)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if it:
+            enc.append(e0.elapsed_time(e1))
+            dcd.append(e1.elapsed_time(e2))
+    res = {"workload": "cfg4: 64 Voronoi images, H 192..1536, W 256..2048, INT8 12-128-128-256, "
+                       "automatic streams and cluster sizes", "images": len(imgs), "pixels": npx,
+           "enc_mpix_s": round(npx / (statistics.mean(enc) * 1e-3) / 1e6, 2),
+           "dec_mpix_s": round(npx / (statistics.mean(dcd) * 1e-3) / 1e6, 2),
+           "roundtrip_mpix_s": round(npx / ((statistics.mean(enc) + statistics.mean(dcd)) * 1e-3) / 1e6, 2),
+           "bpp": round(8.0 * o[-1] / npx, 4), "roundtrip_bit_exact": ok}
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            codec.encode(dev, out=out, offsets=offs)
+            codec.decode(out, o, shapes, outs=decs, status=status)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["graph_roundtrip_mpix_s"] = round(steps * npx / (e0.elapsed_time(e1) * 1e-3) / 1e6, 2)
+        res["graph_bit_exact"] = status.cpu().tolist() == [0] * len(imgs) and all(
+            torch.equal(a, b) for a, b in zip(decs, dev))
+    except RuntimeError as exc:
+        res["graph_roundtrip_mpix_s"] = None
+        res["graph_error"] = str(exc)[:200]
+    codec.close()
+    return res
 
 
 TRAIN_BATCH = 65536

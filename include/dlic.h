@@ -105,10 +105,12 @@ DLIC_API dlic_status dlic_model_info(const dlic_model *model, int *precision, in
  * words per stream. */
 DLIC_API size_t dlic_max_encoded_bytes(int height, int width, int streams);
 
-/* Stream count the library picks when the caller passes none: one stream
- * per pixel a wave can hold, min(height, ceil(width / 3)), so that no two
- * pixels of a wave share a stream (Sec. II-B "rANS": at most one coder
- * instance per row). */
+/* Stream count the library picks when the caller passes none: at least one
+ * stream per pixel a wave can hold, ceil(width / 3) rounded up to a multiple
+ * of 16, but at most one per row (Sec. II-B "rANS": at most one coder
+ * instance per row): min(height, 16 * ceil(ceil(width / 3) / 16)).  No two
+ * pixels of a wave share a stream, and the decoder can split the streams
+ * evenly over clusters of up to 16 CTAs. */
 DLIC_API int dlic_auto_streams(int height, int width);
 
 /* Device workspace, in bytes, that dlic_encode needs for this batch. */
@@ -186,7 +188,10 @@ DLIC_API dlic_status dlic_decode_workspace_size(const dlic_model *model, const d
  * the dimensions the caller expects (from dlic_read_header).  Pixels are
  * decoded as a wavefront: wave t holds the pixels with 3r + c = t, all of
  * whose causal priors lie on earlier waves, and each wave's pixels are
- * predicted and decoded in parallel.  d_status (n int32, device) receives
+ * predicted and decoded in parallel.  Each image is decoded by a cluster of
+ * 1 to 16 CTAs chosen by a cost model (larger images get larger clusters
+ * while the batch fits on the GPU); images with different cluster sizes run
+ * concurrently on internal streams forked from and joined back to `stream`.  d_status (n int32, device) receives
  * DLIC_OK or DLIC_ERR_CORRUPT per image (header mismatch, model hash
  * mismatch, stream overrun, or a final state other than the initial one). */
 DLIC_API dlic_status dlic_decode(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,

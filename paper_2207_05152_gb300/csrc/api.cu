@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -27,6 +28,8 @@ dlic_status cuda_fail(cudaError_t e, const char *what) {
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
 bool tc_decode_supported(const DevModel &m);
+void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P);
+constexpr int kDecodeGroups = 5;   // cluster sizes 1, 2, 4, 8, 16
 
 static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -59,6 +62,10 @@ struct dlic_model {
     void *mem = nullptr;
     int device = 0;
     int num_sms = 0;
+    // streams and events of the batched decoder: one stream per cluster size,
+    // forked from and joined back to the caller's stream
+    cudaStream_t group_stream[kDecodeGroups] = {};
+    cudaEvent_t fork_event = nullptr, join_event[kDecodeGroups] = {};
 };
 
 extern "C" const char *dlic_last_error(void) { return g_err; }
@@ -163,6 +170,15 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         delete m;
         return cuda_fail(e, "cudaMemcpy(model)");
     }
+    for (int g = 0; g < kDecodeGroups && e == cudaSuccess; g++) {
+        e = cudaStreamCreateWithFlags(&m->group_stream[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->join_event[g], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        dlic_model_destroy(m);
+        return cuda_fail(e, "stream / event creation");
+    }
     uint8_t *base = static_cast<uint8_t *>(m->mem);
     d.lut = reinterpret_cast<const uint32_t *>(base + off_lut);
     if (prec == DLIC_FP32) {
@@ -191,7 +207,12 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
 
 extern "C" dlic_status dlic_model_destroy(dlic_model *m) {
     if (!m) return DLIC_OK;
-    cudaError_t e = cudaFree(m->mem);
+    for (int g = 0; g < kDecodeGroups; g++) {
+        if (m->group_stream[g]) cudaStreamDestroy(m->group_stream[g]);
+        if (m->join_event[g]) cudaEventDestroy(m->join_event[g]);
+    }
+    if (m->fork_event) cudaEventDestroy(m->fork_event);
+    cudaError_t e = m->mem ? cudaFree(m->mem) : cudaSuccess;
     delete m;
     return e == cudaSuccess ? DLIC_OK : cuda_fail(e, "cudaFree(model)");
 }
@@ -214,9 +235,9 @@ extern "C" size_t dlic_max_encoded_bytes(int height, int width, int streams) {
 
 extern "C" int dlic_auto_streams(int height, int width) {
     if (height < 1 || width < 1) return 0;
-    int s = (width + 2) / 3;
+    int s = ((width + 2) / 3 + 15) / 16 * 16;
     if (s > height) s = height;
-    if (s > 65535) s = 65535;
+    if (s > 65520) s = 65520;
     return s < 1 ? 1 : s;
 }
 
@@ -376,29 +397,74 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     }
     const bool use_tc = tc_decode_supported(m->dev);
-    size_t off = 0;
-    for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
-        const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
-        DecBatch *b = new DecBatch();
-        b->n = cn;
-        b->in = static_cast<const uint8_t *>(d_in);
-        b->ws = static_cast<uint8_t *>(d_ws);
-        b->status = d_status + c0;
-        for (int k = 0; k < cn; k++) {
-            const dlic_image &g = im[c0 + k];
-            DecImage &e = b->img[k];
-            e.pixels = g.pixels;
-            e.pitch = g.pitch;
-            e.H = g.height;
-            e.W = g.width;
-            e.in_off = h_in_offsets[c0 + k];
-            e.in_bytes = h_in_offsets[c0 + k + 1] - h_in_offsets[c0 + k];
-            e.st_off = off;
-            off += align256(16ull * g.height);
+    // workspace offsets of every image's stream states
+    std::vector<size_t> st_off(n);
+    {
+        size_t off = 0;
+        for (int i = 0; i < n; i++) {
+            st_off[i] = off;
+            off += align256(16ull * im[i].height);
         }
-        cudaError_t e = use_tc ? launch_decode_tc(m->dev, *b, 0, m->num_sms, cs) : launch_decode_cc(m->dev, *b, cs);
-        delete b;
-        if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    }
+    // cluster size of every image (1 on the CUDA-core path)
+    std::vector<int> P(n, 1), Hs(n), Ws(n);
+    for (int i = 0; i < n; i++) {
+        Hs[i] = im[i].height;
+        Ws[i] = im[i].width;
+    }
+    if (use_tc) choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, P.data());
+    int groups_used = 0;
+    for (int gi = 0; gi < kDecodeGroups; gi++)
+        for (int i = 0; i < n; i++)
+            if (P[i] == (1 << gi)) {
+                groups_used++;
+                break;
+            }
+    const bool fork = groups_used > 1;
+    if (fork) {
+        cudaError_t e = cudaEventRecord(m->fork_event, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "fork event");
+    }
+    for (int gi = 0; gi < kDecodeGroups; gi++) {
+        const int cluster = 1 << gi;
+        std::vector<int> members;
+        for (int i = 0; i < n; i++)
+            if (P[i] == cluster) members.push_back(i);
+        if (members.empty()) continue;
+        cudaStream_t gs = fork ? m->group_stream[gi] : cs;
+        if (fork) {
+            cudaError_t e = cudaStreamWaitEvent(gs, m->fork_event, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "fork wait");
+        }
+        for (size_t c0 = 0; c0 < members.size(); c0 += kMaxBatch) {
+            const int cn = (int)std::min<size_t>(kMaxBatch, members.size() - c0);
+            DecBatch *b = new DecBatch();
+            b->n = cn;
+            b->in = static_cast<const uint8_t *>(d_in);
+            b->ws = static_cast<uint8_t *>(d_ws);
+            b->status = d_status;
+            for (int k = 0; k < cn; k++) {
+                const int i = members[c0 + k];
+                const dlic_image &g = im[i];
+                DecImage &e = b->img[k];
+                e.pixels = g.pixels;
+                e.pitch = g.pitch;
+                e.H = g.height;
+                e.W = g.width;
+                e.in_off = h_in_offsets[i];
+                e.in_bytes = h_in_offsets[i + 1] - h_in_offsets[i];
+                e.st_off = st_off[i];
+                e.sidx = i;
+            }
+            cudaError_t e = use_tc ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, gs) : launch_decode_cc(m->dev, *b, gs);
+            delete b;
+            if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+        }
+        if (fork) {
+            cudaError_t e = cudaEventRecord(m->join_event[gi], gs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, m->join_event[gi], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "join");
+        }
     }
     return DLIC_OK;
 }

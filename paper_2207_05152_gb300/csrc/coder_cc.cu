@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
     int S;
     const uint16_t *pay;
     if (!decode_setup(m, im, in, st, &S, &pay)) {
-        if (tid == 0) b.status[blockIdx.x] = DLIC_ERR_CORRUPT;
+        if (tid == 0) b.status[im.sidx] = DLIC_ERR_CORRUPT;
         return;
     }
     float *zs = reinterpret_cast<float *>(smem);                        // [256][CH]
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
         if (q.x != kRansL || q.pos != q.end) s_err = 1;
     }
     __syncthreads();
-    if (tid == 0) b.status[blockIdx.x] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
+    if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
 }
 
 template <int PREC>

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     tc::fence_after_sync();
     // Every CTA of the cluster reads the same header, so this exit is uniform.
     if (!s_ok) {
-        if (tid == 0 && k == 0) atomicMax(b.status + img_idx, (int)DLIC_ERR_CORRUPT);
+        if (tid == 0 && k == 0) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
         if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
         return;
     }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     // CTAs then wait for the very values they read instead of for each other,
     // and no cluster barrier runs per wave.  A CTA can run at most P - 1
     // waves ahead of a reader, and a row's 32 ring columns outlive 24 waves.
-    const bool p2p = P >= 2 && P <= 16 && (S % P) == 0;
+    const bool p2p = prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0;
     uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
     const uint32_t tring_addr = tc::smem_addr(tring);
     const int tqmask = prm.tq - 1;
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && (s_err || s_fail))
-        atomicMax(b.status + img_idx, s_fail ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
+        atomicMax(b.status + im.sidx, s_fail ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tm, 256);
@@ -628,13 +628,59 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     if (P > 1) cluster_sync_all();   // no CTA leaves while others may still write its ring
 }
 
+// Cluster sizes for a batch (the decode autotuner).  A wave of an image
+// whose CTAs hold p pixels costs about kWaveFixed cycles (gather, three MMA
+// round trips, epilogues) plus kWavePerPixelWarp per pixel and table warp
+// (16 warps), over chunks of at most 64 pixels; an image takes waves x that.
+// Starting from one CTA per image, the image with the longest estimate gets
+// its cluster doubled while the clusters of the whole batch still fit on the
+// GPU at once (up to 16 CTAs).
+constexpr double kWaveFixed = 4500.0, kWavePerPixelWarp = 1700.0;
+
+static double est_cycles(int H, int W, int P) {
+    const double waves = 3.0 * (H - 1) + W;
+    const int wave_px = min(H, (W + 2) / 3);
+    int per = (wave_px + P - 1) / P;
+    double per_wave = 0.0;
+    while (per > 0) {
+        const int chunk = min(per, 64);
+        per_wave += kWaveFixed + kWavePerPixelWarp * ((chunk + kDecWarps - 1) / kDecWarps);
+        per -= chunk;
+    }
+    return waves * per_wave;
+}
+
+void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P) {
+    int used = 0;
+    for (int i = 0; i < n; i++) {
+        P[i] = 1;
+        used += 1;
+    }
+    for (;;) {
+        int best = -1;
+        double worst = 0.0;
+        for (int i = 0; i < n; i++) {
+            if (P[i] >= 16 || used + P[i] > num_sms) continue;
+            const double t = est_cycles(H[i], W[i], P[i]);
+            if (t > worst) {
+                worst = t;
+                best = i;
+            }
+        }
+        if (best < 0) break;
+        // stop when the longest image no longer gains from a larger cluster
+        if (est_cycles(H[best], W[best], 2 * P[best]) >= worst) break;
+        used += P[best];
+        P[best] *= 2;
+    }
+}
+
 bool tc_decode_supported(const DevModel &m) {
     return m.precision == DLIC_INT8 && m.tc_w != nullptr && m.h1 == kDecHidden && m.h2 == kDecHidden;
 }
 
-// Chooses the cluster size and chunking for a batch and launches the kernel.
-// P = 8 when the batch is small enough for every image to get its own
-// 8-SM cluster, else one CTA per image.
+// Launches one cluster of `cluster` CTAs per image of the batch (stepping
+// down when a cluster that large cannot be scheduled).
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st) {
     if (b.n == 0) return cudaSuccess;
     int maxH = 1, maxW = 1;
@@ -642,8 +688,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         maxH = max(maxH, b.img[i].H);
         maxW = max(maxW, b.img[i].W);
     }
-    int P = cluster;
-    if (P <= 0) P = (b.n * 16 <= num_sms) ? 16 : (b.n * 8 <= num_sms ? 8 : 1);
+    int P = cluster > 0 ? cluster : 1;
     const int wave_px = min(maxH, (maxW + 2) / 3);
     const int per_cta = (wave_px + P - 1) / P + 1;
     DecTcParams prm;
@@ -652,10 +697,16 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     int rows = 1;
     while (rows < min(maxH, (maxW + 2) / 3) + 4) rows <<= 1;
     prm.ring_rows = rows;
-    int tq = 1;
-    // rows sharing a tagged-ring slot are P * tq apart: more than a wave's
-    // rows plus the reach of the window and a writer's lead
-    while (tq < (min(maxH, (maxW + 2) / 3) + P - 1) / P + 8) tq <<= 1;
+    // Tagged ring (neighbour-to-neighbour mode) only when it stays small;
+    // otherwise the kernel synchronises the cluster once per wave.  Rows
+    // sharing a tagged-ring slot are P * tq apart: more than a wave's rows
+    // plus the reach of the window and a writer's lead.
+    int tq = 0;
+    if (P >= 2) {
+        tq = 1;
+        while (tq < (min(maxH, (maxW + 2) / 3) + P - 1) / P + 8) tq <<= 1;
+        if (4 * tq * 128 > 32768) tq = 0;
+    }
     prm.tq = tq;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
     const DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0);

@@ -68,6 +68,7 @@ struct DecImage {
     uint64_t in_off;              // byte offset of the bitstream in d_in
     uint64_t in_bytes;
     uint64_t st_off;              // per-stream state (x, pos, end) in workspace
+    int32_t sidx;                 // index of the image's status word
 };
 
 struct DecBatch {

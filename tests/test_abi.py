@@ -37,9 +37,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_side_helpers(lib):
     assert lib.dlic_max_encoded_bytes(64, 64, 32) == 24 + 4 * 32 + 2 * (4096 + 64)
     assert lib.dlic_max_encoded_bytes(3, 10, 99) == 24 + 4 * 3 + 2 * (30 + 6)
-    assert lib.dlic_auto_streams(512, 512) == 171
+    assert lib.dlic_auto_streams(512, 512) == 176
     assert lib.dlic_auto_streams(100, 2048) == 100
-    assert lib.dlic_auto_streams(64, 64) == 22
+    assert lib.dlic_auto_streams(64, 64) == 32
+    assert lib.dlic_auto_streams(5, 64) == 5
 
 
 def test_header_parser_and_model_checks(lib, orc):

@@ -32,7 +32,9 @@ def _check(Codec, orc, blob, imgs, streams):
     codec = Codec(blob)
     got = codec.encode_to_bytes([torch.from_numpy(np.ascontiguousarray(i)).cuda() for i in imgs], streams)
     for k, img in enumerate(imgs):
-        want = orc.encode(blob, img, streams[k] if streams else min(img.shape[0], (img.shape[1] + 2) // 3))
+        from paper_2207_05152_gb300 import _lib
+        S = streams[k] if streams else _lib.dlic_auto_streams(img.shape[0], img.shape[1])
+        want = orc.encode(blob, img, S)
         assert got[k] == want, f"image {k}: bitstream differs from the oracle"
     dec, status = codec.decode_bytes(got)
     assert status == [0] * len(imgs)
@@ -114,4 +116,36 @@ def test_corrupt_and_capacity(Codec, orc, prec, widths):
         _lib.dlic_encode(codec.handle, codec._desc([t]), [4], out.data_ptr(), out.numel(),
                          offs.data_ptr(), 0, ws.data_ptr(), ws.numel(), 0)
     assert e.value.code == _lib.DLIC_ERR_CAPACITY
+    codec.close()
+
+
+def test_batched_decode_mixed_cluster_sizes(Codec, orc):
+    # Twelve images of different sizes in one call: the autotuner gives them
+    # different cluster sizes, which run as concurrent groups.
+    sizes = [(30, 40), (64, 64), (100, 180), (20, 300), (150, 90), (200, 260), (45, 45), (120, 400),
+             (16, 16), (90, 120), (300, 200), (60, 500)]
+    imgs = [synth.voronoi_image(h, w, 500 + i) for i, (h, w) in enumerate(sizes)]
+    blob = _models([12, 128, 128, 256], 8, imgs[:3])["int8"]
+    _check(Codec, orc, blob, imgs, None)
+
+
+def test_decode_inside_cuda_graph(Codec, orc):
+    img = synth.voronoi_image(96, 160, 21)
+    blob = _models([12, 128, 128, 256], 9, [img])["int8"]
+    codec = Codec(blob)
+    d_img = torch.from_numpy(img).cuda()
+    out, offs = codec.encode([d_img], None)
+    torch.cuda.synchronize()
+    o = offs.cpu().tolist()
+    dec = torch.empty_like(d_img)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    codec.decode(out, o, [img.shape], outs=[dec], status=status)   # warm-up outside capture
+    torch.cuda.synchronize()
+    dec.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        codec.decode(out, o, [img.shape], outs=[dec], status=status)
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and torch.equal(dec, d_img)
     codec.close()
