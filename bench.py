@@ -230,6 +230,7 @@ def run_ours(args):
 
     train = measure_train(args)
     batch = measure_batch(args)
+    domain = measure_domain_training(args)
 
     # max over ranks of the timed totals
     tot8 = sum(r8["enc"]) + sum(r8["dec"])
@@ -278,6 +279,7 @@ def run_ours(args):
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
         "train": train,
         "batch": batch,
+        "domain_training": domain,
         "gpu_launches": K * (LAUNCHES_PER_STEP["encode"] + LAUNCHES_PER_STEP["decode"]),
         "clocks": r8["clocks"],
         "e2e": {"value": round(ws * K * N / (t_e2e * 1e-3) / 1e6, 3), "unit": "Mpix/s",
@@ -353,6 +355,62 @@ def measure_batch(args):
         res["graph_error"] = str(exc)[:200]
     codec.close()
     return res
+
+
+def measure_domain_training(args, steps: int = 2000):
+    """cfg 5: train 12-128-128-256 for 2000 BF16 steps (batch 65536) on 128
+    synthetic MRI-like 512x512 slices, quantise to INT8, code the 128 slices;
+    bpp and Mpix/s against the untrained (Xavier) network."""
+    import torch
+    import synth
+    from paper_2207_05152_gb300 import model as M
+    from paper_2207_05152_gb300 import train as T
+    from paper_2207_05152_gb300 import workloads
+    from paper_2207_05152_gb300.codec import Codec
+    imgs = workloads.cfg5_images(128)
+    npx = int(sum(i.size for i in imgs))
+    pool_ctx, pool_tgt = T.sample_contexts(imgs, 1 << 21, 5001)
+    calib = pool_ctx[:4096]
+    pc, pt = torch.from_numpy(pool_ctx).cuda(), torch.from_numpy(pool_tgt).cuda()
+    layers0 = synth.xavier_mlp([12, 128, 128, 256], 5)
+    tr = T.Trainer(layers0, "bf16", max_batch=TRAIN_BATCH)
+    gen = torch.Generator(device="cuda").manual_seed(5002)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        idx = torch.randint(0, pc.shape[0], (TRAIN_BATCH,), device="cuda", generator=gen)
+        c, t = pc.index_select(0, idx).contiguous(), pt.index_select(0, idx).contiguous()
+        tr.step(c, t)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    final_loss = float(tr.loss.item())
+    assert tr.status() == 0
+    trained = tr.layers()
+    tr.close()
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    out = {"workload": "cfg5: 128 synthetic MRI-like 512x512 slices; 2000 BF16 steps of batch 65536 "
+                       "from 2M sampled contexts, then INT8 coding", "steps": steps,
+           "train_seconds": round(train_s, 3), "final_loss_bits": round(final_loss, 4)}
+    for name, layers in (("untrained", layers0), ("trained", trained)):
+        codec = Codec(M.int8_blob(layers, calib))
+        enc_out, offs = codec.encode(dev)
+        torch.cuda.synchronize()
+        o = offs.cpu().tolist()
+        decs = [torch.empty_like(d) for d in dev]
+        status = torch.zeros(len(imgs), dtype=torch.int32, device="cuda")
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        codec.encode(dev, out=enc_out, offsets=offs)
+        e1.record(stream)
+        codec.decode(enc_out, o, [i.shape for i in imgs], outs=decs, status=status)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ok = status.cpu().tolist() == [0] * len(imgs) and all(torch.equal(a, b) for a, b in zip(decs, dev))
+        out[name] = {"bpp": round(8.0 * o[-1] / npx, 4), "enc_mpix_s": round(npx / (e0.elapsed_time(e1) * 1e-3) / 1e6, 2),
+                     "dec_mpix_s": round(npx / (e1.elapsed_time(e2) * 1e-3) / 1e6, 2), "roundtrip_bit_exact": ok}
+        codec.close()
+    return out
 
 
 TRAIN_BATCH = 65536

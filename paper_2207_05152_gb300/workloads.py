@@ -40,3 +40,9 @@ def cfg2_image() -> np.ndarray:
 
 def cfg4_images(count: int = 64, seed: int = 4000, **size_kw):
     return synth.batch_images(count, seed, **size_kw)
+
+
+def cfg5_images(count: int = 128, seed: int = 5000):
+    """MRI-like slices: elliptical phantoms with a bias field and Rician noise."""
+    import synth as _s
+    return [_s.phantom_image(512, 512, seed + i) for i in range(count)]
