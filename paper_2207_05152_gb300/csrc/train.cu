@@ -221,11 +221,17 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
 // ---------------------------------------------------------------------------
 // tcgen05 GEMM: C[M x N] = A[M x K] * B[N x K]^T, bf16 operands fed by TMA
 // (128-byte swizzle, 64-element K blocks), FP32 accumulators in tensor
-// memory, a fused row epilogue.  One 128 x N tile per CTA (N <= 256); split-K
-// over gridDim.z for EPI_F32.  Warp 0 loads, warp 1 issues MMAs, warps 2..5
-// run the epilogue (one output row per thread).
+// memory, a fused epilogue.  One 128 x N tile per CTA (N <= 256); split-K
+// over gridDim.z for EPI_F32.  Warp 0 loads, warp 1 issues MMAs, warps 2..9
+// run the epilogue: two warps per tensor-memory lane quarter, each on half of
+// the columns of its 32 rows.  Row-major outputs leave as 16-byte vectors;
+// transposed outputs are staged in shared memory (the drained pipeline
+// stages) and written as coalesced 16-byte rows.  Two stages keep a CTA at
+// 96 KB so that two CTAs share an SM (BF16 mode).
 // ---------------------------------------------------------------------------
-constexpr int kGemmThreads = 192;
+constexpr int kGemmThreads = 320;
+constexpr int kEpiThreads = 256;
+constexpr int kGemmStages = 2;
 
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     uint64_t d = 0;
@@ -246,21 +252,53 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, %0;" ::"r"(kEpiThreads) : "memory"); }
+
+// 16 values as bf16 (and their low parts) in the two layouts: row-major
+// vectors to global memory, transposed 2-byte entries to the staging tile.
+__device__ __forceinline__ void emit16(const EpiArgs &e, const float (&v)[16], int m, int row, int n0, bool valid,
+                                       uint16_t *Thi, uint16_t *Tlo, bool rowmajor) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint16_t a = f2bf(v[2 * j]), b = f2bf(v[2 * j + 1]);
+        hi[j] = a | ((uint32_t)b << 16);
+        lo[j] = f2bf(v[2 * j] - bf2f(a)) | ((uint32_t)f2bf(v[2 * j + 1] - bf2f(b)) << 16);
+        Thi[(n0 + 2 * j) * 128 + row] = a;
+        Thi[(n0 + 2 * j + 1) * 128 + row] = b;
+        if (e.split) {
+            Tlo[(n0 + 2 * j) * 128 + row] = (uint16_t)lo[j];
+            Tlo[(n0 + 2 * j + 1) * 128 + row] = (uint16_t)(lo[j] >> 16);
+        }
+    }
+    if (rowmajor && valid) {
+        uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + (size_t)m * e.N + n0);
+        o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        o[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+        if (e.split) {
+            uint4 *ol = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + e.out_plane + (size_t)m * e.N + n0);
+            ol[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            ol[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+        }
+    }
+}
 
 // SPLIT: operands come as high and low bf16 planes (x = hi + lo) and every K
 // step issues hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits of
 // each operand.
 template <bool SPLIT>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapAl, const __grid_constant__ CUtensorMap mapBl, int K,
               int kb_per_split, int epi, EpiArgs e, int *err) {
-    constexpr int kGemmStages = SPLIT ? 2 : 4;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full[kGemmStages], empty[kGemmStages], accum;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
+    __shared__ float cs[256];
+    __shared__ float red[2][2][128];
+    __shared__ float s_loss[kGemmThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = e.N;
     const uint32_t a_bytes = 128 * 128, b_bytes = (uint32_t)N * 128;
@@ -285,6 +323,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tc::fence_mbar_init();
         s_fail = 0;
     }
+    for (int n = tid; n < 256; n += kGemmThreads) cs[n] = 0.0f;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -326,42 +365,140 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             }
             tc::mma_commit(&empty[s]);
         }
-        if (nkb == 0) {
-            // nothing to accumulate: no MMA has written the accumulator
-        }
         tc::mma_commit(&accum);
     } else if (warp >= 2) {
-        // epilogue: wait for the accumulator, then one row per thread
-        const int q = warp & 3;
-        const int row = 32 * q + lane;
         if (lane == 0 && !tc::mbar_wait(&accum, 0, kGemmWaitLimit)) s_fail = 1;
         __syncwarp();
         tc::mbar_wait(&accum, 0, 1000);   // every lane observes the completed phase
         tc::fence_after_sync();
     }
-    // shared column sums reuse the first pipeline stage (all loads consumed)
+    // all loads and MMAs are done: the pipeline stages become the staging tiles
+    __syncwarp();
     asm volatile("bar.sync 1, %0;" ::"r"(kGemmThreads) : "memory");
-    float *cs = reinterpret_cast<float *>(smem);
-    if (e.colsum)
-        for (int n = tid; n < N; n += kGemmThreads) cs[n] = 0.0f;
-    __syncthreads();
+    uint16_t *Thi = reinterpret_cast<uint16_t *>(smem);
+    uint16_t *Tlo = Thi + (size_t)N * 128;
     float loss_acc = 0.0f;
-    if (warp >= 2 && !s_fail) {
-        const int q = warp & 3;
-        const int row = 32 * q + lane;
-        const int m = m0 + row;
+    const bool staged = epi != EPI_F32;
+    if (warp >= 2) {
+        const int q = warp & 3, hf = (warp - 2) >> 2;
+        const int row = 32 * q + lane, m = m0 + row;
+        const bool valid = m < e.M;
+        // the two halves split the 16-column chunks (the first takes the odd one)
+        const int nch = N / 16, first = (nch + 1) / 2;
+        const int n_lo = hf ? 16 * first : 0, n_hi = hf ? N : 16 * first;
+        const bool active = !s_fail && n_lo < n_hi;
         TmemRow src{tm + ((uint32_t)(32 * q) << 16)};
-        if (nkb > 0) {
-            row_epilogue(epi, e, src, m, m < e.M, e.colsum ? cs : nullptr, &loss_acc);
-        } else if (epi == EPI_F32 && m < e.M) {
-            float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
-            for (int n = 0; n < N; n++) c[n] = 0.0f;
+        if (epi == EPI_F32) {
+            if (active && valid) {
+                float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    if (nkb > 0) {
+                        src.load16(n0, v);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) v[j] = 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(c + n0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+        } else if (epi == EPI_BIAS_RELU) {
+            if (active)
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    src.load16(n0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] = fmaxf(v[j] + e.bias[n0 + j], 0.0f);
+                    emit16(e, v, m, row, n0, valid, Thi, Tlo, true);
+                }
+        } else if (epi == EPI_RELU_GRAD) {
+            if (active)
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    src.load16(n0, v);
+                    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
+                    if (valid) {
+                        const uint4 *ap = reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(e.act) + (size_t)m * N + n0);
+                        a0 = ap[0];
+                        a1 = ap[1];
+                    }
+                    const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const uint32_t bits = (aw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                        const bool pos = valid && bits != 0 && (bits & 0x8000u) == 0;   // bf16 > 0
+                        v[j] = pos ? v[j] : 0.0f;
+                    }
+                    emit16(e, v, m, row, n0, valid, Thi, Tlo, e.out != nullptr);
+                    if (e.colsum) colsum_add(cs + n0, v);
+                }
+        } else {
+            // EPI_SOFTMAX over the full row: halves combine through shared memory
+            float mx = -INFINITY;
+            if (active)
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    src.load16(n0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) mx = fmaxf(mx, v[j] + e.bias[n0 + j]);
+                }
+            red[0][hf][row] = mx;
+            epi_sync();
+            mx = fmaxf(red[0][0][row], red[0][1][row]);
+            float se = 0.0f;
+            if (active)
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    src.load16(n0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) se += expf(v[j] + e.bias[n0 + j] - mx);
+                }
+            red[1][hf][row] = se;
+            epi_sync();
+            se = red[1][0][row] + red[1][1][row];
+            const float lse = mx + logf(se), inv = 1.0f / se;
+            const int y = valid ? e.tgt[m] : -1;
+            if (active)
+                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+                    float v[16];
+                    src.load16(n0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const float zz = v[j] + e.bias[n0 + j];
+                        float g = expf(zz - mx) * inv;
+                        if (n0 + j == y) {
+                            g -= 1.0f;
+                            loss_acc += (lse - zz) / kLn2;
+                        }
+                        v[j] = valid ? g * e.inv_batch_ln2 : 0.0f;
+                    }
+                    emit16(e, v, m, row, n0, valid, Thi, Tlo, true);
+                    if (e.colsum) colsum_add(cs + n0, v);
+                }
+        }
+        if (staged && !s_fail) {
+            // transposed tile -> outT[n][m0 ..] as 16-byte rows
+            epi_sync();
+            const int et = tid - 64;
+            for (int idx = et; idx < N * 16; idx += kEpiThreads) {
+                const int n = idx >> 4, ml = (idx & 15) * 8, gm = m0 + ml;
+                uint16_t *dst = static_cast<uint16_t *>(e.outT) + (size_t)n * e.ldT + gm;
+                const uint4 vh = *reinterpret_cast<const uint4 *>(Thi + n * 128 + ml);
+                if (gm + 8 <= e.M) {
+                    *reinterpret_cast<uint4 *>(dst) = vh;
+                    if (e.split) *reinterpret_cast<uint4 *>(dst + e.outT_plane) = *reinterpret_cast<const uint4 *>(Tlo + n * 128 + ml);
+                } else {
+                    for (int j = 0; j < 8 && gm + j < e.M; j++) {
+                        dst[j] = Thi[n * 128 + ml + j];
+                        if (e.split) dst[j + e.outT_plane] = Tlo[n * 128 + ml + j];
+                    }
+                }
+            }
         }
     }
-    if (e.loss) {
-        for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-    }
-    __shared__ float s_loss[kGemmThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
     if (lane == 0) s_loss[warp] = loss_acc;
     tc::fence_before_sync();
     __syncthreads();
@@ -519,23 +656,50 @@ __global__ void __launch_bounds__(256) k_layer1_f32(const uint8_t *ctx, int B, c
 }
 
 // out[i] = sum_z part[z * stride + i] (fixed order: deterministic)
-__global__ void k_sum_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// out[i] = scale * sum_z part[z * stride + i]: 32 columns per block, the
+// partials split over blockDim.y row groups and combined in a fixed order
+// (deterministic).  With `pad16` the columns are a [h][16] array whose first
+// kPriors entries per row go to a compact [h][kPriors] output.
+__global__ void k_reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int pad16) {
+    __shared__ float red[32][33];
+    const int x = threadIdx.x, y = threadIdx.y, G = blockDim.y;
+    const int i = blockIdx.x * 32 + x;
     float s = 0.0f;
-    for (int z = 0; z < nparts; z++) s += part[(size_t)z * stride + i];
-    out[i] = s * scale;
+    if (i < n) {
+#pragma unroll 4
+        for (int z = y; z < nparts; z += G) s += part[(size_t)z * stride + i];
+    }
+    red[y][x] = s;
+    __syncthreads();
+    if (y == 0 && i < n) {
+        float t = 0.0f;
+        for (int k = 0; k < G; k++) t += red[k][x];
+        t *= scale;
+        if (!pad16) out[i] = t;
+        else if (i % 16 < kPriors) out[(i / 16) * kPriors + i % 16] = t;
+    }
 }
 
-// dW1 is computed against 16 padded feature columns; keep the first 12.
-__global__ void k_compact_w1(const float *g16, int h1, float *g12) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= h1 * kPriors) return;
-    g12[i] = g16[(i / kPriors) * 16 + (i % kPriors)];
+// One shadow entry: bf16 high (and low) planes, or FP32.
+__device__ __forceinline__ void shadow_put(void *Wd, size_t idx, size_t plane, float v, int bf16, int split) {
+    if (bf16) {
+        const uint16_t hi = f2bf(v);
+        reinterpret_cast<uint16_t *>(Wd)[idx] = hi;
+        if (split) reinterpret_cast<uint16_t *>(Wd)[idx + plane] = f2bf(v - bf2f(hi));
+    } else {
+        reinterpret_cast<float *>(Wd)[idx] = v;
+    }
 }
 
+// Adam on the FP32 master weights (bias-corrected, Kingma & Ba) with the
+// updated weights written straight into the GEMM operand copies (row-major
+// and transposed).  The zero padding of the W1 copy is never touched.
+struct ShadowArgs {
+    int h1, h2, bf16, split;
+    void *w1, *w2, *w3, *w2t, *w3t;
+};
 __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2) {
+                       float c1, float c2, ShadowArgs sa) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -543,11 +707,22 @@ __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, fl
     const float v = b2 * ve[i] + (1.0f - b2) * gi * gi;
     mo[i] = m;
     ve[i] = v;
-    p[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    const float w = p[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    p[i] = w;
+    const int h1 = sa.h1, h2 = sa.h2;
+    const int oW2 = h1 * kPriors + h1, oW3 = oW2 + h2 * h1 + h2;
+    if (i < h1 * kPriors) {
+        shadow_put(sa.w1, (size_t)(i / kPriors) * 16 + i % kPriors, (size_t)h1 * 16, w, sa.bf16, sa.split);
+    } else if (i >= oW2 && i < oW2 + h2 * h1) {
+        const int j = i - oW2, o = j / h1, k = j % h1;
+        shadow_put(sa.w2, j, (size_t)h2 * h1, w, sa.bf16, sa.split);
+        shadow_put(sa.w2t, (size_t)k * h2 + o, (size_t)h1 * h2, w, sa.bf16, sa.split);
+    } else if (i >= oW3 && i < oW3 + kSymbols * h2) {
+        const int j = i - oW3, o = j / h2, k = j % h2;
+        shadow_put(sa.w3, j, (size_t)kSymbols * h2, w, sa.bf16, sa.split);
+        shadow_put(sa.w3t, (size_t)k * kSymbols + o, (size_t)h2 * kSymbols, w, sa.bf16, sa.split);
+    }
 }
-
-// Operand copies of the weights: W [out][in] (W1 padded to 16 inputs) and
-// W^T [in][out], in bf16 or fp32.
 __global__ void k_shadow(const float *W, int out, int in, int in_pad, void *Wd, void *WTd, int bf16, int split) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= out * in_pad) return;
@@ -583,7 +758,7 @@ struct dlic_trainer {
     float *params, *grads, *mom, *vel;           // FP32 master state
     void *w1, *w2, *w3, *w2t, *w3t;              // operand copies (bf16 or fp32)
     void *X, *XT, *H1, *H1T, *H2, *H2T, *DZ, *DZT, *DA2, *DA2T, *DA1T;
-    float *C, *part, *colsum, *losspart, *g16;
+    float *C, *part, *colsum, *losspart;
     int *err;
     std::vector<void *> allocs;
 };
@@ -658,7 +833,7 @@ dlic_status gemm(dlic_trainer *t, const void *A, int lda, size_t aplane, const v
         const int nkb = (K + 63) / 64;
         const int per = (nkb + splits - 1) / splits;
         const uint32_t stage = 128 * 128 + ((uint32_t)N * 128 + 1023) / 1024 * 1024;
-        const size_t smem = (size_t)(t->split ? 2 * 2 : 4) * stage + 1024;
+        const size_t smem = (size_t)kGemmStages * (t->split ? 2 : 1) * stage + 1024;
         if (t->split) {
             cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_gemm_tc<true><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, e, t->err);
@@ -679,6 +854,12 @@ dlic_status gemm(dlic_trainer *t, const void *A, int lda, size_t aplane, const v
     if (epi != EPI_F32) k_row_epilogue<<<mt, 128, N * sizeof(float), st>>>(t->C, epi, e);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "fp32 gemm launch");
+}
+
+void reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int pad16,
+                  cudaStream_t st) {
+    const int G = nparts >= 256 ? 32 : 8;
+    k_reduce_parts<<<(n + 31) / 32, dim3(32, G), 0, st>>>(part, nparts, stride, n, out, scale, pad16);
 }
 
 dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
@@ -720,39 +901,38 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     e.colsum = t->colsum; e.loss = t->losspart;
     if ((s = gemm(t, t->H2, h2, Bm * h2, t->w3, h2, (size_t)kSymbols * h2, B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
         return s;
-    k_sum_parts<<<1, 32, 0, st>>>(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B);
+    reduce_parts(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B, 0, st);
     if (!backward) {
         cudaError_t ce = cudaGetLastError();
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
     }
-    k_sum_parts<<<(kSymbols + 127) / 128, 128, 0, st>>>(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f);
+    reduce_parts(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f, 0, st);
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
     if ((s = gemm(t, t->DZ, kSymbols, Bm * kSymbols, t->w3t, kSymbols, (size_t)h2 * kSymbols, B, h2, kSymbols,
                   EPI_RELU_GRAD, e, 1, st)))
         return s;
-    k_sum_parts<<<(h2 + 127) / 128, 128, 0, st>>>(t->colsum, mt, h2, h2, g.b2, 1.0f);
+    reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, st);
     // dh1 = da2 W2, da1 = dh1 * [h1 > 0]; db1
     e = EpiArgs{}; e.act = t->H1; e.out = nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
     e.outT_plane = (size_t)h1 * Bm;
     if ((s = gemm(t, t->DA2, h2, Bm * h2, t->w2t, h2, (size_t)h1 * h2, B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
-    k_sum_parts<<<(h1 + 127) / 128, 128, 0, st>>>(t->colsum, mt, h1, h1, g.b1, 1.0f);
+    reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, st);
     // weight gradients: K = batch, split-K partials summed in a fixed order
     const int splits = max(1, min(64, (B + 1023) / 1024));
     e = EpiArgs{}; e.c = t->part; e.ldc = h2;
     if ((s = gemm(t, t->DZT, P, (size_t)kSymbols * Bm, t->H2T, P, (size_t)h2 * Bm, kSymbols, h2, B, EPI_F32, e, splits,
                   st)))
         return s;
-    k_sum_parts<<<(kSymbols * h2 + 255) / 256, 256, 0, st>>>(t->part, splits, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f);
+    reduce_parts(t->part, splits, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, st);
     e = EpiArgs{}; e.c = t->part; e.ldc = h1;
     if ((s = gemm(t, t->DA2T, P, (size_t)h2 * Bm, t->H1T, P, (size_t)h1 * Bm, h2, h1, B, EPI_F32, e, splits, st)))
         return s;
-    k_sum_parts<<<(h2 * h1 + 255) / 256, 256, 0, st>>>(t->part, splits, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f);
+    reduce_parts(t->part, splits, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, st);
     e = EpiArgs{}; e.c = t->part; e.ldc = 16;
     if ((s = gemm(t, t->DA1T, P, (size_t)h1 * Bm, t->XT, P, 16 * Bm, h1, 16, B, EPI_F32, e, splits, st))) return s;
-    k_sum_parts<<<(h1 * 16 + 255) / 256, 256, 0, st>>>(t->part, splits, (size_t)h1 * 16, h1 * 16, t->g16, 1.0f);
-    k_compact_w1<<<(h1 * kPriors + 255) / 256, 256, 0, st>>>(t->g16, h1, g.W1);
+    reduce_parts(t->part, splits, (size_t)h1 * 16, h1 * 16, g.W1, 1.0f, 1, st);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "backward launch");
 }
@@ -817,7 +997,6 @@ extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_bat
     t->part = (float *)A(4 * 64 * (size_t)kSymbols * hmax);
     t->colsum = (float *)A(4 * (Bm / 128) * kSymbols);
     t->losspart = (float *)A(4 * (Bm / 128));
-    t->g16 = (float *)A(4 * (size_t)h1 * 16);
     t->err = (int *)A(4);
     if (!ok) {
         dlic_trainer_destroy(t);
@@ -884,9 +1063,11 @@ extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, co
     if (s) return s;
     t->step += 1;
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
+    const ShadowArgs sa{t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
     k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, t->grads, t->mom, t->vel, (int)t->nparams, t->lr,
-                                                             t->beta1, t->beta2, t->eps, c1, c2);
-    return refresh_shadows(t, st);
+                                                             t->beta1, t->beta2, t->eps, c1, c2, sa);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "adam launch");
 }
 
 extern "C" dlic_status dlic_trainer_params(dlic_trainer *t, float *d_params, int write, void *stream) {
