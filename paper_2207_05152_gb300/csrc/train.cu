@@ -30,6 +30,7 @@
 namespace dlic {
 
 constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kLog2e = 1.44269504088896340736f;
 constexpr long long kGemmWaitLimit = 4000000000LL;
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_RELU = 1, EPI_SOFTMAX = 2, EPI_RELU_GRAD = 3 };
@@ -220,23 +221,51 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
 
 // ---------------------------------------------------------------------------
 // tcgen05 GEMM: C[M x N] = A[M x K] * B[N x K]^T, bf16 operands fed by TMA
-// (128-byte swizzle, 64-element K blocks), FP32 accumulators in tensor
-// memory, a fused epilogue.  One 128 x N tile per CTA (N <= 256); split-K
-// over gridDim.z for EPI_F32.  Warp 0 loads, warp 1 issues MMAs, warps 2..9
-// run the epilogue: two warps per tensor-memory lane quarter, each on half of
-// the columns of its 32 rows.  Row-major outputs leave as 16-byte vectors;
-// transposed outputs are staged in shared memory (the drained pipeline
-// stages) and written as coalesced 16-byte rows.  Two stages keep a CTA at
-// 96 KB so that two CTAs share an SM (BF16 mode).
+// with 128-byte swizzling, FP32 accumulators in tensor memory, a fused
+// epilogue.  One 128 x N tile per CTA (N <= 256); split-K over gridDim.z for
+// EPI_F32.
+//
+// Each operand is read either K-major (a row of 64 K values per M or N
+// index, 128 bytes) or MN-major (a row of 64 M or N values per K index):
+// the weight gradients dW = dY^T X take both factors straight from the
+// row-major activations [batch][features], so no transposed copy of any
+// activation is ever written.  An MN-major tile is a column of 64-wide
+// boxes, 8 KB apart; columns past the operand's extent are zero-filled (or,
+// for whole boxes, skipped: they only feed outputs that are discarded).
+//
+// Warp 0 loads, warp 1 issues MMAs, warps 2..9 run the epilogue: two warps
+// per tensor-memory lane quarter, each on half of the columns of its 32
+// rows, with row-major outputs leaving as 16-byte vectors.
 // ---------------------------------------------------------------------------
 constexpr int kGemmThreads = 320;
 constexpr int kEpiThreads = 256;
-constexpr int kGemmStages = 2;
+constexpr int kGemmMaxStages = 4;
 
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+struct GemmCfg {
+    int stages;      // pipeline depth (<= kGemmMaxStages)
+    int a_mn, b_mn;  // operand major-ness (1 = MN-major)
+    int n_mma;       // MMA N: N rounded up to 16 (K-major B) or 64 (MN-major B)
+    int b_boxes;     // MN-major B: 64-wide boxes inside the operand
+};
+
+// K-major, 128-byte swizzle: 8-row groups 1024 bytes apart; a K step of 16
+// advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t desc_k128(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// MN-major, 128-byte swizzle: 64-wide MN blocks 8192 bytes apart (leading
+// byte offset), 8-row K groups 1024 bytes apart (stride byte offset); a K
+// step of 16 advances the start address by 2048 bytes.
+__device__ __forceinline__ uint64_t desc_mn128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(8192 >> 4) << 16;
     d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
@@ -252,33 +281,60 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
 }
+// 2^x with the MUFU approximation (relative error about 2^-22; flushes
+// results below 2^-126 to zero).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 2, %0;" ::"r"(kEpiThreads) : "memory"); }
 
-// 16 values as bf16 (and their low parts) in the two layouts: row-major
-// vectors to global memory, transposed 2-byte entries to the staging tile.
-__device__ __forceinline__ void emit16(const EpiArgs &e, const float (&v)[16], int m, int row, int n0, bool valid,
-                                       uint16_t *Thi, uint16_t *Tlo, bool rowmajor) {
-    uint32_t hi[8], lo[8];
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// 16 consecutive values of row m as bf16 (and, in split mode, the low plane
+// bf16(v - hi)) with two 16-byte stores per plane.
+__device__ __forceinline__ void store_row16(const EpiArgs &e, const float (&v)[16], int m, int n0) {
+    uint32_t hi[8];
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const uint16_t a = f2bf(v[2 * j]), b = f2bf(v[2 * j + 1]);
-        hi[j] = a | ((uint32_t)b << 16);
-        lo[j] = f2bf(v[2 * j] - bf2f(a)) | ((uint32_t)f2bf(v[2 * j + 1] - bf2f(b)) << 16);
-        Thi[(n0 + 2 * j) * 128 + row] = a;
-        Thi[(n0 + 2 * j + 1) * 128 + row] = b;
-        if (e.split) {
-            Tlo[(n0 + 2 * j) * 128 + row] = (uint16_t)lo[j];
-            Tlo[(n0 + 2 * j + 1) * 128 + row] = (uint16_t)(lo[j] >> 16);
-        }
+    for (int j = 0; j < 8; j++) hi[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+    uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + (size_t)m * e.N + n0);
+    o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    o[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    if (e.split) {
+        uint32_t lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            lo[j] = pack_bf16x2(v[2 * j] - __uint_as_float(hi[j] << 16), v[2 * j + 1] - __uint_as_float(hi[j] & 0xFFFF0000u));
+        uint4 *ol = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + e.out_plane + (size_t)m * e.N + n0);
+        ol[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        ol[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
     }
-    if (rowmajor && valid) {
-        uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + (size_t)m * e.N + n0);
-        o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        o[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-        if (e.split) {
-            uint4 *ol = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + e.out_plane + (size_t)m * e.N + n0);
-            ol[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-            ol[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+}
+
+// Walks this thread's 16-column chunks [n_lo, n_hi) of its tensor-memory row,
+// loading the next chunk while the current one is processed.
+template <class F>
+__device__ __forceinline__ void for_chunks(uint32_t taddr, int n_lo, int n_hi, F &&f) {
+    if (n_lo >= n_hi) return;
+    uint32_t cur[16], nxt[16];
+    tc::tmem_ld16(taddr + (uint32_t)n_lo, cur);
+    tc::tmem_wait_ld();
+    for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
+        const bool more = n0 + 16 < n_hi;
+        if (more) tc::tmem_ld16(taddr + (uint32_t)(n0 + 16), nxt);
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = __uint_as_float(cur[j]);
+        f(n0, v);
+        if (more) {
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; j++) cur[j] = nxt[j];
         }
     }
 }
@@ -290,32 +346,37 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapAl, const __grid_constant__ CUtensorMap mapBl, int K,
-              int kb_per_split, int epi, EpiArgs e, int *err) {
+              int kb_per_split, int epi, GemmCfg g, EpiArgs e, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[kGemmStages], empty[kGemmStages], accum;
+    __shared__ uint64_t full[kGemmMaxStages], empty[kGemmMaxStages], accum;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float cs[256];
+    __shared__ __align__(16) float s_bias[256];
     __shared__ float red[2][2][128];
     __shared__ float s_loss[kGemmThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int N = e.N;
-    const uint32_t a_bytes = 128 * 128, b_bytes = (uint32_t)N * 128;
+    const int N = e.N, NS = g.stages;
+    const uint32_t a_bytes = 128 * 128, b_bytes = (uint32_t)g.n_mma * 128;
     const uint32_t b_al = (b_bytes + 1023) & ~1023u;
     const uint32_t stage_bytes = SPLIT ? 2 * (a_bytes + b_al) : a_bytes + b_al;
+    const int m0 = blockIdx.x * 128;
+    // bytes a stage's loads deliver (whole boxes past the extent are skipped)
+    const int a_boxes = m0 + 64 < e.M ? 2 : 1;
+    const uint32_t a_load = g.a_mn ? 8192u * a_boxes : a_bytes;
+    const uint32_t b_load = g.b_mn ? 8192u * g.b_boxes : b_bytes;
     const int nkb_total = (K + 63) / 64;
     const int kb0 = blockIdx.z * kb_per_split;
     const int kb1 = min(nkb_total, kb0 + kb_per_split);
     const int nkb = max(0, kb1 - kb0);
-    const int m0 = blockIdx.x * 128;
 
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, 256);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < kGemmStages; s++) {
+        for (int s = 0; s < NS; s++) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
@@ -323,7 +384,12 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         tc::fence_mbar_init();
         s_fail = 0;
     }
-    for (int n = tid; n < 256; n += kGemmThreads) cs[n] = 0.0f;
+    for (int n = tid; n < 256; n += kGemmThreads) {
+        cs[n] = 0.0f;
+        // the softmax works in base 2: its bias is stored pre-scaled by log2(e)
+        const float bv = e.bias && n < N ? e.bias[n] : 0.0f;
+        s_bias[n] = epi == EPI_SOFTMAX ? bv * kLog2e : bv;
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -332,35 +398,47 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     if (warp == 0 && lane == 0) {
         // producer
         for (int i = 0; i < nkb; i++) {
-            const int s = i % kGemmStages;
-            if (!tc::mbar_wait(&empty[s], ((i / kGemmStages) & 1) ^ 1, kGemmWaitLimit)) { s_fail = 1; break; }
+            const int s = i % NS;
+            if (!tc::mbar_wait(&empty[s], ((i / NS) & 1) ^ 1, kGemmWaitLimit)) { s_fail = 1; break; }
             uint8_t *st = smem + s * stage_bytes;
-            mbar_expect_tx(&full[s], SPLIT ? 2 * (a_bytes + b_bytes) : a_bytes + b_bytes);
-            tma_load_2d(tc::smem_addr(st), &mapA, (kb0 + i) * 64, m0, tc::smem_addr(&full[s]));
-            tma_load_2d(tc::smem_addr(st + a_bytes), &mapB, (kb0 + i) * 64, 0, tc::smem_addr(&full[s]));
-            if (SPLIT) {
-                tma_load_2d(tc::smem_addr(st + a_bytes + b_al), &mapAl, (kb0 + i) * 64, m0, tc::smem_addr(&full[s]));
-                tma_load_2d(tc::smem_addr(st + 2 * a_bytes + b_al), &mapBl, (kb0 + i) * 64, 0, tc::smem_addr(&full[s]));
+            const int k = (kb0 + i) * 64;
+            const uint32_t bar = tc::smem_addr(&full[s]);
+            mbar_expect_tx(&full[s], SPLIT ? 2 * (a_load + b_load) : a_load + b_load);
+#pragma unroll 1
+            for (int pl = 0; pl < (SPLIT ? 2 : 1); pl++) {
+                const CUtensorMap *ma = pl ? &mapAl : &mapA, *mb = pl ? &mapBl : &mapB;
+                uint8_t *sa = st + pl * (a_bytes + b_al), *sb = sa + a_bytes;
+                if (g.a_mn)
+                    for (int h = 0; h < a_boxes; h++) tma_load_2d(tc::smem_addr(sa + 8192 * h), ma, m0 + 64 * h, k, bar);
+                else
+                    tma_load_2d(tc::smem_addr(sa), ma, k, m0, bar);
+                if (g.b_mn)
+                    for (int h = 0; h < g.b_boxes; h++) tma_load_2d(tc::smem_addr(sb + 8192 * h), mb, 64 * h, k, bar);
+                else
+                    tma_load_2d(tc::smem_addr(sb), mb, k, 0, bar);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, g.n_mma) | ((uint32_t)g.a_mn << 15) | ((uint32_t)g.b_mn << 16);
+        // start-address step per K = 16 (descriptor units of 16 bytes)
+        const uint32_t astep = g.a_mn ? 128u : 2u, bstep = g.b_mn ? 128u : 2u;
         for (int i = 0; i < nkb; i++) {
-            const int s = i % kGemmStages;
-            if (!tc::mbar_wait(&full[s], (i / kGemmStages) & 1, kGemmWaitLimit)) { s_fail = 1; break; }
+            const int s = i % NS;
+            if (!tc::mbar_wait(&full[s], (i / NS) & 1, kGemmWaitLimit)) { s_fail = 1; break; }
             tc::fence_after_sync();
             uint8_t *st = smem + s * stage_bytes;
-            const uint64_t da = desc_sw128(tc::smem_addr(st)), db = desc_sw128(tc::smem_addr(st + a_bytes));
+            auto dA = [&](uint8_t *p) { return g.a_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
+            auto dB = [&](uint8_t *p) { return g.b_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
+            const uint64_t da = dA(st), db = dB(st + a_bytes);
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++) tc::mma_bf16(tm, da + 2u * ks, db + 2u * ks, idesc, (i | ks) != 0);
+            for (int ks = 0; ks < 4; ks++) tc::mma_bf16(tm, da + astep * ks, db + bstep * ks, idesc, (i | ks) != 0);
             if (SPLIT) {
-                const uint64_t dal = desc_sw128(tc::smem_addr(st + a_bytes + b_al));
-                const uint64_t dbl = desc_sw128(tc::smem_addr(st + 2 * a_bytes + b_al));
+                const uint64_t dal = dA(st + a_bytes + b_al), dbl = dB(st + 2 * a_bytes + b_al);
 #pragma unroll
                 for (int ks = 0; ks < 4; ks++) {
-                    tc::mma_bf16(tm, dal + 2u * ks, db + 2u * ks, idesc, 1u);
-                    tc::mma_bf16(tm, da + 2u * ks, dbl + 2u * ks, idesc, 1u);
+                    tc::mma_bf16(tm, dal + astep * ks, db + bstep * ks, idesc, 1u);
+                    tc::mma_bf16(tm, da + astep * ks, dbl + bstep * ks, idesc, 1u);
                 }
             }
             tc::mma_commit(&empty[s]);
@@ -372,130 +450,105 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         tc::mbar_wait(&accum, 0, 1000);   // every lane observes the completed phase
         tc::fence_after_sync();
     }
-    // all loads and MMAs are done: the pipeline stages become the staging tiles
     __syncwarp();
     asm volatile("bar.sync 1, %0;" ::"r"(kGemmThreads) : "memory");
-    uint16_t *Thi = reinterpret_cast<uint16_t *>(smem);
-    uint16_t *Tlo = Thi + (size_t)N * 128;
     float loss_acc = 0.0f;
-    const bool staged = epi != EPI_F32;
     if (warp >= 2) {
         const int q = warp & 3, hf = (warp - 2) >> 2;
         const int row = 32 * q + lane, m = m0 + row;
         const bool valid = m < e.M;
         // the two halves split the 16-column chunks (the first takes the odd one)
         const int nch = N / 16, first = (nch + 1) / 2;
-        const int n_lo = hf ? 16 * first : 0, n_hi = hf ? N : 16 * first;
-        const bool active = !s_fail && n_lo < n_hi;
-        TmemRow src{tm + ((uint32_t)(32 * q) << 16)};
+        int n_lo = hf ? 16 * first : 0, n_hi = hf ? N : 16 * first;
+        if (s_fail) n_hi = n_lo;
+        const uint32_t taddr = tm + ((uint32_t)(32 * q) << 16);
         if (epi == EPI_F32) {
-            if (active && valid) {
-                float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    if (nkb > 0) {
-                        src.load16(n0, v);
-                    } else {
+            float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
+            if (nkb == 0) {
+                if (valid)
+                    for (int n0 = n_lo; n0 < n_hi; n0 += 4) *reinterpret_cast<float4 *>(c + n0) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
+                    if (valid)
 #pragma unroll
-                        for (int j = 0; j < 16; j++) v[j] = 0.0f;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(c + n0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                }
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4 *>(c + n0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                });
             }
         } else if (epi == EPI_BIAS_RELU) {
-            if (active)
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    src.load16(n0, v);
+            for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
 #pragma unroll
-                    for (int j = 0; j < 16; j++) v[j] = fmaxf(v[j] + e.bias[n0 + j], 0.0f);
-                    emit16(e, v, m, row, n0, valid, Thi, Tlo, true);
-                }
+                for (int j = 0; j < 16; j++) v[j] = fmaxf(v[j] + s_bias[n0 + j], 0.0f);
+                if (valid) store_row16(e, v, m, n0);
+            });
         } else if (epi == EPI_RELU_GRAD) {
-            if (active)
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    src.load16(n0, v);
-                    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
-                    if (valid) {
-                        const uint4 *ap = reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(e.act) + (size_t)m * N + n0);
-                        a0 = ap[0];
-                        a1 = ap[1];
-                    }
-                    const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const uint32_t bits = (aw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                        const bool pos = valid && bits != 0 && (bits & 0x8000u) == 0;   // bf16 > 0
-                        v[j] = pos ? v[j] : 0.0f;
-                    }
-                    emit16(e, v, m, row, n0, valid, Thi, Tlo, e.out != nullptr);
-                    if (e.colsum) colsum_add(cs + n0, v);
-                }
-        } else {
-            // EPI_SOFTMAX over the full row: halves combine through shared memory
-            float mx = -INFINITY;
-            if (active)
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    src.load16(n0, v);
-#pragma unroll
-                    for (int j = 0; j < 16; j++) mx = fmaxf(mx, v[j] + e.bias[n0 + j]);
-                }
-            red[0][hf][row] = mx;
-            epi_sync();
-            mx = fmaxf(red[0][0][row], red[0][1][row]);
-            float se = 0.0f;
-            if (active)
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    src.load16(n0, v);
-#pragma unroll
-                    for (int j = 0; j < 16; j++) se += expf(v[j] + e.bias[n0 + j] - mx);
-                }
-            red[1][hf][row] = se;
-            epi_sync();
-            se = red[1][0][row] + red[1][1][row];
-            const float lse = mx + logf(se), inv = 1.0f / se;
-            const int y = valid ? e.tgt[m] : -1;
-            if (active)
-                for (int n0 = n_lo; n0 < n_hi; n0 += 16) {
-                    float v[16];
-                    src.load16(n0, v);
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const float zz = v[j] + e.bias[n0 + j];
-                        float g = expf(zz - mx) * inv;
-                        if (n0 + j == y) {
-                            g -= 1.0f;
-                            loss_acc += (lse - zz) / kLn2;
-                        }
-                        v[j] = valid ? g * e.inv_batch_ln2 : 0.0f;
-                    }
-                    emit16(e, v, m, row, n0, valid, Thi, Tlo, true);
-                    if (e.colsum) colsum_add(cs + n0, v);
-                }
-        }
-        if (staged && !s_fail) {
-            // transposed tile -> outT[n][m0 ..] as 16-byte rows
-            epi_sync();
-            const int et = tid - 64;
-            for (int idx = et; idx < N * 16; idx += kEpiThreads) {
-                const int n = idx >> 4, ml = (idx & 15) * 8, gm = m0 + ml;
-                uint16_t *dst = static_cast<uint16_t *>(e.outT) + (size_t)n * e.ldT + gm;
-                const uint4 vh = *reinterpret_cast<const uint4 *>(Thi + n * 128 + ml);
-                if (gm + 8 <= e.M) {
-                    *reinterpret_cast<uint4 *>(dst) = vh;
-                    if (e.split) *reinterpret_cast<uint4 *>(dst + e.outT_plane) = *reinterpret_cast<const uint4 *>(Tlo + n * 128 + ml);
-                } else {
-                    for (int j = 0; j < 8 && gm + j < e.M; j++) {
-                        dst[j] = Thi[n * 128 + ml + j];
-                        if (e.split) dst[j + e.outT_plane] = Tlo[n * 128 + ml + j];
-                    }
-                }
+            // the activation that masks the gradient, one chunk ahead
+            const uint4 *ap = reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(e.act) + (size_t)m * N);
+            uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
+            if (valid && n_lo < n_hi) {
+                a0 = ap[n_lo / 8];
+                a1 = ap[n_lo / 8 + 1];
             }
+            for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
+                const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                if (valid && n0 + 16 < n_hi) {
+                    a0 = ap[n0 / 8 + 2];
+                    a1 = ap[n0 / 8 + 3];
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const uint32_t bits = (aw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                    const bool pos = bits != 0 && (bits & 0x8000u) == 0;   // bf16 > 0
+                    v[j] = pos ? v[j] : 0.0f;
+                }
+                if (valid) store_row16(e, v, m, n0);
+                if (e.colsum) colsum_add(cs + n0, v);
+            });
+        } else {
+            // EPI_SOFTMAX: running maximum and rescaled sum over this half's
+            // columns in base 2 (z2 = z log2 e), then the halves combine
+            // through shared memory
+            float m2 = -INFINITY, s2 = 0.0f;
+            for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
+                float z[16], cm = m2;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    z[j] = fmaf(v[j], kLog2e, s_bias[n0 + j]);
+                    cm = fmaxf(cm, z[j]);
+                }
+                float add = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 16; j++) add += fast_exp2(z[j] - cm);
+                s2 = s2 * fast_exp2(m2 - cm) + add;
+                m2 = cm;
+            });
+            red[0][hf][row] = m2;
+            red[1][hf][row] = s2;
+            epi_sync();
+            const float ma = red[0][0][row], mb = red[0][1][row];
+            const float mx = fmaxf(ma, mb);
+            const float se = red[1][0][row] * fast_exp2(ma - mx) + red[1][1][row] * fast_exp2(mb - mx);
+            const float lse2 = mx + log2f(se);
+            const float scale = valid ? e.inv_batch_ln2 / se : 0.0f;
+            const int y = valid ? e.tgt[m] : -1;
+            for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
+                const bool has_y = (y & ~15) == n0;
+                if (has_y) {
+                    // -log2 p_y = lse2 - z2_y
+#pragma unroll
+                    for (int j = 0; j < 16; j++)
+                        if (n0 + j == y) loss_acc += lse2 - fmaf(v[j], kLog2e, s_bias[n0 + j]);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j++) v[j] = fast_exp2(fmaf(v[j], kLog2e, s_bias[n0 + j]) - mx) * scale;
+                if (has_y) {
+#pragma unroll
+                    for (int j = 0; j < 16; j++)
+                        if (n0 + j == y) v[j] -= e.inv_batch_ln2;
+                }
+                if (valid) store_row16(e, v, m, n0);
+                if (e.colsum) colsum_add(cs + n0, v);
+            });
         }
     }
     for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
@@ -588,34 +641,47 @@ __global__ void __launch_bounds__(128) k_row_epilogue(const float *C, int epi, E
 // Small kernels: features, reductions, Adam, weight shadows.
 // ---------------------------------------------------------------------------
 // v / 128 - 1 has at most 8 significant bits: exact in bf16, low plane 0.
-__global__ void k_features(const uint8_t *ctx, int B, int ldT, void *X, void *XT, int bf16, size_t xplane,
-                           size_t xtplane) {
+// Network inputs x/128 - 1 (exact in bf16 and FP32), K padded to 16; the
+// transposed copy XT [16][ldT] only for the FP32 path (XT non-null).  BF16:
+// one context per thread, 12 bytes in, two 16-byte rows out (plus a zero
+// low plane in split mode).
+__global__ void k_features(const uint8_t *ctx, int B, int ldT, void *X, void *XT, int bf16, size_t xplane) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (bf16) {
+        const uint8_t *c = ctx + (size_t)b * kPriors;
+        const bool al4 = (reinterpret_cast<uintptr_t>(c) & 3u) == 0;
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const uint32_t v = al4 ? reinterpret_cast<const uint32_t *>(c)[q]
+                                   : c[4 * q] | (c[4 * q + 1] << 8) | (c[4 * q + 2] << 16) | ((uint32_t)c[4 * q + 3] << 24);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const float x0 = (float)((v >> (16 * h)) & 0xFFu) * 0.0078125f - 1.0f;
+                const float x1 = (float)((v >> (16 * h + 8)) & 0xFFu) * 0.0078125f - 1.0f;
+                w[2 * q + h] = pack_bf16x2(x0, x1);
+            }
+        }
+        w[6] = w[7] = 0u;
+        uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(X) + (size_t)b * 16);
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        if (xplane) {
+            uint4 *ol = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(X) + xplane + (size_t)b * 16);
+            ol[0] = ol[1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        return;
+    }
     for (int k = 0; k < 16; k++) {
         const float x = k < kPriors ? (float)ctx[(size_t)b * kPriors + k] * 0.0078125f - 1.0f : 0.0f;
-        if (bf16) {
-            reinterpret_cast<uint16_t *>(X)[(size_t)b * 16 + k] = f2bf(x);
-            reinterpret_cast<uint16_t *>(XT)[(size_t)k * ldT + b] = f2bf(x);
-            if (xplane) {
-                reinterpret_cast<uint16_t *>(X)[(size_t)b * 16 + k + xplane] = 0;
-                reinterpret_cast<uint16_t *>(XT)[(size_t)k * ldT + b + xtplane] = 0;
-            }
-        } else {
-            reinterpret_cast<float *>(X)[(size_t)b * 16 + k] = x;
-            reinterpret_cast<float *>(XT)[(size_t)k * ldT + b] = x;
-        }
+        reinterpret_cast<float *>(X)[(size_t)b * 16 + k] = x;
+        reinterpret_cast<float *>(XT)[(size_t)k * ldT + b] = x;
     }
 }
 
-// First layer in FP32 on the CUDA cores (K = 12): h1 = relu(W1 x + b1),
-// written as split bf16 (hi and lo planes), row-major and transposed, through
-// a shared-memory tile so both stores are coalesced.  The split mode uses it
-// because a1 sums only 12 products and often sits near the ReLU kink, where
-// 16-bit operand precision would flip masks relative to exact arithmetic.
 __global__ void __launch_bounds__(256) k_layer1_f32(const uint8_t *ctx, int B, const float *W1, const float *b1,
-                                                    int h1, uint16_t *H1, uint16_t *H1T, int ldT, size_t p1,
-                                                    size_t p1T) {
+                                                    int h1, uint16_t *H1, size_t p1) {
     __shared__ float tile[32][257];
     __shared__ float xs[32][kPriors];
     const int tid = threadIdx.x, b0 = blockIdx.x * 32;
@@ -644,14 +710,6 @@ __global__ void __launch_bounds__(256) k_layer1_f32(const uint8_t *ctx, int B, c
         const uint16_t hi = f2bf(v), lo = f2bf(v - bf2f(hi));
         H1[(size_t)(b0 + r) * h1 + j] = hi;
         H1[(size_t)(b0 + r) * h1 + j + p1] = lo;
-    }
-    for (int i = tid; i < 32 * h1; i += 256) {
-        const int j = i / 32, r = i % 32;
-        if (b0 + r >= B) continue;
-        const float v = tile[r][j];
-        const uint16_t hi = f2bf(v), lo = f2bf(v - bf2f(hi));
-        H1T[(size_t)j * ldT + b0 + r] = hi;
-        H1T[(size_t)j * ldT + b0 + r + p1T] = lo;
     }
 }
 
@@ -757,7 +815,8 @@ struct dlic_trainer {
     float lr, beta1, beta2, eps;
     float *params, *grads, *mom, *vel;           // FP32 master state
     void *w1, *w2, *w3, *w2t, *w3t;              // operand copies (bf16 or fp32)
-    void *X, *XT, *H1, *H1T, *H2, *H2T, *DZ, *DZT, *DA2, *DA2T, *DA1T;
+    void *X, *H1, *H2, *DZ, *DA2, *DA1;          // row-major [batch][features]
+    void *XT, *H1T, *H2T, *DZT, *DA2T, *DA1T;    // FP32 path: transposed [features][batch]
     float *C, *part, *colsum, *losspart;
     int *err;
     std::vector<void *> allocs;
@@ -810,10 +869,20 @@ CUresult encode_map(CUtensorMap *map, const void *g, int rows, int cols, int pit
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-// C = A[M x K] B[N x K]^T with the given epilogue; A and B K-major with row
-// pitches lda and ldb (elements).
-dlic_status gemm(dlic_trainer *t, const void *A, int lda, size_t aplane, const void *Bm, int ldb, size_t bplane, int M,
-                 int N, int K, int epi, EpiArgs e, int splits, cudaStream_t st) {
+// A GEMM operand in global memory.  K-major: `rows` M (or N) entries of
+// `cols` = K values; MN-major: `rows` = K entries of `cols` M (or N) values.
+// `pitch` is the row stride and `plane` the element offset of the low plane
+// (split mode).
+struct Operand {
+    const void *p;
+    int rows, cols, pitch;
+    size_t plane;
+    int mn;
+};
+
+// C = A[M x K] B[N x K]^T with the given epilogue.
+dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int N, int K, int epi, EpiArgs e,
+                 int splits, cudaStream_t st) {
     e.M = M;
     e.N = N;
     e.ldT = t->max_batch;
@@ -821,36 +890,48 @@ dlic_status gemm(dlic_trainer *t, const void *A, int lda, size_t aplane, const v
     e.split = t->split;
     const int mt = (M + 127) / 128;
     if (t->bf) {
+        GemmCfg g;
+        g.a_mn = a.mn;
+        g.b_mn = b.mn;
+        g.n_mma = b.mn ? (N + 63) / 64 * 64 : (N + 15) / 16 * 16;
+        g.b_boxes = (N + 63) / 64;
+        // K blocks of 64: a deeper pipeline for the long-K weight gradients
+        // (one CTA per SM); two stages elsewhere (two CTAs per SM in BF16)
+        g.stages = epi == EPI_F32 && !t->split ? 4 : 2;
         CUtensorMap ma, mb, mal, mbl;
-        const uint16_t *A16 = static_cast<const uint16_t *>(A), *B16 = static_cast<const uint16_t *>(Bm);
-        if (encode_map(&ma, A16, M, K, lda, 128) != CUDA_SUCCESS || encode_map(&mb, B16, N, K, ldb, N) != CUDA_SUCCESS)
+        const uint16_t *A16 = static_cast<const uint16_t *>(a.p), *B16 = static_cast<const uint16_t *>(b.p);
+        const int abox = a.mn ? 64 : 128, bbox = b.mn ? 64 : N;
+        if (encode_map(&ma, A16, a.rows, a.cols, a.pitch, abox) != CUDA_SUCCESS ||
+            encode_map(&mb, B16, b.rows, b.cols, b.pitch, bbox) != CUDA_SUCCESS)
             return fail(DLIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (M %d N %d K %d)", M, N, K);
         mal = ma;
         mbl = mb;
-        if (t->split && (encode_map(&mal, A16 + aplane, M, K, lda, 128) != CUDA_SUCCESS ||
-                         encode_map(&mbl, B16 + bplane, N, K, ldb, N) != CUDA_SUCCESS))
+        if (t->split && (encode_map(&mal, A16 + a.plane, a.rows, a.cols, a.pitch, abox) != CUDA_SUCCESS ||
+                         encode_map(&mbl, B16 + b.plane, b.rows, b.cols, b.pitch, bbox) != CUDA_SUCCESS))
             return fail(DLIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (low planes)");
         const int nkb = (K + 63) / 64;
         const int per = (nkb + splits - 1) / splits;
-        const uint32_t stage = 128 * 128 + ((uint32_t)N * 128 + 1023) / 1024 * 1024;
-        const size_t smem = (size_t)kGemmStages * (t->split ? 2 : 1) * stage + 1024;
+        const uint32_t stage = 128 * 128 + ((uint32_t)g.n_mma * 128 + 1023) / 1024 * 1024;
+        const size_t smem = (size_t)g.stages * (t->split ? 2 : 1) * stage + 1024;
         if (t->split) {
             cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gemm_tc<true><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, e, t->err);
+            k_gemm_tc<true><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
         } else {
             cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gemm_tc<false><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, e, t->err);
+            k_gemm_tc<false><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
         }
         cudaError_t ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "k_gemm_tc launch");
         return DLIC_OK;
     }
-    // FP32 path: raw GEMM into C (or the split-K partials), then the row epilogue
+    // FP32 path: raw GEMM into C (or the split-K partials), then the row
+    // epilogue; operands K-major (the transposed activations)
     const int per = ((K + splits - 1) / splits + 7) / 8 * 8;
     float *dst = epi == EPI_F32 ? e.c : t->C;
     const int ldc = epi == EPI_F32 ? e.ldc : N;
-    k_gemm_f32<<<dim3(mt, (N + 127) / 128, splits), 256, 0, st>>>(static_cast<const float *>(A), lda,
-                                                                   static_cast<const float *>(Bm), ldb, dst, M, N, K, per, ldc);
+    k_gemm_f32<<<dim3(mt, (N + 127) / 128, splits), 256, 0, st>>>(static_cast<const float *>(a.p), a.pitch,
+                                                                   static_cast<const float *>(b.p), b.pitch, dst, M, N, K,
+                                                                   per, ldc);
     if (epi != EPI_F32) k_row_epilogue<<<mt, 128, N * sizeof(float), st>>>(t->C, epi, e);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "fp32 gemm launch");
@@ -872,34 +953,45 @@ dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "shadow launch");
 }
 
-// Forward (and, if `grads`, backward) over one batch.
+// Forward (and, if `backward`, backward) over one batch.  BF16 modes keep
+// every activation row-major [batch][features] and read the weight-gradient
+// factors MN-major; the FP32 path also keeps transposed copies [features]
+// [batch] for its K-major CUDA-core GEMM.
 dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss, bool backward,
                 cudaStream_t st) {
     const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128;
     const int bf = t->bf;
     ParamView p = view(t->params, h1, h2);
     ParamView g = view(t->grads, h1, h2);
-    const int P = t->max_batch;   // pitch of every transposed [N][batch] array
-    const size_t Bm = (size_t)P;  // low planes follow each buffer at its full capacity
+    const int P = t->max_batch;   // capacity: pitch of the transposed arrays, offset of the low planes
+    const size_t Bm = (size_t)P;
     const size_t sp = t->split ? 1 : 0;
-    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, B, P, t->X, t->XT, bf, sp * Bm * 16, sp * 16 * Bm);
+    // row-major [B][n] activation (K-major as the A factor of the next layer)
+    auto rowmaj = [&](const void *q, int n) { return Operand{q, B, n, n, Bm * n, 0}; };
+    // weights [out][in] (K-major B factor of a forward or backward GEMM)
+    auto wmat = [&](const void *q, int out, int in) { return Operand{q, out, in, in, (size_t)out * in, 0}; };
+    // weight-gradient factors: MN-major row-major activations (BF16) or
+    // K-major transposed copies (FP32)
+    auto wgrad = [&](const void *rm, const void *tr, int n) {
+        return bf ? Operand{rm, B, n, n, Bm * n, 1} : Operand{tr, n, B, P, (size_t)n * Bm, 0};
+    };
+    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, B, P, t->X, bf ? nullptr : t->XT, bf, sp * Bm * 16);
     EpiArgs e{};
-    // layer 1, 2: bias + ReLU, row-major and transposed activations
+    // layer 1, 2: bias + ReLU
     e.bias = p.b1; e.out = t->H1; e.outT = t->H1T; e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     dlic_status s = DLIC_OK;
     if (t->split)
-        k_layer1_f32<<<(B + 31) / 32, 256, 0, st>>>(ctx, B, p.W1, p.b1, h1, static_cast<uint16_t *>(t->H1),
-                                                     static_cast<uint16_t *>(t->H1T), P, Bm * h1, (size_t)h1 * Bm);
-    else if ((s = gemm(t, t->X, 16, Bm * 16, t->w1, 16, (size_t)h1 * 16, B, h1, 16, EPI_BIAS_RELU, e, 1, st)))
+        k_layer1_f32<<<(B + 31) / 32, 256, 0, st>>>(ctx, B, p.W1, p.b1, h1, static_cast<uint16_t *>(t->H1), Bm * h1);
+    else if ((s = gemm(t, rowmaj(t->X, 16), wmat(t->w1, h1, 16), B, h1, 16, EPI_BIAS_RELU, e, 1, st)))
         return s;
     e = EpiArgs{}; e.bias = p.b2; e.out = t->H2; e.outT = t->H2T; e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
-    if ((s = gemm(t, t->H1, h1, Bm * h1, t->w2, h1, (size_t)h2 * h1, B, h2, h1, EPI_BIAS_RELU, e, 1, st))) return s;
+    if ((s = gemm(t, rowmaj(t->H1, h1), wmat(t->w2, h2, h1), B, h2, h1, EPI_BIAS_RELU, e, 1, st))) return s;
     // layer 3 + softmax cross-entropy: loss partials, dz, db3 partials
     e = EpiArgs{}; e.bias = p.b3; e.out = t->DZ; e.outT = t->DZT; e.tgt = tgt;
     e.out_plane = Bm * kSymbols; e.outT_plane = (size_t)kSymbols * Bm;
     e.inv_batch_ln2 = 1.0f / ((float)B * kLn2);
     e.colsum = t->colsum; e.loss = t->losspart;
-    if ((s = gemm(t, t->H2, h2, Bm * h2, t->w3, h2, (size_t)kSymbols * h2, B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
+    if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, kSymbols, h2), B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
         return s;
     reduce_parts(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B, 0, st);
     if (!backward) {
@@ -910,29 +1002,35 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
-    if ((s = gemm(t, t->DZ, kSymbols, Bm * kSymbols, t->w3t, kSymbols, (size_t)h2 * kSymbols, B, h2, kSymbols,
-                  EPI_RELU_GRAD, e, 1, st)))
+    if ((s = gemm(t, rowmaj(t->DZ, kSymbols), wmat(t->w3t, h2, kSymbols), B, h2, kSymbols, EPI_RELU_GRAD, e, 1, st)))
         return s;
     reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, st);
     // dh1 = da2 W2, da1 = dh1 * [h1 > 0]; db1
-    e = EpiArgs{}; e.act = t->H1; e.out = nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
-    e.outT_plane = (size_t)h1 * Bm;
-    if ((s = gemm(t, t->DA2, h2, Bm * h2, t->w2t, h2, (size_t)h1 * h2, B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
+    e = EpiArgs{}; e.act = t->H1; e.out = bf ? t->DA1 : nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
+    e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
+    if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
     reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, st);
-    // weight gradients: K = batch, split-K partials summed in a fixed order
-    const int splits = max(1, min(64, (B + 1023) / 1024));
+    // weight gradients dW = dY^T X: K = batch, split-K partials summed in a
+    // fixed order; enough splits to cover every SM
+    auto splits_for = [&](int M) {
+        const int nkb = (B + 63) / 64;
+        const int want = bf ? max(1, t->num_sms / ((M + 127) / 128)) : max(1, min(64, (B + 1023) / 1024));
+        const int per = (nkb + min(want, nkb) - 1) / min(want, nkb);
+        return (nkb + per - 1) / per;
+    };
+    int sk = splits_for(kSymbols);
     e = EpiArgs{}; e.c = t->part; e.ldc = h2;
-    if ((s = gemm(t, t->DZT, P, (size_t)kSymbols * Bm, t->H2T, P, (size_t)h2 * Bm, kSymbols, h2, B, EPI_F32, e, splits,
-                  st)))
+    if ((s = gemm(t, wgrad(t->DZ, t->DZT, kSymbols), wgrad(t->H2, t->H2T, h2), kSymbols, h2, B, EPI_F32, e, sk, st)))
         return s;
-    reduce_parts(t->part, splits, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, st);
+    reduce_parts(t->part, sk, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, st);
+    sk = splits_for(h2);
     e = EpiArgs{}; e.c = t->part; e.ldc = h1;
-    if ((s = gemm(t, t->DA2T, P, (size_t)h2 * Bm, t->H1T, P, (size_t)h1 * Bm, h2, h1, B, EPI_F32, e, splits, st)))
-        return s;
-    reduce_parts(t->part, splits, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, st);
+    if ((s = gemm(t, wgrad(t->DA2, t->DA2T, h2), wgrad(t->H1, t->H1T, h1), h2, h1, B, EPI_F32, e, sk, st))) return s;
+    reduce_parts(t->part, sk, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, st);
+    sk = splits_for(h1);
     e = EpiArgs{}; e.c = t->part; e.ldc = 16;
-    if ((s = gemm(t, t->DA1T, P, (size_t)h1 * Bm, t->XT, P, 16 * Bm, h1, 16, B, EPI_F32, e, splits, st))) return s;
-    reduce_parts(t->part, splits, (size_t)h1 * 16, h1 * 16, g.W1, 1.0f, 1, st);
+    if ((s = gemm(t, wgrad(t->DA1, t->DA1T, h1), wgrad(t->X, t->XT, 16), h1, 16, B, EPI_F32, e, sk, st))) return s;
+    reduce_parts(t->part, sk, (size_t)h1 * 16, h1 * 16, g.W1, 1.0f, 1, st);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "backward launch");
 }
@@ -983,18 +1081,23 @@ extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_bat
     t->w2t = A(es * h1 * h2);
     t->w3t = A(es * h2 * kSymbols);
     t->X = A(es * Bm * 16);
-    t->XT = A(es * 16 * Bm);
     t->H1 = A(es * Bm * h1);
-    t->H1T = A(es * h1 * Bm);
     t->H2 = A(es * Bm * h2);
-    t->H2T = A(es * h2 * Bm);
     t->DZ = A(es * Bm * kSymbols);
-    t->DZT = A(es * kSymbols * Bm);
     t->DA2 = A(es * Bm * h2);
-    t->DA2T = A(es * h2 * Bm);
-    t->DA1T = A(es * h1 * Bm);
-    t->C = (float *)A(4 * Bm * kSymbols);
-    t->part = (float *)A(4 * 64 * (size_t)kSymbols * hmax);
+    if (t->bf) {
+        t->DA1 = A(es * Bm * h1);
+    } else {
+        t->XT = A(es * 16 * Bm);
+        t->H1T = A(es * h1 * Bm);
+        t->H2T = A(es * h2 * Bm);
+        t->DZT = A(es * kSymbols * Bm);
+        t->DA2T = A(es * h2 * Bm);
+        t->DA1T = A(es * h1 * Bm);
+        t->C = (float *)A(4 * Bm * kSymbols);
+    }
+    // split-K partials: up to one split per SM (BF16) or 64 (FP32)
+    t->part = (float *)A(4 * (size_t)(t->num_sms > 64 ? t->num_sms : 64) * kSymbols * hmax);
     t->colsum = (float *)A(4 * (Bm / 128) * kSymbols);
     t->losspart = (float *)A(4 * (Bm / 128));
     t->err = (int *)A(4);
