@@ -396,7 +396,13 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     const uint32_t tm = tmem_base;
 
     if (warp == 0 && lane == 0) {
-        // producer
+        // producer; first the activation rows that will mask this tile's
+        // gradient are pulled into L2 (one contiguous block)
+        if (epi == EPI_RELU_GRAD && m0 < e.M) {
+            const uint32_t bytes = (uint32_t)(min(128, e.M - m0) * N * 2);
+            const void *src = static_cast<const uint16_t *>(e.act) + (size_t)m0 * N;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+        }
         for (int i = 0; i < nkb; i++) {
             const int s = i % NS;
             if (!tc::mbar_wait(&empty[s], ((i / NS) & 1) ^ 1, kGemmWaitLimit)) { s_fail = 1; break; }
@@ -680,40 +686,50 @@ __global__ void k_features(const uint8_t *ctx, int B, int ldT, void *X, void *XT
     }
 }
 
-__global__ void __launch_bounds__(256) k_layer1_f32(const uint8_t *ctx, int B, const float *W1, const float *b1,
-                                                    int h1, uint16_t *H1, size_t p1) {
-    __shared__ float tile[32][257];
-    __shared__ float xs[32][kPriors];
-    const int tid = threadIdx.x, b0 = blockIdx.x * 32;
-    for (int i = tid; i < 32 * kPriors; i += 256) {
+// First layer of the BF16 modes on the CUDA cores in FP32 (K = 12 is too
+// thin for the tensor cores to pay): h1 = ReLU(b1 + sum_k W1[j][k] x_k),
+// written as bf16 rows (and low planes when p1 != 0).  32 contexts per
+// block, thread = hidden unit; the bf16 tile is staged in shared memory and
+// leaves as 16-byte rows.
+constexpr int kL1Ctx = 32;
+__global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, const float *W1, const float *b1, int h1,
+                                                uint16_t *H1, size_t p1) {
+    __shared__ __align__(16) uint16_t thi[kL1Ctx * kMaxHidden];
+    __shared__ __align__(16) uint16_t tlo[kL1Ctx * kMaxHidden];
+    __shared__ float xs[kL1Ctx][kPriors];
+    const int tid = threadIdx.x, b0 = blockIdx.x * kL1Ctx;
+    for (int i = tid; i < kL1Ctx * kPriors; i += 256) {
         const int r = i / kPriors, k = i % kPriors;
         xs[r][k] = b0 + r < B ? (float)ctx[(size_t)(b0 + r) * kPriors + k] * 0.0078125f - 1.0f : 0.0f;
     }
     __syncthreads();
-    for (int j = tid; j < h1; j += 256) {
+    if (tid < h1) {
+        const int j = tid;
         float w[kPriors];
 #pragma unroll
         for (int k = 0; k < kPriors; k++) w[k] = W1[j * kPriors + k];
         const float bj = b1[j];
-        for (int r = 0; r < 32; r++) {
+        for (int r = 0; r < kL1Ctx; r++) {
             float acc = bj;
 #pragma unroll
             for (int k = 0; k < kPriors; k++) acc = fmaf(xs[r][k], w[k], acc);
-            tile[r][j] = fmaxf(acc, 0.0f);
+            const float v = fmaxf(acc, 0.0f);
+            const uint16_t hi = f2bf(v);
+            thi[r * h1 + j] = hi;
+            if (p1) tlo[r * h1 + j] = f2bf(v - bf2f(hi));
         }
     }
     __syncthreads();
-    for (int i = tid; i < 32 * h1; i += 256) {
-        const int r = i / h1, j = i % h1;
-        if (b0 + r >= B) continue;
-        const float v = tile[r][j];
-        const uint16_t hi = f2bf(v), lo = f2bf(v - bf2f(hi));
-        H1[(size_t)(b0 + r) * h1 + j] = hi;
-        H1[(size_t)(b0 + r) * h1 + j + p1] = lo;
+    // rows b0.. are contiguous in H1: one block of rows * h1 bf16
+    const int rows = min(kL1Ctx, B - b0), n16 = rows * h1 / 8;
+    uint4 *dst = reinterpret_cast<uint4 *>(H1 + (size_t)b0 * h1);
+    for (int i = tid; i < n16; i += 256) dst[i] = reinterpret_cast<const uint4 *>(thi)[i];
+    if (p1) {
+        uint4 *dl = reinterpret_cast<uint4 *>(H1 + p1 + (size_t)b0 * h1);
+        for (int i = tid; i < n16; i += 256) dl[i] = reinterpret_cast<const uint4 *>(tlo)[i];
     }
 }
 
-// out[i] = sum_z part[z * stride + i] (fixed order: deterministic)
 // out[i] = scale * sum_z part[z * stride + i]: 32 columns per block, the
 // partials split over blockDim.y row groups and combined in a fixed order
 // (deterministic).  With `pad16` the columns are a [h][16] array whose first
@@ -735,6 +751,32 @@ __global__ void k_reduce_parts(const float *part, int nparts, size_t stride, int
         t *= scale;
         if (!pad16) out[i] = t;
         else if (i % 16 < kPriors) out[(i / 16) * kPriors + i % 16] = t;
+    }
+}
+
+// The same for wide outputs (n and stride multiples of 4): 128 columns per
+// block as float4 columns.
+__global__ void k_reduce_parts4(const float *part, int nparts, size_t stride, int n, float *out, float scale) {
+    __shared__ float4 red[8][32];
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int i = (blockIdx.x * 32 + x) * 4;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n) {
+#pragma unroll 4
+        for (int z = y; z < nparts; z += 8) {
+            const float4 v = *reinterpret_cast<const float4 *>(part + (size_t)z * stride + i);
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        }
+    }
+    red[y][x] = s;
+    __syncthreads();
+    if (y == 0 && i < n) {
+        float4 t = red[0][x];
+        for (int k = 1; k < 8; k++) {
+            const float4 v = red[k][x];
+            t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+        }
+        *reinterpret_cast<float4 *>(out + i) = make_float4(t.x * scale, t.y * scale, t.z * scale, t.w * scale);
     }
 }
 
@@ -939,6 +981,10 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
 
 void reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int pad16,
                   cudaStream_t st) {
+    if (!pad16 && n >= 4096 && n % 4 == 0 && stride % 4 == 0 && nparts < 256) {
+        k_reduce_parts4<<<(n + 127) / 128, dim3(32, 8), 0, st>>>(part, nparts, stride, n, out, scale);
+        return;
+    }
     const int G = nparts >= 256 ? 32 : 8;
     k_reduce_parts<<<(n + 31) / 32, dim3(32, G), 0, st>>>(part, nparts, stride, n, out, scale, pad16);
 }
@@ -980,8 +1026,9 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     // layer 1, 2: bias + ReLU
     e.bias = p.b1; e.out = t->H1; e.outT = t->H1T; e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     dlic_status s = DLIC_OK;
-    if (t->split)
-        k_layer1_f32<<<(B + 31) / 32, 256, 0, st>>>(ctx, B, p.W1, p.b1, h1, static_cast<uint16_t *>(t->H1), Bm * h1);
+    if (bf)
+        k_layer1<<<(B + kL1Ctx - 1) / kL1Ctx, 256, 0, st>>>(ctx, B, p.W1, p.b1, h1, static_cast<uint16_t *>(t->H1),
+                                                          sp * Bm * h1);
     else if ((s = gemm(t, rowmaj(t->X, 16), wmat(t->w1, h1, 16), B, h1, 16, EPI_BIAS_RELU, e, 1, st)))
         return s;
     e = EpiArgs{}; e.bias = p.b2; e.out = t->H2; e.outT = t->H2T; e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
