@@ -10,16 +10,18 @@
 // its payload words in shared memory.  Per wave each CTA:
 //   1. gathers the 12 priors of its pixels from a ring buffer of the last
 //      columns of every live row (a replicated copy in every CTA),
-//   2. runs the three dense layers as tcgen05 MMAs with the weights as the
-//      A operand (M = 128 units) and the wave's pixels as the B operand
+//   2. runs the first layer (12 inputs) on the CUDA cores with dp4a, and
+//      the two wide layers as tcgen05 MMAs with the weights as the A
+//      operand (M = 128 units) and the wave's pixels as the B operand
 //      (N = pixels, padded to 16), so a handful of pixels still fills the
 //      M dimension; FP32 accumulators in tensor memory are exact integers,
 //   3. turns the 256 logits of each pixel into its frequency table with one
 //      warp per pixel (warp max, prefix sum, ballot search) and performs the
 //      rANS decoding step of the pixel's stream,
 //   4. writes the decoded pixel to the image and, through distributed shared
-//      memory, to every CTA's ring buffer,
-// then the cluster synchronises once before the next wave.
+//      memory, to the ring buffers of the CTAs that read it,
+// then, unless neighbour-to-neighbour rings are in use, the cluster
+// synchronises once before the next wave.
 #include "coder_device.cuh"
 #include "tc.cuh"
 
@@ -31,7 +33,7 @@ constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
 
 struct DecTcLayout {
-    uint32_t w1, w2, w3, b1, b23, z, ring, tring, rows, pg, dsym, lut, bf, st_x, st_pos, st_end, pay, total;
+    uint32_t w1, w2, w3, pri, b23, z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, total;
 };
 
 // Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
@@ -48,7 +50,7 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
     L.w1 = take(32u * kDecHidden);
     L.w2 = take(2u * kDecHidden * kDecHidden);
     L.w3 = take(512u * kDecHidden);
-    L.b1 = take(32u * nt);
+    L.pri = take(16u * nt);
     L.b23 = take(2u * nt * kDecHidden);
     L.z = take(4u * nt * kSymbols);
     L.ring = take(16u * rows);
@@ -57,7 +59,6 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
     L.pg = take(4u * nt);
     L.dsym = take(rows);
     L.lut = take(4u * 64);
-    L.bf = take(2u * 256);
     L.st_x = take(4u * g);
     L.st_pos = take(4u * g);
     L.st_end = take(4u * g);
@@ -188,8 +189,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
         if (tid < 64) lut[tid] = m.lut[tid];
-        uint16_t *bf = reinterpret_cast<uint16_t *>(smem + L.bf);
-        if (tid < 256) bf[tid] = tc::bf16_of_int(tid - 128);
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
         for (int i = tid; i < prm.ring_rows * 4; i += kDecThreads) ring[i] = 0u;
         uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
@@ -317,17 +316,17 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     uint8_t *ring = smem + L.ring;
     const uint32_t ring_addr = tc::smem_addr(ring);
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
-    uint8_t *b1 = smem + L.b1;
+    uint8_t *pri = smem + L.pri;   // priors of the chunk's pixels as s8 (x - 128), 16 bytes each
     uint8_t *b23 = smem + L.b23;
     float *zb = reinterpret_cast<float *>(smem + L.z);
-    const uint32_t sb1 = tc::smem_addr(b1), sb23 = tc::smem_addr(b23);
-    const uint32_t sw1 = tc::smem_addr(smem + L.w1), sw2 = tc::smem_addr(smem + L.w2),
-                   sw3 = tc::smem_addr(smem + L.w3);
+    const uint32_t sb23 = tc::smem_addr(b23);
+    const uint32_t sw2 = tc::smem_addr(smem + L.w2), sw3 = tc::smem_addr(smem + L.w3);
+    // this thread's row of the first layer's INT8 weights, 4 inputs per word
+    const uint32_t w1a = m.q1t[unit], w1b = m.q1t[kDecHidden + unit], w1c = m.q1t[2 * kDecHidden + unit];
     const int rmask = prm.ring_rows - 1;
     uint32_t phase = 0;
     // Operand descriptors of K step 0; K step ks starts 256 bytes further,
     // i.e. 16 more in the descriptor's start-address field.
-    const uint64_t dw1 = tc::make_desc(sw1, 128u, 256u), db1 = tc::make_desc(sb1, 128u, 256u);
     const uint64_t dw2 = tc::make_desc(sw2, 128u, 16u * kDecHidden);
     const uint64_t dw3 = tc::make_desc(sw3, 128u, 16u * kDecHidden);
     const uint64_t dw3b = tc::make_desc(sw3 + 16u * 16u * kDecHidden, 128u, 16u * kDecHidden);
@@ -343,9 +342,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         if (tid == 0 && !s_fail) {
             tc::fence_after_sync();
             const uint32_t idesc = tc::idesc_bf16_f32(128, NP);
-            if (layer == 1) {
-                tc::mma_bf16(tm, dw1, db1, idesc, 0u);
-            } else if (layer == 2) {
+            if (layer == 2) {
                 // two independent accumulation chains (K halves), summed in
                 // the epilogue: exact, since every partial sum is an integer
                 for (int j = 0; j < kDecHidden / 32; j++)
@@ -398,17 +395,20 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     uint8_t *dsym = smem + L.dsym;   // this wave's decoded pixels, by row-list index
     __shared__ int s_wcnt[kDecWarps];
     const int T = 3 * (H - 1) + W;
+    // When P divides S the owned rows of a wave are r0, r0 + P, ... and no
+    // row list is built.
+    const bool modrows = (S % P) == 0;
+    // Without a per-wave cluster barrier a decoded pixel goes to the image
+    // at once; otherwise the stores wait until the barrier has been arrived at.
+    const bool direct = p2p || P == 1;
     for (int t = 0; t < T; t++) {
         const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
         const int r_hi = min(H - 1, t / 3);
         // rows of this wave owned by this CTA, in increasing order
         int nk = 0;
-        if (S % P == 0) {
-            // owned rows are exactly r = k mod P
-            const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
+        const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
+        if (modrows) {
             nk = r0 <= r_hi ? ((r_hi - r0) >> lgP) + 1 : 0;
-            for (int i = tid; i < nk; i += kDecThreads) rowlist[i] = r0 + (i << lgP);
-            __syncthreads();
         } else {
             for (int seg = r_lo; seg <= r_hi; seg += kDecThreads) {
                 const int r = seg + tid;
@@ -428,17 +428,18 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 __syncthreads();
             }
         }
+        auto row_of = [&](int i) { return modrows ? r0 + (i << lgP) : rowlist[i]; };
         const bool spread = r_hi - r_lo < S;
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
             // 1. priors of the chunk's pixels, four threads per pixel with
-            //    three priors each (zero rows pad the chunk to NP)
+            //    three priors each (the pad pixels up to NP get zeros)
             if (tid < 4 * NP) {
                 const int px = tid >> 2, part = tid & 3;
                 uint32_t v3[3] = {0x80u, 0x80u, 0x80u};
                 if (px < nc) {
-                    const int r = rowlist[base + px], c = t - 3 * r;
+                    const int r = row_of(base + px), c = t - 3 * r;
 #pragma unroll
                     for (int q3 = 0; q3 < 3; q3++) {
                         const int q = 3 * part + q3;
@@ -469,29 +470,31 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         }
                     }
                 }
-                const uint16_t *bf = reinterpret_cast<const uint16_t *>(smem + L.bf);
-                uint16_t *row = reinterpret_cast<uint16_t *>(b1);
+                // network input x - 128 as s8 (out-of-image priors are 0)
 #pragma unroll
-                for (int q3 = 0; q3 < 3; q3++) {
-                    const int q = 3 * part + q3;
-                    row[tc::kmajor_offset(px, q, 16) / 2] = px < nc ? bf[v3[q3]] : (uint16_t)0;
-                }
-                if (part == 3) {
-#pragma unroll
-                    for (int q = kPriors; q < 16; q++) row[tc::kmajor_offset(px, q, 16) / 2] = 0;
-                }
+                for (int q3 = 0; q3 < 3; q3++) pri[16 * px + 3 * part + q3] = (uint8_t)(v3[q3] ^ 0x80u);
                 if (part == 0 && px < nc) {
                     // local stream of the pixel and the warp that runs its
                     // table: by pixel when no two rows of the wave share a
                     // stream, else by stream so that they run in row order
-                    const int r = rowlist[base + px];
+                    const int r = row_of(base + px);
                     const int g = fast_mod(r, S, invS) >> lgP;
                     pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
                 }
             }
-            // 2. the three layers
-            run_layer(1, NP);
-            hidden_epilogue(NP, s1r, o1r, false);
+            // 2. the three layers: the first (K = 12) as dp4a on the CUDA
+            //    cores, thread = (unit, pixel group); exact integer sums
+            //    requantised like the tensor-core epilogues
+            __syncthreads();
+            for (int px = cg; px < NP; px += 4) {
+                const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
+                const int acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
+                const float h = (float)requant_u8(acc, s1r, o1r);
+                const uint32_t mine = __float_as_uint(h) >> 16;   // bf16 of the integer
+                const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                if ((lane & 1) == 0)
+                    *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(px, unit, kDecHidden)) = mine | (other << 16);
+            }
             run_layer(2, NP);
             hidden_epilogue(NP, s2r, o2r, true);
             run_layer(3, NP);
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 const int pg = pixg[i];
                 if ((pg >> 24) != warp) continue;
                 const int g = pg & 0xFFFFFF;
-                const int r = rowlist[base + i], c = t - 3 * r;
+                const int r = row_of(base + i), c = t - 3 * r;
                 const uint32_t x = st_x[g];
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
@@ -581,7 +584,10 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         }
                     }
                     st_x[g] = xn;
-                    dsym[base + i] = (uint8_t)sym;
+                    if (direct)
+                        im.pixels[(int64_t)r * im.pitch + c] = (uint8_t)sym;
+                    else
+                        dsym[base + i] = (uint8_t)sym;
                 }
                 // the row is read by this CTA and, as rows r+1 and r+2, by the
                 // next two CTAs (every CTA when rows are not owned mod P)
@@ -602,17 +608,21 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
             }
             __syncthreads();
         }
-        // The cluster barrier is arrived at before this wave's pixels go to the
-        // image, so its release waits only for the ring writes; the image
-        // stores complete during the next wave.
-        __syncthreads();   // every ring write of this wave precedes the barrier arrival
-        if (!p2p && P > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        for (int i = tid; i < nk; i += kDecThreads) {
-            const int r = rowlist[i];
-            im.pixels[(int64_t)r * im.pitch + (t - 3 * r)] = dsym[i];
+        if (!direct) {
+            // The cluster barrier is arrived at before this wave's pixels go
+            // to the image, so its release waits only for the ring writes; the
+            // image stores complete during the next wave.
+            __syncthreads();   // every ring write of this wave precedes the barrier arrival
+            asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+            for (int i = tid; i < nk; i += kDecThreads) {
+                const int r = row_of(i);
+                im.pixels[(int64_t)r * im.pitch + (t - 3 * r)] = dsym[i];
+            }
+            __syncthreads();   // the row list is rebuilt only after every image store
+            asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else if (!modrows) {
+            __syncthreads();   // the row list is rebuilt only after every reader is done
         }
-        __syncthreads();   // the row list is rebuilt only after every image store
-        if (!p2p && P > 1) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     // final states must be back at the initial value with every word read
     for (int g = tid; g < G; g += kDecThreads)
