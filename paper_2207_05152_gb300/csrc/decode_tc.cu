@@ -433,54 +433,55 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
-            // 1. priors of the chunk's pixels, four threads per pixel with
-            //    three priors each (the pad pixels up to NP get zeros)
-            if (tid < 4 * NP) {
-                const int px = tid >> 2, part = tid & 3;
-                uint32_t v3[3] = {0x80u, 0x80u, 0x80u};
+            // 1. priors of the chunk's pixels, one thread per (pixel, prior)
+            //    so that every ring read is in flight at once; the spare
+            //    thirteenth thread of a pixel records its stream and table
+            //    warp.  Pad pixels up to NP get arbitrary inputs.
+            for (int idx = tid; idx < 16 * NP; idx += kDecThreads) {
+                const int px = idx >> 4, q = idx & 15;
+                if (q > kPriors) continue;
+                uint32_t v = 0x80u;
                 if (px < nc) {
                     const int r = row_of(base + px), c = t - 3 * r;
-#pragma unroll
-                    for (int q3 = 0; q3 < 3; q3++) {
-                        const int q = 3 * part + q3;
-                        const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
-                        const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
-                        const int rr = r + dr, cc = c + dc;
-                        if (rr < 0 || cc < 0 || cc >= W) {
-                            v3[q3] = 0u;
-                        } else if (p2p) {
-                            // entry (round of rr, owner distance, column mod 32)
-                            const int slot = (((rr >> lgP) & tqmask) << 2) | (((int)k - rr) & (P - 1));
-                            const uint32_t *e = tring + slot * 32 + (cc & 31);
-                            const uint32_t want = ring_tag(rr, cc);
-                            uint32_t v = ld_volatile_u32(e);
-                            if ((v & 0xFFFFFF00u) != want) {
-                                const long long t0 = clock64();
-                                do {
-                                    v = ld_volatile_u32(e);
-                                    if (clock64() - t0 > kDecWaitLimit) {
-                                        s_fail = 1;
-                                        break;
-                                    }
-                                } while ((v & 0xFFFFFF00u) != want);
-                            }
-                            v3[q3] = v & 0xFFu;
-                        } else {
-                            v3[q3] = ring[((rr & rmask) << 4) + (cc & 15)];
-                        }
+                    if (q == kPriors) {
+                        // local stream of the pixel and the warp that runs its
+                        // table: by pixel when no two rows of the wave share a
+                        // stream, else by stream so that they run in row order
+                        const int g = fast_mod(r, S, invS) >> lgP;
+                        pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
+                        continue;
                     }
+                    const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
+                    const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+                    const int rr = r + dr, cc = c + dc;
+                    if (rr < 0 || cc < 0 || cc >= W) {
+                        v = 0u;
+                    } else if (p2p) {
+                        // entry (round of rr, owner distance, column mod 32)
+                        const int slot = (((rr >> lgP) & tqmask) << 2) | (((int)k - rr) & (P - 1));
+                        const uint32_t *e = tring + slot * 32 + (cc & 31);
+                        const uint32_t want = ring_tag(rr, cc);
+                        v = ld_volatile_u32(e);
+                        if ((v & 0xFFFFFF00u) != want) {
+                            // bounded wait; after any timeout no wait blocks again
+                            const long long t0 = clock64();
+                            do {
+                                v = ld_volatile_u32(e);
+                                if (clock64() - t0 > kDecWaitLimit || *reinterpret_cast<volatile int *>(&s_fail)) {
+                                    s_fail = 1;
+                                    break;
+                                }
+                            } while ((v & 0xFFFFFF00u) != want);
+                        }
+                        v &= 0xFFu;
+                    } else {
+                        v = ring[((rr & rmask) << 4) + (cc & 15)];
+                    }
+                } else if (q == kPriors) {
+                    continue;
                 }
                 // network input x - 128 as s8 (out-of-image priors are 0)
-#pragma unroll
-                for (int q3 = 0; q3 < 3; q3++) pri[16 * px + 3 * part + q3] = (uint8_t)(v3[q3] ^ 0x80u);
-                if (part == 0 && px < nc) {
-                    // local stream of the pixel and the warp that runs its
-                    // table: by pixel when no two rows of the wave share a
-                    // stream, else by stream so that they run in row order
-                    const int r = row_of(base + px);
-                    const int g = fast_mod(r, S, invS) >> lgP;
-                    pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
-                }
+                pri[16 * px + q] = (uint8_t)(v ^ 0x80u);
             }
             // 2. the three layers: the first (K = 12) as dp4a on the CUDA
             //    cores, thread = (unit, pixel group); exact integer sums
@@ -524,6 +525,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 const int g = pg & 0xFFFFFF;
                 const int r = row_of(base + i), c = t - 3 * r;
                 const uint32_t x = st_x[g];
+                // the stream's next word, fetched before it is known to be needed
+                const uint32_t pos = st_pos[g], pend = st_end[g];
+                const uint32_t next_word = pos < pend ? wsrc[pos] : 0u;
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
@@ -570,14 +574,31 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         clo = cb[q];
                     }
                 sym = __shfl_sync(0xffffffffu, sym, Lh);
+                // the decoded pixel goes out first: the next wave of this CTA
+                // and of the next two CTAs reads it
+                if (p2p) {
+                    if (lane < min(3, P)) {
+                        const int slot = (((r >> lgP) & tqmask) << 2) | lane;
+                        const uint32_t a = tring_addr + 4u * (uint32_t)(slot * 32 + (c & 31));
+                        if (lane == 0)
+                            asm volatile("st.shared::cta.u32 [%0], %1;" ::"r"(a), "r"(ring_tag(r, c) | sym) : "memory");
+                        else
+                            st_cluster_u32(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), ring_tag(r, c) | sym);
+                    }
+                } else if (lane < P) {
+                    const uint32_t a = ring_addr + (uint32_t)(((r & rmask) << 4) + (c & 15));
+                    if (P > 1)
+                        st_cluster_u8(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), sym);
+                    else
+                        ring[((r & rmask) << 4) + (c & 15)] = (uint8_t)sym;
+                }
                 f = __shfl_sync(0xffffffffu, f, Lh);
                 clo = __shfl_sync(0xffffffffu, clo, Lh);
                 if (lane == 0) {
                     uint32_t xn = f * (x >> 16) + slot - clo;
                     if (xn < kRansL) {
-                        const uint32_t pos = st_pos[g];
-                        if (pos < st_end[g]) {
-                            xn = (xn << 16) | wsrc[pos];
+                        if (pos < pend) {
+                            xn = (xn << 16) | next_word;
                             st_pos[g] = pos + 1;
                         } else {
                             s_err = 1;
@@ -588,21 +609,6 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                         im.pixels[(int64_t)r * im.pitch + c] = (uint8_t)sym;
                     else
                         dsym[base + i] = (uint8_t)sym;
-                }
-                // the row is read by this CTA and, as rows r+1 and r+2, by the
-                // next two CTAs (every CTA when rows are not owned mod P)
-                if (p2p) {
-                    if (lane < min(3, P)) {
-                        const int slot = (((r >> lgP) & tqmask) << 2) | lane;
-                        const uint32_t a = tring_addr + 4u * (uint32_t)(slot * 32 + (c & 31));
-                        st_cluster_u32(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), ring_tag(r, c) | sym);
-                    }
-                } else if (lane < P) {
-                    const uint32_t a = ring_addr + (uint32_t)(((r & rmask) << 4) + (c & 15));
-                    if (P > 1)
-                        st_cluster_u8(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), sym);
-                    else
-                        ring[((r & rmask) << 4) + (c & 15)] = (uint8_t)sym;
                 }
                 __syncwarp();
             }
