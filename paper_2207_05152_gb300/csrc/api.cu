@@ -25,10 +25,6 @@ dlic_status cuda_fail(cudaError_t e, const char *what) {
     return fail(DLIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
-cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
-bool tc_decode_supported(const DevModel &m);
-void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P);
 constexpr int kDecodeGroups = 5;   // cluster sizes 1, 2, 4, 8, 16
 
 static inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -396,7 +392,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t) * (size_t)n, cs);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     }
-    const bool use_tc = tc_decode_supported(m->dev);
+    const bool use_wave = wave_decode_supported(m->dev);
     // workspace offsets of every image's stream states
     std::vector<size_t> st_off(n);
     {
@@ -412,7 +408,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         Hs[i] = im[i].height;
         Ws[i] = im[i].width;
     }
-    if (use_tc) choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, P.data());
+    if (use_wave) choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
     int groups_used = 0;
     for (int gi = 0; gi < kDecodeGroups; gi++)
         for (int i = 0; i < n; i++)
@@ -456,7 +452,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
                 e.st_off = st_off[i];
                 e.sidx = i;
             }
-            cudaError_t e = use_tc ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, gs) : launch_decode_cc(m->dev, *b, gs);
+            cudaError_t e = use_wave ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, gs) : launch_decode_cc(m->dev, *b, gs);
             delete b;
             if (e != cudaSuccess) return cuda_fail(e, "decode launch");
         }

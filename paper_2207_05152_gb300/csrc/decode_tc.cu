@@ -33,26 +33,56 @@ constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
 
 struct DecTcLayout {
-    uint32_t w1, w2, w3, pri, b23, z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, total;
+    // INT8 network: bf16 operand tiles, s8 priors, bf16 activations
+    uint32_t w1, w2, w3, pri, b23;
+    // FP32 network: W1^T | b1 | b2 | b3, W2^T, the W3^T staging ring, FP32
+    // inputs and activations (the logits z overlay xs and h1t)
+    uint32_t wf, w2f, w3s, xs, h1t, h2t;
+    uint32_t z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, total;
 };
+
+// FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
+// b1, b2, b3, then W2^T [h1][h2].  W3^T [h2][256] streams through a ring of
+// kW3Stages buffers of kW3Rows rows, refilled by bulk copies from L2.
+constexpr int kW3Rows = 16, kW3Stages = 5;
+__host__ __device__ inline uint32_t dec_f32_weight_floats(int h1, int h2) {
+    return (uint32_t)(kPriors * h1 + h1 + h2 + kSymbols);
+}
 
 // Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
 // the bound on the pixels of one wave), `tslots` tagged-ring rows, `g` owned
-// streams and `pay_words` staged payload words.
-__host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, int g, int pay_words) {
-    DecTcLayout L;
+// streams and `pay_words` staged payload words, for the INT8 tensor-core
+// network or (f32) the FP32 network of widths h1, h2.
+__host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, int g, int pay_words, bool f32 = false,
+                                                  int h1 = kDecHidden, int h2 = kDecHidden) {
+    DecTcLayout L{};
     uint32_t off = 0;
     auto take = [&](uint32_t bytes) {
         const uint32_t o = off;
         off += (bytes + 127u) & ~127u;
         return o;
     };
-    L.w1 = take(32u * kDecHidden);
-    L.w2 = take(2u * kDecHidden * kDecHidden);
-    L.w3 = take(512u * kDecHidden);
-    L.pri = take(16u * nt);
-    L.b23 = take(2u * nt * kDecHidden);
-    L.z = take(4u * nt * kSymbols);
+    if (f32) {
+        L.wf = take(4u * dec_f32_weight_floats(h1, h2));
+        L.w2f = take(4u * h1 * h2);
+        L.w3s = take(4u * kW3Stages * kW3Rows * kSymbols);
+        // xs, then h1t [unit][nt + 4] (conflict-free float4 rows); z
+        // overlays both once the second layer has consumed them
+        const uint32_t xs_bytes = 64u * nt, h1t_bytes = 4u * h1 * (nt + 4), z_bytes = 4u * nt * kSymbols;
+        const uint32_t region = xs_bytes + h1t_bytes > z_bytes ? xs_bytes + h1t_bytes : z_bytes;
+        const uint32_t base = take(region);
+        L.xs = base;
+        L.h1t = base + xs_bytes;
+        L.z = base;
+        L.h2t = take(4u * h2 * (nt + 4));
+    } else {
+        L.w1 = take(32u * kDecHidden);
+        L.w2 = take(2u * kDecHidden * kDecHidden);
+        L.w3 = take(512u * kDecHidden);
+        L.pri = take(16u * nt);
+        L.b23 = take(2u * nt * kDecHidden);
+    }
+    if (!f32) L.z = take(4u * nt * kSymbols);
     L.ring = take(16u * rows);
     L.tring = take(128u * tslots);
     L.rows = take(4u * rows);
@@ -69,6 +99,7 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
 
 struct DecTcParams {
     int P;            // CTAs per image (cluster size)
+    int h1, h2;       // hidden widths (FP32 network)
     int nt;           // pixels per chunk (multiple of 16, <= 128)
     int ring_rows;    // power of two
     int tq;           // tagged ring: row rounds kept per neighbour (power of two)
@@ -162,9 +193,70 @@ __device__ __forceinline__ float key_float(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-__global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
+// FP32 network helpers of the wavefront decoder.  Activations are stored
+// [unit][pitch PT] so that a k row of consecutive pixels is one broadcast
+// load.  Each unit starts from its bias and accumulates fma(x_k, w_jk, acc)
+// for k ascending, the order the encoder uses.
+
+// The logits phase: thread = (2 units, 4 pixels) over `groups` pixel
+// groups; the threads consume w3_chunks staging loads in sequence (rows
+// k0 .. k0 + rows - 1 of W3^T each, k ascending) with the accumulators in
+// registers, and after each chunk every thread synchronises and thread 0
+// refills the buffer just read with the load kW3Stages further on.
+template <class Issue>
+__device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, int &w3_seq, Issue &w3_issue, int h2,
+                                           const float *b3s, const float *h2t, int PT, const uint8_t *w3buf,
+                                           uint64_t *w3bar, float *zb, int &s_fail) {
+    const bool l3 = tid < (kSymbols / 2) * groups;   // at most 128 x 3 < kDecThreads
+    const int up = tid % (kSymbols / 2), p0 = 4 * (tid / (kSymbols / 2));
+    float a[2][4];
+    if (l3) {
+        const float2 bb = *reinterpret_cast<const float2 *>(b3s + 2 * up);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            a[0][j] = bb.x;
+            a[1][j] = bb.y;
+        }
+    }
+    for (int c = 0; c < w3_chunks; c++, w3_seq++) {
+        const int stg = w3_seq % kW3Stages;
+        const int rows = min(kW3Rows, h2 - c * kW3Rows);
+        if (l3) {
+            if (!*reinterpret_cast<volatile int *>(&s_fail) &&
+                !tc::mbar_wait(&w3bar[stg], (uint32_t)(w3_seq / kW3Stages) & 1u, kDecWaitLimit))
+                s_fail = 1;
+            const float *w3c = reinterpret_cast<const float *>(w3buf) + stg * kW3Rows * kSymbols;
+#pragma unroll 4
+            for (int kr = 0; kr < rows; kr++) {
+                const float2 w = *reinterpret_cast<const float2 *>(w3c + kr * kSymbols + 2 * up);
+                const float4 x = *reinterpret_cast<const float4 *>(h2t + (c * kW3Rows + kr) * PT + p0);
+                a[0][0] = __fmaf_rn(x.x, w.x, a[0][0]);
+                a[0][1] = __fmaf_rn(x.y, w.x, a[0][1]);
+                a[0][2] = __fmaf_rn(x.z, w.x, a[0][2]);
+                a[0][3] = __fmaf_rn(x.w, w.x, a[0][3]);
+                a[1][0] = __fmaf_rn(x.x, w.y, a[1][0]);
+                a[1][1] = __fmaf_rn(x.y, w.y, a[1][1]);
+                a[1][2] = __fmaf_rn(x.z, w.y, a[1][2]);
+                a[1][3] = __fmaf_rn(x.w, w.y, a[1][3]);
+            }
+        }
+        __syncthreads();   // every reader is done with this buffer
+        if (tid == 0) w3_issue(w3_seq + kW3Stages);
+    }
+    if (l3) {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            *reinterpret_cast<float2 *>(zb + (p0 + j) * kSymbols + 2 * up) = make_float2(a[0][j], a[1][j]);
+    }
+}
+
+// The wavefront decoder for one image per cluster; F32 selects the FP32
+// network on the CUDA cores instead of the INT8 network on the tensor cores.
+template <bool F32>
+__device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b, const DecTcParams &prm) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
+    __shared__ uint64_t w3bar[kW3Stages];   // FP32: W3^T staging buffers filled
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok, s_S, s_err, s_fail;
 
@@ -179,14 +271,25 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     const DecImage &im = b.img[img_idx];
     const uint8_t *in = b.in + im.in_off;
     const int H = im.H, W = im.W;
-    const DecTcLayout L = dec_layout(NT, prm.ring_rows, 4 * prm.tq, prm.max_g, prm.pay_words);
+    const int h1 = prm.h1, h2 = prm.h2;
+    const DecTcLayout L = dec_layout(NT, prm.ring_rows, 4 * prm.tq, prm.max_g, prm.pay_words, F32, h1, h2);
 
     // --- set-up: weights, parameters, tensor memory, header and streams ---
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w);
-        uint4 *dst = reinterpret_cast<uint4 *>(smem + L.w1);
-        const int n16 = (int)(m.tc_w_bytes / 16);
-        for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
+        if constexpr (F32) {
+            float *wf = reinterpret_cast<float *>(smem + L.wf);
+            for (int i = tid; i < kPriors * h1; i += kDecThreads) wf[i] = m.w1t[i];
+            for (int i = tid; i < h1; i += kDecThreads) wf[kPriors * h1 + i] = m.b1[i];
+            for (int i = tid; i < h2; i += kDecThreads) wf[kPriors * h1 + h1 + i] = m.b2[i];
+            for (int i = tid; i < kSymbols; i += kDecThreads) wf[kPriors * h1 + h1 + h2 + i] = m.b3[i];
+            for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
+                reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
+        } else {
+            const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem + L.w1);
+            const int n16 = (int)(m.tc_w_bytes / 16);
+            for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
+        }
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
         if (tid < 64) lut[tid] = m.lut[tid];
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
@@ -194,12 +297,18 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
         uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
         for (int i = tid; i < prm.tq * 4 * 32; i += kDecThreads) tring[i] = 0u;
     }
-    if (warp == 0) {
-        tc::tmem_alloc(&tmem_base, 256);
-        tc::tmem_relinquish();
+    if constexpr (!F32) {
+        if (warp == 0) {
+            tc::tmem_alloc(&tmem_base, 256);
+            tc::tmem_relinquish();
+        }
     }
     if (tid == 0) {
-        tc::mbar_init(&bar, 1);
+        if constexpr (!F32) {
+            tc::mbar_init(&bar, 1);
+        } else {
+            for (int q = 0; q < kW3Stages; q++) tc::mbar_init(&w3bar[q], 1);
+        }
         tc::fence_mbar_init();
         s_err = 0;
         s_fail = 0;
@@ -292,7 +401,9 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     // Every CTA of the cluster reads the same header, so this exit is uniform.
     if (!s_ok) {
         if (tid == 0 && k == 0) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
-        if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
+        if constexpr (!F32) {
+            if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
+        }
         return;
     }
     // When every CTA owns the rows k mod P (P divides S), a pixel's priors
@@ -307,12 +418,36 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     const int tqmask = prm.tq - 1;
     if (P > 1) cluster_sync_all();   // every CTA's rings are initialised
 
+    // FP32: W3^T streams through kW3Stages staging buffers in a fixed cycle
+    // of chunks (k rows [kW3Rows c, kW3Rows (c + 1))); load number q goes to
+    // buffer q mod kW3Stages and holds chunk q mod w3_chunks.  Every thread
+    // counts the loads it has consumed in w3_seq.
+    const int w3_chunks = (h2 + kW3Rows - 1) / kW3Rows;
+    int w3_seq = 0;
+    auto w3_issue = [&](int q) {
+        const int stg = q % kW3Stages, c = q % w3_chunks;
+        const uint32_t bytes = (uint32_t)min(kW3Rows, h2 - c * kW3Rows) * kSymbols * 4u;
+        const uint32_t bar_a = tc::smem_addr(&w3bar[stg]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_addr(smem + L.w3s + (uint32_t)stg * kW3Rows * kSymbols * 4u)),
+                     "l"(m.w3t + (size_t)c * kW3Rows * kSymbols), "r"(bytes), "r"(bar_a)
+                     : "memory");
+    };
+    if constexpr (F32) {
+        if (tid == 0)
+            for (int q = 0; q < kW3Stages; q++) w3_issue(q);
+    }
+
     const uint32_t tm = tmem_base;
     const int q4 = warp & 3, cg = warp >> 2;                 // lane quarter, column group (0..3)
     const int unit = 32 * q4 + lane;                          // hidden / output unit of this thread
     const uint32_t tm_q = tm + ((uint32_t)(32 * q4) << 16);
-    const float s1r = m.s1[unit], o1r = m.o1[unit], s2r = m.s2[unit], o2r = m.o2[unit];
-    const float s3a = m.s3[unit], o3a = m.o3[unit], s3b = m.s3[128 + unit], o3b = m.o3[128 + unit];
+    float s1r = 0.f, o1r = 0.f, s2r = 0.f, o2r = 0.f, s3a = 0.f, o3a = 0.f, s3b = 0.f, o3b = 0.f;
+    if constexpr (!F32) {
+        s1r = m.s1[unit]; o1r = m.o1[unit]; s2r = m.s2[unit]; o2r = m.o2[unit];
+        s3a = m.s3[unit]; o3a = m.o3[unit]; s3b = m.s3[128 + unit]; o3b = m.o3[128 + unit];
+    }
     uint8_t *ring = smem + L.ring;
     const uint32_t ring_addr = tc::smem_addr(ring);
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
@@ -322,7 +457,12 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     const uint32_t sb23 = tc::smem_addr(b23);
     const uint32_t sw2 = tc::smem_addr(smem + L.w2), sw3 = tc::smem_addr(smem + L.w3);
     // this thread's row of the first layer's INT8 weights, 4 inputs per word
-    const uint32_t w1a = m.q1t[unit], w1b = m.q1t[kDecHidden + unit], w1c = m.q1t[2 * kDecHidden + unit];
+    uint32_t w1a = 0, w1b = 0, w1c = 0;
+    if constexpr (!F32) {
+        w1a = m.q1t[unit];
+        w1b = m.q1t[kDecHidden + unit];
+        w1c = m.q1t[2 * kDecHidden + unit];
+    }
     const int rmask = prm.ring_rows - 1;
     uint32_t phase = 0;
     // Operand descriptors of K step 0; K step ks starts 256 bytes further,
@@ -437,7 +577,8 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
             //    so that every ring read is in flight at once; the spare
             //    thirteenth thread of a pixel records its stream and table
             //    warp.  Pad pixels up to NP get arbitrary inputs.
-            for (int idx = tid; idx < 16 * NP; idx += kDecThreads) {
+            const int NPin = F32 ? (nc + 3) & ~3 : NP;   // pixels whose inputs are written
+            for (int idx = tid; idx < 16 * NPin; idx += kDecThreads) {
                 const int px = idx >> 4, q = idx & 15;
                 if (q > kPriors) continue;
                 uint32_t v = 0x80u;
@@ -480,42 +621,106 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
                 } else if (q == kPriors) {
                     continue;
                 }
-                // network input x - 128 as s8 (out-of-image priors are 0)
-                pri[16 * px + q] = (uint8_t)(v ^ 0x80u);
+                // network input: x/128 - 1 (FP32) or x - 128 as s8; out-of-image
+                // priors are 0
+                if constexpr (F32)
+                    reinterpret_cast<float *>(smem + L.xs)[16 * px + q] = __fmaf_rn((float)v, 0.0078125f, -1.0f);
+                else
+                    pri[16 * px + q] = (uint8_t)(v ^ 0x80u);
             }
-            // 2. the three layers: the first (K = 12) as dp4a on the CUDA
-            //    cores, thread = (unit, pixel group); exact integer sums
-            //    requantised like the tensor-core epilogues
-            __syncthreads();
-            for (int px = cg; px < NP; px += 4) {
-                const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
-                const int acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
-                const float h = (float)requant_u8(acc, s1r, o1r);
-                const uint32_t mine = __float_as_uint(h) >> 16;   // bf16 of the integer
-                const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                if ((lane & 1) == 0)
-                    *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(px, unit, kDecHidden)) = mine | (other << 16);
-            }
-            run_layer(2, NP);
-            hidden_epilogue(NP, s2r, o2r, true);
-            run_layer(3, NP);
-            for (int c0 = 8 * cg; c0 < NP; c0 += 32) {
-                uint32_t va[8], va2[8], vb[8], vb2[8];
-                tmem_ld8(tm_q + (uint32_t)c0, va);
-                tmem_ld8(tm_q + (uint32_t)(NP + c0), va2);
-                tmem_ld8(tm_q + (uint32_t)(2 * NP + c0), vb);
-                tmem_ld8(tm_q + (uint32_t)(3 * NP + c0), vb2);
-                tc::tmem_wait_ld();
+            __syncthreads();   // every prior of the chunk is in place
+            if constexpr (F32) {
+                // 2. the FP32 network on the CUDA cores, fixed order per unit:
+                //    bias first, then fma(x_k, w_jk, acc) for k ascending.
+                //    Thread = (unit, 4 pixels); activations [unit][pitch PT].
+                const float *xs = reinterpret_cast<const float *>(smem + L.xs);
+                const float *wf = reinterpret_cast<const float *>(smem + L.wf);
+                const float *w1s = wf, *b1s = wf + kPriors * h1, *b2s = b1s + h1, *b3s = b2s + h2;
+                const float *w3s = b3s + kSymbols;
+                float *h1t = reinterpret_cast<float *>(smem + L.h1t);
+                float *h2t = reinterpret_cast<float *>(smem + L.h2t);
+                const int PT = NT + 4;
+                const int NG = (nc + 3) >> 2;
+                for (int it = tid; it < h1 * NG; it += kDecThreads) {
+                    const int u = it % h1, p0 = 4 * (it / h1);
+                    float a[4];
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    const float a = __fadd_rn(__uint_as_float(va[e]), __uint_as_float(va2[e]));
-                    const float bsum = __fadd_rn(__uint_as_float(vb[e]), __uint_as_float(vb2[e]));
-                    zb[(c0 + e) * kSymbols + unit] = __fmaf_rn(a, s3a, o3a);
-                    zb[(c0 + e) * kSymbols + 128 + unit] = __fmaf_rn(bsum, s3b, o3b);
+                    for (int j = 0; j < 4; j++) a[j] = b1s[u];
+#pragma unroll
+                    for (int kk = 0; kk < kPriors; kk++) {
+                        const float w = w1s[kk * h1 + u];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[16 * (p0 + j) + kk], w, a[j]);
+                    }
+                    *reinterpret_cast<float4 *>(h1t + u * PT + p0) =
+                        make_float4(a[0] > 0.0f ? a[0] : 0.0f, a[1] > 0.0f ? a[1] : 0.0f, a[2] > 0.0f ? a[2] : 0.0f,
+                                    a[3] > 0.0f ? a[3] : 0.0f);
                 }
+                __syncthreads();
+                // second layer: thread = (4 units, 2 pixels), W2^T in shared memory
+                const int NPP = (nc + 1) >> 1;
+                const float *w2s = reinterpret_cast<const float *>(smem + L.w2f);
+                for (int it = tid; it < (h2 / 4) * NPP; it += kDecThreads) {
+                    const int uq = it % (h2 / 4), p0 = 2 * (it / (h2 / 4));
+                    const float4 bb = *reinterpret_cast<const float4 *>(b2s + 4 * uq);
+                    float a0[4] = {bb.x, bb.y, bb.z, bb.w}, a1[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll 4
+                    for (int kk = 0; kk < h1; kk++) {
+                        const float4 w = *reinterpret_cast<const float4 *>(w2s + kk * h2 + 4 * uq);
+                        const float2 x = *reinterpret_cast<const float2 *>(h1t + kk * PT + p0);
+                        a0[0] = __fmaf_rn(x.x, w.x, a0[0]);
+                        a0[1] = __fmaf_rn(x.x, w.y, a0[1]);
+                        a0[2] = __fmaf_rn(x.x, w.z, a0[2]);
+                        a0[3] = __fmaf_rn(x.x, w.w, a0[3]);
+                        a1[0] = __fmaf_rn(x.y, w.x, a1[0]);
+                        a1[1] = __fmaf_rn(x.y, w.y, a1[1]);
+                        a1[2] = __fmaf_rn(x.y, w.z, a1[2]);
+                        a1[3] = __fmaf_rn(x.y, w.w, a1[3]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+                        *reinterpret_cast<float2 *>(h2t + (4 * uq + i) * PT + p0) =
+                            make_float2(a0[i] > 0.0f ? a0[i] : 0.0f, a1[i] > 0.0f ? a1[i] : 0.0f);
+                }
+                __syncthreads();
+                // logits: W3^T arrives chunk by chunk in the staging buffers;
+                // z overlays the inputs and the first layer's activations
+                f32_logits(tid, NG, w3_chunks, w3_seq, w3_issue, h2, b3s, h2t, PT, smem + L.w3s, w3bar, zb, s_fail);
+                __syncthreads();
+            } else {
+                // 2. the three layers: the first (K = 12) as dp4a on the CUDA
+                //    cores, thread = (unit, pixel group); exact integer sums
+                //    requantised like the tensor-core epilogues
+                for (int px = cg; px < NP; px += 4) {
+                    const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
+                    const int acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
+                    const float h = (float)requant_u8(acc, s1r, o1r);
+                    const uint32_t mine = __float_as_uint(h) >> 16;   // bf16 of the integer
+                    const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                    if ((lane & 1) == 0)
+                        *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(px, unit, kDecHidden)) = mine | (other << 16);
+                }
+                run_layer(2, NP);
+                hidden_epilogue(NP, s2r, o2r, true);
+                run_layer(3, NP);
+                for (int c0 = 8 * cg; c0 < NP; c0 += 32) {
+                    uint32_t va[8], va2[8], vb[8], vb2[8];
+                    tmem_ld8(tm_q + (uint32_t)c0, va);
+                    tmem_ld8(tm_q + (uint32_t)(NP + c0), va2);
+                    tmem_ld8(tm_q + (uint32_t)(2 * NP + c0), vb);
+                    tmem_ld8(tm_q + (uint32_t)(3 * NP + c0), vb2);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const float a = __fadd_rn(__uint_as_float(va[e]), __uint_as_float(va2[e]));
+                        const float bsum = __fadd_rn(__uint_as_float(vb[e]), __uint_as_float(vb2[e]));
+                        zb[(c0 + e) * kSymbols + unit] = __fmaf_rn(a, s3a, o3a);
+                        zb[(c0 + e) * kSymbols + 128 + unit] = __fmaf_rn(bsum, s3b, o3b);
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
             }
-            tc::fence_before_sync();
-            __syncthreads();
             // 3. tables and rANS steps, one warp per pixel; pixels that share a
             //    stream go to the same warp (by local stream index), in row
             //    order.
@@ -630,6 +835,13 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
             __syncthreads();   // the row list is rebuilt only after every reader is done
         }
     }
+    // FP32: the loads issued ahead for a next wave complete before the CTA
+    // leaves (its shared memory must not be written after it exits)
+    if constexpr (F32) {
+        if (tid == 0)
+            for (int q = w3_seq; q < w3_seq + kW3Stages; q++)
+                if (!tc::mbar_wait(&w3bar[q % kW3Stages], (uint32_t)(q / kW3Stages) & 1u, kDecWaitLimit)) s_fail = 1;
+    }
     // final states must be back at the initial value with every word read
     for (int g = tid; g < G; g += kDecThreads)
         if (st_x[g] != kRansL || st_pos[g] != st_end[g]) s_err = 1;
@@ -637,11 +849,20 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
     __syncthreads();
     if (tid == 0 && (s_err || s_fail))
         atomicMax(b.status + im.sidx, s_fail ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
-    if (warp == 0) {
-        tc::fence_after_sync();
-        tc::tmem_dealloc(tm, 256);
+    if constexpr (!F32) {
+        if (warp == 0) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(tm, 256);
+        }
     }
     if (P > 1) cluster_sync_all();   // no CTA leaves while others may still write its ring
+}
+
+__global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
+    decode_wave<false>(m, b, prm);
+}
+__global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBatch b, DecTcParams prm) {
+    decode_wave<true>(m, b, prm);
 }
 
 // Cluster sizes for a batch (the decode autotuner).  A wave of an image
@@ -652,21 +873,25 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBat
 // its cluster doubled while the clusters of the whole batch still fit on the
 // GPU at once (up to 16 CTAs).
 constexpr double kWaveFixed = 4500.0, kWavePerPixelWarp = 1700.0;
+// FP32 network: the CUDA cores' multiply-adds (about 50K per pixel at
+// 128 a cycle) add to the table rounds, in chunks of 16 pixels.
+constexpr double kWaveFixedF32 = 5000.0, kWavePerPixelF32 = 420.0;
 
-static double est_cycles(int H, int W, int P) {
+static double est_cycles(int H, int W, int P, bool f32) {
     const double waves = 3.0 * (H - 1) + W;
     const int wave_px = min(H, (W + 2) / 3);
     int per = (wave_px + P - 1) / P;
     double per_wave = 0.0;
     while (per > 0) {
-        const int chunk = min(per, 64);
-        per_wave += kWaveFixed + kWavePerPixelWarp * ((chunk + kDecWarps - 1) / kDecWarps);
+        const int chunk = min(per, f32 ? 16 : 64);
+        per_wave += f32 ? kWaveFixedF32 + kWavePerPixelF32 * ((chunk + 3) & ~3) + kWavePerPixelWarp
+                        : kWaveFixed + kWavePerPixelWarp * ((chunk + kDecWarps - 1) / kDecWarps);
         per -= chunk;
     }
     return waves * per_wave;
 }
 
-void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P) {
+void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P) {
     int used = 0;
     for (int i = 0; i < n; i++) {
         P[i] = 1;
@@ -677,7 +902,7 @@ void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P) {
         double worst = 0.0;
         for (int i = 0; i < n; i++) {
             if (P[i] >= 16 || used + P[i] > num_sms) continue;
-            const double t = est_cycles(H[i], W[i], P[i]);
+            const double t = est_cycles(H[i], W[i], P[i], f32);
             if (t > worst) {
                 worst = t;
                 best = i;
@@ -685,19 +910,26 @@ void choose_clusters(const int *H, const int *W, int n, int num_sms, int *P) {
         }
         if (best < 0) break;
         // stop when the longest image no longer gains from a larger cluster
-        if (est_cycles(H[best], W[best], 2 * P[best]) >= worst) break;
+        if (est_cycles(H[best], W[best], 2 * P[best], f32) >= worst) break;
         used += P[best];
         P[best] *= 2;
     }
 }
 
-bool tc_decode_supported(const DevModel &m) {
-    return m.precision == DLIC_INT8 && m.tc_w != nullptr && m.h1 == kDecHidden && m.h2 == kDecHidden;
+// The cluster wavefront decoder runs the INT8 network of widths 128 on the
+// tensor cores, and FP32 networks whose W3^T fits in 128 KB of shared memory
+// on the CUDA cores; other networks use the one-CTA-per-image decoder.
+bool wave_decode_supported(const DevModel &m) {
+    if (m.precision == DLIC_INT8) return m.tc_w != nullptr && m.h1 == kDecHidden && m.h2 == kDecHidden;
+    return m.precision == DLIC_FP32 && m.h1 >= 4 && m.h1 <= kMaxHidden && m.h2 >= 4 && m.h2 <= 128 && m.h1 % 4 == 0 &&
+           m.h2 % 4 == 0;
 }
 
 // Launches one cluster of `cluster` CTAs per image of the batch (stepping
 // down when a cluster that large cannot be scheduled).
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st) {
+    const bool f32 = m.precision == DLIC_FP32;
+    void (*kern)(DevModel, DecBatch, DecTcParams) = f32 ? k_decode_f32 : k_decode_tc;
     if (b.n == 0) return cudaSuccess;
     int maxH = 1, maxW = 1;
     for (int i = 0; i < b.n; i++) {
@@ -709,7 +941,9 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     const int per_cta = (wave_px + P - 1) / P + 1;
     DecTcParams prm;
     prm.P = P;
-    prm.nt = min(64, (per_cta + 15) & ~15);
+    prm.h1 = m.h1;
+    prm.h2 = m.h2;
+    prm.nt = f32 ? 12 : min(64, (per_cta + 15) & ~15);
     int rows = 1;
     while (rows < min(maxH, (maxW + 2) / 3) + 4) rows <<= 1;
     prm.ring_rows = rows;
@@ -725,15 +959,18 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     }
     prm.tq = tq;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
-    const DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0);
+    const DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+    // the payload of the owned streams is staged in what shared memory is
+    // left (INT8; the FP32 decoder leaves it to the L1 cache, which also
+    // serves W2^T)
     const int budget = 227 * 1024 - 8192;
-    prm.pay_words = L0.total < (uint32_t)budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
+    prm.pay_words = !f32 && L0.total < (uint32_t)budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
-    const DecTcLayout L = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, prm.pay_words);
-    if (L.total > (uint32_t)(227 * 1024)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    const DecTcLayout L = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, prm.pay_words, f32, m.h1, m.h2);
+    if (L.total > (uint32_t)(227 * 1024)) return f32 ? launch_decode_cc(m, b, st) : cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_decode_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kDecThreads);
@@ -750,7 +987,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         attr[0].val.clusterDim.x = (unsigned)P;
         cfg.gridDim = dim3((unsigned)(b.n * P));
         int nclusters = 0;
-        if (P == 1 || (cudaOccupancyMaxActiveClusters(&nclusters, k_decode_tc, &cfg) == cudaSuccess && nclusters > 0))
+        if (P == 1 || (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0))
             break;
         cudaGetLastError();
         P >>= 1;
@@ -760,7 +997,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         // smaller clusters hold more streams and pixels per CTA
         return launch_decode_tc(m, b, P, num_sms, st);
     }
-    return cudaLaunchKernelEx(&cfg, k_decode_tc, m, b, prm);
+    return cudaLaunchKernelEx(&cfg, kern, m, b, prm);
 }
 
 }  // namespace dlic

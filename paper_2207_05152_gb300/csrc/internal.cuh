@@ -93,6 +93,12 @@ cudaError_t launch_rans_encode(const EncBatch &b, int total_streams, cudaStream_
 cudaError_t launch_pack(const DevModel &m, const EncBatch &b, uint8_t *out,
                         uint64_t *out_offsets, cudaStream_t st);
 cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st);
+// Decoders (coder_cc.cu: one CTA per image; decode_tc.cu: one cluster per
+// image, wavefront)
+cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
+cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
+bool wave_decode_supported(const DevModel &m);
+void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
 
 // Rows of stream s (rows s, s + S, ...) and the first entry of its region in
 // stream-ordered per-pixel buffers: every earlier stream holds W pixels per
