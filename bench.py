@@ -300,7 +300,7 @@ def measure_batch(args):
     import torch
     from paper_2207_05152_gb300 import workloads
     from paper_2207_05152_gb300.codec import Codec
-    _, blob8, _ = workloads.models()
+    _, blob8, blob32 = workloads.models()
     imgs = workloads.cfg4_images(64)
     npx = int(sum(i.size for i in imgs))
     codec = Codec(blob8)
@@ -353,6 +353,26 @@ def measure_batch(args):
     except RuntimeError as exc:
         res["graph_roundtrip_mpix_s"] = None
         res["graph_error"] = str(exc)[:200]
+    codec.close()
+    # the plain FP32 network (same widths) on the same batch: CUDA-core
+    # prediction and the FP32 cluster wavefront decoder, one timed pass after
+    # one warm-up pass
+    codec = Codec(blob32)
+    out32, offs32 = codec.encode(dev)
+    torch.cuda.synchronize()
+    o32 = offs32.cpu().tolist()
+    codec.decode(out32, o32, shapes, outs=decs, status=status)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    codec.encode(dev, out=out32, offsets=offs32)
+    e1.record(stream)
+    codec.decode(out32, o32, shapes, outs=decs, status=status)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ok32 = status.cpu().tolist() == [0] * len(imgs) and all(torch.equal(a, b) for a, b in zip(decs, dev))
+    res["fp32_path"] = {"enc_mpix_s": round(npx / (e0.elapsed_time(e1) * 1e-3) / 1e6, 2),
+                        "dec_mpix_s": round(npx / (e1.elapsed_time(e2) * 1e-3) / 1e6, 2),
+                        "bpp": round(8.0 * o32[-1] / npx, 4), "roundtrip_bit_exact": ok32}
     codec.close()
     return res
 

@@ -62,11 +62,13 @@ SHAPES = [(1, 1, 1), (1, 7, 1), (7, 1, 4), (2, 3, 2), (5, 64, 9), (16, 16, 16), 
 
 
 @pytest.mark.parametrize("prec,widths", [("fp32", [12, 32, 48, 256]), ("int8", [12, 32, 48, 256]),
-                                         ("int8", [12, 128, 128, 256])])
+                                         ("int8", [12, 128, 128, 256]), ("fp32", [12, 32, 256, 256])])
 def test_edge_shapes(Codec, orc, prec, widths):
     # INT8 12-128-128-256 runs the tensor-core encoder and the cluster
     # wavefront decoder; the narrower INT8 network the tensor-core encoder and
-    # the CUDA-core decoder; FP32 the CUDA-core kernels.
+    # the one-CTA-per-image decoder; FP32 with h2 <= 128 the CUDA-core encoder
+    # and the FP32 cluster wavefront decoder; FP32 with h2 = 256 the
+    # one-CTA-per-image decoder.
     imgs = [synth.value_noise_image(h, w, 7 * h + w) for h, w, _ in SHAPES]
     blob = _models(widths, 5, [synth.voronoi_image(40, 40, 2)])[prec]
     _check(Codec, orc, blob, imgs, [s for _, _, s in SHAPES])
@@ -126,6 +128,15 @@ def test_batched_decode_mixed_cluster_sizes(Codec, orc):
              (16, 16), (90, 120), (300, 200), (60, 500)]
     imgs = [synth.voronoi_image(h, w, 500 + i) for i, (h, w) in enumerate(sizes)]
     blob = _models([12, 128, 128, 256], 8, imgs[:3])["int8"]
+    _check(Codec, orc, blob, imgs, None)
+
+
+def test_fp32_batched_decode_mixed_cluster_sizes(Codec, orc):
+    # The FP32 cluster decoder over a batch of uneven sizes (cluster sizes
+    # from 1 upwards, several chunks of pixels per wave in the small clusters).
+    sizes = [(24, 40), (70, 90), (130, 250), (18, 200), (160, 60), (40, 320)]
+    imgs = [synth.voronoi_image(h, w, 700 + i) for i, (h, w) in enumerate(sizes)]
+    blob = _models([12, 64, 64, 256], 10, imgs[:2])["fp32"]
     _check(Codec, orc, blob, imgs, None)
 
 
