@@ -12,9 +12,12 @@
 // frequency table after the last layer) reads the accumulators back with
 // tcgen05.ld, one pixel per thread.
 //
-// CTA: two warpgroups, each owning a tile slot of 256 tensor-memory columns
-// and its own A buffers, so one warpgroup's epilogue overlaps the other's
-// MMAs.  Weights stay in shared memory for the whole persistent CTA.
+// CTA: four warpgroups, two per tile slot.  A slot owns 256 tensor-memory
+// columns and its own A buffers, so one slot's epilogue overlaps the other's
+// MMAs; within a slot the two warpgroups read the same accumulator rows
+// (pixels) and split the columns: hidden units for the requantisation,
+// symbols for the frequency table (partial maxima and sums meet in shared
+// memory).  Weights stay in shared memory for the whole persistent CTA.
 #include "coder_device.cuh"
 #include "tc.cuh"
 
@@ -55,8 +58,9 @@ __host__ __device__ inline TcLayout tc_layout(int h1, int h2) {
     return L;
 }
 
-__device__ __forceinline__ void wg_sync(int wg) {
-    asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory");
+constexpr int kTcThreads = 512;
+__device__ __forceinline__ void slot_sync(int slot) {
+    asm volatile("bar.sync %0, 256;" ::"r"(slot + 1) : "memory");
 }
 
 // Requantises 16 accumulator columns to u8 activations and stores them as
@@ -78,12 +82,15 @@ __device__ __forceinline__ void requant_store16(const uint32_t (&v)[16], const f
         make_uint4(packed[4], packed[5], packed[6], packed[7]);
 }
 
-__global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, int *err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatch b, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bars[kTcSlots];
     __shared__ uint32_t tmem_base;
     __shared__ int wg_fail[kTcSlots];
+    __shared__ float s_max[kTcSlots][2][128];
+    __shared__ uint32_t s_w[kTcSlots][3][128];   // the high half's W, P_sym and w_sym
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
+    const int slot = wg & 1, half = wg >> 1;
     const int h1 = m.h1, h2 = m.h2;
     const TcLayout L = tc_layout(h1, h2);
 
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
         for (int j = 0; j < kTcSlots; j++) tc::mbar_init(&bars[j], 1);
         tc::fence_mbar_init();
     }
-    if (t == 0) wg_fail[wg] = 0;
+    if (tid < kTcSlots) wg_fail[tid] = 0;
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -120,9 +127,9 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
     const float *s2 = reinterpret_cast<const float *>(smem + L.s2), *o2 = reinterpret_cast<const float *>(smem + L.o2);
     const float *s3 = reinterpret_cast<const float *>(smem + L.s3), *o3 = reinterpret_cast<const float *>(smem + L.o3);
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
-    uint8_t *a1 = smem + L.a1[wg];
-    uint8_t *a23 = smem + L.a23[wg];
-    const uint32_t tm = tmem_base + 256u * wg;                       // this slot's columns
+    uint8_t *a1 = smem + L.a1[slot];
+    uint8_t *a23 = smem + L.a23[slot];
+    const uint32_t tm = tmem_base + 256u * slot;                     // this slot's columns
     const uint32_t tm_row = tm + ((uint32_t)(32 * (warp & 3)) << 16); // this warp's lane quarter
     const uint32_t sa1 = tc::smem_addr(a1), sa23 = tc::smem_addr(a23);
     const uint32_t sw1 = tc::smem_addr(smem + L.w1), sw2 = tc::smem_addr(smem + L.w2),
@@ -133,23 +140,23 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
     auto layer = [&](uint32_t sa, uint32_t sw, int K, int N) -> bool {
         tc::fence_smem_to_async();
         tc::fence_before_sync();
-        wg_sync(wg);
-        if (t == 0) {
+        slot_sync(slot);
+        if (half == 0 && t == 0) {
             tc::fence_after_sync();
             const uint32_t idesc = tc::idesc_bf16_f32(kTcTile, N);
             for (int ks = 0; ks < K / 16; ks++)
                 tc::mma_bf16(tm, tc::make_desc(sa + 256u * ks, 128u, 16u * K),
                              tc::make_desc(sw + 256u * ks, 128u, 16u * K), idesc, ks > 0);
-            tc::mma_commit(&bars[wg]);
-            if (!tc::mbar_wait(&bars[wg], phase, kTcWaitLimit)) wg_fail[wg] = 1;
+            tc::mma_commit(&bars[slot]);
+            if (!tc::mbar_wait(&bars[slot], phase, kTcWaitLimit)) wg_fail[slot] = 1;
         }
         phase ^= 1u;
-        wg_sync(wg);
+        slot_sync(slot);
         tc::fence_after_sync();
-        return wg_fail[wg] == 0;
+        return wg_fail[slot] == 0;
     };
 
-    for (int tile = blockIdx.x * kTcSlots + wg; tile < b.total_tiles; tile += gridDim.x * kTcSlots) {
+    for (int tile = blockIdx.x * kTcSlots + slot; tile < b.total_tiles; tile += gridDim.x * kTcSlots) {
         int ii = 0;
         while (ii + 1 < b.n && b.img[ii + 1].tile_begin <= tile) ii++;
         const EncImage &im = b.img[ii];
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
         const int r = active ? (int)(p / im.W) : 0, c = active ? (int)(p % im.W) : 0;
 
         // A1: the 12 priors as v - 128, padded to K = 16 with zeros
-        {
+        if (half == 0) {
             uint8_t pri[kPriors];
             if (active) gather_priors(im.pixels, im.pitch, im.H, im.W, r, c, pri);
             uint32_t w[8];
@@ -173,14 +180,18 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
             *reinterpret_cast<uint4 *>(a1 + tc::kmajor_offset(t, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
         if (!layer(sa1, sw1, 16, h1)) break;
-        for (int c0 = 0; c0 < h1; c0 += 16) {
+        // requantisation: each warpgroup of the slot takes half of the
+        // 16-column chunks (the first half the odd one)
+        const int n1 = h1 / 16, f1 = (n1 + 1) / 2;
+        for (int c0 = half ? 16 * f1 : 0; c0 < (half ? h1 : 16 * f1); c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(tm_row + c0, v);
             tc::tmem_wait_ld();
             requant_store16(v, s1, o1, a23, t, c0, h1);
         }
         if (!layer(sa23, sw2, h1, h2)) break;
-        for (int c0 = 0; c0 < h2; c0 += 16) {
+        const int n2 = h2 / 16, f2 = (n2 + 1) / 2;
+        for (int c0 = half ? 16 * f2 : 0; c0 < (half ? h2 : 16 * f2); c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(tm_row + c0, v);
             tc::tmem_wait_ld();
@@ -188,9 +199,11 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
         }
         if (!layer(sa23, sw3, h2, kSymbols)) break;
 
-        // frequency table of the pixel's own value (see coder_device.cuh)
+        // frequency table of the pixel's own value (see coder_device.cuh);
+        // this warpgroup's 128 symbols, then the halves combine
+        const int sb = 128 * half;
         float zmax = -INFINITY;
-        for (int c0 = 0; c0 < kSymbols; c0 += 16) {
+        for (int c0 = sb; c0 < sb + 128; c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(tm_row + c0, v);
             tc::tmem_wait_ld();
@@ -200,9 +213,12 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
                 zmax = z > zmax ? z : zmax;
             }
         }
+        s_max[slot][half][t] = zmax;
+        slot_sync(slot);
+        zmax = fmaxf(zmax, s_max[slot][half ^ 1][t]);
         const int sym = active ? im.pixels[r * im.pitch + c] : 0;
         uint32_t Wsum = 0, Ps = 0, ws = 0;
-        for (int c0 = 0; c0 < kSymbols; c0 += 16) {
+        for (int c0 = sb; c0 < sb + 128; c0 += 16) {
             uint32_t v[16];
             tc::tmem_ld16(tm_row + c0, v);
             tc::tmem_wait_ld();
@@ -216,7 +232,18 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
                 ws = i == sym ? w : ws;
             }
         }
-        if (active) {
+        if (half == 1) {
+            s_w[slot][0][t] = Wsum;
+            s_w[slot][1][t] = Ps;
+            s_w[slot][2][t] = ws;
+        }
+        slot_sync(slot);
+        if (half == 0) {
+            Wsum += s_w[slot][0][t];
+            Ps += s_w[slot][1][t];   // the two halves' parts of sum_{i < sym} w_i
+            ws += s_w[slot][2][t];   // w_sym from whichever half holds sym
+        }
+        if (active && half == 0) {
             const uint32_t Q = table_q(Wsum);
             const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
             const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
@@ -225,7 +252,7 @@ __global__ void __launch_bounds__(256, 1) k_encode_tc(DevModel m, EncBatch b, in
         }
         tc::fence_before_sync();   // tensor-memory reads done before the next tile's MMAs
     }
-    if (t == 0 && wg_fail[wg]) atomicExch(err, DLIC_ERR_TIMEOUT);
+    if (tid < kTcSlots && wg_fail[tid]) atomicExch(err, DLIC_ERR_TIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -268,7 +295,7 @@ cudaError_t launch_predict_tc(const DevModel &m, const EncBatch &b, int *err, in
     const int per_cta = kTcSlots;
     int grid = (b.total_tiles + per_cta - 1) / per_cta;
     if (grid > num_sms) grid = num_sms;
-    k_encode_tc<<<grid, 256, L.total, st>>>(m, b, err);
+    k_encode_tc<<<grid, kTcThreads, L.total, st>>>(m, b, err);
     return cudaGetLastError();
 }
 

@@ -122,15 +122,18 @@ __global__ void k_image_offsets(EncBatch b, uint64_t *out_offsets) {
 
 // Writes header, word counts and payloads; one CTA per image, one warp per
 // stream at a time.
+// Container assembly: blockIdx.y = image; block x = 0 writes the header and
+// the word counts; every block's warps copy whole streams (one warp per
+// stream, strided over the blocks of the image).
 __global__ void k_pack(DevModel m, EncBatch b, uint8_t *out, const uint64_t *out_offsets) {
-    const EncImage &im = b.img[blockIdx.x];
+    const EncImage &im = b.img[blockIdx.y];
     const int S = im.S, tid = threadIdx.x;
-    uint8_t *o = out + out_offsets[blockIdx.x];
+    uint8_t *o = out + out_offsets[blockIdx.y];
     const uint32_t *cnt = reinterpret_cast<const uint32_t *>(b.ws + im.cnt_off);
     const uint32_t *xfin = reinterpret_cast<const uint32_t *>(b.ws + im.xfin_off);
     const uint32_t *soff = reinterpret_cast<const uint32_t *>(b.ws + im.soff_off);
     const uint16_t *words = reinterpret_cast<const uint16_t *>(b.ws + im.words_off);
-    if (tid < kHeaderBytes) {
+    if (blockIdx.x == 0 && tid < kHeaderBytes) {
         uint8_t v;
         if (tid < 4) v = "DLC1"[tid];
         else if (tid < 8) v = (uint8_t)((uint32_t)im.H >> (8 * (tid - 4)));
@@ -141,7 +144,7 @@ __global__ void k_pack(DevModel m, EncBatch b, uint8_t *out, const uint64_t *out
         else v = (uint8_t)(m.hash >> (8 * (tid - 16)));
         o[tid] = v;
     }
-    for (int s = tid; s < S; s += blockDim.x) {
+    for (int s = tid; blockIdx.x == 0 && s < S; s += blockDim.x) {
         const uint32_t c = cnt[s];
         o[kHeaderBytes + 4 * s + 0] = (uint8_t)c;
         o[kHeaderBytes + 4 * s + 1] = (uint8_t)(c >> 8);
@@ -149,8 +152,8 @@ __global__ void k_pack(DevModel m, EncBatch b, uint8_t *out, const uint64_t *out
         o[kHeaderBytes + 4 * s + 3] = (uint8_t)(c >> 24);
     }
     uint16_t *pay = reinterpret_cast<uint16_t *>(o + kHeaderBytes + 4 * S);
-    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    for (int s = warp; s < S; s += nwarp) {
+    const int lane = tid & 31, nwarp = blockDim.x >> 5;
+    for (int s = blockIdx.x * nwarp + (tid >> 5); s < S; s += gridDim.x * nwarp) {
         const uint32_t n = cnt[s] - 2, base = soff[s];
         const uint16_t *src = words + stream_word_base(im.H, im.W, S, s);
         if (lane == 0) {
@@ -172,7 +175,11 @@ cudaError_t launch_pack(const DevModel &m, const EncBatch &b, uint8_t *out, uint
     if (b.n == 0) return cudaSuccess;
     k_stream_offsets<<<b.n, 256, 0, st>>>(b);
     k_image_offsets<<<1, 32, 0, st>>>(b, out_offsets);
-    k_pack<<<b.n, 256, 0, st>>>(m, b, out, out_offsets);
+    int max_s = 1;
+    for (int i = 0; i < b.n; i++) max_s = max_s > b.img[i].S ? max_s : b.img[i].S;
+    // up to 8 streams per block; at most 1024 blocks per image
+    const int nblk = (max_s + 7) / 8 < 1024 ? (max_s + 7) / 8 : 1024;
+    k_pack<<<dim3(nblk, b.n), 256, 0, st>>>(m, b, out, out_offsets);
     return cudaGetLastError();
 }
 
