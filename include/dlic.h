@@ -191,9 +191,13 @@ DLIC_API dlic_status dlic_decode_workspace_size(const dlic_model *model, const d
  * predicted and decoded in parallel.  Each image is decoded by a cluster of
  * 1 to 16 CTAs chosen by a cost model (larger images get larger clusters
  * while the batch fits on the GPU); images with different cluster sizes run
- * concurrently on internal streams forked from and joined back to `stream`.  d_status (n int32, device) receives
- * DLIC_OK or DLIC_ERR_CORRUPT per image (header mismatch, model hash
- * mismatch, stream overrun, or a final state other than the initial one). */
+ * concurrently on internal streams forked from and joined back to `stream`.
+ * INT8 networks of widths 128 run on the tensor cores, FP32 networks with
+ * h2 <= 128 on the CUDA cores, other networks in one CTA per image.
+ * d_status (n int32, device) receives DLIC_OK or DLIC_ERR_CORRUPT per image
+ * (header mismatch, model hash mismatch, stream overrun, or a final state
+ * other than the initial one), or DLIC_ERR_TIMEOUT when a bounded wait of
+ * the decoder ran out. */
 DLIC_API dlic_status dlic_decode(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,
                         int n, const dlic_image *h_images, int32_t *d_status, void *d_workspace,
                         size_t workspace_bytes, void *stream);
@@ -212,11 +216,12 @@ DLIC_API size_t dlic_train_param_count(int h1, int h2);
 /* Creates a trainer: FP32 master weights (copied from h_params, host),
  * Adam moments (lr 1e-3, betas 0.9 / 0.999, eps 1e-8, bias-corrected) and
  * device buffers for batches of up to max_batch contexts.  mode
- * DLIC_TRAIN_BF16 runs every product on the tensor cores with bf16 operands
- * and FP32 accumulation; DLIC_TRAIN_BF16X3 stores every operand as two bf16
- * planes (x = hi + lo) and accumulates hi*hi + lo*hi + hi*lo on the tensor
- * cores (about 16 significant bits per operand, three times the MMAs);
- * DLIC_TRAIN_FP32 runs them in FP32 on the CUDA cores.
+ * DLIC_TRAIN_BF16 runs the two wide layers and every backward product on
+ * the tensor cores with bf16 operands and FP32 accumulation (the 12-input
+ * first layer in FP32 on the CUDA cores); DLIC_TRAIN_BF16X3 stores every
+ * tensor-core operand as two bf16 planes (x = hi + lo) and accumulates
+ * hi*hi + lo*hi + hi*lo (about 16 significant bits per operand, three times
+ * the MMAs); DLIC_TRAIN_FP32 runs every product in FP32 on the CUDA cores.
  * Allocates its device memory here and frees it in dlic_trainer_destroy. */
 DLIC_API dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_batch, const float *h_params,
                                          dlic_trainer **out);
@@ -229,7 +234,8 @@ DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const uint8_t *d_
                                         float *d_loss_bits, void *stream);
 
 /* Loss and its gradient with respect to every parameter (the adjoint of the
- * forward pass, activations recomputed from the batch); d_grads (device,
+ * forward pass).  The activations are recomputed from the batch: nothing
+ * is kept from an earlier dlic_train_forward.  d_grads (device,
  * dlic_train_param_count floats, may be NULL) receives the gradient in the
  * parameter layout. */
 DLIC_API dlic_status dlic_train_backward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
