@@ -78,6 +78,19 @@ def test_bf16_gradient_against_fp64(T, mode, tol):
         assert ew < tol and eb < tol
 
 
+@pytest.mark.parametrize("mode,tol", [("bf16", 3e-2), ("bf16x3", 1e-3)])
+def test_bf16_odd_widths_and_batch(T, mode, tol):
+    # widths that are not multiples of 64 (partial MN-major boxes, an odd
+    # number of 16-column chunks) and a batch that is not a multiple of 128
+    # (a ragged last tile, a split-K tail)
+    layers, ctx, tgt = _data(T, 1000, 17, widths=(12, 48, 80, 256))
+    loss, g = _grads(T, mode, layers, ctx, tgt)
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    assert abs(loss - loss64) <= 1e-3 * loss64
+    for (gw, gb), (rw, rb) in zip(g, ref):
+        assert _rel(gw, rw) < tol and _rel(gb, rb) < tol
+
+
 def test_gradient_matches_finite_differences(T):
     # The FP32 GPU gradient against central differences of the FP64 loss,
     # to within 1e-3 of the tensor's largest gradient entry.
