@@ -450,6 +450,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     }
     uint8_t *ring = smem + L.ring;
     const uint32_t ring_addr = tc::smem_addr(ring);
+    // the ring bases of the CTAs this lane stores to (the cluster window is
+    // linear within a CTA, so the mapping is computed once)
+    const uint32_t tring_dst = (P > 1 && lane < 3) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
+    const uint32_t ring_dst = (P > 1 && lane < P) ? map_shared(ring_addr, (k + (uint32_t)lane) % (uint32_t)P) : ring_addr;
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     uint8_t *pri = smem + L.pri;   // priors of the chunk's pixels as s8 (x - 128), 16 bytes each
     uint8_t *b23 = smem + L.b23;
@@ -784,16 +788,17 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 if (p2p) {
                     if (lane < min(3, P)) {
                         const int slot = (((r >> lgP) & tqmask) << 2) | lane;
-                        const uint32_t a = tring_addr + 4u * (uint32_t)(slot * 32 + (c & 31));
+                        const uint32_t off = 4u * (uint32_t)(slot * 32 + (c & 31));
                         if (lane == 0)
-                            asm volatile("st.shared::cta.u32 [%0], %1;" ::"r"(a), "r"(ring_tag(r, c) | sym) : "memory");
+                            asm volatile("st.shared::cta.u32 [%0], %1;" ::"r"(tring_addr + off), "r"(ring_tag(r, c) | sym)
+                                         : "memory");
                         else
-                            st_cluster_u32(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), ring_tag(r, c) | sym);
+                            st_cluster_u32(tring_dst + off, ring_tag(r, c) | sym);
                     }
                 } else if (lane < P) {
-                    const uint32_t a = ring_addr + (uint32_t)(((r & rmask) << 4) + (c & 15));
+                    const uint32_t off = (uint32_t)(((r & rmask) << 4) + (c & 15));
                     if (P > 1)
-                        st_cluster_u8(map_shared(a, (k + (uint32_t)lane) % (uint32_t)P), sym);
+                        st_cluster_u8(ring_dst + off, sym);
                     else
                         ring[((r & rmask) << 4) + (c & 15)] = (uint8_t)sym;
                 }
