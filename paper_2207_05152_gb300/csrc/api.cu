@@ -421,12 +421,20 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         cudaError_t e = cudaEventRecord(m->fork_event, cs);
         if (e != cudaSuccess) return cuda_fail(e, "fork event");
     }
-    for (int gi = 0; gi < kDecodeGroups; gi++) {
+    // the largest clusters (the longest images) are launched first, and within
+    // a group the longest images first, so that CTAs beyond one per SM queue
+    // behind them
+    const bool f32 = m->dev.precision == DLIC_FP32;
+    for (int gi = kDecodeGroups - 1; gi >= 0; gi--) {
         const int cluster = 1 << gi;
         std::vector<int> members;
         for (int i = 0; i < n; i++)
             if (P[i] == cluster) members.push_back(i);
         if (members.empty()) continue;
+        if (use_wave)
+            std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
+                return decode_estimate(Hs[a], Ws[a], cluster, f32) > decode_estimate(Hs[b], Ws[b], cluster, f32);
+            });
         cudaStream_t gs = fork ? m->group_stream[gi] : cs;
         if (fork) {
             cudaError_t e = cudaStreamWaitEvent(gs, m->fork_event, 0);

@@ -871,13 +871,14 @@ __global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBa
 }
 
 // Cluster sizes for a batch (the decode autotuner).  A wave of an image
-// whose CTAs hold p pixels costs about kWaveFixed cycles (gather, three MMA
-// round trips, epilogues) plus kWavePerPixelWarp per pixel and table warp
-// (16 warps), over chunks of at most 64 pixels; an image takes waves x that.
-// Starting from one CTA per image, the image with the longest estimate gets
-// its cluster doubled while the clusters of the whole batch still fit on the
-// GPU at once (up to 16 CTAs).
-constexpr double kWaveFixed = 4500.0, kWavePerPixelWarp = 1700.0;
+// whose CTAs hold p pixels costs about kWaveFixed cycles (gather, MMA round
+// trips, epilogues) plus kWavePerPixelWarp per round of 16 table warps and
+// kWavePerPixel per pixel, over chunks of at most 64 pixels (constants from
+// clock64 phase timings on GB300); an image takes waves x that.  Starting
+// from one CTA per image, the image with the longest estimate gets its
+// cluster doubled while the clusters of the whole batch still fit on the
+// GPU at once (up to 16 CTAs per image).
+constexpr double kWaveFixed = 4200.0, kWavePerPixelWarp = 1900.0, kWavePerPixel = 65.0;
 // FP32 network: the CUDA cores' multiply-adds (about 50K per pixel at
 // 128 a cycle) add to the table rounds, in chunks of 16 pixels.
 constexpr double kWaveFixedF32 = 5000.0, kWavePerPixelF32 = 420.0;
@@ -890,11 +891,13 @@ static double est_cycles(int H, int W, int P, bool f32) {
     while (per > 0) {
         const int chunk = min(per, f32 ? 16 : 64);
         per_wave += f32 ? kWaveFixedF32 + kWavePerPixelF32 * ((chunk + 3) & ~3) + kWavePerPixelWarp
-                        : kWaveFixed + kWavePerPixelWarp * ((chunk + kDecWarps - 1) / kDecWarps);
+                        : kWaveFixed + kWavePerPixelWarp * ((chunk + kDecWarps - 1) / kDecWarps) + kWavePerPixel * chunk;
         per -= chunk;
     }
     return waves * per_wave;
 }
+
+double decode_estimate(int H, int W, int P, bool f32) { return est_cycles(H, W, P, f32); }
 
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P) {
     int used = 0;

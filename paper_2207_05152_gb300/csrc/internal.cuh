@@ -99,6 +99,7 @@ cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t 
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
+double decode_estimate(int H, int W, int P, bool f32);   // cycles, the autotuner's cost model
 
 // Rows of stream s (rows s, s + S, ...) and the first entry of its region in
 // stream-ordered per-pixel buffers: every earlier stream holds W pixels per
