@@ -98,6 +98,178 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
 }
 
 // ---------------------------------------------------------------------------
+// Encoder prediction with the FP32 network, 64 pixels per CTA: the layers
+// as register tiles on the CUDA cores (each unit of each pixel still starts
+// from its bias and accumulates fma(x_k, w_jk, acc) for k ascending, so the
+// result is the same as one pixel per thread), weights read as 16-byte rows
+// through L1/L2, activations in shared memory [unit][pitch kF32Pitch]; then
+// one warp per pixel for the frequency table of the pixel's own value.
+// ---------------------------------------------------------------------------
+constexpr int kF32Tile = 64, kF32Pitch = kF32Tile + 4, kF32Threads = 256;
+
+__host__ __device__ inline size_t f32_predict_smem(int h1, int h2) {
+    const size_t xs = (size_t)kF32Tile * 16 * 4, h1t = (size_t)h1 * kF32Pitch * 4, z = (size_t)kF32Tile * kSymbols * 4;
+    const size_t region = xs + h1t > z ? xs + h1t : z;   // z overlays xs and h1t
+    return region + (size_t)h2 * kF32Pitch * 4;
+}
+
+// acc[i][j] (units 4 uq + i, pixels p0 + j) over k rows of w (row stride ldw)
+// and the activation rows act[k][p0 ..] (pitch kF32Pitch).
+template <int J>
+__device__ __forceinline__ void f32_tile(float (&acc)[4][J], const float *w, int ldw, const float *act, int K, int uq,
+                                         int p0) {
+#pragma unroll 2
+    for (int k = 0; k < K; k++) {
+        const float4 wv = __ldg(reinterpret_cast<const float4 *>(w + (size_t)k * ldw) + uq);
+        const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int j4 = 0; j4 < J / 4; j4++) {
+            const float4 xv = *reinterpret_cast<const float4 *>(act + k * kF32Pitch + p0 + 4 * j4);
+            const float xk[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int jj = 0; jj < 4; jj++) acc[i][4 * j4 + jj] = __fmaf_rn(xk[jj], wk[i], acc[i][4 * j4 + jj]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t f32_key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncBatch b) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t lut_s[64];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int h1 = m.h1, h2 = m.h2;
+    if (tid < 64) lut_s[tid] = m.lut[tid];
+    float *xs = reinterpret_cast<float *>(smem);                         // [64][16]
+    float *h1t = xs + kF32Tile * 16;                                      // [h1][pitch]
+    float *zs = reinterpret_cast<float *>(smem);                         // [64][256], after layer 2
+    const size_t region = f32_predict_smem(h1, h2) - (size_t)h2 * kF32Pitch * 4;
+    float *h2t = reinterpret_cast<float *>(smem + region);                // [h2][pitch]
+
+    const int tile = blockIdx.x;
+    int ii = 0;
+    while (ii + 1 < b.n && b.img[ii + 1].tile_begin <= tile) ii++;
+    const EncImage &im = b.img[ii];
+    const int64_t p_base = (int64_t)(tile - im.tile_begin) * kF32Tile;
+    const int64_t npx = (int64_t)im.H * im.W;
+    // inputs x/128 - 1 of the 64 pixels (pixels past the image get zeros)
+    for (int i = tid; i < kF32Tile * kPriors; i += kF32Threads) {
+        const int p = i / kPriors, q = i % kPriors;
+        const int64_t pp = p_base + p;
+        float v = 0.0f;
+        if (pp < npx) {
+            const int r = (int)(pp / im.W), c = (int)(pp % im.W);
+            const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
+            const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+            const int rr = r + dr, cc = c + dc;
+            const uint32_t pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[rr * im.pitch + cc] : 0u;
+            v = __fmaf_rn((float)pv, 0.0078125f, -1.0f);
+        }
+        xs[p * 16 + q] = v;
+    }
+    __syncthreads();
+    // layer 1: thread = (unit, 4 pixels)
+    for (int it = tid; it < h1 * (kF32Tile / 4); it += kF32Threads) {
+        const int u = it % h1, p0 = 4 * (it / h1);
+        float a[4];
+        const float bias = __ldg(m.b1 + u);
+#pragma unroll
+        for (int j = 0; j < 4; j++) a[j] = bias;
+#pragma unroll
+        for (int k = 0; k < kPriors; k++) {
+            const float w = __ldg(m.w1t + k * h1 + u);
+#pragma unroll
+            for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[(p0 + j) * 16 + k], w, a[j]);
+        }
+        *reinterpret_cast<float4 *>(h1t + u * kF32Pitch + p0) =
+            make_float4(a[0] > 0.0f ? a[0] : 0.0f, a[1] > 0.0f ? a[1] : 0.0f, a[2] > 0.0f ? a[2] : 0.0f,
+                        a[3] > 0.0f ? a[3] : 0.0f);
+    }
+    __syncthreads();
+    // layer 2: thread = (4 units, 8 pixels)
+    for (int it = tid; it < (h2 / 4) * (kF32Tile / 8); it += kF32Threads) {
+        const int uq = it % (h2 / 4), p0 = 8 * (it / (h2 / 4));
+        float acc[4][8];
+        const float4 bb = __ldg(reinterpret_cast<const float4 *>(m.b2) + uq);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            acc[0][j] = bb.x; acc[1][j] = bb.y; acc[2][j] = bb.z; acc[3][j] = bb.w;
+        }
+        f32_tile<8>(acc, m.w2t, h2, h1t, h1, uq, p0);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j4 = 0; j4 < 2; j4++)
+                *reinterpret_cast<float4 *>(h2t + (4 * uq + i) * kF32Pitch + p0 + 4 * j4) = make_float4(
+                    acc[i][4 * j4] > 0.0f ? acc[i][4 * j4] : 0.0f, acc[i][4 * j4 + 1] > 0.0f ? acc[i][4 * j4 + 1] : 0.0f,
+                    acc[i][4 * j4 + 2] > 0.0f ? acc[i][4 * j4 + 2] : 0.0f,
+                    acc[i][4 * j4 + 3] > 0.0f ? acc[i][4 * j4 + 3] : 0.0f);
+    }
+    __syncthreads();
+    // logits: thread = (4 units, 8 pixels); z [pixel][256] overlays xs and h1t
+    for (int it = tid; it < (kSymbols / 4) * (kF32Tile / 8); it += kF32Threads) {
+        const int uq = it % (kSymbols / 4), p0 = 8 * (it / (kSymbols / 4));
+        float acc[4][8];
+        const float4 bb = __ldg(reinterpret_cast<const float4 *>(m.b3) + uq);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            acc[0][j] = bb.x; acc[1][j] = bb.y; acc[2][j] = bb.z; acc[3][j] = bb.w;
+        }
+        f32_tile<8>(acc, m.w3t, kSymbols, h2t, h2, uq, p0);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            *reinterpret_cast<float4 *>(zs + (p0 + j) * kSymbols + 4 * uq) =
+                make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+    }
+    __syncthreads();
+    // frequency table of each pixel's own value, one warp per pixel
+    uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
+    for (int p = warp; p < kF32Tile; p += kF32Threads / 32) {
+        const int64_t pp = p_base + p;
+        if (pp >= npx) break;
+        const int r = (int)(pp / im.W), c = (int)(pp % im.W);
+        const int sym = im.pixels[r * im.pitch + c];
+        float z[8];
+        const float4 za = *reinterpret_cast<const float4 *>(zs + p * kSymbols + 8 * lane);
+        const float4 zc = *reinterpret_cast<const float4 *>(zs + p * kSymbols + 8 * lane + 4);
+        z[0] = za.x; z[1] = za.y; z[2] = za.z; z[3] = za.w; z[4] = zc.x; z[5] = zc.y; z[6] = zc.z; z[7] = zc.w;
+        uint32_t key = f32_key(z[0]);
+#pragma unroll
+        for (int q = 1; q < 8; q++) key = max(key, f32_key(z[q]));
+        const uint32_t km = __reduce_max_sync(0xffffffffu, key);
+        const float mx = __uint_as_float((km & 0x80000000u) ? (km & 0x7FFFFFFFu) : ~km);
+        uint32_t lw = 0, lp = 0, lsym = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int i = 8 * lane + q;
+            const uint32_t w = table_weight(mx, z[q], m.tscale, lut_s);
+            lw += w;
+            lp += i < sym ? w : 0u;
+            lsym = i == sym ? w : lsym;
+        }
+        const uint32_t W = __reduce_add_sync(0xffffffffu, lw);
+        const uint32_t Ps = __reduce_add_sync(0xffffffffu, lp);
+        const uint32_t ws = __reduce_add_sync(0xffffffffu, lsym);
+        if (lane == 0) {
+            const uint32_t Q = table_q(W);
+            const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
+            const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
+            fc[stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
+        }
+    }
+}
+
+bool f32_predict_supported(const DevModel &m) {
+    return m.precision == DLIC_FP32 && m.h1 % 4 == 0 && m.h2 % 4 == 0 && m.h1 <= kMaxHidden && m.h2 <= kMaxHidden &&
+           f32_predict_smem(m.h1, m.h2) <= 227 * 1024;
+}
+
+// ---------------------------------------------------------------------------
 // Wavefront decoder (Sec. II-B "Preprocessor"): one CTA per image.  Wave t
 // holds the pixels (r, t - 3r); all their priors were decoded on earlier
 // waves.  Pixels of a wave are predicted in parallel; the rANS step of
@@ -295,7 +467,12 @@ static size_t decode_smem(const DevModel &m) {
 
 cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
-    if (m.precision == DLIC_FP32) {
+    if (m.precision == DLIC_FP32 && f32_predict_supported(m)) {
+        // 64-pixel tiles, as the encoder plans them for the CUDA-core path
+        const size_t sm = f32_predict_smem(m.h1, m.h2);
+        cudaFuncSetAttribute(k_predict_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_predict_f32<<<b.total_tiles, kF32Threads, sm, st>>>(m, b);
+    } else if (m.precision == DLIC_FP32) {
         const size_t sm = predict_smem<DLIC_FP32>(m);
         cudaFuncSetAttribute(k_predict_cc<DLIC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_predict_cc<DLIC_FP32><<<b.total_tiles, kCH, sm, st>>>(m, b);
