@@ -141,10 +141,10 @@ __device__ __forceinline__ uint32_t f32_key(float f) {
 
 __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncBatch b) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ uint32_t lut_s[64];
+    __shared__ uint32_t lut_s[kTableSteps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int h1 = m.h1, h2 = m.h2;
-    if (tid < 64) lut_s[tid] = m.lut[tid];
+    expand_lut(m.lut, lut_s, tid, kF32Threads);
     float *xs = reinterpret_cast<float *>(smem);                         // [64][16]
     float *h1t = xs + kF32Tile * 16;                                      // [h1][pitch]
     float *zs = reinterpret_cast<float *>(smem);                         // [64][256], after layer 2
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const int i = 8 * lane + q;
-            const uint32_t w = table_weight(mx, z[q], m.tscale, lut_s);
+            const uint32_t w = table_weight2(mx, z[q], m.tscale, lut_s);
             lw += w;
             lp += i < sym ? w : 0u;
             lsym = i == sym ? w : lsym;

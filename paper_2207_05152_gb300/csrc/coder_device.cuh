@@ -182,6 +182,18 @@ __device__ __forceinline__ uint32_t table_weight(float m, float z, float tscale,
     return lut_s[u & 63] >> (u >> 6);
 }
 
+// The same weight from the expanded table lut2[u] = lut[u mod 64] >> (u div 64)
+// (kTableSteps entries, built once per CTA by expand_lut).
+constexpr int kTableSteps = 1536;
+__device__ __forceinline__ uint32_t table_weight2(float m, float z, float tscale, const uint32_t *lut2_s) {
+    float y = __fmul_rn(__fsub_rn(m, z), tscale);
+    y = y <= 1535.0f ? y : 1535.0f;
+    return lut2_s[__float2int_rn(y)];
+}
+__device__ __forceinline__ void expand_lut(const uint32_t *lut_g, uint32_t *lut2_s, int tid, int nthreads) {
+    for (int u = tid; u < kTableSteps; u += nthreads) lut2_s[u] = __ldg(lut_g + (u & 63)) >> (u >> 6);
+}
+
 __device__ __forceinline__ uint32_t table_q(uint32_t W) {
     return (uint32_t)((65280ull << 32) / (unsigned long long)W);
 }

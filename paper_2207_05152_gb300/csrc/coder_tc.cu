@@ -53,7 +53,7 @@ __host__ __device__ inline TcLayout tc_layout(int h1, int h2) {
     L.o2 = take(4u * h2);
     L.s3 = take(4u * kSymbols);
     L.o3 = take(4u * kSymbols);
-    L.lut = take(4u * 64);
+    L.lut = take(4u * kTableSteps);
     L.total = off;
     return L;
 }
@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
         for (int i = tid; i < h1; i += blockDim.x) { s1[i] = m.s1[i]; o1[i] = m.o1[i]; }
         for (int i = tid; i < h2; i += blockDim.x) { s2[i] = m.s2[i]; o2[i] = m.o2[i]; }
         for (int i = tid; i < kSymbols; i += blockDim.x) { s3[i] = m.s3[i]; o3[i] = m.o3[i]; }
-        uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
-        if (tid < 64) lut[tid] = m.lut[tid];
+        expand_lut(m.lut, reinterpret_cast<uint32_t *>(smem + L.lut), tid, blockDim.x);
     }
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, 256 * kTcSlots);
@@ -226,12 +225,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
             for (int q = 0; q < 16; q++) {
                 const int i = c0 + q;
                 const float z = __fmaf_rn(__uint_as_float(v[q]), s3[i], o3[i]);
-                const uint32_t w = table_weight(zmax, z, m.tscale, lut);
+                const uint32_t w = table_weight2(zmax, z, m.tscale, lut);
+                // at the pixel's own value: the running total so far and its weight
+                const bool at = i == sym;
+                Ps = at ? Wsum : Ps;
+                ws = at ? w : ws;
                 Wsum += w;
-                Ps += i < sym ? w : 0u;
-                ws = i == sym ? w : ws;
             }
         }
+        // this half's part of sum_{i < sym} w_i: all of it when sym lies above the half
+        if (sym >= sb + 128) Ps = Wsum;
         if (half == 1) {
             s_w[slot][0][t] = Wsum;
             s_w[slot][1][t] = Ps;

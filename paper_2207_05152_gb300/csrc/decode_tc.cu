@@ -76,7 +76,7 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
         L.z = base;
         L.h2t = take(4u * h2 * (nt + 4));
     } else {
-        L.w1 = take(32u * kDecHidden);
+        L.w1 = 0;   // the first layer runs as dp4a: its bf16 tile is not copied
         L.w2 = take(2u * kDecHidden * kDecHidden);
         L.w3 = take(512u * kDecHidden);
         L.pri = take(16u * nt);
@@ -285,9 +285,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
                 reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
         } else {
-            const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w);
-            uint4 *dst = reinterpret_cast<uint4 *>(smem + L.w1);
-            const int n16 = (int)(m.tc_w_bytes / 16);
+            // W2 | W3 of the weight image (after the 32 x 128-byte W1 tile)
+            const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w) + 32 * kDecHidden / 16;
+            uint4 *dst = reinterpret_cast<uint4 *>(smem + L.w2);
+            const int n16 = (int)(m.tc_w_bytes / 16) - 32 * kDecHidden / 16;
             for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
         }
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
@@ -967,16 +968,28 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     }
     prm.tq = tq;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
-    const DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+    // dynamic shared memory available next to the kernel's static arrays
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const uint32_t limit = (uint32_t)optin > fa.sharedSizeBytes ? (uint32_t)optin - (uint32_t)fa.sharedSizeBytes : 0u;
+    // smaller pixel chunks when the rings of a wide image leave no room
+    DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+    while (!f32 && L0.total > limit && prm.nt > 16) {
+        prm.nt /= 2;
+        L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+    }
     // the payload of the owned streams is staged in what shared memory is
-    // left (INT8; the FP32 decoder leaves it to the L1 cache, which also
-    // serves W2^T)
-    const int budget = 227 * 1024 - 8192;
-    prm.pay_words = !f32 && L0.total < (uint32_t)budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
+    // left (INT8; the FP32 decoder leaves it to the L1 cache)
+    const uint32_t budget = limit > 4096u ? limit - 4096u : 0u;
+    prm.pay_words = !f32 && L0.total < budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
     const DecTcLayout L = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, prm.pay_words, f32, m.h1, m.h2);
-    if (L.total > (uint32_t)(227 * 1024)) return f32 ? launch_decode_cc(m, b, st) : cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (L.total > limit) return f32 ? launch_decode_cc(m, b, st) : cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;

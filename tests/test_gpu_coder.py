@@ -131,6 +131,15 @@ def test_batched_decode_mixed_cluster_sizes(Codec, orc):
     _check(Codec, orc, blob, imgs, None)
 
 
+def test_wide_images_small_clusters(Codec, orc):
+    # wide images among many small ones get small clusters: hundreds of
+    # pixels per CTA and wave, large rings, smaller pixel chunks
+    sizes = [(40, 2048), (300, 1600)] + [(24, 32)] * 40
+    imgs = [synth.voronoi_image(h, w, 900 + i) for i, (h, w) in enumerate(sizes)]
+    blob = _models([12, 128, 128, 256], 11, imgs[:1])["int8"]
+    _check(Codec, orc, blob, imgs, None)
+
+
 def test_fp32_batched_decode_mixed_cluster_sizes(Codec, orc):
     # The FP32 cluster decoder over a batch of uneven sizes (cluster sizes
     # from 1 upwards, several chunks of pixels per wave in the small clusters).
