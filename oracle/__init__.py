@@ -6,9 +6,9 @@ ctypes) and an FP64 reference of the training loss and its gradient
 leg use this package; the CUDA library never imports or links it.
 """
 from .coder import (build, lib, encode, decode, symbol_tables, pixel_table, logits,
-                    table_from_logits, gather, rans_enc_step, rans_dec_step, fnv1a64,
+                    table_from_logits, gather, gather_window, rans_enc_step, rans_dec_step, fnv1a64,
                     max_encoded_bytes)
 
 __all__ = ["build", "lib", "encode", "decode", "symbol_tables", "pixel_table", "logits",
-           "table_from_logits", "gather", "rans_enc_step", "rans_dec_step", "fnv1a64",
+           "table_from_logits", "gather", "gather_window", "rans_enc_step", "rans_dec_step", "fnv1a64",
            "max_encoded_bytes"]

@@ -43,6 +43,8 @@ def lib():
             L.or_fnv1a64.argtypes = [U8P, C.c_size_t]
             L.or_gather.restype = None
             L.or_gather.argtypes = [U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
+            L.or_gather_window.restype = C.c_int
+            L.or_gather_window.argtypes = [C.c_int, C.c_int, C.c_int, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
             L.or_table_from_logits.restype = C.c_int
             L.or_table_from_logits.argtypes = [F32P, C.c_float, U32P, U32P]
             L.or_rans_enc_step.restype = C.c_int
@@ -90,6 +92,16 @@ def gather(img: np.ndarray, r: int, c: int) -> np.ndarray:
     img = np.ascontiguousarray(img, dtype=np.uint8)
     out = np.zeros(12, np.uint8)
     lib().or_gather(_p(img, U8P), img.shape[0], img.shape[1], r, c, _p(out, U8P))
+    return out
+
+
+def gather_window(window, img: np.ndarray, r: int, c: int) -> np.ndarray:
+    """Priors of pixel (r, c) for the causal window (u, l, r_reach)."""
+    u, l, rr = window
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    out = np.zeros(u * (l + rr + 1) + l, np.uint8)
+    n = lib().or_gather_window(u, l, rr, _p(img, U8P), img.shape[0], img.shape[1], r, c, _p(out, U8P))
+    assert n == out.size
     return out
 
 
@@ -141,8 +153,10 @@ def pixel_table(blob: bytes, img: np.ndarray, r: int, c: int):
 
 
 def logits(blob: bytes, pri: np.ndarray) -> np.ndarray:
+    """Logits [n, 256] for prior vectors [n, window size] (u8)."""
     b = _bytes(blob)
-    pri = np.ascontiguousarray(pri, dtype=np.uint8).reshape(-1, 12)
+    n_in = int(np.frombuffer(b[8:12].tobytes(), "<u4")[0])
+    pri = np.ascontiguousarray(pri, dtype=np.uint8).reshape(-1, n_in)
     z = np.zeros((pri.shape[0], 256), np.float32)
     st = lib().or_logits(_p(b, U8P), b.size, _p(pri, U8P), pri.shape[0], _p(z, F32P))
     if st:

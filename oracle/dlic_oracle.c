@@ -32,7 +32,8 @@
 #define OR_ERR_CAPACITY 2
 #define OR_ERR_CORRUPT 3
 
-#define NPRI 12
+#define NPRI 12           /* priors of the default radius-2 window */
+#define MAXPRI 96         /* largest window the coder takes */
 #define NSYM 256
 #define TOTAL_M 65536u      /* frequency table total, 2^16 */
 #define RANS_L 65536u       /* rANS lower bound, 2^16 */
@@ -41,8 +42,13 @@
 /* Model blob (little-endian; layout fixed in the model format)        */
 /* ------------------------------------------------------------------ */
 
+/* Causal window: rows r-u .. r-1 at columns c-l .. c+r, then row r at
+ * columns c-l .. c-1 (n = u (l + r + 1) + l priors, in that order). */
+typedef struct { int u, l, r, n; } window_t;
+
 typedef struct {
     int precision;               /* 0 = FP32, 1 = INT8 */
+    window_t win;
     int h1, h2;
     float tscale;
     uint32_t lut[64];
@@ -87,7 +93,20 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     uint32_t n_in = rd_u32(blob + 8), h1 = rd_u32(blob + 12), h2 = rd_u32(blob + 16);
     uint32_t n_out = rd_u32(blob + 20), radius = rd_u32(blob + 24);
     if (m->precision != 0 && m->precision != 1) return OR_ERR_INVALID;
-    if (n_in != NPRI || n_out != NSYM || radius != 2) return OR_ERR_INVALID;
+    /* window field: 2 = the default radius-2 window; otherwise
+     * 1 << 24 | u | l << 8 | r << 16 with 1 <= u <= 8, l <= 8 and r <= 2
+     * (a right reach of at most 2 keeps every prior on an earlier wave of
+     * t = 3 row + column) */
+    if (radius == 2) {
+        m->win.u = 2; m->win.l = 2; m->win.r = 2;
+    } else if ((radius >> 24) == 1) {
+        m->win.u = (int)(radius & 0xFF); m->win.l = (int)((radius >> 8) & 0xFF); m->win.r = (int)((radius >> 16) & 0xFF);
+        if (m->win.u < 1 || m->win.u > 8 || m->win.l > 8 || m->win.r > 2) return OR_ERR_INVALID;
+    } else {
+        return OR_ERR_INVALID;
+    }
+    m->win.n = m->win.u * (m->win.l + m->win.r + 1) + m->win.l;
+    if (m->win.n > MAXPRI || (int)n_in != m->win.n || n_out != NSYM) return OR_ERR_INVALID;
     if (h1 < 1 || h1 > 4096 || h2 < 1 || h2 > 4096) return OR_ERR_INVALID;
     m->h1 = (int)h1; m->h2 = (int)h2;
     m->tscale = rd_f32(blob + 28);
@@ -97,7 +116,7 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
         if (m->lut[k] > (1u << 23)) return OR_ERR_INVALID;
     }
     if (m->lut[0] != (1u << 23)) return OR_ERR_INVALID;
-    int dims_in[3] = {NPRI, (int)h1, (int)h2}, dims_out[3] = {(int)h1, (int)h2, NSYM};
+    int dims_in[3] = {m->win.n, (int)h1, (int)h2}, dims_out[3] = {(int)h1, (int)h2, NSYM};
     size_t need = 288;
     for (int l = 0; l < 3; l++) {
         size_t wn = (size_t)dims_in[l] * dims_out[l];
@@ -131,19 +150,40 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
 
 /* ------------------------------------------------------------------ */
 /* Causal prior gather (Sec. II-A, Fig. 1 left; dummy value per Fig. 1 */
-/* right).  Reading: radius-2 window, priors in the order               */
-/*   row r-2: c-2..c+2, row r-1: c-2..c+2, row r: c-2, c-1;            */
-/* pixels outside the image read as 0.                                  */
+/* right; "any window shape", Sec. II-A, e.g. the 9x9 window of Fig. 6 */
+/* with the target in the last row, third column from the right).       */
+/* Reading: rows r-u..r-1 at columns c-l..c+r, then row r at columns    */
+/* c-l..c-1, row by row, left to right; pixels outside the image read   */
+/* as 0.  The default window (u, l, r) = (2, 2, 2) gives the 12 priors  */
+/*   row r-2: c-2..c+2, row r-1: c-2..c+2, row r: c-2, c-1.            */
 /* ------------------------------------------------------------------ */
 
-static const int PRI_DR[NPRI] = {-2, -2, -2, -2, -2, -1, -1, -1, -1, -1, 0, 0};
-static const int PRI_DC[NPRI] = {-2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -2, -1};
-
-void or_gather(const uint8_t *img, int H, int W, int r, int c, uint8_t pri[NPRI]) {
-    for (int k = 0; k < NPRI; k++) {
-        int rr = r + PRI_DR[k], cc = c + PRI_DC[k];
+static void gather_win(const window_t *w, const uint8_t *img, int H, int W, int r, int c, uint8_t *pri) {
+    const int wid = w->l + w->r + 1;
+    for (int k = 0; k < w->n; k++) {
+        int dr, dc;
+        if (k < w->u * wid) {
+            dr = -w->u + k / wid;
+            dc = -w->l + k % wid;
+        } else {
+            dr = 0;
+            dc = -w->l + (k - w->u * wid);
+        }
+        int rr = r + dr, cc = c + dc;
         pri[k] = (rr >= 0 && rr < H && cc >= 0 && cc < W) ? img[(size_t)rr * W + cc] : 0;
     }
+}
+
+void or_gather(const uint8_t *img, int H, int W, int r, int c, uint8_t pri[NPRI]) {
+    const window_t w = {2, 2, 2, NPRI};
+    gather_win(&w, img, H, W, r, c, pri);
+}
+
+/* The priors of window (u, l, r) at pixel (r0, c0); returns their count. */
+int or_gather_window(int u, int l, int rr, const uint8_t *img, int H, int W, int r0, int c0, uint8_t *pri) {
+    const window_t w = {u, l, rr, u * (l + rr + 1) + l};
+    gather_win(&w, img, H, W, r0, c0, pri);
+    return w.n;
 }
 
 /* ------------------------------------------------------------------ */
@@ -156,9 +196,9 @@ void or_gather(const uint8_t *img, int H, int W, int r, int c, uint8_t pri[NPRI]
 /* fma(acc, s_j, o_j).                                                  */
 /* ------------------------------------------------------------------ */
 
-static void mlp_fp32(const model_t *m, const uint8_t pri[NPRI], float z[NSYM]) {
+static void mlp_fp32(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     float a[4096], b[4096];
-    for (int k = 0; k < NPRI; k++) a[k] = fmaf((float)pri[k], 0.0078125f, -1.0f);
+    for (int k = 0; k < m->win.n; k++) a[k] = fmaf((float)pri[k], 0.0078125f, -1.0f);
     float *in = a, *out = b;
     for (int l = 0; l < 3; l++) {
         int ni = m->n_in[l], no = m->n_out[l];
@@ -180,9 +220,9 @@ static float requant_u8(int32_t acc, float s, float o) {
     return t;
 }
 
-static void mlp_int8(const model_t *m, const uint8_t pri[NPRI], float z[NSYM]) {
+static void mlp_int8(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     int32_t a[4096], b[4096];
-    for (int k = 0; k < NPRI; k++) a[k] = (int32_t)pri[k] - 128;
+    for (int k = 0; k < m->win.n; k++) a[k] = (int32_t)pri[k] - 128;
     int32_t *in = a, *out = b;
     for (int l = 0; l < 3; l++) {
         int ni = m->n_in[l], no = m->n_out[l];
@@ -198,7 +238,7 @@ static void mlp_int8(const model_t *m, const uint8_t pri[NPRI], float z[NSYM]) {
     }
 }
 
-static void mlp(const model_t *m, const uint8_t pri[NPRI], float z[NSYM]) {
+static void mlp(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     if (m->precision == 0) mlp_fp32(m, pri, z);
     else mlp_int8(m, pri, z);
 }
@@ -286,7 +326,9 @@ int or_rans_dec_step(uint64_t *x, const uint32_t *cum, int nsym, int Lb, int bb,
 /* ------------------------------------------------------------------ */
 /* Wavefront order (Sec. II-B "Preprocessor", Fig. 1 right).  Reading:  */
 /* pixel (r, c) belongs to wave t = 3r + c, the smallest slope for      */
-/* which every prior of the radius-2 window lies on an earlier wave.    */
+/* which every prior of a window with a right reach of at most 2 lies   */
+/* on an earlier wave (prior (r - d, c + e), d >= 1, e <= 2, is on wave */
+/* t - 3d + e < t).                                                     */
 /* Streams (Sec. II-B "rANS": at most one per row): row r is coded by   */
 /* stream r mod S, S <= H, and each stream holds its pixels ordered by  */
 /* (t, r) ascending, which is the order in which a wavefront decoder    */
@@ -310,8 +352,9 @@ static size_t stream_order(int H, int W, int S, int s, px_t *order) {
 /* ------------------------------------------------------------------ */
 /* Container.  Reading (the paper stores one bitstream per coder         */
 /* instance and says nothing of the framing):                           */
-/*   "DLC1", u32 H, u32 W, u8 radius, u8 precision, u16 S, u64 model    */
-/*   hash, u32 words[S], then S payloads of u16 words.  Each payload    */
+/*   "DLC1", u32 H, u32 W, u8 window rows u (2 for the default         */
+/*   window), u8 precision, u16 S, u64 model hash, u32 words[S], then   */
+/*   S payloads of u16 words.  Each payload                             */
 /*   opens with the final encoder state (high half first) followed by   */
 /*   the renormalisation words in the order the decoder reads them.     */
 /* All fields little-endian.                                            */
@@ -332,10 +375,10 @@ int or_pixel_table(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
-    uint8_t pri[NPRI];
+    uint8_t pri[MAXPRI];
     float z[NSYM];
     uint32_t cum[NSYM + 1];
-    or_gather(img, H, W, r, c, pri);
+    gather_win(&m.win, img, H, W, r, c, pri);
     mlp(&m, pri, z);
     st = or_table_from_logits(z, m.tscale, m.lut, cum);
     if (z_out) memcpy(z_out, z, sizeof(z));
@@ -344,12 +387,12 @@ int or_pixel_table(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H
     return st;
 }
 
-/* Logits of the model for a batch of prior vectors (n x 12, u8). */
+/* Logits of the model for a batch of prior vectors (n x window size, u8). */
 int or_logits(const uint8_t *blob, size_t blob_n, const uint8_t *pri, int n, float *z_out) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
-    for (int i = 0; i < n; i++) mlp(&m, pri + (size_t)i * NPRI, z_out + (size_t)i * NSYM);
+    for (int i = 0; i < n; i++) mlp(&m, pri + (size_t)i * m.win.n, z_out + (size_t)i * NSYM);
     model_free(&m);
     return OR_OK;
 }
@@ -359,10 +402,10 @@ static int symbol_tables(const model_t *m, const uint8_t *img, int H, int W, uin
     double bits = 0.0;
     for (int r = 0; r < H; r++)
         for (int c = 0; c < W; c++) {
-            uint8_t pri[NPRI];
+            uint8_t pri[MAXPRI];
             float z[NSYM];
             uint32_t cum[NSYM + 1];
-            or_gather(img, H, W, r, c, pri);
+            gather_win(&m->win, img, H, W, r, c, pri);
             mlp(m, pri, z);
             int st = or_table_from_logits(z, m->tscale, m->lut, cum);
             if (st) return st;
@@ -406,7 +449,7 @@ int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H,
     memcpy(out, "DLC1", 4);
     wr_u32(out + 4, (uint32_t)H);
     wr_u32(out + 8, (uint32_t)W);
-    out[12] = 2;
+    out[12] = (uint8_t)m.win.u;   /* rows of the window above the pixel (2 for the default) */
     out[13] = (uint8_t)m.precision;
     wr_u16(out + 14, (uint32_t)S);
     for (int k = 0; k < 8; k++) out[16 + k] = (uint8_t)(m.hash >> (8 * k));
@@ -451,7 +494,7 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
     int S = in[14] | (in[15] << 8);
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)in[16 + k] << (8 * k);
-    if (h != H || w != W || in[12] != 2 || in[13] != m.precision || hash != m.hash || S < 1 ||
+    if (h != H || w != W || in[12] != m.win.u || in[13] != m.precision || hash != m.hash || S < 1 ||
         S > H || n < 24 + 4 * (size_t)S) {
         model_free(&m);
         return OR_ERR_CORRUPT;
@@ -487,10 +530,10 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
             int c = t - 3 * r;
             if (c < 0 || c >= W) continue;
             int s = r % S;
-            uint8_t pri[NPRI];
+            uint8_t pri[MAXPRI];
             float z[NSYM];
             uint32_t cum[NSYM + 1];
-            or_gather(img_out, H, W, r, c, pri);
+            gather_win(&m.win, img_out, H, W, r, c, pri);
             mlp(&m, pri, z);
             if (or_table_from_logits(z, m.tscale, m.lut, cum)) { st = OR_ERR_INVALID; break; }
             int sym = or_rans_dec_step(&x[s], cum, NSYM, 16, 16, 16, all + start[s], (int)words[s],

@@ -10,13 +10,17 @@ coder uses:
 
     0    char[4] "DLM1"
     4    u32 precision            0 = FP32 network, 1 = INT8 network
-    8    u32 n_in (12), n_h1, n_h2, n_out (256), radius (2)
+    8    u32 n_in, n_h1, n_h2, n_out (256), window
+         window = 2: the default radius-2 window (n_in = 12); otherwise
+         1 << 24 | u | l << 8 | r << 16: rows r-u..r-1 at columns c-l..c+r,
+         then row r at columns c-l..c-1 (n_in = u (l + r + 1) + l, at most
+         96; u <= 8, l <= 8, r <= 2)
     28   f32 tscale               logit difference -> table units (64 / ln 2)
     32   u32 lut[64]              lut[k] = round(2^23 * 2^(-k/64)), lut[0] = 2^23
     288  layer data
-         FP32: W1 f32[h1][12], b1 f32[h1], W2 f32[h2][h1], b2 f32[h2],
+         FP32: W1 f32[h1][n_in], b1 f32[h1], W2 f32[h2][h1], b2 f32[h2],
                W3 f32[256][h2], b3 f32[256]
-         INT8: W1 i8[h1][12], s1 f32[h1], o1 f32[h1],
+         INT8: W1 i8[h1][n_in], s1 f32[h1], o1 f32[h1],
                W2 i8[h2][h1], s2 f32[h2], o2 f32[h2],
                W3 i8[256][h2], s3 f32[256], o3 f32[256]
 
@@ -38,6 +42,33 @@ PREC_INT8 = 1
 N_IN = 12
 N_OUT = 256
 RADIUS = 2
+DEFAULT_WINDOW = (2, 2, 2)
+FIG6_WINDOW = (8, 6, 2)   # 9 x 9 window, target in the last row, third column from the right
+
+
+def window_size(window) -> int:
+    u, l, r = window
+    return u * (l + r + 1) + l
+
+
+def window_field(window) -> int:
+    """The blob's window field: 2 for the default window, else the packed
+    (u, l, r)."""
+    window = tuple(int(v) for v in window)
+    if window == DEFAULT_WINDOW:
+        return RADIUS
+    u, l, r = window
+    if not (1 <= u <= 8 and 0 <= l <= 8 and 0 <= r <= 2) or window_size(window) > 96:
+        raise ValueError("window must have 1 <= u <= 8, l <= 8, r <= 2 and at most 96 priors")
+    return (1 << 24) | u | (l << 8) | (r << 16)
+
+
+def window_of_field(field: int):
+    if field == RADIUS:
+        return DEFAULT_WINDOW
+    if field >> 24 != 1:
+        raise ValueError("unknown window field")
+    return (field & 0xFF, (field >> 8) & 0xFF, (field >> 16) & 0xFF)
 HEADER_BYTES = 288
 TSCALE = np.float32(64.0 / np.log(2.0))
 
@@ -50,21 +81,21 @@ def table_lut() -> np.ndarray:
     return np.rint(np.exp2(23.0 - k / 64.0)).astype(np.uint32)
 
 
-def _header(precision: int, h1: int, h2: int) -> bytes:
-    hdr = MAGIC + struct.pack("<6I", precision, N_IN, h1, h2, N_OUT, RADIUS)
+def _header(precision: int, h1: int, h2: int, window=DEFAULT_WINDOW) -> bytes:
+    hdr = MAGIC + struct.pack("<6I", precision, window_size(window), h1, h2, N_OUT, window_field(window))
     hdr += struct.pack("<f", float(TSCALE))
     hdr += table_lut().astype("<u4").tobytes()
     assert len(hdr) == HEADER_BYTES
     return hdr
 
 
-def _check_widths(layers):
+def _check_widths(layers, window=DEFAULT_WINDOW):
     if len(layers) != 3:
         raise ValueError("the coder network has exactly three dense layers")
     (w1, b1), (w2, b2), (w3, b3) = layers
     h1, h2 = w1.shape[0], w2.shape[0]
-    if w1.shape != (h1, N_IN) or w2.shape != (h2, h1) or w3.shape != (N_OUT, h2):
-        raise ValueError("layer shapes must be (h1,12), (h2,h1), (256,h2)")
+    if w1.shape != (h1, window_size(window)) or w2.shape != (h2, h1) or w3.shape != (N_OUT, h2):
+        raise ValueError("layer shapes must be (h1, window size), (h2, h1), (256, h2)")
     if b1.shape != (h1,) or b2.shape != (h2,) or b3.shape != (N_OUT,):
         raise ValueError("bias shapes do not match the layers")
     if h1 % 16 or h2 % 16 or not (16 <= h1 <= 256) or not (16 <= h2 <= 256):
@@ -72,10 +103,11 @@ def _check_widths(layers):
     return h1, h2
 
 
-def fp32_blob(layers) -> bytes:
-    """Blob of an FP32 network given [(W1, b1), (W2, b2), (W3, b3)]."""
-    h1, h2 = _check_widths(layers)
-    out = [_header(PREC_FP32, h1, h2)]
+def fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
+    """Blob of an FP32 network given [(W1, b1), (W2, b2), (W3, b3)] for the
+    causal window (u, l, r)."""
+    h1, h2 = _check_widths(layers, window)
+    out = [_header(PREC_FP32, h1, h2, window)]
     for w, b in layers:
         out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
         out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
@@ -98,18 +130,18 @@ def _forward_fp32(layers, ctx_u8):
     return acts, x
 
 
-def int8_blob(layers, calib_ctx: np.ndarray) -> bytes:
+def int8_blob(layers, calib_ctx: np.ndarray, window=DEFAULT_WINDOW) -> bytes:
     """Post-training quantisation of an FP32 network to the INT8 blob.
 
     Weights: per-output-channel symmetric scale max|w| / 127, round half to
     even, clamp to +-127.  Hidden activations: u8 with a per-layer scale
-    max(h) / 255 over the calibration contexts (u8 array [N, 12]).  Inputs:
-    v - 128 with scale 1/128."""
-    h1, h2 = _check_widths(layers)
+    max(h) / 255 over the calibration contexts (u8 array [N, window size]).
+    Inputs: v - 128 with scale 1/128."""
+    h1, h2 = _check_widths(layers, window)
     acts, _ = _forward_fp32(layers, np.asarray(calib_ctx, dtype=np.uint8))
     act_scale = [max(float(a.max()), 1e-6) / 255.0 for a in acts]
     in_scale = [1.0 / 128.0, act_scale[0], act_scale[1]]
-    out = [_header(PREC_INT8, h1, h2)]
+    out = [_header(PREC_INT8, h1, h2, window)]
     for li, (w, b) in enumerate(layers):
         w = w.astype(np.float64)
         b = b.astype(np.float64)
@@ -136,7 +168,7 @@ def parse_blob(blob: bytes) -> dict:
     (tscale,) = struct.unpack_from("<f", blob, 28)
     lut = np.frombuffer(blob, dtype="<u4", count=64, offset=32)
     d = dict(precision=prec, n_in=n_in, h1=h1, h2=h2, n_out=n_out, radius=radius,
-             tscale=tscale, lut=lut)
+             window=window_of_field(radius), tscale=tscale, lut=lut)
     off = HEADER_BYTES
     dims = [(h1, n_in), (h2, h1), (n_out, h2)]
     for li, (o, i) in enumerate(dims, start=1):

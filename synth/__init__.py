@@ -210,38 +210,47 @@ def batch_images(count: int, seed: int, **size_kw):
     return [voronoi_image(h, w, seed * 131 + i + 1) for i, (h, w) in enumerate(sizes)]
 
 
-def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02):
+def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, window=(2, 2, 2)):
     """FP32 weights for which the network's PDF is a discretised Gaussian of
     standard deviation `sigma` grey levels around a linear prediction from the
     priors (the mean of the left and upper neighbours plus a gradient term),
     plus small seeded perturbations in every weight.  The prediction is
     carried through the ReLU layers as relu(x) - relu(-x), so the network
     represents it exactly; it gives realistic, peaked tables without a
-    training run.  Input features are v / 128 - 1 in the prior order
-    (r-2: c-2..c+2, r-1: c-2..c+2, r: c-2, c-1)."""
+    training run.  Input features are v / 128 - 1 in the prior order of the
+    causal window (u, l, r): rows r-u..r-1 at columns c-l..c+r, then row r at
+    columns c-l..c-1 (the default (2, 2, 2): r-2: c-2..c+2, r-1: c-2..c+2,
+    r: c-2, c-1).  With the default window every prior is carried through
+    the ReLU layers, otherwise the three that the prediction uses."""
+    u, l, rr = window
+    wid = l + rr + 1
+    n = u * wid + l
     n_in, h1, h2, n_out = widths
-    assert n_in == 12 and n_out == 256 and h1 >= 24 and h2 >= 24
+    i_left, i_up, i_upleft = u * wid + l - 1, (u - 1) * wid + l, (u - 1) * wid + l - 1
+    carried = list(range(n)) if tuple(window) == (2, 2, 2) else [i_upleft, i_up, i_left]
+    nc = 2 * len(carried)
+    assert n_in == n and n_out == 256 and h1 >= nc and h2 >= nc and l >= 1
     rng = Rng(seed)
-    alpha = np.zeros(12)
-    alpha[11] = 0.75      # left neighbour
-    alpha[7] = 0.75       # upper neighbour
-    alpha[6] = -0.5       # upper-left neighbour
-    w1 = noise * rng.normal(h1 * 12).reshape(h1, 12)
-    w1[:24] = 0.0
-    for k in range(12):
-        w1[2 * k, k] = 1.0
-        w1[2 * k + 1, k] = -1.0
+    alpha = np.zeros(n)
+    alpha[i_left] = 0.75      # left neighbour
+    alpha[i_up] = 0.75        # upper neighbour
+    alpha[i_upleft] = -0.5    # upper-left neighbour
+    w1 = noise * rng.normal(h1 * n).reshape(h1, n)
+    w1[:nc] = 0.0
+    for j, k in enumerate(carried):
+        w1[2 * j, k] = 1.0
+        w1[2 * j + 1, k] = -1.0
     b1 = np.zeros(h1)
     w2 = noise * rng.normal(h2 * h1).reshape(h2, h1) / np.sqrt(h1)
-    w2[:24, :] = 0.0
-    w2[:24, :24] = np.eye(24)
+    w2[:nc, :] = 0.0
+    w2[:nc, :nc] = np.eye(nc)
     b2 = np.zeros(h2)
     t = np.arange(256) / 128.0 - 1.0
     beta = 1.0 / (2.0 * (sigma / 128.0) ** 2)
     pred = np.zeros(h2)
-    for k in range(12):
-        pred[2 * k] = alpha[k]
-        pred[2 * k + 1] = -alpha[k]
+    for j, k in enumerate(carried):
+        pred[2 * j] = alpha[k]
+        pred[2 * j + 1] = -alpha[k]
     w3 = 2.0 * beta * t[:, None] * pred[None, :]
     w3 += noise * rng.normal(256 * h2).reshape(256, h2)
     b3 = -beta * t * t

@@ -15,17 +15,25 @@ def fp32_model(widths, seed=1, kind="predictive"):
     return layers, M.fp32_blob(layers)
 
 
-def calib_contexts(images, count=4096, seed=77):
-    """Priors (u8 [count, 12]) of pixels drawn uniformly from the images,
-    zero-padded at the borders: calibration data for quantisation."""
+def window_offsets(window=(2, 2, 2)):
+    """(dr, dc) of every prior of the causal window (u, l, r), in order."""
+    u, l, r = window
+    offs = [(-u + k // (l + r + 1), -l + k % (l + r + 1)) for k in range(u * (l + r + 1))]
+    return offs + [(0, -l + k) for k in range(l)]
+
+
+def calib_contexts(images, count=4096, seed=77, window=(2, 2, 2)):
+    """Priors (u8 [count, window size]) of pixels drawn uniformly from the
+    images, zero-padded at the borders: calibration data for quantisation."""
     idx, rr, cc = synth.sample_positions(images, count, seed)
-    out = np.zeros((count, 12), np.uint8)
-    dr = [-2, -2, -2, -2, -2, -1, -1, -1, -1, -1, 0, 0]
-    dc = [-2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -2, -1]
+    offs = window_offsets(window)
+    out = np.zeros((count, len(offs)), np.uint8)
+    dr = [o[0] for o in offs]
+    dc = [o[1] for o in offs]
     for n, (i, r, c) in enumerate(zip(idx, rr, cc)):
         img = images[i]
         H, W = img.shape
-        for k in range(12):
+        for k in range(len(offs)):
             y, x = r + dr[k], c + dc[k]
             out[n, k] = img[y, x] if 0 <= y < H and 0 <= x < W else 0
     return out
