@@ -75,12 +75,21 @@ DLIC_API const char *dlic_last_error(void);
 /* ---------------------------------------------------------------------- */
 
 /* Creates a coder model from a model blob (host memory, little-endian):
- *   "DLM1", u32 precision (DLIC_FP32 / DLIC_INT8), u32 12, u32 h1, u32 h2,
- *   u32 256, u32 radius = 2, f32 tscale, u32 lut[64], then the three dense
+ *   "DLM1", u32 precision (DLIC_FP32 / DLIC_INT8), u32 n_in, u32 h1, u32 h2,
+ *   u32 256, u32 window, f32 tscale, u32 lut[64], then the three dense
  *   layers (FP32: W f32[out][in] and b f32[out] per layer; INT8: W i8[out][in],
  *   s f32[out], o f32[out] per layer).
- * The network maps the 12 causal priors of a pixel to 256 logits (Sec. II-B,
+ * The network maps the causal priors of a pixel to 256 logits (Sec. II-B,
  * "Neural Network Architecture": dense layers, a 256-way softmax output).
+ * The window ("any window shape", Sec. II-A) is window = 2 for the default
+ * 12 priors (rows r-2, r-1 at columns c-2..c+2, then (r, c-2), (r, c-1)), or
+ * 1 << 24 | u | l << 8 | rr << 16 for rows r-u..r-1 at columns c-l..c+rr,
+ * then row r at columns c-l..c-1 (1 <= u <= 8, l <= 8, rr <= 2, so that
+ * wave t = 3r + c stays valid), with n_in = u (l + rr + 1) + l priors; the
+ * 9 x 9 window of Fig. 6 is (8, 6, 2), 78 priors.  Windows other than the
+ * default need the tensor-core INT8 kernels (h1, h2 <= 128 to encode,
+ * h1 = h2 = 128 to decode) or the FP32 tiled kernels (h2 <= 128)
+ * (DLIC_ERR_UNSUPPORTED otherwise).
  * h1 and h2 must be multiples of 16 in [16, 256].  The blob is copied; the
  * model owns device copies of the weights in the layouts the kernels use.
  * The model hash (FNV-1a 64 of the blob) is written into every bitstream and
@@ -131,7 +140,8 @@ DLIC_API dlic_status dlic_encode_workspace_size(const dlic_model *model, const d
  *                 is then invalid).
  *  d_workspace:   at least dlic_encode_workspace_size bytes, 256-aligned.
  * Bitstream layout (little-endian): "DLC1", u32 height, u32 width,
- * u8 radius (2), u8 precision, u16 S, u64 model hash, u32 words[S], then S
+ * u8 window rows u (2 for the default window), u8 precision, u16 S, u64
+ * model hash, u32 words[S], then S
  * payloads of u16 words; each payload opens with the final rANS state (high
  * half first) and continues with the renormalisation words in the order the
  * decoder reads them.  Row r is coded by stream r mod S; a stream's pixels

@@ -65,7 +65,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    # every symbol must resolve at link time (a missing definition fails the
+    # build instead of the first load)
+    cmd = [NVCC] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -74,8 +74,19 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     const uint32_t prec = le32(b + 4), n_in = le32(b + 8), h1 = le32(b + 12), h2 = le32(b + 16),
                    n_out = le32(b + 20), radius = le32(b + 24);
     if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
-    if (n_in != kPriors || n_out != kSymbols || radius != 2)
-        return fail(DLIC_ERR_INVALID, "model must map 12 radius-2 priors to 256 logits");
+    // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16
+    int wu = 2, wl = 2, wr = 2;
+    if (radius != 2) {
+        if ((radius >> 24) != 1) return fail(DLIC_ERR_INVALID, "unknown window field 0x%x", radius);
+        wu = (int)(radius & 0xFF);
+        wl = (int)((radius >> 8) & 0xFF);
+        wr = (int)((radius >> 16) & 0xFF);
+        if (wu < 1 || wu > 8 || wl > 8 || wr > 2)
+            return fail(DLIC_ERR_INVALID, "window must have 1..8 rows above, left reach <= 8, right reach <= 2");
+    }
+    const int npri = wu * (wl + wr + 1) + wl;
+    if (npri > kMaxPriors || (int)n_in != npri || n_out != kSymbols)
+        return fail(DLIC_ERR_INVALID, "model must map the %d priors of its window to 256 logits", npri);
     if (h1 < 16 || h1 > kMaxHidden || h1 % 16 || h2 < 16 || h2 > kMaxHidden || h2 % 16)
         return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
     const float tscale = lef32(b + 28);
@@ -86,7 +97,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         if (lut[k] > (1u << 23)) return fail(DLIC_ERR_INVALID, "lut entries must be <= 2^23");
     }
     if (lut[0] != (1u << 23)) return fail(DLIC_ERR_INVALID, "lut[0] must be 2^23");
-    const int din[3] = {kPriors, (int)h1, (int)h2}, dout[3] = {(int)h1, (int)h2, kSymbols};
+    const int din[3] = {npri, (int)h1, (int)h2}, dout[3] = {(int)h1, (int)h2, kSymbols};
+    const int k1 = (npri + 15) / 16 * 16;   // first-layer K of the tensor-core operands
     size_t need = 288;
     for (int l = 0; l < 3; l++)
         need += prec == 0 ? 4ull * din[l] * dout[l] + 4ull * dout[l] : (size_t)din[l] * dout[l] + 8ull * dout[l];
@@ -104,6 +116,10 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.precision = (int)prec;
     d.h1 = (int)h1;
     d.h2 = (int)h2;
+    d.wu = wu;
+    d.wl = wl;
+    d.wr = wr;
+    d.n_in = npri;
     d.tscale = tscale;
     d.hash = fnv1a64(b, n);
     size_t off_lut = put(lut, sizeof(lut));
@@ -128,8 +144,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             pp += (size_t)din[l] * dout[l] + 8ull * dout[l];
         }
         if (h1 <= 128 && h2 <= 128) {
-            std::vector<uint16_t> img(tc_weight_bytes((int)h1, (int)h2) / 2);
-            tc_pack_weights((int)h1, (int)h2, raw[0], raw[1], raw[2], img.data());
+            std::vector<uint16_t> img(tc_weight_bytes((int)h1, (int)h2, k1) / 2);
+            tc_pack_weights((int)h1, (int)h2, npri, k1, raw[0], raw[1], raw[2], img.data());
             offs[15] = put(img.data(), img.size() * 2);
             d.tc_w_bytes = (uint32_t)(img.size() * 2);
         }
@@ -197,6 +213,16 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         if (d.tc_w_bytes) d.tc_w = reinterpret_cast<const uint16_t *>(base + offs[15]);
     }
     m->dev = d;
+    if (!default_window(d)) {
+        // other windows run on the tensor-core INT8 kernels and the FP32
+        // tiled / cluster kernels only
+        const bool enc_ok = prec == DLIC_INT8 ? (h1 <= 128 && h2 <= 128) : f32_predict_supported(d);
+        if (!enc_ok || !wave_decode_supported(d)) {
+            dlic_model_destroy(m);
+            return fail(DLIC_ERR_UNSUPPORTED, "a window other than the default needs INT8 widths 128/128 or an FP32 "
+                                              "network with h2 <= 128");
+        }
+    }
     *out = m;
     return DLIC_OK;
 }
@@ -347,7 +373,7 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
 extern "C" dlic_status dlic_read_header(const void *h_bits, size_t bytes, int *height, int *width,
                                         int *streams, int *precision, uint64_t *hash) {
     const uint8_t *h = static_cast<const uint8_t *>(h_bits);
-    if (!h || bytes < (size_t)kHeaderBytes || memcmp(h, "DLC1", 4) != 0 || h[12] != 2)
+    if (!h || bytes < (size_t)kHeaderBytes || memcmp(h, "DLC1", 4) != 0 || h[12] < 1 || h[12] > 8)
         return fail(DLIC_ERR_CORRUPT, "not a DLIC bitstream");
     if (height) *height = (int)le32(h + 4);
     if (width) *width = (int)le32(h + 8);

@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
 // ---------------------------------------------------------------------------
 constexpr int kF32Tile = 64, kF32Pitch = kF32Tile + 4, kF32Threads = 256;
 
-__host__ __device__ inline size_t f32_predict_smem(int h1, int h2) {
-    const size_t xs = (size_t)kF32Tile * 16 * 4, h1t = (size_t)h1 * kF32Pitch * 4, z = (size_t)kF32Tile * kSymbols * 4;
+// xs holds the tile's inputs [64][k1] (the window's priors padded to 16).
+__host__ __device__ inline size_t f32_predict_smem(int h1, int h2, int k1) {
+    const size_t xs = (size_t)kF32Tile * k1 * 4, h1t = (size_t)h1 * kF32Pitch * 4, z = (size_t)kF32Tile * kSymbols * 4;
     const size_t region = xs + h1t > z ? xs + h1t : z;   // z overlays xs and h1t
     return region + (size_t)h2 * kF32Pitch * 4;
 }
@@ -143,12 +144,12 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut_s[kTableSteps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int h1 = m.h1, h2 = m.h2;
+    const int h1 = m.h1, h2 = m.h2, npri = m.n_in, K1 = (npri + 15) / 16 * 16;
     expand_lut(m.lut, lut_s, tid, kF32Threads);
-    float *xs = reinterpret_cast<float *>(smem);                         // [64][16]
-    float *h1t = xs + kF32Tile * 16;                                      // [h1][pitch]
+    float *xs = reinterpret_cast<float *>(smem);                         // [64][K1]
+    float *h1t = xs + kF32Tile * K1;                                      // [h1][pitch]
     float *zs = reinterpret_cast<float *>(smem);                         // [64][256], after layer 2
-    const size_t region = f32_predict_smem(h1, h2) - (size_t)h2 * kF32Pitch * 4;
+    const size_t region = f32_predict_smem(h1, h2, K1) - (size_t)h2 * kF32Pitch * 4;
     float *h2t = reinterpret_cast<float *>(smem + region);                // [h2][pitch]
 
     const int tile = blockIdx.x;
@@ -158,19 +159,19 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
     const int64_t p_base = (int64_t)(tile - im.tile_begin) * kF32Tile;
     const int64_t npx = (int64_t)im.H * im.W;
     // inputs x/128 - 1 of the 64 pixels (pixels past the image get zeros)
-    for (int i = tid; i < kF32Tile * kPriors; i += kF32Threads) {
-        const int p = i / kPriors, q = i % kPriors;
+    for (int i = tid; i < kF32Tile * npri; i += kF32Threads) {
+        const int p = i / npri, q = i % npri;
         const int64_t pp = p_base + p;
         float v = 0.0f;
         if (pp < npx) {
             const int r = (int)(pp / im.W), c = (int)(pp % im.W);
-            const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
-            const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+            int dr, dc;
+            window_offset(m, q, dr, dc);
             const int rr = r + dr, cc = c + dc;
             const uint32_t pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[rr * im.pitch + cc] : 0u;
             v = __fmaf_rn((float)pv, 0.0078125f, -1.0f);
         }
-        xs[p * 16 + q] = v;
+        xs[p * K1 + q] = v;
     }
     __syncthreads();
     // layer 1: thread = (unit, 4 pixels)
@@ -180,11 +181,11 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
         const float bias = __ldg(m.b1 + u);
 #pragma unroll
         for (int j = 0; j < 4; j++) a[j] = bias;
-#pragma unroll
-        for (int k = 0; k < kPriors; k++) {
+#pragma unroll 4
+        for (int k = 0; k < npri; k++) {
             const float w = __ldg(m.w1t + k * h1 + u);
 #pragma unroll
-            for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[(p0 + j) * 16 + k], w, a[j]);
+            for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[(p0 + j) * K1 + k], w, a[j]);
         }
         *reinterpret_cast<float4 *>(h1t + u * kF32Pitch + p0) =
             make_float4(a[0] > 0.0f ? a[0] : 0.0f, a[1] > 0.0f ? a[1] : 0.0f, a[2] > 0.0f ? a[2] : 0.0f,
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
 
 bool f32_predict_supported(const DevModel &m) {
     return m.precision == DLIC_FP32 && m.h1 % 4 == 0 && m.h2 % 4 == 0 && m.h1 <= kMaxHidden && m.h2 <= kMaxHidden &&
-           f32_predict_smem(m.h1, m.h2) <= 227 * 1024;
+           f32_predict_smem(m.h1, m.h2, (m.n_in + 15) / 16 * 16) <= 200 * 1024;
 }
 
 // ---------------------------------------------------------------------------
@@ -299,7 +300,7 @@ __device__ bool decode_setup(const DevModel &m, const DecImage &im, const uint8_
             for (int k = 0; k < 8; k++) hash |= (uint64_t)h[16 + k] << (8 * k);
             S = h[14] | (h[15] << 8);
             ok = h[0] == 'D' && h[1] == 'L' && h[2] == 'C' && h[3] == '1' &&
-                 rd_le32(h + 4) == (uint32_t)im.H && rd_le32(h + 8) == (uint32_t)im.W && h[12] == 2 &&
+                 rd_le32(h + 4) == (uint32_t)im.H && rd_le32(h + 8) == (uint32_t)im.W && h[12] == m.wu &&
                  h[13] == m.precision && hash == m.hash && S >= 1 && S <= im.H &&
                  im.in_bytes >= (uint64_t)kHeaderBytes + 4ull * S;
         }
@@ -467,9 +468,10 @@ static size_t decode_smem(const DevModel &m) {
 
 cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
+    if (!default_window(m) && !(m.precision == DLIC_FP32 && f32_predict_supported(m))) return cudaErrorNotSupported;
     if (m.precision == DLIC_FP32 && f32_predict_supported(m)) {
         // 64-pixel tiles, as the encoder plans them for the CUDA-core path
-        const size_t sm = f32_predict_smem(m.h1, m.h2);
+        const size_t sm = f32_predict_smem(m.h1, m.h2, (m.n_in + 15) / 16 * 16);
         cudaFuncSetAttribute(k_predict_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_predict_f32<<<b.total_tiles, kF32Threads, sm, st>>>(m, b);
     } else if (m.precision == DLIC_FP32) {
@@ -486,6 +488,7 @@ cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t
 
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st) {
     if (b.n == 0) return cudaSuccess;
+    if (!default_window(m)) return cudaErrorNotSupported;   // one thread per pixel: the 12-prior window only
     if (m.precision == DLIC_FP32) {
         const size_t sm = decode_smem<DLIC_FP32>(m);
         cudaFuncSetAttribute(k_decode_cc<DLIC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

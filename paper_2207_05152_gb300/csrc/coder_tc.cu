@@ -31,7 +31,10 @@ struct TcLayout {
     uint32_t w1, w2, w3, a1[kTcSlots], a23[kTcSlots], s1, o1, s2, o2, s3, o3, lut, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int h1, int h2) {
+// k1: the first layer's K, the window's priors padded to 16.  A slot's A1
+// tile (pixels x k1) and its hidden-activation tile share one buffer: the
+// first layer's MMA has read A1 before the first requantisation writes.
+__host__ __device__ inline TcLayout tc_layout(int h1, int h2, int k1) {
     TcLayout L;
     uint32_t off = 0;
     auto take = [&](uint32_t bytes) {
@@ -39,13 +42,14 @@ __host__ __device__ inline TcLayout tc_layout(int h1, int h2) {
         off += (bytes + 127u) & ~127u;
         return o;
     };
-    L.w1 = take(32u * h1);
+    L.w1 = take(2u * k1 * h1);
     L.w2 = take(2u * h1 * h2);
     L.w3 = take(512u * h2);
-    const int hmax = h1 > h2 ? h1 : h2;
+    int hmax = h1 > h2 ? h1 : h2;
+    hmax = hmax > k1 ? hmax : k1;
     for (int j = 0; j < kTcSlots; j++) {
-        L.a1[j] = take(kTcTile * 16 * 2);
         L.a23[j] = take(kTcTile * hmax * 2);
+        L.a1[j] = L.a23[j];
     }
     L.s1 = take(4u * h1);
     L.o1 = take(4u * h1);
@@ -88,11 +92,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
     __shared__ uint32_t tmem_base;
     __shared__ int wg_fail[kTcSlots];
     __shared__ float s_max[kTcSlots][2][128];
+    __shared__ char2 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
     __shared__ uint32_t s_w[kTcSlots][3][128];   // the high half's W, P_sym and w_sym
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
     const int slot = wg & 1, half = wg >> 1;
     const int h1 = m.h1, h2 = m.h2;
-    const TcLayout L = tc_layout(h1, h2);
+    const int K1 = (m.n_in + 15) / 16 * 16;
+    const TcLayout L = tc_layout(h1, h2, K1);
 
     // weights (already in operand layout) and epilogue parameters
     {
@@ -107,6 +113,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
         for (int i = tid; i < h2; i += blockDim.x) { s2[i] = m.s2[i]; o2[i] = m.o2[i]; }
         for (int i = tid; i < kSymbols; i += blockDim.x) { s3[i] = m.s3[i]; o3[i] = m.o3[i]; }
         expand_lut(m.lut, reinterpret_cast<uint32_t *>(smem + L.lut), tid, blockDim.x);
+        if (tid < m.n_in) {
+            int dr, dc;
+            window_offset(m, tid, dr, dc);
+            s_woff[tid] = make_char2((signed char)dr, (signed char)dc);
+        }
     }
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, 256 * kTcSlots);
@@ -163,22 +174,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
         const bool active = p < (int64_t)im.H * im.W;
         const int r = active ? (int)(p / im.W) : 0, c = active ? (int)(p % im.W) : 0;
 
-        // A1: the 12 priors as v - 128, padded to K = 16 with zeros
-        if (half == 0) {
-            uint8_t pri[kPriors];
-            if (active) gather_priors(im.pixels, im.pitch, im.H, im.W, r, c, pri);
-            uint32_t w[8];
+        // A1: the window's priors as v - 128 (pixels outside the image are
+        // 0), padded to K1 with zeros; the two warpgroups of the slot take
+        // alternate 8-column chunks
+        for (int j = half; j < K1 / 8; j += 2) {
+            uint32_t w[4];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int k0 = 2 * q, k1 = 2 * q + 1;
-                const uint32_t lo = (k0 < kPriors && active) ? tc::bf16_of_int((int)pri[k0] - 128) : 0u;
-                const uint32_t hi = (k1 < kPriors && active) ? tc::bf16_of_int((int)pri[k1] - 128) : 0u;
-                w[q] = lo | (hi << 16);
+            for (int e = 0; e < 4; e++) {
+                uint32_t pair = 0;
+#pragma unroll
+                for (int hb = 0; hb < 2; hb++) {
+                    const int q = 8 * j + 2 * e + hb;
+                    uint32_t v = 0u;
+                    if (active && q < m.n_in) {
+                        const char2 o = s_woff[q];
+                        const int rr = r + o.x, cc = c + o.y;
+                        const int pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[(int64_t)rr * im.pitch + cc] : 0;
+                        v = tc::bf16_of_int(pv - 128);
+                    }
+                    pair |= v << (16 * hb);
+                }
+                w[e] = pair;
             }
-            *reinterpret_cast<uint4 *>(a1 + tc::kmajor_offset(t, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4 *>(a1 + tc::kmajor_offset(t, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+            *reinterpret_cast<uint4 *>(a1 + tc::kmajor_offset(t, 8 * j, K1)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        if (!layer(sa1, sw1, 16, h1)) break;
+        if (!layer(sa1, sw1, K1, h1)) break;
         // requantisation: each warpgroup of the slot takes half of the
         // 16-column chunks (the first half the odd one)
         const int n1 = h1 / 16, f1 = (n1 + 1) / 2;
@@ -268,20 +288,21 @@ bool tc_supported(const DevModel &m) {
     return m.precision == DLIC_INT8 && m.tc_w != nullptr && m.h1 <= 128 && m.h2 <= 128;
 }
 
-size_t tc_weight_bytes(int h1, int h2) {
-    const TcLayout L = tc_layout(h1, h2);
+size_t tc_weight_bytes(int h1, int h2, int k1) {
+    const TcLayout L = tc_layout(h1, h2, k1);
     return L.w3 + 512u * h2;
 }
 
 // Host image of the bf16 operand tiles W1 (h1 x 16), W2 (h2 x h1), W3
 // (256 x h2) from the int8 weights (row-major [out][in]).
-void tc_pack_weights(int h1, int h2, const int8_t *q1, const int8_t *q2, const int8_t *q3, uint16_t *out) {
-    const TcLayout L = tc_layout(h1, h2);
+void tc_pack_weights(int h1, int h2, int n_in, int k1, const int8_t *q1, const int8_t *q2, const int8_t *q3,
+                     uint16_t *out) {
+    const TcLayout L = tc_layout(h1, h2, k1);
     uint8_t *base = reinterpret_cast<uint8_t *>(out);
-    for (size_t i = 0; i < tc_weight_bytes(h1, h2) / 2; i++) out[i] = 0;
+    for (size_t i = 0; i < tc_weight_bytes(h1, h2, k1) / 2; i++) out[i] = 0;
     for (int j = 0; j < h1; j++)
-        for (int k = 0; k < kPriors; k++)
-            *reinterpret_cast<uint16_t *>(base + L.w1 + tc::kmajor_offset(j, k, 16)) = tc::bf16_of_int(q1[j * kPriors + k]);
+        for (int k = 0; k < n_in; k++)
+            *reinterpret_cast<uint16_t *>(base + L.w1 + tc::kmajor_offset(j, k, k1)) = tc::bf16_of_int(q1[j * n_in + k]);
     for (int j = 0; j < h2; j++)
         for (int k = 0; k < h1; k++)
             *reinterpret_cast<uint16_t *>(base + L.w2 + tc::kmajor_offset(j, k, h1)) = tc::bf16_of_int(q2[j * h1 + k]);
@@ -292,7 +313,7 @@ void tc_pack_weights(int h1, int h2, const int8_t *q1, const int8_t *q2, const i
 
 cudaError_t launch_predict_tc(const DevModel &m, const EncBatch &b, int *err, int num_sms, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
-    const TcLayout L = tc_layout(m.h1, m.h2);
+    const TcLayout L = tc_layout(m.h1, m.h2, (m.n_in + 15) / 16 * 16);
     cudaError_t e = cudaFuncSetAttribute(k_encode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     const int per_cta = kTcSlots;

@@ -41,20 +41,34 @@ struct DecTcLayout {
     uint32_t z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, total;
 };
 
+struct DecTcParams {
+    int P;            // CTAs per image (cluster size)
+    int h1, h2;       // hidden widths (FP32 network)
+    int nt;           // pixels per chunk (multiple of 16, <= 128)
+    int ring_rows;    // power of two
+    int tq;           // tagged ring: row rounds kept (power of two)
+    int max_g;        // owned streams per CTA (upper bound)
+    int pay_words;    // staged payload capacity per CTA (words); 0 = read from global
+    int k1;           // network inputs per pixel: the window's priors padded to 16
+    int tslots;       // tagged-ring slots per row round: one per row distance 0..rows above
+    int tcols;        // tagged-ring columns kept per row (power of two)
+    int rcols;        // byte-ring columns kept per row (power of two)
+};
+
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
 // b1, b2, b3, then W2^T [h1][h2].  W3^T [h2][256] streams through a ring of
 // kW3Stages buffers of kW3Rows rows, refilled by bulk copies from L2.
 constexpr int kW3Rows = 16, kW3Stages = 5;
-__host__ __device__ inline uint32_t dec_f32_weight_floats(int h1, int h2) {
-    return (uint32_t)(kPriors * h1 + h1 + h2 + kSymbols);
+__host__ __device__ inline uint32_t dec_f32_weight_floats(int n_in, int h1, int h2) {
+    return (uint32_t)(n_in * h1 + h1 + h2 + kSymbols);
 }
 
 // Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
 // the bound on the pixels of one wave), `tslots` tagged-ring rows, `g` owned
 // streams and `pay_words` staged payload words, for the INT8 tensor-core
 // network or (f32) the FP32 network of widths h1, h2.
-__host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, int g, int pay_words, bool f32 = false,
-                                                  int h1 = kDecHidden, int h2 = kDecHidden) {
+__host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f32) {
+    const int nt = prm.nt, rows = prm.ring_rows, g = prm.max_g, pay_words = prm.pay_words, h1 = prm.h1, h2 = prm.h2;
     DecTcLayout L{};
     uint32_t off = 0;
     auto take = [&](uint32_t bytes) {
@@ -63,12 +77,12 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
         return o;
     };
     if (f32) {
-        L.wf = take(4u * dec_f32_weight_floats(h1, h2));
+        L.wf = take(4u * dec_f32_weight_floats(prm.k1, h1, h2));
         L.w2f = take(4u * h1 * h2);
         L.w3s = take(4u * kW3Stages * kW3Rows * kSymbols);
         // xs, then h1t [unit][nt + 4] (conflict-free float4 rows); z
         // overlays both once the second layer has consumed them
-        const uint32_t xs_bytes = 64u * nt, h1t_bytes = 4u * h1 * (nt + 4), z_bytes = 4u * nt * kSymbols;
+        const uint32_t xs_bytes = 4u * prm.k1 * nt, h1t_bytes = 4u * h1 * (nt + 4), z_bytes = 4u * nt * kSymbols;
         const uint32_t region = xs_bytes + h1t_bytes > z_bytes ? xs_bytes + h1t_bytes : z_bytes;
         const uint32_t base = take(region);
         L.xs = base;
@@ -76,15 +90,15 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
         L.z = base;
         L.h2t = take(4u * h2 * (nt + 4));
     } else {
-        L.w1 = 0;   // the first layer runs as dp4a: its bf16 tile is not copied
+        L.w1 = take((uint32_t)prm.k1 * kDecHidden);   // W1 as s8 words [k1 / 4][128] (the first layer runs as dp4a)
         L.w2 = take(2u * kDecHidden * kDecHidden);
         L.w3 = take(512u * kDecHidden);
-        L.pri = take(16u * nt);
+        L.pri = take((uint32_t)prm.k1 * nt);
         L.b23 = take(2u * nt * kDecHidden);
     }
     if (!f32) L.z = take(4u * nt * kSymbols);
-    L.ring = take(16u * rows);
-    L.tring = take(128u * tslots);
+    L.ring = take((uint32_t)prm.rcols * rows);
+    L.tring = take(4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * rows);
     L.pg = take(4u * nt);
     L.dsym = take(rows);
@@ -97,15 +111,6 @@ __host__ __device__ inline DecTcLayout dec_layout(int nt, int rows, int tslots, 
     return L;
 }
 
-struct DecTcParams {
-    int P;            // CTAs per image (cluster size)
-    int h1, h2;       // hidden widths (FP32 network)
-    int nt;           // pixels per chunk (multiple of 16, <= 128)
-    int ring_rows;    // power of two
-    int tq;           // tagged ring: row rounds kept per neighbour (power of two)
-    int max_g;        // owned streams per CTA (upper bound)
-    int pay_words;    // staged payload capacity per CTA (words); 0 = read from global
-};
 
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -260,6 +265,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok, s_S, s_err, s_fail;
 
+    __shared__ char2 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
     __shared__ uint32_t s_part[kDecThreads];
     __shared__ uint32_t s_gpart[kDecThreads];
 
@@ -272,31 +278,41 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const uint8_t *in = b.in + im.in_off;
     const int H = im.H, W = im.W;
     const int h1 = prm.h1, h2 = prm.h2;
-    const DecTcLayout L = dec_layout(NT, prm.ring_rows, 4 * prm.tq, prm.max_g, prm.pay_words, F32, h1, h2);
+    const DecTcLayout L = dec_layout(prm, F32);
+    const int K1 = prm.k1, NPRI = m.n_in;
 
     // --- set-up: weights, parameters, tensor memory, header and streams ---
     {
         if constexpr (F32) {
             float *wf = reinterpret_cast<float *>(smem + L.wf);
-            for (int i = tid; i < kPriors * h1; i += kDecThreads) wf[i] = m.w1t[i];
-            for (int i = tid; i < h1; i += kDecThreads) wf[kPriors * h1 + i] = m.b1[i];
-            for (int i = tid; i < h2; i += kDecThreads) wf[kPriors * h1 + h1 + i] = m.b2[i];
-            for (int i = tid; i < kSymbols; i += kDecThreads) wf[kPriors * h1 + h1 + h2 + i] = m.b3[i];
+            for (int i = tid; i < NPRI * h1; i += kDecThreads) wf[i] = m.w1t[i];
+            for (int i = tid; i < h1; i += kDecThreads) wf[NPRI * h1 + i] = m.b1[i];
+            for (int i = tid; i < h2; i += kDecThreads) wf[NPRI * h1 + h1 + i] = m.b2[i];
+            for (int i = tid; i < kSymbols; i += kDecThreads) wf[NPRI * h1 + h1 + h2 + i] = m.b3[i];
             for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
                 reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
         } else {
-            // W2 | W3 of the weight image (after the 32 x 128-byte W1 tile)
-            const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w) + 32 * kDecHidden / 16;
+            // W2 | W3 of the weight image (after the k1 x 128 bf16 W1 tile)
+            const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w) + 16 * K1;
             uint4 *dst = reinterpret_cast<uint4 *>(smem + L.w2);
-            const int n16 = (int)(m.tc_w_bytes / 16) - 32 * kDecHidden / 16;
+            const int n16 = (int)(m.tc_w_bytes / 16) - 16 * K1;
             for (int i = tid; i < n16; i += kDecThreads) dst[i] = __ldg(src + i);
+            // W1 as s8 words [k1 / 4][128] for the dp4a first layer
+            uint32_t *w1q = reinterpret_cast<uint32_t *>(smem + L.w1);
+            for (int i = tid; i < (K1 / 4) * kDecHidden; i += kDecThreads)
+                w1q[i] = i < ((NPRI + 3) / 4) * kDecHidden ? __ldg(m.q1t + i) : 0u;
         }
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
         if (tid < 64) lut[tid] = m.lut[tid];
+        if (tid < m.n_in) {
+            int dr, dc;
+            window_offset(m, tid, dr, dc);
+            s_woff[tid] = make_char2((signed char)dr, (signed char)dc);
+        }
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
-        for (int i = tid; i < prm.ring_rows * 4; i += kDecThreads) ring[i] = 0u;
+        for (int i = tid; i < prm.ring_rows * prm.rcols / 4; i += kDecThreads) ring[i] = 0u;
         uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
-        for (int i = tid; i < prm.tq * 4 * 32; i += kDecThreads) tring[i] = 0u;
+        for (int i = tid; i < prm.tq * prm.tslots * prm.tcols; i += kDecThreads) tring[i] = 0u;
     }
     if constexpr (!F32) {
         if (warp == 0) {
@@ -323,7 +339,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             const uint32_t hh = in[4] | (in[5] << 8) | (in[6] << 16) | ((uint32_t)in[7] << 24);
             const uint32_t ww = in[8] | (in[9] << 8) | (in[10] << 16) | ((uint32_t)in[11] << 24);
             ok = in[0] == 'D' && in[1] == 'L' && in[2] == 'C' && in[3] == '1' && hh == (uint32_t)H &&
-                 ww == (uint32_t)W && in[12] == 2 && in[13] == m.precision && hash == m.hash && S >= 1 &&
+                 ww == (uint32_t)W && in[12] == m.wu && in[13] == m.precision && hash == m.hash && S >= 1 &&
                  S <= H && (S + P - 1) / P <= prm.max_g && im.in_bytes >= (uint64_t)kHeaderBytes + 4ull * S;
         }
         s_ok = ok;
@@ -408,15 +424,23 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         return;
     }
     // When every CTA owns the rows k mod P (P divides S), a pixel's priors
-    // come from its own rows and those of CTAs k-1 and k-2, which push each
-    // decoded pixel into a tagged ring (32 columns of every row they own):
-    // CTAs then wait for the very values they read instead of for each other,
-    // and no cluster barrier runs per wave.  A CTA can run at most P - 1
-    // waves ahead of a reader, and a row's 32 ring columns outlive 24 waves.
-    const bool p2p = prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0;
+    // come from rows r - d, d = 0 .. rows above, owned by CTAs k - d, which
+    // push each decoded pixel into a tagged ring slot per row distance
+    // (tcols columns of every row they own): CTAs then wait for the very
+    // values they read instead of for each other, and no cluster barrier
+    // runs per wave.  A CTA can run at most P - 1 waves ahead of a reader;
+    // the launcher sizes tcols above 3 (rows above) + left reach + P, so an
+    // entry outlives its last reader, and tq so that rows sharing a slot are
+    // more than a wave's rows apart.
+    // (the tags hold 11 bits of the row and 12 of the column: wider images
+    // use the byte ring)
+    const bool p2p = prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0 && W <= 4096;
     uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
     const uint32_t tring_addr = tc::smem_addr(tring);
-    const int tqmask = prm.tq - 1;
+    const int tqmask = prm.tq - 1, tcmask = prm.tcols - 1, rcmask = prm.rcols - 1;
+    // gather threads per pixel: the priors and one more, rounded to a power of two
+    const int lg_slot = NPRI + 1 <= 16 ? 4 : (NPRI + 1 <= 32 ? 5 : (NPRI + 1 <= 64 ? 6 : 7));
+    const int slot_px = 1 << lg_slot;
     if (P > 1) cluster_sync_all();   // every CTA's rings are initialised
 
     // FP32: W3^T streams through kW3Stages staging buffers in a fixed cycle
@@ -453,7 +477,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const uint32_t ring_addr = tc::smem_addr(ring);
     // the ring bases of the CTAs this lane stores to (the cluster window is
     // linear within a CTA, so the mapping is computed once)
-    const uint32_t tring_dst = (P > 1 && lane < 3) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
+    const uint32_t tring_dst =
+        (P > 1 && lane < prm.tslots) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
     const uint32_t ring_dst = (P > 1 && lane < P) ? map_shared(ring_addr, (k + (uint32_t)lane) % (uint32_t)P) : ring_addr;
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     uint8_t *pri = smem + L.pri;   // priors of the chunk's pixels as s8 (x - 128), 16 bytes each
@@ -462,11 +487,13 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const uint32_t sb23 = tc::smem_addr(b23);
     const uint32_t sw2 = tc::smem_addr(smem + L.w2), sw3 = tc::smem_addr(smem + L.w3);
     // this thread's row of the first layer's INT8 weights, 4 inputs per word
+    // (from the zero-padded copy in shared memory)
     uint32_t w1a = 0, w1b = 0, w1c = 0;
     if constexpr (!F32) {
-        w1a = m.q1t[unit];
-        w1b = m.q1t[kDecHidden + unit];
-        w1c = m.q1t[2 * kDecHidden + unit];
+        const uint32_t *w1q0 = reinterpret_cast<const uint32_t *>(smem + L.w1);
+        w1a = w1q0[unit];
+        w1b = w1q0[kDecHidden + unit];
+        w1c = w1q0[2 * kDecHidden + unit];
     }
     const int rmask = prm.ring_rows - 1;
     uint32_t phase = 0;
@@ -580,16 +607,16 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             const int NP = (nc + 15) & ~15;
             // 1. priors of the chunk's pixels, one thread per (pixel, prior)
             //    so that every ring read is in flight at once; the spare
-            //    thirteenth thread of a pixel records its stream and table
+            //    thread after a pixel's priors records its stream and table
             //    warp.  Pad pixels up to NP get arbitrary inputs.
             const int NPin = F32 ? (nc + 3) & ~3 : NP;   // pixels whose inputs are written
-            for (int idx = tid; idx < 16 * NPin; idx += kDecThreads) {
-                const int px = idx >> 4, q = idx & 15;
-                if (q > kPriors) continue;
+            for (int idx = tid; idx < slot_px * NPin; idx += kDecThreads) {
+                const int px = idx >> lg_slot, q = idx & (slot_px - 1);
+                if (q > NPRI) continue;
                 uint32_t v = 0x80u;
                 if (px < nc) {
                     const int r = row_of(base + px), c = t - 3 * r;
-                    if (q == kPriors) {
+                    if (q == NPRI) {
                         // local stream of the pixel and the warp that runs its
                         // table: by pixel when no two rows of the wave share a
                         // stream, else by stream so that they run in row order
@@ -597,15 +624,14 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
                         continue;
                     }
-                    const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
-                    const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
-                    const int rr = r + dr, cc = c + dc;
+                    const char2 o = s_woff[q];
+                    const int dr = o.x, rr = r + dr, cc = c + o.y;
                     if (rr < 0 || cc < 0 || cc >= W) {
                         v = 0u;
                     } else if (p2p) {
-                        // entry (round of rr, owner distance, column mod 32)
-                        const int slot = (((rr >> lgP) & tqmask) << 2) | (((int)k - rr) & (P - 1));
-                        const uint32_t *e = tring + slot * 32 + (cc & 31);
+                        // entry (round of rr, row distance, column mod tcols)
+                        const int slot = ((rr >> lgP) & tqmask) * prm.tslots - dr;
+                        const uint32_t *e = tring + slot * prm.tcols + (cc & tcmask);
                         const uint32_t want = ring_tag(rr, cc);
                         v = ld_volatile_u32(e);
                         if ((v & 0xFFFFFF00u) != want) {
@@ -621,7 +647,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         }
                         v &= 0xFFu;
                     } else {
-                        v = ring[((rr & rmask) << 4) + (cc & 15)];
+                        v = ring[(rr & rmask) * prm.rcols + (cc & rcmask)];
                     }
                 } else if (q == kPriors) {
                     continue;
@@ -629,9 +655,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 // network input: x/128 - 1 (FP32) or x - 128 as s8; out-of-image
                 // priors are 0
                 if constexpr (F32)
-                    reinterpret_cast<float *>(smem + L.xs)[16 * px + q] = __fmaf_rn((float)v, 0.0078125f, -1.0f);
+                    reinterpret_cast<float *>(smem + L.xs)[K1 * px + q] = __fmaf_rn((float)v, 0.0078125f, -1.0f);
                 else
-                    pri[16 * px + q] = (uint8_t)(v ^ 0x80u);
+                    pri[K1 * px + q] = (uint8_t)(v ^ 0x80u);
             }
             __syncthreads();   // every prior of the chunk is in place
             if constexpr (F32) {
@@ -640,7 +666,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 //    Thread = (unit, 4 pixels); activations [unit][pitch PT].
                 const float *xs = reinterpret_cast<const float *>(smem + L.xs);
                 const float *wf = reinterpret_cast<const float *>(smem + L.wf);
-                const float *w1s = wf, *b1s = wf + kPriors * h1, *b2s = b1s + h1, *b3s = b2s + h2;
+                const float *w1s = wf, *b1s = wf + NPRI * h1, *b2s = b1s + h1, *b3s = b2s + h2;
                 const float *w3s = b3s + kSymbols;
                 float *h1t = reinterpret_cast<float *>(smem + L.h1t);
                 float *h2t = reinterpret_cast<float *>(smem + L.h2t);
@@ -651,11 +677,11 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     float a[4];
 #pragma unroll
                     for (int j = 0; j < 4; j++) a[j] = b1s[u];
-#pragma unroll
-                    for (int kk = 0; kk < kPriors; kk++) {
+#pragma unroll 4
+                    for (int kk = 0; kk < NPRI; kk++) {
                         const float w = w1s[kk * h1 + u];
 #pragma unroll
-                        for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[16 * (p0 + j) + kk], w, a[j]);
+                        for (int j = 0; j < 4; j++) a[j] = __fmaf_rn(xs[K1 * (p0 + j) + kk], w, a[j]);
                     }
                     *reinterpret_cast<float4 *>(h1t + u * PT + p0) =
                         make_float4(a[0] > 0.0f ? a[0] : 0.0f, a[1] > 0.0f ? a[1] : 0.0f, a[2] > 0.0f ? a[2] : 0.0f,
@@ -696,9 +722,20 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 // 2. the three layers: the first (K = 12) as dp4a on the CUDA
                 //    cores, thread = (unit, pixel group); exact integer sums
                 //    requantised like the tensor-core epilogues
+                const uint32_t *w1q = reinterpret_cast<const uint32_t *>(smem + L.w1);
                 for (int px = cg; px < NP; px += 4) {
-                    const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
-                    const int acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
+                    int acc;
+                    if (K1 == 16) {
+                        const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
+                        acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
+                        if (NPRI > 12) acc = dp4a_ss(xv.w, w1q[3 * kDecHidden + unit], acc);
+                    } else {
+                        // a wider window: its priors as words, W1 words from shared memory
+                        acc = 0;
+                        const uint32_t *xw = reinterpret_cast<const uint32_t *>(pri + K1 * px);
+#pragma unroll 4
+                        for (int k4 = 0; k4 < K1 / 4; k4++) acc = dp4a_ss(xw[k4], w1q[k4 * kDecHidden + unit], acc);
+                    }
                     const float h = (float)requant_u8(acc, s1r, o1r);
                     const uint32_t mine = __float_as_uint(h) >> 16;   // bf16 of the integer
                     const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
@@ -784,12 +821,13 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         clo = cb[q];
                     }
                 sym = __shfl_sync(0xffffffffu, sym, Lh);
-                // the decoded pixel goes out first: the next wave of this CTA
-                // and of the next two CTAs reads it
+                // the decoded pixel goes out first: the next waves of this CTA
+                // and of the CTAs owning the rows below it read it
                 if (p2p) {
-                    if (lane < min(3, P)) {
-                        const int slot = (((r >> lgP) & tqmask) << 2) | lane;
-                        const uint32_t off = 4u * (uint32_t)(slot * 32 + (c & 31));
+                    if (lane < prm.tslots) {
+                        // row distance d = lane: the CTA k + d reads this row as r - d
+                        const int slot = ((r >> lgP) & tqmask) * prm.tslots + lane;
+                        const uint32_t off = 4u * (uint32_t)(slot * prm.tcols + (c & tcmask));
                         if (lane == 0)
                             asm volatile("st.shared::cta.u32 [%0], %1;" ::"r"(tring_addr + off), "r"(ring_tag(r, c) | sym)
                                          : "memory");
@@ -797,11 +835,11 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                             st_cluster_u32(tring_dst + off, ring_tag(r, c) | sym);
                     }
                 } else if (lane < P) {
-                    const uint32_t off = (uint32_t)(((r & rmask) << 4) + (c & 15));
+                    const uint32_t off = (uint32_t)((r & rmask) * prm.rcols + (c & rcmask));
                     if (P > 1)
                         st_cluster_u8(ring_dst + off, sym);
                     else
-                        ring[((r & rmask) << 4) + (c & 15)] = (uint8_t)sym;
+                        ring[(r & rmask) * prm.rcols + (c & rcmask)] = (uint8_t)sym;
                 }
                 f = __shfl_sync(0xffffffffu, f, Lh);
                 clo = __shfl_sync(0xffffffffu, clo, Lh);
@@ -953,18 +991,26 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     prm.h1 = m.h1;
     prm.h2 = m.h2;
     prm.nt = f32 ? 12 : min(64, (per_cta + 15) & ~15);
+    prm.k1 = (m.n_in + 15) / 16 * 16;
+    prm.tslots = m.wu + 1;
+    // ring columns kept per row: an entry must outlive its last reader,
+    // 3 (rows above) + left reach waves later (plus a writer's lead of up
+    // to P - 1 waves in the tagged ring)
+    prm.tcols = 3 * m.wu + m.wl + P + 2 <= 32 ? 32 : 64;
+    prm.rcols = 3 * m.wu + m.wl + 2 <= 16 ? 16 : 32;
     int rows = 1;
-    while (rows < min(maxH, (maxW + 2) / 3) + 4) rows <<= 1;
+    while (rows < wave_px + m.wu + 2) rows <<= 1;
     prm.ring_rows = rows;
     // Tagged ring (neighbour-to-neighbour mode) only when it stays small;
     // otherwise the kernel synchronises the cluster once per wave.  Rows
-    // sharing a tagged-ring slot are P * tq apart: more than a wave's rows
-    // plus the reach of the window and a writer's lead.
+    // sharing a tagged-ring slot are P * tq apart: more than the rows of a
+    // wave plus the rows above and a writer's lead (P - 1 waves), with a
+    // round to spare.
     int tq = 0;
     if (P >= 2) {
         tq = 1;
-        while (tq < (min(maxH, (maxW + 2) / 3) + P - 1) / P + 8) tq <<= 1;
-        if (4 * tq * 128 > 32768) tq = 0;
+        while (tq < (wave_px + m.wu + P + P - 1) / P + 1) tq <<= 1;
+        if (4 * prm.tcols * prm.tslots * tq > 48 * 1024) tq = 0;
     }
     prm.tq = tq;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
@@ -977,17 +1023,18 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     if (e != cudaSuccess) return e;
     const uint32_t limit = (uint32_t)optin > fa.sharedSizeBytes ? (uint32_t)optin - (uint32_t)fa.sharedSizeBytes : 0u;
     // smaller pixel chunks when the rings of a wide image leave no room
-    DecTcLayout L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+    prm.pay_words = 0;
+    DecTcLayout L0 = dec_layout(prm, f32);
     while (!f32 && L0.total > limit && prm.nt > 16) {
         prm.nt /= 2;
-        L0 = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, 0, f32, m.h1, m.h2);
+        L0 = dec_layout(prm, f32);
     }
     // the payload of the owned streams is staged in what shared memory is
     // left (INT8; the FP32 decoder leaves it to the L1 cache)
     const uint32_t budget = limit > 4096u ? limit - 4096u : 0u;
     prm.pay_words = !f32 && L0.total < budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
-    const DecTcLayout L = dec_layout(prm.nt, rows, 4 * prm.tq, prm.max_g, prm.pay_words, f32, m.h1, m.h2);
+    const DecTcLayout L = dec_layout(prm, f32);
     if (L.total > limit) return f32 ? launch_decode_cc(m, b, st) : cudaErrorInvalidConfiguration;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;

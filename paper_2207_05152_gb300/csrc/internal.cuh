@@ -9,7 +9,8 @@
 
 namespace dlic {
 
-constexpr int kPriors = 12;        // radius-2 causal window
+constexpr int kPriors = 12;        // priors of the default radius-2 causal window
+constexpr int kMaxPriors = 96;     // largest window: rows up <= 8, left reach <= 8, right reach <= 2
 constexpr int kSymbols = 256;      // 8-bit alphabet
 constexpr uint32_t kRansL = 1u << 16;
 constexpr uint32_t kTotal = 1u << 16;
@@ -21,6 +22,9 @@ constexpr int kMaxHidden = 256;
 struct DevModel {
     int precision;   // DLIC_FP32 / DLIC_INT8
     int h1, h2;
+    // causal window: rows r-wu..r-1 at columns c-wl..c+wr, then row r at
+    // columns c-wl..c-1 (n_in priors in that order); (2, 2, 2) by default
+    int wu, wl, wr, n_in;
     float tscale;
     const uint32_t *lut;          // 64 entries
     // FP32 network, transposed: WkT[k * out + j] = W[j][k]
@@ -87,8 +91,10 @@ dlic_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st);
 cudaError_t launch_predict_tc(const DevModel &m, const EncBatch &b, int *err, int num_sms, cudaStream_t st);
 bool tc_supported(const DevModel &m);
-size_t tc_weight_bytes(int h1, int h2);
-void tc_pack_weights(int h1, int h2, const int8_t *q1, const int8_t *q2, const int8_t *q3, uint16_t *out);
+size_t tc_weight_bytes(int h1, int h2, int k1);
+void tc_pack_weights(int h1, int h2, int n_in, int k1, const int8_t *q1, const int8_t *q2, const int8_t *q3,
+                     uint16_t *out);
+bool f32_predict_supported(const DevModel &m);
 cudaError_t launch_rans_encode(const EncBatch &b, int total_streams, cudaStream_t st);
 cudaError_t launch_pack(const DevModel &m, const EncBatch &b, uint8_t *out,
                         uint64_t *out_offsets, cudaStream_t st);
@@ -139,6 +145,19 @@ __host__ __device__ inline int64_t stream_pos(int H, int W, int S, int r, int c)
     const int64_t same_wave = (W - c - 1) / D;
     return before + (kr < same_wave ? kr : same_wave);
 }
+
+// Offsets (dr, dc) of prior q of the model's window.
+__host__ __device__ inline void window_offset(const DevModel &m, int q, int &dr, int &dc) {
+    const int wid = m.wl + m.wr + 1;
+    if (q < m.wu * wid) {
+        dr = -m.wu + q / wid;
+        dc = -m.wl + q % wid;
+    } else {
+        dr = 0;
+        dc = -m.wl + (q - m.wu * wid);
+    }
+}
+__host__ __device__ inline bool default_window(const DevModel &m) { return m.wu == 2 && m.wl == 2 && m.wr == 2; }
 
 // Index of pixel (r, c) in the stream-ordered per-pixel table buffer.
 __host__ __device__ inline int64_t stream_index(int H, int W, int S, int r, int c) {

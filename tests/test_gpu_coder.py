@@ -169,3 +169,43 @@ def test_decode_inside_cuda_graph(Codec, orc):
     torch.cuda.synchronize()
     assert int(status.item()) == 0 and torch.equal(dec, d_img)
     codec.close()
+
+
+# --- other causal windows ("any window shape", Sec. II-A; Fig. 6's 9 x 9) ---
+
+def _window_models(widths, seed, images, window):
+    from tests.helpers import calib_contexts
+    layers = synth.predictive_mlp(widths, seed, window=window)
+    return {"fp32": M.fp32_blob(layers, window),
+            "int8": M.int8_blob(layers, calib_contexts(images, window=window), window)}
+
+
+@pytest.mark.parametrize("window", [M.FIG6_WINDOW, (4, 1, 2), (1, 3, 2), (3, 1, 1)])
+@pytest.mark.parametrize("prec,h", [("int8", 128), ("fp32", 64)])
+def test_windows_match_oracle(Codec, orc, window, prec, h):
+    # tensor-core INT8 encoder and cluster decoder (first-layer K = the
+    # window's priors padded to 16; rings with one slot per row distance),
+    # FP32 tiled encoder and FP32 cluster decoder
+    n = M.window_size(window)
+    shapes = [(96, 160, 16), (1, 9, 1), (7, 1, 4), (20, 33, 5), (40, 260, 8)]
+    imgs = [synth.voronoi_image(hh, ww, 11 * hh + ww) for hh, ww, _ in shapes]
+    blob = _window_models([n, h, h, 256], 12, imgs[:1], window)[prec]
+    got = _check(Codec, orc, blob, imgs, [s for _, _, s in shapes])
+    assert all(g[12] == window[0] for g in got)
+
+
+def test_fig6_window_batched_cluster_sizes(Codec, orc):
+    # cluster sizes from 1 (byte ring, one cluster barrier per wave) to 16
+    sizes = [(30, 40), (200, 260), (16, 16), (120, 400), (300, 200), (60, 500)]
+    imgs = [synth.voronoi_image(hh, ww, 950 + i) for i, (hh, ww) in enumerate(sizes)]
+    blob = _window_models([78, 128, 128, 256], 13, imgs[:1], M.FIG6_WINDOW)["int8"]
+    _check(Codec, orc, blob, imgs, None)
+
+
+def test_window_needs_supported_kernels(Codec):
+    from paper_2207_05152_gb300 import _lib
+    img = synth.voronoi_image(40, 40, 2)
+    blob = _window_models([78, 64, 64, 256], 14, [img], M.FIG6_WINDOW)["int8"]   # INT8 decode needs 128/128
+    with pytest.raises(_lib.DlicError) as e:
+        Codec(blob)
+    assert e.value.code == _lib.DLIC_ERR_UNSUPPORTED
