@@ -257,7 +257,9 @@ __device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, i
 
 // The wavefront decoder for one image per cluster; F32 selects the FP32
 // network on the CUDA cores instead of the INT8 network on the tensor cores.
-template <bool F32>
+// DEF compiles the default window (the 12 priors of Fig. 2: two rows above,
+// two columns either side) with its sizes and offsets as constants.
+template <bool F32, bool DEF>
 __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b, const DecTcParams &prm) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
@@ -279,7 +281,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const int H = im.H, W = im.W;
     const int h1 = prm.h1, h2 = prm.h2;
     const DecTcLayout L = dec_layout(prm, F32);
-    const int K1 = prm.k1, NPRI = m.n_in;
+    const int K1 = DEF ? 16 : prm.k1, NPRI = DEF ? kPriors : m.n_in;
+    const int TSLOTS = DEF ? 3 : prm.tslots, TCOLS = DEF ? 32 : prm.tcols, RCOLS = DEF ? 16 : prm.rcols;
 
     // --- set-up: weights, parameters, tensor memory, header and streams ---
     {
@@ -437,9 +440,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const bool p2p = prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0 && W <= 4096;
     uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
     const uint32_t tring_addr = tc::smem_addr(tring);
-    const int tqmask = prm.tq - 1, tcmask = prm.tcols - 1, rcmask = prm.rcols - 1;
+    const int tqmask = prm.tq - 1, tcmask = TCOLS - 1, rcmask = RCOLS - 1;
     // gather threads per pixel: the priors and one more, rounded to a power of two
-    const int lg_slot = NPRI + 1 <= 16 ? 4 : (NPRI + 1 <= 32 ? 5 : (NPRI + 1 <= 64 ? 6 : 7));
+    const int lg_slot = DEF || NPRI + 1 <= 16 ? 4 : (NPRI + 1 <= 32 ? 5 : (NPRI + 1 <= 64 ? 6 : 7));
     const int slot_px = 1 << lg_slot;
     if (P > 1) cluster_sync_all();   // every CTA's rings are initialised
 
@@ -478,7 +481,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // the ring bases of the CTAs this lane stores to (the cluster window is
     // linear within a CTA, so the mapping is computed once)
     const uint32_t tring_dst =
-        (P > 1 && lane < prm.tslots) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
+        (P > 1 && lane < TSLOTS) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
     const uint32_t ring_dst = (P > 1 && lane < P) ? map_shared(ring_addr, (k + (uint32_t)lane) % (uint32_t)P) : ring_addr;
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     uint8_t *pri = smem + L.pri;   // priors of the chunk's pixels as s8 (x - 128), 16 bytes each
@@ -624,14 +627,22 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
                         continue;
                     }
-                    const char2 o = s_woff[q];
-                    const int dr = o.x, rr = r + dr, cc = c + o.y;
+                    int dr, dc;
+                    if (DEF) {
+                        dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
+                        dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+                    } else {
+                        const char2 o = s_woff[q];
+                        dr = o.x;
+                        dc = o.y;
+                    }
+                    const int rr = r + dr, cc = c + dc;
                     if (rr < 0 || cc < 0 || cc >= W) {
                         v = 0u;
                     } else if (p2p) {
                         // entry (round of rr, row distance, column mod tcols)
-                        const int slot = ((rr >> lgP) & tqmask) * prm.tslots - dr;
-                        const uint32_t *e = tring + slot * prm.tcols + (cc & tcmask);
+                        const int slot = ((rr >> lgP) & tqmask) * TSLOTS - dr;
+                        const uint32_t *e = tring + slot * TCOLS + (cc & tcmask);
                         const uint32_t want = ring_tag(rr, cc);
                         v = ld_volatile_u32(e);
                         if ((v & 0xFFFFFF00u) != want) {
@@ -647,9 +658,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         }
                         v &= 0xFFu;
                     } else {
-                        v = ring[(rr & rmask) * prm.rcols + (cc & rcmask)];
+                        v = ring[(rr & rmask) * RCOLS + (cc & rcmask)];
                     }
-                } else if (q == kPriors) {
+                } else if (q == NPRI) {
                     continue;
                 }
                 // network input: x/128 - 1 (FP32) or x - 128 as s8; out-of-image
@@ -824,10 +835,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 // the decoded pixel goes out first: the next waves of this CTA
                 // and of the CTAs owning the rows below it read it
                 if (p2p) {
-                    if (lane < prm.tslots) {
+                    if (lane < TSLOTS) {
                         // row distance d = lane: the CTA k + d reads this row as r - d
-                        const int slot = ((r >> lgP) & tqmask) * prm.tslots + lane;
-                        const uint32_t off = 4u * (uint32_t)(slot * prm.tcols + (c & tcmask));
+                        const int slot = ((r >> lgP) & tqmask) * TSLOTS + lane;
+                        const uint32_t off = 4u * (uint32_t)(slot * TCOLS + (c & tcmask));
                         if (lane == 0)
                             asm volatile("st.shared::cta.u32 [%0], %1;" ::"r"(tring_addr + off), "r"(ring_tag(r, c) | sym)
                                          : "memory");
@@ -835,11 +846,11 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                             st_cluster_u32(tring_dst + off, ring_tag(r, c) | sym);
                     }
                 } else if (lane < P) {
-                    const uint32_t off = (uint32_t)((r & rmask) * prm.rcols + (c & rcmask));
+                    const uint32_t off = (uint32_t)((r & rmask) * RCOLS + (c & rcmask));
                     if (P > 1)
                         st_cluster_u8(ring_dst + off, sym);
                     else
-                        ring[(r & rmask) * prm.rcols + (c & rcmask)] = (uint8_t)sym;
+                        ring[off] = (uint8_t)sym;
                 }
                 f = __shfl_sync(0xffffffffu, f, Lh);
                 clo = __shfl_sync(0xffffffffu, clo, Lh);
@@ -902,11 +913,13 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     if (P > 1) cluster_sync_all();   // no CTA leaves while others may still write its ring
 }
 
+template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<false>(m, b, prm);
+    decode_wave<false, DEF>(m, b, prm);
 }
+template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<true>(m, b, prm);
+    decode_wave<true, DEF>(m, b, prm);
 }
 
 // Cluster sizes for a batch (the decode autotuner).  A wave of an image
@@ -976,7 +989,10 @@ bool wave_decode_supported(const DevModel &m) {
 // down when a cluster that large cannot be scheduled).
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st) {
     const bool f32 = m.precision == DLIC_FP32;
-    void (*kern)(DevModel, DecBatch, DecTcParams) = f32 ? k_decode_f32 : k_decode_tc;
+    // the default window runs the instance with its sizes as constants
+    const bool def = default_window(m);
+    void (*kern)(DevModel, DecBatch, DecTcParams) =
+        f32 ? (def ? k_decode_f32<true> : k_decode_f32<false>) : (def ? k_decode_tc<true> : k_decode_tc<false>);
     if (b.n == 0) return cudaSuccess;
     int maxH = 1, maxW = 1;
     for (int i = 0; i < b.n; i++) {

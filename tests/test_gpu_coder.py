@@ -180,7 +180,7 @@ def _window_models(widths, seed, images, window):
             "int8": M.int8_blob(layers, calib_contexts(images, window=window), window)}
 
 
-@pytest.mark.parametrize("window", [M.FIG6_WINDOW, (4, 1, 2), (1, 3, 2), (3, 1, 1)])
+@pytest.mark.parametrize("window", [M.FIG6_WINDOW, (4, 1, 2), (1, 3, 2), (3, 1, 1), (1, 7, 1)])
 @pytest.mark.parametrize("prec,h", [("int8", 128), ("fp32", 64)])
 def test_windows_match_oracle(Codec, orc, window, prec, h):
     # tensor-core INT8 encoder and cluster decoder (first-layer K = the
