@@ -215,6 +215,16 @@ def run_ours(args):
 
     r8 = measure(blob8, args.steps, args.warmup, clocks=True)
     r32 = measure(blob32, max(2, args.steps // 3), 2)
+    # the same image with the 9 x 9 causal window of Fig. 6 (78 priors)
+    from paper_2207_05152_gb300 import model as M, workloads
+    _, f6_8, f6_32 = workloads.models(window=M.FIG6_WINDOW)
+    r6 = measure(f6_8, max(2, args.steps // 3), 2)
+    r6f = measure(f6_32, 2, 2)
+
+    def leg(r):
+        return {"enc_mpix_s": round(N / (statistics.mean(r["enc"]) * 1e-3) / 1e6, 3),
+                "dec_mpix_s": round(N / (statistics.mean(r["dec"]) * 1e-3) / 1e6, 3),
+                "bpp": round(8.0 * r["nbytes"] / N, 4), "roundtrip_bit_exact": r["ok"]}
 
     # end to end through the public API: pinned host image in, decoded image out
     codec = Codec(blob8)
@@ -284,9 +294,10 @@ def run_ours(args):
         "dec_mpix_s": round(N / (dec_mean * 1e-3) / 1e6, 3),
         "bpp": round(bpp, 4),
         "roundtrip_bit_exact": r8["ok"],
-        "fp32_path": {"enc_mpix_s": round(N / (statistics.mean(r32["enc"]) * 1e-3) / 1e6, 3),
-                      "dec_mpix_s": round(N / (statistics.mean(r32["dec"]) * 1e-3) / 1e6, 3),
-                      "bpp": round(8.0 * r32["nbytes"] / N, 4), "roundtrip_bit_exact": r32["ok"]},
+        "fp32_path": leg(r32),
+        "fig6_window": {"window": "9x9 of Fig. 6 (8 rows above, 6 left, 2 right: 78 priors)",
+                        "widths": [M.window_size(M.FIG6_WINDOW), 128, 128, 256],
+                        "int8": leg(r6), "fp32": leg(r6f)},
         "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},

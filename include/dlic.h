@@ -100,6 +100,21 @@ DLIC_API dlic_status dlic_model_create(const void *h_blob, size_t blob_bytes, dl
  * flight on any stream. */
 DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
 
+/* How the wavefront decoder keeps the priors of the pixels it decodes
+ * (Sec. II-B: a pixel's priors are pixels of earlier waves).
+ *  DLIC_PLAN_AUTO        the fastest plan whose shared memory fits: a
+ *                        tagged ring that CTAs of a cluster write into one
+ *                        another's shared memory (no per-wave barrier), else
+ *                        a byte ring with one cluster barrier per wave, else
+ *                        the priors read back from the output image;
+ *  DLIC_PLAN_BYTE_RING   the byte ring, or the image when it does not fit;
+ *  DLIC_PLAN_IMAGE       always the image (one cluster barrier per wave).
+ * Every plan gives the same decoded pixels; the forced plans exist to test
+ * and measure the ones AUTO takes for long waves.  Applies to later
+ * dlic_decode calls with this model; DLIC_ERR_INVALID for another value. */
+enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2 };
+DLIC_API dlic_status dlic_model_set_decode_plan(dlic_model *model, int plan);
+
 /* Precision tag, hidden widths and hash of a model. */
 DLIC_API dlic_status dlic_model_info(const dlic_model *model, int *precision, int *h1, int *h2,
                             uint64_t *hash);
@@ -204,6 +219,10 @@ DLIC_API dlic_status dlic_decode_workspace_size(const dlic_model *model, const d
  * concurrently on internal streams forked from and joined back to `stream`.
  * INT8 networks of widths 128 run on the tensor cores, FP32 networks with
  * h2 <= 128 on the CUDA cores, other networks in one CTA per image.
+ * An image whose waves (min(height, ceil(width / 3)) pixels) leave no
+ * shared-memory plan room on the cluster decoder (about 20000 pixels for
+ * INT8 networks) returns DLIC_ERR_UNSUPPORTED before anything is enqueued;
+ * the default-window FP32 decoder falls back to one CTA per image.
  * d_status (n int32, device) receives DLIC_OK or DLIC_ERR_CORRUPT per image
  * (header mismatch, model hash mismatch, stream overrun, or a final state
  * other than the initial one), or DLIC_ERR_TIMEOUT when a bounded wait of

@@ -17,6 +17,7 @@ DLIC_OK, DLIC_ERR_INVALID, DLIC_ERR_CAPACITY, DLIC_ERR_CORRUPT = 0, 1, 2, 3
 DLIC_ERR_TIMEOUT, DLIC_ERR_CUDA, DLIC_ERR_UNSUPPORTED = 4, 5, 6
 DLIC_FP32, DLIC_INT8 = 0, 1
 DLIC_TRAIN_BF16, DLIC_TRAIN_FP32, DLIC_TRAIN_BF16X3 = 0, 1, 2
+DLIC_PLAN_AUTO, DLIC_PLAN_BYTE_RING, DLIC_PLAN_IMAGE = 0, 1, 2
 
 
 class DlicError(RuntimeError):
@@ -40,6 +41,7 @@ SIGNATURES = {
     "dlic_last_error": (C.c_char_p, []),
     "dlic_model_create": (_I, [_VP, _SZ, C.POINTER(_VP)]),
     "dlic_model_destroy": (_I, [_VP]),
+    "dlic_model_set_decode_plan": (_I, [_VP, _I]),
     "dlic_model_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_uint64)]),
     "dlic_max_encoded_bytes": (_SZ, [_I, _I, _I]),
     "dlic_auto_streams": (_I, [_I, _I]),
@@ -115,6 +117,10 @@ def dlic_model_create(blob: bytes) -> int:
 
 def dlic_model_destroy(model: int):
     check(lib().dlic_model_destroy(model))
+
+
+def dlic_model_set_decode_plan(model: int, plan: int):
+    check(lib().dlic_model_set_decode_plan(model, plan))
 
 
 def dlic_model_info(model: int):

@@ -17,12 +17,14 @@ class Codec:
     """One coder model on the current CUDA device (Sec. II-B: the same model
     and the same arithmetic at encode and decode)."""
 
-    def __init__(self, blob: bytes):
+    def __init__(self, blob: bytes, decode_plan: int = _lib.DLIC_PLAN_AUTO):
         if not torch.cuda.is_available():
             raise RuntimeError("the DLIC library needs a CUDA device")
         self.blob = bytes(blob)
         self.handle = _lib.dlic_model_create(self.blob)
         self.precision, self.h1, self.h2, self.hash = _lib.dlic_model_info(self.handle)
+        if decode_plan != _lib.DLIC_PLAN_AUTO:
+            _lib.dlic_model_set_decode_plan(self.handle, decode_plan)
         self._ws = None
 
     def close(self):

@@ -62,6 +62,7 @@ struct dlic_model {
     // forked from and joined back to the caller's stream
     cudaStream_t group_stream[kDecodeGroups] = {};
     cudaEvent_t fork_event = nullptr, join_event[kDecodeGroups] = {};
+    int decode_plan = DLIC_PLAN_AUTO;
 };
 
 extern "C" const char *dlic_last_error(void) { return g_err; }
@@ -224,6 +225,14 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         }
     }
     *out = m;
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_model_set_decode_plan(dlic_model *m, int plan) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (plan != DLIC_PLAN_AUTO && plan != DLIC_PLAN_BYTE_RING && plan != DLIC_PLAN_IMAGE)
+        return fail(DLIC_ERR_INVALID, "unknown decode plan %d", plan);
+    m->decode_plan = plan;
     return DLIC_OK;
 }
 
@@ -434,7 +443,14 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         Hs[i] = im[i].height;
         Ws[i] = im[i].width;
     }
-    if (use_wave) choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
+    if (use_wave) {
+        choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
+        // checked before anything is enqueued
+        for (int i = 0; i < n; i++)
+            if (!wave_decode_fits(m->dev, Hs[i], Ws[i], P[i], m->decode_plan))
+                return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d has waves too long for the decoder's shared memory",
+                            i, Hs[i], Ws[i]);
+    }
     int groups_used = 0;
     for (int gi = 0; gi < kDecodeGroups; gi++)
         for (int i = 0; i < n; i++)
@@ -451,6 +467,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
     // a group the longest images first, so that CTAs beyond one per SM queue
     // behind them
     const bool f32 = m->dev.precision == DLIC_FP32;
+    dlic_status err = DLIC_OK;
     for (int gi = kDecodeGroups - 1; gi >= 0; gi--) {
         const int cluster = 1 << gi;
         std::vector<int> members;
@@ -486,15 +503,21 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
                 e.st_off = st_off[i];
                 e.sidx = i;
             }
-            cudaError_t e = use_wave ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, gs) : launch_decode_cc(m->dev, *b, gs);
+            cudaError_t e = use_wave ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs) : launch_decode_cc(m->dev, *b, gs);
             delete b;
-            if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+            if (e != cudaSuccess && err == DLIC_OK)
+                err = e == cudaErrorNotSupported ? fail(DLIC_ERR_UNSUPPORTED, "decode launch: no shared-memory plan fits")
+                                                 : cuda_fail(e, "decode launch");
+            if (err != DLIC_OK) break;
         }
+        // a forked group joins the caller's stream even after an error, so
+        // that nothing launched outlives the call's ordering
         if (fork) {
             cudaError_t e = cudaEventRecord(m->join_event[gi], gs);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, m->join_event[gi], 0);
-            if (e != cudaSuccess) return cuda_fail(e, "join");
+            if (e != cudaSuccess && err == DLIC_OK) err = cuda_fail(e, "join");
         }
+        if (err != DLIC_OK) break;
     }
-    return DLIC_OK;
+    return err;
 }

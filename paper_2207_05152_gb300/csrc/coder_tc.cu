@@ -86,6 +86,8 @@ __device__ __forceinline__ void requant_store16(const uint32_t (&v)[16], const f
         make_uint4(packed[4], packed[5], packed[6], packed[7]);
 }
 
+// DEF: the default window of 12 priors (K1 = 16, offsets as constants).
+template <bool DEF>
 __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatch b, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bars[kTcSlots];
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
     const int slot = wg & 1, half = wg >> 1;
     const int h1 = m.h1, h2 = m.h2;
-    const int K1 = (m.n_in + 15) / 16 * 16;
+    const int NPRI = DEF ? kPriors : m.n_in, K1 = DEF ? 16 : (m.n_in + 15) / 16 * 16;
     const TcLayout L = tc_layout(h1, h2, K1);
 
     // weights (already in operand layout) and epilogue parameters
@@ -186,9 +188,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
                 for (int hb = 0; hb < 2; hb++) {
                     const int q = 8 * j + 2 * e + hb;
                     uint32_t v = 0u;
-                    if (active && q < m.n_in) {
-                        const char2 o = s_woff[q];
-                        const int rr = r + o.x, cc = c + o.y;
+                    if (active && q < NPRI) {
+                        int dr, dc;
+                        if (DEF) {
+                            dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
+                            dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+                        } else {
+                            const char2 o = s_woff[q];
+                            dr = o.x;
+                            dc = o.y;
+                        }
+                        const int rr = r + dr, cc = c + dc;
                         const int pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[(int64_t)rr * im.pitch + cc] : 0;
                         v = tc::bf16_of_int(pv - 128);
                     }
@@ -314,12 +324,13 @@ void tc_pack_weights(int h1, int h2, int n_in, int k1, const int8_t *q1, const i
 cudaError_t launch_predict_tc(const DevModel &m, const EncBatch &b, int *err, int num_sms, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
     const TcLayout L = tc_layout(m.h1, m.h2, (m.n_in + 15) / 16 * 16);
-    cudaError_t e = cudaFuncSetAttribute(k_encode_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    void (*kern)(DevModel, EncBatch, int *) = default_window(m) ? k_encode_tc<true> : k_encode_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     const int per_cta = kTcSlots;
     int grid = (b.total_tiles + per_cta - 1) / per_cta;
     if (grid > num_sms) grid = num_sms;
-    k_encode_tc<<<grid, kTcThreads, L.total, st>>>(m, b, err);
+    kern<<<grid, kTcThreads, L.total, st>>>(m, b, err);
     return cudaGetLastError();
 }
 

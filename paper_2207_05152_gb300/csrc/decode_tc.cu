@@ -45,7 +45,8 @@ struct DecTcParams {
     int P;            // CTAs per image (cluster size)
     int h1, h2;       // hidden widths (FP32 network)
     int nt;           // pixels per chunk (multiple of 16, <= 128)
-    int ring_rows;    // power of two
+    int ring_rows;    // byte-ring rows (power of two); 0 with gimg
+    int list_rows;    // capacity of the per-wave row list and decoded-pixel buffer
     int tq;           // tagged ring: row rounds kept (power of two)
     int max_g;        // owned streams per CTA (upper bound)
     int pay_words;    // staged payload capacity per CTA (words); 0 = read from global
@@ -53,6 +54,8 @@ struct DecTcParams {
     int tslots;       // tagged-ring slots per row round: one per row distance 0..rows above
     int tcols;        // tagged-ring columns kept per row (power of two)
     int rcols;        // byte-ring columns kept per row (power of two)
+    int gimg;         // 1: priors are read back from the output image (no ring; one
+                      // cluster barrier per wave), for waves too long for the rings
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -63,10 +66,11 @@ __host__ __device__ inline uint32_t dec_f32_weight_floats(int n_in, int h1, int 
     return (uint32_t)(n_in * h1 + h1 + h2 + kSymbols);
 }
 
-// Shared-memory plan for chunks of up to nt pixels, `rows` ring rows (also
-// the bound on the pixels of one wave), `tslots` tagged-ring rows, `g` owned
-// streams and `pay_words` staged payload words, for the INT8 tensor-core
-// network or (f32) the FP32 network of widths h1, h2.
+// Shared-memory plan of a CTA: chunks of up to nt pixels, the byte ring
+// (ring_rows x rcols), the tagged ring (tq rounds x tslots x tcols words),
+// the wave's row list, max_g owned streams and pay_words staged payload
+// words, for the INT8 tensor-core network or (f32) the FP32 network of
+// widths h1, h2.
 __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f32) {
     const int nt = prm.nt, rows = prm.ring_rows, g = prm.max_g, pay_words = prm.pay_words, h1 = prm.h1, h2 = prm.h2;
     DecTcLayout L{};
@@ -97,11 +101,11 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.b23 = take(2u * nt * kDecHidden);
     }
     if (!f32) L.z = take(4u * nt * kSymbols);
-    L.ring = take((uint32_t)prm.rcols * rows);
-    L.tring = take(4u * prm.tcols * prm.tslots * prm.tq);
-    L.rows = take(4u * rows);
+    L.ring = take(prm.gimg ? 0u : (uint32_t)prm.rcols * rows);
+    L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
+    L.rows = take(4u * prm.list_rows);
     L.pg = take(4u * nt);
-    L.dsym = take(rows);
+    L.dsym = take(prm.gimg ? 0u : (uint32_t)prm.list_rows);   // decoded pixels held back until the barrier
     L.lut = take(4u * 64);
     L.st_x = take(4u * g);
     L.st_pos = take(4u * g);
@@ -437,7 +441,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // more than a wave's rows apart.
     // (the tags hold 11 bits of the row and 12 of the column: wider images
     // use the byte ring)
-    const bool p2p = prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0 && W <= 4096;
+    const bool gimg = prm.gimg != 0;
+    const bool p2p = !gimg && prm.tq > 0 && P >= 2 && P <= 16 && (S % P) == 0 && W <= 4096;
     uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
     const uint32_t tring_addr = tc::smem_addr(tring);
     const int tqmask = prm.tq - 1, tcmask = TCOLS - 1, rcmask = RCOLS - 1;
@@ -575,7 +580,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const bool modrows = (S % P) == 0;
     // Without a per-wave cluster barrier a decoded pixel goes to the image
     // at once; otherwise the stores wait until the barrier has been arrived at.
-    const bool direct = p2p || P == 1;
+    const bool direct = p2p || P == 1 || gimg;
     for (int t = 0; t < T; t++) {
         const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
         const int r_hi = min(H - 1, t / 3);
@@ -657,6 +662,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                             } while ((v & 0xFFFFFF00u) != want);
                         }
                         v &= 0xFFu;
+                    } else if (gimg) {
+                        // stored to the image before the last wave's barrier
+                        v = __ldcg(im.pixels + (int64_t)rr * im.pitch + cc);
                     } else {
                         v = ring[(rr & rmask) * RCOLS + (cc & rcmask)];
                     }
@@ -845,7 +853,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         else
                             st_cluster_u32(tring_dst + off, ring_tag(r, c) | sym);
                     }
-                } else if (lane < P) {
+                } else if (!gimg && lane < P) {
                     const uint32_t off = (uint32_t)((r & rmask) * RCOLS + (c & rcmask));
                     if (P > 1)
                         st_cluster_u8(ring_dst + off, sym);
@@ -886,6 +894,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
             __syncthreads();   // the row list is rebuilt only after every image store
             asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else if (gimg && P > 1) {
+            // every CTA's image stores of this wave before any CTA's next gather
+            cluster_sync_all();
         } else if (!modrows) {
             __syncthreads();   // the row list is rebuilt only after every reader is done
         }
@@ -985,24 +996,35 @@ bool wave_decode_supported(const DevModel &m) {
            m.h2 % 4 == 0;
 }
 
-// Launches one cluster of `cluster` CTAs per image of the batch (stepping
-// down when a cluster that large cannot be scheduled).
-cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st) {
-    const bool f32 = m.precision == DLIC_FP32;
+static void (*wave_kernel(const DevModel &m))(DevModel, DecBatch, DecTcParams) {
     // the default window runs the instance with its sizes as constants
     const bool def = default_window(m);
-    void (*kern)(DevModel, DecBatch, DecTcParams) =
-        f32 ? (def ? k_decode_f32<true> : k_decode_f32<false>) : (def ? k_decode_tc<true> : k_decode_tc<false>);
-    if (b.n == 0) return cudaSuccess;
-    int maxH = 1, maxW = 1;
-    for (int i = 0; i < b.n; i++) {
-        maxH = max(maxH, b.img[i].H);
-        maxW = max(maxW, b.img[i].W);
-    }
-    int P = cluster > 0 ? cluster : 1;
-    const int wave_px = min(maxH, (maxW + 2) / 3);
+    if (m.precision == DLIC_FP32) return def ? k_decode_f32<true> : k_decode_f32<false>;
+    return def ? k_decode_tc<true> : k_decode_tc<false>;
+}
+
+// Dynamic shared memory a CTA of the kernel may take next to its static arrays.
+static cudaError_t smem_limit(void (*kern)(DevModel, DecBatch, DecTcParams), uint32_t &limit) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    limit = (uint32_t)optin > fa.sharedSizeBytes ? (uint32_t)optin - (uint32_t)fa.sharedSizeBytes : 0u;
+    return cudaSuccess;
+}
+
+// Shared-memory plan for images up to maxH x maxW in clusters of P CTAs
+// within `limit` bytes.  In order of preference: the tagged ring; (INT8)
+// smaller pixel chunks; the byte ring with one cluster barrier per wave;
+// priors read back from the output image.  False when none fits.
+static bool plan_wave(const DevModel &m, int maxH, int maxW, int P, uint32_t limit, int plan, DecTcParams &prm) {
+    const bool f32 = m.precision == DLIC_FP32;
+    const int wave_px = min(maxH, (maxW + 2) / 3);   // rows of the longest wave
     const int per_cta = (wave_px + P - 1) / P + 1;
-    DecTcParams prm;
+    prm = DecTcParams{};
     prm.P = P;
     prm.h1 = m.h1;
     prm.h2 = m.h2;
@@ -1017,41 +1039,63 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     int rows = 1;
     while (rows < wave_px + m.wu + 2) rows <<= 1;
     prm.ring_rows = rows;
-    // Tagged ring (neighbour-to-neighbour mode) only when it stays small;
-    // otherwise the kernel synchronises the cluster once per wave.  Rows
-    // sharing a tagged-ring slot are P * tq apart: more than the rows of a
-    // wave plus the rows above and a writer's lead (P - 1 waves), with a
-    // round to spare.
+    prm.list_rows = (wave_px + 15) & ~15;
+    // Tagged ring (neighbour-to-neighbour mode) only when it stays small.
+    // Rows sharing a tagged-ring slot are P * tq apart: more than the rows
+    // of a wave plus the rows above and a writer's lead (P - 1 waves), with
+    // a round to spare.
     int tq = 0;
     if (P >= 2) {
         tq = 1;
         while (tq < (wave_px + m.wu + P + P - 1) / P + 1) tq <<= 1;
         if (4 * prm.tcols * prm.tslots * tq > 48 * 1024) tq = 0;
     }
-    prm.tq = tq;
+    prm.tq = plan == DLIC_PLAN_AUTO ? tq : 0;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
-    // dynamic shared memory available next to the kernel's static arrays
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-    if (e != cudaSuccess) return e;
-    const uint32_t limit = (uint32_t)optin > fa.sharedSizeBytes ? (uint32_t)optin - (uint32_t)fa.sharedSizeBytes : 0u;
-    // smaller pixel chunks when the rings of a wide image leave no room
     prm.pay_words = 0;
-    DecTcLayout L0 = dec_layout(prm, f32);
-    while (!f32 && L0.total > limit && prm.nt > 16) {
-        prm.nt /= 2;
-        L0 = dec_layout(prm, f32);
+    auto size = [&] { return dec_layout(prm, f32).total; };
+    while (!f32 && size() > limit && prm.nt > 16) prm.nt /= 2;
+    if (size() > limit) prm.tq = 0;
+    if (size() > limit || plan == DLIC_PLAN_IMAGE) {
+        prm.gimg = 1;
+        prm.ring_rows = 0;
     }
+    if (size() > limit) return false;
     // the payload of the owned streams is staged in what shared memory is
     // left (INT8; the FP32 decoder leaves it to the L1 cache)
-    const uint32_t budget = limit > 4096u ? limit - 4096u : 0u;
-    prm.pay_words = !f32 && L0.total < budget ? (int)((budget - L0.total) / 2) & ~63 : 0;
+    const uint32_t base = size(), budget = limit > 4096u ? limit - 4096u : 0u;
+    prm.pay_words = !f32 && base < budget ? (int)((budget - base) / 2) & ~63 : 0;
     if (prm.pay_words > 65536) prm.pay_words = 65536;
+    return true;
+}
+
+bool wave_decode_fits(const DevModel &m, int H, int W, int P, int plan) {
+    if (m.precision == DLIC_FP32 && default_window(m)) return true;   // the one-CTA decoder takes the rest
+    uint32_t limit = 0;
+    DecTcParams prm;
+    return smem_limit(wave_kernel(m), limit) == cudaSuccess && plan_wave(m, H, W, P, limit, plan, prm);
+}
+
+// Launches one cluster of `cluster` CTAs per image of the batch (stepping
+// down when a cluster that large cannot be scheduled).
+cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan,
+                             cudaStream_t st) {
+    const bool f32 = m.precision == DLIC_FP32;
+    void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m);
+    if (b.n == 0) return cudaSuccess;
+    int maxH = 1, maxW = 1;
+    for (int i = 0; i < b.n; i++) {
+        maxH = max(maxH, b.img[i].H);
+        maxW = max(maxW, b.img[i].W);
+    }
+    int P = cluster > 0 ? cluster : 1;
+    uint32_t limit = 0;
+    cudaError_t e = smem_limit(kern, limit);
+    if (e != cudaSuccess) return e;
+    DecTcParams prm;
+    if (!plan_wave(m, maxH, maxW, P, limit, plan, prm))
+        return f32 && default_window(m) ? launch_decode_cc(m, b, st) : cudaErrorNotSupported;
     const DecTcLayout L = dec_layout(prm, f32);
-    if (L.total > limit) return f32 ? launch_decode_cc(m, b, st) : cudaErrorInvalidConfiguration;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1079,7 +1123,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     }
     if (P != prm.P) {
         // smaller clusters hold more streams and pixels per CTA
-        return launch_decode_tc(m, b, P, num_sms, st);
+        return launch_decode_tc(m, b, P, num_sms, plan, st);
     }
     return cudaLaunchKernelEx(&cfg, kern, m, b, prm);
 }

@@ -102,8 +102,10 @@ cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st)
 // Decoders (coder_cc.cu: one CTA per image; decode_tc.cu: one cluster per
 // image, wavefront)
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
-cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, cudaStream_t st);
+cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);
+// whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)
+bool wave_decode_fits(const DevModel &m, int H, int W, int P, int plan);
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
 double decode_estimate(int H, int W, int P, bool f32);   // cycles, the autotuner's cost model
 

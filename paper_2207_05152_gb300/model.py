@@ -51,6 +51,16 @@ def window_size(window) -> int:
     return u * (l + r + 1) + l
 
 
+def window_offsets(window) -> list:
+    """(row, column) offset of every prior of the causal window (u rows
+    above, l columns left, r right; Sec. II-A), in the network's input
+    order: the rows above top to bottom, each left to right, then the l
+    pixels left of the target."""
+    u, l, r = window
+    span = l + r + 1
+    return [(k // span - u, k % span - l) for k in range(u * span)] + [(0, k - l) for k in range(l)]
+
+
 def window_field(window) -> int:
     """The blob's window field: 2 for the default window, else the packed
     (u, l, r)."""

@@ -2,6 +2,8 @@
 
 cfg2: one 512 x 512 Voronoi image, INT8 (and FP32) network 12-128-128-256
       with synthetic predictive weights, 256 rANS streams.
+fig6: the cfg2 image and streams with the 9 x 9 causal window of Fig. 6
+      (78 priors), network 78-128-128-256.
 cfg4: a batch of Voronoi images of uneven sizes (default 64, heights
       192..1536, widths 256..2048), the same INT8 network, automatic streams.
 """
@@ -15,23 +17,29 @@ from . import model as M
 WIDTHS = [12, 128, 128, 256]
 
 
-def calibration_contexts(seed: int = 4242, count: int = 4096) -> np.ndarray:
-    """Priors of `count` pixels of a separate synthetic image (zero-padded),
-    the calibration data of the INT8 quantisation."""
+def calibration_contexts(seed: int = 4242, count: int = 4096, window=M.DEFAULT_WINDOW) -> np.ndarray:
+    """Priors of `count` pixels of a separate synthetic image (0 outside
+    it), the calibration data of the INT8 quantisation."""
     cal_img = synth.voronoi_image(256, 256, seed)
     rng = synth.Rng(seed + 1)
     rr = rng.integers(count, 0, 255)
     cc = rng.integers(count, 0, 255)
-    pad = np.zeros((258, 260), np.uint8)
-    pad[2:, 2:258] = cal_img
-    return np.stack([np.concatenate([pad[r:r + 2, c:c + 5].reshape(-1), pad[r + 2, c:c + 2]])
-                     for r, c in zip(rr, cc)])
+    offs = M.window_offsets(window)
+    out = np.zeros((count, len(offs)), np.uint8)
+    for n, (r, c) in enumerate(zip(rr, cc)):
+        for k, (dr, dc) in enumerate(offs):
+            y, x = int(r) + dr, int(c) + dc
+            if 0 <= y < 256 and 0 <= x < 256:
+                out[n, k] = cal_img[y, x]
+    return out
 
 
-def models(seed: int = 2):
-    """(layers, INT8 blob, FP32 blob) of the synthetic predictive network."""
-    layers = synth.predictive_mlp(WIDTHS, seed)
-    return layers, M.int8_blob(layers, calibration_contexts()), M.fp32_blob(layers)
+def models(seed: int = 2, window=M.DEFAULT_WINDOW, hidden: int = 128):
+    """(layers, INT8 blob, FP32 blob) of the synthetic predictive network
+    over the causal window (u, l, r)."""
+    layers = synth.predictive_mlp([M.window_size(window), hidden, hidden, 256], seed, window=window)
+    return (layers, M.int8_blob(layers, calibration_contexts(window=window), window),
+            M.fp32_blob(layers, window))
 
 
 def cfg2_image() -> np.ndarray:

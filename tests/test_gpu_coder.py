@@ -209,3 +209,71 @@ def test_window_needs_supported_kernels(Codec):
     with pytest.raises(_lib.DlicError) as e:
         Codec(blob)
     assert e.value.code == _lib.DLIC_ERR_UNSUPPORTED
+
+
+# --- decoder prior plans (tagged ring, byte ring, read back from the image) ---
+
+@pytest.mark.parametrize("plan", ["byte_ring", "image"])
+@pytest.mark.parametrize("prec,h,window", [("int8", 128, M.DEFAULT_WINDOW), ("fp32", 64, M.DEFAULT_WINDOW),
+                                           ("int8", 128, M.FIG6_WINDOW), ("fp32", 64, M.FIG6_WINDOW)])
+def test_forced_decode_plans(Codec, orc, plan, prec, h, window):
+    # every plan decodes the same pixels; cluster sizes 1 to 16 over the batch
+    from paper_2207_05152_gb300 import _lib
+    sizes = [(96, 160), (1, 9), (7, 1), (20, 33), (200, 260), (120, 400), (300, 200), (16, 16)]
+    imgs = [synth.voronoi_image(hh, ww, 31 * hh + ww) for hh, ww in sizes]
+    blob = _window_models([M.window_size(window), h, h, 256], 15, imgs[:1], window)[prec]
+    code = {"byte_ring": _lib.DLIC_PLAN_BYTE_RING, "image": _lib.DLIC_PLAN_IMAGE}[plan]
+    codec = Codec(blob, decode_plan=code)
+    dev = [torch.from_numpy(i).cuda() for i in imgs]
+    got = codec.encode_to_bytes(dev, None)
+    for k, img in enumerate(imgs):
+        assert got[k] == orc.encode(blob, img, _lib.dlic_auto_streams(*img.shape))
+    dec, status = codec.decode_bytes(got)
+    assert status == [0] * len(imgs)
+    for k, img in enumerate(imgs):
+        assert np.array_equal(dec[k], img), f"image {k} {img.shape}"
+    codec.close()
+
+
+def test_long_waves_read_priors_from_image():
+    # 4096 x 12288: waves of 4096 pixels are too long for the rings, so the
+    # cluster decoder reads priors back from the output image; the round trip
+    # must be lossless (a property that holds at any size)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_05152_gb300.codec import Codec as C
+    tile = synth.voronoi_image(512, 768, 77)
+    img = np.ascontiguousarray(np.tile(tile, (8, 16)))
+    img[::7, ::5] ^= 0x55                     # break the tiling's periodicity
+    blob = _models([12, 128, 128, 256], 16, [tile])["int8"]
+    codec = C(blob)
+    d = torch.from_numpy(img).cuda()
+    out, offs = codec.encode([d], None)
+    o = offs.cpu().tolist()
+    dec = torch.empty_like(d)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    codec.decode(out, o, [img.shape], outs=[dec], status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and torch.equal(dec, d)
+    codec.close()
+
+
+def test_waves_beyond_every_plan_are_refused(Codec):
+    # 30000 x 90000: no shared-memory plan holds a wave's rows; the call
+    # fails on the host before anything is enqueued (the buffers are real
+    # and large enough all the same)
+    from paper_2207_05152_gb300 import _lib
+    blob = _models([12, 128, 128, 256], 17, [synth.voronoi_image(40, 40, 3)])["int8"]
+    codec = Codec(blob)
+    H, W = 30000, 90000
+    out = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    data = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = codec._workspace(_lib.dlic_decode_workspace_size(codec.handle, codec._desc([out])))
+    with pytest.raises(_lib.DlicError) as e:
+        _lib.dlic_decode(codec.handle, data.data_ptr(), [0, data.numel()], codec._desc([out]), st.data_ptr(),
+                         ws.data_ptr(), ws.numel(), 0)
+    assert e.value.code == _lib.DLIC_ERR_UNSUPPORTED
+    codec.close()
+    del out
+    torch.cuda.empty_cache()
