@@ -738,28 +738,47 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 f32_logits(tid, NG, w3_chunks, w3_seq, w3_issue, h2, b3s, h2t, PT, smem + L.w3s, w3bar, zb, s_fail);
                 __syncthreads();
             } else {
-                // 2. the three layers: the first (K = 12) as dp4a on the CUDA
-                //    cores, thread = (unit, pixel group); exact integer sums
-                //    requantised like the tensor-core epilogues
+                // 2. the three layers: the first (K = the window's priors) as
+                //    dp4a on the CUDA cores, exact integer sums requantised like
+                //    the tensor-core epilogues.  Thread = (unit, pixel group):
+                //    four pixels of the group at a time (NP is a multiple of 16),
+                //    their dot products interleaved
                 const uint32_t *w1q = reinterpret_cast<const uint32_t *>(smem + L.w1);
-                for (int px = cg; px < NP; px += 4) {
-                    int acc;
+                const uint32_t w1d = K1 == 16 && NPRI > 12 ? w1q[3 * kDecHidden + unit] : 0u;
+                for (int p0 = cg; p0 < NP; p0 += 16) {
+                    int acc[4];
                     if (K1 == 16) {
-                        const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * px);
-                        acc = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
-                        if (NPRI > 12) acc = dp4a_ss(xv.w, w1q[3 * kDecHidden + unit], acc);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const uint4 xv = *reinterpret_cast<const uint4 *>(pri + 16 * (p0 + 4 * j));
+                            acc[j] = dp4a_ss(xv.z, w1c, dp4a_ss(xv.y, w1b, dp4a_ss(xv.x, w1a, 0)));
+                            if (NPRI > 12) acc[j] = dp4a_ss(xv.w, w1d, acc[j]);
+                        }
                     } else {
                         // a wider window: its priors as words, W1 words from shared memory
-                        acc = 0;
-                        const uint32_t *xw = reinterpret_cast<const uint32_t *>(pri + K1 * px);
-#pragma unroll 4
-                        for (int k4 = 0; k4 < K1 / 4; k4++) acc = dp4a_ss(xw[k4], w1q[k4 * kDecHidden + unit], acc);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) acc[j] = 0;
+                        for (int k16 = 0; k16 < K1 / 16; k16++) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 4; e++) w[e] = w1q[(4 * k16 + e) * kDecHidden + unit];
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                const uint4 xv = *reinterpret_cast<const uint4 *>(pri + K1 * (p0 + 4 * j) + 16 * k16);
+                                acc[j] = dp4a_ss(xv.w, w[3], dp4a_ss(xv.z, w[2], dp4a_ss(xv.y, w[1], dp4a_ss(xv.x, w[0], acc[j]))));
+                            }
+                        }
                     }
-                    const float h = (float)requant_u8(acc, s1r, o1r);
-                    const uint32_t mine = __float_as_uint(h) >> 16;   // bf16 of the integer
-                    const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                    if ((lane & 1) == 0)
-                        *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(px, unit, kDecHidden)) = mine | (other << 16);
+                    uint32_t mine[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) mine[j] = __float_as_uint((float)requant_u8(acc[j], s1r, o1r)) >> 16;   // bf16 of the integer
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const uint32_t other = __shfl_xor_sync(0xffffffffu, mine[j], 1);
+                        if ((lane & 1) == 0)
+                            *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(p0 + 4 * j, unit, kDecHidden)) =
+                                mine[j] | (other << 16);
+                    }
                 }
                 run_layer(2, NP);
                 hidden_epilogue(NP, s2r, o2r, true);
