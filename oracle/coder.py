@@ -67,6 +67,13 @@ def lib():
                                     C.c_size_t]
             L.or_decode.restype = C.c_int
             L.or_decode.argtypes = [U8P, C.c_size_t, U8P, C.c_size_t, U8P, C.c_int, C.c_int]
+            L.or_gather_window3.restype = C.c_int
+            L.or_gather_window3.argtypes = [C.c_int] * 7 + [U8P, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
+            L.or_encode_volume.restype = C.c_int64
+            L.or_encode_volume.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P,
+                                           C.c_size_t, U64P]
+            L.or_decode_volume.restype = C.c_int
+            L.or_decode_volume.argtypes = [U8P, C.c_size_t, U8P, U64P, C.c_int, U8P, C.c_int, C.c_int]
             _lib = L
     return _lib
 
@@ -102,6 +109,20 @@ def gather_window(window, img: np.ndarray, r: int, c: int) -> np.ndarray:
     out = np.zeros(u * (l + rr + 1) + l, np.uint8)
     n = lib().or_gather_window(u, l, rr, _p(img, U8P), img.shape[0], img.shape[1], r, c, _p(out, U8P))
     assert n == out.size
+    return out
+
+
+def gather_window3(window, below, img: np.ndarray, r: int, c: int) -> np.ndarray:
+    """Priors of pixel (r, c) of a slice for the 3D window (u, l, r_reach,
+    pu, pd, pl, pr); below is the previous slice, or None for the first."""
+    u, l, rr, pu, pd, pl, pr = window
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    n = u * (l + rr + 1) + l + (pu + pd + 1) * (pl + pr + 1)
+    out = np.zeros(n, np.uint8)
+    bp = _p(np.ascontiguousarray(below, dtype=np.uint8), U8P) if below is not None else None
+    got = lib().or_gather_window3(u, l, rr, pu, pd, pl, pr, bp, _p(img, U8P), img.shape[0], img.shape[1], r, c,
+                                  _p(out, U8P))
+    assert got == n
     return out
 
 
@@ -201,3 +222,29 @@ def decode(blob: bytes, data: bytes, H: int, W: int):
     img = np.zeros((H, W), np.uint8)
     st = lib().or_decode(_p(b, U8P), b.size, _p(d, U8P), n, _p(img, U8P), H, W)
     return int(st), img
+
+
+def encode_volume(blob: bytes, vol: np.ndarray, streams: int):
+    """(bytes, offsets): the D slice containers of a volume (D x H x W)
+    coded with a 3D window, back to back, and the D + 1 byte offsets."""
+    b = _bytes(blob)
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    D, H, W = vol.shape
+    cap = D * max_encoded_bytes(H, W, streams)
+    out = np.zeros(cap, np.uint8)
+    offs = np.zeros(D + 1, np.uint64)
+    n = lib().or_encode_volume(_p(b, U8P), b.size, _p(vol, U8P), D, H, W, streams, _p(out, U8P), cap,
+                               _p(offs, U64P))
+    if n < 0:
+        raise ValueError(f"oracle encode error {-n}")
+    return out[:n].tobytes(), [int(o) for o in offs]
+
+
+def decode_volume(blob: bytes, data: bytes, offsets, D: int, H: int, W: int):
+    """(status, volume D x H x W) of a volume coded by encode_volume."""
+    b = _bytes(blob)
+    d = _bytes(data) if len(data) else np.zeros(1, np.uint8)
+    offs = np.asarray(offsets, dtype=np.uint64)
+    vol = np.zeros((D, H, W), np.uint8)
+    st = lib().or_decode_volume(_p(b, U8P), b.size, _p(d, U8P), _p(offs, U64P), D, _p(vol, U8P), H, W)
+    return int(st), vol

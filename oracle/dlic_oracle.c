@@ -43,8 +43,12 @@
 /* ------------------------------------------------------------------ */
 
 /* Causal window: rows r-u .. r-1 at columns c-l .. c+r, then row r at
- * columns c-l .. c-1 (n = u (l + r + 1) + l priors, in that order). */
-typedef struct { int u, l, r, n; } window_t;
+ * columns c-l .. c-1 (n2 = u (l + r + 1) + l priors, in that order).  A 3D
+ * window (Sec. IV "3D Dependencies": two layers, the lower one may reach
+ * below the target's row) adds, from the previous slice, rows r-pu .. r+pd
+ * at columns c-pl .. c+pr, row by row, left to right: n = n2 + n3 priors,
+ * n3 = (pu + pd + 1)(pl + pr + 1). */
+typedef struct { int u, l, r, n2, pu, pd, pl, pr, n3, n, vol; } window_t;
 
 typedef struct {
     int precision;               /* 0 = FP32, 1 = INT8 */
@@ -96,16 +100,26 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     /* window field: 2 = the default radius-2 window; otherwise
      * 1 << 24 | u | l << 8 | r << 16 with 1 <= u <= 8, l <= 8 and r <= 2
      * (a right reach of at most 2 keeps every prior on an earlier wave of
-     * t = 3 row + column) */
+     * t = 3 row + column).
+     * A 3D window: 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 |
+     * pl << 18 | pr << 22 (4 bits each, r 2 bits), pu, pd, pl, pr <= 8. */
     if (radius == 2) {
         m->win.u = 2; m->win.l = 2; m->win.r = 2;
     } else if ((radius >> 24) == 1) {
         m->win.u = (int)(radius & 0xFF); m->win.l = (int)((radius >> 8) & 0xFF); m->win.r = (int)((radius >> 16) & 0xFF);
-        if (m->win.u < 1 || m->win.u > 8 || m->win.l > 8 || m->win.r > 2) return OR_ERR_INVALID;
+    } else if ((radius >> 28) == 2 && ((radius >> 26) & 3) == 0) {
+        m->win.u = (int)(radius & 0xF); m->win.l = (int)((radius >> 4) & 0xF); m->win.r = (int)((radius >> 8) & 3);
+        m->win.pu = (int)((radius >> 10) & 0xF); m->win.pd = (int)((radius >> 14) & 0xF);
+        m->win.pl = (int)((radius >> 18) & 0xF); m->win.pr = (int)((radius >> 22) & 0xF);
+        if (m->win.pu > 8 || m->win.pd > 8 || m->win.pl > 8 || m->win.pr > 8) return OR_ERR_INVALID;
+        m->win.vol = 1;
+        m->win.n3 = (m->win.pu + m->win.pd + 1) * (m->win.pl + m->win.pr + 1);
     } else {
         return OR_ERR_INVALID;
     }
-    m->win.n = m->win.u * (m->win.l + m->win.r + 1) + m->win.l;
+    if (m->win.u < 1 || m->win.u > 8 || m->win.l > 8 || m->win.r > 2) return OR_ERR_INVALID;
+    m->win.n2 = m->win.u * (m->win.l + m->win.r + 1) + m->win.l;
+    m->win.n = m->win.n2 + m->win.n3;
     if (m->win.n > MAXPRI || (int)n_in != m->win.n || n_out != NSYM) return OR_ERR_INVALID;
     if (h1 < 1 || h1 > 4096 || h2 < 1 || h2 > 4096) return OR_ERR_INVALID;
     m->h1 = (int)h1; m->h2 = (int)h2;
@@ -160,7 +174,7 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
 
 static void gather_win(const window_t *w, const uint8_t *img, int H, int W, int r, int c, uint8_t *pri) {
     const int wid = w->l + w->r + 1;
-    for (int k = 0; k < w->n; k++) {
+    for (int k = 0; k < w->n2; k++) {
         int dr, dc;
         if (k < w->u * wid) {
             dr = -w->u + k / wid;
@@ -174,15 +188,39 @@ static void gather_win(const window_t *w, const uint8_t *img, int H, int W, int 
     }
 }
 
+/* A 3D window at (r, c) of a slice: the slice's own window, then the lower
+ * layer from `below` (the previous slice, H x W), or zeros for the first
+ * slice (below == NULL). */
+static void gather_win3(const window_t *w, const uint8_t *below, const uint8_t *img, int H, int W, int r, int c,
+                        uint8_t *pri) {
+    gather_win(w, img, H, W, r, c, pri);
+    const int wid = w->pl + w->pr + 1;
+    for (int k = 0; k < w->n3; k++) {
+        int rr = r - w->pu + k / wid, cc = c - w->pl + k % wid;
+        pri[w->n2 + k] = (below && rr >= 0 && rr < H && cc >= 0 && cc < W) ? below[(size_t)rr * W + cc] : 0;
+    }
+}
+
 void or_gather(const uint8_t *img, int H, int W, int r, int c, uint8_t pri[NPRI]) {
-    const window_t w = {2, 2, 2, NPRI};
+    const window_t w = {2, 2, 2, NPRI, 0, 0, 0, 0, 0, NPRI, 0};
     gather_win(&w, img, H, W, r, c, pri);
 }
 
 /* The priors of window (u, l, r) at pixel (r0, c0); returns their count. */
 int or_gather_window(int u, int l, int rr, const uint8_t *img, int H, int W, int r0, int c0, uint8_t *pri) {
-    const window_t w = {u, l, rr, u * (l + rr + 1) + l};
+    const int n2 = u * (l + rr + 1) + l;
+    const window_t w = {u, l, rr, n2, 0, 0, 0, 0, 0, n2, 0};
     gather_win(&w, img, H, W, r0, c0, pri);
+    return w.n;
+}
+
+/* The priors of a 3D window at (r0, c0) of a slice with the previous slice
+ * `below` (NULL for the first slice); returns their count. */
+int or_gather_window3(int u, int l, int rr, int pu, int pd, int pl, int pr, const uint8_t *below, const uint8_t *img,
+                      int H, int W, int r0, int c0, uint8_t *pri) {
+    const int n2 = u * (l + rr + 1) + l, n3 = (pu + pd + 1) * (pl + pr + 1);
+    const window_t w = {u, l, rr, n2, pu, pd, pl, pr, n3, n2 + n3, 1};
+    gather_win3(&w, below, img, H, W, r0, c0, pri);
     return w.n;
 }
 
@@ -375,6 +413,10 @@ int or_pixel_table(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
+    if (m.win.vol) {
+        model_free(&m);
+        return OR_ERR_INVALID;   /* a 3D window needs the previous slice */
+    }
     uint8_t pri[MAXPRI];
     float z[NSYM];
     uint32_t cum[NSYM + 1];
@@ -397,7 +439,17 @@ int or_logits(const uint8_t *blob, size_t blob_n, const uint8_t *pri, int n, flo
     return OR_OK;
 }
 
-static int symbol_tables(const model_t *m, const uint8_t *img, int H, int W, uint32_t *fc_out,
+/* The model's priors at (r, c): the 2D window, or a 3D window over the
+ * slice img and the previous slice `below` (NULL for the first slice). */
+static void gather_model(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, int r, int c,
+                         uint8_t *pri) {
+    if (m->win.vol)
+        gather_win3(&m->win, below, img, H, W, r, c, pri);
+    else
+        gather_win(&m->win, img, H, W, r, c, pri);
+}
+
+static int symbol_tables(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, uint32_t *fc_out,
                          double *bits_out) {
     double bits = 0.0;
     for (int r = 0; r < H; r++)
@@ -405,7 +457,7 @@ static int symbol_tables(const model_t *m, const uint8_t *img, int H, int W, uin
             uint8_t pri[MAXPRI];
             float z[NSYM];
             uint32_t cum[NSYM + 1];
-            gather_win(&m->win, img, H, W, r, c, pri);
+            gather_model(m, below, img, H, W, r, c, pri);
             mlp(m, pri, z);
             int st = or_table_from_logits(z, m->tscale, m->lut, cum);
             if (st) return st;
@@ -425,34 +477,34 @@ int or_symbol_tables(const uint8_t *blob, size_t blob_n, const uint8_t *img, int
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
-    st = symbol_tables(&m, img, H, W, fc_out, bits_out);
+    st = m.win.vol ? OR_ERR_INVALID : symbol_tables(&m, NULL, img, H, W, fc_out, bits_out);
     model_free(&m);
     return st;
 }
 
-/* Encodes one H x W image with S streams (S is clipped to H).  Returns the
- * number of bytes written to out, or minus an error code. */
-int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H, int W, int S,
-                  uint8_t *out, size_t cap) {
+/* Codes one slice (or 2D image) into a container at out; below is the
+ * previous slice for a 3D window (NULL otherwise).  Returns the bytes
+ * written or minus an error code. */
+static int64_t encode_slice(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, int S,
+                            uint8_t *out, size_t cap) {
     if (H < 1 || W < 1 || S < 1 || H > 65535 * 64 || W > 65535 * 64) return -OR_ERR_INVALID;
     if (S > H) S = H;
     if (S > 65535) return -OR_ERR_INVALID;
     if (cap < or_max_encoded_bytes(H, W, S)) return -OR_ERR_CAPACITY;
-    model_t m;
-    int st = model_load(&m, blob, blob_n);
-    if (st) return -st;
     size_t N = (size_t)H * W;
     uint32_t *fc = malloc(4 * N);
-    st = symbol_tables(&m, img, H, W, fc, NULL);
-    if (st) { free(fc); model_free(&m); return -st; }
+    int st = symbol_tables(m, below, img, H, W, fc, NULL);
+    if (st) { free(fc); return -st; }
 
     memcpy(out, "DLC1", 4);
     wr_u32(out + 4, (uint32_t)H);
     wr_u32(out + 8, (uint32_t)W);
-    out[12] = (uint8_t)m.win.u;   /* rows of the window above the pixel (2 for the default) */
-    out[13] = (uint8_t)m.precision;
+    /* rows of the window above the pixel (2 for the default window), with
+     * bit 7 set in the slices of a volume coded with a 3D window */
+    out[12] = (uint8_t)(m->win.u | (m->win.vol ? 0x80 : 0));
+    out[13] = (uint8_t)m->precision;
     wr_u16(out + 14, (uint32_t)S);
-    for (int k = 0; k < 8; k++) out[16 + k] = (uint8_t)(m.hash >> (8 * k));
+    for (int k = 0; k < 8; k++) out[16 + k] = (uint8_t)(m->hash >> (8 * k));
     size_t pos = 24 + 4 * (size_t)S;
 
     px_t *order = malloc(sizeof(px_t) * ((size_t)(H / S + 1) * W));
@@ -475,6 +527,41 @@ int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H,
         for (size_t k = ne; k-- > 0;) { wr_u16(out + pos, emit[k]); pos += 2; }
     }
     free(order); free(emit); free(fc);
+    return (int64_t)pos;
+}
+
+/* Encodes one H x W image with S streams (S is clipped to H).  Returns the
+ * number of bytes written to out, or minus an error code. */
+int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H, int W, int S,
+                  uint8_t *out, size_t cap) {
+    model_t m;
+    int st = model_load(&m, blob, blob_n);
+    if (st) return -st;
+    int64_t n = m.win.vol ? -OR_ERR_INVALID : encode_slice(&m, NULL, img, H, W, S, out, cap);
+    model_free(&m);
+    return n;
+}
+
+/* Encodes a volume of D slices of H x W (slice z at vol + z H W) with a 3D
+ * window, each slice as its own container with S streams, back to back;
+ * offsets[z] .. offsets[z + 1] bound slice z's container.  Returns the total
+ * bytes or minus an error code. */
+int64_t or_encode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *vol, int D, int H, int W, int S,
+                         uint8_t *out, size_t cap, uint64_t *offsets) {
+    if (D < 1) return -OR_ERR_INVALID;
+    model_t m;
+    int st = model_load(&m, blob, blob_n);
+    if (st) return -st;
+    if (!m.win.vol) { model_free(&m); return -OR_ERR_INVALID; }
+    size_t pos = 0, N = (size_t)H * W;
+    offsets[0] = 0;
+    for (int z = 0; z < D; z++) {
+        int64_t n = encode_slice(&m, z ? vol + (size_t)(z - 1) * N : NULL, vol + (size_t)z * N, H, W, S, out + pos,
+                                 cap - pos);
+        if (n < 0) { model_free(&m); return n; }
+        pos += (size_t)n;
+        offsets[z + 1] = pos;
+    }
     model_free(&m);
     return (int64_t)pos;
 }
@@ -482,23 +569,19 @@ int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H,
 /* Decodes one bitstream into img_out (H x W, dims read from the header and
  * checked against the caller's).  Pixels are decoded one at a time in wave
  * order (t ascending, then r ascending): a topological order of the causal
- * dependencies that visits every stream in its own order. */
-int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, uint8_t *img_out,
-              int H, int W) {
+ * dependencies that visits every stream in its own order.  below: the
+ * decoded previous slice for a 3D window (NULL otherwise). */
+static int decode_slice(const model_t *m, const uint8_t *below, const uint8_t *in, size_t n, uint8_t *img_out,
+                        int H, int W) {
     if (H < 1 || W < 1) return OR_ERR_INVALID;
     if (n < 24 || memcmp(in, "DLC1", 4) != 0) return OR_ERR_CORRUPT;
-    model_t m;
-    int st = model_load(&m, blob, blob_n);
-    if (st) return st;
     int h = (int)rd_u32(in + 4), w = (int)rd_u32(in + 8);
     int S = in[14] | (in[15] << 8);
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)in[16 + k] << (8 * k);
-    if (h != H || w != W || in[12] != m.win.u || in[13] != m.precision || hash != m.hash || S < 1 ||
-        S > H || n < 24 + 4 * (size_t)S) {
-        model_free(&m);
+    if (h != H || w != W || in[12] != (m->win.u | (m->win.vol ? 0x80 : 0)) || in[13] != m->precision ||
+        hash != m->hash || S < 1 || S > H || n < 24 + 4 * (size_t)S)
         return OR_ERR_CORRUPT;
-    }
     uint32_t *words = malloc(4 * (size_t)S), *start = malloc(4 * (size_t)S);
     size_t total = 0;
     for (int s = 0; s < S; s++) {
@@ -507,7 +590,7 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
         total += words[s];
     }
     if (24 + 4 * (size_t)S + 2 * total != n) {
-        free(words); free(start); model_free(&m);
+        free(words); free(start);
         return OR_ERR_CORRUPT;
     }
     const uint8_t *pay = in + 24 + 4 * (size_t)S;
@@ -515,7 +598,7 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
     for (size_t k = 0; k < total; k++) all[k] = pay[2 * k] | (pay[2 * k + 1] << 8);
     uint64_t *x = malloc(8 * (size_t)S);
     int *pos = malloc(sizeof(int) * (size_t)S);
-    st = OR_OK;
+    int st = OR_OK;
     for (int s = 0; s < S && st == OR_OK; s++) {
         const uint32_t *ws = all + start[s];
         if (words[s] < 2) { st = OR_ERR_CORRUPT; break; }
@@ -533,9 +616,9 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
             uint8_t pri[MAXPRI];
             float z[NSYM];
             uint32_t cum[NSYM + 1];
-            gather_win(&m.win, img_out, H, W, r, c, pri);
-            mlp(&m, pri, z);
-            if (or_table_from_logits(z, m.tscale, m.lut, cum)) { st = OR_ERR_INVALID; break; }
+            gather_model(m, below, img_out, H, W, r, c, pri);
+            mlp(m, pri, z);
+            if (or_table_from_logits(z, m->tscale, m->lut, cum)) { st = OR_ERR_INVALID; break; }
             int sym = or_rans_dec_step(&x[s], cum, NSYM, 16, 16, 16, all + start[s], (int)words[s],
                                        &pos[s]);
             if (sym < 0) { st = OR_ERR_CORRUPT; break; }
@@ -545,6 +628,34 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
     for (int s = 0; s < S && st == OR_OK; s++)
         if (x[s] != RANS_L || (uint32_t)pos[s] != words[s]) st = OR_ERR_CORRUPT;
     free(all); free(x); free(pos); free(words); free(start);
+    return st;
+}
+
+int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, uint8_t *img_out,
+              int H, int W) {
+    model_t m;
+    int st = model_load(&m, blob, blob_n);
+    if (st) return st;
+    st = m.win.vol ? OR_ERR_INVALID : decode_slice(&m, NULL, in, n, img_out, H, W);
+    model_free(&m);
+    return st;
+}
+
+/* Decodes a volume coded by or_encode_volume: slice z from bytes
+ * offsets[z] .. offsets[z + 1] of in, slices in order (every prior of the
+ * lower layer lies in the slice before, already decoded).  Returns the first
+ * slice's error, if any. */
+int or_decode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *in, const uint64_t *offsets, int D,
+                     uint8_t *vol_out, int H, int W) {
+    if (D < 1) return OR_ERR_INVALID;
+    model_t m;
+    int st = model_load(&m, blob, blob_n);
+    if (st) return st;
+    if (!m.win.vol) { model_free(&m); return OR_ERR_INVALID; }
+    size_t N = (size_t)H * W;
+    for (int z = 0; z < D && st == OR_OK; z++)
+        st = decode_slice(&m, z ? vol_out + (size_t)(z - 1) * N : NULL, in + offsets[z], offsets[z + 1] - offsets[z],
+                          vol_out + (size_t)z * N, H, W);
     model_free(&m);
     return st;
 }

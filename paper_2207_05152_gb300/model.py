@@ -14,7 +14,10 @@ coder uses:
          window = 2: the default radius-2 window (n_in = 12); otherwise
          1 << 24 | u | l << 8 | r << 16: rows r-u..r-1 at columns c-l..c+r,
          then row r at columns c-l..c-1 (n_in = u (l + r + 1) + l, at most
-         96; u <= 8, l <= 8, r <= 2)
+         96; u <= 8, l <= 8, r <= 2); or a 3D window (Sec. IV "3D
+         Dependencies") 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 |
+         pl << 18 | pr << 22: the 2D window, then from the previous slice
+         rows r-pu..r+pd at columns c-pl..c+pr (pu, pd, pl, pr <= 8)
     28   f32 tscale               logit difference -> table units (64 / ln 2)
     32   u32 lut[64]              lut[k] = round(2^23 * 2^(-k/64)), lut[0] = 2^23
     288  layer data
@@ -44,11 +47,31 @@ N_OUT = 256
 RADIUS = 2
 DEFAULT_WINDOW = (2, 2, 2)
 FIG6_WINDOW = (8, 6, 2)   # 9 x 9 window, target in the last row, third column from the right
+# 3D window: the default 2D window plus the 3 x 3 neighbourhood of the pixel
+# in the previous slice (one row below the target's row: the lower layer is
+# shifted down, Sec. IV "3D Wavefront")
+VOLUME_WINDOW = (2, 2, 2, 1, 1, 1, 1)
+
+
+def is_volume(window) -> bool:
+    return len(window) == 7
 
 
 def window_size(window) -> int:
-    u, l, r = window
-    return u * (l + r + 1) + l
+    u, l, r = window[:3]
+    n = u * (l + r + 1) + l
+    if is_volume(window):
+        pu, pd, pl, pr = window[3:]
+        n += (pu + pd + 1) * (pl + pr + 1)
+    return n
+
+
+def volume_wave_shift(window) -> int:
+    """Waves by which slice z + 1 lags slice z in the 3D wavefront: the
+    smallest shift that puts every prior of the previous slice on an earlier
+    wave, 3 pd + pr + 1 (the lower layer's reach below and right)."""
+    pd, pr = window[4], window[6]
+    return 3 * pd + pr + 1
 
 
 def window_offsets(window) -> list:
@@ -56,15 +79,34 @@ def window_offsets(window) -> list:
     above, l columns left, r right; Sec. II-A), in the network's input
     order: the rows above top to bottom, each left to right, then the l
     pixels left of the target."""
-    u, l, r = window
+    u, l, r = window[:3]
     span = l + r + 1
     return [(k // span - u, k % span - l) for k in range(u * span)] + [(0, k - l) for k in range(l)]
+
+
+def window_offsets3(window) -> list:
+    """(slice, row, column) offset of every prior of a 2D or 3D window, in
+    the network's input order: the 2D window in the pixel's own slice
+    (slice offset 0), then for a 3D window the previous slice's rows
+    r-pu..r+pd, each at columns c-pl..c+pr (slice offset -1)."""
+    offs = [(0, dr, dc) for dr, dc in window_offsets(window[:3])]
+    if is_volume(window):
+        pu, pd, pl, pr = window[3:]
+        offs += [(-1, dr, dc) for dr in range(-pu, pd + 1) for dc in range(-pl, pr + 1)]
+    return offs
 
 
 def window_field(window) -> int:
     """The blob's window field: 2 for the default window, else the packed
     (u, l, r)."""
     window = tuple(int(v) for v in window)
+    if is_volume(window):
+        u, l, r, pu, pd, pl, pr = window
+        if not (1 <= u <= 8 and 0 <= l <= 8 and 0 <= r <= 2 and max(pu, pd, pl, pr) <= 8 and min(window) >= 0) \
+                or window_size(window) > 96:
+            raise ValueError("3D window must have 1 <= u <= 8, l <= 8, r <= 2, pu, pd, pl, pr <= 8 and at most "
+                             "96 priors")
+        return (2 << 28) | u | (l << 4) | (r << 8) | (pu << 10) | (pd << 14) | (pl << 18) | (pr << 22)
     if window == DEFAULT_WINDOW:
         return RADIUS
     u, l, r = window
@@ -76,6 +118,9 @@ def window_field(window) -> int:
 def window_of_field(field: int):
     if field == RADIUS:
         return DEFAULT_WINDOW
+    if field >> 28 == 2:
+        return (field & 0xF, (field >> 4) & 0xF, (field >> 8) & 3, (field >> 10) & 0xF, (field >> 14) & 0xF,
+                (field >> 18) & 0xF, (field >> 22) & 0xF)
     if field >> 24 != 1:
         raise ValueError("unknown window field")
     return (field & 0xFF, (field >> 8) & 0xFF, (field >> 16) & 0xFF)

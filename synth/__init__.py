@@ -156,6 +156,40 @@ def phantom_image(height: int, width: int, seed: int) -> np.ndarray:
     return _to_u8(np.sqrt((s + n1) ** 2 + n2 ** 2))
 
 
+def phantom_volume(depth: int, height: int, width: int, seed: int) -> np.ndarray:
+    """MRI-like volume (depth x height x width): 3..8 nested ellipsoids of
+    random centre, axes, in-plane angle and intensity, times a smooth
+    quadratic bias field in [0.8, 1.2], with Rician noise
+    sqrt((s + n1)^2 + n2^2), sigma drawn from U[3, 10]; consecutive slices
+    share the anatomy, as the slices of a scan do."""
+    rng = Rng(seed)
+    n_ell = int(rng.integers(1, 3, 8)[0])
+    zs = (np.arange(depth, dtype=np.float64)[:, None, None] - depth / 2) / max(depth / 2, 1.0)
+    ys = (np.arange(height, dtype=np.float64)[None, :, None] - height / 2) / (height / 2)
+    xs = (np.arange(width, dtype=np.float64)[None, None, :] - width / 2) / (width / 2)
+    vol = np.zeros((depth, height, width))
+    scale = 1.0
+    for _ in range(n_ell):
+        p = rng.uniform(8)
+        z0, y0, x0 = (p[0] - 0.5) * 0.3 * scale, (p[1] - 0.5) * 0.3 * scale, (p[2] - 0.5) * 0.3 * scale
+        az, ay, ax = (0.8 + 0.6 * p[3]) * scale, (0.5 + 0.4 * p[4]) * scale, (0.5 + 0.4 * p[5]) * scale
+        th = np.pi * p[6]
+        val = 30.0 + 180.0 * p[7]
+        yr = (ys - y0) * np.cos(th) + (xs - x0) * np.sin(th)
+        xr = -(ys - y0) * np.sin(th) + (xs - x0) * np.cos(th)
+        inside = (yr / ay) ** 2 + (xr / ax) ** 2 + ((zs - z0) / az) ** 2 <= 1.0
+        vol[inside] = val
+        scale *= 0.8
+    q = rng.uniform(6, -0.1, 0.1)
+    bias = np.clip(1.0 + q[0] * ys + q[1] * xs + q[2] * zs + q[3] * ys * ys + q[4] * xs * xs + q[5] * zs * zs,
+                   0.8, 1.2)
+    sigma = float(rng.uniform(1, 3.0, 10.0)[0])
+    s = vol * bias
+    n1 = sigma * rng.normal(s.size).reshape(s.shape)
+    n2 = sigma * rng.normal(s.size).reshape(s.shape)
+    return _to_u8(np.sqrt((s + n1) ** 2 + n2 ** 2))
+
+
 def uneven_sizes(count: int, seed: int, hmin=192, hmax=1536, wmin=256, wmax=2048):
     """Heights and widths drawn independently and uniformly (inclusive)."""
     rng = Rng(seed)
@@ -220,14 +254,24 @@ def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, w
     training run.  Input features are v / 128 - 1 in the prior order of the
     causal window (u, l, r): rows r-u..r-1 at columns c-l..c+r, then row r at
     columns c-l..c-1 (the default (2, 2, 2): r-2: c-2..c+2, r-1: c-2..c+2,
-    r: c-2, c-1).  With the default window every prior is carried through
-    the ReLU layers, otherwise the three that the prediction uses."""
-    u, l, rr = window
+    r: c-2, c-1), then for a 3D window (u, l, r, pu, pd, pl, pr) the
+    previous slice's rows r-pu..r+pd at columns c-pl..c+pr.  With the
+    default window every prior is carried through the ReLU layers, otherwise
+    the ones that the prediction uses (for a 3D window also the previous
+    slice's pixel at the target's position)."""
+    u, l, rr = window[:3]
     wid = l + rr + 1
-    n = u * wid + l
-    n_in, h1, h2, n_out = widths
+    n2 = u * wid + l
+    n = n2
     i_left, i_up, i_upleft = u * wid + l - 1, (u - 1) * wid + l, (u - 1) * wid + l - 1
     carried = list(range(n)) if tuple(window) == (2, 2, 2) else [i_upleft, i_up, i_left]
+    if len(window) == 7:
+        # 3D window: the previous slice's pixel at the target's position joins
+        pu, pd, pl, pr = window[3:]
+        n += (pu + pd + 1) * (pl + pr + 1)
+        i_below = n2 + pu * (pl + pr + 1) + pl
+        carried = [i_upleft, i_up, i_left, i_below]
+    n_in, h1, h2, n_out = widths
     nc = 2 * len(carried)
     assert n_in == n and n_out == 256 and h1 >= nc and h2 >= nc and l >= 1
     rng = Rng(seed)
@@ -235,6 +279,9 @@ def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, w
     alpha[i_left] = 0.75      # left neighbour
     alpha[i_up] = 0.75        # upper neighbour
     alpha[i_upleft] = -0.5    # upper-left neighbour
+    if len(window) == 7:
+        alpha[:n2] *= 0.75
+        alpha[i_below] = 0.25     # the same position one slice down
     w1 = noise * rng.normal(h1 * n).reshape(h1, n)
     w1[:nc] = 0.0
     for j, k in enumerate(carried):

@@ -24,17 +24,22 @@ def window_offsets(window=(2, 2, 2)):
 
 def calib_contexts(images, count=4096, seed=77, window=(2, 2, 2)):
     """Priors (u8 [count, window size]) of pixels drawn uniformly from the
-    images, zero-padded at the borders: calibration data for quantisation."""
+    images, zero-padded at the borders: calibration data for quantisation.
+    For a 3D window the images are the consecutive slices of a volume and
+    the lower layer comes from the slice before (zeros for the first)."""
     idx, rr, cc = synth.sample_positions(images, count, seed)
-    offs = window_offsets(window)
+    offs = [(0, dr, dc) for dr, dc in window_offsets(window[:3])]
+    if len(window) == 7:
+        pu, pd, pl, pr = window[3:]
+        offs += [(-1, dr, dc) for dr in range(-pu, pd + 1) for dc in range(-pl, pr + 1)]
     out = np.zeros((count, len(offs)), np.uint8)
-    dr = [o[0] for o in offs]
-    dc = [o[1] for o in offs]
     for n, (i, r, c) in enumerate(zip(idx, rr, cc)):
-        img = images[i]
-        H, W = img.shape
-        for k in range(len(offs)):
-            y, x = r + dr[k], c + dc[k]
+        for k, (dz, dr, dc) in enumerate(offs):
+            if i + dz < 0:
+                continue
+            img = images[i + dz]
+            H, W = img.shape
+            y, x = r + dr, c + dc
             out[n, k] = img[y, x] if 0 <= y < H and 0 <= x < W else 0
     return out
 
