@@ -67,6 +67,22 @@ typedef struct {
     int64_t pitch;
 } dlic_image;
 
+/* A volume of `depth` slices of height x width 8-bit pixels in device memory
+ * (Sec. IV: scans coded with a 3D window): slice z starts at
+ * pixels + z * slice_pitch (slice_pitch >= pitch * height), its row r at
+ * + r * pitch.  streams: the rANS streams of every slice, at most one per
+ * row (0 = dlic_auto_streams when encoding; when decoding, the count in the
+ * slices' headers, from dlic_read_header).  depth <= 2047. */
+typedef struct {
+    uint8_t *pixels;
+    int32_t depth;
+    int32_t height;
+    int32_t width;
+    int32_t streams;
+    int64_t pitch;
+    int64_t slice_pitch;
+} dlic_volume;
+
 /* Thread-local description of the last error returned by this thread. */
 DLIC_API const char *dlic_last_error(void);
 
@@ -230,6 +246,51 @@ DLIC_API dlic_status dlic_decode_workspace_size(const dlic_model *model, const d
 DLIC_API dlic_status dlic_decode(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,
                         int n, const dlic_image *h_images, int32_t *d_status, void *d_workspace,
                         size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Volumes (Sec. IV "3D Dependencies", "3D Wavefront")                      */
+/* ---------------------------------------------------------------------- */
+
+/* A model whose window field is 3D (2 << 28 | u | l << 4 | r << 8 | pu << 10 |
+ * pd << 14 | pl << 18 | pr << 22) predicts pixel (z, r, c) from its slice's
+ * causal window (u, l, r) and, from slice z - 1, rows r-pu..r+pd at columns
+ * c-pl..c+pr (row by row; zeros for the first slice and outside the slice).
+ * Such a model codes volumes only (dlic_encode and dlic_decode refuse it
+ * with DLIC_ERR_INVALID, and the volume calls refuse 2D models). */
+
+/* Device workspace, in bytes, that dlic_encode_volume needs for these volumes. */
+DLIC_API dlic_status dlic_encode_volume_workspace_size(const dlic_model *model, const dlic_volume *h_volumes, int n,
+                                              size_t *bytes);
+
+/* Encodes n volumes.  Every slice is coded on its own, with its own streams,
+ * into a "DLC1" container whose byte 12 is u | 0x80; the containers follow
+ * one another slice by slice, volume by volume, in d_out.  d_out_offsets
+ * (device, sum of depths + 1 entries) receives the byte offset of every
+ * slice's container and the total.  Capacity, workspace and status as for
+ * dlic_encode (each slice needs dlic_max_encoded_bytes). */
+DLIC_API dlic_status dlic_encode_volume(const dlic_model *model, const dlic_volume *h_volumes, int n, void *d_out,
+                               size_t out_capacity, uint64_t *d_out_offsets, int32_t *d_status,
+                               void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Device workspace, in bytes, that dlic_decode_volume needs. */
+DLIC_API dlic_status dlic_decode_volume_workspace_size(const dlic_model *model, const dlic_volume *h_volumes, int n,
+                                              size_t *bytes);
+
+/* Decodes n volumes; volume i is the bytes [h_in_offsets[i], h_in_offsets[i + 1])
+ * of d_in (host array of n + 1 even offsets): its slices' containers back to
+ * back, as dlic_encode_volume wrote them.  All slices of a volume decode at
+ * once in one cluster of CTAs as a 3D wavefront: pixel (z, r, c) is on wave
+ * 3r + c + (3 pd + pr + 1) z, so every prior from slice z - 1 is decoded
+ * before it is read (priors are read back from the output volume, one cluster
+ * barrier per wave); the first slice is complete after 3(H-1) + W waves, the
+ * volume after (3 pd + pr + 1)(depth - 1) more.  The cluster size divides
+ * h_volumes[i].streams, which must equal the slices' stream count.  Networks
+ * as for the cluster decoder (INT8 of widths 128, FP32 with h2 <= 128).
+ * d_status (n int32, device): DLIC_OK, DLIC_ERR_CORRUPT (a slice's header,
+ * sizes or final states) or DLIC_ERR_TIMEOUT. */
+DLIC_API dlic_status dlic_decode_volume(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,
+                               int n, const dlic_volume *h_volumes, int32_t *d_status, void *d_workspace,
+                               size_t workspace_bytes, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Training (Sec. III-A: categorical cross-entropy reported in bits)        */

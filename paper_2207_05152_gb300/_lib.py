@@ -31,9 +31,15 @@ class dlic_image(C.Structure):
                 ("pitch", C.c_int64)]
 
 
+class dlic_volume(C.Structure):
+    _fields_ = [("pixels", C.c_void_p), ("depth", C.c_int32), ("height", C.c_int32), ("width", C.c_int32),
+                ("streams", C.c_int32), ("pitch", C.c_int64), ("slice_pitch", C.c_int64)]
+
+
 _VP = C.c_void_p
 _SZ = C.c_size_t
 _I = C.c_int
+_VOLP = C.POINTER(dlic_volume)
 _IMGP = C.POINTER(dlic_image)
 
 # name -> (restype, argtypes); every symbol include/dlic.h declares
@@ -52,6 +58,10 @@ SIGNATURES = {
                               C.POINTER(C.c_uint64)]),
     "dlic_decode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_SZ)]),
     "dlic_decode": (_I, [_VP, _VP, C.POINTER(C.c_uint64), _I, _IMGP, _VP, _VP, _SZ, _VP]),
+    "dlic_encode_volume_workspace_size": (_I, [_VP, _VOLP, _I, C.POINTER(_SZ)]),
+    "dlic_encode_volume": (_I, [_VP, _VOLP, _I, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
+    "dlic_decode_volume_workspace_size": (_I, [_VP, _VOLP, _I, C.POINTER(_SZ)]),
+    "dlic_decode_volume": (_I, [_VP, _VP, C.POINTER(C.c_uint64), _I, _VOLP, _VP, _VP, _SZ, _VP]),
     "dlic_train_param_count": (_SZ, [_I, _I]),
     "dlic_trainer_create": (_I, [_I, _I, _I, _I, _VP, C.POINTER(_VP)]),
     "dlic_trainer_destroy": (_I, [_VP]),
@@ -183,6 +193,43 @@ def dlic_decode(model: int, d_in: int, in_offsets, images, d_status: int, d_ws: 
     arr, n = images_array(images)
     check(lib().dlic_decode(model, d_in, u64_array(in_offsets), n, arr, d_status, d_ws, ws_bytes,
                             stream or None))
+
+
+def volumes_array(volumes):
+    """volumes: sequence of (ptr, depth, height, width, streams, pitch, slice_pitch)."""
+    n = len(volumes)
+    arr = (dlic_volume * max(1, n))()
+    for i, v in enumerate(volumes):
+        arr[i] = dlic_volume(*v)
+    return arr, n
+
+
+def dlic_encode_volume_workspace_size(model: int, volumes) -> int:
+    arr, n = volumes_array(volumes)
+    out = _SZ()
+    check(lib().dlic_encode_volume_workspace_size(model, arr, n, C.byref(out)))
+    return out.value
+
+
+def dlic_encode_volume(model: int, volumes, d_out: int, out_capacity: int, d_out_offsets: int, d_status: int,
+                       d_ws: int, ws_bytes: int, stream: int = 0):
+    arr, n = volumes_array(volumes)
+    check(lib().dlic_encode_volume(model, arr, n, d_out, out_capacity, d_out_offsets, d_status or None, d_ws,
+                                   ws_bytes, stream or None))
+
+
+def dlic_decode_volume_workspace_size(model: int, volumes) -> int:
+    arr, n = volumes_array(volumes)
+    out = _SZ()
+    check(lib().dlic_decode_volume_workspace_size(model, arr, n, C.byref(out)))
+    return out.value
+
+
+def dlic_decode_volume(model: int, d_in: int, in_offsets, volumes, d_status: int, d_ws: int, ws_bytes: int,
+                       stream: int = 0):
+    arr, n = volumes_array(volumes)
+    check(lib().dlic_decode_volume(model, d_in, u64_array(in_offsets), n, arr, d_status, d_ws, ws_bytes,
+                                   stream or None))
 
 
 def dlic_train_param_count(h1: int, h2: int) -> int:

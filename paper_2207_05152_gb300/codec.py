@@ -103,6 +103,51 @@ class Codec:
                          status.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
         return outs, status
 
+    # --- volumes (3D window models; Sec. IV) ---
+
+    @staticmethod
+    def _vdesc(vols, streams):
+        out = []
+        for t, s in zip(vols, streams):
+            if t.dtype != torch.uint8 or t.dim() != 3 or not t.is_cuda:
+                raise ValueError("volumes must be 3-D uint8 CUDA tensors (depth, height, width)")
+            if t.stride(2) != 1:
+                raise ValueError("volume rows must be contiguous")
+            out.append((t.data_ptr(), t.shape[0], t.shape[1], t.shape[2], int(s), t.stride(1), t.stride(0)))
+        return out
+
+    def encode_volume(self, volumes, streams=None, status=None, stream=None):
+        """Encodes a list of (depth, height, width) uint8 CUDA tensors.
+        Returns (bytes tensor, per-slice offsets tensor of sum(depth) + 1
+        int64 on the device)."""
+        streams = streams or [0] * len(volumes)
+        desc = self._vdesc(volumes, streams)
+        cap = 0
+        for (_, d, h, w, s, _, _) in desc:
+            cap += d * _lib.dlic_max_encoded_bytes(h, w, s or _lib.dlic_auto_streams(h, w))
+        out = torch.empty(max(cap, 1), dtype=torch.uint8, device="cuda")
+        offsets = torch.empty(sum(d[1] for d in desc) + 1, dtype=torch.int64, device="cuda")
+        ws = self._workspace(_lib.dlic_encode_volume_workspace_size(self.handle, desc))
+        _lib.dlic_encode_volume(self.handle, desc, out.data_ptr(), out.numel(), offsets.data_ptr(),
+                                status.data_ptr() if status is not None else 0, ws.data_ptr(), ws.numel(),
+                                _stream_handle(stream))
+        return out, offsets
+
+    def decode_volume(self, data: torch.Tensor, offsets, shapes, streams, outs=None, status=None, stream=None):
+        """Decodes volumes; offsets: host sequence of n + 1 byte offsets (each
+        volume's slice containers back to back); shapes: (depth, height,
+        width) per volume; streams: each volume's stream count."""
+        n = len(shapes)
+        if outs is None:
+            outs = [torch.empty(s, dtype=torch.uint8, device="cuda") for s in shapes]
+        if status is None:
+            status = torch.empty(max(1, n), dtype=torch.int32, device="cuda")
+        desc = self._vdesc(outs, streams)
+        ws = self._workspace(_lib.dlic_decode_volume_workspace_size(self.handle, desc))
+        _lib.dlic_decode_volume(self.handle, data.data_ptr(), [int(o) for o in offsets], desc, status.data_ptr(),
+                                ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return outs, status
+
     def decode_bytes(self, streams_bytes, shapes=None):
         """Decodes host bitstreams; returns (list of uint8 host arrays, statuses)."""
         if shapes is None:

@@ -75,17 +75,33 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     const uint32_t prec = le32(b + 4), n_in = le32(b + 8), h1 = le32(b + 12), h2 = le32(b + 16),
                    n_out = le32(b + 20), radius = le32(b + 24);
     if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
-    // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16
-    int wu = 2, wl = 2, wr = 2;
+    // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16,
+    // or a 3D window 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 | pl << 18 | pr << 22
+    int wu = 2, wl = 2, wr = 2, vol = 0, pu = 0, pd = 0, pl = 0, pr = 0;
     if (radius != 2) {
-        if ((radius >> 24) != 1) return fail(DLIC_ERR_INVALID, "unknown window field 0x%x", radius);
-        wu = (int)(radius & 0xFF);
-        wl = (int)((radius >> 8) & 0xFF);
-        wr = (int)((radius >> 16) & 0xFF);
+        if ((radius >> 24) == 1) {
+            wu = (int)(radius & 0xFF);
+            wl = (int)((radius >> 8) & 0xFF);
+            wr = (int)((radius >> 16) & 0xFF);
+        } else if ((radius >> 28) == 2 && ((radius >> 26) & 3) == 0) {
+            vol = 1;
+            wu = (int)(radius & 0xF);
+            wl = (int)((radius >> 4) & 0xF);
+            wr = (int)((radius >> 8) & 3);
+            pu = (int)((radius >> 10) & 0xF);
+            pd = (int)((radius >> 14) & 0xF);
+            pl = (int)((radius >> 18) & 0xF);
+            pr = (int)((radius >> 22) & 0xF);
+            if (pu > 8 || pd > 8 || pl > 8 || pr > 8)
+                return fail(DLIC_ERR_INVALID, "3D window reaches must be <= 8");
+        } else {
+            return fail(DLIC_ERR_INVALID, "unknown window field 0x%x", radius);
+        }
         if (wu < 1 || wu > 8 || wl > 8 || wr > 2)
             return fail(DLIC_ERR_INVALID, "window must have 1..8 rows above, left reach <= 8, right reach <= 2");
     }
-    const int npri = wu * (wl + wr + 1) + wl;
+    const int n2 = wu * (wl + wr + 1) + wl;
+    const int npri = n2 + (vol ? (pu + pd + 1) * (pl + pr + 1) : 0);
     if (npri > kMaxPriors || (int)n_in != npri || n_out != kSymbols)
         return fail(DLIC_ERR_INVALID, "model must map the %d priors of its window to 256 logits", npri);
     if (h1 < 16 || h1 > kMaxHidden || h1 % 16 || h2 < 16 || h2 > kMaxHidden || h2 % 16)
@@ -121,6 +137,12 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.wl = wl;
     d.wr = wr;
     d.n_in = npri;
+    d.n2 = n2;
+    d.vol = vol;
+    d.pu = pu;
+    d.pd = pd;
+    d.pl = pl;
+    d.pr = pr;
     d.tscale = tscale;
     d.hash = fnv1a64(b, n);
     size_t off_lut = put(lut, sizeof(lut));
@@ -299,29 +321,45 @@ static size_t enc_image_bytes(int H, int W, int S) {
     return align256(4 * N) + align256(2 * (N + 2ull * S)) + 3 * align256(4ull * S);
 }
 
+// One image, or one slice of a volume (with the slice before it), to encode.
+struct EncItem {
+    const uint8_t *pixels, *below;
+    int H, W, S;
+    int64_t pitch;
+};
+
+static size_t enc_ws_bytes(const std::vector<EncItem> &it) {
+    size_t total = align256(8ull * (it.size() + 1)) + 256;
+    for (const EncItem &e : it) total += enc_image_bytes(e.H, e.W, e.S);
+    return total;
+}
+
+static std::vector<EncItem> image_items(const dlic_image *im, int n, const int *streams) {
+    std::vector<EncItem> it((size_t)n);
+    for (int i = 0; i < n; i++) it[i] = {im[i].pixels, nullptr, im[i].height, im[i].width, clip_streams(im[i], streams, i), im[i].pitch};
+    return it;
+}
+
 extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
                                                   const int *streams, size_t *bytes) {
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, streams, false);
     if (st) return st;
-    size_t total = align256(8ull * (n + 1)) + 256;
-    for (int i = 0; i < n; i++) total += enc_image_bytes(im[i].height, im[i].width, clip_streams(im[i], streams, i));
-    *bytes = total;
+    *bytes = enc_ws_bytes(image_items(im, n, streams));
     return DLIC_OK;
 }
 
-extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, int n, const int *streams,
-                                   void *d_out, size_t out_capacity, uint64_t *d_out_offsets,
-                                   int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {
-    if (!m) return fail(DLIC_ERR_INVALID, "null model");
-    dlic_status st = check_images(im, n, streams, false);
-    if (st) return st;
+// Predicts, rANS-codes and packs every item into its own container, back to
+// back in d_out; d_out_offsets gets items + 1 byte offsets.
+static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> &it, void *d_out, size_t out_capacity,
+                                uint64_t *d_out_offsets, int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {
+    const int n = (int)it.size();
     if (n == 0) return DLIC_OK;
     if (!d_out || !d_out_offsets || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(DLIC_ERR_INVALID, "workspace must be 256-byte aligned");
-    size_t need_ws = 0, need_out = 0;
-    dlic_encode_workspace_size(m, im, n, streams, &need_ws);
-    for (int i = 0; i < n; i++) need_out += dlic_max_encoded_bytes(im[i].height, im[i].width, clip_streams(im[i], streams, i));
+    size_t need_out = 0;
+    const size_t need_ws = enc_ws_bytes(it);
+    for (const EncItem &e : it) need_out += dlic_max_encoded_bytes(e.H, e.W, e.S);
     if (ws_bytes < need_ws) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need_ws);
     if (out_capacity < need_out) return fail(DLIC_ERR_CAPACITY, "output capacity %zu < %zu bytes", out_capacity, need_out);
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -347,13 +385,14 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
         b->tile_px = tile_px;
         int tiles = 0, total_streams = 0;
         for (int k = 0; k < cn; k++) {
-            const dlic_image &g = im[c0 + k];
+            const EncItem &g = it[c0 + k];
             EncImage &e = b->img[k];
             e.pixels = g.pixels;
+            e.below = g.below;
             e.pitch = g.pitch;
-            e.H = g.height;
-            e.W = g.width;
-            e.S = clip_streams(g, streams, c0 + k);
+            e.H = g.H;
+            e.W = g.W;
+            e.S = g.S;
             e.tile_begin = tiles;
             const size_t N = (size_t)e.H * e.W;
             tiles += (int)((N + tile_px - 1) / tile_px);
@@ -379,10 +418,75 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
     return DLIC_OK;
 }
 
+extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, int n, const int *streams,
+                                   void *d_out, size_t out_capacity, uint64_t *d_out_offsets,
+                                   int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 3D window: use dlic_encode_volume");
+    dlic_status st = check_images(im, n, streams, false);
+    if (st) return st;
+    return encode_items(m, image_items(im, n, streams), d_out, out_capacity, d_out_offsets, d_status, d_ws, ws_bytes,
+                        stream);
+}
+
+static dlic_status check_volumes(const dlic_volume *v, int n, bool decode) {
+    if (n < 0) return fail(DLIC_ERR_INVALID, "negative volume count");
+    if (n > 0 && !v) return fail(DLIC_ERR_INVALID, "null volume array");
+    for (int i = 0; i < n; i++) {
+        const dlic_volume &g = v[i];
+        if (!g.pixels) return fail(DLIC_ERR_INVALID, "volume %d: null pixels", i);
+        if (g.depth < 1 || g.height < 1 || g.width < 1)
+            return fail(DLIC_ERR_INVALID, "volume %d: empty volume (%d x %d x %d)", i, g.depth, g.height, g.width);
+        if (g.height > (1 << 20) || g.width > (1 << 20) || g.depth > kMaxSlices)
+            return fail(DLIC_ERR_UNSUPPORTED, "volume %d: above 2^20 rows or columns or %d slices", i, kMaxSlices);
+        if (g.pitch < g.width) return fail(DLIC_ERR_INVALID, "volume %d: pitch < width", i);
+        if (g.slice_pitch < g.pitch * (int64_t)g.height) return fail(DLIC_ERR_INVALID, "volume %d: slices overlap", i);
+        if (g.streams < (decode ? 1 : 0) || g.streams > 65535)
+            return fail(DLIC_ERR_INVALID, "volume %d: stream count %d outside [%d, 65535]", i, g.streams, decode ? 1 : 0);
+    }
+    return DLIC_OK;
+}
+
+static int volume_streams(const dlic_volume &v) {
+    const int s = v.streams ? v.streams : dlic_auto_streams(v.height, v.width);
+    return s < v.height ? s : v.height;
+}
+
+static std::vector<EncItem> volume_items(const dlic_volume *v, int n) {
+    std::vector<EncItem> it;
+    for (int i = 0; i < n; i++)
+        for (int z = 0; z < v[i].depth; z++) {
+            const uint8_t *slice = v[i].pixels + (int64_t)z * v[i].slice_pitch;
+            it.push_back({slice, z ? slice - v[i].slice_pitch : nullptr, v[i].height, v[i].width, volume_streams(v[i]),
+                          v[i].pitch});
+        }
+    return it;
+}
+
+extern "C" dlic_status dlic_encode_volume_workspace_size(const dlic_model *m, const dlic_volume *v, int n,
+                                                         size_t *bytes) {
+    if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
+    dlic_status st = check_volumes(v, n, false);
+    if (st) return st;
+    *bytes = enc_ws_bytes(volume_items(v, n));
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_encode_volume(const dlic_model *m, const dlic_volume *v, int n, void *d_out,
+                                          size_t out_capacity, uint64_t *d_out_offsets, int32_t *d_status,
+                                          void *d_ws, size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (!m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 2D window: use dlic_encode");
+    dlic_status st = check_volumes(v, n, false);
+    if (st) return st;
+    return encode_items(m, volume_items(v, n), d_out, out_capacity, d_out_offsets, d_status, d_ws, ws_bytes, stream);
+}
+
 extern "C" dlic_status dlic_read_header(const void *h_bits, size_t bytes, int *height, int *width,
                                         int *streams, int *precision, uint64_t *hash) {
     const uint8_t *h = static_cast<const uint8_t *>(h_bits);
-    if (!h || bytes < (size_t)kHeaderBytes || memcmp(h, "DLC1", 4) != 0 || h[12] < 1 || h[12] > 8)
+    // byte 12: window rows above (1..8), bit 7 set in the slices of a volume
+    if (!h || bytes < (size_t)kHeaderBytes || memcmp(h, "DLC1", 4) != 0 || (h[12] & 0x7F) < 1 || (h[12] & 0x7F) > 8)
         return fail(DLIC_ERR_CORRUPT, "not a DLIC bitstream");
     if (height) *height = (int)le32(h + 4);
     if (width) *width = (int)le32(h + 8);
@@ -396,60 +500,103 @@ extern "C" dlic_status dlic_read_header(const void *h_bits, size_t bytes, int *h
     return DLIC_OK;
 }
 
+// One image, or one volume, to decode.
+struct DecItem {
+    uint8_t *pixels;
+    int H, W, D, S;
+    int64_t pitch, slice_pitch;
+};
+
+static size_t dec_ws_bytes(const std::vector<DecItem> &it) {
+    size_t total = 0;
+    for (const DecItem &e : it) total += align256(16ull * e.H);
+    return total < 256 ? 256 : total;
+}
+
+static std::vector<DecItem> dec_image_items(const dlic_image *im, int n) {
+    std::vector<DecItem> it((size_t)n);
+    for (int i = 0; i < n; i++) it[i] = {im[i].pixels, im[i].height, im[i].width, 1, 0, im[i].pitch, 0};
+    return it;
+}
+
+static std::vector<DecItem> dec_volume_items(const dlic_volume *v, int n) {
+    std::vector<DecItem> it((size_t)n);
+    for (int i = 0; i < n; i++)
+        it[i] = {v[i].pixels, v[i].height, v[i].width, v[i].depth, volume_streams(v[i]), v[i].pitch, v[i].slice_pitch};
+    return it;
+}
+
 extern "C" dlic_status dlic_decode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
                                                   size_t *bytes) {
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, nullptr, true);
     if (st) return st;
-    size_t total = 0;
-    for (int i = 0; i < n; i++) total += align256(16ull * im[i].height);
-    *bytes = total < 256 ? 256 : total;
+    *bytes = dec_ws_bytes(dec_image_items(im, n));
     return DLIC_OK;
 }
 
-extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const uint64_t *h_in_offsets,
-                                   int n, const dlic_image *im, int32_t *d_status, void *d_ws,
-                                   size_t ws_bytes, void *stream) {
-    if (!m) return fail(DLIC_ERR_INVALID, "null model");
-    dlic_status st = check_images(im, n, nullptr, true);
+extern "C" dlic_status dlic_decode_volume_workspace_size(const dlic_model *m, const dlic_volume *v, int n,
+                                                         size_t *bytes) {
+    if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
+    dlic_status st = check_volumes(v, n, true);
     if (st) return st;
+    *bytes = dec_ws_bytes(dec_volume_items(v, n));
+    return DLIC_OK;
+}
+
+// Decodes item i from bytes [h_in_offsets[i], h_in_offsets[i + 1]) of d_in
+// (a volume: its slices' containers back to back).
+static dlic_status decode_items(const dlic_model *m, const void *d_in, const uint64_t *h_in_offsets,
+                                const std::vector<DecItem> &it, int32_t *d_status, void *d_ws, size_t ws_bytes,
+                                void *stream) {
+    const int n = (int)it.size();
     if (n == 0) return DLIC_OK;
     if (!d_in || !h_in_offsets || !d_status || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
-    size_t need = 0;
-    dlic_decode_workspace_size(m, im, n, &need);
+    const size_t need = dec_ws_bytes(it);
     if (ws_bytes < need) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need);
     for (int i = 0; i < n; i++) {
         if (h_in_offsets[i + 1] < h_in_offsets[i]) return fail(DLIC_ERR_INVALID, "offsets must not decrease");
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
     }
+    const bool vol = m->dev.vol != 0;
+    const bool use_wave = wave_decode_supported(m->dev);
+    if (vol && !use_wave) return fail(DLIC_ERR_UNSUPPORTED, "volumes decode on the cluster wavefront kernels only");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     {
         cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t) * (size_t)n, cs);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     }
-    const bool use_wave = wave_decode_supported(m->dev);
     // workspace offsets of every image's stream states
     std::vector<size_t> st_off(n);
     {
         size_t off = 0;
         for (int i = 0; i < n; i++) {
             st_off[i] = off;
-            off += align256(16ull * im[i].height);
+            off += align256(16ull * it[i].H);
         }
     }
     // cluster size of every image (1 on the CUDA-core path)
     std::vector<int> P(n, 1), Hs(n), Ws(n);
     for (int i = 0; i < n; i++) {
-        Hs[i] = im[i].height;
-        Ws[i] = im[i].width;
+        Hs[i] = it[i].H;
+        Ws[i] = it[i].W;
     }
     if (use_wave) {
-        choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
+        if (vol) {
+            // a volume's wave spans its slices: the largest cluster that
+            // divides its stream count (each CTA owns the rows k mod P)
+            for (int i = 0; i < n; i++) {
+                P[i] = 16;
+                while (it[i].S % P[i]) P[i] >>= 1;
+            }
+        } else {
+            choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
+        }
         // checked before anything is enqueued
         for (int i = 0; i < n; i++)
-            if (!wave_decode_fits(m->dev, Hs[i], Ws[i], P[i], m->decode_plan))
-                return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d has waves too long for the decoder's shared memory",
-                            i, Hs[i], Ws[i]);
+            if (!wave_decode_fits(m->dev, Hs[i], Ws[i], it[i].D, P[i], m->decode_plan))
+                return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d (x %d) needs more shared memory than the "
+                            "decoder's plans allow", i, Hs[i], Ws[i], it[i].D);
     }
     int groups_used = 0;
     for (int gi = 0; gi < kDecodeGroups; gi++)
@@ -476,7 +623,8 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         if (members.empty()) continue;
         if (use_wave)
             std::stable_sort(members.begin(), members.end(), [&](int a, int b) {
-                return decode_estimate(Hs[a], Ws[a], cluster, f32) > decode_estimate(Hs[b], Ws[b], cluster, f32);
+                return decode_estimate(Hs[a], Ws[a], cluster, f32) * it[a].D >
+                       decode_estimate(Hs[b], Ws[b], cluster, f32) * it[b].D;
             });
         cudaStream_t gs = fork ? m->group_stream[gi] : cs;
         if (fork) {
@@ -492,12 +640,14 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
             b->status = d_status;
             for (int k = 0; k < cn; k++) {
                 const int i = members[c0 + k];
-                const dlic_image &g = im[i];
+                const DecItem &g = it[i];
                 DecImage &e = b->img[k];
                 e.pixels = g.pixels;
                 e.pitch = g.pitch;
-                e.H = g.height;
-                e.W = g.width;
+                e.slice_pitch = g.slice_pitch;
+                e.H = g.H;
+                e.W = g.W;
+                e.D = g.D;
                 e.in_off = h_in_offsets[i];
                 e.in_bytes = h_in_offsets[i + 1] - h_in_offsets[i];
                 e.st_off = st_off[i];
@@ -520,4 +670,24 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
         if (err != DLIC_OK) break;
     }
     return err;
+}
+
+extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const uint64_t *h_in_offsets,
+                                   int n, const dlic_image *im, int32_t *d_status, void *d_ws,
+                                   size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 3D window: use dlic_decode_volume");
+    dlic_status st = check_images(im, n, nullptr, true);
+    if (st) return st;
+    return decode_items(m, d_in, h_in_offsets, dec_image_items(im, n), d_status, d_ws, ws_bytes, stream);
+}
+
+extern "C" dlic_status dlic_decode_volume(const dlic_model *m, const void *d_in, const uint64_t *h_in_offsets,
+                                          int n, const dlic_volume *v, int32_t *d_status, void *d_ws,
+                                          size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (!m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 2D window: use dlic_decode");
+    dlic_status st = check_volumes(v, n, true);
+    if (st) return st;
+    return decode_items(m, d_in, h_in_offsets, dec_volume_items(v, n), d_status, d_ws, ws_bytes, stream);
 }

@@ -165,10 +165,12 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
         float v = 0.0f;
         if (pp < npx) {
             const int r = (int)(pp / im.W), c = (int)(pp % im.W);
-            int dr, dc;
-            window_offset(m, q, dr, dc);
+            int dz, dr, dc;
+            window_offset(m, q, dz, dr, dc);
             const int rr = r + dr, cc = c + dc;
-            const uint32_t pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[rr * im.pitch + cc] : 0u;
+            const uint8_t *src = dz ? im.below : im.pixels;   // the previous slice for a 3D window
+            const uint32_t pv =
+                (src && rr >= 0 && rr < im.H && cc >= 0 && cc < im.W) ? src[(int64_t)rr * im.pitch + cc] : 0u;
             v = __fmaf_rn((float)pv, 0.0078125f, -1.0f);
         }
         xs[p * K1 + q] = v;

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
     __shared__ uint32_t tmem_base;
     __shared__ int wg_fail[kTcSlots];
     __shared__ float s_max[kTcSlots][2][128];
-    __shared__ char2 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
+    __shared__ char4 s_woff[kMaxPriors];   // (row, column, slice) offset of every prior of the window
     __shared__ uint32_t s_w[kTcSlots][3][128];   // the high half's W, P_sym and w_sym
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
     const int slot = wg & 1, half = wg >> 1;
@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
         for (int i = tid; i < kSymbols; i += blockDim.x) { s3[i] = m.s3[i]; o3[i] = m.o3[i]; }
         expand_lut(m.lut, reinterpret_cast<uint32_t *>(smem + L.lut), tid, blockDim.x);
         if (tid < m.n_in) {
-            int dr, dc;
-            window_offset(m, tid, dr, dc);
-            s_woff[tid] = make_char2((signed char)dr, (signed char)dc);
+            int dz, dr, dc;
+            window_offset(m, tid, dz, dr, dc);
+            s_woff[tid] = make_char4((signed char)dr, (signed char)dc, (signed char)dz, 0);
         }
     }
     if (warp == 0) {
@@ -189,17 +189,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
                     const int q = 8 * j + 2 * e + hb;
                     uint32_t v = 0u;
                     if (active && q < NPRI) {
-                        int dr, dc;
+                        int dr, dc, pv;
                         if (DEF) {
                             dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
                             dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+                            const int rr = r + dr, cc = c + dc;
+                            pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[(int64_t)rr * im.pitch + cc] : 0;
                         } else {
-                            const char2 o = s_woff[q];
-                            dr = o.x;
-                            dc = o.y;
+                            // a 3D window reads its lower layer from the previous slice
+                            const char4 o = s_woff[q];
+                            const int rr = r + o.x, cc = c + o.y;
+                            const uint8_t *src = o.z ? im.below : im.pixels;
+                            pv = (src && rr >= 0 && rr < im.H && cc >= 0 && cc < im.W) ? src[(int64_t)rr * im.pitch + cc]
+                                                                                      : 0;
                         }
-                        const int rr = r + dr, cc = c + dc;
-                        const int pv = (rr >= 0 && cc >= 0 && cc < im.W) ? im.pixels[(int64_t)rr * im.pitch + cc] : 0;
                         v = tc::bf16_of_int(pv - 128);
                     }
                     pair |= v << (16 * hb);

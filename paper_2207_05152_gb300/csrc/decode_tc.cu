@@ -56,6 +56,7 @@ struct DecTcParams {
     int rcols;        // byte-ring columns kept per row (power of two)
     int gimg;         // 1: priors are read back from the output image (no ring; one
                       // cluster barrier per wave), for waves too long for the rings
+    int depth;        // slices per image (volumes); stream states are kept per slice
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -107,9 +108,9 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
     L.pg = take(4u * nt);
     L.dsym = take(prm.gimg ? 0u : (uint32_t)prm.list_rows);   // decoded pixels held back until the barrier
     L.lut = take(4u * 64);
-    L.st_x = take(4u * g);
-    L.st_pos = take(4u * g);
-    L.st_end = take(4u * g);
+    L.st_x = take(4u * g * prm.depth);
+    L.st_pos = take(4u * g * prm.depth);
+    L.st_end = take(4u * g * prm.depth);
     L.pay = take(2u * pay_words);
     L.total = off;
     return L;
@@ -270,8 +271,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     __shared__ uint64_t w3bar[kW3Stages];   // FP32: W3^T staging buffers filled
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok, s_S, s_err, s_fail;
+    __shared__ uint64_t s_next;   // byte offset of the next slice's container
 
-    __shared__ char2 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
+    __shared__ char4 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
     __shared__ uint32_t s_part[kDecThreads];
     __shared__ uint32_t s_gpart[kDecThreads];
 
@@ -312,9 +314,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
         if (tid < 64) lut[tid] = m.lut[tid];
         if (tid < m.n_in) {
-            int dr, dc;
-            window_offset(m, tid, dr, dc);
-            s_woff[tid] = make_char2((signed char)dr, (signed char)dc);
+            int dz, dr, dc;
+            window_offset(m, tid, dz, dr, dc);
+            s_woff[tid] = make_char4((signed char)dr, (signed char)dc, (signed char)dz, 0);
         }
         uint32_t *ring = reinterpret_cast<uint32_t *>(smem + L.ring);
         for (int i = tid; i < prm.ring_rows * prm.rcols / 4; i += kDecThreads) ring[i] = 0u;
@@ -336,34 +338,46 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         tc::fence_mbar_init();
         s_err = 0;
         s_fail = 0;
-
-        int ok = im.in_bytes >= (uint64_t)kHeaderBytes;
-        int S = 0;
-        if (ok) {
-            uint64_t hash = 0;
-            for (int q = 0; q < 8; q++) hash |= (uint64_t)in[16 + q] << (8 * q);
-            S = in[14] | (in[15] << 8);
-            const uint32_t hh = in[4] | (in[5] << 8) | (in[6] << 16) | ((uint32_t)in[7] << 24);
-            const uint32_t ww = in[8] | (in[9] << 8) | (in[10] << 16) | ((uint32_t)in[11] << 24);
-            ok = in[0] == 'D' && in[1] == 'L' && in[2] == 'C' && in[3] == '1' && hh == (uint32_t)H &&
-                 ww == (uint32_t)W && in[12] == m.wu && in[13] == m.precision && hash == m.hash && S >= 1 &&
-                 S <= H && (S + P - 1) / P <= prm.max_g && im.in_bytes >= (uint64_t)kHeaderBytes + 4ull * S;
-        }
-        s_ok = ok;
-        s_S = S;
+        s_ok = 1;
+        s_S = 0;
+        s_next = 0;
     }
     __syncthreads();
-    const int S = s_S;
-    const int G = (S - (int)k + P - 1) / P;    // streams owned by this CTA: s = k + P g
-    const float invS = 1.0f / (float)(S > 0 ? S : 1);
+    // Headers and streams of every slice: a 2D image is one slice; the
+    // slices of a volume (3D window) are back-to-back containers with the
+    // same stream count, their stream states kept at z * GS + g.
+    const bool vol = !DEF && m.vol != 0;
+    const int D = vol ? im.D : 1, GS = prm.max_g;
     uint32_t *st_x = reinterpret_cast<uint32_t *>(smem + L.st_x);
     uint32_t *st_pos = reinterpret_cast<uint32_t *>(smem + L.st_pos);
     uint32_t *st_end = reinterpret_cast<uint32_t *>(smem + L.st_end);
-    const uint16_t *pay = reinterpret_cast<const uint16_t *>(in + kHeaderBytes + 4 * S);
-    const uint16_t *wsrc = pay;
-    if (s_ok) {
+    const uint16_t *wsrc = nullptr;
+    for (int z = 0; z < D; z++) {
+        const uint64_t slice_off = s_next;
+        const uint8_t *sin = in + slice_off;
+        if (tid == 0) {
+            int ok = s_ok && im.in_bytes >= slice_off + (uint64_t)kHeaderBytes;
+            if (ok) {
+                uint64_t hash = 0;
+                for (int q = 0; q < 8; q++) hash |= (uint64_t)sin[16 + q] << (8 * q);
+                const int Sz = sin[14] | (sin[15] << 8);
+                const uint32_t hh = sin[4] | (sin[5] << 8) | (sin[6] << 16) | ((uint32_t)sin[7] << 24);
+                const uint32_t ww = sin[8] | (sin[9] << 8) | (sin[10] << 16) | ((uint32_t)sin[11] << 24);
+                ok = sin[0] == 'D' && sin[1] == 'L' && sin[2] == 'C' && sin[3] == '1' && hh == (uint32_t)H &&
+                     ww == (uint32_t)W && sin[12] == (m.wu | (vol ? 0x80 : 0)) && sin[13] == m.precision &&
+                     hash == m.hash && Sz >= 1 && Sz <= H && (Sz + P - 1) / P <= prm.max_g &&
+                     (z == 0 || Sz == s_S) && (!vol || Sz % P == 0) &&
+                     im.in_bytes >= slice_off + (uint64_t)kHeaderBytes + 4ull * Sz;
+                s_S = Sz;
+            }
+            if (!ok) s_ok = 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;   // uniform: every thread reads the same flag
+        const int S = s_S;
+        const uint16_t *pay = reinterpret_cast<const uint16_t *>(sin + kHeaderBytes + 4 * S);
         // exclusive scan of the word counts of all streams (chunked per thread)
-        const uint8_t *cnt = in + kHeaderBytes;
+        const uint8_t *cnt = sin + kHeaderBytes;
         const int per = (S + kDecThreads - 1) / kDecThreads;
         const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
         uint32_t sum = 0, gsum = 0;
@@ -387,20 +401,26 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 acc += v;
                 gacc += gv;
             }
-            if ((uint64_t)kHeaderBytes + 4ull * S + 2ull * acc != im.in_bytes) s_ok = 0;
+            // the slices fill the input exactly
+            const uint64_t next = slice_off + (uint64_t)kHeaderBytes + 4ull * S + 2ull * acc;
+            if (z == D - 1 ? next != im.in_bytes : next > im.in_bytes) s_ok = 0;
+            s_next = next;
             // payload of the owned streams staged in shared memory if it fits
-            s_fail = gacc <= (uint64_t)prm.pay_words ? 1 : 0;
+            // (2D images; a volume's streams read the input through L1)
+            s_fail = !vol && gacc <= (uint64_t)prm.pay_words ? 1 : 0;
         }
         __syncthreads();
         const bool staged = s_fail != 0;
+        // word index of this slice's payload relative to the stream source
+        const uint32_t word0 = vol ? (uint32_t)((slice_off + kHeaderBytes + 4ull * S) / 2) : 0u;
         if (s_ok) {
             uint16_t *spay = reinterpret_cast<uint16_t *>(smem + L.pay);
             uint32_t start = s_part[tid], lstart = s_gpart[tid];
             for (int s = s0; s < s1; s++) {
                 const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
                 if (s % P == (int)k) {
-                    const int g = s / P;
-                    const uint32_t base = staged ? lstart : start;
+                    const int g = z * GS + s / P;
+                    const uint32_t base = staged ? lstart : word0 + start;
                     st_x[g] = ((uint32_t)pay[start] << 16) | pay[start + 1];
                     st_pos[g] = base + 2;
                     st_end[g] = base + c;
@@ -410,14 +430,18 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 }
                 start += c;
             }
-            if (staged) wsrc = spay;
+            wsrc = vol ? reinterpret_cast<const uint16_t *>(in) : (staged ? spay : pay);
         }
         __syncthreads();
+        const int G = (S - (int)k + P - 1) / P;    // streams owned by this CTA: s = k + P g
         if (s_ok)
             for (int g = tid; g < G; g += kDecThreads)
-                if (st_x[g] < kRansL) s_err = 1;
+                if (st_x[z * GS + g] < kRansL) s_err = 1;
         if (tid == 0) s_fail = 0;
+        __syncthreads();
     }
+    const int S = s_S;
+    const float invS = 1.0f / (float)(S > 0 ? S : 1);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -574,10 +598,15 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     int *pixg = reinterpret_cast<int *>(smem + L.pg);
     uint8_t *dsym = smem + L.dsym;   // this wave's decoded pixels, by row-list index
     __shared__ int s_wcnt[kDecWarps];
-    const int T = 3 * (H - 1) + W;
+    // A volume's slices run as one 3D wavefront (Sec. IV "3D Wavefront"):
+    // pixel (z, r, c) is on wave 3r + c + VSH z, every slice VSH waves behind
+    // the one before it, so that the lower layer of its window is decoded.
+    const int T2 = 3 * (H - 1) + W;
+    const int VSH = vol ? volume_shift(m) : 0;
+    const int T = T2 + VSH * (D - 1);
     // When P divides S the owned rows of a wave are r0, r0 + P, ... and no
-    // row list is built.
-    const bool modrows = (S % P) == 0;
+    // row list is built (a volume lists (slice, row) pairs, with P | S).
+    const bool modrows = (S % P) == 0 && !vol;
     // Without a per-wave cluster barrier a decoded pixel goes to the image
     // at once; otherwise the stores wait until the barrier has been arrived at.
     const bool direct = p2p || P == 1 || gimg;
@@ -587,7 +616,40 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         // rows of this wave owned by this CTA, in increasing order
         int nk = 0;
         const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
-        if (modrows) {
+        if (vol) {
+            // the slices on this wave (t - VSH z in [0, T2)), in slice
+            // order, each with its owned rows r0(z), r0(z) + P, ...:
+            // thread = slice, block-wide exclusive scan of the counts
+            const int z_lo = t >= T2 ? (t - T2) / VSH + 1 : 0, z_hi = min(D - 1, t / VSH);
+            for (int zb = z_lo; zb <= z_hi; zb += kDecThreads) {
+                const int z = zb + tid;
+                int cnt = 0, rz = 0;
+                if (z <= z_hi) {
+                    const int tz = t - VSH * z;
+                    const int rl = tz - W + 1 > 0 ? (tz - W + 3) / 3 : 0, rh = min(H - 1, tz / 3);
+                    rz = rl + (((int)k - rl) & (P - 1));
+                    cnt = rz <= rh ? ((rh - rz) >> lgP) + 1 : 0;
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += o;
+                }
+                if (lane == 31) s_wcnt[warp] = incl;
+                __syncthreads();
+                int before = nk + incl - cnt, total = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < kDecWarps; w2++) {
+                    const int cw = s_wcnt[w2];
+                    before += w2 < warp ? cw : 0;
+                    total += cw;
+                }
+                for (int j = 0; j < cnt; j++) rowlist[before + j] = (z << 20) | (rz + (j << lgP));
+                nk += total;
+                __syncthreads();
+            }
+        } else if (modrows) {
             nk = r0 <= r_hi ? ((r_hi - r0) >> lgP) + 1 : 0;
         } else {
             for (int seg = r_lo; seg <= r_hi; seg += kDecThreads) {
@@ -609,7 +671,21 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
         }
         auto row_of = [&](int i) { return modrows ? r0 + (i << lgP) : rowlist[i]; };
-        const bool spread = r_hi - r_lo < S;
+        // (slice, row, column) of the wave's i-th owned pixel
+        auto pix_of = [&](int i, int &z, int &r, int &c) {
+            if (vol) {
+                const int e = rowlist[i];
+                z = e >> 20;
+                r = e & 0xFFFFF;
+                c = t - VSH * z - 3 * r;
+            } else {
+                z = 0;
+                r = row_of(i);
+                c = t - 3 * r;
+            }
+        };
+        // no two rows of a slice's wave share a stream
+        const bool spread = vol ? min(H, (W + 2) / 3) <= S : r_hi - r_lo < S;
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
@@ -623,26 +699,30 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 if (q > NPRI) continue;
                 uint32_t v = 0x80u;
                 if (px < nc) {
-                    const int r = row_of(base + px), c = t - 3 * r;
+                    int z, r, c;
+                    pix_of(base + px, z, r, c);
                     if (q == NPRI) {
                         // local stream of the pixel and the warp that runs its
                         // table: by pixel when no two rows of the wave share a
                         // stream, else by stream so that they run in row order
-                        const int g = fast_mod(r, S, invS) >> lgP;
+                        const int g = z * GS + (fast_mod(r, S, invS) >> lgP);
                         pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
                         continue;
                     }
-                    int dr, dc;
+                    int dr, dc, dz = 0;
                     if (DEF) {
                         dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
                         dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
                     } else {
-                        const char2 o = s_woff[q];
+                        const char4 o = s_woff[q];
                         dr = o.x;
                         dc = o.y;
+                        dz = o.z;
                     }
-                    const int rr = r + dr, cc = c + dc;
-                    if (rr < 0 || cc < 0 || cc >= W) {
+                    const int rr = r + dr, cc = c + dc, zz = z + dz;
+                    // (a 3D window's lower layer may reach below the row and
+                    // off the first slice)
+                    if (rr < 0 || cc < 0 || cc >= W || (vol && (zz < 0 || rr >= H))) {
                         v = 0u;
                     } else if (p2p) {
                         // entry (round of rr, row distance, column mod tcols)
@@ -664,7 +744,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         v &= 0xFFu;
                     } else if (gimg) {
                         // stored to the image before the last wave's barrier
-                        v = __ldcg(im.pixels + (int64_t)rr * im.pitch + cc);
+                        v = __ldcg(im.pixels + (int64_t)zz * im.slice_pitch + (int64_t)rr * im.pitch + cc);
                     } else {
                         v = ring[(rr & rmask) * RCOLS + (cc & rcmask)];
                     }
@@ -808,7 +888,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 const int pg = pixg[i];
                 if ((pg >> 24) != warp) continue;
                 const int g = pg & 0xFFFFFF;
-                const int r = row_of(base + i), c = t - 3 * r;
+                int zs, r, c;
+                pix_of(base + i, zs, r, c);
                 const uint32_t x = st_x[g];
                 // the stream's next word, fetched before it is known to be needed
                 const uint32_t pos = st_pos[g], pend = st_end[g];
@@ -893,7 +974,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     }
                     st_x[g] = xn;
                     if (direct)
-                        im.pixels[(int64_t)r * im.pitch + c] = (uint8_t)sym;
+                        im.pixels[(int64_t)zs * im.slice_pitch + (int64_t)r * im.pitch + c] = (uint8_t)sym;
                     else
                         dsym[base + i] = (uint8_t)sym;
                 }
@@ -928,8 +1009,13 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 if (!tc::mbar_wait(&w3bar[q % kW3Stages], (uint32_t)(q / kW3Stages) & 1u, kDecWaitLimit)) s_fail = 1;
     }
     // final states must be back at the initial value with every word read
-    for (int g = tid; g < G; g += kDecThreads)
-        if (st_x[g] != kRansL || st_pos[g] != st_end[g]) s_err = 1;
+    {
+        const int G = (S - (int)k + P - 1) / P;
+        for (int i = tid; i < D * G; i += kDecThreads) {
+            const int g = (i / G) * GS + i % G;
+            if (st_x[g] != kRansL || st_pos[g] != st_end[g]) s_err = 1;
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0 && (s_err || s_fail))
@@ -1039,9 +1125,10 @@ static cudaError_t smem_limit(void (*kern)(DevModel, DecBatch, DecTcParams), uin
 // within `limit` bytes.  In order of preference: the tagged ring; (INT8)
 // smaller pixel chunks; the byte ring with one cluster barrier per wave;
 // priors read back from the output image.  False when none fits.
-static bool plan_wave(const DevModel &m, int maxH, int maxW, int P, uint32_t limit, int plan, DecTcParams &prm) {
+static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, uint32_t limit, int plan,
+                      DecTcParams &prm) {
     const bool f32 = m.precision == DLIC_FP32;
-    const int wave_px = min(maxH, (maxW + 2) / 3);   // rows of the longest wave
+    const int wave_px = min(maxH, (maxW + 2) / 3);   // rows of the longest wave (per slice)
     const int per_cta = (wave_px + P - 1) / P + 1;
     prm = DecTcParams{};
     prm.P = P;
@@ -1059,6 +1146,14 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int P, uint32_t lim
     while (rows < wave_px + m.wu + 2) rows <<= 1;
     prm.ring_rows = rows;
     prm.list_rows = (wave_px + 15) & ~15;
+    prm.depth = 1;
+    if (m.vol) {
+        // a volume's wave holds the slices t - VSH z in [0, 3(H-1) + W), each
+        // with at most ceil(wave_px / P) rows of a CTA (P divides S)
+        const int active = min(maxD, (3 * (maxH - 1) + maxW) / volume_shift(m) + 1);
+        prm.depth = maxD;
+        prm.list_rows = (active * ((wave_px + P - 1) / P) + 15) & ~15;
+    }
     // Tagged ring (neighbour-to-neighbour mode) only when it stays small.
     // Rows sharing a tagged-ring slot are P * tq apart: more than the rows
     // of a wave plus the rows above and a writer's lead (P - 1 waves), with
@@ -1069,13 +1164,14 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int P, uint32_t lim
         while (tq < (wave_px + m.wu + P + P - 1) / P + 1) tq <<= 1;
         if (4 * prm.tcols * prm.tslots * tq > 48 * 1024) tq = 0;
     }
-    prm.tq = plan == DLIC_PLAN_AUTO ? tq : 0;
+    prm.tq = plan == DLIC_PLAN_AUTO && !m.vol ? tq : 0;
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
     prm.pay_words = 0;
     auto size = [&] { return dec_layout(prm, f32).total; };
     while (!f32 && size() > limit && prm.nt > 16) prm.nt /= 2;
     if (size() > limit) prm.tq = 0;
-    if (size() > limit || plan == DLIC_PLAN_IMAGE) {
+    // volumes read every prior back from the output volume
+    if (size() > limit || plan == DLIC_PLAN_IMAGE || m.vol) {
         prm.gimg = 1;
         prm.ring_rows = 0;
     }
@@ -1088,11 +1184,11 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int P, uint32_t lim
     return true;
 }
 
-bool wave_decode_fits(const DevModel &m, int H, int W, int P, int plan) {
+bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan) {
     if (m.precision == DLIC_FP32 && default_window(m)) return true;   // the one-CTA decoder takes the rest
     uint32_t limit = 0;
     DecTcParams prm;
-    return smem_limit(wave_kernel(m), limit) == cudaSuccess && plan_wave(m, H, W, P, limit, plan, prm);
+    return smem_limit(wave_kernel(m), limit) == cudaSuccess && plan_wave(m, H, W, D, P, limit, plan, prm);
 }
 
 // Launches one cluster of `cluster` CTAs per image of the batch (stepping
@@ -1102,17 +1198,18 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     const bool f32 = m.precision == DLIC_FP32;
     void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m);
     if (b.n == 0) return cudaSuccess;
-    int maxH = 1, maxW = 1;
+    int maxH = 1, maxW = 1, maxD = 1;
     for (int i = 0; i < b.n; i++) {
         maxH = max(maxH, b.img[i].H);
         maxW = max(maxW, b.img[i].W);
+        maxD = max(maxD, b.img[i].D);
     }
     int P = cluster > 0 ? cluster : 1;
     uint32_t limit = 0;
     cudaError_t e = smem_limit(kern, limit);
     if (e != cudaSuccess) return e;
     DecTcParams prm;
-    if (!plan_wave(m, maxH, maxW, P, limit, plan, prm))
+    if (!plan_wave(m, maxH, maxW, maxD, P, limit, plan, prm))
         return f32 && default_window(m) ? launch_decode_cc(m, b, st) : cudaErrorNotSupported;
     const DecTcLayout L = dec_layout(prm, f32);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);

@@ -23,8 +23,11 @@ struct DevModel {
     int precision;   // DLIC_FP32 / DLIC_INT8
     int h1, h2;
     // causal window: rows r-wu..r-1 at columns c-wl..c+wr, then row r at
-    // columns c-wl..c-1 (n_in priors in that order); (2, 2, 2) by default
+    // columns c-wl..c-1 (n2 priors in that order); (2, 2, 2) by default.
+    // A 3D window (vol = 1) adds the previous slice's rows r-pu..r+pd at
+    // columns c-pl..c+pr (Sec. IV "3D Dependencies"): n_in = n2 + n3.
     int wu, wl, wr, n_in;
+    int vol, pu, pd, pl, pr, n2;
     float tscale;
     const uint32_t *lut;          // 64 entries
     // FP32 network, transposed: WkT[k * out + j] = W[j][k]
@@ -42,6 +45,7 @@ struct DevModel {
 // Per-image encode descriptor.
 struct EncImage {
     const uint8_t *pixels;
+    const uint8_t *below;         // previous slice of a volume (3D window), or null
     int64_t pitch;
     int32_t H, W, S;
     int32_t tile_begin;           // first 128-pixel tile of this image
@@ -53,6 +57,7 @@ struct EncImage {
 };
 
 constexpr int kMaxBatch = 192;    // images per launch (kernel-parameter space)
+constexpr int kMaxSlices = 2047;  // slices per volume (11 bits in the decoder's row list)
 constexpr int kPredictTile = 64;  // pixels per CUDA-core prediction CTA
 
 struct EncBatch {
@@ -68,7 +73,9 @@ struct EncBatch {
 struct DecImage {
     uint8_t *pixels;
     int64_t pitch;
+    int64_t slice_pitch;          // volumes: bytes between slices
     int32_t H, W;
+    int32_t D;                    // slices (1 for a 2D image)
     uint64_t in_off;              // byte offset of the bitstream in d_in
     uint64_t in_bytes;
     uint64_t st_off;              // per-stream state (x, pos, end) in workspace
@@ -105,7 +112,7 @@ cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t 
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)
-bool wave_decode_fits(const DevModel &m, int H, int W, int P, int plan);
+bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan);
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
 double decode_estimate(int H, int W, int P, bool f32);   // cycles, the autotuner's cost model
 
@@ -149,17 +156,28 @@ __host__ __device__ inline int64_t stream_pos(int H, int W, int S, int r, int c)
 }
 
 // Offsets (dr, dc) of prior q of the model's window.
-__host__ __device__ inline void window_offset(const DevModel &m, int q, int &dr, int &dc) {
+// (slice, row, column) offset of prior q: dz = -1 for the previous slice
+__host__ __device__ inline void window_offset(const DevModel &m, int q, int &dz, int &dr, int &dc) {
     const int wid = m.wl + m.wr + 1;
+    dz = 0;
     if (q < m.wu * wid) {
         dr = -m.wu + q / wid;
         dc = -m.wl + q % wid;
-    } else {
+    } else if (q < m.n2) {
         dr = 0;
         dc = -m.wl + (q - m.wu * wid);
+    } else {
+        const int wid3 = m.pl + m.pr + 1, k = q - m.n2;
+        dz = -1;
+        dr = -m.pu + k / wid3;
+        dc = -m.pl + k % wid3;
     }
 }
-__host__ __device__ inline bool default_window(const DevModel &m) { return m.wu == 2 && m.wl == 2 && m.wr == 2; }
+__host__ __device__ inline bool default_window(const DevModel &m) {
+    return m.wu == 2 && m.wl == 2 && m.wr == 2 && !m.vol;
+}
+// waves by which a slice lags the one before in the 3D wavefront
+__host__ __device__ inline int volume_shift(const DevModel &m) { return 3 * m.pd + m.pr + 1; }
 
 // Index of pixel (r, c) in the stream-ordered per-pixel table buffer.
 __host__ __device__ inline int64_t stream_index(int H, int W, int S, int r, int c) {
