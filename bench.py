@@ -258,6 +258,7 @@ def run_ours(args):
 
     train = measure_train(args)
     batch = measure_batch(args)
+    volume = measure_volume(args)
     domain = measure_domain_training(args)
 
     # max over ranks of the timed totals
@@ -303,6 +304,7 @@ def run_ours(args):
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
         "train": train,
         "batch": batch,
+        "volume": volume,
         "domain_training": domain,
         "gpu_launches": K * (LAUNCHES_PER_STEP["encode"] + LAUNCHES_PER_STEP["decode"]),
         "clocks": r8["clocks"],
@@ -397,6 +399,77 @@ def measure_batch(args):
     res["fp32_path"] = {"enc_mpix_s": round(npx / (e0.elapsed_time(e1) * 1e-3) / 1e6, 2),
                         "dec_mpix_s": round(npx / (e1.elapsed_time(e2) * 1e-3) / 1e6, 2),
                         "bpp": round(8.0 * o32[-1] / npx, 4), "roundtrip_bit_exact": ok32}
+    codec.close()
+    return res
+
+
+def measure_volume(args):
+    """A scan of 35 slices of 256 x 256 (the size of the paper's Table III)
+    coded with a 3D window: the default 2D window plus the 3 x 3
+    neighbourhood one slice down, INT8 21-128-128-256.  Every slice is its own
+    container; decode runs all slices at once as a 3D wavefront (one cluster).
+    For context: the same slices with the 2D model, as a batch of 35 images."""
+    import torch
+    from paper_2207_05152_gb300 import _lib, model as M, workloads
+    from paper_2207_05152_gb300.codec import Codec
+    vol = workloads.volume_scan()
+    D, H, W = vol.shape
+    npx = int(vol.size)
+    _, blob3, _ = workloads.models(window=M.VOLUME_WINDOW)
+    codec = Codec(blob3)
+    dv = torch.from_numpy(vol).cuda()
+    S = _lib.dlic_auto_streams(H, W)
+    out, offs = codec.encode_volume([dv], [S])
+    torch.cuda.synchronize()
+    o = offs.cpu().tolist()
+    dec = torch.empty_like(dv)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    codec.decode_volume(out, [0, o[-1]], [vol.shape], [S], outs=[dec], status=status)
+    torch.cuda.synchronize()
+    ok = int(status.item()) == 0 and torch.equal(dec, dv)
+    stream = torch.cuda.current_stream()
+    enc, dcd = [], []
+    for it in range(max(2, args.steps // 3) + 1):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        codec.encode_volume([dv], [S])
+        e1.record(stream)
+        codec.decode_volume(out, [0, o[-1]], [vol.shape], [S], outs=[dec], status=status)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if it:
+            enc.append(e0.elapsed_time(e1))
+            dcd.append(e1.elapsed_time(e2))
+    ok = ok and int(status.item()) == 0 and torch.equal(dec, dv)
+    codec.close()
+    shift = M.volume_wave_shift(M.VOLUME_WINDOW)
+    T2 = 3 * (H - 1) + W
+    res = {"workload": f"{D} x {H} x {W} phantom scan, INT8 21-128-128-256, 3D window (2,2,2) + 3x3 one slice "
+                       f"down, {S} streams per slice", "voxels": npx,
+           "enc_mpix_s": round(npx / (statistics.mean(enc) * 1e-3) / 1e6, 2),
+           "dec_mpix_s": round(npx / (statistics.mean(dcd) * 1e-3) / 1e6, 2),
+           "dec_ms": round(statistics.mean(dcd), 3), "bpp": round(8.0 * o[-1] / npx, 4),
+           "roundtrip_bit_exact": ok, "waves_3d": T2 + shift * (D - 1), "first_slice_waves": T2,
+           "slice_by_slice_waves": D * T2}
+    # the 2D model (same weights without the lower layer) on the same slices
+    _, blob2, _ = workloads.models()
+    codec = Codec(blob2)
+    slices = [dv[z] for z in range(D)]
+    out2, offs2 = codec.encode(slices, [S] * D)
+    torch.cuda.synchronize()
+    o2 = offs2.cpu().tolist()
+    decs = [torch.empty_like(x) for x in slices]
+    st2 = torch.zeros(D, dtype=torch.int32, device="cuda")
+    codec.decode(out2, o2, [(H, W)] * D, outs=decs, status=st2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    codec.decode(out2, o2, [(H, W)] * D, outs=decs, status=st2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["2d_window_same_slices"] = {"bpp": round(8.0 * o2[-1] / npx, 4),
+                                    "dec_mpix_s": round(npx / (e0.elapsed_time(e1) * 1e-3) / 1e6, 2),
+                                    "roundtrip_bit_exact": st2.cpu().tolist() == [0] * D and all(
+                                        torch.equal(a, b) for a, b in zip(decs, slices))}
     codec.close()
     return res
 

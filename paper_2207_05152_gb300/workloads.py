@@ -2,6 +2,8 @@
 
 cfg2: one 512 x 512 Voronoi image, INT8 (and FP32) network 12-128-128-256
       with synthetic predictive weights, 256 rANS streams.
+volume: a 35 x 256 x 256 phantom scan (Table III's size) with the 3D window
+      (2, 2, 2) + the 3 x 3 neighbourhood one slice down, 21-128-128-256.
 fig6: the cfg2 image and streams with the 9 x 9 causal window of Fig. 6
       (78 priors), network 78-128-128-256.
 cfg4: a batch of Voronoi images of uneven sizes (default 64, heights
@@ -19,7 +21,10 @@ WIDTHS = [12, 128, 128, 256]
 
 def calibration_contexts(seed: int = 4242, count: int = 4096, window=M.DEFAULT_WINDOW) -> np.ndarray:
     """Priors of `count` pixels of a separate synthetic image (0 outside
-    it), the calibration data of the INT8 quantisation."""
+    it), the calibration data of the INT8 quantisation; for a 3D window, of
+    voxels of a separate synthetic volume."""
+    if M.is_volume(window):
+        return _volume_calibration(seed, count, window)
     cal_img = synth.voronoi_image(256, 256, seed)
     rng = synth.Rng(seed + 1)
     rr = rng.integers(count, 0, 255)
@@ -32,6 +37,28 @@ def calibration_contexts(seed: int = 4242, count: int = 4096, window=M.DEFAULT_W
             if 0 <= y < 256 and 0 <= x < 256:
                 out[n, k] = cal_img[y, x]
     return out
+
+
+def _volume_calibration(seed: int, count: int, window) -> np.ndarray:
+    cal = synth.phantom_volume(8, 128, 128, seed)
+    rng = synth.Rng(seed + 1)
+    zz = rng.integers(count, 0, 7)
+    rr = rng.integers(count, 0, 127)
+    cc = rng.integers(count, 0, 127)
+    offs = M.window_offsets3(window)
+    out = np.zeros((count, len(offs)), np.uint8)
+    for n, (z, r, c) in enumerate(zip(zz, rr, cc)):
+        for k, (dz, dr, dc) in enumerate(offs):
+            v, y, x = int(z) + dz, int(r) + dr, int(c) + dc
+            if v >= 0 and 0 <= y < 128 and 0 <= x < 128:
+                out[n, k] = cal[v, y, x]
+    return out
+
+
+def volume_scan(depth: int = 35, size: int = 256, seed: int = 5100) -> np.ndarray:
+    """A synthetic scan of `depth` slices of size x size (the 256 x 256 x 35
+    of the paper's Table III by default)."""
+    return synth.phantom_volume(depth, size, size, seed)
 
 
 def models(seed: int = 2, window=M.DEFAULT_WINDOW, hidden: int = 128):
