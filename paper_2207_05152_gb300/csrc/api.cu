@@ -507,9 +507,14 @@ struct DecItem {
     int64_t pitch, slice_pitch;
 };
 
+// per item: stream states (a volume's: header, x, position, end per stream)
+static size_t dec_item_bytes(const DecItem &e) {
+    return e.D > 1 || e.S ? align256(256 + 12ull * e.D * e.S) : align256(16ull * e.H);
+}
+
 static size_t dec_ws_bytes(const std::vector<DecItem> &it) {
     size_t total = 0;
-    for (const DecItem &e : it) total += align256(16ull * e.H);
+    for (const DecItem &e : it) total += dec_item_bytes(e);
     return total < 256 ? 256 : total;
 }
 
@@ -572,7 +577,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         size_t off = 0;
         for (int i = 0; i < n; i++) {
             st_off[i] = off;
-            off += align256(16ull * it[i].H);
+            off += dec_item_bytes(it[i]);
         }
     }
     // cluster size of every image (1 on the CUDA-core path)
@@ -581,11 +586,17 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         Hs[i] = it[i].H;
         Ws[i] = it[i].W;
     }
+    // volumes that the whole GPU decodes, one after another (cluster size 0:
+    // in no group)
+    std::vector<char> on_grid(n, 0);
     if (use_wave) {
         if (vol) {
-            // a volume's wave spans its slices: the largest cluster that
-            // divides its stream count (each CTA owns the rows k mod P)
+            // a volume's wave spans its slices: every SM (cooperative grid),
+            // else the largest cluster that divides its stream count (each
+            // CTA owns the rows k mod P)
             for (int i = 0; i < n; i++) {
+                on_grid[i] = m->decode_plan == DLIC_PLAN_AUTO &&
+                             grid_decode_eligible(m->dev, it[i].H, it[i].W, it[i].D, it[i].S);
                 P[i] = 16;
                 while (it[i].S % P[i]) P[i] >>= 1;
             }
@@ -594,9 +605,38 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         }
         // checked before anything is enqueued
         for (int i = 0; i < n; i++)
-            if (!wave_decode_fits(m->dev, Hs[i], Ws[i], it[i].D, P[i], m->decode_plan))
+            if (!on_grid[i] && !wave_decode_fits(m->dev, Hs[i], Ws[i], it[i].D, P[i], m->decode_plan))
                 return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d (x %d) needs more shared memory than the "
                             "decoder's plans allow", i, Hs[i], Ws[i], it[i].D);
+    }
+    auto fill = [&](DecImage &e, int i) {
+        const DecItem &g = it[i];
+        e.pixels = g.pixels;
+        e.pitch = g.pitch;
+        e.slice_pitch = g.slice_pitch;
+        e.H = g.H;
+        e.W = g.W;
+        e.D = g.D;
+        e.S = g.S;
+        e.in_off = h_in_offsets[i];
+        e.in_bytes = h_in_offsets[i + 1] - h_in_offsets[i];
+        e.st_off = st_off[i];
+        e.sidx = i;
+    };
+    for (int i = 0; i < n; i++) {
+        if (!on_grid[i]) continue;
+        P[i] = 0;
+        DecBatch *b = new DecBatch();
+        b->n = 1;
+        b->in = static_cast<const uint8_t *>(d_in);
+        b->ws = static_cast<uint8_t *>(d_ws);
+        b->status = d_status;
+        fill(b->img[0], i);
+        cudaError_t e = launch_decode_grid(m->dev, *b, m->num_sms, cs);
+        delete b;
+        if (e != cudaSuccess)
+            return e == cudaErrorNotSupported ? fail(DLIC_ERR_UNSUPPORTED, "volume %d: the grid decoder does not fit", i)
+                                              : cuda_fail(e, "grid decode launch");
     }
     int groups_used = 0;
     for (int gi = 0; gi < kDecodeGroups; gi++)
@@ -638,21 +678,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
             b->in = static_cast<const uint8_t *>(d_in);
             b->ws = static_cast<uint8_t *>(d_ws);
             b->status = d_status;
-            for (int k = 0; k < cn; k++) {
-                const int i = members[c0 + k];
-                const DecItem &g = it[i];
-                DecImage &e = b->img[k];
-                e.pixels = g.pixels;
-                e.pitch = g.pitch;
-                e.slice_pitch = g.slice_pitch;
-                e.H = g.H;
-                e.W = g.W;
-                e.D = g.D;
-                e.in_off = h_in_offsets[i];
-                e.in_bytes = h_in_offsets[i + 1] - h_in_offsets[i];
-                e.st_off = st_off[i];
-                e.sidx = i;
-            }
+            for (int k = 0; k < cn; k++) fill(b->img[k], members[c0 + k]);
             cudaError_t e = use_wave ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs) : launch_decode_cc(m->dev, *b, gs);
             delete b;
             if (e != cudaSuccess && err == DLIC_OK)

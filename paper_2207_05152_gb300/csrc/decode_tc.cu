@@ -38,7 +38,7 @@ struct DecTcLayout {
     // FP32 network: W1^T | b1 | b2 | b3, W2^T, the W3^T staging ring, FP32
     // inputs and activations (the logits z overlay xs and h1t)
     uint32_t wf, w2f, w3s, xs, h1t, h2t;
-    uint32_t z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, total;
+    uint32_t z, ring, tring, rows, pg, dsym, lut, st_x, st_pos, st_end, pay, zpre, total;
 };
 
 struct DecTcParams {
@@ -57,6 +57,7 @@ struct DecTcParams {
     int gimg;         // 1: priors are read back from the output image (no ring; one
                       // cluster barrier per wave), for waves too long for the rings
     int depth;        // slices per image (volumes); stream states are kept per slice
+    int zlist;        // grid decoder: capacity of the per-wave table of active slices
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -106,6 +107,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
     L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * prm.list_rows);
     L.pg = take(4u * nt);
+    L.zpre = take(4u * prm.zlist);
     L.dsym = take(prm.gimg ? 0u : (uint32_t)prm.list_rows);   // decoded pixels held back until the barrier
     L.lut = take(4u * 64);
     L.st_x = take(4u * g * prm.depth);
@@ -136,6 +138,28 @@ __device__ __forceinline__ void st_cluster_u8(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid decoder of a volume: the volume's state block in the workspace, at
+// im.st_off: a 256-byte header (stream count, ok flag, wave-barrier counter,
+// failure flag), then x, position and end of every stream (z S + s).
+struct VolState {
+    uint32_t *hdr, *x, *pos, *end;
+};
+__host__ __device__ inline size_t vol_state_bytes(int D, int S) { return 256 + 12ull * D * S; }
+__device__ __forceinline__ VolState vol_state(const DecBatch &b, const DecImage &im) {
+    VolState v;
+    v.hdr = reinterpret_cast<uint32_t *>(b.ws + im.st_off);
+    v.x = v.hdr + 64;
+    v.pos = v.x + (size_t)im.D * im.S;
+    v.end = v.pos + (size_t)im.D * im.S;
+    return v;
+}
+
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.volatile.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(tc::smem_addr(p)) : "memory");
@@ -260,11 +284,119 @@ __device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, i
     }
 }
 
+// Grid decoder of a volume, before the wave kernel: walks the slices'
+// containers (back to back; each header checked against the model and the
+// volume), and writes every stream's initial state, read position and end
+// to the volume's state block.  One CTA.
+__global__ void __launch_bounds__(kDecThreads) k_volume_setup(DevModel m, DecBatch b) {
+    __shared__ uint32_t s_part[kDecThreads];
+    __shared__ int s_ok;
+    __shared__ uint64_t s_next;
+    const int tid = threadIdx.x;
+    const DecImage &im = b.img[0];
+    const uint8_t *in = b.in + im.in_off;
+    const VolState vs = vol_state(b, im);
+    const int S = im.S, H = im.H, W = im.W;
+    if (tid == 0) {
+        s_ok = 1;
+        s_next = 0;
+        vs.hdr[0] = (uint32_t)S;
+        vs.hdr[2] = 0u;   // wave-barrier arrivals
+        vs.hdr[3] = 0u;   // a wait ran out
+    }
+    __syncthreads();
+    for (int z = 0; z < im.D; z++) {
+        const uint64_t off = s_next;
+        const uint8_t *sin = in + off;
+        if (tid == 0) {
+            int ok = im.in_bytes >= off + (uint64_t)kHeaderBytes;
+            if (ok) {
+                uint64_t hash = 0;
+                for (int q = 0; q < 8; q++) hash |= (uint64_t)sin[16 + q] << (8 * q);
+                const uint32_t hh = sin[4] | (sin[5] << 8) | (sin[6] << 16) | ((uint32_t)sin[7] << 24);
+                const uint32_t ww = sin[8] | (sin[9] << 8) | (sin[10] << 16) | ((uint32_t)sin[11] << 24);
+                ok = sin[0] == 'D' && sin[1] == 'L' && sin[2] == 'C' && sin[3] == '1' && hh == (uint32_t)H &&
+                     ww == (uint32_t)W && sin[12] == (m.wu | 0x80) && sin[13] == m.precision && hash == m.hash &&
+                     (sin[14] | (sin[15] << 8)) == S && im.in_bytes >= off + (uint64_t)kHeaderBytes + 4ull * S;
+            }
+            if (!ok) s_ok = 0;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const uint8_t *cnt = sin + kHeaderBytes;
+        const uint16_t *pay = reinterpret_cast<const uint16_t *>(sin + kHeaderBytes + 4 * S);
+        const int per = (S + kDecThreads - 1) / kDecThreads;
+        const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
+        uint32_t sum = 0;
+        int bad = 0;
+        for (int s = s0; s < s1; s++) {
+            const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
+            bad |= c < 2;
+            sum += c;
+        }
+        s_part[tid] = sum;
+        if (bad) s_ok = 0;
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t acc = 0;
+            for (int q = 0; q < kDecThreads; q++) {
+                const uint32_t v = s_part[q];
+                s_part[q] = (uint32_t)acc;
+                acc += v;
+            }
+            const uint64_t next = off + (uint64_t)kHeaderBytes + 4ull * S + 2ull * acc;
+            if (z == im.D - 1 ? next != im.in_bytes : next > im.in_bytes) s_ok = 0;
+            s_next = next;
+        }
+        __syncthreads();
+        if (s_ok) {
+            // positions count 16-bit words from the start of the volume
+            const uint32_t word0 = (uint32_t)((off + kHeaderBytes + 4ull * S) / 2);
+            uint32_t start = s_part[tid];
+            for (int s = s0; s < s1; s++) {
+                const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
+                const size_t g = (size_t)z * S + s;
+                const uint32_t x = ((uint32_t)pay[start] << 16) | pay[start + 1];
+                if (x < kRansL) s_ok = 0;
+                vs.x[g] = x;
+                vs.pos[g] = word0 + start + 2;
+                vs.end[g] = word0 + start + c;
+                start += c;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        vs.hdr[1] = (uint32_t)s_ok;
+        if (!s_ok) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
+    }
+}
+
+// Grid decoder of a volume, after the wave kernel: every stream must be back
+// at the initial state with every word read.  One CTA.
+__global__ void __launch_bounds__(kDecThreads) k_volume_finish(DecBatch b) {
+    const DecImage &im = b.img[0];
+    const VolState vs = vol_state(b, im);
+    if (!vs.hdr[1]) return;   // the setup found a bad header (already reported)
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const size_t n = (size_t)im.D * im.S;
+    for (size_t g = threadIdx.x; g < n; g += kDecThreads)
+        if (vs.x[g] != kRansL || vs.pos[g] != vs.end[g]) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && (s_bad || vs.hdr[3]))
+        atomicMax(b.status + im.sidx, vs.hdr[3] ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
+}
+
 // The wavefront decoder for one image per cluster; F32 selects the FP32
 // network on the CUDA cores instead of the INT8 network on the tensor cores.
 // DEF compiles the default window (the 12 priors of Fig. 2: two rows above,
-// two columns either side) with its sizes and offsets as constants.
-template <bool F32, bool DEF>
+// two columns either side) with its sizes and offsets as constants.  GRID
+// decodes one volume with every CTA of a cooperative grid (no cluster):
+// each wave's pixels are split evenly over the CTAs, stream states live in
+// the workspace and the waves are separated by a grid-wide barrier.
+template <bool F32, bool DEF, bool GRID>
 __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b, const DecTcParams &prm) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
@@ -281,7 +413,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const int P = prm.P, NT = prm.nt;
     const int lgP = __ffs(P) - 1;                 // P is a power of two
     const uint32_t k = P > 1 ? cluster_rank() : 0u;
-    const int img_idx = blockIdx.x / P;
+    const int img_idx = GRID ? 0 : blockIdx.x / P;
     const DecImage &im = b.img[img_idx];
     const uint8_t *in = b.in + im.in_off;
     const int H = im.H, W = im.W;
@@ -352,7 +484,20 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     uint32_t *st_pos = reinterpret_cast<uint32_t *>(smem + L.st_pos);
     uint32_t *st_end = reinterpret_cast<uint32_t *>(smem + L.st_end);
     const uint16_t *wsrc = nullptr;
-    for (int z = 0; z < D; z++) {
+    if constexpr (GRID) {
+        // states written by k_volume_setup; every CTA reads the same flag
+        const VolState vs = vol_state(b, im);
+        if (tid == 0) {
+            s_S = (int)__ldcg(vs.hdr);
+            s_ok = (int)__ldcg(vs.hdr + 1);
+        }
+        st_x = vs.x;
+        st_pos = vs.pos;
+        st_end = vs.end;
+        wsrc = reinterpret_cast<const uint16_t *>(in);
+        __syncthreads();
+    }
+    for (int z = 0; z < (GRID ? 0 : D); z++) {
         const uint64_t slice_off = s_next;
         const uint8_t *sin = in + slice_off;
         if (tid == 0) {
@@ -595,6 +740,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     };
 
     int *rowlist = reinterpret_cast<int *>(smem + L.rows);
+    int *zpre = reinterpret_cast<int *>(smem + L.zpre);   // grid decoder: first index of each active slice
     int *pixg = reinterpret_cast<int *>(smem + L.pg);
     uint8_t *dsym = smem + L.dsym;   // this wave's decoded pixels, by row-list index
     __shared__ int s_wcnt[kDecWarps];
@@ -616,7 +762,56 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         // rows of this wave owned by this CTA, in increasing order
         int nk = 0;
         const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
-        if (vol) {
+        if (GRID) {
+            // every row of the slices on this wave, in slice order; this CTA
+            // takes the indices [kb n / NB, (kb + 1) n / NB): thread = slice,
+            // block-wide exclusive scan of the row counts into zpre
+            const int z_lo = t >= T2 ? (t - T2) / VSH + 1 : 0, z_hi = min(D - 1, t / VSH);
+            const int nz = z_hi - z_lo + 1;
+            int n = 0;
+            for (int zb = 0; zb < nz; zb += kDecThreads) {
+                const int zi = zb + tid;
+                int cnt = 0;
+                if (zi < nz) {
+                    const int tz = t - VSH * (z_lo + zi);
+                    const int rl = tz - W + 1 > 0 ? (tz - W + 3) / 3 : 0, rh = min(H - 1, tz / 3);
+                    cnt = rh - rl + 1;
+                }
+                int incl = cnt;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += o;
+                }
+                if (lane == 31) s_wcnt[warp] = incl;
+                __syncthreads();
+                int before = n + incl - cnt, total = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < kDecWarps; w2++) {
+                    const int cw = s_wcnt[w2];
+                    before += w2 < warp ? cw : 0;
+                    total += cw;
+                }
+                if (zi < nz) zpre[zi] = before;
+                n += total;
+                __syncthreads();
+            }
+            const int NB = (int)gridDim.x, kb = (int)blockIdx.x;
+            const int i0 = (int)((long long)n * kb / NB), i1 = (int)((long long)n * (kb + 1) / NB);
+            nk = i1 - i0;
+            for (int j = tid; j < nk; j += kDecThreads) {
+                const int gi = i0 + j;
+                int lo = 0, hi = nz - 1;   // the last slice whose first index is <= gi
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (zpre[mid] <= gi) lo = mid; else hi = mid - 1;
+                }
+                const int z = z_lo + lo, tz = t - VSH * z;
+                const int rl = tz - W + 1 > 0 ? (tz - W + 3) / 3 : 0;
+                rowlist[j] = (z << 20) | (rl + gi - zpre[lo]);
+            }
+            __syncthreads();
+        } else if (vol) {
             // the slices on this wave (t - VSH z in [0, T2)), in slice
             // order, each with its owned rows r0(z), r0(z) + P, ...:
             // thread = slice, block-wide exclusive scan of the counts
@@ -685,7 +880,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
         };
         // no two rows of a slice's wave share a stream
-        const bool spread = vol ? min(H, (W + 2) / 3) <= S : r_hi - r_lo < S;
+        const bool spread = GRID || (vol ? min(H, (W + 2) / 3) <= S : r_hi - r_lo < S);
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
@@ -705,7 +900,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         // local stream of the pixel and the warp that runs its
                         // table: by pixel when no two rows of the wave share a
                         // stream, else by stream so that they run in row order
-                        const int g = z * GS + (fast_mod(r, S, invS) >> lgP);
+                        const int g = GRID ? z * S + fast_mod(r, S, invS) : z * GS + (fast_mod(r, S, invS) >> lgP);
                         pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
                         continue;
                     }
@@ -890,9 +1085,11 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 const int g = pg & 0xFFFFFF;
                 int zs, r, c;
                 pix_of(base + i, zs, r, c);
-                const uint32_t x = st_x[g];
+                // (the grid decoder's states were last written by other CTAs:
+                // read them from L2)
+                const uint32_t x = GRID ? __ldcg(st_x + g) : st_x[g];
                 // the stream's next word, fetched before it is known to be needed
-                const uint32_t pos = st_pos[g], pend = st_end[g];
+                const uint32_t pos = GRID ? __ldcg(st_pos + g) : st_pos[g], pend = GRID ? __ldcg(st_end + g) : st_end[g];
                 const uint32_t next_word = pos < pend ? wsrc[pos] : 0u;
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
@@ -994,6 +1191,28 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
             __syncthreads();   // the row list is rebuilt only after every image store
             asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else if (GRID) {
+            // grid-wide barrier: arrivals accumulate in the volume's header,
+            // wave t is complete at (t + 1) NB; a wait that runs out marks
+            // the volume so that every other CTA stops waiting too
+            const VolState vs = vol_state(b, im);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(vs.hdr + 2, 1u);
+                const uint32_t target = (uint32_t)(t + 1) * gridDim.x;
+                const long long t0 = clock64();
+                while (ld_acquire_gpu_u32(vs.hdr + 2) < target) {
+                    if (ld_acquire_gpu_u32(vs.hdr + 3) || clock64() - t0 > kDecWaitLimit) {
+                        atomicExch(vs.hdr + 3, 1u);
+                        s_fail = 1;
+                        break;
+                    }
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_fail) break;
         } else if (gimg && P > 1) {
             // every CTA's image stores of this wave before any CTA's next gather
             cluster_sync_all();
@@ -1009,7 +1228,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 if (!tc::mbar_wait(&w3bar[q % kW3Stages], (uint32_t)(q / kW3Stages) & 1u, kDecWaitLimit)) s_fail = 1;
     }
     // final states must be back at the initial value with every word read
-    {
+    // (the grid decoder's are checked by k_volume_finish)
+    if (!GRID) {
         const int G = (S - (int)k + P - 1) / P;
         for (int i = tid; i < D * G; i += kDecThreads) {
             const int g = (i / G) * GS + i % G;
@@ -1031,11 +1251,18 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
 
 template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<false, DEF>(m, b, prm);
+    decode_wave<false, DEF, false>(m, b, prm);
 }
 template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<true, DEF>(m, b, prm);
+    decode_wave<true, DEF, false>(m, b, prm);
+}
+// one volume over a cooperative grid
+__global__ void __launch_bounds__(kDecThreads, 1) k_decode_grid_tc(DevModel m, DecBatch b, DecTcParams prm) {
+    decode_wave<false, false, true>(m, b, prm);
+}
+__global__ void __launch_bounds__(kDecThreads, 1) k_decode_grid_f32(DevModel m, DecBatch b, DecTcParams prm) {
+    decode_wave<true, false, true>(m, b, prm);
 }
 
 // Cluster sizes for a batch (the decode autotuner).  A wave of an image
@@ -1242,6 +1469,64 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         return launch_decode_tc(m, b, P, num_sms, plan, st);
     }
     return cudaLaunchKernelEx(&cfg, kern, m, b, prm);
+}
+
+// One volume decoded by every SM: k_volume_setup, the wave kernel as a
+// cooperative grid of one CTA per SM (co-residency is what makes its
+// grid-wide barrier safe), then k_volume_finish.  Needs no two rows of a
+// slice's wave on one stream (the wave's pixels go to any CTA) and fewer
+// than 2^24 streams in the volume.
+bool grid_decode_eligible(const DevModel &m, int H, int W, int D, int S) {
+    return m.vol && min(H, (W + 2) / 3) <= S && (long long)D * S < (1ll << 24) && wave_decode_supported(m);
+}
+
+cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st) {
+    const bool f32 = m.precision == DLIC_FP32;
+    void (*kern)(DevModel, DecBatch, DecTcParams) = f32 ? k_decode_grid_f32 : k_decode_grid_tc;
+    uint32_t limit = 0;
+    cudaError_t e = smem_limit(kern, limit);
+    if (e != cudaSuccess) return e;
+    const DecImage &im = b.img[0];
+    const int H = im.H, W = im.W, D = im.D;
+    const int wave_px = min(H, (W + 2) / 3), T2 = 3 * (H - 1) + W;
+    const int active = min(D, T2 / volume_shift(m) + 1);
+    const int NB = num_sms;
+    const long long nmax = (long long)active * wave_px;
+    const int per_cta = (int)((nmax + NB - 1) / NB);
+    DecTcParams prm{};
+    prm.P = 1;
+    prm.h1 = m.h1;
+    prm.h2 = m.h2;
+    prm.k1 = (m.n_in + 15) / 16 * 16;
+    prm.tslots = m.wu + 1;
+    prm.tcols = 32;
+    prm.rcols = 16;
+    prm.gimg = 1;
+    prm.depth = D;
+    prm.max_g = 0;   // stream states live in the workspace
+    prm.nt = f32 ? 12 : min(64, max(16, (per_cta + 15) & ~15));
+    prm.list_rows = (per_cta + 15) & ~15;
+    prm.zlist = active + 1;
+    while (!f32 && dec_layout(prm, f32).total > limit && prm.nt > 16) prm.nt /= 2;
+    const DecTcLayout L = dec_layout(prm, f32);
+    if (L.total > limit) return cudaErrorNotSupported;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecThreads, L.total);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    k_volume_setup<<<1, kDecThreads, 0, st>>>(m, b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    DevModel ma = m;
+    DecBatch ba = b;
+    void *args[] = {&ma, &ba, &prm};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3((unsigned)NB), dim3(kDecThreads), args,
+                                    L.total, st);
+    if (e != cudaSuccess) return e;
+    k_volume_finish<<<1, kDecThreads, 0, st>>>(b);
+    return cudaGetLastError();
 }
 
 }  // namespace dlic

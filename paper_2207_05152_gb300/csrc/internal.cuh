@@ -76,6 +76,7 @@ struct DecImage {
     int64_t slice_pitch;          // volumes: bytes between slices
     int32_t H, W;
     int32_t D;                    // slices (1 for a 2D image)
+    int32_t S;                    // volumes: the caller's stream count per slice
     uint64_t in_off;              // byte offset of the bitstream in d_in
     uint64_t in_bytes;
     uint64_t st_off;              // per-stream state (x, pos, end) in workspace
@@ -113,6 +114,9 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
 bool wave_decode_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)
 bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan);
+// a volume on every SM at once (cooperative grid) instead of one cluster
+bool grid_decode_eligible(const DevModel &m, int H, int W, int D, int S);
+cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st);
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
 double decode_estimate(int H, int W, int P, bool f32);   // cycles, the autotuner's cost model
 

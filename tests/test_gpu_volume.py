@@ -28,9 +28,9 @@ def _blob(window, prec, h, vol, seed=3):
     return M.int8_blob(layers, calib_contexts(list(vol), window=window), window)
 
 
-def _roundtrip(Codec, orc, blob, vols, streams):
+def _roundtrip(Codec, orc, blob, vols, streams, plan=0):
     from paper_2207_05152_gb300 import _lib
-    codec = Codec(blob)
+    codec = Codec(blob, decode_plan=plan)
     dev = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in vols]
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     out, offs = codec.encode_volume(dev, streams, status=status)
@@ -59,17 +59,24 @@ def _roundtrip(Codec, orc, blob, vols, streams):
     return host, offs
 
 
-SHAPES = [(4, 40, 60, 16), (1, 9, 13, 3), (3, 1, 20, 1), (5, 7, 1, 4), (6, 33, 70, 8), (2, 64, 200, 32)]
+# (depth, height, width, streams): waves of a slice longer than the streams
+# run on one cluster (sizes 1 to 16, the largest power of two dividing the
+# streams), the others on the whole GPU (cooperative grid)
+SHAPES = [(4, 40, 60, 16), (1, 9, 13, 3), (3, 1, 20, 1), (5, 7, 1, 4), (6, 33, 70, 8), (2, 64, 200, 32),
+          (9, 40, 60, 20), (20, 96, 160, 64)]
 
 
+@pytest.mark.parametrize("plan", ["auto", "image"])
 @pytest.mark.parametrize("prec,h", [("int8", 128), ("fp32", 64)])
 @pytest.mark.parametrize("window", [M.VOLUME_WINDOW, (2, 3, 1, 2, 2, 2, 2), (3, 2, 2, 0, 3, 1, 4)])
-def test_volumes_match_oracle(Codec, orc, prec, h, window):
-    # cluster sizes 1 to 16 (the largest power of two dividing the streams)
+def test_volumes_match_oracle(Codec, orc, prec, h, window, plan):
+    # plan "image" keeps every volume on one cluster
+    from paper_2207_05152_gb300 import _lib
     vols = [synth.phantom_volume(d, hh, w, 13 * d + hh) for d, hh, w, _ in SHAPES]
     blob = _blob(window, prec, h, vols[0])
+    code = _lib.DLIC_PLAN_AUTO if plan == "auto" else _lib.DLIC_PLAN_IMAGE
     for v, (_, _, _, s) in zip(vols, SHAPES):
-        _roundtrip(Codec, orc, blob, [v], [s])
+        _roundtrip(Codec, orc, blob, [v], [s], code)
 
 
 def test_volume_batch_and_auto_streams(Codec, orc):
