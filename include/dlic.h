@@ -279,13 +279,20 @@ DLIC_API dlic_status dlic_decode_volume_workspace_size(const dlic_model *model, 
 /* Decodes n volumes; volume i is the bytes [h_in_offsets[i], h_in_offsets[i + 1])
  * of d_in (host array of n + 1 even offsets): its slices' containers back to
  * back, as dlic_encode_volume wrote them.  All slices of a volume decode at
- * once in one cluster of CTAs as a 3D wavefront: pixel (z, r, c) is on wave
+ * once as a 3D wavefront: pixel (z, r, c) is on wave
  * 3r + c + (3 pd + pr + 1) z, so every prior from slice z - 1 is decoded
- * before it is read (priors are read back from the output volume, one cluster
- * barrier per wave); the first slice is complete after 3(H-1) + W waves, the
- * volume after (3 pd + pr + 1)(depth - 1) more.  The cluster size divides
- * h_volumes[i].streams, which must equal the slices' stream count.  Networks
- * as for the cluster decoder (INT8 of widths 128, FP32 with h2 <= 128).
+ * before it is read (priors are read back from the output volume); the first
+ * slice is complete after 3(H-1) + W waves, the volume after
+ * (3 pd + pr + 1)(depth - 1) more.  When no slice's wave holds two rows of
+ * one stream (min(height, ceil(width / 3)) <= streams) and depth x streams
+ * < 2^24, the whole GPU decodes the volume: one CTA per SM in a cooperative
+ * launch, each wave's pixels split evenly over the CTAs, stream states in the
+ * workspace, one grid-wide barrier per wave (volumes one after another).
+ * Otherwise, or under a forced decode plan, one cluster of up to 16 CTAs
+ * (the largest power of two dividing the streams) decodes it with one
+ * cluster barrier per wave.  h_volumes[i].streams must equal the slices'
+ * stream count.  Networks as for the cluster decoder (INT8 of widths 128,
+ * FP32 with h2 <= 128).
  * d_status (n int32, device): DLIC_OK, DLIC_ERR_CORRUPT (a slice's header,
  * sizes or final states) or DLIC_ERR_TIMEOUT. */
 DLIC_API dlic_status dlic_decode_volume(const dlic_model *model, const void *d_in, const uint64_t *h_in_offsets,
