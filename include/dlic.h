@@ -124,11 +124,20 @@ DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
  *                        a byte ring with one cluster barrier per wave, else
  *                        the priors read back from the output image;
  *  DLIC_PLAN_BYTE_RING   the byte ring, or the image when it does not fit;
- *  DLIC_PLAN_IMAGE       always the image (one cluster barrier per wave).
+ *  DLIC_PLAN_IMAGE       always the image (one cluster barrier per wave);
+ *  DLIC_PLAN_GRID        the whole batch on every SM at once: one cooperative
+ *                        grid of one CTA per SM, each wave's pixels (of all
+ *                        images) split evenly over the CTAs, priors read back
+ *                        from the images, stream states in the workspace, one
+ *                        grid-wide barrier per wave.  AUTO takes it for
+ *                        volumes (when no slice's wave holds two rows of one
+ *                        stream) and for 2D batches whose clusters would fill
+ *                        at most half the SMs with more than 64 pixels per CTA
+ *                        and wave (a few very wide images).
  * Every plan gives the same decoded pixels; the forced plans exist to test
  * and measure the ones AUTO takes for long waves.  Applies to later
  * dlic_decode calls with this model; DLIC_ERR_INVALID for another value. */
-enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2 };
+enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2, DLIC_PLAN_GRID = 3 };
 DLIC_API dlic_status dlic_model_set_decode_plan(dlic_model *model, int plan);
 
 /* Precision tag, hidden widths and hash of a model. */

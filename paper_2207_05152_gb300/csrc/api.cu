@@ -252,7 +252,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
 
 extern "C" dlic_status dlic_model_set_decode_plan(dlic_model *m, int plan) {
     if (!m) return fail(DLIC_ERR_INVALID, "null model");
-    if (plan != DLIC_PLAN_AUTO && plan != DLIC_PLAN_BYTE_RING && plan != DLIC_PLAN_IMAGE)
+    if (plan != DLIC_PLAN_AUTO && plan != DLIC_PLAN_BYTE_RING && plan != DLIC_PLAN_IMAGE && plan != DLIC_PLAN_GRID)
         return fail(DLIC_ERR_INVALID, "unknown decode plan %d", plan);
     m->decode_plan = plan;
     return DLIC_OK;
@@ -509,7 +509,9 @@ struct DecItem {
 
 // per item: stream states (a volume's: header, x, position, end per stream)
 static size_t dec_item_bytes(const DecItem &e) {
-    return e.D > 1 || e.S ? align256(256 + 12ull * e.D * e.S) : align256(16ull * e.H);
+    // a 2D image: up to H streams of 16 bytes (one CTA per image) or of 12
+    // bytes after a 256-byte header (grid decoder)
+    return e.D > 1 || e.S ? align256(256 + 12ull * e.D * e.S) : align256(256 + 16ull * e.H);
 }
 
 static size_t dec_ws_bytes(const std::vector<DecItem> &it) {
@@ -586,29 +588,6 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         Hs[i] = it[i].H;
         Ws[i] = it[i].W;
     }
-    // volumes that the whole GPU decodes, one after another (cluster size 0:
-    // in no group)
-    std::vector<char> on_grid(n, 0);
-    if (use_wave) {
-        if (vol) {
-            // a volume's wave spans its slices: every SM (cooperative grid),
-            // else the largest cluster that divides its stream count (each
-            // CTA owns the rows k mod P)
-            for (int i = 0; i < n; i++) {
-                on_grid[i] = m->decode_plan == DLIC_PLAN_AUTO &&
-                             grid_decode_eligible(m->dev, it[i].H, it[i].W, it[i].D, it[i].S);
-                P[i] = 16;
-                while (it[i].S % P[i]) P[i] >>= 1;
-            }
-        } else {
-            choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
-        }
-        // checked before anything is enqueued
-        for (int i = 0; i < n; i++)
-            if (!on_grid[i] && !wave_decode_fits(m->dev, Hs[i], Ws[i], it[i].D, P[i], m->decode_plan))
-                return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d (x %d) needs more shared memory than the "
-                            "decoder's plans allow", i, Hs[i], Ws[i], it[i].D);
-    }
     auto fill = [&](DecImage &e, int i) {
         const DecItem &g = it[i];
         e.pixels = g.pixels;
@@ -617,25 +596,80 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         e.H = g.H;
         e.W = g.W;
         e.D = g.D;
-        e.S = g.S;
+        e.S = g.S ? g.S : g.H;   // 2D: the stream capacity of the grid decoder's state block
         e.in_off = h_in_offsets[i];
         e.in_bytes = h_in_offsets[i + 1] - h_in_offsets[i];
         e.st_off = st_off[i];
         e.sidx = i;
     };
-    for (int i = 0; i < n; i++) {
-        if (!on_grid[i]) continue;
-        P[i] = 0;
+    auto new_batch = [&]() {
         DecBatch *b = new DecBatch();
-        b->n = 1;
         b->in = static_cast<const uint8_t *>(d_in);
         b->ws = static_cast<uint8_t *>(d_ws);
         b->status = d_status;
-        fill(b->img[0], i);
+        return b;
+    };
+    // Items that the whole GPU decodes as one cooperative grid (cluster size
+    // 0: in no group): volumes one after another, or a 2D batch in chunks.
+    std::vector<char> on_grid(n, 0);
+    const int plan = m->decode_plan;
+    if (use_wave) {
+        if (vol) {
+            // a volume's wave spans its slices: every SM (cooperative grid),
+            // else the largest cluster that divides its stream count (each
+            // CTA owns the rows k mod P)
+            for (int i = 0; i < n; i++) {
+                on_grid[i] = (plan == DLIC_PLAN_AUTO || plan == DLIC_PLAN_GRID) &&
+                             grid_decode_eligible(m->dev, it[i].H, it[i].W, it[i].D, it[i].S);
+                P[i] = 16;
+                while (it[i].S % P[i]) P[i] >>= 1;
+            }
+        } else {
+            choose_clusters(Hs.data(), Ws.data(), n, m->num_sms, m->dev.precision == DLIC_FP32, P.data());
+            // The grid spreads every wave over all SMs but waits for its
+            // slowest CTA at each wave; clusters run their images without a
+            // common barrier.  AUTO takes the grid when the clusters would
+            // leave most SMs idle while their CTAs hold several chunks of
+            // pixels per wave (a few very wide images).
+            int used = 0, per = 0;
+            for (int i = 0; i < n; i++) {
+                used += P[i];
+                per = std::max(per, (std::min(it[i].H, (it[i].W + 2) / 3) + P[i] - 1) / P[i]);
+            }
+            bool grid = plan == DLIC_PLAN_GRID ||
+                        (plan == DLIC_PLAN_AUTO && 2 * used <= m->num_sms && per > kGridMinChunkPixels);
+            for (int c0 = 0; grid && c0 < n; c0 += kMaxBatch) {
+                DecBatch *b = new_batch();
+                b->n = std::min(kMaxBatch, n - c0);
+                for (int k = 0; k < b->n; k++) fill(b->img[k], c0 + k);
+                grid = grid_decode_fits(m->dev, *b, m->num_sms);
+                delete b;
+            }
+            if (grid)
+                for (int i = 0; i < n; i++) on_grid[i] = 1;
+        }
+        // checked before anything is enqueued
+        for (int i = 0; i < n; i++)
+            if (!on_grid[i] && !wave_decode_fits(m->dev, Hs[i], Ws[i], it[i].D, P[i], plan))
+                return fail(DLIC_ERR_UNSUPPORTED, "image %d: %d x %d (x %d) needs more shared memory than the "
+                            "decoder's plans allow", i, Hs[i], Ws[i], it[i].D);
+    }
+    for (int c0 = 0; c0 < n;) {
+        if (!on_grid[c0]) {
+            c0++;
+            continue;
+        }
+        DecBatch *b = new_batch();
+        b->n = 0;
+        // a volume alone; 2D images in chunks of up to kMaxBatch
+        for (int i = c0; i < n && on_grid[i] && b->n < (vol ? 1 : kMaxBatch); i++) fill(b->img[b->n++], i);
+        for (int k = 0; k < b->n; k++) P[c0 + k] = 0;
         cudaError_t e = launch_decode_grid(m->dev, *b, m->num_sms, cs);
+        const int first = c0;
+        c0 += b->n;
         delete b;
         if (e != cudaSuccess)
-            return e == cudaErrorNotSupported ? fail(DLIC_ERR_UNSUPPORTED, "volume %d: the grid decoder does not fit", i)
+            return e == cudaErrorNotSupported ? fail(DLIC_ERR_UNSUPPORTED, "item %d: the grid decoder does not fit", first)
                                               : cuda_fail(e, "grid decode launch");
     }
     int groups_used = 0;

@@ -57,7 +57,9 @@ struct DecTcParams {
     int gimg;         // 1: priors are read back from the output image (no ring; one
                       // cluster barrier per wave), for waves too long for the rings
     int depth;        // slices per image (volumes); stream states are kept per slice
-    int zlist;        // grid decoder: capacity of the per-wave table of active slices
+    int zlist;        // grid decoder: capacity of the per-wave table of active slices (and,
+                      // for a batch, of the per-image stream count, flags and wave count)
+    int T;            // grid decoder of a batch: waves of the longest image
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -389,6 +391,106 @@ __global__ void __launch_bounds__(kDecThreads) k_volume_finish(DecBatch b) {
         atomicMax(b.status + im.sidx, vs.hdr[3] ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
 }
 
+// Grid decoder of a batch of 2D images, before the wave kernel: CTA i
+// checks image i's header and writes its streams' states to the image's
+// state block (positions count 16-bit words from the start of the input
+// buffer), with the stream count and whether no wave holds two rows of one
+// stream ("spread"; the other images go whole to one CTA per wave).  The
+// state block of image 0 also carries the grid's wave-barrier counter.
+__global__ void __launch_bounds__(kDecThreads) k_batch_setup(DevModel m, DecBatch b) {
+    __shared__ uint32_t s_part[kDecThreads];
+    __shared__ int s_ok, s_S;
+    const int tid = threadIdx.x;
+    const DecImage &im = b.img[blockIdx.x];
+    const uint8_t *in = b.in + im.in_off;
+    const VolState vs = vol_state(b, im);
+    const int H = im.H, W = im.W;
+    if (tid == 0) {
+        int ok = im.in_bytes >= (uint64_t)kHeaderBytes, S = 0;
+        if (ok) {
+            uint64_t hash = 0;
+            for (int q = 0; q < 8; q++) hash |= (uint64_t)in[16 + q] << (8 * q);
+            S = in[14] | (in[15] << 8);
+            const uint32_t hh = in[4] | (in[5] << 8) | (in[6] << 16) | ((uint32_t)in[7] << 24);
+            const uint32_t ww = in[8] | (in[9] << 8) | (in[10] << 16) | ((uint32_t)in[11] << 24);
+            ok = in[0] == 'D' && in[1] == 'L' && in[2] == 'C' && in[3] == '1' && hh == (uint32_t)H &&
+                 ww == (uint32_t)W && in[12] == m.wu && in[13] == m.precision && hash == m.hash && S >= 1 &&
+                 S <= H && im.in_bytes >= (uint64_t)kHeaderBytes + 4ull * S;
+        }
+        s_ok = ok;
+        s_S = ok ? S : 1;
+        if (blockIdx.x == 0) {
+            vs.hdr[2] = 0u;   // wave-barrier arrivals
+            vs.hdr[3] = 0u;   // a wait ran out
+        }
+    }
+    __syncthreads();
+    const int S = s_S;
+    if (s_ok) {
+        const uint8_t *cnt = in + kHeaderBytes;
+        const uint16_t *pay = reinterpret_cast<const uint16_t *>(in + kHeaderBytes + 4 * S);
+        const int per = (S + kDecThreads - 1) / kDecThreads;
+        const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
+        uint32_t sum = 0;
+        int bad = 0;
+        for (int s = s0; s < s1; s++) {
+            const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
+            bad |= c < 2;
+            sum += c;
+        }
+        s_part[tid] = sum;
+        if (bad) s_ok = 0;
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t acc = 0;
+            for (int q = 0; q < kDecThreads; q++) {
+                const uint32_t v = s_part[q];
+                s_part[q] = (uint32_t)acc;
+                acc += v;
+            }
+            if ((uint64_t)kHeaderBytes + 4ull * S + 2ull * acc != im.in_bytes) s_ok = 0;
+        }
+        __syncthreads();
+        if (s_ok) {
+            const uint32_t word0 = (uint32_t)((im.in_off + kHeaderBytes + 4ull * S) / 2);
+            uint32_t start = s_part[tid];
+            for (int s = s0; s < s1; s++) {
+                const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
+                const uint32_t x = ((uint32_t)pay[start] << 16) | pay[start + 1];
+                if (x < kRansL) s_ok = 0;
+                vs.x[s] = x;
+                vs.pos[s] = word0 + start + 2;
+                vs.end[s] = word0 + start + c;
+                start += c;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        vs.hdr[0] = (uint32_t)S;
+        vs.hdr[1] = (uint32_t)s_ok;
+        vs.hdr[4] = (uint32_t)(min(H, (W + 2) / 3) <= S);
+        if (!s_ok) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
+    }
+}
+
+// After the grid decoder of a batch: CTA i checks image i's final states.
+__global__ void __launch_bounds__(kDecThreads) k_batch_finish(DecBatch b) {
+    const DecImage &im = b.img[blockIdx.x];
+    const VolState vs = vol_state(b, im);
+    const uint32_t failed = vol_state(b, b.img[0]).hdr[3];
+    if (!vs.hdr[1]) return;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const int S = (int)vs.hdr[0];
+    for (int g = threadIdx.x; g < S; g += kDecThreads)
+        if (vs.x[g] != kRansL || vs.pos[g] != vs.end[g]) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && (s_bad || failed))
+        atomicMax(b.status + im.sidx, failed ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
+}
+
 // The wavefront decoder for one image per cluster; F32 selects the FP32
 // network on the CUDA cores instead of the INT8 network on the tensor cores.
 // DEF compiles the default window (the 12 priors of Fig. 2: two rows above,
@@ -484,17 +586,37 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     uint32_t *st_pos = reinterpret_cast<uint32_t *>(smem + L.st_pos);
     uint32_t *st_end = reinterpret_cast<uint32_t *>(smem + L.st_end);
     const uint16_t *wsrc = nullptr;
+    // grid decoder of a batch of 2D images: per image its stream count,
+    // flags (1: header good, 2: spread) and wave count, after zpre
+    const bool gb = GRID && !vol;
+    int *itS = reinterpret_cast<int *>(smem + L.zpre) + (b.n + 1);
+    int *itflag = itS + (b.n + 1), *itT2 = itflag + (b.n + 1);
     if constexpr (GRID) {
-        // states written by k_volume_setup; every CTA reads the same flag
-        const VolState vs = vol_state(b, im);
-        if (tid == 0) {
-            s_S = (int)__ldcg(vs.hdr);
-            s_ok = (int)__ldcg(vs.hdr + 1);
+        if (gb) {
+            // states written by k_batch_setup; a bad image just has no pixels
+            for (int i = tid; i < b.n; i += kDecThreads) {
+                const VolState vi = vol_state(b, b.img[i]);
+                itS[i] = (int)__ldcg(vi.hdr);
+                itflag[i] = (int)(__ldcg(vi.hdr + 1) | (__ldcg(vi.hdr + 4) << 1));
+                itT2[i] = 3 * (b.img[i].H - 1) + b.img[i].W;
+            }
+            if (tid == 0) {
+                s_S = 1;
+                s_ok = 1;
+            }
+            wsrc = reinterpret_cast<const uint16_t *>(b.in);
+        } else {
+            // states written by k_volume_setup; every CTA reads the same flag
+            const VolState vs = vol_state(b, im);
+            if (tid == 0) {
+                s_S = (int)__ldcg(vs.hdr);
+                s_ok = (int)__ldcg(vs.hdr + 1);
+            }
+            st_x = vs.x;
+            st_pos = vs.pos;
+            st_end = vs.end;
+            wsrc = reinterpret_cast<const uint16_t *>(in);
         }
-        st_x = vs.x;
-        st_pos = vs.pos;
-        st_end = vs.end;
-        wsrc = reinterpret_cast<const uint16_t *>(in);
         __syncthreads();
     }
     for (int z = 0; z < (GRID ? 0 : D); z++) {
@@ -744,12 +866,33 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     int *pixg = reinterpret_cast<int *>(smem + L.pg);
     uint8_t *dsym = smem + L.dsym;   // this wave's decoded pixels, by row-list index
     __shared__ int s_wcnt[kDecWarps];
+    // exclusive prefix of v over the CTA's threads (total of all in `total`)
+    auto block_scan = [&](int v, int &total) {
+        int incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) s_wcnt[warp] = incl;
+        __syncthreads();
+        int before = incl - v;
+        total = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kDecWarps; w2++) {
+            const int cw = s_wcnt[w2];
+            before += w2 < warp ? cw : 0;
+            total += cw;
+        }
+        __syncthreads();
+        return before;
+    };
     // A volume's slices run as one 3D wavefront (Sec. IV "3D Wavefront"):
     // pixel (z, r, c) is on wave 3r + c + VSH z, every slice VSH waves behind
     // the one before it, so that the lower layer of its window is decoded.
     const int T2 = 3 * (H - 1) + W;
     const int VSH = vol ? volume_shift(m) : 0;
-    const int T = T2 + VSH * (D - 1);
+    const int T = gb ? prm.T : T2 + VSH * (D - 1);
     // When P divides S the owned rows of a wave are r0, r0 + P, ... and no
     // row list is built (a volume lists (slice, row) pairs, with P | S).
     const bool modrows = (S % P) == 0 && !vol;
@@ -762,7 +905,50 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         // rows of this wave owned by this CTA, in increasing order
         int nk = 0;
         const int r0 = r_lo + (((int)k - r_lo) & (P - 1));
-        if (GRID) {
+        int nd = 0;   // grid batch: pixels of this CTA's whole (not spread) images, listed first
+        if (gb) {
+            const int NB = (int)gridDim.x, kb = (int)blockIdx.x;
+            // images whose waves hold two rows of one stream go whole to CTA
+            // i mod NB, in row order (n <= kMaxBatch < kDecThreads: thread = image)
+            {
+                const int i = tid;
+                int cnt = 0, rl = 0;
+                if (i < b.n && itflag[i] == 1 && i % NB == kb && t < itT2[i]) {
+                    rl = t - b.img[i].W + 1 > 0 ? (t - b.img[i].W + 3) / 3 : 0;
+                    cnt = min(b.img[i].H - 1, t / 3) - rl + 1;
+                }
+                int total;
+                const int before = block_scan(cnt, total);
+                for (int j = 0; j < cnt; j++) rowlist[before + j] = (i << 20) | (rl + j);
+                nd = total;
+            }
+            // the spread images' rows split evenly over the grid
+            {
+                const int i = tid;
+                int cnt = 0;
+                if (i < b.n && itflag[i] == 3 && t < itT2[i]) {
+                    const int rl = t - b.img[i].W + 1 > 0 ? (t - b.img[i].W + 3) / 3 : 0;
+                    cnt = min(b.img[i].H - 1, t / 3) - rl + 1;
+                }
+                int n;
+                const int before = block_scan(cnt, n);
+                if (i < b.n) zpre[i] = before;
+                __syncthreads();
+                const int i0 = (int)((long long)n * kb / NB), i1 = (int)((long long)n * (kb + 1) / NB);
+                for (int j = tid; j < i1 - i0; j += kDecThreads) {
+                    const int gi = i0 + j;
+                    int lo = 0, hi = b.n - 1;   // the last image whose first index is <= gi
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (zpre[mid] <= gi) lo = mid; else hi = mid - 1;
+                    }
+                    const int rl = t - b.img[lo].W + 1 > 0 ? (t - b.img[lo].W + 3) / 3 : 0;
+                    rowlist[nd + j] = (lo << 20) | (rl + gi - zpre[lo]);
+                }
+                nk = nd + (i1 - i0);
+                __syncthreads();
+            }
+        } else if (GRID) {
             // every row of the slices on this wave, in slice order; this CTA
             // takes the indices [kb n / NB, (kb + 1) n / NB): thread = slice,
             // block-wide exclusive scan of the row counts into zpre
@@ -866,9 +1052,14 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
         }
         auto row_of = [&](int i) { return modrows ? r0 + (i << lgP) : rowlist[i]; };
-        // (slice, row, column) of the wave's i-th owned pixel
+        // (slice or image, row, column) of the wave's i-th owned pixel
         auto pix_of = [&](int i, int &z, int &r, int &c) {
-            if (vol) {
+            if (gb) {
+                const int e = rowlist[i];
+                z = e >> 20;
+                r = e & 0xFFFFF;
+                c = t - 3 * r;
+            } else if (vol) {
                 const int e = rowlist[i];
                 z = e >> 20;
                 r = e & 0xFFFFF;
@@ -880,7 +1071,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             }
         };
         // no two rows of a slice's wave share a stream
-        const bool spread = GRID || (vol ? min(H, (W + 2) / 3) <= S : r_hi - r_lo < S);
+        const bool spread = gb ? nd == 0 : (GRID || (vol ? min(H, (W + 2) / 3) <= S : r_hi - r_lo < S));
         for (int base = 0; base < nk; base += NT) {
             const int nc = min(NT, nk - base);
             const int NP = (nc + 15) & ~15;
@@ -900,8 +1091,16 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         // local stream of the pixel and the warp that runs its
                         // table: by pixel when no two rows of the wave share a
                         // stream, else by stream so that they run in row order
-                        const int g = GRID ? z * S + fast_mod(r, S, invS) : z * GS + (fast_mod(r, S, invS) >> lgP);
-                        pixg[px] = g | ((spread ? px % kDecWarps : g % kDecWarps) << 24);
+                        int g;
+                        bool own_warp = spread;   // warp by pixel, else by stream (row order)
+                        if (gb) {
+                            const int Si = itS[z];
+                            g = (z << 16) | fast_mod(r, Si, 1.0f / (float)Si);
+                            own_warp = itflag[z] == 3;
+                        } else {
+                            g = GRID ? z * S + fast_mod(r, S, invS) : z * GS + (fast_mod(r, S, invS) >> lgP);
+                        }
+                        pixg[px] = g | ((own_warp ? px % kDecWarps : g % kDecWarps) << 24);
                         continue;
                     }
                     int dr, dc, dz = 0;
@@ -915,9 +1114,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         dz = o.z;
                     }
                     const int rr = r + dr, cc = c + dc, zz = z + dz;
+                    const int Wz = gb ? b.img[z].W : W;
                     // (a 3D window's lower layer may reach below the row and
                     // off the first slice)
-                    if (rr < 0 || cc < 0 || cc >= W || (vol && (zz < 0 || rr >= H))) {
+                    if (rr < 0 || cc < 0 || cc >= Wz || (vol && (zz < 0 || rr >= H))) {
                         v = 0u;
                     } else if (p2p) {
                         // entry (round of rr, row distance, column mod tcols)
@@ -939,7 +1139,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         v &= 0xFFu;
                     } else if (gimg) {
                         // stored to the image before the last wave's barrier
-                        v = __ldcg(im.pixels + (int64_t)zz * im.slice_pitch + (int64_t)rr * im.pitch + cc);
+                        v = gb ? __ldcg(b.img[z].pixels + (int64_t)rr * b.img[z].pitch + cc)
+                               : __ldcg(im.pixels + (int64_t)zz * im.slice_pitch + (int64_t)rr * im.pitch + cc);
                     } else {
                         v = ring[(rr & rmask) * RCOLS + (cc & rcmask)];
                     }
@@ -1086,10 +1287,19 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 int zs, r, c;
                 pix_of(base + i, zs, r, c);
                 // (the grid decoder's states were last written by other CTAs:
-                // read them from L2)
-                const uint32_t x = GRID ? __ldcg(st_x + g) : st_x[g];
+                // read them from L2; a batch keeps them per image)
+                uint32_t *sx = st_x, *sp = st_pos, *se = st_end;
+                int gs = g;
+                if (gb) {
+                    const VolState vi = vol_state(b, b.img[g >> 16]);
+                    sx = vi.x;
+                    sp = vi.pos;
+                    se = vi.end;
+                    gs = g & 0xFFFF;
+                }
+                const uint32_t x = GRID ? __ldcg(sx + gs) : sx[gs];
                 // the stream's next word, fetched before it is known to be needed
-                const uint32_t pos = GRID ? __ldcg(st_pos + g) : st_pos[g], pend = GRID ? __ldcg(st_end + g) : st_end[g];
+                const uint32_t pos = GRID ? __ldcg(sp + gs) : sp[gs], pend = GRID ? __ldcg(se + gs) : se[gs];
                 const uint32_t next_word = pos < pend ? wsrc[pos] : 0u;
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
@@ -1164,14 +1374,15 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     if (xn < kRansL) {
                         if (pos < pend) {
                             xn = (xn << 16) | next_word;
-                            st_pos[g] = pos + 1;
+                            sp[gs] = pos + 1;
                         } else {
                             s_err = 1;
                         }
                     }
-                    st_x[g] = xn;
+                    sx[gs] = xn;
                     if (direct)
-                        im.pixels[(int64_t)zs * im.slice_pitch + (int64_t)r * im.pitch + c] = (uint8_t)sym;
+                        (gb ? b.img[zs].pixels + (int64_t)r * b.img[zs].pitch
+                            : im.pixels + (int64_t)zs * im.slice_pitch + (int64_t)r * im.pitch)[c] = (uint8_t)sym;
                     else
                         dsym[base + i] = (uint8_t)sym;
                 }
@@ -1480,20 +1691,11 @@ bool grid_decode_eligible(const DevModel &m, int H, int W, int D, int S) {
     return m.vol && min(H, (W + 2) / 3) <= S && (long long)D * S < (1ll << 24) && wave_decode_supported(m);
 }
 
-cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st) {
+// Shared-memory plan of the grid decoder for a volume (b.img[0]) or a batch
+// of 2D images; false when none fits.
+static bool plan_grid(const DevModel &m, const DecBatch &b, int NB, uint32_t limit, DecTcParams &prm) {
     const bool f32 = m.precision == DLIC_FP32;
-    void (*kern)(DevModel, DecBatch, DecTcParams) = f32 ? k_decode_grid_f32 : k_decode_grid_tc;
-    uint32_t limit = 0;
-    cudaError_t e = smem_limit(kern, limit);
-    if (e != cudaSuccess) return e;
-    const DecImage &im = b.img[0];
-    const int H = im.H, W = im.W, D = im.D;
-    const int wave_px = min(H, (W + 2) / 3), T2 = 3 * (H - 1) + W;
-    const int active = min(D, T2 / volume_shift(m) + 1);
-    const int NB = num_sms;
-    const long long nmax = (long long)active * wave_px;
-    const int per_cta = (int)((nmax + NB - 1) / NB);
-    DecTcParams prm{};
+    prm = DecTcParams{};
     prm.P = 1;
     prm.h1 = m.h1;
     prm.h2 = m.h2;
@@ -1502,21 +1704,65 @@ cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms
     prm.tcols = 32;
     prm.rcols = 16;
     prm.gimg = 1;
-    prm.depth = D;
     prm.max_g = 0;   // stream states live in the workspace
+    long long wave = 0;   // pixels of the longest wave
+    int designated = 0;   // pixels a CTA may get from whole (not spread) images
+    if (m.vol) {
+        const DecImage &im = b.img[0];
+        const int wave_px = min(im.H, (im.W + 2) / 3), T2 = 3 * (im.H - 1) + im.W;
+        const int active = min(im.D, T2 / volume_shift(m) + 1);
+        wave = (long long)active * wave_px;
+        prm.depth = im.D;
+        prm.zlist = active + 1;
+    } else {
+        int maxw = 0;
+        for (int i = 0; i < b.n; i++) {
+            const int w = min(b.img[i].H, (b.img[i].W + 2) / 3);
+            wave += w;
+            maxw = max(maxw, w);
+            prm.T = max(prm.T, 3 * (b.img[i].H - 1) + b.img[i].W);
+        }
+        designated = ((b.n + NB - 1) / NB) * maxw;
+        prm.depth = 1;
+        prm.zlist = 4 * (b.n + 1);
+    }
+    const int per_cta = (int)((wave + NB - 1) / NB);
     prm.nt = f32 ? 12 : min(64, max(16, (per_cta + 15) & ~15));
-    prm.list_rows = (per_cta + 15) & ~15;
-    prm.zlist = active + 1;
+    prm.list_rows = (per_cta + designated + 15) & ~15;
     while (!f32 && dec_layout(prm, f32).total > limit && prm.nt > 16) prm.nt /= 2;
-    const DecTcLayout L = dec_layout(prm, f32);
-    if (L.total > limit) return cudaErrorNotSupported;
+    return dec_layout(prm, f32).total <= limit;
+}
+
+static void (*grid_kernel(const DevModel &m))(DevModel, DecBatch, DecTcParams) {
+    return m.precision == DLIC_FP32 ? k_decode_grid_f32 : k_decode_grid_tc;
+}
+
+bool grid_decode_fits(const DevModel &m, const DecBatch &b, int num_sms) {
+    uint32_t limit = 0;
+    DecTcParams prm;
+    return wave_decode_supported(m) && smem_limit(grid_kernel(m), limit) == cudaSuccess &&
+           plan_grid(m, b, num_sms, limit, prm);
+}
+
+cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st) {
+    void (*kern)(DevModel, DecBatch, DecTcParams) = grid_kernel(m);
+    uint32_t limit = 0;
+    cudaError_t e = smem_limit(kern, limit);
+    if (e != cudaSuccess) return e;
+    const int NB = num_sms;
+    DecTcParams prm;
+    if (!plan_grid(m, b, NB, limit, prm)) return cudaErrorNotSupported;
+    const DecTcLayout L = dec_layout(prm, m.precision == DLIC_FP32);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDecThreads, L.total);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
-    k_volume_setup<<<1, kDecThreads, 0, st>>>(m, b);
+    if (m.vol)
+        k_volume_setup<<<1, kDecThreads, 0, st>>>(m, b);
+    else
+        k_batch_setup<<<b.n, kDecThreads, 0, st>>>(m, b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     DevModel ma = m;
@@ -1525,7 +1771,10 @@ cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms
     e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3((unsigned)NB), dim3(kDecThreads), args,
                                     L.total, st);
     if (e != cudaSuccess) return e;
-    k_volume_finish<<<1, kDecThreads, 0, st>>>(b);
+    if (m.vol)
+        k_volume_finish<<<1, kDecThreads, 0, st>>>(b);
+    else
+        k_batch_finish<<<b.n, kDecThreads, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,9 @@ struct EncImage {
 
 constexpr int kMaxBatch = 192;    // images per launch (kernel-parameter space)
 constexpr int kMaxSlices = 2047;  // slices per volume (11 bits in the decoder's row list)
+// a 2D batch goes to the grid decoder when its clusters would fill at most
+// half the SMs with more than this many pixels per CTA and wave
+constexpr int kGridMinChunkPixels = 64;
 constexpr int kPredictTile = 64;  // pixels per CUDA-core prediction CTA
 
 struct EncBatch {
@@ -117,6 +120,8 @@ bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan);
 // a volume on every SM at once (cooperative grid) instead of one cluster
 bool grid_decode_eligible(const DevModel &m, int H, int W, int D, int S);
 cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st);
+// whether a batch of 2D images (or one volume) fits the grid decoder's shared-memory plan
+bool grid_decode_fits(const DevModel &m, const DecBatch &b, int num_sms);
 void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, int *P);
 double decode_estimate(int H, int W, int P, bool f32);   // cycles, the autotuner's cost model
 

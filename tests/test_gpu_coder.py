@@ -28,8 +28,8 @@ def _models(widths, seed, images):
     return {"fp32": M.fp32_blob(layers), "int8": M.int8_blob(layers, calib_contexts(images))}
 
 
-def _check(Codec, orc, blob, imgs, streams):
-    codec = Codec(blob)
+def _check(Codec, orc, blob, imgs, streams, plan=0):
+    codec = Codec(blob, decode_plan=plan)
     got = codec.encode_to_bytes([torch.from_numpy(np.ascontiguousarray(i)).cuda() for i in imgs], streams)
     for k, img in enumerate(imgs):
         from paper_2207_05152_gb300 import _lib
@@ -277,3 +277,48 @@ def test_waves_beyond_every_plan_are_refused(Codec):
     codec.close()
     del out
     torch.cuda.empty_cache()
+
+
+# --- the grid decoder: a batch's waves over every SM (cooperative launch) ---
+
+@pytest.mark.parametrize("prec,widths", [("int8", [12, 128, 128, 256]), ("fp32", [12, 64, 64, 256])])
+def test_grid_plan_edge_shapes(Codec, orc, prec, widths):
+    # images whose waves hold two rows of one stream (streams below the wave
+    # length) go whole to one CTA per wave, the others are split evenly
+    from paper_2207_05152_gb300 import _lib
+    imgs = [synth.value_noise_image(h, w, 7 * h + w) for h, w, _ in SHAPES]
+    blob = _models(widths, 5, [synth.voronoi_image(40, 40, 2)])[prec]
+    _check(Codec, orc, blob, imgs, [s for _, _, s in SHAPES], _lib.DLIC_PLAN_GRID)
+
+
+@pytest.mark.parametrize("window", [M.DEFAULT_WINDOW, M.FIG6_WINDOW])
+def test_grid_plan_batch(Codec, orc, window):
+    from paper_2207_05152_gb300 import _lib
+    sizes = [(30, 40), (64, 64), (100, 180), (20, 300), (150, 90), (200, 260), (45, 45), (120, 400),
+             (16, 16), (90, 120), (300, 200), (60, 500)]
+    imgs = [synth.voronoi_image(h, w, 800 + i) for i, (h, w) in enumerate(sizes)]
+    blob = _window_models([M.window_size(window), 128, 128, 256], 8, imgs[:3], window)["int8"]
+    _check(Codec, orc, blob, imgs, None, _lib.DLIC_PLAN_GRID)
+
+
+def test_auto_plan_takes_the_grid_for_very_wide_images():
+    # one 1100 x 3300 image: waves of 1100 pixels, more than 64 for each CTA
+    # of a 16-CTA cluster, so the automatic plan takes the grid; the round
+    # trip must be lossless (the encoder is pinned to the oracle elsewhere)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2207_05152_gb300.codec import Codec as C
+    tile = synth.voronoi_image(550, 660, 31)
+    img = np.ascontiguousarray(np.tile(tile, (2, 5)))
+    img[::5, ::3] ^= 0x33
+    blob = _models([12, 128, 128, 256], 9, [tile])["int8"]
+    codec = C(blob)
+    d = torch.from_numpy(img).cuda()
+    out, offs = codec.encode([d], None)
+    o = offs.cpu().tolist()
+    dec = torch.empty_like(d)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    codec.decode(out, o, [img.shape], outs=[dec], status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and torch.equal(dec, d)
+    codec.close()
