@@ -2,6 +2,7 @@
 
     python -m paper_2207_05152_gb300.profile_case --case cfg2 --iters 2
     python -m paper_2207_05152_gb300.profile_case --case cfg4 --count 8 --iters 1
+    python -m paper_2207_05152_gb300.profile_case --case volume --iters 1
 
 Each iteration encodes and decodes the batch and checks the round trip.
 """
@@ -18,7 +19,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4"])
+    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4", "volume"])
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--count", type=int, default=8)
     ap.add_argument("--precision", default="int8", choices=["int8", "fp32"])
@@ -26,6 +27,22 @@ def main():
     import torch
     from paper_2207_05152_gb300 import workloads
     from paper_2207_05152_gb300.codec import Codec
+    if args.case == "volume":
+        # the 35 x 256 x 256 scan with the 3D window (grid decoder)
+        from paper_2207_05152_gb300 import _lib, model as M
+        _, b3, b3f = workloads.models(window=M.VOLUME_WINDOW)
+        vol = workloads.volume_scan()
+        codec = Codec(b3 if args.precision == "int8" else b3f)
+        dv = torch.from_numpy(vol).cuda()
+        S = _lib.dlic_auto_streams(vol.shape[1], vol.shape[2])
+        for _ in range(args.iters):
+            out, offs = codec.encode_volume([dv], [S])
+            o = offs.cpu().tolist()
+            dec, status = codec.decode_volume(out, [0, o[-1]], [vol.shape], [S])
+            torch.cuda.synchronize()
+            assert int(status[0].item()) == 0 and torch.equal(dec[0], dv)
+        print("ok volume", vol.shape)
+        return
     _, blob8, blob32 = workloads.models()
     imgs = [workloads.cfg2_image()] if args.case == "cfg2" else workloads.cfg4_images(args.count)
     streams = [256] if args.case == "cfg2" else None
