@@ -471,7 +471,55 @@ def measure_volume(args):
                                     "roundtrip_bit_exact": st2.cpu().tolist() == [0] * D and all(
                                         torch.equal(a, b) for a, b in zip(decs, slices))}
     codec.close()
+    res["trained"] = _train_volume_windows(vol, dv, S)
     return res
+
+
+def _train_volume_windows(vol, dv, S, steps: int = 1000):
+    """Sec. IV's comparison of 2D and 3D windows with trained networks: a
+    12-128-128-256 (2D window) and a 21-128-128-256 (3D window) network, each
+    trained for `steps` BF16 steps of batch 65536 on 2M contexts sampled from
+    the scan, quantised to INT8, then the scan coded (2D: the slices as a
+    batch; 3D: as a volume)."""
+    import torch
+    import synth
+    from paper_2207_05152_gb300 import model as M
+    from paper_2207_05152_gb300 import train as T
+    from paper_2207_05152_gb300.codec import Codec
+    D, H, W = vol.shape
+    npx = int(vol.size)
+    out = {"steps": steps, "contexts": 1 << 21}
+    for name, window in (("2d", M.DEFAULT_WINDOW), ("3d", M.VOLUME_WINDOW)):
+        ctx, tgt = T.sample_window_contexts(list(vol), 1 << 21, 5101, window)
+        pc, pt = torch.from_numpy(ctx).cuda(), torch.from_numpy(tgt).cuda()
+        tr = T.Trainer(synth.xavier_mlp([M.window_size(window), 128, 128, 256], 5), "bf16", max_batch=TRAIN_BATCH)
+        gen = torch.Generator(device="cuda").manual_seed(5102)
+        for _ in range(steps):
+            idx = torch.randint(0, pc.shape[0], (TRAIN_BATCH,), device="cuda", generator=gen)
+            tr.step(pc.index_select(0, idx).contiguous(), pt.index_select(0, idx).contiguous())
+        torch.cuda.synchronize()
+        assert tr.status() == 0
+        loss = float(tr.loss.item())
+        codec = Codec(M.int8_blob(tr.layers(), ctx[:4096], window))
+        tr.close()
+        if name == "2d":
+            slices = [dv[z] for z in range(D)]
+            enc, offs = codec.encode(slices, [S] * D)
+            torch.cuda.synchronize()
+            o = offs.cpu().tolist()
+            decs, st = codec.decode(enc, o, [(H, W)] * D)
+            torch.cuda.synchronize()
+            ok = st[:D].cpu().tolist() == [0] * D and all(torch.equal(a, b) for a, b in zip(decs, slices))
+        else:
+            enc, offs = codec.encode_volume([dv], [S])
+            torch.cuda.synchronize()
+            o = offs.cpu().tolist()
+            decs, st = codec.decode_volume(enc, [0, o[-1]], [vol.shape], [S])
+            torch.cuda.synchronize()
+            ok = int(st[0].item()) == 0 and torch.equal(decs[0], dv)
+        out[name] = {"final_loss_bits": round(loss, 4), "bpp": round(8.0 * o[-1] / npx, 4), "roundtrip_bit_exact": ok}
+        codec.close()
+    return out
 
 
 def measure_domain_training(args, steps: int = 2000):

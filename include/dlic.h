@@ -314,27 +314,28 @@ DLIC_API dlic_status dlic_decode_volume(const dlic_model *model, const void *d_i
 
 enum { DLIC_TRAIN_BF16 = 0, DLIC_TRAIN_FP32 = 1, DLIC_TRAIN_BF16X3 = 2 };
 
-/* Number of FP32 parameters of a 12 -> h1 -> h2 -> 256 network, laid out as
- * W1 [h1][12], b1 [h1], W2 [h2][h1], b2 [h2], W3 [256][h2], b3 [256] (the
+/* Number of FP32 parameters of an n_in -> h1 -> h2 -> 256 network (n_in:
+ * the priors of the model's window, 12 for the default window), laid out as
+ * W1 [h1][n_in], b1 [h1], W2 [h2][h1], b2 [h2], W3 [256][h2], b3 [256] (the
  * layer order of an FP32 model blob). */
-DLIC_API size_t dlic_train_param_count(int h1, int h2);
+DLIC_API size_t dlic_train_param_count(int n_in, int h1, int h2);
 
 /* Creates a trainer: FP32 master weights (copied from h_params, host),
  * Adam moments (lr 1e-3, betas 0.9 / 0.999, eps 1e-8, bias-corrected) and
  * device buffers for batches of up to max_batch contexts.  mode
  * DLIC_TRAIN_BF16 runs the two wide layers and every backward product on
- * the tensor cores with bf16 operands and FP32 accumulation (the 12-input
- * first layer in FP32 on the CUDA cores); DLIC_TRAIN_BF16X3 stores every
+ * the tensor cores with bf16 operands and FP32 accumulation (the first
+ * layer, n_in <= 96 inputs, in FP32 on the CUDA cores); DLIC_TRAIN_BF16X3 stores every
  * tensor-core operand as two bf16 planes (x = hi + lo) and accumulates
  * hi*hi + lo*hi + hi*lo (about 16 significant bits per operand, three times
  * the MMAs); DLIC_TRAIN_FP32 runs every product in FP32 on the CUDA cores.
  * Allocates its device memory here and frees it in dlic_trainer_destroy. */
-DLIC_API dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_batch, const float *h_params,
+DLIC_API dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, int max_batch, const float *h_params,
                                          dlic_trainer **out);
 DLIC_API dlic_status dlic_trainer_destroy(dlic_trainer *trainer);
 
-/* Loss of a batch: d_ctx holds B x 12 u8 causal priors (the gather order of
- * dlic_encode), d_tgt B u8 target pixels; *d_loss_bits (device float)
+/* Loss of a batch: d_ctx holds B x n_in u8 causal priors (the window's
+ * order, as the coder gathers them), d_tgt B u8 target pixels; *d_loss_bits (device float)
  * receives mean_b -log2 softmax(z_b)[y_b]. */
 DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
                                         float *d_loss_bits, void *stream);

@@ -62,8 +62,8 @@ SIGNATURES = {
     "dlic_encode_volume": (_I, [_VP, _VOLP, _I, _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "dlic_decode_volume_workspace_size": (_I, [_VP, _VOLP, _I, C.POINTER(_SZ)]),
     "dlic_decode_volume": (_I, [_VP, _VP, C.POINTER(C.c_uint64), _I, _VOLP, _VP, _VP, _SZ, _VP]),
-    "dlic_train_param_count": (_SZ, [_I, _I]),
-    "dlic_trainer_create": (_I, [_I, _I, _I, _I, _VP, C.POINTER(_VP)]),
+    "dlic_train_param_count": (_SZ, [_I, _I, _I]),
+    "dlic_trainer_create": (_I, [_I, _I, _I, _I, _I, _VP, C.POINTER(_VP)]),
     "dlic_trainer_destroy": (_I, [_VP]),
     "dlic_train_forward": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "dlic_train_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP]),
@@ -232,14 +232,14 @@ def dlic_decode_volume(model: int, d_in: int, in_offsets, volumes, d_status: int
                                    stream or None))
 
 
-def dlic_train_param_count(h1: int, h2: int) -> int:
-    return int(lib().dlic_train_param_count(h1, h2))
+def dlic_train_param_count(n_in: int, h1: int, h2: int) -> int:
+    return int(lib().dlic_train_param_count(n_in, h1, h2))
 
 
-def dlic_trainer_create(h1: int, h2: int, mode: int, max_batch: int, h_params) -> int:
+def dlic_trainer_create(n_in: int, h1: int, h2: int, mode: int, max_batch: int, h_params) -> int:
     """h_params: contiguous float32 numpy array of dlic_train_param_count values."""
     h = _VP()
-    check(lib().dlic_trainer_create(h1, h2, mode, max_batch, h_params.ctypes.data, C.byref(h)))
+    check(lib().dlic_trainer_create(n_in, h1, h2, mode, max_batch, h_params.ctypes.data, C.byref(h)))
     return h.value
 
 

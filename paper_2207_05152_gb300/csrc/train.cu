@@ -647,13 +647,25 @@ __global__ void __launch_bounds__(128) k_row_epilogue(const float *C, int epi, E
 // Small kernels: features, reductions, Adam, weight shadows.
 // ---------------------------------------------------------------------------
 // v / 128 - 1 has at most 8 significant bits: exact in bf16, low plane 0.
-// Network inputs x/128 - 1 (exact in bf16 and FP32), K padded to 16; the
-// transposed copy XT [16][ldT] only for the FP32 path (XT non-null).  BF16:
-// one context per thread, 12 bytes in, two 16-byte rows out (plus a zero
-// low plane in split mode).
-__global__ void k_features(const uint8_t *ctx, int B, int ldT, void *X, void *XT, int bf16, size_t xplane) {
+// Network inputs x/128 - 1 (exact in bf16 and FP32) of n_in priors per
+// context, K padded to k1 (a multiple of 16); the transposed copy XT
+// [k1][ldT] only for the FP32 path (XT non-null).  BF16: one context per
+// thread; the 12-prior window reads three words and writes two 16-byte rows
+// (plus a zero low plane in split mode).
+__global__ void k_features(const uint8_t *ctx, int B, int n_in, int k1, int ldT, void *X, void *XT, int bf16,
+                           size_t xplane) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (bf16 && n_in != kPriors) {
+        uint16_t *o = static_cast<uint16_t *>(X) + (size_t)b * k1;
+        for (int k = 0; k < k1; k += 2) {
+            const float x0 = k < n_in ? (float)ctx[(size_t)b * n_in + k] * 0.0078125f - 1.0f : 0.0f;
+            const float x1 = k + 1 < n_in ? (float)ctx[(size_t)b * n_in + k + 1] * 0.0078125f - 1.0f : 0.0f;
+            reinterpret_cast<uint32_t *>(o)[k / 2] = pack_bf16x2(x0, x1);
+            if (xplane) reinterpret_cast<uint32_t *>(o + xplane)[k / 2] = 0u;
+        }
+        return;
+    }
     if (bf16) {
         const uint8_t *c = ctx + (size_t)b * kPriors;
         const bool al4 = (reinterpret_cast<uintptr_t>(c) & 3u) == 0;
@@ -679,40 +691,43 @@ __global__ void k_features(const uint8_t *ctx, int B, int ldT, void *X, void *XT
         }
         return;
     }
-    for (int k = 0; k < 16; k++) {
-        const float x = k < kPriors ? (float)ctx[(size_t)b * kPriors + k] * 0.0078125f - 1.0f : 0.0f;
-        reinterpret_cast<float *>(X)[(size_t)b * 16 + k] = x;
+    for (int k = 0; k < k1; k++) {
+        const float x = k < n_in ? (float)ctx[(size_t)b * n_in + k] * 0.0078125f - 1.0f : 0.0f;
+        reinterpret_cast<float *>(X)[(size_t)b * k1 + k] = x;
         reinterpret_cast<float *>(XT)[(size_t)k * ldT + b] = x;
     }
 }
 
-// First layer of the BF16 modes on the CUDA cores in FP32 (K = 12 is too
-// thin for the tensor cores to pay): h1 = ReLU(b1 + sum_k W1[j][k] x_k),
-// written as bf16 rows (and low planes when p1 != 0).  32 contexts per
-// block, thread = hidden unit; the bf16 tile is staged in shared memory and
+// First layer of the BF16 modes on the CUDA cores in FP32 (K = the
+// window's priors, at most 96, is too thin for the tensor cores to pay):
+// h1 = ReLU(b1 + sum_k W1[j][k] x_k), written as bf16 rows (and low planes
+// when p1 != 0).  32 contexts per block, thread = hidden unit holding its
+// NMAX weights (zero past n_in); the bf16 tile is staged in shared memory and
 // leaves as 16-byte rows.
 constexpr int kL1Ctx = 32;
-__global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, const float *W1, const float *b1, int h1,
-                                                uint16_t *H1, size_t p1) {
+template <int NMAX>
+__global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n_in, const float *W1, const float *b1,
+                                                int h1, uint16_t *H1, size_t p1) {
     __shared__ __align__(16) uint16_t thi[kL1Ctx * kMaxHidden];
     __shared__ __align__(16) uint16_t tlo[kL1Ctx * kMaxHidden];
-    __shared__ float xs[kL1Ctx][kPriors];
+    __shared__ float xs[kL1Ctx][NMAX];
     const int tid = threadIdx.x, b0 = blockIdx.x * kL1Ctx;
-    for (int i = tid; i < kL1Ctx * kPriors; i += 256) {
-        const int r = i / kPriors, k = i % kPriors;
-        xs[r][k] = b0 + r < B ? (float)ctx[(size_t)(b0 + r) * kPriors + k] * 0.0078125f - 1.0f : 0.0f;
+    for (int i = tid; i < kL1Ctx * NMAX; i += 256) {
+        const int r = i / NMAX, k = i % NMAX;
+        xs[r][k] = b0 + r < B && k < n_in ? (float)ctx[(size_t)(b0 + r) * n_in + k] * 0.0078125f - 1.0f : 0.0f;
     }
     __syncthreads();
     if (tid < h1) {
         const int j = tid;
-        float w[kPriors];
+        float w[NMAX];
 #pragma unroll
-        for (int k = 0; k < kPriors; k++) w[k] = W1[j * kPriors + k];
+        for (int k = 0; k < NMAX; k++) w[k] = k < n_in ? W1[j * n_in + k] : 0.0f;
         const float bj = b1[j];
         for (int r = 0; r < kL1Ctx; r++) {
             float acc = bj;
+            // (the zero weights past n_in add exact zeros)
 #pragma unroll
-            for (int k = 0; k < kPriors; k++) acc = fmaf(xs[r][k], w[k], acc);
+            for (int k = 0; k < NMAX; k++) acc = fmaf(xs[r][k], w[k], acc);
             const float v = fmaxf(acc, 0.0f);
             const uint16_t hi = f2bf(v);
             thi[r * h1 + j] = hi;
@@ -732,9 +747,10 @@ __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, const
 
 // out[i] = scale * sum_z part[z * stride + i]: 32 columns per block, the
 // partials split over blockDim.y row groups and combined in a fixed order
-// (deterministic).  With `pad16` the columns are a [h][16] array whose first
-// kPriors entries per row go to a compact [h][kPriors] output.
-__global__ void k_reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int pad16) {
+// (deterministic).  With `kpad` the columns are a [h][kpad] array whose first
+// kin entries per row go to a compact [h][kin] output.
+__global__ void k_reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int kpad,
+                               int kin) {
     __shared__ float red[32][33];
     const int x = threadIdx.x, y = threadIdx.y, G = blockDim.y;
     const int i = blockIdx.x * 32 + x;
@@ -749,8 +765,8 @@ __global__ void k_reduce_parts(const float *part, int nparts, size_t stride, int
         float t = 0.0f;
         for (int k = 0; k < G; k++) t += red[k][x];
         t *= scale;
-        if (!pad16) out[i] = t;
-        else if (i % 16 < kPriors) out[(i / 16) * kPriors + i % 16] = t;
+        if (!kpad) out[i] = t;
+        else if (i % kpad < kin) out[(i / kpad) * kin + i % kpad] = t;
     }
 }
 
@@ -795,7 +811,7 @@ __device__ __forceinline__ void shadow_put(void *Wd, size_t idx, size_t plane, f
 // updated weights written straight into the GEMM operand copies (row-major
 // and transposed).  The zero padding of the W1 copy is never touched.
 struct ShadowArgs {
-    int h1, h2, bf16, split;
+    int n_in, k1, h1, h2, bf16, split;
     void *w1, *w2, *w3, *w2t, *w3t;
 };
 __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, float lr, float b1, float b2, float eps,
@@ -809,10 +825,10 @@ __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, fl
     ve[i] = v;
     const float w = p[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
     p[i] = w;
-    const int h1 = sa.h1, h2 = sa.h2;
-    const int oW2 = h1 * kPriors + h1, oW3 = oW2 + h2 * h1 + h2;
-    if (i < h1 * kPriors) {
-        shadow_put(sa.w1, (size_t)(i / kPriors) * 16 + i % kPriors, (size_t)h1 * 16, w, sa.bf16, sa.split);
+    const int h1 = sa.h1, h2 = sa.h2, n_in = sa.n_in;
+    const int oW2 = h1 * n_in + h1, oW3 = oW2 + h2 * h1 + h2;
+    if (i < h1 * n_in) {
+        shadow_put(sa.w1, (size_t)(i / n_in) * sa.k1 + i % n_in, (size_t)h1 * sa.k1, w, sa.bf16, sa.split);
     } else if (i >= oW2 && i < oW2 + h2 * h1) {
         const int j = i - oW2, o = j / h1, k = j % h1;
         shadow_put(sa.w2, j, (size_t)h2 * h1, w, sa.bf16, sa.split);
@@ -850,6 +866,7 @@ using namespace dlic;
 // Trainer object and C ABI
 // ===========================================================================
 struct dlic_trainer {
+    int n_in, k1;                                // network inputs (the window's priors), padded to 16
     int h1, h2, mode, max_batch, num_sms;
     int bf, split;                               // bf16 operands; hi + lo planes
     size_t nparams;
@@ -866,17 +883,17 @@ struct dlic_trainer {
 
 namespace {
 
-size_t param_count(int h1, int h2) {
-    return (size_t)h1 * kPriors + h1 + (size_t)h2 * h1 + h2 + (size_t)kSymbols * h2 + kSymbols;
+size_t param_count(int n_in, int h1, int h2) {
+    return (size_t)h1 * n_in + h1 + (size_t)h2 * h1 + h2 + (size_t)kSymbols * h2 + kSymbols;
 }
 
 struct ParamView {
     float *W1, *b1, *W2, *b2, *W3, *b3;
 };
-ParamView view(float *p, int h1, int h2) {
+ParamView view(float *p, int n_in, int h1, int h2) {
     ParamView v;
     v.W1 = p;
-    v.b1 = v.W1 + (size_t)h1 * kPriors;
+    v.b1 = v.W1 + (size_t)h1 * n_in;
     v.W2 = v.b1 + h1;
     v.b2 = v.W2 + (size_t)h2 * h1;
     v.W3 = v.b2 + h2;
@@ -979,20 +996,20 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "fp32 gemm launch");
 }
 
-void reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int pad16,
+void reduce_parts(const float *part, int nparts, size_t stride, int n, float *out, float scale, int kpad, int kin,
                   cudaStream_t st) {
-    if (!pad16 && n >= 4096 && n % 4 == 0 && stride % 4 == 0 && nparts < 256) {
+    if (!kpad && n >= 4096 && n % 4 == 0 && stride % 4 == 0 && nparts < 256) {
         k_reduce_parts4<<<(n + 127) / 128, dim3(32, 8), 0, st>>>(part, nparts, stride, n, out, scale);
         return;
     }
     const int G = nparts >= 256 ? 32 : 8;
-    k_reduce_parts<<<(n + 31) / 32, dim3(32, G), 0, st>>>(part, nparts, stride, n, out, scale, pad16);
+    k_reduce_parts<<<(n + 31) / 32, dim3(32, G), 0, st>>>(part, nparts, stride, n, out, scale, kpad, kin);
 }
 
 dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
-    ParamView p = view(t->params, t->h1, t->h2);
+    ParamView p = view(t->params, t->n_in, t->h1, t->h2);
     const int bf = t->bf, sp = t->split;
-    k_shadow<<<(t->h1 * 16 + 255) / 256, 256, 0, st>>>(p.W1, t->h1, kPriors, 16, t->w1, nullptr, bf, sp);
+    k_shadow<<<(t->h1 * t->k1 + 255) / 256, 256, 0, st>>>(p.W1, t->h1, t->n_in, t->k1, t->w1, nullptr, bf, sp);
     k_shadow<<<(t->h2 * t->h1 + 255) / 256, 256, 0, st>>>(p.W2, t->h2, t->h1, t->h1, t->w2, t->w2t, bf, sp);
     k_shadow<<<(kSymbols * t->h2 + 255) / 256, 256, 0, st>>>(p.W3, kSymbols, t->h2, t->h2, t->w3, t->w3t, bf, sp);
     cudaError_t ce = cudaGetLastError();
@@ -1005,10 +1022,10 @@ dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
 // [batch] for its K-major CUDA-core GEMM.
 dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss, bool backward,
                 cudaStream_t st) {
-    const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128;
+    const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128, n_in = t->n_in, k1 = t->k1;
     const int bf = t->bf;
-    ParamView p = view(t->params, h1, h2);
-    ParamView g = view(t->grads, h1, h2);
+    ParamView p = view(t->params, n_in, h1, h2);
+    ParamView g = view(t->grads, n_in, h1, h2);
     const int P = t->max_batch;   // capacity: pitch of the transposed arrays, offset of the low planes
     const size_t Bm = (size_t)P;
     const size_t sp = t->split ? 1 : 0;
@@ -1021,16 +1038,25 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     auto wgrad = [&](const void *rm, const void *tr, int n) {
         return bf ? Operand{rm, B, n, n, Bm * n, 1} : Operand{tr, n, B, P, (size_t)n * Bm, 0};
     };
-    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, B, P, t->X, bf ? nullptr : t->XT, bf, sp * Bm * 16);
+    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, B, n_in, k1, P, t->X, bf ? nullptr : t->XT, bf, sp * Bm * k1);
     EpiArgs e{};
     // layer 1, 2: bias + ReLU
     e.bias = p.b1; e.out = t->H1; e.outT = t->H1T; e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     dlic_status s = DLIC_OK;
-    if (bf)
-        k_layer1<<<(B + kL1Ctx - 1) / kL1Ctx, 256, 0, st>>>(ctx, B, p.W1, p.b1, h1, static_cast<uint16_t *>(t->H1),
-                                                          sp * Bm * h1);
-    else if ((s = gemm(t, rowmaj(t->X, 16), wmat(t->w1, h1, 16), B, h1, 16, EPI_BIAS_RELU, e, 1, st)))
+    if (bf) {
+        const int nb = (B + kL1Ctx - 1) / kL1Ctx;
+        uint16_t *H1 = static_cast<uint16_t *>(t->H1);
+        if (n_in <= 16)
+            k_layer1<16><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+        else if (n_in <= 32)
+            k_layer1<32><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+        else if (n_in <= 64)
+            k_layer1<64><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+        else
+            k_layer1<96><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+    } else if ((s = gemm(t, rowmaj(t->X, k1), wmat(t->w1, h1, k1), B, h1, k1, EPI_BIAS_RELU, e, 1, st))) {
         return s;
+    }
     e = EpiArgs{}; e.bias = p.b2; e.out = t->H2; e.outT = t->H2T; e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
     if ((s = gemm(t, rowmaj(t->H1, h1), wmat(t->w2, h2, h1), B, h2, h1, EPI_BIAS_RELU, e, 1, st))) return s;
     // layer 3 + softmax cross-entropy: loss partials, dz, db3 partials
@@ -1040,23 +1066,23 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     e.colsum = t->colsum; e.loss = t->losspart;
     if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, kSymbols, h2), B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
         return s;
-    reduce_parts(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B, 0, st);
+    reduce_parts(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B, 0, 0, st);
     if (!backward) {
         cudaError_t ce = cudaGetLastError();
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
     }
-    reduce_parts(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f, 0, st);
+    reduce_parts(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f, 0, 0, st);
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
     if ((s = gemm(t, rowmaj(t->DZ, kSymbols), wmat(t->w3t, h2, kSymbols), B, h2, kSymbols, EPI_RELU_GRAD, e, 1, st)))
         return s;
-    reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, st);
+    reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, 0, st);
     // dh1 = da2 W2, da1 = dh1 * [h1 > 0]; db1
     e = EpiArgs{}; e.act = t->H1; e.out = bf ? t->DA1 : nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
     e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
-    reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, st);
+    reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, 0, st);
     // weight gradients dW = dY^T X: K = batch, split-K partials summed in a
     // fixed order; enough splits to cover every SM
     auto splits_for = [&](int M) {
@@ -1069,27 +1095,28 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     e = EpiArgs{}; e.c = t->part; e.ldc = h2;
     if ((s = gemm(t, wgrad(t->DZ, t->DZT, kSymbols), wgrad(t->H2, t->H2T, h2), kSymbols, h2, B, EPI_F32, e, sk, st)))
         return s;
-    reduce_parts(t->part, sk, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, st);
+    reduce_parts(t->part, sk, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, 0, st);
     sk = splits_for(h2);
     e = EpiArgs{}; e.c = t->part; e.ldc = h1;
     if ((s = gemm(t, wgrad(t->DA2, t->DA2T, h2), wgrad(t->H1, t->H1T, h1), h2, h1, B, EPI_F32, e, sk, st))) return s;
-    reduce_parts(t->part, sk, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, st);
+    reduce_parts(t->part, sk, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, 0, st);
     sk = splits_for(h1);
-    e = EpiArgs{}; e.c = t->part; e.ldc = 16;
-    if ((s = gemm(t, wgrad(t->DA1, t->DA1T, h1), wgrad(t->X, t->XT, 16), h1, 16, B, EPI_F32, e, sk, st))) return s;
-    reduce_parts(t->part, sk, (size_t)h1 * 16, h1 * 16, g.W1, 1.0f, 1, st);
+    e = EpiArgs{}; e.c = t->part; e.ldc = k1;
+    if ((s = gemm(t, wgrad(t->DA1, t->DA1T, h1), wgrad(t->X, t->XT, k1), h1, k1, B, EPI_F32, e, sk, st))) return s;
+    reduce_parts(t->part, sk, (size_t)h1 * k1, h1 * k1, g.W1, 1.0f, k1, n_in, st);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "backward launch");
 }
 
 }  // namespace
 
-extern "C" size_t dlic_train_param_count(int h1, int h2) { return param_count(h1, h2); }
+extern "C" size_t dlic_train_param_count(int n_in, int h1, int h2) { return param_count(n_in, h1, h2); }
 
-extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_batch, const float *h_params,
+extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, int max_batch, const float *h_params,
                                            dlic_trainer **out) {
     if (!out) return fail(DLIC_ERR_INVALID, "null output");
     *out = nullptr;
+    if (n_in < 1 || n_in > kMaxPriors) return fail(DLIC_ERR_INVALID, "network inputs must be in [1, %d]", kMaxPriors);
     if (h1 < 16 || h1 > 256 || h1 % 16 || h2 < 16 || h2 > 256 || h2 % 16)
         return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
     if (mode != DLIC_TRAIN_BF16 && mode != DLIC_TRAIN_FP32 && mode != DLIC_TRAIN_BF16X3)
@@ -1097,11 +1124,13 @@ extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_bat
     if (max_batch < 1 || max_batch > (1 << 22)) return fail(DLIC_ERR_INVALID, "max_batch must be in [1, 2^22]");
     if (!h_params) return fail(DLIC_ERR_INVALID, "null initial parameters");
     dlic_trainer *t = new dlic_trainer();
+    t->n_in = n_in;
+    t->k1 = (n_in + 15) / 16 * 16;
     t->h1 = h1; t->h2 = h2; t->mode = mode;
     t->bf = mode != DLIC_TRAIN_FP32;
     t->split = mode == DLIC_TRAIN_BF16X3;
     t->max_batch = (max_batch + 127) / 128 * 128;
-    t->nparams = param_count(h1, h2);
+    t->nparams = param_count(n_in, h1, h2);
     t->step = 0;
     t->lr = 1e-3f; t->beta1 = 0.9f; t->beta2 = 0.999f; t->eps = 1e-8f;
     int dev = 0;
@@ -1122,12 +1151,12 @@ extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_bat
     t->grads = (float *)A(4 * t->nparams);
     t->mom = (float *)A(4 * t->nparams);
     t->vel = (float *)A(4 * t->nparams);
-    t->w1 = A(es * h1 * 16);
+    t->w1 = A(es * h1 * t->k1);
     t->w2 = A(es * h2 * h1);
     t->w3 = A(es * kSymbols * h2);
     t->w2t = A(es * h1 * h2);
     t->w3t = A(es * h2 * kSymbols);
-    t->X = A(es * Bm * 16);
+    t->X = A(es * Bm * t->k1);
     t->H1 = A(es * Bm * h1);
     t->H2 = A(es * Bm * h2);
     t->DZ = A(es * Bm * kSymbols);
@@ -1135,7 +1164,7 @@ extern "C" dlic_status dlic_trainer_create(int h1, int h2, int mode, int max_bat
     if (t->bf) {
         t->DA1 = A(es * Bm * h1);
     } else {
-        t->XT = A(es * 16 * Bm);
+        t->XT = A(es * t->k1 * Bm);
         t->H1T = A(es * h1 * Bm);
         t->H2T = A(es * h2 * Bm);
         t->DZT = A(es * kSymbols * Bm);
@@ -1213,7 +1242,7 @@ extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, co
     if (s) return s;
     t->step += 1;
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
-    const ShadowArgs sa{t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
+    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
     k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, t->grads, t->mom, t->vel, (int)t->nparams, t->lr,
                                                              t->beta1, t->beta2, t->eps, c1, c2, sa);
     cudaError_t ce = cudaGetLastError();

@@ -24,9 +24,9 @@ def flatten(layers) -> np.ndarray:
     return np.concatenate([np.asarray(a, np.float32).reshape(-1) for wb in layers for a in wb])
 
 
-def unflatten(vec, h1: int, h2: int):
+def unflatten(vec, h1: int, h2: int, n_in: int = 12):
     v = np.asarray(vec, np.float32)
-    shapes = [(h1, 12), (h1,), (h2, h1), (h2,), (256, h2), (256,)]
+    shapes = [(h1, n_in), (h1,), (h2, h1), (h2,), (256, h2), (256,)]
     out, off = [], 0
     for s in shapes:
         n = int(np.prod(s))
@@ -57,17 +57,46 @@ def sample_contexts(images, count: int, seed: int):
     return ctx, tgt
 
 
+def sample_window_contexts(images, count: int, seed: int, window):
+    """(ctx u8 [count, window size], tgt u8 [count]) for any causal window
+    (u, l, r), or a 3D window (u, l, r, pu, pd, pl, pr) over the consecutive
+    slices of a volume (`images` are then its slices; the lower layer comes
+    from the slice before, zeros for the first).  Positions drawn uniformly;
+    priors outside an image or the volume are 0."""
+    import synth
+    idx, rr, cc = synth.sample_positions(images, count, seed)
+    offs = M.window_offsets3(window)
+    ctx = np.zeros((count, len(offs)), np.uint8)
+    tgt = np.zeros(count, np.uint8)
+    for i, img in enumerate(images):
+        sel = np.nonzero(idx == i)[0]
+        if sel.size == 0:
+            continue
+        H, W = img.shape
+        r, c = rr[sel], cc[sel]
+        for k, (dz, dr, dc) in enumerate(offs):
+            if i + dz < 0:
+                continue
+            src = images[i + dz]
+            y, x = r + dr, c + dc
+            ok = (y >= 0) & (y < H) & (x >= 0) & (x < W)
+            ctx[sel[ok], k] = src[y[ok], x[ok]]
+        tgt[sel] = img[r, c]
+    return ctx, tgt
+
+
 class Trainer:
     """FP32 master weights + Adam on the current CUDA device."""
 
     def __init__(self, layers, mode: str = "bf16", max_batch: int = 65536):
+        self.n_in = layers[0][0].shape[1]   # the window's priors
         self.h1 = layers[0][0].shape[0]
         self.h2 = layers[1][0].shape[0]
         self.mode = mode
-        self.nparams = _lib.dlic_train_param_count(self.h1, self.h2)
+        self.nparams = _lib.dlic_train_param_count(self.n_in, self.h1, self.h2)
         flat = np.ascontiguousarray(flatten(layers))
         assert flat.size == self.nparams
-        self.handle = _lib.dlic_trainer_create(self.h1, self.h2, MODES[mode], max_batch, flat)
+        self.handle = _lib.dlic_trainer_create(self.n_in, self.h1, self.h2, MODES[mode], max_batch, flat)
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
     def close(self):
@@ -112,10 +141,12 @@ class Trainer:
         _lib.dlic_trainer_params(self.handle, flat.data_ptr(), True, self._stream())
 
     def layers(self):
-        return unflatten(self.params().cpu().numpy(), self.h1, self.h2)
+        return unflatten(self.params().cpu().numpy(), self.h1, self.h2, self.n_in)
 
-    def fp32_blob(self) -> bytes:
-        return M.fp32_blob(self.layers())
+    def fp32_blob(self, window=M.DEFAULT_WINDOW) -> bytes:
+        """The trained network as an FP32 model blob for `window` (whose
+        prior count is the trainer's n_in)."""
+        return M.fp32_blob(self.layers(), window)
 
     def status(self) -> int:
         return _lib.dlic_trainer_status(self.handle)

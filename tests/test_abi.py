@@ -64,3 +64,14 @@ def test_header_parser_and_model_checks(lib, orc):
     with pytest.raises(lib.DlicError) as e:
         lib.dlic_model_create(bytes(bad))
     assert e.value.code == lib.DLIC_ERR_INVALID
+
+
+def test_window_contexts_match_the_default_sampler():
+    import numpy as np
+    # the general sampler with the default window gives the 12-prior contexts
+    import synth
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.voronoi_image(30, 41, 5), synth.voronoi_image(17, 9, 6)]
+    a, ta = T.sample_contexts(imgs, 500, 3)
+    b, tb = T.sample_window_contexts(imgs, 500, 3, (2, 2, 2))
+    assert np.array_equal(a, b) and np.array_equal(ta, tb)

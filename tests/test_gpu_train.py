@@ -45,7 +45,7 @@ def _grads(T, mode, layers, ctx, tgt):
     loss, g = tr.backward(c, t)
     torch.cuda.synchronize()
     assert tr.status() == 0
-    out = float(loss.item()), T.unflatten(g.cpu().numpy(), tr.h1, tr.h2)
+    out = float(loss.item()), T.unflatten(g.cpu().numpy(), tr.h1, tr.h2, tr.n_in)
     tr.close()
     return out
 
@@ -142,3 +142,25 @@ def test_autograd_function(T):
     assert abs(float(loss) - loss64) < 1e-4
     assert _rel(theta.grad.cpu().numpy(), flat) < 1e-4
     tr.close()
+
+
+@pytest.mark.parametrize("window", [(8, 6, 2), (1, 1, 1), (2, 2, 2, 1, 1, 1, 1)])
+@pytest.mark.parametrize("mode,tol", [("fp32", 2e-4), ("bf16x3", 1e-3)])
+def test_window_gradients_against_fp64(T, window, mode, tol):
+    # other causal windows (Fig. 6's 9 x 9: 78 inputs; a 4-input window) and
+    # a 3D window over the slices of a volume (21 inputs): the first layer's
+    # K padded to 16, 80
+    from paper_2207_05152_gb300 import model as M
+    n = M.window_size(window)
+    imgs = list(synth.phantom_volume(4, 64, 64, 3)) if len(window) == 7 else [synth.config_image(3, i) for i in range(2)]
+    ctx, tgt = T.sample_window_contexts(imgs, 2048, 11, window)
+    layers = synth.xavier_mlp([n, 128, 128, 256], 11)
+    rng = synth.Rng(111)
+    layers = [(w, (0.05 * rng.normal(b.size)).astype(np.float32)) for w, b in layers]
+    loss, g = _grads(T, mode, layers, ctx, tgt)
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    errs = [(_rel(gw, rw), _rel(gb, rb)) for (gw, gb), (rw, rb) in zip(g, ref)]
+    print(window, mode, errs)
+    assert abs(loss - loss64) <= 1e-3 * loss64
+    for ew, eb in errs:
+        assert ew < tol and eb < tol
