@@ -122,3 +122,28 @@ def test_corrupt_slice_is_reported(Codec, orc):
         else:
             assert s == _lib.DLIC_ERR_CORRUPT or not np.array_equal(dec[0].cpu().numpy(), vol)
     codec.close()
+
+
+def test_pitched_volume(Codec, orc):
+    # rows and slices with padding: pitch > width, slice pitch > pitch x height,
+    # read by the encoder and written by the decoder (grid and cluster paths)
+    from paper_2207_05152_gb300 import _lib
+    vol = synth.phantom_volume(5, 30, 44, 21)
+    blob = _blob(M.VOLUME_WINDOW, "int8", 128, vol)
+    for plan in (_lib.DLIC_PLAN_AUTO, _lib.DLIC_PLAN_IMAGE):
+        codec = Codec(blob, decode_plan=plan)
+        big = torch.zeros((5, 33, 52), dtype=torch.uint8, device="cuda")
+        big[:, :30, :44] = torch.from_numpy(vol).cuda()
+        view = big[:, :30, :44]
+        out, offs = codec.encode_volume([view], [16])
+        torch.cuda.synchronize()
+        o = offs.cpu().tolist()
+        want, woffs = orc.encode_volume(blob, vol, 16)
+        assert out[:o[-1]].cpu().numpy().tobytes() == want
+        dst = torch.full((5, 31, 47), 7, dtype=torch.uint8, device="cuda")
+        dec, st = codec.decode_volume(out, [0, o[-1]], [vol.shape], [16], outs=[dst[:, :30, :44]])
+        torch.cuda.synchronize()
+        assert int(st[0].item()) == 0
+        assert np.array_equal(dst[:, :30, :44].cpu().numpy(), vol)
+        assert int(dst[:, 30:, :].max().item()) == 7 and int(dst[:, :, 44:].max().item()) == 7   # padding untouched
+        codec.close()
