@@ -60,6 +60,7 @@ struct DecTcParams {
     int zlist;        // grid decoder: capacity of the per-wave table of active slices (and,
                       // for a batch, of the per-image stream count, flags and wave count)
     int T;            // grid decoder of a batch: waves of the longest image
+    int lut2;         // 1: the table's powers of two expanded to kTableSteps entries
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -111,7 +112,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
     L.pg = take(4u * nt);
     L.zpre = take(4u * prm.zlist);
     L.dsym = take(prm.gimg ? 0u : (uint32_t)prm.list_rows);   // decoded pixels held back until the barrier
-    L.lut = take(4u * 64);
+    L.lut = take(prm.lut2 ? 4u * kTableSteps : 4u * 64);
     L.st_x = take(4u * g * prm.depth);
     L.st_pos = take(4u * g * prm.depth);
     L.st_end = take(4u * g * prm.depth);
@@ -546,7 +547,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 w1q[i] = i < ((NPRI + 3) / 4) * kDecHidden ? __ldg(m.q1t + i) : 0u;
         }
         uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
-        if (tid < 64) lut[tid] = m.lut[tid];
+        if (prm.lut2)
+            expand_lut(m.lut, lut, tid, kDecThreads);   // lut2[u] = lut[u mod 64] >> (u div 64)
+        else if (tid < 64)
+            lut[tid] = m.lut[tid];
         if (tid < m.n_in) {
             int dz, dr, dc;
             window_offset(m, tid, dz, dr, dc);
@@ -780,6 +784,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         (P > 1 && lane < TSLOTS) ? map_shared(tring_addr, (k + (uint32_t)lane) % (uint32_t)P) : tring_addr;
     const uint32_t ring_dst = (P > 1 && lane < P) ? map_shared(ring_addr, (k + (uint32_t)lane) % (uint32_t)P) : ring_addr;
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
+    const bool use_lut2 = prm.lut2 != 0;
     uint8_t *pri = smem + L.pri;   // priors of the chunk's pixels as s8 (x - 128), 16 bytes each
     uint8_t *b23 = smem + L.b23;
     float *zb = reinterpret_cast<float *>(smem + L.z);
@@ -1304,14 +1309,16 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
-                uint32_t key = float_key(z[0]);
+                // the lane's maximum, then the warp's through an order-preserving
+                // integer key (a zero maximum's sign changes no weight)
+                float lmax = z[0];
 #pragma unroll
-                for (int q = 1; q < 8; q++) key = max(key, float_key(z[q]));
-                const float mx = key_float(__reduce_max_sync(0xffffffffu, key));
+                for (int q = 1; q < 8; q++) lmax = fmaxf(lmax, z[q]);
+                const float mx = key_float(__reduce_max_sync(0xffffffffu, float_key(lmax)));
                 uint32_t w[8], lsum = 0;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    w[q] = table_weight(mx, z[q], m.tscale, lut);
+                    w[q] = use_lut2 ? table_weight2(mx, z[q], m.tscale, lut) : table_weight(mx, z[q], m.tscale, lut);
                     lsum += w[q];
                 }
                 // the total (and from it Q) runs beside the prefix scan
@@ -1606,6 +1613,9 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, ui
     prm.max_g = (min(maxH, 65535) + P - 1) / P;
     prm.pay_words = 0;
     auto size = [&] { return dec_layout(prm, f32).total; };
+    // the expanded power-of-two table (6 KB) only where it costs no chunk size
+    prm.lut2 = 1;
+    if (size() > limit) prm.lut2 = 0;
     while (!f32 && size() > limit && prm.nt > 16) prm.nt /= 2;
     if (size() > limit) prm.tq = 0;
     // volumes read every prior back from the output volume
@@ -1729,6 +1739,8 @@ static bool plan_grid(const DevModel &m, const DecBatch &b, int NB, uint32_t lim
     const int per_cta = (int)((wave + NB - 1) / NB);
     prm.nt = f32 ? 12 : min(64, max(16, (per_cta + 15) & ~15));
     prm.list_rows = (per_cta + designated + 15) & ~15;
+    prm.lut2 = 1;
+    if (dec_layout(prm, f32).total > limit) prm.lut2 = 0;
     while (!f32 && dec_layout(prm, f32).total > limit && prm.nt > 16) prm.nt /= 2;
     return dec_layout(prm, f32).total <= limit;
 }
