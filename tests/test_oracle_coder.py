@@ -244,3 +244,7 @@ def test_golden_small_bitstreams(orc):
         with open(os.path.join(GOLDEN, name + ".hex")) as fh:
             want = bytes.fromhex(fh.read().strip())
         assert orc.encode(blob, img, S) == want, name
+    for name, blob, vol, S in mg.volume_cases():
+        with open(os.path.join(GOLDEN, name + ".hex")) as fh:
+            want = bytes.fromhex(fh.read().strip())
+        assert orc.encode_volume(blob, vol, S)[0] == want, name

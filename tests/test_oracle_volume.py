@@ -141,3 +141,18 @@ def test_window_fields_round_trip():
         M.window_field((2, 2, 3, 1, 1, 1, 1))
     with pytest.raises(ValueError):
         M.window_field((8, 8, 2, 2, 2, 2, 2))      # 148 priors
+
+
+def test_blob_writer_matches_the_struct_layout():
+    # the package's blob writer, for the 9 x 9 and the 3D window, against the
+    # layout packed field by field in the golden-fixture script
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_golden.py")
+    spec = importlib.util.spec_from_file_location("mg", path)
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    fig6 = synth.predictive_mlp([78, 32, 32, 256], 6, window=M.FIG6_WINDOW)
+    assert M.fp32_blob(fig6, M.FIG6_WINDOW) == [c for c in mg.cases() if c[0].startswith("fig6")][0][1]
+    vol = synth.predictive_mlp([21, 32, 32, 256], 7, window=VOL)
+    assert M.fp32_blob(vol, VOL) == mg.volume_cases()[0][1]
