@@ -102,9 +102,10 @@ DLIC_API const char *dlic_last_error(void);
  * 1 << 24 | u | l << 8 | rr << 16 for rows r-u..r-1 at columns c-l..c+rr,
  * then row r at columns c-l..c-1 (1 <= u <= 8, l <= 8, rr <= 2, so that
  * wave t = 3r + c stays valid), with n_in = u (l + rr + 1) + l priors; the
- * 9 x 9 window of Fig. 6 is (8, 6, 2), 78 priors.  Windows other than the
- * default need the tensor-core INT8 kernels (h1, h2 <= 128 to encode,
- * h1 = h2 = 128 to decode) or the FP32 tiled kernels (h2 <= 128)
+ * 9 x 9 window of Fig. 6 is (8, 6, 2), 78 priors.  A 3D window (see the
+ * volume calls below) adds a layer from the previous slice.  Windows other
+ * than the default need the tensor-core INT8 kernels (h1, h2 <= 128 to
+ * encode, h1 = h2 = 128 to decode) or the FP32 tiled kernels (h2 <= 128)
  * (DLIC_ERR_UNSUPPORTED otherwise).
  * h1 and h2 must be multiples of 16 in [16, 256].  The blob is copied; the
  * model owns device copies of the weights in the layouts the kernels use.
@@ -136,7 +137,8 @@ DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
  *                        and wave (a few very wide images).
  * Every plan gives the same decoded pixels; the forced plans exist to test
  * and measure the ones AUTO takes for long waves.  Applies to later
- * dlic_decode calls with this model; DLIC_ERR_INVALID for another value. */
+ * dlic_decode and dlic_decode_volume calls with this model;
+ * DLIC_ERR_INVALID for another value. */
 enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2, DLIC_PLAN_GRID = 3 };
 DLIC_API dlic_status dlic_model_set_decode_plan(dlic_model *model, int plan);
 
@@ -224,7 +226,9 @@ DLIC_API dlic_status dlic_encode_noalloc(const dlic_model *model, const dlic_ima
 /* Decoding (Sec. II-A Fig. 2 right; Sec. II-B "Preprocessor" wavefront)   */
 /* ---------------------------------------------------------------------- */
 
-/* Parses a bitstream header held in host memory (at least 24 bytes). */
+/* Parses a bitstream header held in host memory (at least 24 bytes): a 2D
+ * image's container or one slice's container of a volume (byte 12 with bit
+ * 7 set); DLIC_ERR_CORRUPT when it is neither. */
 DLIC_API dlic_status dlic_read_header(const void *h_bitstream, size_t bytes, int *height, int *width,
                              int *streams, int *precision, uint64_t *model_hash);
 
