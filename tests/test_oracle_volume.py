@@ -156,3 +156,18 @@ def test_blob_writer_matches_the_struct_layout():
     assert M.fp32_blob(fig6, M.FIG6_WINDOW) == [c for c in mg.cases() if c[0].startswith("fig6")][0][1]
     vol = synth.predictive_mlp([21, 32, 32, 256], 7, window=VOL)
     assert M.fp32_blob(vol, VOL) == mg.volume_cases()[0][1]
+
+
+@pytest.mark.parametrize("window", [VOL, (3, 2, 2, 0, 3, 1, 4)])
+def test_training_contexts_match_the_oracle_gather(orc, window):
+    # the trainer's context sampler over the slices of a volume gives, at
+    # every sampled voxel, the oracle's 3D gather
+    from paper_2207_05152_gb300 import train as T
+    vol = synth.phantom_volume(4, 12, 15, 30)
+    slices = list(vol)
+    ctx, tgt = T.sample_window_contexts(slices, 300, 31, window)
+    idx, rr, cc = synth.sample_positions(slices, 300, 31)
+    for n, (z, r, c) in enumerate(zip(idx, rr, cc)):
+        want = orc.gather_window3(window, slices[z - 1] if z else None, slices[z], int(r), int(c))
+        assert np.array_equal(ctx[n], want), (z, r, c)
+        assert tgt[n] == slices[z][r, c]
