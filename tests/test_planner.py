@@ -1,0 +1,69 @@
+"""The wavefront decoder's shared-memory planner (host code in decode_tc.cu),
+compiled with nvcc into a host program and run on the CPU: which prior store
+each case gets, and that every accepted plan fits the shared memory."""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+LIMIT = 232448 - 5120
+
+
+@pytest.fixture(scope="module")
+def plans():
+    if not (os.path.exists(NVCC) or shutil.which("nvcc")):
+        pytest.skip("nvcc is not available")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "planner_check")
+        cmd = [NVCC if os.path.exists(NVCC) else "nvcc", "-std=c++17", "--expt-relaxed-constexpr",
+               "-gencode", "arch=compute_103a,code=sm_103a", "-I", os.path.join(HERE, "..", "include"),
+               "-o", exe, os.path.join(HERE, "planner_check.cu")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    res = {}
+    for line in out.splitlines():
+        name, *v = line.split()
+        ok, nt, tq, gimg, ring_rows, list_rows, lut2, total = map(int, v)
+        res[name] = dict(ok=ok, nt=nt, tq=tq, gimg=gimg, ring_rows=ring_rows, list_rows=list_rows, lut2=lut2,
+                         total=total)
+    return res
+
+
+def test_accepted_plans_fit(plans):
+    for name, p in plans.items():
+        if p["ok"]:
+            assert 0 < p["total"] <= LIMIT, name
+
+
+def test_default_image_gets_the_tagged_ring(plans):
+    p = plans["int8_default_512"]
+    assert p["ok"] and p["tq"] > 0 and p["gimg"] == 0 and p["lut2"] == 1 and p["nt"] == 16
+
+
+def test_forced_plans(plans):
+    assert plans["int8_byte_ring_512"]["tq"] == 0 and plans["int8_byte_ring_512"]["gimg"] == 0
+    assert plans["int8_image_512"]["gimg"] == 1 and plans["int8_image_512"]["ring_rows"] == 0
+
+
+def test_big_fp32_window_drops_the_tagged_ring(plans):
+    # 78 inputs x 128 units of FP32 weights leave no room for the tagged ring
+    p = plans["fp32_fig6_512"]
+    assert p["ok"] and p["tq"] == 0 and p["gimg"] == 0
+
+
+def test_long_waves_read_the_image_and_longer_ones_are_refused(plans):
+    assert plans["int8_wide_4096x12288"]["ok"] and plans["int8_wide_4096x12288"]["gimg"] == 1
+    assert not plans["int8_huge_30000x90000"]["ok"]
+
+
+def test_volumes(plans):
+    p = plans["int8_volume_35x256"]
+    assert p["ok"] and p["gimg"] == 1 and p["tq"] == 0
+    # 35 slices can be active at once, each with ceil(86 / 16) rows of a CTA
+    assert p["list_rows"] >= 35 * 6
+    assert plans["grid_volume_128x512"]["ok"] and plans["grid_batch_64x1536x2048"]["ok"]
