@@ -78,5 +78,28 @@ int main() {
         show("grid_batch_64x1536x2048", ok, p, false);
         delete b;
     }
+    // the decode autotuner: cluster sizes for a few batches
+    {
+        const int H1[1] = {512}, W1[1] = {512};
+        int P1[1];
+        choose_clusters(H1, W1, 1, 152, false, P1);
+        printf("clusters single_512 %d\n", P1[0]);
+        int H64[64], W64[64], P64[64];
+        for (int i = 0; i < 64; i++) {
+            H64[i] = 192 + (i * 37) % 1345;
+            W64[i] = 256 + (i * 53) % 1793;
+        }
+        choose_clusters(H64, W64, 64, 152, false, P64);
+        printf("clusters batch64");
+        for (int i = 0; i < 64; i++) printf(" %d", P64[i]);
+        printf("\n");
+        int Ht[200], Wt[200], Pt[200];
+        for (int i = 0; i < 200; i++) {
+            Ht[i] = 16;
+            Wt[i] = 16;
+        }
+        choose_clusters(Ht, Wt, 200, 152, false, Pt);
+        printf("clusters tiny200 %d %d\n", Pt[0], Pt[199]);
+    }
     return 0;
 }

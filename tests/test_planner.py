@@ -28,6 +28,9 @@ def plans():
     res = {}
     for line in out.splitlines():
         name, *v = line.split()
+        if name == "clusters":
+            res["clusters_" + v[0]] = [int(x) for x in v[1:]]
+            continue
         ok, nt, tq, gimg, ring_rows, list_rows, lut2, total = map(int, v)
         res[name] = dict(ok=ok, nt=nt, tq=tq, gimg=gimg, ring_rows=ring_rows, list_rows=list_rows, lut2=lut2,
                          total=total)
@@ -36,7 +39,7 @@ def plans():
 
 def test_accepted_plans_fit(plans):
     for name, p in plans.items():
-        if p["ok"]:
+        if isinstance(p, dict) and p["ok"]:
             assert 0 < p["total"] <= LIMIT, name
 
 
@@ -67,3 +70,13 @@ def test_volumes(plans):
     # 35 slices can be active at once, each with ceil(86 / 16) rows of a CTA
     assert p["list_rows"] >= 35 * 6
     assert plans["grid_volume_128x512"]["ok"] and plans["grid_batch_64x1536x2048"]["ok"]
+
+
+def test_autotuner_cluster_sizes(plans):
+    # one image gets the largest cluster; a batch shares the SMs (power-of-two
+    # clusters of at most 16, at most one CTA per SM in all); tiny images that
+    # already fill the GPU keep one CTA each
+    assert plans["clusters_single_512"] == [16]
+    ps = plans["clusters_batch64"]
+    assert all(p in (1, 2, 4, 8, 16) for p in ps) and sum(ps) <= 152 and max(ps) > 1
+    assert plans["clusters_tiny200"] == [1, 1]
