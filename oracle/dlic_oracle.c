@@ -50,16 +50,19 @@
  * n3 = (pu + pd + 1)(pl + pr + 1). */
 typedef struct { int u, l, r, n2, pu, pd, pl, pr, n3, n, vol; } window_t;
 
+#define MAXLAYERS 9            /* up to 8 hidden layers and the output layer */
+
 typedef struct {
     int precision;               /* 0 = FP32, 1 = INT8 */
     window_t win;
     int h1, h2;
+    int nl;                      /* dense layers: hidden layers + the output layer */
     float tscale;
     uint32_t lut[64];
-    float *w[3], *b[3];          /* FP32 network: W[l] is out x in, row-major */
-    int8_t *q[3];                /* INT8 network weights, out x in */
-    float *s[3], *o[3];          /* INT8 per-output scale and offset */
-    int n_in[3], n_out[3];
+    float *w[MAXLAYERS], *b[MAXLAYERS];   /* FP32 network: W[l] is out x in, row-major */
+    int8_t *q[MAXLAYERS];                 /* INT8 network weights, out x in */
+    float *s[MAXLAYERS], *o[MAXLAYERS];   /* INT8 per-output scale and offset */
+    int n_in[MAXLAYERS], n_out[MAXLAYERS];
     uint64_t hash;
 } model_t;
 
@@ -85,17 +88,56 @@ uint64_t or_fnv1a64(const uint8_t *p, size_t n) {
 }
 
 static void model_free(model_t *m) {
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < MAXLAYERS; l++) {
         free(m->w[l]); free(m->b[l]); free(m->q[l]); free(m->s[l]); free(m->o[l]);
     }
 }
 
+/* Two layouts (little-endian):
+ *   "DLM1": u32 precision, n_in, h1, h2, n_out (256), window, f32 tscale,
+ *           u32 lut[64], then 3 dense layers (288-byte header);
+ *   "DLM2" (deeper networks, Sec. II-B: six dense layers): u32 precision,
+ *           n_in, L (hidden layers, 1..8), widths[8] (hidden widths, unused
+ *           entries 0), n_out (256), window, f32 tscale, u32 0, u32 lut[64],
+ *           then L + 1 dense layers (320-byte header).
+ * Each dense layer: FP32 W f32[out][in], b f32[out]; INT8 W i8[out][in],
+ * s f32[out], o f32[out]. */
 static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     memset(m, 0, sizeof(*m));
-    if (n < 288 || memcmp(blob, "DLM1", 4) != 0) return OR_ERR_INVALID;
+    int deep = 0;
+    uint32_t widths[MAXLAYERS] = {0};
+    if (n >= 320 && memcmp(blob, "DLM2", 4) == 0) {
+        deep = 1;
+    } else if (n < 288 || memcmp(blob, "DLM1", 4) != 0) {
+        return OR_ERR_INVALID;
+    }
     m->precision = (int)rd_u32(blob + 4);
-    uint32_t n_in = rd_u32(blob + 8), h1 = rd_u32(blob + 12), h2 = rd_u32(blob + 16);
-    uint32_t n_out = rd_u32(blob + 20), radius = rd_u32(blob + 24);
+    uint32_t n_in = rd_u32(blob + 8), h1, h2, n_out, radius;
+    const uint8_t *pre;   /* tscale, then (after any padding) the lut */
+    if (deep) {
+        uint32_t L = rd_u32(blob + 12);
+        if (L < 1 || L > MAXLAYERS - 1) return OR_ERR_INVALID;
+        for (uint32_t l = 0; l < 8; l++) {
+            widths[l] = rd_u32(blob + 16 + 4 * l);
+            if ((l < L) != (widths[l] != 0)) return OR_ERR_INVALID;
+            if (l < L && widths[l] > 4096) return OR_ERR_INVALID;
+        }
+        m->nl = (int)L + 1;
+        n_out = rd_u32(blob + 48);
+        radius = rd_u32(blob + 52);
+        h1 = widths[0];
+        h2 = widths[L - 1];
+        pre = blob + 56;
+    } else {
+        h1 = rd_u32(blob + 12);
+        h2 = rd_u32(blob + 16);
+        n_out = rd_u32(blob + 20);
+        radius = rd_u32(blob + 24);
+        widths[0] = h1;
+        widths[1] = h2;
+        m->nl = 3;
+        pre = blob + 28;
+    }
     if (m->precision != 0 && m->precision != 1) return OR_ERR_INVALID;
     /* window field: 2 = the default radius-2 window; otherwise
      * 1 << 24 | u | l << 8 | r << 16 with 1 <= u <= 8, l <= 8 and r <= 2
@@ -123,22 +165,27 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     if (m->win.n > MAXPRI || (int)n_in != m->win.n || n_out != NSYM) return OR_ERR_INVALID;
     if (h1 < 1 || h1 > 4096 || h2 < 1 || h2 > 4096) return OR_ERR_INVALID;
     m->h1 = (int)h1; m->h2 = (int)h2;
-    m->tscale = rd_f32(blob + 28);
+    m->tscale = rd_f32(pre);
     if (!(m->tscale > 0.0f)) return OR_ERR_INVALID;
+    const uint8_t *lutp = deep ? blob + 64 : blob + 32;
     for (int k = 0; k < 64; k++) {
-        m->lut[k] = rd_u32(blob + 32 + 4 * k);
+        m->lut[k] = rd_u32(lutp + 4 * k);
         if (m->lut[k] > (1u << 23)) return OR_ERR_INVALID;
     }
     if (m->lut[0] != (1u << 23)) return OR_ERR_INVALID;
-    int dims_in[3] = {m->win.n, (int)h1, (int)h2}, dims_out[3] = {(int)h1, (int)h2, NSYM};
-    size_t need = 288;
-    for (int l = 0; l < 3; l++) {
+    int dims_in[MAXLAYERS], dims_out[MAXLAYERS];
+    for (int l = 0; l < m->nl; l++) {
+        dims_in[l] = l == 0 ? m->win.n : (int)widths[l - 1];
+        dims_out[l] = l == m->nl - 1 ? NSYM : (int)widths[l];
+    }
+    size_t need = deep ? 320 : 288;
+    for (int l = 0; l < m->nl; l++) {
         size_t wn = (size_t)dims_in[l] * dims_out[l];
         need += m->precision == 0 ? 4 * wn + 4 * (size_t)dims_out[l] : wn + 8 * (size_t)dims_out[l];
     }
     if (need != n) return OR_ERR_INVALID;
-    const uint8_t *p = blob + 288;
-    for (int l = 0; l < 3; l++) {
+    const uint8_t *p = blob + (deep ? 320 : 288);
+    for (int l = 0; l < m->nl; l++) {
         int ni = dims_in[l], no = dims_out[l];
         m->n_in[l] = ni; m->n_out[l] = no;
         size_t wn = (size_t)ni * no;
@@ -238,12 +285,12 @@ static void mlp_fp32(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     float a[4096], b[4096];
     for (int k = 0; k < m->win.n; k++) a[k] = fmaf((float)pri[k], 0.0078125f, -1.0f);
     float *in = a, *out = b;
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < m->nl; l++) {
         int ni = m->n_in[l], no = m->n_out[l];
         for (int j = 0; j < no; j++) {
             float acc = m->b[l][j];
             for (int k = 0; k < ni; k++) acc = fmaf(in[k], m->w[l][(size_t)j * ni + k], acc);
-            if (l < 2) acc = acc > 0.0f ? acc : 0.0f;
+            if (l < m->nl - 1) acc = acc > 0.0f ? acc : 0.0f;
             out[j] = acc;
         }
         float *t = in; in = out; out = t;
@@ -262,12 +309,12 @@ static void mlp_int8(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     int32_t a[4096], b[4096];
     for (int k = 0; k < m->win.n; k++) a[k] = (int32_t)pri[k] - 128;
     int32_t *in = a, *out = b;
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < m->nl; l++) {
         int ni = m->n_in[l], no = m->n_out[l];
         for (int j = 0; j < no; j++) {
             int32_t acc = 0;
             for (int k = 0; k < ni; k++) acc += (int32_t)m->q[l][(size_t)j * ni + k] * in[k];
-            if (l < 2)
+            if (l < m->nl - 1)
                 out[j] = (int32_t)requant_u8(acc, m->s[l][j], m->o[l][j]);
             else
                 z[j] = fmaf((float)acc, m->s[l][j], m->o[l][j]);

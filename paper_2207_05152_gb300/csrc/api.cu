@@ -71,6 +71,10 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     if (!h_blob || !out) return fail(DLIC_ERR_INVALID, "null argument");
     *out = nullptr;
     const uint8_t *b = static_cast<const uint8_t *>(h_blob);
+    // deeper networks ("DLM2": up to 8 hidden layers) are defined by the model
+    // format but have no GPU kernels in this build
+    if (n >= 4 && memcmp(b, "DLM2", 4) == 0)
+        return fail(DLIC_ERR_UNSUPPORTED, "networks of more than two hidden layers have no GPU kernels in this build");
     if (n < 288 || memcmp(b, "DLM1", 4) != 0) return fail(DLIC_ERR_INVALID, "not a DLIC model blob");
     const uint32_t prec = le32(b + 4), n_in = le32(b + 8), h1 = le32(b + 12), h2 = le32(b + 16),
                    n_out = le32(b + 20), radius = le32(b + 24);

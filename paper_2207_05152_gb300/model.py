@@ -179,10 +179,32 @@ def _forward_fp32(layers, ctx_u8):
     acts = []
     for li, (w, b) in enumerate(layers):
         x = x @ w.astype(np.float64).T + b.astype(np.float64)
-        if li < 2:
+        if li < len(layers) - 1:
             x = np.maximum(x, 0.0)
             acts.append(x)
     return acts, x
+
+
+def _quantise(layers, calib_ctx):
+    """Per-layer (Wq, s, o) of the post-training quantisation (any depth)."""
+    acts, _ = _forward_fp32(layers, np.asarray(calib_ctx, dtype=np.uint8))
+    act_scale = [max(float(a.max()), 1e-6) / 255.0 for a in acts]
+    in_scale = [1.0 / 128.0] + act_scale
+    out = []
+    for li, (w, b) in enumerate(layers):
+        w = w.astype(np.float64)
+        b = b.astype(np.float64)
+        sw = np.abs(w).max(axis=1) / 127.0
+        sw[sw == 0] = 1.0
+        wq = np.clip(np.rint(w / sw[:, None]), -127, 127).astype(np.int8)
+        if li < len(layers) - 1:
+            s = sw * in_scale[li] / act_scale[li]
+            o = b / act_scale[li]
+        else:
+            s = sw * in_scale[li]
+            o = b
+        out.append((wq, s, o))
+    return out
 
 
 def int8_blob(layers, calib_ctx: np.ndarray, window=DEFAULT_WINDOW) -> bytes:
@@ -193,22 +215,63 @@ def int8_blob(layers, calib_ctx: np.ndarray, window=DEFAULT_WINDOW) -> bytes:
     max(h) / 255 over the calibration contexts (u8 array [N, window size]).
     Inputs: v - 128 with scale 1/128."""
     h1, h2 = _check_widths(layers, window)
-    acts, _ = _forward_fp32(layers, np.asarray(calib_ctx, dtype=np.uint8))
-    act_scale = [max(float(a.max()), 1e-6) / 255.0 for a in acts]
-    in_scale = [1.0 / 128.0, act_scale[0], act_scale[1]]
     out = [_header(PREC_INT8, h1, h2, window)]
+    for wq, s, o in _quantise(layers, calib_ctx):
+        out.append(wq.tobytes())
+        out.append(s.astype("<f4").tobytes())
+        out.append(o.astype("<f4").tobytes())
+    return b"".join(out)
+
+
+# --- deeper networks (Sec. II-B "Neural Network Architecture": six dense
+# layers): the "DLM2" blob, L hidden layers of any widths up to 4096 ---
+DEEP_MAGIC = b"DLM2"
+DEEP_HEADER_BYTES = 320
+MAX_HIDDEN_LAYERS = 8
+
+
+def _deep_header(precision: int, widths, window) -> bytes:
+    L = len(widths)
+    hdr = DEEP_MAGIC + struct.pack("<3I", precision, window_size(window), L)
+    hdr += struct.pack("<8I", *(list(widths) + [0] * (MAX_HIDDEN_LAYERS - L)))
+    hdr += struct.pack("<2IfI", N_OUT, window_field(window), float(TSCALE), 0)
+    hdr += table_lut().astype("<u4").tobytes()
+    assert len(hdr) == DEEP_HEADER_BYTES
+    return hdr
+
+
+def _check_deep(layers, window):
+    if not 2 <= len(layers) <= MAX_HIDDEN_LAYERS + 1:
+        raise ValueError("a deep network has 1 to 8 hidden layers and the output layer")
+    widths, n = [], window_size(window)
     for li, (w, b) in enumerate(layers):
-        w = w.astype(np.float64)
-        b = b.astype(np.float64)
-        sw = np.abs(w).max(axis=1) / 127.0
-        sw[sw == 0] = 1.0
-        wq = np.clip(np.rint(w / sw[:, None]), -127, 127).astype(np.int8)
-        if li < 2:
-            s = sw * in_scale[li] / act_scale[li]
-            o = b / act_scale[li]
-        else:
-            s = sw * in_scale[li]
-            o = b
+        if w.ndim != 2 or w.shape[1] != n or b.shape != (w.shape[0],):
+            raise ValueError(f"layer {li}: shape {w.shape} does not chain from {n} inputs")
+        n = w.shape[0]
+        if li < len(layers) - 1:
+            if not 1 <= n <= 4096:
+                raise ValueError("hidden widths must be in [1, 4096]")
+            widths.append(n)
+    if n != N_OUT:
+        raise ValueError("the output layer has 256 units")
+    return widths
+
+
+def deep_fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
+    """"DLM2" blob of an FP32 network [(W1, b1), ..., (W_out, b_out)] of
+    1..8 hidden layers."""
+    out = [_deep_header(PREC_FP32, _check_deep(layers, window), window)]
+    for w, b in layers:
+        out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
+        out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
+    return b"".join(out)
+
+
+def deep_int8_blob(layers, calib_ctx: np.ndarray, window=DEFAULT_WINDOW) -> bytes:
+    """"DLM2" blob of the INT8 quantisation (the rules of int8_blob) of a
+    network of 1..8 hidden layers."""
+    out = [_deep_header(PREC_INT8, _check_deep(layers, window), window)]
+    for wq, s, o in _quantise(layers, calib_ctx):
         out.append(wq.tobytes())
         out.append(s.astype("<f4").tobytes())
         out.append(o.astype("<f4").tobytes())

@@ -3,6 +3,7 @@ include/dlic.h declares; host-side argument checks run without a device."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,3 +76,14 @@ def test_window_contexts_match_the_default_sampler():
     a, ta = T.sample_contexts(imgs, 500, 3)
     b, tb = T.sample_window_contexts(imgs, 500, 3, (2, 2, 2))
     assert np.array_equal(a, b) and np.array_equal(ta, tb)
+
+
+def test_deeper_networks_are_refused_before_any_device_call(lib):
+    # a valid "DLM2" blob (three hidden layers): the GPU kernels cover two
+    import synth
+    from paper_2207_05152_gb300 import model as M
+    layers = synth.predictive_mlp([12, 32, 32, 256], 5)
+    deep = layers[:-1] + [(np.eye(32, dtype=np.float32), np.zeros(32, np.float32))] + layers[-1:]
+    with pytest.raises(lib.DlicError) as e:
+        lib.dlic_model_create(M.deep_fp32_blob(deep))
+    assert e.value.code == lib.DLIC_ERR_UNSUPPORTED
