@@ -107,8 +107,18 @@ DLIC_API const char *dlic_last_error(void);
  * than the default need the tensor-core INT8 kernels (h1, h2 <= 128 to
  * encode, h1 = h2 = 128 to decode) or the FP32 tiled kernels (h2 <= 128)
  * (DLIC_ERR_UNSUPPORTED otherwise).
- * h1 and h2 must be multiples of 16 in [16, 256].  The blob is copied; the
- * model owns device copies of the weights in the layouts the kernels use.
+ * h1 and h2 must be multiples of 16 in [16, 256].
+ * Networks of other depths (Sec. II-B: the paper's network has six dense
+ * layers) come as
+ *   "DLM2", u32 precision, u32 n_in, u32 L (hidden layers, 1..8),
+ *   u32 widths[8] (the L hidden widths, then zeros), u32 256, u32 window,
+ *   f32 tscale, u32 0, u32 lut[64], then the L + 1 dense layers as above.
+ * With L = 2 it is the same network as the "DLM1" blob and runs the same
+ * kernels.  Other L run on the CUDA-core one-pixel-per-thread encoder and
+ * decoder, with the default window only and hidden widths that are
+ * multiples of 4 in [4, 256] (DLIC_ERR_UNSUPPORTED otherwise).
+ * The blob is copied; the model owns device copies of the weights in the
+ * layouts the kernels use.
  * The model hash (FNV-1a 64 of the blob) is written into every bitstream and
  * checked by the decoder.  Returns DLIC_ERR_INVALID for a malformed blob. */
 DLIC_API dlic_status dlic_model_create(const void *h_blob, size_t blob_bytes, dlic_model **out);
@@ -142,7 +152,7 @@ DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
 enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2, DLIC_PLAN_GRID = 3 };
 DLIC_API dlic_status dlic_model_set_decode_plan(dlic_model *model, int plan);
 
-/* Precision tag, hidden widths and hash of a model. */
+/* Precision tag, first and last hidden widths and hash of a model. */
 DLIC_API dlic_status dlic_model_info(const dlic_model *model, int *precision, int *h1, int *h2,
                             uint64_t *hash);
 

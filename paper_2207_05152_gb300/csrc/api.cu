@@ -71,13 +71,36 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     if (!h_blob || !out) return fail(DLIC_ERR_INVALID, "null argument");
     *out = nullptr;
     const uint8_t *b = static_cast<const uint8_t *>(h_blob);
-    // deeper networks ("DLM2": up to 8 hidden layers) are defined by the model
-    // format but have no GPU kernels in this build
-    if (n >= 4 && memcmp(b, "DLM2", 4) == 0)
-        return fail(DLIC_ERR_UNSUPPORTED, "networks of more than two hidden layers have no GPU kernels in this build");
-    if (n < 288 || memcmp(b, "DLM1", 4) != 0) return fail(DLIC_ERR_INVALID, "not a DLIC model blob");
-    const uint32_t prec = le32(b + 4), n_in = le32(b + 8), h1 = le32(b + 12), h2 = le32(b + 16),
-                   n_out = le32(b + 20), radius = le32(b + 24);
+    // "DLM1": two hidden layers, 288-byte header (u32 precision, n_in, h1,
+    // h2, n_out, window, f32 tscale, u32 lut[64]).  "DLM2": 1..8 hidden
+    // layers, 320-byte header (u32 precision, n_in, L, widths[8], n_out,
+    // window, f32 tscale, u32 0, u32 lut[64]).  Then the dense layers.
+    const bool dlm2 = n >= 320 && memcmp(b, "DLM2", 4) == 0;
+    if (!dlm2 && (n < 288 || memcmp(b, "DLM1", 4) != 0)) return fail(DLIC_ERR_INVALID, "not a DLIC model blob");
+    const uint32_t prec = le32(b + 4), n_in = le32(b + 8);
+    uint32_t widths[kMaxLayers - 1] = {0}, n_out, radius;
+    int L = 2;
+    size_t hdr = 288, tscale_at = 28, lut_at = 32;
+    if (dlm2) {
+        L = (int)le32(b + 12);
+        if (L < 1 || L > kMaxLayers - 1) return fail(DLIC_ERR_INVALID, "a network has 1..%d hidden layers", kMaxLayers - 1);
+        for (int l = 0; l < kMaxLayers - 1; l++) {
+            widths[l] = le32(b + 16 + 4 * l);
+            if ((l < L) != (widths[l] != 0)) return fail(DLIC_ERR_INVALID, "exactly the first %d hidden widths are nonzero", L);
+        }
+        n_out = le32(b + 48);
+        radius = le32(b + 52);
+        hdr = 320;
+        tscale_at = 56;
+        lut_at = 64;
+    } else {
+        widths[0] = le32(b + 12);
+        widths[1] = le32(b + 16);
+        n_out = le32(b + 20);
+        radius = le32(b + 24);
+    }
+    const uint32_t h1 = widths[0], h2 = widths[L - 1];
+    const bool deep = L != 2;   // the layer-table kernels
     if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
     // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16,
     // or a 3D window 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 | pl << 18 | pr << 22
@@ -108,20 +131,37 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     const int npri = n2 + (vol ? (pu + pd + 1) * (pl + pr + 1) : 0);
     if (npri > kMaxPriors || (int)n_in != npri || n_out != kSymbols)
         return fail(DLIC_ERR_INVALID, "model must map the %d priors of its window to 256 logits", npri);
-    if (h1 < 16 || h1 > kMaxHidden || h1 % 16 || h2 < 16 || h2 > kMaxHidden || h2 % 16)
-        return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
-    const float tscale = lef32(b + 28);
+    for (int l = 0; l < L; l++)
+        if (widths[l] > 4096) return fail(DLIC_ERR_INVALID, "hidden widths must be <= 4096");
+    if (!deep) {
+        if (h1 < 16 || h1 > kMaxHidden || h1 % 16 || h2 < 16 || h2 > kMaxHidden || h2 % 16)
+            return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
+    } else {
+        for (int l = 0; l < L; l++)
+            if (widths[l] < 4 || widths[l] > kMaxHidden || widths[l] % 4)
+                return fail(DLIC_ERR_UNSUPPORTED, "hidden widths of a network of %d hidden layers must be multiples "
+                            "of 4 in [4, 256]", L);
+        if (radius != 2)
+            return fail(DLIC_ERR_UNSUPPORTED, "networks of other than two hidden layers run with the default window only");
+    }
+    const float tscale = lef32(b + tscale_at);
     if (!(tscale > 0.0f)) return fail(DLIC_ERR_INVALID, "tscale must be positive");
     uint32_t lut[64];
     for (int k = 0; k < 64; k++) {
-        lut[k] = le32(b + 32 + 4 * k);
+        lut[k] = le32(b + lut_at + 4 * k);
         if (lut[k] > (1u << 23)) return fail(DLIC_ERR_INVALID, "lut entries must be <= 2^23");
     }
     if (lut[0] != (1u << 23)) return fail(DLIC_ERR_INVALID, "lut[0] must be 2^23");
-    const int din[3] = {npri, (int)h1, (int)h2}, dout[3] = {(int)h1, (int)h2, kSymbols};
+    const int nl = L + 1;
+    int din[kMaxLayers], dout[kMaxLayers], hmax = 0;
+    for (int l = 0; l < nl; l++) {
+        din[l] = l == 0 ? npri : (int)widths[l - 1];
+        dout[l] = l == nl - 1 ? kSymbols : (int)widths[l];
+        if (l < L) hmax = std::max(hmax, (int)widths[l]);
+    }
     const int k1 = (npri + 15) / 16 * 16;   // first-layer K of the tensor-core operands
-    size_t need = 288;
-    for (int l = 0; l < 3; l++)
+    size_t need = hdr;
+    for (int l = 0; l < nl; l++)
         need += prec == 0 ? 4ull * din[l] * dout[l] + 4ull * dout[l] : (size_t)din[l] * dout[l] + 8ull * dout[l];
     if (need != n) return fail(DLIC_ERR_INVALID, "blob size %zu does not match its header (%zu)", n, need);
 
@@ -137,6 +177,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.precision = (int)prec;
     d.h1 = (int)h1;
     d.h2 = (int)h2;
+    d.nl = nl;
+    d.hmax = hmax;
     d.wu = wu;
     d.wl = wl;
     d.wr = wr;
@@ -150,33 +192,37 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.tscale = tscale;
     d.hash = fnv1a64(b, n);
     size_t off_lut = put(lut, sizeof(lut));
-    size_t offs[16] = {0};
-    const uint8_t *p = b + 288;
+    // offs[3 l .. 3 l + 2]: layer l's weights and its bias (FP32) or scale
+    // and offset (INT8); offs[3 kMaxLayers]: the tensor-core operand image
+    size_t offs[3 * kMaxLayers + 1] = {0};
+    const int kTcImage = 3 * kMaxLayers;
+    const size_t off_table = deep ? put(std::vector<DevLayer>(nl).data(), sizeof(DevLayer) * nl) : 0;
+    const uint8_t *p = b + hdr;
     if (prec == DLIC_FP32) {
-        for (int l = 0; l < 3; l++) {
+        for (int l = 0; l < nl; l++) {
             std::vector<float> wt((size_t)din[l] * dout[l]), bias(dout[l]);
             for (int j = 0; j < dout[l]; j++)
                 for (int k = 0; k < din[l]; k++) wt[(size_t)k * dout[l] + j] = lef32(p + 4 * ((size_t)j * din[l] + k));
             p += 4ull * din[l] * dout[l];
             for (int j = 0; j < dout[l]; j++) bias[j] = lef32(p + 4 * j);
             p += 4ull * dout[l];
-            offs[2 * l] = put(wt.data(), wt.size() * 4);
-            offs[2 * l + 1] = put(bias.data(), bias.size() * 4);
+            offs[3 * l] = put(wt.data(), wt.size() * 4);
+            offs[3 * l + 1] = put(bias.data(), bias.size() * 4);
         }
     } else {
-        const int8_t *raw[3];
+        const int8_t *raw[kMaxLayers];
         const uint8_t *pp = p;
-        for (int l = 0; l < 3; l++) {
+        for (int l = 0; l < nl; l++) {
             raw[l] = reinterpret_cast<const int8_t *>(pp);
             pp += (size_t)din[l] * dout[l] + 8ull * dout[l];
         }
-        if (h1 <= 128 && h2 <= 128) {
+        if (!deep && h1 <= 128 && h2 <= 128) {
             std::vector<uint16_t> img(tc_weight_bytes((int)h1, (int)h2, k1) / 2);
             tc_pack_weights((int)h1, (int)h2, npri, k1, raw[0], raw[1], raw[2], img.data());
-            offs[15] = put(img.data(), img.size() * 2);
+            offs[kTcImage] = put(img.data(), img.size() * 2);
             d.tc_w_bytes = (uint32_t)(img.size() * 2);
         }
-        for (int l = 0; l < 3; l++) {
+        for (int l = 0; l < nl; l++) {
             const int k4n = (din[l] + 3) / 4;
             std::vector<uint32_t> qt((size_t)k4n * dout[l], 0u);
             for (int j = 0; j < dout[l]; j++)
@@ -203,6 +249,20 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         delete m;
         return cuda_fail(e, "cudaMalloc(model)");
     }
+    uint8_t *base = static_cast<uint8_t *>(m->mem);
+    if (deep) {
+        // the layer table holds device addresses: written once they are known
+        std::vector<DevLayer> table(nl);
+        for (int l = 0; l < nl; l++) {
+            table[l].w = base + offs[3 * l];
+            table[l].a = reinterpret_cast<const float *>(base + offs[3 * l + 1]);
+            table[l].o = prec == DLIC_INT8 ? reinterpret_cast<const float *>(base + offs[3 * l + 2]) : nullptr;
+            table[l].n_in = din[l];
+            table[l].n_out = dout[l];
+        }
+        memcpy(host.data() + off_table, table.data(), sizeof(DevLayer) * nl);
+        d.layers = reinterpret_cast<const DevLayer *>(base + off_table);
+    }
     e = cudaMemcpy(m->mem, host.data(), host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(m->mem);
@@ -218,15 +278,16 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         dlic_model_destroy(m);
         return cuda_fail(e, "stream / event creation");
     }
-    uint8_t *base = static_cast<uint8_t *>(m->mem);
     d.lut = reinterpret_cast<const uint32_t *>(base + off_lut);
-    if (prec == DLIC_FP32) {
+    if (deep) {
+        // the kernels read the layer table only
+    } else if (prec == DLIC_FP32) {
         d.w1t = reinterpret_cast<const float *>(base + offs[0]);
         d.b1 = reinterpret_cast<const float *>(base + offs[1]);
-        d.w2t = reinterpret_cast<const float *>(base + offs[2]);
-        d.b2 = reinterpret_cast<const float *>(base + offs[3]);
-        d.w3t = reinterpret_cast<const float *>(base + offs[4]);
-        d.b3 = reinterpret_cast<const float *>(base + offs[5]);
+        d.w2t = reinterpret_cast<const float *>(base + offs[3]);
+        d.b2 = reinterpret_cast<const float *>(base + offs[4]);
+        d.w3t = reinterpret_cast<const float *>(base + offs[6]);
+        d.b3 = reinterpret_cast<const float *>(base + offs[7]);
     } else {
         d.q1t = reinterpret_cast<const uint32_t *>(base + offs[0]);
         d.s1 = reinterpret_cast<const float *>(base + offs[1]);
@@ -237,7 +298,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         d.q3t = reinterpret_cast<const uint32_t *>(base + offs[6]);
         d.s3 = reinterpret_cast<const float *>(base + offs[7]);
         d.o3 = reinterpret_cast<const float *>(base + offs[8]);
-        if (d.tc_w_bytes) d.tc_w = reinterpret_cast<const uint16_t *>(base + offs[15]);
+        if (d.tc_w_bytes) d.tc_w = reinterpret_cast<const uint16_t *>(base + offs[kTcImage]);
     }
     m->dev = d;
     if (!default_window(d)) {

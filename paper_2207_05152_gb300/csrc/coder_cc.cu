@@ -44,10 +44,153 @@ __host__ __device__ inline size_t hidden_bytes(int h) {
 }
 
 // ---------------------------------------------------------------------------
+// Networks of other than two hidden layers (Sec. II-B "Neural Network
+// Architecture": six dense layers), one pixel per thread, from the model's
+// layer table.  The same arithmetic as the fixed-depth helpers: FP32 units
+// start from the bias and accumulate fma(x_k, w_jk, acc) for k ascending,
+// then ReLU; INT8 units are exact dp4a dot products, requantised to u8.
+// Hidden layer l of L writes shared buffer B when L - 1 - l is even, else A,
+// so that the last hidden layer is always in B.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8_t *A, uint8_t *B, int tid) {
+    const int L = m.nl - 1;
+    for (int l = 0; l < L; l++) {
+        const DevLayer ly = m.layers[l];
+        uint8_t *out = ((L - 1 - l) & 1) ? A : B;
+        const uint8_t *in = ((L - l) & 1) ? A : B;   // written by layer l - 1
+        if constexpr (PREC == DLIC_FP32) {
+            const float *wt = static_cast<const float *>(ly.w);
+            const float *xs = reinterpret_cast<const float *>(in);
+            float *os = reinterpret_cast<float *>(out);
+            float x0[kPriors];
+#pragma unroll
+            for (int k = 0; k < kPriors; k++) x0[k] = __fmaf_rn((float)pri[k], 0.0078125f, -1.0f);
+            for (int j0 = 0; j0 < ly.n_out; j0 += 4) {
+                float a0 = __ldg(ly.a + j0), a1 = __ldg(ly.a + j0 + 1), a2 = __ldg(ly.a + j0 + 2),
+                      a3 = __ldg(ly.a + j0 + 3);
+                if (l == 0) {   // n_in = kPriors (the default window)
+#pragma unroll
+                    for (int k = 0; k < kPriors; k++) {
+                        const float4 w = __ldg(reinterpret_cast<const float4 *>(wt + (size_t)k * ly.n_out + j0));
+                        a0 = __fmaf_rn(x0[k], w.x, a0);
+                        a1 = __fmaf_rn(x0[k], w.y, a1);
+                        a2 = __fmaf_rn(x0[k], w.z, a2);
+                        a3 = __fmaf_rn(x0[k], w.w, a3);
+                    }
+                } else {
+                    for (int k = 0; k < ly.n_in; k++) {
+                        const float xk = xs[k * kCH + tid];
+                        const float4 w = __ldg(reinterpret_cast<const float4 *>(wt + (size_t)k * ly.n_out + j0));
+                        a0 = __fmaf_rn(xk, w.x, a0);
+                        a1 = __fmaf_rn(xk, w.y, a1);
+                        a2 = __fmaf_rn(xk, w.z, a2);
+                        a3 = __fmaf_rn(xk, w.w, a3);
+                    }
+                }
+                os[(j0 + 0) * kCH + tid] = a0 > 0.0f ? a0 : 0.0f;
+                os[(j0 + 1) * kCH + tid] = a1 > 0.0f ? a1 : 0.0f;
+                os[(j0 + 2) * kCH + tid] = a2 > 0.0f ? a2 : 0.0f;
+                os[(j0 + 3) * kCH + tid] = a3 > 0.0f ? a3 : 0.0f;
+            }
+        } else {
+            const uint32_t *wq = static_cast<const uint32_t *>(ly.w);
+            const uint32_t *xs = reinterpret_cast<const uint32_t *>(in);
+            uint32_t *os = reinterpret_cast<uint32_t *>(out);
+            uint32_t x0[kPriors / 4];   // priors v - 128 as signed bytes
+#pragma unroll
+            for (int k4 = 0; k4 < kPriors / 4; k4++)
+                x0[k4] = (uint32_t)(uint8_t)(pri[4 * k4] ^ 0x80) | ((uint32_t)(uint8_t)(pri[4 * k4 + 1] ^ 0x80) << 8) |
+                         ((uint32_t)(uint8_t)(pri[4 * k4 + 2] ^ 0x80) << 16) |
+                         ((uint32_t)(uint8_t)(pri[4 * k4 + 3] ^ 0x80) << 24);
+            const int k4n = ly.n_in >> 2;
+            for (int j0 = 0; j0 < ly.n_out; j0 += 4) {
+                int a[4] = {0, 0, 0, 0};
+                if (l == 0) {   // n_in = kPriors: signed inputs
+#pragma unroll
+                    for (int k4 = 0; k4 < kPriors / 4; k4++) {
+                        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(wq + (size_t)k4 * ly.n_out + j0));
+                        a[0] = dp4a_ss(x0[k4], w.x, a[0]);
+                        a[1] = dp4a_ss(x0[k4], w.y, a[1]);
+                        a[2] = dp4a_ss(x0[k4], w.z, a[2]);
+                        a[3] = dp4a_ss(x0[k4], w.w, a[3]);
+                    }
+                } else {        // u8 hidden units
+                    for (int k4 = 0; k4 < k4n; k4++) {
+                        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(wq + (size_t)k4 * ly.n_out + j0));
+                        const uint32_t xk = xs[k4 * kCH + tid];
+                        a[0] = dp4a_us(xk, w.x, a[0]);
+                        a[1] = dp4a_us(xk, w.y, a[1]);
+                        a[2] = dp4a_us(xk, w.z, a[2]);
+                        a[3] = dp4a_us(xk, w.w, a[3]);
+                    }
+                }
+                uint32_t packed = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    packed |= requant_u8(a[q], __ldg(ly.a + j0 + q), __ldg(ly.o + j0 + q)) << (8 * q);
+                os[(j0 >> 2) * kCH + tid] = packed;
+            }
+        }
+    }
+}
+
+// Logits j0 .. j0 + 3 of the output layer from the last hidden layer (in B).
+template <int PREC>
+__device__ __forceinline__ void deep_logits4(const DevModel &m, const uint8_t *B, int tid, int j0, float z[4]) {
+    const DevLayer ly = m.layers[m.nl - 1];
+    if constexpr (PREC == DLIC_FP32) {
+        const float *wt = static_cast<const float *>(ly.w);
+        const float *xs = reinterpret_cast<const float *>(B);
+        float a0 = __ldg(ly.a + j0), a1 = __ldg(ly.a + j0 + 1), a2 = __ldg(ly.a + j0 + 2), a3 = __ldg(ly.a + j0 + 3);
+        for (int k = 0; k < ly.n_in; k++) {
+            const float xk = xs[k * kCH + tid];
+            const float4 w = __ldg(reinterpret_cast<const float4 *>(wt + (size_t)k * kSymbols + j0));
+            a0 = __fmaf_rn(xk, w.x, a0);
+            a1 = __fmaf_rn(xk, w.y, a1);
+            a2 = __fmaf_rn(xk, w.z, a2);
+            a3 = __fmaf_rn(xk, w.w, a3);
+        }
+        z[0] = a0; z[1] = a1; z[2] = a2; z[3] = a3;
+    } else {
+        const uint32_t *wq = static_cast<const uint32_t *>(ly.w);
+        const uint32_t *xs = reinterpret_cast<const uint32_t *>(B);
+        int a[4] = {0, 0, 0, 0};
+        for (int k4 = 0; k4 < (ly.n_in >> 2); k4++) {
+            const uint32_t xk = xs[k4 * kCH + tid];
+            const uint4 w = __ldg(reinterpret_cast<const uint4 *>(wq + (size_t)k4 * kSymbols + j0));
+            a[0] = dp4a_us(xk, w.x, a[0]);
+            a[1] = dp4a_us(xk, w.y, a[1]);
+            a[2] = dp4a_us(xk, w.z, a[2]);
+            a[3] = dp4a_us(xk, w.w, a[3]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) z[q] = __fmaf_rn(__int2float_rn(a[q]), __ldg(ly.a + j0 + q), __ldg(ly.o + j0 + q));
+    }
+}
+
+// Hidden layers and logits of either network depth: the fixed-depth helpers
+// for two hidden layers, the layer table otherwise.
+template <int PREC, bool DEEP>
+__device__ __forceinline__ void net_hidden(const DevModel &m, const uint8_t *pri, uint8_t *A, uint8_t *B, int tid) {
+    if constexpr (DEEP)
+        deep_hidden<PREC>(m, pri, A, B, tid);
+    else
+        hidden<PREC>(m, pri, A, B, tid);
+}
+template <int PREC, bool DEEP>
+__device__ __forceinline__ void net_logits4(const DevModel &m, const uint8_t *B, int tid, int j0, float z[4]) {
+    if constexpr (DEEP)
+        deep_logits4<PREC>(m, B, tid, j0, z);
+    else
+        logits4<PREC>(m, B, tid, j0, z);
+}
+
+// ---------------------------------------------------------------------------
 // Encoder prediction: every pixel of every image at once (the encoder knows
 // all priors).  Writes (f, c) of the pixel's own value as f | c << 16.
 // ---------------------------------------------------------------------------
-template <int PREC>
+template <int PREC, bool DEEP>
 __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut_s[64];
@@ -65,14 +208,14 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
 
     uint8_t pri[kPriors];
     gather_priors(im.pixels, im.pitch, im.H, im.W, r, c, pri);
-    void *h1 = smem;
-    void *h2 = smem + hidden_bytes<PREC>(m.h1);
-    hidden<PREC>(m, pri, h1, h2, tid);
+    uint8_t *h1 = smem;
+    uint8_t *h2 = smem + hidden_bytes<PREC>(DEEP ? m.hmax : m.h1);
+    net_hidden<PREC, DEEP>(m, pri, h1, h2, tid);
 
     float zmax = -INFINITY;
     for (int j0 = 0; j0 < kSymbols; j0 += 4) {
         float z[4];
-        logits4<PREC>(m, h2, tid, j0, z);
+        net_logits4<PREC, DEEP>(m, h2, tid, j0, z);
 #pragma unroll
         for (int q = 0; q < 4; q++) zmax = z[q] > zmax ? z[q] : zmax;
     }
@@ -80,7 +223,7 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
     uint32_t W = 0, Ps = 0, ws = 0;
     for (int j0 = 0; j0 < kSymbols; j0 += 4) {
         float z[4];
-        logits4<PREC>(m, h2, tid, j0, z);
+        net_logits4<PREC, DEEP>(m, h2, tid, j0, z);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int i = j0 + q;
@@ -268,7 +411,7 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
 }
 
 bool f32_predict_supported(const DevModel &m) {
-    return m.precision == DLIC_FP32 && m.h1 % 4 == 0 && m.h2 % 4 == 0 && m.h1 <= kMaxHidden && m.h2 <= kMaxHidden &&
+    return m.precision == DLIC_FP32 && m.nl == 3 && m.h1 % 4 == 0 && m.h2 % 4 == 0 && m.h1 <= kMaxHidden && m.h2 <= kMaxHidden &&
            f32_predict_smem(m.h1, m.h2, (m.n_in + 15) / 16 * 16) <= 200 * 1024;
 }
 
@@ -356,7 +499,7 @@ __device__ bool decode_setup(const DevModel &m, const DecImage &im, const uint8_
     return s_ok != 0;
 }
 
-template <int PREC>
+template <int PREC, bool DEEP>
 __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut_s[64];
@@ -374,8 +517,8 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
         return;
     }
     float *zs = reinterpret_cast<float *>(smem);                        // [256][CH]
-    void *h1 = smem;                                                     // aliases zs (dead by then)
-    void *h2 = smem + (size_t)kSymbols * kCH * 4;
+    uint8_t *h1 = smem;                                                  // aliases zs (dead by then)
+    uint8_t *h2 = smem + (size_t)kSymbols * kCH * 4;
     const int H = im.H, W = im.W;
     const int T = 3 * (H - 1) + W;
     for (int t = 0; t < T; t++) {
@@ -391,11 +534,11 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
             if (active) {
                 uint8_t pri[kPriors];
                 gather_priors(im.pixels, im.pitch, H, W, r, c, pri);
-                hidden<PREC>(m, pri, h1, h2, tid);
+                net_hidden<PREC, DEEP>(m, pri, h1, h2, tid);
                 float zmax = -INFINITY;
                 for (int j0 = 0; j0 < kSymbols; j0 += 4) {
                     float z[4];
-                    logits4<PREC>(m, h2, tid, j0, z);
+                    net_logits4<PREC, DEEP>(m, h2, tid, j0, z);
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         zs[(j0 + q) * kCH + tid] = z[q];
@@ -458,49 +601,59 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
     if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
 }
 
+static bool deep_net(const DevModel &m) { return m.nl != 3; }
+
+// A (the first hidden layer, or every other one of a deeper network) and B
 template <int PREC>
 static size_t predict_smem(const DevModel &m) {
-    return hidden_bytes<PREC>(m.h1) + hidden_bytes<PREC>(m.h2);
+    return deep_net(m) ? 2 * hidden_bytes<PREC>(m.hmax) : hidden_bytes<PREC>(m.h1) + hidden_bytes<PREC>(m.h2);
 }
 
+// the table [256][CH] (A aliases it; every hidden width is <= 256) and B
 template <int PREC>
 static size_t decode_smem(const DevModel &m) {
-    return (size_t)kSymbols * kCH * 4 + hidden_bytes<PREC>(m.h2);
+    return (size_t)kSymbols * kCH * 4 + hidden_bytes<PREC>(deep_net(m) ? m.hmax : m.h2);
+}
+
+template <int PREC, bool DEEP>
+static cudaError_t predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st) {
+    const size_t sm = predict_smem<PREC>(m);
+    cudaError_t e = cudaFuncSetAttribute(k_predict_cc<PREC, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_predict_cc<PREC, DEEP><<<b.total_tiles, kCH, sm, st>>>(m, b);
+    return cudaGetLastError();
+}
+
+template <int PREC, bool DEEP>
+static cudaError_t decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st) {
+    const size_t sm = decode_smem<PREC>(m);
+    cudaError_t e = cudaFuncSetAttribute(k_decode_cc<PREC, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_decode_cc<PREC, DEEP><<<b.n, kCH, sm, st>>>(m, b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
     if (!default_window(m) && !(m.precision == DLIC_FP32 && f32_predict_supported(m))) return cudaErrorNotSupported;
+    const bool deep = deep_net(m);
     if (m.precision == DLIC_FP32 && f32_predict_supported(m)) {
         // 64-pixel tiles, as the encoder plans them for the CUDA-core path
         const size_t sm = f32_predict_smem(m.h1, m.h2, (m.n_in + 15) / 16 * 16);
         cudaFuncSetAttribute(k_predict_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_predict_f32<<<b.total_tiles, kF32Threads, sm, st>>>(m, b);
-    } else if (m.precision == DLIC_FP32) {
-        const size_t sm = predict_smem<DLIC_FP32>(m);
-        cudaFuncSetAttribute(k_predict_cc<DLIC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_predict_cc<DLIC_FP32><<<b.total_tiles, kCH, sm, st>>>(m, b);
-    } else {
-        const size_t sm = predict_smem<DLIC_INT8>(m);
-        cudaFuncSetAttribute(k_predict_cc<DLIC_INT8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_predict_cc<DLIC_INT8><<<b.total_tiles, kCH, sm, st>>>(m, b);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    if (m.precision == DLIC_FP32) return deep ? predict_cc<DLIC_FP32, true>(m, b, st) : predict_cc<DLIC_FP32, false>(m, b, st);
+    return deep ? predict_cc<DLIC_INT8, true>(m, b, st) : predict_cc<DLIC_INT8, false>(m, b, st);
 }
 
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st) {
     if (b.n == 0) return cudaSuccess;
     if (!default_window(m)) return cudaErrorNotSupported;   // one thread per pixel: the 12-prior window only
-    if (m.precision == DLIC_FP32) {
-        const size_t sm = decode_smem<DLIC_FP32>(m);
-        cudaFuncSetAttribute(k_decode_cc<DLIC_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_decode_cc<DLIC_FP32><<<b.n, kCH, sm, st>>>(m, b);
-    } else {
-        const size_t sm = decode_smem<DLIC_INT8>(m);
-        cudaFuncSetAttribute(k_decode_cc<DLIC_INT8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_decode_cc<DLIC_INT8><<<b.n, kCH, sm, st>>>(m, b);
-    }
-    return cudaGetLastError();
+    const bool deep = deep_net(m);
+    if (m.precision == DLIC_FP32) return deep ? decode_cc<DLIC_FP32, true>(m, b, st) : decode_cc<DLIC_FP32, false>(m, b, st);
+    return deep ? decode_cc<DLIC_INT8, true>(m, b, st) : decode_cc<DLIC_INT8, false>(m, b, st);
 }
 
 }  // namespace dlic

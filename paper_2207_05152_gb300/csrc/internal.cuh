@@ -19,9 +19,24 @@ constexpr int kHeaderBytes = 24;
 constexpr int kMaxHidden = 256;
 
 // Device-side view of a model (passed to kernels by value).
+// One dense layer of a network of other than two hidden layers, transposed
+// like the fixed-depth arrays below: FP32 w = W^T [in][out] (f32), a = bias;
+// INT8 w = [in / 4][out] (u32, 4 inputs per word), a = scale s, o = offset.
+struct DevLayer {
+    const void *w;
+    const float *a, *o;
+    int32_t n_in, n_out;
+};
+constexpr int kMaxLayers = 9;     // deeper networks: up to 8 hidden layers and the output layer
+
 struct DevModel {
     int precision;   // DLIC_FP32 / DLIC_INT8
-    int h1, h2;
+    int h1, h2;      // first and last hidden widths
+    // dense layers (3 for two hidden layers); a network of other depth runs
+    // on the one-pixel-per-thread kernels from the layer table, whose widest
+    // hidden layer has hmax units
+    int nl, hmax;
+    const DevLayer *layers;       // device array of nl entries (other depths only)
     // causal window: rows r-wu..r-1 at columns c-wl..c+wr, then row r at
     // columns c-wl..c-1 (n2 priors in that order); (2, 2, 2) by default.
     // A 3D window (vol = 1) adds the previous slice's rows r-pu..r+pd at

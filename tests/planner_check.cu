@@ -25,6 +25,8 @@ static DevModel model(int prec, int u, int l, int r, int vol, int pu, int pd, in
     m.pr = pr;
     m.n_in = m.n2 + (vol ? (pu + pd + 1) * (pl + pr + 1) : 0);
     m.h1 = m.h2 = h;
+    m.nl = 3;
+    m.hmax = h;
     return m;
 }
 

@@ -78,12 +78,37 @@ def test_window_contexts_match_the_default_sampler():
     assert np.array_equal(a, b) and np.array_equal(ta, tb)
 
 
-def test_deeper_networks_are_refused_before_any_device_call(lib):
-    # a valid "DLM2" blob (three hidden layers): the GPU kernels cover two
+def test_deeper_network_blobs_are_checked_before_any_device_call(lib):
+    # "DLM2" blobs the GPU library refuses while parsing (no device needed):
+    # another window with other than two hidden layers, hidden widths outside
+    # the one-pixel-per-thread kernels' range, malformed headers
+    import struct
     import synth
     from paper_2207_05152_gb300 import model as M
-    layers = synth.predictive_mlp([12, 32, 32, 256], 5)
-    deep = layers[:-1] + [(np.eye(32, dtype=np.float32), np.zeros(32, np.float32))] + layers[-1:]
-    with pytest.raises(lib.DlicError) as e:
-        lib.dlic_model_create(M.deep_fp32_blob(deep))
-    assert e.value.code == lib.DLIC_ERR_UNSUPPORTED
+
+    def deep(widths, window=M.DEFAULT_WINDOW, seed=5):
+        rng = synth.Rng(seed)
+        dims = [M.window_size(window)] + widths + [256]
+        layers = [((0.1 * rng.normal(o * i)).reshape(o, i).astype(np.float32), np.zeros(o, np.float32))
+                  for i, o in zip(dims[:-1], dims[1:])]
+        return M.deep_fp32_blob(layers, window)
+
+    cases = [
+        (deep([32, 32, 32], window=(3, 3, 2)), lib.DLIC_ERR_UNSUPPORTED),   # three hidden layers, wider window
+        (deep([32, 6, 32]), lib.DLIC_ERR_UNSUPPORTED),                      # width not a multiple of 4
+        (deep([32, 260, 32]), lib.DLIC_ERR_UNSUPPORTED),                    # width above 256
+        (deep([24, 40]), lib.DLIC_ERR_UNSUPPORTED),                         # two hidden layers: multiples of 16
+    ]
+    good = deep([32, 48, 32])
+    bad_l = bytearray(good)
+    bad_l[12:16] = struct.pack("<I", 0)                                      # no hidden layer
+    cases.append((bytes(bad_l), lib.DLIC_ERR_INVALID))
+    bad_w = bytearray(good)
+    bad_w[28:32] = struct.pack("<I", 16)                                     # a width past L
+    cases.append((bytes(bad_w), lib.DLIC_ERR_INVALID))
+    cases.append((good[:-4], lib.DLIC_ERR_INVALID))                          # truncated
+    cases.append((good + b"\0\0\0\0", lib.DLIC_ERR_INVALID))                # trailing bytes
+    for blob, code in cases:
+        with pytest.raises(lib.DlicError) as e:
+            lib.dlic_model_create(blob)
+        assert e.value.code == code, (len(blob), e.value)
