@@ -220,6 +220,9 @@ def run_ours(args):
     _, f6_8, f6_32 = workloads.models(window=M.FIG6_WINDOW)
     r6 = measure(f6_8, max(2, args.steps // 3), 2)
     r6f = measure(f6_32, 2, 2)
+    # six dense layers (five hidden, widths 128) on the CUDA-core coder
+    deep8, _ = workloads.deep_models()
+    rdeep = measure(deep8, 2, 2)
 
     def leg(r):
         return {"enc_mpix_s": round(N / (statistics.mean(r["enc"]) * 1e-3) / 1e6, 3),
@@ -299,6 +302,8 @@ def run_ours(args):
         "fig6_window": {"window": "9x9 of Fig. 6 (8 rows above, 6 left, 2 right: 78 priors)",
                         "widths": [M.window_size(M.FIG6_WINDOW), 128, 128, 256],
                         "int8": leg(r6), "fp32": leg(r6f)},
+        "deep_network": {"widths": [12, 128, 128, 128, 128, 128, 256], "precision": "int8",
+                         "kernels": "CUDA-core encoder, unit-split wavefront decoder", **leg(rdeep)},
         "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},

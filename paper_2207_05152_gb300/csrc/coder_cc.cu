@@ -50,12 +50,18 @@ __host__ __device__ inline size_t hidden_bytes(int h) {
 // start from the bias and accumulate fma(x_k, w_jk, acc) for k ascending,
 // then ReLU; INT8 units are exact dp4a dot products, requantised to u8.
 // Hidden layer l of L writes shared buffer B when L - 1 - l is even, else A,
-// so that the last hidden layer is always in B.
+// so that the last hidden layer is always in B.  With G > 1 threads per
+// pixel, thread group g computes the unit quads g, g + G, ... of every layer
+// and the CTA meets at a barrier after each layer (every group reaches it;
+// inactive threads compute nothing).  Shared-memory column tid is the pixel's.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8_t *A, uint8_t *B, int tid) {
+template <int PREC, int G>
+__device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8_t *A, uint8_t *B, int tid, int g,
+                            bool active) {
     const int L = m.nl - 1;
     for (int l = 0; l < L; l++) {
+        if (G > 1 && l > 0) __syncthreads();
+        if (!active) continue;
         const DevLayer ly = m.layers[l];
         uint8_t *out = ((L - 1 - l) & 1) ? A : B;
         const uint8_t *in = ((L - l) & 1) ? A : B;   // written by layer l - 1
@@ -66,7 +72,7 @@ __device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8
             float x0[kPriors];
 #pragma unroll
             for (int k = 0; k < kPriors; k++) x0[k] = __fmaf_rn((float)pri[k], 0.0078125f, -1.0f);
-            for (int j0 = 0; j0 < ly.n_out; j0 += 4) {
+            for (int j0 = 4 * g; j0 < ly.n_out; j0 += 4 * G) {
                 float a0 = __ldg(ly.a + j0), a1 = __ldg(ly.a + j0 + 1), a2 = __ldg(ly.a + j0 + 2),
                       a3 = __ldg(ly.a + j0 + 3);
                 if (l == 0) {   // n_in = kPriors (the default window)
@@ -104,7 +110,7 @@ __device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8
                          ((uint32_t)(uint8_t)(pri[4 * k4 + 2] ^ 0x80) << 16) |
                          ((uint32_t)(uint8_t)(pri[4 * k4 + 3] ^ 0x80) << 24);
             const int k4n = ly.n_in >> 2;
-            for (int j0 = 0; j0 < ly.n_out; j0 += 4) {
+            for (int j0 = 4 * g; j0 < ly.n_out; j0 += 4 * G) {
                 int a[4] = {0, 0, 0, 0};
                 if (l == 0) {   // n_in = kPriors: signed inputs
 #pragma unroll
@@ -133,6 +139,7 @@ __device__ void deep_hidden(const DevModel &m, const uint8_t pri[kPriors], uint8
             }
         }
     }
+    if (G > 1) __syncthreads();
 }
 
 // Logits j0 .. j0 + 3 of the output layer from the last hidden layer (in B).
@@ -174,7 +181,7 @@ __device__ __forceinline__ void deep_logits4(const DevModel &m, const uint8_t *B
 template <int PREC, bool DEEP>
 __device__ __forceinline__ void net_hidden(const DevModel &m, const uint8_t *pri, uint8_t *A, uint8_t *B, int tid) {
     if constexpr (DEEP)
-        deep_hidden<PREC>(m, pri, A, B, tid);
+        deep_hidden<PREC, 1>(m, pri, A, B, tid, 0, true);
     else
         hidden<PREC>(m, pri, A, B, tid);
 }
@@ -429,12 +436,16 @@ __device__ __forceinline__ uint32_t rd_le32(const uint8_t *p) {
     return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
 
+// Threads per pixel and per CTA of the decoder for deeper networks.
+constexpr int kDeepGroups = 8, kDeepThreads = kCH * kDeepGroups;
+
 // Parses and checks the header, then sets up every stream's state from the
-// word counts.  Returns false (uniformly across the CTA) for a corrupt header.
+// word counts (CTAs of at most kDeepThreads threads).  Returns false
+// (uniformly across the CTA) for a corrupt header.
 __device__ bool decode_setup(const DevModel &m, const DecImage &im, const uint8_t *in,
                              StreamState *st, int *S_out, const uint16_t **pay_out) {
     __shared__ int s_ok, s_S;
-    __shared__ uint32_t s_part[256];
+    __shared__ uint32_t s_part[kDeepThreads];
     const int tid = threadIdx.x, nth = blockDim.x;
     if (tid == 0) {
         int ok = im.in_bytes >= (uint64_t)kHeaderBytes;
@@ -499,7 +510,7 @@ __device__ bool decode_setup(const DevModel &m, const DecImage &im, const uint8_
     return s_ok != 0;
 }
 
-template <int PREC, bool DEEP>
+template <int PREC>
 __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut_s[64];
@@ -534,11 +545,11 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
             if (active) {
                 uint8_t pri[kPriors];
                 gather_priors(im.pixels, im.pitch, H, W, r, c, pri);
-                net_hidden<PREC, DEEP>(m, pri, h1, h2, tid);
+                hidden<PREC>(m, pri, h1, h2, tid);
                 float zmax = -INFINITY;
                 for (int j0 = 0; j0 < kSymbols; j0 += 4) {
                     float z[4];
-                    net_logits4<PREC, DEEP>(m, h2, tid, j0, z);
+                    logits4<PREC>(m, h2, tid, j0, z);
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         zs[(j0 + q) * kCH + tid] = z[q];
@@ -601,6 +612,133 @@ __global__ void __launch_bounds__(kCH) k_decode_cc(DevModel m, DecBatch b) {
     if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Wavefront decoder for networks of other than two hidden layers: the
+// decoder above with kDeepGroups threads per pixel.  Thread (g, p) owns
+// pixel slot p of the wave's chunk and unit group g: it computes the unit
+// quads g, g + G, ... of every layer (a CTA barrier after each layer), the
+// logits quads of the same pattern, and the table weights of those symbols.
+// The partial maxima and weight sums meet in shared memory (a maximum and an
+// integer sum: the same values in any order); the rANS step of the pixel
+// runs in group 0 in the row order of the one-thread-per-pixel decoder.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(kDeepThreads) k_decode_deep(DevModel m, DecBatch b) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t lut_s[64];
+    __shared__ float s_zmax[kDeepGroups][kCH];
+    __shared__ uint32_t s_wsum[kDeepGroups][kCH];
+    __shared__ int s_err;
+    const int tid = threadIdx.x, p = tid % kCH, g = tid / kCH;
+    const DecImage &im = b.img[blockIdx.x];
+    if (tid < 64) lut_s[tid] = m.lut[tid];
+    if (tid == 0) s_err = 0;
+    StreamState *st = reinterpret_cast<StreamState *>(b.ws + im.st_off);
+    const uint8_t *in = b.in + im.in_off;
+    int S;
+    const uint16_t *pay;
+    if (!decode_setup(m, im, in, st, &S, &pay)) {
+        if (tid == 0) b.status[im.sidx] = DLIC_ERR_CORRUPT;
+        return;
+    }
+    float *zs = reinterpret_cast<float *>(smem);                        // [256][CH]
+    uint8_t *A = smem;                                                   // aliases zs (dead by then)
+    uint8_t *B = smem + (size_t)kSymbols * kCH * 4;
+    const int H = im.H, W = im.W;
+    const int T = 3 * (H - 1) + W;
+    for (int t = 0; t < T; t++) {
+        if (s_err) break;
+        const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
+        const int r_hi = min(H - 1, t / 3);
+        const int n_t = r_hi - r_lo + 1;
+        for (int base = 0; base < n_t; base += kCH) {
+            const int pix = base + p;
+            const bool active = pix < n_t;
+            const int r = r_lo + pix, c = t - 3 * r;
+            uint8_t pri[kPriors];
+            if (active) gather_priors(im.pixels, im.pitch, H, W, r, c, pri);
+            deep_hidden<PREC, kDeepGroups>(m, pri, A, B, p, g, active);   // ends at a barrier
+            float zmax = -INFINITY;
+            if (active) {
+                for (int j0 = 4 * g; j0 < kSymbols; j0 += 4 * kDeepGroups) {
+                    float z[4];
+                    deep_logits4<PREC>(m, B, p, j0, z);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        zs[(j0 + q) * kCH + p] = z[q];
+                        zmax = z[q] > zmax ? z[q] : zmax;
+                    }
+                }
+            }
+            s_zmax[g][p] = zmax;
+            __syncthreads();
+            float mx = s_zmax[0][p];
+#pragma unroll
+            for (int k = 1; k < kDeepGroups; k++) mx = s_zmax[k][p] > mx ? s_zmax[k][p] : mx;
+            uint32_t wpart = 0;
+            if (active) {
+                for (int j0 = 4 * g; j0 < kSymbols; j0 += 4 * kDeepGroups)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const float zi = zs[(j0 + q) * kCH + p];
+                        wpart += table_weight(mx, zi, m.tscale, lut_s);
+                        zs[(j0 + q) * kCH + p] = __fsub_rn(mx, zi);   // keep m - z for the search
+                    }
+            }
+            s_wsum[g][p] = wpart;
+            __syncthreads();
+            uint32_t Wsum = 0;
+#pragma unroll
+            for (int k = 0; k < kDeepGroups; k++) Wsum += s_wsum[k][p];
+            const uint32_t Q = active ? table_q(Wsum) : 0u;
+            const int rounds = (min(kCH, n_t - base) + S - 1) / S;
+            for (int rnd = 0; rnd < rounds; rnd++) {
+                if (g == 0 && active && p / S == rnd) {
+                    StreamState q = st[r % S];
+                    const uint32_t slot = q.x & 0xFFFFu;
+                    uint32_t P = 0, c_lo = 0, f = 1;
+                    int sym = kSymbols - 1;
+                    for (int i = 0; i < kSymbols; i++) {
+                        float y = __fmul_rn(zs[i * kCH + p], m.tscale);
+                        y = y <= 1535.0f ? y : 1535.0f;
+                        const int u = __float2int_rn(y);
+                        const uint32_t w = lut_s[u & 63] >> (u >> 6);
+                        const uint32_t lo = (uint32_t)i + __umulhi(P, Q);
+                        const uint32_t hi = i == kSymbols - 1 ? kTotal : (uint32_t)i + 1u + __umulhi(P + w, Q);
+                        if (hi > slot) {
+                            sym = i;
+                            c_lo = lo;
+                            f = hi - lo;
+                            break;
+                        }
+                        P += w;
+                    }
+                    q.x = f * (q.x >> 16) + slot - c_lo;
+                    if (q.x < kRansL) {
+                        if (q.pos < q.end) {
+                            q.x = (q.x << 16) | pay[q.pos];
+                            q.pos++;
+                        } else {
+                            s_err = 1;
+                        }
+                    }
+                    st[r % S] = q;
+                    im.pixels[(int64_t)r * im.pitch + c] = (uint8_t)sym;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    // final states must be back at the initial value L with every word read
+    for (int s2 = tid; s2 < S && !s_err; s2 += kDeepThreads) {
+        const StreamState q = st[s2];
+        if (q.x != kRansL || q.pos != q.end) s_err = 1;
+    }
+    __syncthreads();
+    if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
+}
+
 static bool deep_net(const DevModel &m) { return m.nl != 3; }
 
 // A (the first hidden layer, or every other one of a deeper network) and B
@@ -627,9 +765,10 @@ static cudaError_t predict_cc(const DevModel &m, const EncBatch &b, cudaStream_t
 template <int PREC, bool DEEP>
 static cudaError_t decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st) {
     const size_t sm = decode_smem<PREC>(m);
-    cudaError_t e = cudaFuncSetAttribute(k_decode_cc<PREC, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    void (*kern)(DevModel, DecBatch) = DEEP ? k_decode_deep<PREC> : k_decode_cc<PREC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_decode_cc<PREC, DEEP><<<b.n, kCH, sm, st>>>(m, b);
+    kern<<<b.n, DEEP ? kDeepThreads : kCH, sm, st>>>(m, b);
     return cudaGetLastError();
 }
 

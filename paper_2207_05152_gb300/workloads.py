@@ -69,6 +69,16 @@ def models(seed: int = 2, window=M.DEFAULT_WINDOW, hidden: int = 128):
             M.fp32_blob(layers, window))
 
 
+def deep_models(seed: int = 2, extra: int = 3, hidden: int = 128):
+    """(INT8 blob, FP32 blob) of a network of six dense layers (Sec. II-B):
+    the synthetic predictive network with `extra` hidden identity layers
+    (W = I, b = 0) before its output layer, as "DLM2" blobs."""
+    layers = synth.predictive_mlp([M.window_size(M.DEFAULT_WINDOW), hidden, hidden, 256], seed)
+    eye = [(np.eye(hidden, dtype=np.float32), np.zeros(hidden, np.float32)) for _ in range(extra)]
+    deep = layers[:-1] + eye + layers[-1:]
+    return M.deep_int8_blob(deep, calibration_contexts()), M.deep_fp32_blob(deep)
+
+
 def cfg2_image() -> np.ndarray:
     return synth.config_image(2)
 
