@@ -434,7 +434,8 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
     int32_t *err = d_status ? d_status : reinterpret_cast<int32_t *>(ws + off);
     off += 256;
     uint8_t *out = static_cast<uint8_t *>(d_out);
-    const bool use_tc = tc_supported(m->dev);
+    // networks of other than two hidden layers: the one-pixel-per-thread kernels
+    const bool use_tc = m->dev.nl == 3 && tc_supported(m->dev);
     const int tile_px = use_tc ? 128 : kPredictTile;
     {
         cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), cs);
@@ -631,7 +632,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
     }
     const bool vol = m->dev.vol != 0;
-    const bool use_wave = wave_decode_supported(m->dev);
+    const bool use_wave = m->dev.nl == 3 && wave_decode_supported(m->dev);
     if (vol && !use_wave) return fail(DLIC_ERR_UNSUPPORTED, "volumes decode on the cluster wavefront kernels only");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     {

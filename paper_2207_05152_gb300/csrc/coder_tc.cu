@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
 }
 
 bool tc_supported(const DevModel &m) {
-    return m.precision == DLIC_INT8 && m.nl == 3 && m.tc_w != nullptr && m.h1 <= 128 && m.h2 <= 128;
+    return m.precision == DLIC_INT8 && m.tc_w != nullptr && m.h1 <= 128 && m.h2 <= 128;
 }
 
 size_t tc_weight_bytes(int h1, int h2, int k1) {

@@ -1539,10 +1539,8 @@ void choose_clusters(const int *H, const int *W, int n, int num_sms, bool f32, i
 
 // The cluster wavefront decoder runs the INT8 network of widths 128 on the
 // tensor cores, and FP32 networks whose W3^T fits in 128 KB of shared memory
-// on the CUDA cores; other networks (other widths, other depths) use the
-// one-CTA-per-image decoder.
+// on the CUDA cores; other networks use the one-CTA-per-image decoder.
 bool wave_decode_supported(const DevModel &m) {
-    if (m.nl != 3) return false;
     if (m.precision == DLIC_INT8) return m.tc_w != nullptr && m.h1 == kDecHidden && m.h2 == kDecHidden;
     return m.precision == DLIC_FP32 && m.h1 >= 4 && m.h1 <= kMaxHidden && m.h2 >= 4 && m.h2 <= 128 && m.h1 % 4 == 0 &&
            m.h2 % 4 == 0;
