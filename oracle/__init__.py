@@ -7,8 +7,8 @@ leg use this package; the CUDA library never imports or links it.
 """
 from .coder import (build, lib, encode, decode, symbol_tables, pixel_table, logits,
                     table_from_logits, gather, gather_window, rans_enc_step, rans_dec_step, fnv1a64,
-                    max_encoded_bytes, gather_window3, encode_volume, decode_volume)
+                    max_encoded_bytes, gather_window3, encode_volume, decode_volume, symbols)
 
 __all__ = ["build", "lib", "encode", "decode", "symbol_tables", "pixel_table", "logits",
            "table_from_logits", "gather", "gather_window", "rans_enc_step", "rans_dec_step", "fnv1a64",
-           "max_encoded_bytes", "gather_window3", "encode_volume", "decode_volume"]
+           "max_encoded_bytes", "gather_window3", "encode_volume", "decode_volume", "symbols"]

@@ -17,6 +17,8 @@ _lock = threading.Lock()
 _lib = None
 
 U8P = C.POINTER(C.c_uint8)
+U16P = C.POINTER(C.c_uint16)
+VP = C.c_void_p
 U32P = C.POINTER(C.c_uint32)
 F32P = C.POINTER(C.c_float)
 F64P = C.POINTER(C.c_double)
@@ -47,6 +49,8 @@ def lib():
             L.or_gather_window.argtypes = [C.c_int, C.c_int, C.c_int, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
             L.or_table_from_logits.restype = C.c_int
             L.or_table_from_logits.argtypes = [F32P, C.c_float, U32P, U32P]
+            L.or_table_k.restype = C.c_int
+            L.or_table_k.argtypes = [F32P, C.c_int, C.c_float, U32P, U32P]
             L.or_rans_enc_step.restype = C.c_int
             L.or_rans_enc_step.argtypes = [U64P, C.c_uint32, C.c_uint32, C.c_int, C.c_int, C.c_int,
                                            U32P, C.c_int]
@@ -56,24 +60,24 @@ def lib():
             L.or_max_encoded_bytes.restype = C.c_size_t
             L.or_max_encoded_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
             L.or_pixel_table.restype = C.c_int
-            L.or_pixel_table.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, C.c_int,
+            L.or_pixel_table.argtypes = [U8P, C.c_size_t, VP, C.c_int, C.c_int, C.c_int, C.c_int,
                                          F32P, U32P]
             L.or_logits.restype = C.c_int
-            L.or_logits.argtypes = [U8P, C.c_size_t, U8P, C.c_int, F32P]
+            L.or_logits.argtypes = [U8P, C.c_size_t, U16P, C.c_int, F32P]
             L.or_symbol_tables.restype = C.c_int
-            L.or_symbol_tables.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, U32P, F64P]
+            L.or_symbol_tables.argtypes = [U8P, C.c_size_t, VP, C.c_int, C.c_int, U32P, F64P]
             L.or_encode.restype = C.c_int64
-            L.or_encode.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, U8P,
+            L.or_encode.argtypes = [U8P, C.c_size_t, VP, C.c_int, C.c_int, C.c_int, U8P,
                                     C.c_size_t]
             L.or_decode.restype = C.c_int
-            L.or_decode.argtypes = [U8P, C.c_size_t, U8P, C.c_size_t, U8P, C.c_int, C.c_int]
+            L.or_decode.argtypes = [U8P, C.c_size_t, U8P, C.c_size_t, VP, C.c_int, C.c_int]
             L.or_gather_window3.restype = C.c_int
             L.or_gather_window3.argtypes = [C.c_int] * 7 + [U8P, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P]
             L.or_encode_volume.restype = C.c_int64
-            L.or_encode_volume.argtypes = [U8P, C.c_size_t, U8P, C.c_int, C.c_int, C.c_int, C.c_int, U8P,
+            L.or_encode_volume.argtypes = [U8P, C.c_size_t, VP, C.c_int, C.c_int, C.c_int, C.c_int, U8P,
                                            C.c_size_t, U64P]
             L.or_decode_volume.restype = C.c_int
-            L.or_decode_volume.argtypes = [U8P, C.c_size_t, U8P, U64P, C.c_int, U8P, C.c_int, C.c_int]
+            L.or_decode_volume.argtypes = [U8P, C.c_size_t, U8P, U64P, C.c_int, VP, C.c_int, C.c_int]
             _lib = L
     return _lib
 
@@ -84,6 +88,17 @@ def _p(a, t):
 
 def _bytes(b) -> np.ndarray:
     return np.frombuffer(bytes(b), dtype=np.uint8).copy()
+
+
+def symbols(blob: bytes) -> int:
+    """Output neurons of a model blob: 256 (8-bit pixels) or 4096 (12-bit)."""
+    off = 48 if bytes(blob[:4]) == b"DLM2" else 20
+    return int(np.frombuffer(bytes(blob[off:off + 4]), "<u4")[0])
+
+
+def _pixels(blob: bytes, img) -> np.ndarray:
+    """img as the model's sample type: u8 for 8-bit, u16 for 12-bit pixels."""
+    return np.ascontiguousarray(img, dtype=np.uint16 if symbols(blob) == 4096 else np.uint8)
 
 
 def fnv1a64(data: bytes) -> int:
@@ -127,11 +142,12 @@ def gather_window3(window, below, img: np.ndarray, r: int, c: int) -> np.ndarray
 
 
 def table_from_logits(z, tscale: float, lut) -> np.ndarray:
-    """Cumulative table c_0..c_256 (uint32) for one logit vector."""
-    z = np.ascontiguousarray(z, dtype=np.float32)
+    """Cumulative table c_0..c_K (uint32) for one logit vector of K symbols
+    (256, or 4096 for 12-bit pixels)."""
+    z = np.ascontiguousarray(z, dtype=np.float32).reshape(-1)
     lut = np.ascontiguousarray(lut, dtype=np.uint32)
-    cum = np.zeros(257, np.uint32)
-    st = lib().or_table_from_logits(_p(z, F32P), C.c_float(tscale), _p(lut, U32P), _p(cum, U32P))
+    cum = np.zeros(z.size + 1, np.uint32)
+    st = lib().or_table_k(_p(z, F32P), z.size, C.c_float(tscale), _p(lut, U32P), _p(cum, U32P))
     if st:
         raise ValueError(f"oracle table error {st}")
     return cum
@@ -161,12 +177,14 @@ def rans_dec_step(x: int, cum, words, pos: int, Lb=16, bb=16, Mb=16):
 
 
 def pixel_table(blob: bytes, img: np.ndarray, r: int, c: int):
-    """(logits[256] float32, cum[257] uint32) of pixel (r, c)."""
+    """(logits[K] float32, cum[K + 1] uint32) of pixel (r, c), K the model's
+    symbol count."""
     b = _bytes(blob)
-    img = np.ascontiguousarray(img, dtype=np.uint8)
-    z = np.zeros(256, np.float32)
-    cum = np.zeros(257, np.uint32)
-    st = lib().or_pixel_table(_p(b, U8P), b.size, _p(img, U8P), img.shape[0], img.shape[1], r, c,
+    img = _pixels(blob, img)
+    K = symbols(blob)
+    z = np.zeros(K, np.float32)
+    cum = np.zeros(K + 1, np.uint32)
+    st = lib().or_pixel_table(_p(b, U8P), b.size, img.ctypes.data, img.shape[0], img.shape[1], r, c,
                               _p(z, F32P), _p(cum, U32P))
     if st:
         raise ValueError(f"oracle error {st}")
@@ -174,12 +192,12 @@ def pixel_table(blob: bytes, img: np.ndarray, r: int, c: int):
 
 
 def logits(blob: bytes, pri: np.ndarray) -> np.ndarray:
-    """Logits [n, 256] for prior vectors [n, window size] (u8)."""
+    """Logits [n, K] for prior vectors [n, window size] (sample values)."""
     b = _bytes(blob)
     n_in = int(np.frombuffer(b[8:12].tobytes(), "<u4")[0])
-    pri = np.ascontiguousarray(pri, dtype=np.uint8).reshape(-1, n_in)
-    z = np.zeros((pri.shape[0], 256), np.float32)
-    st = lib().or_logits(_p(b, U8P), b.size, _p(pri, U8P), pri.shape[0], _p(z, F32P))
+    pri = np.ascontiguousarray(pri, dtype=np.uint16).reshape(-1, n_in)
+    z = np.zeros((pri.shape[0], symbols(blob)), np.float32)
+    st = lib().or_logits(_p(b, U8P), b.size, _p(pri, U16P), pri.shape[0], _p(z, F32P))
     if st:
         raise ValueError(f"oracle error {st}")
     return z
@@ -188,10 +206,10 @@ def logits(blob: bytes, pri: np.ndarray) -> np.ndarray:
 def symbol_tables(blob: bytes, img: np.ndarray):
     """(f | c << 16 per pixel as uint32 [H, W], ideal bits sum -log2(f/2^16))."""
     b = _bytes(blob)
-    img = np.ascontiguousarray(img, dtype=np.uint8)
+    img = _pixels(blob, img)
     fc = np.zeros(img.shape, np.uint32)
     bits = (C.c_double * 1)()
-    st = lib().or_symbol_tables(_p(b, U8P), b.size, _p(img, U8P), img.shape[0], img.shape[1],
+    st = lib().or_symbol_tables(_p(b, U8P), b.size, img.ctypes.data, img.shape[0], img.shape[1],
                                 _p(fc, U32P), bits)
     if st:
         raise ValueError(f"oracle error {st}")
@@ -199,12 +217,13 @@ def symbol_tables(blob: bytes, img: np.ndarray):
 
 
 def encode(blob: bytes, img: np.ndarray, streams: int) -> bytes:
+    """The container of one image (u8 samples, or u16 for a 12-bit model)."""
     b = _bytes(blob)
-    img = np.ascontiguousarray(img, dtype=np.uint8)
+    img = _pixels(blob, img)
     H, W = img.shape
     cap = max_encoded_bytes(H, W, streams)
     out = np.zeros(cap, np.uint8)
-    n = lib().or_encode(_p(b, U8P), b.size, _p(img, U8P), H, W, streams, _p(out, U8P), cap)
+    n = lib().or_encode(_p(b, U8P), b.size, img.ctypes.data, H, W, streams, _p(out, U8P), cap)
     if n < 0:
         raise ValueError(f"oracle encode error {-n}")
     return out[:n].tobytes()
@@ -219,8 +238,8 @@ def decode(blob: bytes, data: bytes, H: int, W: int):
         n = 0
     else:
         n = d.size
-    img = np.zeros((H, W), np.uint8)
-    st = lib().or_decode(_p(b, U8P), b.size, _p(d, U8P), n, _p(img, U8P), H, W)
+    img = np.zeros((H, W), np.uint16 if symbols(blob) == 4096 else np.uint8)
+    st = lib().or_decode(_p(b, U8P), b.size, _p(d, U8P), n, img.ctypes.data, H, W)
     return int(st), img
 
 
@@ -228,12 +247,12 @@ def encode_volume(blob: bytes, vol: np.ndarray, streams: int):
     """(bytes, offsets): the D slice containers of a volume (D x H x W)
     coded with a 3D window, back to back, and the D + 1 byte offsets."""
     b = _bytes(blob)
-    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    vol = _pixels(blob, vol)
     D, H, W = vol.shape
     cap = D * max_encoded_bytes(H, W, streams)
     out = np.zeros(cap, np.uint8)
     offs = np.zeros(D + 1, np.uint64)
-    n = lib().or_encode_volume(_p(b, U8P), b.size, _p(vol, U8P), D, H, W, streams, _p(out, U8P), cap,
+    n = lib().or_encode_volume(_p(b, U8P), b.size, vol.ctypes.data, D, H, W, streams, _p(out, U8P), cap,
                                _p(offs, U64P))
     if n < 0:
         raise ValueError(f"oracle encode error {-n}")
@@ -245,6 +264,6 @@ def decode_volume(blob: bytes, data: bytes, offsets, D: int, H: int, W: int):
     b = _bytes(blob)
     d = _bytes(data) if len(data) else np.zeros(1, np.uint8)
     offs = np.asarray(offsets, dtype=np.uint64)
-    vol = np.zeros((D, H, W), np.uint8)
-    st = lib().or_decode_volume(_p(b, U8P), b.size, _p(d, U8P), _p(offs, U64P), D, _p(vol, U8P), H, W)
+    vol = np.zeros((D, H, W), np.uint16 if symbols(blob) == 4096 else np.uint8)
+    st = lib().or_decode_volume(_p(b, U8P), b.size, _p(d, U8P), _p(offs, U64P), D, vol.ctypes.data, H, W)
     return int(st), vol

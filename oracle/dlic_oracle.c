@@ -10,6 +10,7 @@
  *   - Sec. II-B "Preprocessor": wavefront processing, identical network inputs
  *     at encode and decode;
  *   - Sec. II-B "Neural Network Architecture": dense layers, 256-way softmax;
+ *   - Sec. IV "Higher Bit Depth": 12-bit pixels, 4096 output neurons;
  *   - Sec. II-B "rANS": rANS coder, many coder instances and bitstreams, at
  *     most one per pixel row, 32-bit arithmetic.
  * Where the paper is silent (window radius, dummy value, table quantisation,
@@ -34,7 +35,8 @@
 
 #define NPRI 12           /* priors of the default radius-2 window */
 #define MAXPRI 96         /* largest window the coder takes */
-#define NSYM 256
+#define NSYM 256            /* symbols of an 8-bit image */
+#define NSYM_MAX 4096       /* symbols of a 12-bit image (Sec. IV "Higher Bit Depth") */
 #define TOTAL_M 65536u      /* frequency table total, 2^16 */
 #define RANS_L 65536u       /* rANS lower bound, 2^16 */
 
@@ -57,6 +59,7 @@ typedef struct {
     window_t win;
     int h1, h2;
     int nl;                      /* dense layers: hidden layers + the output layer */
+    int nsym, bits;              /* output neurons = symbols: 256 (8-bit) or 4096 (12-bit) */
     float tscale;
     uint32_t lut[64];
     float *w[MAXLAYERS], *b[MAXLAYERS];   /* FP32 network: W[l] is out x in, row-major */
@@ -94,7 +97,8 @@ static void model_free(model_t *m) {
 }
 
 /* Two layouts (little-endian):
- *   "DLM1": u32 precision, n_in, h1, h2, n_out (256), window, f32 tscale,
+ *   "DLM1": u32 precision, n_in, h1, h2, n_out (256, or 4096 for 12-bit
+ *           pixels), window, f32 tscale,
  *           u32 lut[64], then 3 dense layers (288-byte header);
  *   "DLM2" (deeper networks, Sec. II-B: six dense layers): u32 precision,
  *           n_in, L (hidden layers, 1..8), widths[8] (hidden widths, unused
@@ -162,7 +166,13 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     if (m->win.u < 1 || m->win.u > 8 || m->win.l > 8 || m->win.r > 2) return OR_ERR_INVALID;
     m->win.n2 = m->win.u * (m->win.l + m->win.r + 1) + m->win.l;
     m->win.n = m->win.n2 + m->win.n3;
-    if (m->win.n > MAXPRI || (int)n_in != m->win.n || n_out != NSYM) return OR_ERR_INVALID;
+    /* 256 outputs code 8-bit pixels; 4096 outputs 12-bit pixels (Sec. IV
+     * "Higher Bit Depth"), with the FP32 network only (an INT8 input byte
+     * cannot hold a 12-bit prior) */
+    if (m->win.n > MAXPRI || (int)n_in != m->win.n || (n_out != NSYM && n_out != NSYM_MAX)) return OR_ERR_INVALID;
+    if (n_out == NSYM_MAX && m->precision != 0) return OR_ERR_INVALID;
+    m->nsym = (int)n_out;
+    m->bits = n_out == NSYM_MAX ? 12 : 8;
     if (h1 < 1 || h1 > 4096 || h2 < 1 || h2 > 4096) return OR_ERR_INVALID;
     m->h1 = (int)h1; m->h2 = (int)h2;
     m->tscale = rd_f32(pre);
@@ -176,7 +186,7 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
     int dims_in[MAXLAYERS], dims_out[MAXLAYERS];
     for (int l = 0; l < m->nl; l++) {
         dims_in[l] = l == 0 ? m->win.n : (int)widths[l - 1];
-        dims_out[l] = l == m->nl - 1 ? NSYM : (int)widths[l];
+        dims_out[l] = l == m->nl - 1 ? m->nsym : (int)widths[l];
     }
     size_t need = deep ? 320 : 288;
     for (int l = 0; l < m->nl; l++) {
@@ -219,7 +229,12 @@ static int model_load(model_t *m, const uint8_t *blob, size_t n) {
 /*   row r-2: c-2..c+2, row r-1: c-2..c+2, row r: c-2, c-1.            */
 /* ------------------------------------------------------------------ */
 
-static void gather_win(const window_t *w, const uint8_t *img, int H, int W, int r, int c, uint8_t *pri) {
+/* Pixel i of an image of 8-bit (u8) or 12-bit (u16) samples. */
+static uint32_t px_at(const void *img, int bits, size_t i) {
+    return bits == 12 ? ((const uint16_t *)img)[i] : ((const uint8_t *)img)[i];
+}
+
+static void gather_win(const window_t *w, const void *img, int bits, int H, int W, int r, int c, uint16_t *pri) {
     const int wid = w->l + w->r + 1;
     for (int k = 0; k < w->n2; k++) {
         int dr, dc;
@@ -231,33 +246,39 @@ static void gather_win(const window_t *w, const uint8_t *img, int H, int W, int 
             dc = -w->l + (k - w->u * wid);
         }
         int rr = r + dr, cc = c + dc;
-        pri[k] = (rr >= 0 && rr < H && cc >= 0 && cc < W) ? img[(size_t)rr * W + cc] : 0;
+        pri[k] = (uint16_t)((rr >= 0 && rr < H && cc >= 0 && cc < W) ? px_at(img, bits, (size_t)rr * W + cc) : 0);
     }
 }
 
 /* A 3D window at (r, c) of a slice: the slice's own window, then the lower
  * layer from `below` (the previous slice, H x W), or zeros for the first
  * slice (below == NULL). */
-static void gather_win3(const window_t *w, const uint8_t *below, const uint8_t *img, int H, int W, int r, int c,
-                        uint8_t *pri) {
-    gather_win(w, img, H, W, r, c, pri);
+static void gather_win3(const window_t *w, const void *below, const void *img, int bits, int H, int W, int r,
+                        int c, uint16_t *pri) {
+    gather_win(w, img, bits, H, W, r, c, pri);
     const int wid = w->pl + w->pr + 1;
     for (int k = 0; k < w->n3; k++) {
         int rr = r - w->pu + k / wid, cc = c - w->pl + k % wid;
-        pri[w->n2 + k] = (below && rr >= 0 && rr < H && cc >= 0 && cc < W) ? below[(size_t)rr * W + cc] : 0;
+        pri[w->n2 + k] =
+            (uint16_t)((below && rr >= 0 && rr < H && cc >= 0 && cc < W) ? px_at(below, bits, (size_t)rr * W + cc) : 0);
     }
 }
 
 void or_gather(const uint8_t *img, int H, int W, int r, int c, uint8_t pri[NPRI]) {
     const window_t w = {2, 2, 2, NPRI, 0, 0, 0, 0, 0, NPRI, 0};
-    gather_win(&w, img, H, W, r, c, pri);
+    uint16_t p16[NPRI];
+    gather_win(&w, img, 8, H, W, r, c, p16);
+    for (int k = 0; k < NPRI; k++) pri[k] = (uint8_t)p16[k];
 }
 
 /* The priors of window (u, l, r) at pixel (r0, c0); returns their count. */
 int or_gather_window(int u, int l, int rr, const uint8_t *img, int H, int W, int r0, int c0, uint8_t *pri) {
     const int n2 = u * (l + rr + 1) + l;
     const window_t w = {u, l, rr, n2, 0, 0, 0, 0, 0, n2, 0};
-    gather_win(&w, img, H, W, r0, c0, pri);
+    uint16_t p16[MAXPRI];
+    if (n2 > MAXPRI) return -1;
+    gather_win(&w, img, 8, H, W, r0, c0, p16);
+    for (int k = 0; k < w.n; k++) pri[k] = (uint8_t)p16[k];
     return w.n;
 }
 
@@ -267,13 +288,17 @@ int or_gather_window3(int u, int l, int rr, int pu, int pd, int pl, int pr, cons
                       int H, int W, int r0, int c0, uint8_t *pri) {
     const int n2 = u * (l + rr + 1) + l, n3 = (pu + pd + 1) * (pl + pr + 1);
     const window_t w = {u, l, rr, n2, pu, pd, pl, pr, n3, n2 + n3, 1};
-    gather_win3(&w, below, img, H, W, r0, c0, pri);
+    uint16_t p16[MAXPRI];
+    if (n2 + n3 > MAXPRI) return -1;
+    gather_win3(&w, below, img, 8, H, W, r0, c0, p16);
+    for (int k = 0; k < w.n; k++) pri[k] = (uint8_t)p16[k];
     return w.n;
 }
 
 /* ------------------------------------------------------------------ */
 /* Density-estimation network (Sec. II-B).                              */
-/* FP32 reading: input v/128 - 1; each unit starts from its bias and    */
+/* FP32 reading: input v/128 - 1 (8-bit) or v/2048 - 1 (12-bit), exact; */
+/* each unit starts from its bias and                                   */
 /* accumulates fma(x_k, w_jk, acc) for k = 0, 1, ... in order; ReLU on  */
 /* hidden units.                                                        */
 /* INT8 reading: input v - 128, exact integer dot products, hidden      */
@@ -281,9 +306,10 @@ int or_gather_window3(int u, int l, int rr, int pu, int pd, int pl, int pr, cons
 /* fma(acc, s_j, o_j).                                                  */
 /* ------------------------------------------------------------------ */
 
-static void mlp_fp32(const model_t *m, const uint8_t *pri, float z[NSYM]) {
+static void mlp_fp32(const model_t *m, const uint16_t *pri, float *z) {
     float a[4096], b[4096];
-    for (int k = 0; k < m->win.n; k++) a[k] = fmaf((float)pri[k], 0.0078125f, -1.0f);
+    const float scale = m->bits == 12 ? 0.00048828125f : 0.0078125f;   /* 2^-11 or 2^-7 */
+    for (int k = 0; k < m->win.n; k++) a[k] = fmaf((float)pri[k], scale, -1.0f);
     float *in = a, *out = b;
     for (int l = 0; l < m->nl; l++) {
         int ni = m->n_in[l], no = m->n_out[l];
@@ -295,7 +321,7 @@ static void mlp_fp32(const model_t *m, const uint8_t *pri, float z[NSYM]) {
         }
         float *t = in; in = out; out = t;
     }
-    for (int i = 0; i < NSYM; i++) z[i] = in[i];
+    for (int i = 0; i < m->nsym; i++) z[i] = in[i];
 }
 
 static float requant_u8(int32_t acc, float s, float o) {
@@ -305,7 +331,7 @@ static float requant_u8(int32_t acc, float s, float o) {
     return t;
 }
 
-static void mlp_int8(const model_t *m, const uint8_t *pri, float z[NSYM]) {
+static void mlp_int8(const model_t *m, const uint16_t *pri, float *z) {
     int32_t a[4096], b[4096];
     for (int k = 0; k < m->win.n; k++) a[k] = (int32_t)pri[k] - 128;
     int32_t *in = a, *out = b;
@@ -323,7 +349,7 @@ static void mlp_int8(const model_t *m, const uint8_t *pri, float z[NSYM]) {
     }
 }
 
-static void mlp(const model_t *m, const uint8_t *pri, float z[NSYM]) {
+static void mlp(const model_t *m, const uint16_t *pri, float *z) {
     if (m->precision == 0) mlp_fp32(m, pri, z);
     else mlp_int8(m, pri, z);
 }
@@ -336,19 +362,22 @@ static void mlp(const model_t *m, const uint8_t *pri, float z[NSYM]) {
 /*   y_i = min((m - z_i) * tscale, 1535)       (two roundings)          */
 /*   u_i = rint(y_i)                          (half to even)            */
 /*   w_i = lut[u_i mod 64] >> (u_i div 64)     ~ 2^23 * exp(z_i - m)    */
-/*   W   = sum_i w_i,   Q = floor(65280 * 2^32 / W)                     */
-/*   c_i = i + floor(P_i * Q / 2^32),  P_i = sum_{j<i} w_j,  c_256=2^16 */
+/*   W   = sum_i w_i,   Q = floor((2^16 - K) * 2^32 / W)                */
+/*   c_i = i + floor(P_i * Q / 2^32),  P_i = sum_{j<i} w_j,  c_K = 2^16 */
 /*   f_i = c_{i+1} - c_i    (every f_i >= 1, sum f_i = 2^16)            */
+/* for K symbols: 256 (2^16 - K = 65280) or 4096 for 12-bit pixels     */
+/* (Sec. IV "Higher Bit Depth"; 2^16 - K = 61440, and W, P_i up to     */
+/* 2^35 in 64-bit integers).                                            */
 /* ------------------------------------------------------------------ */
 
-int or_table_from_logits(const float z[NSYM], float tscale, const uint32_t lut[64],
-                         uint32_t cum[NSYM + 1]) {
+int or_table_k(const float *z, int K, float tscale, const uint32_t lut[64], uint32_t *cum) {
+    if (K < 2 || K > NSYM_MAX) return OR_ERR_INVALID;
     float m = z[0];
-    for (int i = 1; i < NSYM; i++)
+    for (int i = 1; i < K; i++)
         if (z[i] > m) m = z[i];
-    uint32_t w[NSYM];
+    uint32_t w[NSYM_MAX];
     uint64_t Wsum = 0;
-    for (int i = 0; i < NSYM; i++) {
+    for (int i = 0; i < K; i++) {
         float d = m - z[i];
         float y = d * tscale;
         if (!(y <= 1535.0f)) y = 1535.0f;
@@ -356,15 +385,20 @@ int or_table_from_logits(const float z[NSYM], float tscale, const uint32_t lut[6
         w[i] = lut[u & 63] >> (u >> 6);
         Wsum += w[i];
     }
-    if (Wsum == 0 || Wsum > 0x80000000ull) return OR_ERR_INVALID;
-    uint64_t Q = (65280ull << 32) / Wsum;
+    if (Wsum == 0 || Wsum > (uint64_t)K << 23) return OR_ERR_INVALID;
+    uint64_t Q = ((uint64_t)(TOTAL_M - (uint32_t)K) << 32) / Wsum;
     uint64_t P = 0;
-    for (int i = 0; i < NSYM; i++) {
+    for (int i = 0; i < K; i++) {
         cum[i] = (uint32_t)i + (uint32_t)((P * Q) >> 32);
         P += w[i];
     }
-    cum[NSYM] = TOTAL_M;
+    cum[K] = TOTAL_M;
     return OR_OK;
+}
+
+int or_table_from_logits(const float z[NSYM], float tscale, const uint32_t lut[64],
+                         uint32_t cum[NSYM + 1]) {
+    return or_table_k(z, NSYM, tscale, lut, cum);
 }
 
 /* ------------------------------------------------------------------ */
@@ -438,7 +472,8 @@ static size_t stream_order(int H, int W, int S, int s, px_t *order) {
 /* Container.  Reading (the paper stores one bitstream per coder         */
 /* instance and says nothing of the framing):                           */
 /*   "DLC1", u32 H, u32 W, u8 window rows u (2 for the default         */
-/*   window), u8 precision, u16 S, u64 model hash, u32 words[S], then   */
+/*   window), u8 precision (bit 4 set for 12-bit pixels), u16 S, u64    */
+/*   model hash, u32 words[S], then                                     */
 /*   S payloads of u16 words.  Each payload                             */
 /*   opens with the final encoder state (high half first) followed by   */
 /*   the renormalisation words in the order the decoder reads them.     */
@@ -455,7 +490,9 @@ size_t or_max_encoded_bytes(int H, int W, int S) {
 
 /* Per-pixel table of the model at pixel (r, c) of an image whose pixels
  * before (r, c) in wave order are those of img (later pixels are not read). */
-int or_pixel_table(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H, int W,
+/* img holds u8 samples for a model of 256 outputs, u16 for 4096; z_out
+ * and cum_out take the model's symbol count (+ 1). */
+int or_pixel_table(const uint8_t *blob, size_t blob_n, const void *img, int H, int W,
                    int r, int c, float *z_out, uint32_t *cum_out) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
@@ -464,51 +501,53 @@ int or_pixel_table(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H
         model_free(&m);
         return OR_ERR_INVALID;   /* a 3D window needs the previous slice */
     }
-    uint8_t pri[MAXPRI];
-    float z[NSYM];
-    uint32_t cum[NSYM + 1];
-    gather_win(&m.win, img, H, W, r, c, pri);
+    uint16_t pri[MAXPRI];
+    float z[NSYM_MAX];
+    uint32_t cum[NSYM_MAX + 1];
+    gather_win(&m.win, img, m.bits, H, W, r, c, pri);
     mlp(&m, pri, z);
-    st = or_table_from_logits(z, m.tscale, m.lut, cum);
-    if (z_out) memcpy(z_out, z, sizeof(z));
-    if (cum_out) memcpy(cum_out, cum, sizeof(cum));
+    st = or_table_k(z, m.nsym, m.tscale, m.lut, cum);
+    if (z_out) memcpy(z_out, z, sizeof(float) * m.nsym);
+    if (cum_out) memcpy(cum_out, cum, sizeof(uint32_t) * (m.nsym + 1));
     model_free(&m);
     return st;
 }
 
-/* Logits of the model for a batch of prior vectors (n x window size, u8). */
-int or_logits(const uint8_t *blob, size_t blob_n, const uint8_t *pri, int n, float *z_out) {
+/* Logits of the model for a batch of prior vectors (n x window size, u16),
+ * n x the model's symbol count. */
+int or_logits(const uint8_t *blob, size_t blob_n, const uint16_t *pri, int n, float *z_out) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
-    for (int i = 0; i < n; i++) mlp(&m, pri + (size_t)i * m.win.n, z_out + (size_t)i * NSYM);
+    for (int i = 0; i < n; i++) mlp(&m, pri + (size_t)i * m.win.n, z_out + (size_t)i * m.nsym);
     model_free(&m);
     return OR_OK;
 }
 
 /* The model's priors at (r, c): the 2D window, or a 3D window over the
  * slice img and the previous slice `below` (NULL for the first slice). */
-static void gather_model(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, int r, int c,
-                         uint8_t *pri) {
+static void gather_model(const model_t *m, const void *below, const void *img, int H, int W, int r, int c,
+                         uint16_t *pri) {
     if (m->win.vol)
-        gather_win3(&m->win, below, img, H, W, r, c, pri);
+        gather_win3(&m->win, below, img, m->bits, H, W, r, c, pri);
     else
-        gather_win(&m->win, img, H, W, r, c, pri);
+        gather_win(&m->win, img, m->bits, H, W, r, c, pri);
 }
 
-static int symbol_tables(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, uint32_t *fc_out,
+static int symbol_tables(const model_t *m, const void *below, const void *img, int H, int W, uint32_t *fc_out,
                          double *bits_out) {
     double bits = 0.0;
+    float z[NSYM_MAX];
+    uint32_t cum[NSYM_MAX + 1];
     for (int r = 0; r < H; r++)
         for (int c = 0; c < W; c++) {
-            uint8_t pri[MAXPRI];
-            float z[NSYM];
-            uint32_t cum[NSYM + 1];
+            uint16_t pri[MAXPRI];
             gather_model(m, below, img, H, W, r, c, pri);
             mlp(m, pri, z);
-            int st = or_table_from_logits(z, m->tscale, m->lut, cum);
+            int st = or_table_k(z, m->nsym, m->tscale, m->lut, cum);
             if (st) return st;
-            uint8_t v = img[(size_t)r * W + c];
+            uint32_t v = px_at(img, m->bits, (size_t)r * W + c);
+            if (v >= (uint32_t)m->nsym) return OR_ERR_INVALID;   /* a 12-bit sample above 4095 */
             uint32_t f = cum[v + 1] - cum[v];
             fc_out[(size_t)r * W + c] = f | (cum[v] << 16);
             bits -= log2((double)f / 65536.0);
@@ -519,7 +558,7 @@ static int symbol_tables(const model_t *m, const uint8_t *below, const uint8_t *
 
 /* Per-pixel (f, c) of every pixel in raster order, as f | c << 16 and,
  * optionally, the ideal code length sum of -log2(f / 2^16) in float64. */
-int or_symbol_tables(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H, int W,
+int or_symbol_tables(const uint8_t *blob, size_t blob_n, const void *img, int H, int W,
                      uint32_t *fc_out, double *bits_out) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
@@ -532,7 +571,7 @@ int or_symbol_tables(const uint8_t *blob, size_t blob_n, const uint8_t *img, int
 /* Codes one slice (or 2D image) into a container at out; below is the
  * previous slice for a 3D window (NULL otherwise).  Returns the bytes
  * written or minus an error code. */
-static int64_t encode_slice(const model_t *m, const uint8_t *below, const uint8_t *img, int H, int W, int S,
+static int64_t encode_slice(const model_t *m, const void *below, const void *img, int H, int W, int S,
                             uint8_t *out, size_t cap) {
     if (H < 1 || W < 1 || S < 1 || H > 65535 * 64 || W > 65535 * 64) return -OR_ERR_INVALID;
     if (S > H) S = H;
@@ -549,7 +588,8 @@ static int64_t encode_slice(const model_t *m, const uint8_t *below, const uint8_
     /* rows of the window above the pixel (2 for the default window), with
      * bit 7 set in the slices of a volume coded with a 3D window */
     out[12] = (uint8_t)(m->win.u | (m->win.vol ? 0x80 : 0));
-    out[13] = (uint8_t)m->precision;
+    /* precision, with bit 4 set for 12-bit pixels */
+    out[13] = (uint8_t)(m->precision | (m->bits == 12 ? 0x10 : 0));
     wr_u16(out + 14, (uint32_t)S);
     for (int k = 0; k < 8; k++) out[16 + k] = (uint8_t)(m->hash >> (8 * k));
     size_t pos = 24 + 4 * (size_t)S;
@@ -579,7 +619,7 @@ static int64_t encode_slice(const model_t *m, const uint8_t *below, const uint8_
 
 /* Encodes one H x W image with S streams (S is clipped to H).  Returns the
  * number of bytes written to out, or minus an error code. */
-int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H, int W, int S,
+int64_t or_encode(const uint8_t *blob, size_t blob_n, const void *img, int H, int W, int S,
                   uint8_t *out, size_t cap) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
@@ -593,7 +633,7 @@ int64_t or_encode(const uint8_t *blob, size_t blob_n, const uint8_t *img, int H,
  * window, each slice as its own container with S streams, back to back;
  * offsets[z] .. offsets[z + 1] bound slice z's container.  Returns the total
  * bytes or minus an error code. */
-int64_t or_encode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *vol, int D, int H, int W, int S,
+int64_t or_encode_volume(const uint8_t *blob, size_t blob_n, const void *vol, int D, int H, int W, int S,
                          uint8_t *out, size_t cap, uint64_t *offsets) {
     if (D < 1) return -OR_ERR_INVALID;
     model_t m;
@@ -603,8 +643,10 @@ int64_t or_encode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *vol,
     size_t pos = 0, N = (size_t)H * W;
     offsets[0] = 0;
     for (int z = 0; z < D; z++) {
-        int64_t n = encode_slice(&m, z ? vol + (size_t)(z - 1) * N : NULL, vol + (size_t)z * N, H, W, S, out + pos,
-                                 cap - pos);
+        const size_t bps = m.bits == 12 ? 2 : 1;   /* bytes per sample */
+        const uint8_t *v8 = (const uint8_t *)vol;
+        int64_t n = encode_slice(&m, z ? v8 + (size_t)(z - 1) * N * bps : NULL, v8 + (size_t)z * N * bps, H, W, S,
+                                 out + pos, cap - pos);
         if (n < 0) { model_free(&m); return n; }
         pos += (size_t)n;
         offsets[z + 1] = pos;
@@ -618,7 +660,7 @@ int64_t or_encode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *vol,
  * order (t ascending, then r ascending): a topological order of the causal
  * dependencies that visits every stream in its own order.  below: the
  * decoded previous slice for a 3D window (NULL otherwise). */
-static int decode_slice(const model_t *m, const uint8_t *below, const uint8_t *in, size_t n, uint8_t *img_out,
+static int decode_slice(const model_t *m, const void *below, const uint8_t *in, size_t n, void *img_out,
                         int H, int W) {
     if (H < 1 || W < 1) return OR_ERR_INVALID;
     if (n < 24 || memcmp(in, "DLC1", 4) != 0) return OR_ERR_CORRUPT;
@@ -626,7 +668,8 @@ static int decode_slice(const model_t *m, const uint8_t *below, const uint8_t *i
     int S = in[14] | (in[15] << 8);
     uint64_t hash = 0;
     for (int k = 0; k < 8; k++) hash |= (uint64_t)in[16 + k] << (8 * k);
-    if (h != H || w != W || in[12] != (m->win.u | (m->win.vol ? 0x80 : 0)) || in[13] != m->precision ||
+    if (h != H || w != W || in[12] != (m->win.u | (m->win.vol ? 0x80 : 0)) ||
+        in[13] != (m->precision | (m->bits == 12 ? 0x10 : 0)) ||
         hash != m->hash || S < 1 || S > H || n < 24 + 4 * (size_t)S)
         return OR_ERR_CORRUPT;
     uint32_t *words = malloc(4 * (size_t)S), *start = malloc(4 * (size_t)S);
@@ -653,23 +696,26 @@ static int decode_slice(const model_t *m, const uint8_t *below, const uint8_t *i
         pos[s] = 2;
         if (x[s] < RANS_L) st = OR_ERR_CORRUPT;
     }
-    memset(img_out, 0, (size_t)H * W);
+    memset(img_out, 0, (size_t)H * W * (m->bits == 12 ? 2 : 1));
+    float z[NSYM_MAX];
+    uint32_t cum[NSYM_MAX + 1];
     int T = 3 * (H - 1) + W;
     for (int t = 0; t < T && st == OR_OK; t++) {
         for (int r = 0; r < H && st == OR_OK; r++) {
             int c = t - 3 * r;
             if (c < 0 || c >= W) continue;
             int s = r % S;
-            uint8_t pri[MAXPRI];
-            float z[NSYM];
-            uint32_t cum[NSYM + 1];
+            uint16_t pri[MAXPRI];
             gather_model(m, below, img_out, H, W, r, c, pri);
             mlp(m, pri, z);
-            if (or_table_from_logits(z, m->tscale, m->lut, cum)) { st = OR_ERR_INVALID; break; }
-            int sym = or_rans_dec_step(&x[s], cum, NSYM, 16, 16, 16, all + start[s], (int)words[s],
+            if (or_table_k(z, m->nsym, m->tscale, m->lut, cum)) { st = OR_ERR_INVALID; break; }
+            int sym = or_rans_dec_step(&x[s], cum, m->nsym, 16, 16, 16, all + start[s], (int)words[s],
                                        &pos[s]);
             if (sym < 0) { st = OR_ERR_CORRUPT; break; }
-            img_out[(size_t)r * W + c] = (uint8_t)sym;
+            if (m->bits == 12)
+                ((uint16_t *)img_out)[(size_t)r * W + c] = (uint16_t)sym;
+            else
+                ((uint8_t *)img_out)[(size_t)r * W + c] = (uint8_t)sym;
         }
     }
     for (int s = 0; s < S && st == OR_OK; s++)
@@ -678,7 +724,7 @@ static int decode_slice(const model_t *m, const uint8_t *below, const uint8_t *i
     return st;
 }
 
-int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, uint8_t *img_out,
+int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, void *img_out,
               int H, int W) {
     model_t m;
     int st = model_load(&m, blob, blob_n);
@@ -693,16 +739,17 @@ int or_decode(const uint8_t *blob, size_t blob_n, const uint8_t *in, size_t n, u
  * lower layer lies in the slice before, already decoded).  Returns the first
  * slice's error, if any. */
 int or_decode_volume(const uint8_t *blob, size_t blob_n, const uint8_t *in, const uint64_t *offsets, int D,
-                     uint8_t *vol_out, int H, int W) {
+                     void *vol_out, int H, int W) {
     if (D < 1) return OR_ERR_INVALID;
     model_t m;
     int st = model_load(&m, blob, blob_n);
     if (st) return st;
     if (!m.win.vol) { model_free(&m); return OR_ERR_INVALID; }
-    size_t N = (size_t)H * W;
+    const size_t N = (size_t)H * W * (m.bits == 12 ? 2 : 1);   /* bytes per slice */
+    uint8_t *v8 = (uint8_t *)vol_out;
     for (int z = 0; z < D && st == OR_OK; z++)
-        st = decode_slice(&m, z ? vol_out + (size_t)(z - 1) * N : NULL, in + offsets[z], offsets[z + 1] - offsets[z],
-                          vol_out + (size_t)z * N, H, W);
+        st = decode_slice(&m, z ? v8 + (size_t)(z - 1) * N : NULL, in + offsets[z], offsets[z + 1] - offsets[z],
+                          v8 + (size_t)z * N, H, W);
     model_free(&m);
     return st;
 }

@@ -10,7 +10,9 @@ coder uses:
 
     0    char[4] "DLM1"
     4    u32 precision            0 = FP32 network, 1 = INT8 network
-    8    u32 n_in, n_h1, n_h2, n_out (256), window
+    8    u32 n_in, n_h1, n_h2, n_out, window
+         n_out = 256 for 8-bit pixels, 4096 for 12-bit pixels (Sec. IV
+         "Higher Bit Depth"; FP32 networks only, input v / 2048 - 1)
          window = 2: the default radius-2 window (n_in = 12); otherwise
          1 << 24 | u | l << 8 | r << 16: rows r-u..r-1 at columns c-l..c+r,
          then row r at columns c-l..c-1 (n_in = u (l + r + 1) + l, at most
@@ -44,6 +46,7 @@ PREC_FP32 = 0
 PREC_INT8 = 1
 N_IN = 12
 N_OUT = 256
+N_OUT_12 = 4096   # 12-bit pixels: one output neuron per value (Sec. IV "Higher Bit Depth")
 RADIUS = 2
 DEFAULT_WINDOW = (2, 2, 2)
 FIG6_WINDOW = (8, 6, 2)   # 9 x 9 window, target in the last row, third column from the right
@@ -136,22 +139,22 @@ def table_lut() -> np.ndarray:
     return np.rint(np.exp2(23.0 - k / 64.0)).astype(np.uint32)
 
 
-def _header(precision: int, h1: int, h2: int, window=DEFAULT_WINDOW) -> bytes:
-    hdr = MAGIC + struct.pack("<6I", precision, window_size(window), h1, h2, N_OUT, window_field(window))
+def _header(precision: int, h1: int, h2: int, window=DEFAULT_WINDOW, n_out: int = N_OUT) -> bytes:
+    hdr = MAGIC + struct.pack("<6I", precision, window_size(window), h1, h2, n_out, window_field(window))
     hdr += struct.pack("<f", float(TSCALE))
     hdr += table_lut().astype("<u4").tobytes()
     assert len(hdr) == HEADER_BYTES
     return hdr
 
 
-def _check_widths(layers, window=DEFAULT_WINDOW):
+def _check_widths(layers, window=DEFAULT_WINDOW, n_out: int = N_OUT):
     if len(layers) != 3:
         raise ValueError("the coder network has exactly three dense layers")
     (w1, b1), (w2, b2), (w3, b3) = layers
     h1, h2 = w1.shape[0], w2.shape[0]
-    if w1.shape != (h1, window_size(window)) or w2.shape != (h2, h1) or w3.shape != (N_OUT, h2):
-        raise ValueError("layer shapes must be (h1, window size), (h2, h1), (256, h2)")
-    if b1.shape != (h1,) or b2.shape != (h2,) or b3.shape != (N_OUT,):
+    if w1.shape != (h1, window_size(window)) or w2.shape != (h2, h1) or w3.shape != (n_out, h2):
+        raise ValueError(f"layer shapes must be (h1, window size), (h2, h1), ({n_out}, h2)")
+    if b1.shape != (h1,) or b2.shape != (h2,) or b3.shape != (n_out,):
         raise ValueError("bias shapes do not match the layers")
     if h1 % 16 or h2 % 16 or not (16 <= h1 <= 256) or not (16 <= h2 <= 256):
         raise ValueError("hidden widths must be multiples of 16 in [16, 256]")
@@ -163,6 +166,17 @@ def fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
     causal window (u, l, r)."""
     h1, h2 = _check_widths(layers, window)
     out = [_header(PREC_FP32, h1, h2, window)]
+    for w, b in layers:
+        out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
+        out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
+    return b"".join(out)
+
+
+def fp32_blob12(layers) -> bytes:
+    """Blob of an FP32 network for 12-bit pixels, [(W1, b1), (W2, b2),
+    (W3, b3)] with 4096 outputs, over the default window."""
+    h1, h2 = _check_widths(layers, DEFAULT_WINDOW, N_OUT_12)
+    out = [_header(PREC_FP32, h1, h2, DEFAULT_WINDOW, N_OUT_12)]
     for w, b in layers:
         out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
         out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())

@@ -156,6 +156,36 @@ def phantom_image(height: int, width: int, seed: int) -> np.ndarray:
     return _to_u8(np.sqrt((s + n1) ** 2 + n2 ** 2))
 
 
+def phantom_image12(height: int, width: int, seed: int) -> np.ndarray:
+    """12-bit MRI-like slice (uint16, 0..4095; Sec. IV: one 12-bit channel):
+    the construction of phantom_image on a 16x finer intensity scale (tissue
+    480..3360, Rician noise sigma from U[48, 160]), so that the background
+    near zero dominates the histogram as in the paper's MRI data."""
+    rng = Rng(seed)
+    n_ell = int(rng.integers(1, 3, 8)[0])
+    ys = (np.arange(height, dtype=np.float64)[:, None] - height / 2) / (height / 2)
+    xs = (np.arange(width, dtype=np.float64)[None, :] - width / 2) / (width / 2)
+    img = np.zeros((height, width))
+    scale = 1.0
+    for _ in range(n_ell):
+        p = rng.uniform(6)
+        y0, x0 = (p[0] - 0.5) * 0.3 * scale, (p[1] - 0.5) * 0.3 * scale
+        ay, ax = (0.5 + 0.4 * p[2]) * scale, (0.5 + 0.4 * p[3]) * scale
+        th = np.pi * p[4]
+        val = 16.0 * (30.0 + 180.0 * p[5])
+        yr = (ys - y0) * np.cos(th) + (xs - x0) * np.sin(th)
+        xr = -(ys - y0) * np.sin(th) + (xs - x0) * np.cos(th)
+        img[(yr / ay) ** 2 + (xr / ax) ** 2 <= 1.0] = val
+        scale *= 0.8
+    q = rng.uniform(5, -0.1, 0.1)
+    bias = np.clip(1.0 + q[0] * ys + q[1] * xs + q[2] * ys * ys + q[3] * xs * xs + q[4] * xs * ys, 0.8, 1.2)
+    sigma = 16.0 * float(rng.uniform(1, 3.0, 10.0)[0])
+    s = img * bias
+    n1 = sigma * rng.normal(height * width).reshape(height, width)
+    n2 = sigma * rng.normal(height * width).reshape(height, width)
+    return np.clip(np.rint(np.sqrt((s + n1) ** 2 + n2 ** 2)), 0, 4095).astype(np.uint16)
+
+
 def phantom_volume(depth: int, height: int, width: int, seed: int) -> np.ndarray:
     """MRI-like volume (depth x height x width): 3..8 nested ellipsoids of
     random centre, axes, in-plane angle and intensity, times a smooth
@@ -244,7 +274,7 @@ def batch_images(count: int, seed: int, **size_kw):
     return [voronoi_image(h, w, seed * 131 + i + 1) for i, (h, w) in enumerate(sizes)]
 
 
-def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, window=(2, 2, 2)):
+def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, window=(2, 2, 2), levels: int = 256):
     """FP32 weights for which the network's PDF is a discretised Gaussian of
     standard deviation `sigma` grey levels around a linear prediction from the
     priors (the mean of the left and upper neighbours plus a gradient term),
@@ -273,7 +303,7 @@ def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, w
         carried = [i_upleft, i_up, i_left, i_below]
     n_in, h1, h2, n_out = widths
     nc = 2 * len(carried)
-    assert n_in == n and n_out == 256 and h1 >= nc and h2 >= nc and l >= 1
+    assert n_in == n and n_out == levels and h1 >= nc and h2 >= nc and l >= 1
     rng = Rng(seed)
     alpha = np.zeros(n)
     alpha[i_left] = 0.75      # left neighbour
@@ -292,14 +322,15 @@ def predictive_mlp(widths, seed: int, sigma: float = 6.0, noise: float = 0.02, w
     w2[:nc, :] = 0.0
     w2[:nc, :nc] = np.eye(nc)
     b2 = np.zeros(h2)
-    t = np.arange(256) / 128.0 - 1.0
-    beta = 1.0 / (2.0 * (sigma / 128.0) ** 2)
+    half = levels / 2.0   # inputs and output levels as v / half - 1
+    t = np.arange(levels) / half - 1.0
+    beta = 1.0 / (2.0 * (sigma / half) ** 2)
     pred = np.zeros(h2)
     for j, k in enumerate(carried):
         pred[2 * j] = alpha[k]
         pred[2 * j + 1] = -alpha[k]
     w3 = 2.0 * beta * t[:, None] * pred[None, :]
-    w3 += noise * rng.normal(256 * h2).reshape(256, h2)
+    w3 += noise * rng.normal(levels * h2).reshape(levels, h2)
     b3 = -beta * t * t
     return [(w1.astype(np.float32), b1.astype(np.float32)),
             (w2.astype(np.float32), b2.astype(np.float32)),
