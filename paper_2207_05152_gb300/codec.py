@@ -15,7 +15,10 @@ def _stream_handle(stream=None) -> int:
 
 class Codec:
     """One coder model on the current CUDA device (Sec. II-B: the same model
-    and the same arithmetic at encode and decode)."""
+    and the same arithmetic at encode and decode).  Images are uint8 tensors
+    for a model of 256 outputs; for a 12-bit model (4096 outputs, Sec. IV
+    "Higher Bit Depth") they are int16 (or uint16) tensors of values
+    0..4095, and decoded images come back as int16."""
 
     def __init__(self, blob: bytes, decode_plan: int = _lib.DLIC_PLAN_AUTO):
         if not torch.cuda.is_available():
@@ -23,6 +26,9 @@ class Codec:
         self.blob = bytes(blob)
         self.handle = _lib.dlic_model_create(self.blob)
         self.precision, self.h1, self.h2, self.hash = _lib.dlic_model_info(self.handle)
+        from .model import model_symbols
+        self.bits = 12 if model_symbols(self.blob) == 4096 else 8
+        self.dtype = torch.int16 if self.bits == 12 else torch.uint8
         if decode_plan != _lib.DLIC_PLAN_AUTO:
             _lib.dlic_model_set_decode_plan(self.handle, decode_plan)
         self._ws = None
@@ -44,15 +50,16 @@ class Codec:
             self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         return self._ws
 
-    @staticmethod
-    def _desc(imgs):
+    def _desc(self, imgs):
+        """(pointer, height, width, pitch in bytes) of each image."""
+        ok = (torch.uint8,) if self.bits == 8 else (torch.int16, getattr(torch, "uint16", torch.int16))
         out = []
         for t in imgs:
-            if t.dtype != torch.uint8 or t.dim() != 2 or not t.is_cuda:
-                raise ValueError("images must be 2-D uint8 CUDA tensors")
+            if t.dtype not in ok or t.dim() != 2 or not t.is_cuda:
+                raise ValueError(f"images must be 2-D {'uint8' if self.bits == 8 else 'int16'} CUDA tensors")
             if t.stride(1) != 1:
                 raise ValueError("image rows must be contiguous")
-            out.append((t.data_ptr(), t.shape[0], t.shape[1], t.stride(0)))
+            out.append((t.data_ptr(), t.shape[0], t.shape[1], t.stride(0) * t.element_size()))
         return out
 
     def capacity(self, shapes, streams=None) -> int:
@@ -93,7 +100,7 @@ class Codec:
         decoded uint8 tensors, int32 status tensor on the device)."""
         n = len(shapes)
         if outs is None:
-            outs = [torch.empty((h, w), dtype=torch.uint8, device="cuda") for h, w in shapes]
+            outs = [torch.empty((h, w), dtype=self.dtype, device="cuda") for h, w in shapes]
         if status is None:
             status = torch.empty(max(1, n), dtype=torch.int32, device="cuda")
         desc = self._desc(outs)
@@ -149,7 +156,8 @@ class Codec:
         return outs, status
 
     def decode_bytes(self, streams_bytes, shapes=None):
-        """Decodes host bitstreams; returns (list of uint8 host arrays, statuses)."""
+        """Decodes host bitstreams; returns (list of host arrays, statuses):
+        uint8 arrays, or uint16 arrays for a 12-bit model."""
         if shapes is None:
             shapes = []
             for b in streams_bytes:
@@ -161,4 +169,7 @@ class Codec:
         data = torch.frombuffer(bytearray(b"".join(streams_bytes) or b"\0"), dtype=torch.uint8).cuda()
         outs, status = self.decode(data, offs, shapes)
         torch.cuda.synchronize()
-        return [o.cpu().numpy() for o in outs], status[: len(shapes)].cpu().tolist()
+        host = [o.cpu().numpy() for o in outs]
+        if self.bits == 12:
+            host = [h.view("<u2") for h in host]
+        return host, status[: len(shapes)].cpu().tolist()

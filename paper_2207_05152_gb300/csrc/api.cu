@@ -100,7 +100,10 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         radius = le32(b + 24);
     }
     const uint32_t h1 = widths[0], h2 = widths[L - 1];
-    const bool deep = L != 2;   // the layer-table kernels
+    // 4096 outputs: 12-bit pixels (Sec. IV "Higher Bit Depth"), on the
+    // layer-table FP32 kernels like networks of other depths
+    const bool twelve = n_out == (uint32_t)kSymbols12;
+    const bool deep = L != 2 || twelve;   // the layer-table kernels
     if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
     // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16,
     // or a 3D window 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 | pl << 18 | pr << 22
@@ -129,8 +132,10 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     }
     const int n2 = wu * (wl + wr + 1) + wl;
     const int npri = n2 + (vol ? (pu + pd + 1) * (pl + pr + 1) : 0);
-    if (npri > kMaxPriors || (int)n_in != npri || n_out != kSymbols)
-        return fail(DLIC_ERR_INVALID, "model must map the %d priors of its window to 256 logits", npri);
+    if (npri > kMaxPriors || (int)n_in != npri || (n_out != kSymbols && !twelve))
+        return fail(DLIC_ERR_INVALID, "model must map the %d priors of its window to 256 (or 4096) logits", npri);
+    if (twelve && prec != DLIC_FP32)
+        return fail(DLIC_ERR_INVALID, "a 12-bit model (4096 outputs) has an FP32 network");
     for (int l = 0; l < L; l++)
         if (widths[l] > 4096) return fail(DLIC_ERR_INVALID, "hidden widths must be <= 4096");
     if (!deep) {
@@ -139,10 +144,11 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     } else {
         for (int l = 0; l < L; l++)
             if (widths[l] < 4 || widths[l] > kMaxHidden || widths[l] % 4)
-                return fail(DLIC_ERR_UNSUPPORTED, "hidden widths of a network of %d hidden layers must be multiples "
-                            "of 4 in [4, 256]", L);
+                return fail(DLIC_ERR_UNSUPPORTED, "hidden widths of a 12-bit network or of a network of %d hidden "
+                            "layers must be multiples of 4 in [4, 256]", L);
         if (radius != 2)
-            return fail(DLIC_ERR_UNSUPPORTED, "networks of other than two hidden layers run with the default window only");
+            return fail(DLIC_ERR_UNSUPPORTED, "12-bit networks and networks of other than two hidden layers run with "
+                                              "the default window only");
     }
     const float tscale = lef32(b + tscale_at);
     if (!(tscale > 0.0f)) return fail(DLIC_ERR_INVALID, "tscale must be positive");
@@ -156,7 +162,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     int din[kMaxLayers], dout[kMaxLayers], hmax = 0;
     for (int l = 0; l < nl; l++) {
         din[l] = l == 0 ? npri : (int)widths[l - 1];
-        dout[l] = l == nl - 1 ? kSymbols : (int)widths[l];
+        dout[l] = l == nl - 1 ? (int)n_out : (int)widths[l];
         if (l < L) hmax = std::max(hmax, (int)widths[l]);
     }
     const int k1 = (npri + 15) / 16 * 16;   // first-layer K of the tensor-core operands
@@ -179,6 +185,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.h2 = (int)h2;
     d.nl = nl;
     d.hmax = hmax;
+    d.bits = twelve ? 12 : 8;
     d.wu = wu;
     d.wl = wl;
     d.wr = wr;
@@ -359,7 +366,8 @@ extern "C" int dlic_auto_streams(int height, int width) {
     return s < 1 ? 1 : s;
 }
 
-static dlic_status check_images(const dlic_image *im, int n, const int *streams, bool writable) {
+// bps: bytes per sample, 1 (8-bit) or 2 (12-bit: u16 samples, 2-byte aligned rows)
+static dlic_status check_images(const dlic_image *im, int n, const int *streams, bool writable, int bps) {
     if (n < 0) return fail(DLIC_ERR_INVALID, "negative image count");
     if (n > 0 && !im) return fail(DLIC_ERR_INVALID, "null image array");
     for (int i = 0; i < n; i++) {
@@ -368,7 +376,10 @@ static dlic_status check_images(const dlic_image *im, int n, const int *streams,
             return fail(DLIC_ERR_INVALID, "image %d: empty image (%d x %d)", i, im[i].height, im[i].width);
         if (im[i].height > (1 << 20) || im[i].width > (1 << 20))
             return fail(DLIC_ERR_UNSUPPORTED, "image %d: dimension above 2^20", i);
-        if (im[i].pitch < im[i].width) return fail(DLIC_ERR_INVALID, "image %d: pitch < width", i);
+        if (im[i].pitch < (int64_t)bps * im[i].width)
+            return fail(DLIC_ERR_INVALID, "image %d: pitch < width x %d bytes", i, bps);
+        if (bps == 2 && ((reinterpret_cast<uintptr_t>(im[i].pixels) | (uintptr_t)im[i].pitch) & 1))
+            return fail(DLIC_ERR_INVALID, "image %d: 12-bit samples need 2-byte aligned pixels and an even pitch", i);
         if (streams && (streams[i] < 1 || streams[i] > 65535))
             return fail(DLIC_ERR_INVALID, "image %d: stream count %d outside [1, 65535]", i, streams[i]);
     }
@@ -408,7 +419,7 @@ static std::vector<EncItem> image_items(const dlic_image *im, int n, const int *
 extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
                                                   const int *streams, size_t *bytes) {
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
-    dlic_status st = check_images(im, n, streams, false);
+    dlic_status st = check_images(im, n, streams, false, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
     *bytes = enc_ws_bytes(image_items(im, n, streams));
     return DLIC_OK;
@@ -435,7 +446,7 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
     off += 256;
     uint8_t *out = static_cast<uint8_t *>(d_out);
     // networks of other than two hidden layers: the one-pixel-per-thread kernels
-    const bool use_tc = m->dev.nl == 3 && tc_supported(m->dev);
+    const bool use_tc = m->dev.nl == 3 && m->dev.bits == 8 && tc_supported(m->dev);
     const int tile_px = use_tc ? 128 : kPredictTile;
     {
         cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), cs);
@@ -475,7 +486,9 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
             off += align256(4ull * e.S);
         }
         b->total_tiles = tiles;
-        cudaError_t e = use_tc ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs) : launch_predict_cc(m->dev, *b, cs);
+        cudaError_t e = use_tc                  ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
+                        : m->dev.bits == 12 ? launch_predict12(m->dev, *b, cs)
+                                            : launch_predict_cc(m->dev, *b, cs);
         if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
         if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
         delete b;
@@ -489,7 +502,7 @@ extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, in
                                    int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {
     if (!m) return fail(DLIC_ERR_INVALID, "null model");
     if (m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 3D window: use dlic_encode_volume");
-    dlic_status st = check_images(im, n, streams, false);
+    dlic_status st = check_images(im, n, streams, false, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
     return encode_items(m, image_items(im, n, streams), d_out, out_capacity, d_out_offsets, d_status, d_ws, ws_bytes,
                         stream);
@@ -602,7 +615,7 @@ static std::vector<DecItem> dec_volume_items(const dlic_volume *v, int n) {
 extern "C" dlic_status dlic_decode_workspace_size(const dlic_model *m, const dlic_image *im, int n,
                                                   size_t *bytes) {
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
-    dlic_status st = check_images(im, n, nullptr, true);
+    dlic_status st = check_images(im, n, nullptr, true, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
     *bytes = dec_ws_bytes(dec_image_items(im, n));
     return DLIC_OK;
@@ -632,7 +645,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
     }
     const bool vol = m->dev.vol != 0;
-    const bool use_wave = m->dev.nl == 3 && wave_decode_supported(m->dev);
+    const bool use_wave = m->dev.nl == 3 && m->dev.bits == 8 && wave_decode_supported(m->dev);
     if (vol && !use_wave) return fail(DLIC_ERR_UNSUPPORTED, "volumes decode on the cluster wavefront kernels only");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     {
@@ -779,7 +792,9 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
             b->ws = static_cast<uint8_t *>(d_ws);
             b->status = d_status;
             for (int k = 0; k < cn; k++) fill(b->img[k], members[c0 + k]);
-            cudaError_t e = use_wave ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs) : launch_decode_cc(m->dev, *b, gs);
+            cudaError_t e = use_wave              ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs)
+                            : m->dev.bits == 12 ? launch_decode12(m->dev, *b, gs)
+                                                : launch_decode_cc(m->dev, *b, gs);
             delete b;
             if (e != cudaSuccess && err == DLIC_OK)
                 err = e == cudaErrorNotSupported ? fail(DLIC_ERR_UNSUPPORTED, "decode launch: no shared-memory plan fits")
@@ -803,7 +818,7 @@ extern "C" dlic_status dlic_decode(const dlic_model *m, const void *d_in, const 
                                    size_t ws_bytes, void *stream) {
     if (!m) return fail(DLIC_ERR_INVALID, "null model");
     if (m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 3D window: use dlic_decode_volume");
-    dlic_status st = check_images(im, n, nullptr, true);
+    dlic_status st = check_images(im, n, nullptr, true, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
     return decode_items(m, d_in, h_in_offsets, dec_image_items(im, n), d_status, d_ws, ws_bytes, stream);
 }

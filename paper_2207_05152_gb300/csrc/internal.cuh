@@ -12,6 +12,7 @@ namespace dlic {
 constexpr int kPriors = 12;        // priors of the default radius-2 causal window
 constexpr int kMaxPriors = 96;     // largest window: rows up <= 8, left reach <= 8, right reach <= 2
 constexpr int kSymbols = 256;      // 8-bit alphabet
+constexpr int kSymbols12 = 4096;   // 12-bit alphabet (Sec. IV "Higher Bit Depth")
 constexpr uint32_t kRansL = 1u << 16;
 constexpr uint32_t kTotal = 1u << 16;
 constexpr uint32_t kQuantTotal = 65280u;   // 2^16 - 256: mass shared out by the PDF
@@ -36,7 +37,8 @@ struct DevModel {
     // on the one-pixel-per-thread kernels from the layer table, whose widest
     // hidden layer has hmax units
     int nl, hmax;
-    const DevLayer *layers;       // device array of nl entries (other depths only)
+    const DevLayer *layers;       // device array of nl entries (other depths, 12-bit models)
+    int bits;                     // 8, or 12: u16 samples, 4096 outputs, FP32 layer-table kernels
     // causal window: rows r-wu..r-1 at columns c-wl..c+wr, then row r at
     // columns c-wl..c-1 (n2 priors in that order); (2, 2, 2) by default.
     // A 3D window (vol = 1) adds the previous slice's rows r-pu..r+pd at
@@ -128,6 +130,9 @@ cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st)
 // Decoders (coder_cc.cu: one CTA per image; decode_tc.cu: one cluster per
 // image, wavefront)
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
+// 12-bit pixels (coder12.cu): warp-per-pixel FP32 kernels over the layer table
+cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, cudaStream_t st);
+cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t st);
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)

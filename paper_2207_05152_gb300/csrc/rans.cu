@@ -139,7 +139,7 @@ __global__ void k_pack(DevModel m, EncBatch b, uint8_t *out, const uint64_t *out
         else if (tid < 8) v = (uint8_t)((uint32_t)im.H >> (8 * (tid - 4)));
         else if (tid < 12) v = (uint8_t)((uint32_t)im.W >> (8 * (tid - 8)));
         else if (tid == 12) v = (uint8_t)(m.wu | (m.vol ? 0x80 : 0));   // window rows above; bit 7: a volume's slice
-        else if (tid == 13) v = (uint8_t)m.precision;
+        else if (tid == 13) v = (uint8_t)(m.precision | (m.bits == 12 ? 0x10 : 0));   // bit 4: 12-bit pixels
         else if (tid < 16) v = (uint8_t)((uint32_t)S >> (8 * (tid - 14)));
         else v = (uint8_t)(m.hash >> (8 * (tid - 16)));
         o[tid] = v;

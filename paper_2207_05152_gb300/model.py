@@ -172,6 +172,12 @@ def fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
     return b"".join(out)
 
 
+def model_symbols(blob: bytes) -> int:
+    """Output neurons of a "DLM1" or "DLM2" blob: 256 (8-bit pixels) or 4096."""
+    off = 48 if bytes(blob[:4]) == DEEP_MAGIC else 20
+    return struct.unpack_from("<I", blob, off)[0]
+
+
 def fp32_blob12(layers) -> bytes:
     """Blob of an FP32 network for 12-bit pixels, [(W1, b1), (W2, b2),
     (W3, b3)] with 4096 outputs, over the default window."""
@@ -244,11 +250,11 @@ DEEP_HEADER_BYTES = 320
 MAX_HIDDEN_LAYERS = 8
 
 
-def _deep_header(precision: int, widths, window) -> bytes:
+def _deep_header(precision: int, widths, window, n_out: int = N_OUT) -> bytes:
     L = len(widths)
     hdr = DEEP_MAGIC + struct.pack("<3I", precision, window_size(window), L)
     hdr += struct.pack("<8I", *(list(widths) + [0] * (MAX_HIDDEN_LAYERS - L)))
-    hdr += struct.pack("<2IfI", N_OUT, window_field(window), float(TSCALE), 0)
+    hdr += struct.pack("<2IfI", n_out, window_field(window), float(TSCALE), 0)
     hdr += table_lut().astype("<u4").tobytes()
     assert len(hdr) == DEEP_HEADER_BYTES
     return hdr
@@ -266,15 +272,15 @@ def _check_deep(layers, window):
             if not 1 <= n <= 4096:
                 raise ValueError("hidden widths must be in [1, 4096]")
             widths.append(n)
-    if n != N_OUT:
-        raise ValueError("the output layer has 256 units")
+    if n not in (N_OUT, N_OUT_12):
+        raise ValueError("the output layer has 256 units (4096 for 12-bit pixels)")
     return widths
 
 
 def deep_fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
     """"DLM2" blob of an FP32 network [(W1, b1), ..., (W_out, b_out)] of
-    1..8 hidden layers."""
-    out = [_deep_header(PREC_FP32, _check_deep(layers, window), window)]
+    1..8 hidden layers (256 outputs, or 4096 for 12-bit pixels)."""
+    out = [_deep_header(PREC_FP32, _check_deep(layers, window), window, layers[-1][0].shape[0])]
     for w, b in layers:
         out.append(np.ascontiguousarray(w, dtype="<f4").tobytes())
         out.append(np.ascontiguousarray(b, dtype="<f4").tobytes())
@@ -284,6 +290,8 @@ def deep_fp32_blob(layers, window=DEFAULT_WINDOW) -> bytes:
 def deep_int8_blob(layers, calib_ctx: np.ndarray, window=DEFAULT_WINDOW) -> bytes:
     """"DLM2" blob of the INT8 quantisation (the rules of int8_blob) of a
     network of 1..8 hidden layers."""
+    if layers[-1][0].shape[0] != N_OUT:
+        raise ValueError("an INT8 network has 256 outputs (8-bit pixels)")
     out = [_deep_header(PREC_INT8, _check_deep(layers, window), window)]
     for wq, s, o in _quantise(layers, calib_ctx):
         out.append(wq.tobytes())

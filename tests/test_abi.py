@@ -112,3 +112,36 @@ def test_deeper_network_blobs_are_checked_before_any_device_call(lib):
         with pytest.raises(lib.DlicError) as e:
             lib.dlic_model_create(blob)
         assert e.value.code == code, (len(blob), e.value)
+
+
+def test_twelve_bit_blobs_are_checked_before_any_device_call(lib):
+    # 4096 outputs (12-bit pixels): FP32 only, the default window, hidden
+    # widths multiples of 4 up to 256
+    import struct
+    import synth
+    from paper_2207_05152_gb300 import model as M
+
+    def net(widths, window=M.DEFAULT_WINDOW, seed=6):
+        rng = synth.Rng(seed)
+        dims = [M.window_size(window)] + widths + [4096]
+        return [((0.1 * rng.normal(o * i)).reshape(o, i).astype(np.float32), np.zeros(o, np.float32))
+                for i, o in zip(dims[:-1], dims[1:])]
+
+    i8 = [M._header(M.PREC_INT8, 32, 32, M.DEFAULT_WINDOW, 4096)]
+    for o, i in ((32, 12), (32, 32), (4096, 32)):
+        i8 += [np.zeros((o, i), np.int8).tobytes(), np.ones(o, "<f4").tobytes(), np.zeros(o, "<f4").tobytes()]
+    cases = [
+        (b"".join(i8), lib.DLIC_ERR_INVALID),                                        # INT8, 4096 outputs
+        (M.deep_fp32_blob(net([32, 32], (3, 3, 2)), (3, 3, 2)), lib.DLIC_ERR_UNSUPPORTED),   # another window
+        (M.deep_fp32_blob(net([32, 6])), lib.DLIC_ERR_UNSUPPORTED),                 # width not a multiple of 4
+        (M.deep_fp32_blob(net([32, 512])), lib.DLIC_ERR_UNSUPPORTED),               # width above 256
+    ]
+    good = M.fp32_blob12(net([32, 32]))
+    bad_out = bytearray(good)
+    bad_out[20:24] = struct.pack("<I", 1024)                                         # neither 256 nor 4096
+    cases.append((bytes(bad_out), lib.DLIC_ERR_INVALID))
+    cases.append((good[:-4], lib.DLIC_ERR_INVALID))
+    for blob, code in cases:
+        with pytest.raises(lib.DlicError) as e:
+            lib.dlic_model_create(blob)
+        assert e.value.code == code, (len(blob), e.value)
