@@ -23,6 +23,8 @@ static_assert(k12Tile == kPredictTile, "the encoder plans CUDA-core tiles of kPr
 constexpr uint64_t k12Slack = kTotal - kSymbols12;     // 2^16 - 4096: the table's free mass
 constexpr int k12InPitch = 16;                         // encoder: floats per pixel of the input rows
 constexpr int k12PerLane = kSymbols12 / 32;            // decoder: consecutive values each lane searches
+constexpr int k12Chains = 8;                           // decoder: logits each lane computes side by side
+static_assert(kSymbols12 % (32 * k12Chains) == 0, "the logit loop covers the values in whole steps");
 
 __device__ __forceinline__ uint32_t px12(const uint8_t *img, int64_t pitch, int r, int c) {
     return *reinterpret_cast<const uint16_t *>(img + (int64_t)r * pitch + 2 * (int64_t)c);
@@ -273,13 +275,24 @@ __global__ void __launch_bounds__(k12Threads) k_decode12(DevModel m, DecBatch b)
                     hin = hout;
                     hout = hout == hA ? hB : hA;
                 }
-                // logits and their maximum
+                // logits and their maximum: each lane runs eight values'
+                // chains side by side (values i, i + 32, ..., i + 224)
                 float mx = -INFINITY;
-                for (int i = lane; i < kSymbols12; i += 32) {
-                    float acc = __ldg(lo.a + i);
-                    for (int k = 0; k < lo.n_in; k++) acc = __fmaf_rn(hin[k], __ldg(wo + (size_t)k * kSymbols12 + i), acc);
-                    zs[i] = acc;
-                    mx = acc > mx ? acc : mx;
+                for (int i = lane; i < kSymbols12; i += 32 * k12Chains) {
+                    float acc[k12Chains];
+#pragma unroll
+                    for (int j = 0; j < k12Chains; j++) acc[j] = __ldg(lo.a + i + 32 * j);
+                    for (int k = 0; k < lo.n_in; k++) {
+                        const float hk = hin[k];
+                        const float *wk = wo + (size_t)k * kSymbols12 + i;
+#pragma unroll
+                        for (int j = 0; j < k12Chains; j++) acc[j] = __fmaf_rn(hk, __ldg(wk + 32 * j), acc[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < k12Chains; j++) {
+                        zs[i + 32 * j] = acc[j];
+                        mx = acc[j] > mx ? acc[j] : mx;
+                    }
                 }
                 mx = warp_max(mx);
                 __syncwarp();
