@@ -57,9 +57,12 @@ enum { DLIC_FP32 = 0, DLIC_INT8 = 1 };
 typedef struct dlic_model dlic_model;
 typedef struct dlic_trainer dlic_trainer;
 
-/* One 8-bit grayscale image in device memory: row r starts at
- * pixels + r * pitch; pitch >= width.  dlic_encode only reads the pixels,
- * dlic_decode writes them. */
+/* One grayscale image in device memory: row r starts at pixels + r * pitch
+ * (pitch in bytes).  With a model of 256 outputs the samples are 8-bit
+ * (uint8_t, pitch >= width); with a model of 4096 outputs (12-bit pixels,
+ * Sec. IV "Higher Bit Depth") they are uint16_t values 0..4095, pixels
+ * 2-byte aligned, pitch even and >= 2 * width.  dlic_encode only reads the
+ * pixels, dlic_decode writes them. */
 typedef struct {
     uint8_t *pixels;
     int32_t height;
@@ -117,6 +120,11 @@ DLIC_API const char *dlic_last_error(void);
  * kernels.  Other L run on the CUDA-core one-pixel-per-thread encoder and
  * decoder, with the default window only and hidden widths that are
  * multiples of 4 in [4, 256] (DLIC_ERR_UNSUPPORTED otherwise).
+ * 12-bit pixels (Sec. IV "Higher Bit Depth"): n_out = 4096 in either blob,
+ * an FP32 network (DLIC_ERR_INVALID for INT8), network inputs v / 2048 - 1,
+ * the frequency tables of 2^16 with 4096 values (each f >= 1); the default
+ * window and hidden widths that are multiples of 4 in [4, 256]
+ * (DLIC_ERR_UNSUPPORTED otherwise); CUDA-core warp-per-pixel kernels.
  * The blob is copied; the model owns device copies of the weights in the
  * layouts the kernels use.
  * The model hash (FNV-1a 64 of the blob) is written into every bitstream and
@@ -238,7 +246,8 @@ DLIC_API dlic_status dlic_encode_noalloc(const dlic_model *model, const dlic_ima
 
 /* Parses a bitstream header held in host memory (at least 24 bytes): a 2D
  * image's container or one slice's container of a volume (byte 12 with bit
- * 7 set); DLIC_ERR_CORRUPT when it is neither. */
+ * 7 set); DLIC_ERR_CORRUPT when it is neither.  precision receives header
+ * byte 13: the model's precision, with bit 4 (0x10) set for 12-bit pixels. */
 DLIC_API dlic_status dlic_read_header(const void *h_bitstream, size_t bytes, int *height, int *width,
                              int *streams, int *precision, uint64_t *model_hash);
 
