@@ -65,6 +65,50 @@ def sample_window_contexts(images, count: int, seed: int, window):
     priors outside an image or the volume are 0."""
     import synth
     idx, rr, cc = synth.sample_positions(images, count, seed)
+    return _contexts_at(images, idx, rr, cc, window)
+
+
+def rare_value_positions(images, count: int, seed: int, alpha: float = 1.0):
+    """`count` (image, row, col) triples drawn with probability proportional
+    to hist(v)^-alpha, v the pixel's value and hist the value histogram over
+    all the images (Sec. IV "Color Frequencies": rare values upsampled into
+    the training set).  alpha = 1 draws every value present equally often;
+    alpha = 0 is the uniform draw over pixels."""
+    import synth
+    flat = np.concatenate([im.reshape(-1) for im in images])
+    hist = np.bincount(flat, minlength=256).astype(np.float64)
+    w = hist[flat] ** -float(alpha)
+    cum = np.cumsum(w)
+    u = synth.Rng(seed).uniform(count) * cum[-1]
+    pick = np.minimum(np.searchsorted(cum, u, side="right"), flat.size - 1)
+    sizes = np.array([im.size for im in images], dtype=np.int64)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    idx = np.searchsorted(starts, pick, side="right") - 1
+    rem = pick - starts[idx]
+    widths = np.array([im.shape[1] for im in images], dtype=np.int64)
+    return idx, rem // widths[idx], rem % widths[idx]
+
+
+def sample_upsampled_contexts(images, count: int, seed: int, window=M.DEFAULT_WINDOW, share: float = 0.25,
+                              alpha: float = 1.0):
+    """Training contexts with rare values upsampled (Sec. IV "Color
+    Frequencies"): round(share * count) positions from rare_value_positions,
+    the rest uniform (sample_window_contexts with the same seed), the
+    upsampled ones last.  Drawing a context k times as often weights its
+    loss term k-fold in expectation, so this one sampler also stands for the
+    paper's frequency-weighted loss; share = 0 gives the uniform sampler's
+    output exactly."""
+    n_up = int(round(share * count))
+    ctx, tgt = sample_window_contexts(images, count - n_up, seed, window)
+    if n_up == 0:
+        return ctx, tgt
+    idx, rr, cc = rare_value_positions(images, n_up, seed + 0x5EED, alpha)
+    c2, t2 = _contexts_at(images, idx, rr, cc, window)
+    return np.concatenate([ctx, c2]), np.concatenate([tgt, t2])
+
+
+def _contexts_at(images, idx, rr, cc, window):
+    count = idx.size
     offs = M.window_offsets3(window)
     ctx = np.zeros((count, len(offs)), np.uint8)
     tgt = np.zeros(count, np.uint8)
