@@ -3,6 +3,8 @@
     python -m paper_2207_05152_gb300.profile_case --case cfg2 --iters 2
     python -m paper_2207_05152_gb300.profile_case --case cfg4 --count 8 --iters 1
     python -m paper_2207_05152_gb300.profile_case --case volume --iters 1
+    python -m paper_2207_05152_gb300.profile_case --case deep --size 128 --iters 1
+    python -m paper_2207_05152_gb300.profile_case --case twelve --size 64 --iters 1
 
 Each iteration encodes and decodes the batch and checks the round trip.
 """
@@ -19,7 +21,8 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4", "volume"])
+    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4", "volume", "deep", "twelve"])
+    ap.add_argument("--size", type=int, default=128, help="deep / twelve: the square image's side")
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--count", type=int, default=8)
     ap.add_argument("--precision", default="int8", choices=["int8", "fp32"])
@@ -42,6 +45,30 @@ def main():
             torch.cuda.synchronize()
             assert int(status[0].item()) == 0 and torch.equal(dec[0], dv)
         print("ok volume", vol.shape)
+        return
+    if args.case in ("deep", "twelve"):
+        # six dense layers (five hidden, widths 128) on an 8-bit crop of the
+        # cfg-2 image, or a 12-bit MRI-like slice with 12-128-128-4096
+        import numpy as np
+        import synth
+        from paper_2207_05152_gb300 import model as M
+        n = args.size
+        if args.case == "deep":
+            deep8, deep32 = workloads.deep_models()
+            codec = Codec(deep8 if args.precision == "int8" else deep32)
+            img = np.ascontiguousarray(workloads.cfg2_image()[:n, :n])
+            dv = torch.from_numpy(img).cuda()
+        else:
+            codec = Codec(M.fp32_blob12(synth.predictive_mlp([12, 128, 128, 4096], 12, sigma=96.0, levels=4096)))
+            img = synth.phantom_image12(n, n, 12)
+            dv = torch.from_numpy(img.astype(np.int16)).cuda()
+        for _ in range(args.iters):
+            out, offs = codec.encode([dv], [min(n, 96)])
+            o = offs.cpu().tolist()
+            dec, status = codec.decode(out, o, [img.shape])
+            torch.cuda.synchronize()
+            assert int(status[0].item()) == 0 and torch.equal(dec[0], dv)
+        print("ok", args.case, img.shape)
         return
     _, blob8, blob32 = workloads.models()
     imgs = [workloads.cfg2_image()] if args.case == "cfg2" else workloads.cfg4_images(args.count)
