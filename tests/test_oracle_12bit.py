@@ -139,3 +139,32 @@ def test_refusals(orc):
     flag[13] = 0                                  # the 12-bit flag cleared
     st, _ = orc.decode(blob, bytes(flag), 9, 11)
     assert st == 3
+
+
+def test_deeper_12bit_network_in_the_dlm2_blob(orc):
+    # three hidden layers and 4096 outputs: the "DLM2" header fields, float64
+    # logits with inputs v / 2048 - 1, and a round trip
+    rng = synth.Rng(17)
+    dims = [12, 40, 24, 56, 4096]
+    layers = [((rng.normal(o * i).reshape(o, i) * np.sqrt(2.0 / i)).astype(np.float32),
+               (0.05 * rng.normal(o)).astype(np.float32)) for i, o in zip(dims[:-1], dims[1:])]
+    blob = M.deep_fp32_blob(layers)
+    assert blob[:4] == b"DLM2" and M.model_symbols(blob) == 4096 and orc.symbols(blob) == 4096
+    prec, n_in, L = struct.unpack_from("<3I", blob, 4)
+    widths = struct.unpack_from("<8I", blob, 16)
+    assert (prec, n_in, L) == (0, 12, 3) and widths == (40, 24, 56, 0, 0, 0, 0, 0)
+    assert struct.unpack_from("<I", blob, 48)[0] == 4096
+    pri = synth.Rng(18).integers(60, 0, 4096).reshape(5, 12).astype(np.uint16)
+    z = orc.logits(blob, pri)
+    x = pri.astype(np.float64) / 2048.0 - 1.0
+    for li, (w, b) in enumerate(layers):
+        x = x @ w.astype(np.float64).T + b
+        if li < len(layers) - 1:
+            x = np.maximum(x, 0.0)
+    assert np.max(np.abs(z - x)) <= 1e-5 * np.abs(x).max()
+    img = synth.phantom_image12(14, 19, 2)
+    data = orc.encode(blob, img, 3)
+    st, dec = orc.decode(blob, data, 14, 19)
+    assert st == 0 and np.array_equal(dec, img)
+    with pytest.raises(ValueError):   # INT8 with 4096 outputs has no blob
+        M.deep_int8_blob(layers, np.zeros((4, 12), np.uint8))
