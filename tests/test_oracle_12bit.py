@@ -168,3 +168,28 @@ def test_deeper_12bit_network_in_the_dlm2_blob(orc):
     assert st == 0 and np.array_equal(dec, img)
     with pytest.raises(ValueError):   # INT8 with 4096 outputs has no blob
         M.deep_int8_blob(layers, np.zeros((4, 12), np.uint8))
+
+
+def test_twelve_bit_volume_round_trip(orc):
+    # the paper's MRI setting: 12-bit slices with a 3D window (Sec. IV); a
+    # model whose lower-layer weights are zero codes every slice like the 2D
+    # model of the same other weights (the lower layer only adds zero terms)
+    win3 = M.VOLUME_WINDOW
+    n3 = M.window_size(win3)
+    rng = synth.Rng(31)
+    w1 = (rng.normal(32 * n3).reshape(32, n3) * 0.2).astype(np.float32)
+    w1[:, 12:] = 0.0
+    rest = [((rng.normal(32 * 32).reshape(32, 32) * 0.2).astype(np.float32), np.zeros(32, np.float32)),
+            ((rng.normal(4096 * 32).reshape(4096, 32) * 0.2).astype(np.float32), np.zeros(4096, np.float32))]
+    b1 = np.zeros(32, np.float32)
+    blob3 = M.deep_fp32_blob([(w1, b1)] + rest, win3)
+    blob2 = M.deep_fp32_blob([(np.ascontiguousarray(w1[:, :12]), b1)] + rest)
+    vol = np.stack([synth.phantom_image12(11, 13, 40 + z) for z in range(3)])
+    data, offs = orc.encode_volume(blob3, vol, 4)
+    st, dec = orc.decode_volume(blob3, data, offs, 3, 11, 13)
+    assert st == 0 and dec.dtype == np.uint16 and np.array_equal(dec, vol)
+    for z in range(3):
+        sl = data[offs[z]:offs[z + 1]]
+        flat = orc.encode(blob2, vol[z], 4)
+        assert sl[12] == 2 | 0x80 and sl[13] == 0x10
+        assert sl[24:] == flat[24:]                 # the payload: identical
