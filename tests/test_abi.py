@@ -145,3 +145,19 @@ def test_twelve_bit_blobs_are_checked_before_any_device_call(lib):
         with pytest.raises(lib.DlicError) as e:
             lib.dlic_model_create(blob)
         assert e.value.code == code, (len(blob), e.value)
+
+
+def test_read_header_of_a_twelve_bit_container(lib, orc):
+    # the host-side header parse: byte 13 carries the precision with bit 4
+    # set for 12-bit pixels
+    import synth
+    from paper_2207_05152_gb300 import model as M
+    blob = M.fp32_blob12(synth.predictive_mlp([12, 32, 32, 4096], 3, sigma=96.0, levels=4096))
+    img = synth.phantom_image12(9, 14, 2)
+    data = orc.encode(blob, img, 3)
+    h = lib.dlic_read_header(data)
+    assert (h["height"], h["width"], h["streams"], h["precision"]) == (9, 14, 3, 0x10)
+    assert h["hash"] == orc.fnv1a64(blob)
+    with pytest.raises(lib.DlicError) as e:
+        lib.dlic_read_header(b"DLC2" + data[4:])
+    assert e.value.code == lib.DLIC_ERR_CORRUPT
