@@ -61,8 +61,9 @@ typedef struct dlic_trainer dlic_trainer;
  * (pitch in bytes).  With a model of 256 outputs the samples are 8-bit
  * (uint8_t, pitch >= width); with a model of 4096 outputs (12-bit pixels,
  * Sec. IV "Higher Bit Depth") they are uint16_t values 0..4095, pixels
- * 2-byte aligned, pitch even and >= 2 * width.  dlic_encode only reads the
- * pixels, dlic_decode writes them. */
+ * 2-byte aligned, pitch even and >= 2 * width (a sample above 4095 is not
+ * checked on the device: its bitstream does not decode to it).  dlic_encode
+ * only reads the pixels, dlic_decode writes them. */
 typedef struct {
     uint8_t *pixels;
     int32_t height;
