@@ -61,9 +61,9 @@ typedef struct dlic_trainer dlic_trainer;
  * (pitch in bytes).  With a model of 256 outputs the samples are 8-bit
  * (uint8_t, pitch >= width); with a model of 4096 outputs (12-bit pixels,
  * Sec. IV "Higher Bit Depth") they are uint16_t values 0..4095, pixels
- * 2-byte aligned, pitch even and >= 2 * width (a sample above 4095 is not
- * checked on the device: its bitstream does not decode to it).  dlic_encode
- * only reads the pixels, dlic_decode writes them. */
+ * 2-byte aligned, pitch even and >= 2 * width; dlic_encode refuses an
+ * image with a sample above 4095 by writing DLIC_ERR_INVALID to its status
+ * word).  dlic_encode only reads the pixels, dlic_decode writes them. */
 typedef struct {
     uint8_t *pixels;
     int32_t height;
@@ -161,6 +161,20 @@ DLIC_API dlic_status dlic_model_destroy(dlic_model *model);
 enum { DLIC_PLAN_AUTO = 0, DLIC_PLAN_BYTE_RING = 1, DLIC_PLAN_IMAGE = 2, DLIC_PLAN_GRID = 3 };
 DLIC_API dlic_status dlic_model_set_decode_plan(dlic_model *model, int plan);
 
+/* How long (in SM clock cycles) the wavefront decoders of this model wait
+ * for another CTA before giving up: a pixel that a neighbouring CTA of the
+ * cluster pushes into the tagged ring, or the grid-wide wave barrier of
+ * DLIC_PLAN_GRID.  The default, 4e9 cycles (about 2 s), is restored by
+ * cycles <= 0.  A wait that runs out makes the decoder stop waiting for the
+ * rest of the call, finish every wave without further waits on other CTAs
+ * (still waiting for its own tensor-core work and bulk copies, which always
+ * complete), and report DLIC_ERR_TIMEOUT in the image's d_status; the
+ * decoded pixels are then invalid and the device stays usable.  A limit of a
+ * few hundred cycles makes such waits run out on purpose, which is how the
+ * error path is tested.  Not part of the paper's method: a diagnostic of
+ * this library.  Applies to later decode calls with this model. */
+DLIC_API dlic_status dlic_model_set_peer_wait_limit(dlic_model *model, long long cycles);
+
 /* Precision tag, first and last hidden widths and hash of a model. */
 DLIC_API dlic_status dlic_model_info(const dlic_model *model, int *precision, int *h1, int *h2,
                             uint64_t *hash);
@@ -196,9 +210,10 @@ DLIC_API dlic_status dlic_encode_workspace_size(const dlic_model *model, const d
  *                 batch (checked on the host: DLIC_ERR_CAPACITY).
  *  d_out_offsets: n + 1 u64 byte offsets written by the device; bitstream i
  *                 occupies [d_out_offsets[i], d_out_offsets[i + 1]).
- *  d_status:      one int32 on the device, or NULL; receives DLIC_OK, or
- *                 DLIC_ERR_TIMEOUT if a tensor-core wait ran out (the output
- *                 is then invalid).
+ *  d_status:      one int32 on the device, or NULL; receives DLIC_OK,
+ *                 DLIC_ERR_TIMEOUT if a tensor-core wait ran out, or
+ *                 DLIC_ERR_INVALID if a 12-bit sample exceeds 4095 (the
+ *                 output is then invalid).
  *  d_workspace:   at least dlic_encode_workspace_size bytes, 256-aligned.
  * Bitstream layout (little-endian): "DLC1", u32 height, u32 width,
  * u8 window rows u (2 for the default window), u8 precision, u16 S, u64
@@ -229,9 +244,10 @@ DLIC_API dlic_status dlic_encode(const dlic_model *model, const dlic_image *h_im
  * the output bitstreams are identical.  A batch whose workspace
  * (dlic_encode_workspace_size) exceeds the block is rejected with
  * DLIC_ERR_CAPACITY before anything is enqueued.
- *  - The first call on a device looks up the block's device address with
- *    that device current (a host-side lookup, no allocation); make that
- *    first call before any stream capture.
+ *  - Every call looks up the block's device address on the current device
+ *    (a host-side query, no allocation).  The first lookup on a device may
+ *    load the library's device code there; make the first call on each
+ *    device before any stream capture.
  *  - All calls share the one block and it keeps the previous call's data.
  *    Nothing in it needs to start at zero: each call writes every word it
  *    reads before reading it.  Calls whose work overlaps on the GPU (two
@@ -375,6 +391,18 @@ DLIC_API dlic_status dlic_train_backward(dlic_trainer *trainer, const uint8_t *d
 /* Forward, backward and one Adam update of the master weights. */
 DLIC_API dlic_status dlic_train_step(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
                                      float *d_loss_bits, void *stream);
+
+/* One Adam update of the master weights (and their bf16 operand copies)
+ * with a gradient the caller supplies: d_grads (device, in the parameter
+ * layout of dlic_train_param_count floats).  With data-parallel training
+ * over several GPUs each rank computes its batch's gradient with
+ * dlic_train_backward, the ranks average them (weighted by batch size) with
+ * one all-reduce, and every rank applies the same average here, so the
+ * replicas stay identical (Sec. III-A: the network is trained on the loss in
+ * bits; data parallelism is this library's way of spreading that work).
+ * dlic_train_backward followed by dlic_train_apply of its own gradient is
+ * exactly dlic_train_step. */
+DLIC_API dlic_status dlic_train_apply(dlic_trainer *trainer, const float *d_grads, void *stream);
 
 /* Copies the FP32 master weights out of (write = 0) or into (write = 1) the
  * trainer; d_params is a device buffer of dlic_train_param_count floats. */

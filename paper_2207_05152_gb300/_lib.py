@@ -48,6 +48,7 @@ SIGNATURES = {
     "dlic_model_create": (_I, [_VP, _SZ, C.POINTER(_VP)]),
     "dlic_model_destroy": (_I, [_VP]),
     "dlic_model_set_decode_plan": (_I, [_VP, _I]),
+    "dlic_model_set_peer_wait_limit": (_I, [_VP, C.c_longlong]),
     "dlic_model_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_uint64)]),
     "dlic_max_encoded_bytes": (_SZ, [_I, _I, _I]),
     "dlic_auto_streams": (_I, [_I, _I]),
@@ -68,6 +69,7 @@ SIGNATURES = {
     "dlic_train_forward": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "dlic_train_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "dlic_train_step": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    "dlic_train_apply": (_I, [_VP, _VP, _VP]),
     "dlic_trainer_params": (_I, [_VP, _VP, _I, _VP]),
     "dlic_trainer_status": (_I, [_VP, C.POINTER(C.c_int32)]),
 }
@@ -131,6 +133,10 @@ def dlic_model_destroy(model: int):
 
 def dlic_model_set_decode_plan(model: int, plan: int):
     check(lib().dlic_model_set_decode_plan(model, plan))
+
+
+def dlic_model_set_peer_wait_limit(model: int, cycles: int):
+    check(lib().dlic_model_set_peer_wait_limit(model, int(cycles)))
 
 
 def dlic_model_info(model: int):
@@ -258,6 +264,10 @@ def dlic_train_backward(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: in
 
 def dlic_train_step(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, stream: int = 0):
     check(lib().dlic_train_step(trainer, d_ctx, d_tgt, B, d_loss, stream or None))
+
+
+def dlic_train_apply(trainer: int, d_grads: int, stream: int = 0):
+    check(lib().dlic_train_apply(trainer, d_grads, stream or None))
 
 
 def dlic_trainer_params(trainer: int, d_params: int, write: bool, stream: int = 0):

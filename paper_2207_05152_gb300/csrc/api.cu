@@ -198,6 +198,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     d.pr = pr;
     d.tscale = tscale;
     d.hash = fnv1a64(b, n);
+    d.peer_wait_limit = kDefaultPeerWaitLimit;
     size_t off_lut = put(lut, sizeof(lut));
     // offs[3 l .. 3 l + 2]: layer l's weights and its bias (FP32) or scale
     // and offset (INT8); offs[3 kMaxLayers]: the tensor-core operand image
@@ -327,6 +328,12 @@ extern "C" dlic_status dlic_model_set_decode_plan(dlic_model *m, int plan) {
     if (plan != DLIC_PLAN_AUTO && plan != DLIC_PLAN_BYTE_RING && plan != DLIC_PLAN_IMAGE && plan != DLIC_PLAN_GRID)
         return fail(DLIC_ERR_INVALID, "unknown decode plan %d", plan);
     m->decode_plan = plan;
+    return DLIC_OK;
+}
+
+extern "C" dlic_status dlic_model_set_peer_wait_limit(dlic_model *m, long long cycles) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    m->dev.peer_wait_limit = cycles > 0 ? cycles : kDefaultPeerWaitLimit;
     return DLIC_OK;
 }
 
@@ -487,7 +494,7 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
         }
         b->total_tiles = tiles;
         cudaError_t e = use_tc                  ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
-                        : m->dev.bits == 12 ? launch_predict12(m->dev, *b, cs)
+                        : m->dev.bits == 12 ? launch_predict12(m->dev, *b, err, cs)
                                             : launch_predict_cc(m->dev, *b, cs);
         if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
         if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
@@ -644,6 +651,10 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         if (h_in_offsets[i + 1] < h_in_offsets[i]) return fail(DLIC_ERR_INVALID, "offsets must not decrease");
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
     }
+    // stream read positions are 32-bit counts of 16-bit words
+    if (h_in_offsets[n] >= (1ull << 33))
+        return fail(DLIC_ERR_INVALID, "input of %llu bytes: at most 8 GiB per decode call",
+                    (unsigned long long)h_in_offsets[n]);
     const bool vol = m->dev.vol != 0;
     const bool use_wave = m->dev.nl == 3 && m->dev.bits == 8 && wave_decode_supported(m->dev);
     if (vol && !use_wave) return fail(DLIC_ERR_UNSUPPORTED, "volumes decode on the cluster wavefront kernels only");

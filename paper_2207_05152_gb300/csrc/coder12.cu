@@ -69,7 +69,7 @@ __host__ __device__ inline size_t predict12_warp_floats(int hmax) {
     return (size_t)k12PixPerWarp * k12InPitch + 2 * (size_t)k12PixPerWarp * hmax;
 }
 
-__global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b) {
+__global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b, int *err) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut2[kTableSteps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b
     for (int p = 0; p < k12PixPerWarp; p++) {
         const uint64_t Wt = warp_sum64(wl[p]), Ps = warp_sum64(pl[p]), Wsym = warp_sum64(ws[p]);
         if (lane == p && p0 + p < npx) {
+            // a sample above 4095 has no table entry: the image is refused
+            if (sym[p] >= (uint32_t)kSymbols12) atomicCAS(err, DLIC_OK, DLIC_ERR_INVALID);
             const uint64_t Q = table_q12(Wt);
             const uint32_t c_lo = sym[p] + (uint32_t)((Ps * Q) >> 32);
             const uint32_t c_hi =
@@ -367,13 +369,13 @@ __global__ void __launch_bounds__(k12Threads) k_decode12(DevModel m, DecBatch b)
     if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
 }
 
-cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, cudaStream_t st) {
+cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cudaStream_t st) {
     if (b.total_tiles == 0) return cudaSuccess;
     if (m.bits != 12 || m.precision != DLIC_FP32 || !default_window(m) || !m.layers) return cudaErrorNotSupported;
     const size_t sm = 4ull * k12Warps * predict12_warp_floats(m.hmax);
     cudaError_t e = cudaFuncSetAttribute(k_predict12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_predict12<<<b.total_tiles, k12Threads, sm, st>>>(m, b);
+    k_predict12<<<b.total_tiles, k12Threads, sm, st>>>(m, b, err);
     return cudaGetLastError();
 }
 

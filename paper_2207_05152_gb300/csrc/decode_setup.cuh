@@ -47,14 +47,19 @@ __device__ inline bool decode_setup(const DevModel &m, const DecImage &im, const
     // block-wide exclusive scan of the word counts (chunked per thread)
     const int per = (S + nth - 1) / nth;
     const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
-    uint32_t sum = 0;
+    // 64-bit sums: no count, and no thread's share of the counts, may exceed
+    // the input's word count (the host keeps that below 2^32), so the 32-bit
+    // prefix sums below are exact for every header that passes
+    const uint64_t max_words = im.in_bytes / 2;
+    uint64_t sum = 0;
     int bad = 0;
     for (int s = s0; s < s1; s++) {
         const uint32_t c = rd_le32(cnt + 4 * s);
         bad |= c < 2;
         sum += c;
     }
-    s_part[tid] = sum;
+    bad |= sum > max_words;
+    s_part[tid] = (uint32_t)sum;
     if (bad) s_ok = 0;
     __syncthreads();
     if (tid == 0) {

@@ -243,7 +243,7 @@ __device__ __forceinline__ float key_float(uint32_t k) {
 template <class Issue>
 __device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, int &w3_seq, Issue &w3_issue, int h2,
                                            const float *b3s, const float *h2t, int PT, const uint8_t *w3buf,
-                                           uint64_t *w3bar, float *zb, int &s_fail) {
+                                           uint64_t *w3bar, float *zb, int &s_fail, int &s_cfail) {
     const bool l3 = tid < (kSymbols / 2) * groups;   // at most 128 x 3 < kDecThreads
     const int up = tid % (kSymbols / 2), p0 = 4 * (tid / (kSymbols / 2));
     float a[2][4];
@@ -259,9 +259,14 @@ __device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, i
         const int stg = w3_seq % kW3Stages;
         const int rows = min(kW3Rows, h2 - c * kW3Rows);
         if (l3) {
-            if (!*reinterpret_cast<volatile int *>(&s_fail) &&
-                !tc::mbar_wait(&w3bar[stg], (uint32_t)(w3_seq / kW3Stages) & 1u, kDecWaitLimit))
+            // every issued copy is waited for, also after a peer wait ran
+            // out (a copy from L2 always lands); only a copy that did not
+            // land stops the waits and the refills
+            if (!*reinterpret_cast<volatile int *>(&s_cfail) &&
+                !tc::mbar_wait(&w3bar[stg], (uint32_t)(w3_seq / kW3Stages) & 1u, kDecWaitLimit)) {
+                s_cfail = 1;
                 s_fail = 1;
+            }
             const float *w3c = reinterpret_cast<const float *>(w3buf) + stg * kW3Rows * kSymbols;
 #pragma unroll 4
             for (int kr = 0; kr < rows; kr++) {
@@ -278,7 +283,7 @@ __device__ __forceinline__ void f32_logits(int tid, int groups, int w3_chunks, i
             }
         }
         __syncthreads();   // every reader is done with this buffer
-        if (tid == 0) w3_issue(w3_seq + kW3Stages);
+        if (tid == 0 && !s_cfail) w3_issue(w3_seq + kW3Stages);
     }
     if (l3) {
 #pragma unroll
@@ -330,14 +335,17 @@ __global__ void __launch_bounds__(kDecThreads) k_volume_setup(DevModel m, DecBat
         const uint16_t *pay = reinterpret_cast<const uint16_t *>(sin + kHeaderBytes + 4 * S);
         const int per = (S + kDecThreads - 1) / kDecThreads;
         const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
-        uint32_t sum = 0;
+        // 64-bit sums, each bounded by the input's word count (below 2^32,
+        // checked on the host), so the 32-bit prefix sums are exact
+        uint64_t sum = 0;
         int bad = 0;
         for (int s = s0; s < s1; s++) {
             const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
             bad |= c < 2;
             sum += c;
         }
-        s_part[tid] = sum;
+        bad |= sum > im.in_bytes / 2;
+        s_part[tid] = (uint32_t)sum;
         if (bad) s_ok = 0;
         __syncthreads();
         if (tid == 0) {
@@ -432,14 +440,17 @@ __global__ void __launch_bounds__(kDecThreads) k_batch_setup(DevModel m, DecBatc
         const uint16_t *pay = reinterpret_cast<const uint16_t *>(in + kHeaderBytes + 4 * S);
         const int per = (S + kDecThreads - 1) / kDecThreads;
         const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
-        uint32_t sum = 0;
+        // 64-bit sums, each bounded by the input's word count (below 2^32,
+        // checked on the host), so the 32-bit prefix sums are exact
+        uint64_t sum = 0;
         int bad = 0;
         for (int s = s0; s < s1; s++) {
             const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
             bad |= c < 2;
             sum += c;
         }
-        s_part[tid] = sum;
+        bad |= sum > im.in_bytes / 2;
+        s_part[tid] = (uint32_t)sum;
         if (bad) s_ok = 0;
         __syncthreads();
         if (tid == 0) {
@@ -505,7 +516,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     __shared__ uint64_t bar;
     __shared__ uint64_t w3bar[kW3Stages];   // FP32: W3^T staging buffers filled
     __shared__ uint32_t tmem_base;
-    __shared__ int s_ok, s_S, s_err, s_fail;
+    __shared__ int s_ok, s_S, s_err, s_fail, s_cfail;
     __shared__ uint64_t s_next;   // byte offset of the next slice's container
 
     __shared__ char4 s_woff[kMaxPriors];   // (row, column) offset of every prior of the window
@@ -576,6 +587,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         tc::fence_mbar_init();
         s_err = 0;
         s_fail = 0;
+        s_cfail = 0;
         s_ok = 1;
         s_S = 0;
         s_next = 0;
@@ -651,7 +663,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         const uint8_t *cnt = sin + kHeaderBytes;
         const int per = (S + kDecThreads - 1) / kDecThreads;
         const int s0 = min(S, tid * per), s1 = min(S, s0 + per);
-        uint32_t sum = 0, gsum = 0;
+        // 64-bit sums, each bounded by the input's word count (below 2^32,
+        // checked on the host), so the 32-bit prefix sums are exact
+        uint64_t sum = 0, gsum = 0;
         int bad = 0;
         for (int s = s0; s < s1; s++) {
             const uint32_t c = cnt[4 * s] | (cnt[4 * s + 1] << 8) | (cnt[4 * s + 2] << 16) | ((uint32_t)cnt[4 * s + 3] << 24);
@@ -659,8 +673,9 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             sum += c;
             if (s % P == (int)k) gsum += c;
         }
-        s_part[tid] = sum;
-        s_gpart[tid] = gsum;
+        bad |= sum > im.in_bytes / 2;
+        s_part[tid] = (uint32_t)sum;
+        s_gpart[tid] = (uint32_t)gsum;
         if (bad) s_ok = 0;
         __syncthreads();
         if (tid == 0) {
@@ -1135,7 +1150,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                             const long long t0 = clock64();
                             do {
                                 v = ld_volatile_u32(e);
-                                if (clock64() - t0 > kDecWaitLimit || *reinterpret_cast<volatile int *>(&s_fail)) {
+                                if (clock64() - t0 > m.peer_wait_limit || *reinterpret_cast<volatile int *>(&s_fail)) {
                                     s_fail = 1;
                                     break;
                                 }
@@ -1216,7 +1231,8 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 __syncthreads();
                 // logits: W3^T arrives chunk by chunk in the staging buffers;
                 // z overlays the inputs and the first layer's activations
-                f32_logits(tid, NG, w3_chunks, w3_seq, w3_issue, h2, b3s, h2t, PT, smem + L.w3s, w3bar, zb, s_fail);
+                f32_logits(tid, NG, w3_chunks, w3_seq, w3_issue, h2, b3s, h2t, PT, smem + L.w3s, w3bar, zb, s_fail,
+                           s_cfail);
                 __syncthreads();
             } else {
                 // 2. the three layers: the first (K = the window's priors) as
@@ -1421,7 +1437,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 const uint32_t target = (uint32_t)(t + 1) * gridDim.x;
                 const long long t0 = clock64();
                 while (ld_acquire_gpu_u32(vs.hdr + 2) < target) {
-                    if (ld_acquire_gpu_u32(vs.hdr + 3) || clock64() - t0 > kDecWaitLimit) {
+                    if (ld_acquire_gpu_u32(vs.hdr + 3) || clock64() - t0 > m.peer_wait_limit) {
                         atomicExch(vs.hdr + 3, 1u);
                         s_fail = 1;
                         break;
@@ -1441,9 +1457,13 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // FP32: the loads issued ahead for a next wave complete before the CTA
     // leaves (its shared memory must not be written after it exits)
     if constexpr (F32) {
-        if (tid == 0)
+        if (tid == 0 && !s_cfail)
             for (int q = w3_seq; q < w3_seq + kW3Stages; q++)
-                if (!tc::mbar_wait(&w3bar[q % kW3Stages], (uint32_t)(q / kW3Stages) & 1u, kDecWaitLimit)) s_fail = 1;
+                if (!tc::mbar_wait(&w3bar[q % kW3Stages], (uint32_t)(q / kW3Stages) & 1u, kDecWaitLimit)) {
+                    s_cfail = 1;
+                    s_fail = 1;
+                    break;
+                }
     }
     // final states must be back at the initial value with every word read
     // (the grid decoder's are checked by k_volume_finish)

@@ -57,7 +57,14 @@ struct DevModel {
     const uint16_t *tc_w;         // packed image of W1|W2|W3 operand tiles
     uint32_t tc_w_bytes;
     uint64_t hash;
+    // clock cycles a wavefront decoder waits for another CTA (a tagged-ring
+    // entry of a neighbour, the grid-wide wave barrier) before it gives up
+    // with DLIC_ERR_TIMEOUT; waits on the CTA's own tensor-core work and
+    // bulk copies keep their own, fixed limit
+    long long peer_wait_limit;
 };
+
+constexpr long long kDefaultPeerWaitLimit = 4000000000LL;   // about 2 s at 2 GHz
 
 // Per-image encode descriptor.
 struct EncImage {
@@ -131,7 +138,7 @@ cudaError_t launch_decode(const DevModel &m, const DecBatch &b, cudaStream_t st)
 // image, wavefront)
 cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t st);
 // 12-bit pixels (coder12.cu): warp-per-pixel FP32 kernels over the layer table
-cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, cudaStream_t st);
+cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cudaStream_t st);
 cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t st);
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);

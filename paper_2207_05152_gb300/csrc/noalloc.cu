@@ -8,8 +8,6 @@
 // implicit device synchronisation cudaMalloc / cudaFree can trigger.  This
 // entry point takes the workspace from a fixed block of device memory that
 // the library declares itself, so the call allocates nothing.
-#include <mutex>
-
 #include "internal.cuh"
 
 // The shared scratch block: 16 MiB, enough for about 2.5 million pixels of
@@ -18,32 +16,16 @@
 static constexpr size_t kNoAllocScratchBytes = DLIC_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices] = {nullptr};
-}  // namespace
-
 extern "C" dlic_status dlic_encode_noalloc(const dlic_model *model, const dlic_image *h_images, int n,
                                           const int *h_streams, void *d_out, size_t out_capacity,
                                           uint64_t *d_out_offsets, int32_t *d_status, void *stream) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return dlic::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices)
-        return dlic::fail(DLIC_ERR_UNSUPPORTED, "dlic_encode_noalloc supports devices 0..%d", kMaxDevices - 1);
+    // The host-side name of the array is not a device address.  The address
+    // is looked up on every call, with the caller's device current: a cheap
+    // host query that allocates nothing, and that stays right after a device
+    // reset reloads the library's module (a cached address would not).
     void *scratch = nullptr;
-    {
-        // The host-side name of the array is not a device address: look the
-        // address up once per device, with that device current.
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
-            if (e != cudaSuccess) return dlic::cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-            g_noalloc_ptr[dev] = scratch;
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_scratch);
+    if (e != cudaSuccess) return dlic::cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
     size_t need = 0;
     dlic_status st = dlic_encode_workspace_size(model, h_images, n, h_streams, &need);
     if (st != DLIC_OK) return st;

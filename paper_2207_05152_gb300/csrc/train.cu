@@ -13,9 +13,12 @@
 //
 // Two arithmetic modes: BF16 operands with FP32 accumulation on the tensor
 // cores (tcgen05, TMA-fed, epilogues fused), and plain FP32 on the CUDA
-// cores.  Every product is a GEMM C = A B^T with both operands K-major
-// (row-major, K contiguous); the backward pass uses transposed copies of the
-// activations (written by the producing epilogues) and of the weights.
+// cores.  Every product is a GEMM C = A B^T.  In the BF16 modes the
+// activations stay row-major [batch][features]: the weight gradients read
+// them as MN-major operands, so no transposed copy of an activation is
+// written; the Adam kernel keeps row-major and transposed bf16 copies of the
+// weights.  The FP32 GEMMs take K-major operands only, so in that mode the
+// producing epilogues also write transposed copies of the activations.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -1244,6 +1247,18 @@ extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, co
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
     const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
     k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, t->grads, t->mom, t->vel, (int)t->nparams, t->lr,
+                                                             t->beta1, t->beta2, t->eps, c1, c2, sa);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "adam launch");
+}
+
+extern "C" dlic_status dlic_train_apply(dlic_trainer *t, const float *d_grads, void *stream) {
+    if (!t || !d_grads) return fail(DLIC_ERR_INVALID, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    t->step += 1;
+    const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
+    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
+    k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, d_grads, t->mom, t->vel, (int)t->nparams, t->lr,
                                                              t->beta1, t->beta2, t->eps, c1, c2, sa);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "adam launch");

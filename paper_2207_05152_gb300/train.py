@@ -175,6 +175,14 @@ class Trainer:
                              self.loss.data_ptr(), self._stream())
         return self.loss
 
+    def apply(self, grads: torch.Tensor):
+        """One Adam update with the given gradient (device float32, the
+        parameter layout): backward() then apply() of its own gradient is
+        step()."""
+        if grads.dtype != torch.float32 or not grads.is_cuda or grads.numel() != self.nparams:
+            raise ValueError(f"grads must be {self.nparams} float32 values on the device")
+        _lib.dlic_train_apply(self.handle, grads.contiguous().data_ptr(), self._stream())
+
     def params(self) -> torch.Tensor:
         out = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
         _lib.dlic_trainer_params(self.handle, out.data_ptr(), False, self._stream())

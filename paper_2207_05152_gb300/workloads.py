@@ -91,3 +91,35 @@ def cfg5_images(count: int = 128, seed: int = 5000):
     """MRI-like slices: elliptical phantoms with a bias field and Rician noise."""
     import synth as _s
     return [_s.phantom_image(512, 512, seed + i) for i in range(count)]
+
+
+def cfg5_training(steps: int = 2000, mode: str = "bf16", batch: int = 65536, seed: int = 5000,
+                  images=None):
+    """cfg 5's training run on the current CUDA device: a 12-128-128-256
+    network from seeded Xavier weights, `steps` steps of `batch` contexts
+    drawn (on the device, seeded) from 2M contexts sampled uniformly from
+    the 128 MRI-like slices.  Returns a dict with the untrained and trained
+    layers, the calibration contexts of their INT8 quantisation (the first
+    4096 sampled contexts), the final loss in bits and the seconds the
+    steps took."""
+    import time
+    import torch
+    from . import train as T
+    imgs = images if images is not None else cfg5_images(128, seed)
+    pool_ctx, pool_tgt = T.sample_contexts(imgs, 1 << 21, seed + 1)
+    pc, pt = torch.from_numpy(pool_ctx).cuda(), torch.from_numpy(pool_tgt).cuda()
+    layers0 = synth.xavier_mlp(WIDTHS, 5)
+    tr = T.Trainer(layers0, mode, max_batch=batch)
+    gen = torch.Generator(device="cuda").manual_seed(seed + 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        idx = torch.randint(0, pc.shape[0], (batch,), device="cuda", generator=gen)
+        tr.step(pc.index_select(0, idx).contiguous(), pt.index_select(0, idx).contiguous())
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    status = tr.status()
+    out = {"untrained": layers0, "trained": tr.layers(), "calib": pool_ctx[:4096],
+           "final_loss_bits": float(tr.loss.item()), "seconds": seconds, "status": status}
+    tr.close()
+    return out

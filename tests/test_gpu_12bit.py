@@ -114,3 +114,28 @@ def test_corrupt_stream_is_reported(Codec, orc):
     if st[0] == 0:
         assert np.array_equal(dec[0], want_img)
     codec.close()
+
+
+@pytest.mark.parametrize("value", [4096, 65535])
+def test_samples_above_4095_are_refused(Codec, orc, value):
+    # a 12-bit sample beyond the 4096-value table has no frequency: the
+    # oracle refuses the image, and the device writes DLIC_ERR_INVALID to
+    # the encode status word
+    from paper_2207_05152_gb300 import _lib
+    blob = _blob12()
+    img = _image(17, 29, 4)
+    img[9, 13] = value
+    with pytest.raises(ValueError):
+        orc.encode(blob, img, 4)
+    codec = Codec(blob)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    codec.encode([torch.from_numpy(img.view(np.int16)).cuda()], [4], status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == _lib.DLIC_ERR_INVALID
+    # the same call on a valid image afterwards reports success
+    img[9, 13] = 4095
+    status.zero_()
+    codec.encode([_dev(img)], [4], status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    codec.close()

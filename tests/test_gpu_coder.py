@@ -121,6 +121,29 @@ def test_corrupt_and_capacity(Codec, orc, prec, widths):
     codec.close()
 
 
+@pytest.mark.parametrize("prec,widths,plan", [("int8", [12, 32, 32, 256], 0), ("int8", [12, 128, 128, 256], 0),
+                                              ("int8", [12, 128, 128, 256], 3), ("fp32", [12, 64, 64, 256], 1)])
+def test_word_counts_that_wrap_32_bits_are_corrupt(Codec, orc, prec, widths, plan):
+    # 1030 streams, more than one per decoder thread: two counts of the same
+    # thread raised by 2^31 each leave a 32-bit sum (and so the total-length
+    # check) unchanged, but would put the next stream's start 2^31 words past
+    # the input.  Every decoder must report a corrupt stream instead.
+    from paper_2207_05152_gb300 import _lib
+    H, W, S = 1030, 5, 1030
+    img = synth.value_noise_image(H, W, 41)
+    blob = _models(widths, 6, [synth.voronoi_image(40, 40, 2)])[prec]
+    data = bytearray(orc.encode(blob, img, S))
+    for s in (0, 1):
+        c = int.from_bytes(data[24 + 4 * s:28 + 4 * s], "little")
+        data[24 + 4 * s:28 + 4 * s] = (c + (1 << 31)).to_bytes(4, "little")
+    want_status, _ = orc.decode(blob, bytes(data), H, W)
+    assert want_status == _lib.DLIC_ERR_CORRUPT
+    codec = Codec(blob, decode_plan=plan)
+    _, st = codec.decode_bytes([bytes(data)], [(H, W)])
+    assert st == [_lib.DLIC_ERR_CORRUPT]
+    codec.close()
+
+
 def test_batched_decode_mixed_cluster_sizes(Codec, orc):
     # Twelve images of different sizes in one call: the autotuner gives them
     # different cluster sizes, which run as concurrent groups.

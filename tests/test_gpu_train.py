@@ -108,6 +108,28 @@ def test_gradient_matches_finite_differences(T):
                 assert abs(fd - arr[i]) <= 1e-3 * scale + 1e-7
 
 
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3"])
+def test_cfg3_gradient_matches_finite_differences(T, mode):
+    # The training workload's network (12-256-256-256) on a 2048-context
+    # subset: GPU gradient entries against central differences of the FP64
+    # loss, to within 1e-3 of the tensor's largest entry.  Each tensor's two
+    # largest entries and two seeded ones are checked.
+    layers, ctx, tgt = _data(T, 2048, 19)
+    _, g = _grads(T, mode, layers, ctx, tgt)
+    ref, _ = train64.gradient(layers, ctx, tgt)
+    for layer in range(3):
+        for which in range(2):
+            arr = g[layer][which].reshape(-1)
+            r64 = ref[layer][which].reshape(-1)
+            scale = np.abs(r64).max()
+            picks = list(np.argsort(-np.abs(r64))[:2]) + list(synth.Rng(60 + 2 * layer + which).integers(2, 0, arr.size - 1))
+            for i in picks:
+                theta = np.asarray(layers[layer][which], np.float64).reshape(-1)[int(i)]
+                h = 1e-6 * max(1.0, abs(theta))
+                fd = train64.finite_difference(layers, ctx, tgt, layer, which, int(i), h)
+                assert abs(fd - arr[i]) <= 1e-3 * scale + 1e-7, (layer, which, int(i), fd, arr[i])
+
+
 @pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
 def test_adam_step_and_training_progress(T, mode):
     layers, ctx, tgt = _data(T, 4096, 11, widths=(12, 64, 64, 256))
@@ -164,3 +186,27 @@ def test_window_gradients_against_fp64(T, window, mode, tol):
     assert abs(loss - loss64) <= 1e-3 * loss64
     for ew, eb in errs:
         assert ew < tol and eb < tol
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16", "bf16x3"])
+def test_apply_of_own_gradient_is_the_step(T, mode):
+    # dlic_train_backward + dlic_train_apply of its own gradient must be
+    # dlic_train_step bit for bit; the data-parallel step on one rank too
+    from paper_2207_05152_gb300 import sharding
+    layers, ctx, tgt = _data(T, 3000, 23, widths=(12, 64, 64, 256))
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    a = T.Trainer(layers, mode, max_batch=3000)
+    b = T.Trainer(layers, mode, max_batch=3000)
+    d = sharding.DataParallelTrainer(T.Trainer(layers, mode, max_batch=3000))
+    for _ in range(3):
+        a.step(c, t)
+        _, g = b.backward(c, t)
+        b.apply(g)
+        d.step(c, t)
+    pa, pb, pd = a.params(), b.params(), d.trainer.params()
+    torch.cuda.synchronize()
+    assert torch.equal(pa, pb) and torch.equal(pa, pd)
+    assert a.status() == 0 and b.status() == 0
+    for tr in (a, b, d.trainer):
+        tr.close()

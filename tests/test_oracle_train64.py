@@ -70,3 +70,54 @@ def test_adam_first_step_closed_form():
     want = theta - 1e-3 * grad / (np.abs(grad) + 1e-8)
     assert np.allclose(t, want, rtol=0, atol=1e-15)
     assert np.allclose(m, 0.1 * grad) and np.allclose(v, 0.001 * grad * grad)
+
+
+def _kink_free(params, x, a1, h1, a2, layer, which, i, h):
+    """True if moving parameter i of (layer, which) by +-h leaves the sign of
+    every pre-activation it reaches unchanged."""
+    w2 = np.asarray(params[1][0], np.float64)
+    if layer == 2:
+        return True
+    fan_in = x.shape[1] if layer == 0 else h1.shape[1]
+    unit = i // fan_in if which == 0 else i
+    src = (x if layer == 0 else h1)[:, i % fan_in] if which == 0 else np.ones(x.shape[0])
+    d = np.abs(h * src)                         # change of the unit's pre-activation per context
+    pre = a1 if layer == 0 else a2
+    if np.any(np.abs(pre[:, unit]) <= d):
+        return False
+    if layer == 1:
+        return True
+    d2 = d[:, None] * np.abs(w2[:, unit])[None, :] * (a1[:, unit] > 0)[:, None]
+    return not np.any(np.abs(a2) <= d2)
+
+
+@pytest.mark.slow
+def test_gradient_vs_central_differences_cfg3_widths():
+    # The training workload's own network (12-256-256-256) on its 2048-context
+    # subset: cfg-3-style images, contexts sampled as the trainer's data.
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.config_image(3, i) for i in range(2)]
+    ctx, tgt = T.sample_contexts(imgs, 2048, 11)
+    params = _params([12, 256, 256, 256], 12)
+    grads, _ = train64.gradient(params, ctx, tgt)
+    _, (x, a1, h1, a2, h2, z, lse) = train64.forward(params, ctx, tgt)
+    checked = 0
+    for layer in range(3):
+        for which in range(2):
+            g = grads[layer][which].reshape(-1)
+            # the largest entries (where a dropped term or a wrong index
+            # shows most) and a few seeded ones
+            picks = list(np.argsort(-np.abs(g))[:2]) + list(synth.Rng(40 + 2 * layer + which).integers(2, 0, g.size - 1))
+            for i in picks:
+                i = int(i)
+                theta = params[layer][which].reshape(-1)[i]
+                h = 1e-6 * max(1.0, abs(theta))
+                # with 2048 contexts and 256 units, a perturbation of h can
+                # move some downstream pre-activation across zero; central
+                # differences are only checked where none crosses (margin 2x)
+                if not _kink_free(params, x, a1, h1, a2, layer, which, i, 2.0 * h):
+                    continue
+                fd = train64.finite_difference(params, ctx, tgt, layer, which, i, h)
+                assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (layer, which, i, fd, g[i])
+                checked += 1
+    assert checked >= 16
