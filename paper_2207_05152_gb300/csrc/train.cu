@@ -97,11 +97,14 @@ struct GlobalRow {
     }
 };
 
-// Adds 16 column values of this thread's row into the shared column sums:
-// a reduce-scatter across the warp (each lane ends with one column's warp
-// total for lanes 0..15 after four halving steps) and one shared atomic per
-// column and warp.
-__device__ __forceinline__ void colsum_add(float *cs, float (&v)[16]) {
+// Adds 16 column values of this thread's row into the shared column
+// partials: a reduce-scatter across the warp (each lane ends with one
+// column's warp total for lanes 0..15 after four halving steps), then one
+// plain store per column into the warp's slot, cs[slot * stride + column].
+// Exactly one warp writes each (slot, column), and the four slots are added
+// in a fixed order afterwards, so the bias gradients are the same bits on
+// every run.
+__device__ __forceinline__ void colsum_add(float *cs, int slot, int stride, float (&v)[16]) {
     const int lane = threadIdx.x & 31;
     float a[16];
 #pragma unroll
@@ -118,15 +121,17 @@ __device__ __forceinline__ void colsum_add(float *cs, float (&v)[16]) {
     }
     // lane holds the sum over its 16-lane half for column (lane & 15)
     a[0] += __shfl_xor_sync(0xffffffffu, a[0], 16);
-    if (lane < 16) atomicAdd(cs + (lane & 15), a[0]);
+    if (lane < 16) cs[slot * stride + lane] = a[0];
 }
 
-// Column sums go through shared memory: `cs` holds N floats zeroed by the
-// caller; each warp adds its rows' values (colsum_add).
+// Column sums go through shared memory: `cs` holds four slots of N floats
+// zeroed by the caller; warp w of the CTA's four stores its rows' column
+// totals into slot w (colsum_add).
 template <class Row>
 __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, bool valid, float *cs,
                              float *loss_acc) {
     const int N = e.N;
+    const int cslot = (threadIdx.x >> 5) & 3;
     if (epi == EPI_F32) {
         if (!valid) return;
         float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
@@ -160,7 +165,7 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
                 if (cs) {
 #pragma unroll
                     for (int j = 0; j < 16; j++) v[j] = 0.0f;
-                    colsum_add(cs + n0, v);
+                    colsum_add(cs + n0, cslot, N, v);
                 }
                 continue;
             }
@@ -172,7 +177,7 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
                 store_val(e, e.outT, (size_t)(n0 + j) * e.ldT + m, g, e.outT_plane);
                 v[j] = g;
             }
-            if (cs) colsum_add(cs + n0, v);
+            if (cs) colsum_add(cs + n0, cslot, N, v);
         }
         return;
     }
@@ -201,7 +206,7 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
             if (cs) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) v[j] = 0.0f;
-                colsum_add(cs + n0, v);
+                colsum_add(cs + n0, cslot, N, v);
             }
             continue;
         }
@@ -218,7 +223,7 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
             store_val(e, e.outT, (size_t)(n0 + j) * e.ldT + m, g, e.outT_plane);
             v[j] = g;
         }
-        if (cs) colsum_add(cs + n0, v);
+        if (cs) colsum_add(cs + n0, cslot, N, v);
     }
 }
 
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     __shared__ uint64_t full[kGemmMaxStages], empty[kGemmMaxStages], accum;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
-    __shared__ float cs[256];
+    __shared__ float cs[4 * 256];   // column partials, one slot per lane quarter
     __shared__ __align__(16) float s_bias[256];
     __shared__ float red[2][2][128];
     __shared__ float s_loss[kGemmThreads / 32];
@@ -387,8 +392,8 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         tc::fence_mbar_init();
         s_fail = 0;
     }
+    for (int n = tid; n < 4 * 256; n += kGemmThreads) cs[n] = 0.0f;
     for (int n = tid; n < 256; n += kGemmThreads) {
-        cs[n] = 0.0f;
         // the softmax works in base 2: its bias is stored pre-scaled by log2(e)
         const float bv = e.bias && n < N ? e.bias[n] : 0.0f;
         s_bias[n] = epi == EPI_SOFTMAX ? bv * kLog2e : bv;
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
                     v[j] = pos ? v[j] : 0.0f;
                 }
                 if (valid) store_row16(e, v, m, n0);
-                if (e.colsum) colsum_add(cs + n0, v);
+                if (e.colsum) colsum_add(cs + n0, q, 256, v);
             });
         } else {
             // EPI_SOFTMAX: running maximum and rescaled sum over this half's
@@ -556,7 +561,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
                         if (n0 + j == y) v[j] -= e.inv_batch_ln2;
                 }
                 if (valid) store_row16(e, v, m, n0);
-                if (e.colsum) colsum_add(cs + n0, v);
+                if (e.colsum) colsum_add(cs + n0, q, 256, v);
             });
         }
     }
@@ -565,7 +570,8 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     tc::fence_before_sync();
     __syncthreads();
     if (e.colsum)
-        for (int n = tid; n < N; n += kGemmThreads) e.colsum[(size_t)blockIdx.x * N + n] = cs[n];
+        for (int n = tid; n < N; n += kGemmThreads)
+            e.colsum[(size_t)blockIdx.x * N + n] = ((cs[n] + cs[256 + n]) + cs[512 + n]) + cs[768 + n];
     if (e.loss && tid == 0) {
         float t = 0.0f;
         for (int w = 0; w < kGemmThreads / 32; w++) t += s_loss[w];
@@ -629,9 +635,9 @@ __global__ void __launch_bounds__(256) k_gemm_f32(const float *A, int lda, const
 // Row epilogue over an FP32 C in global memory (the FP32 path); 128 rows per
 // CTA so the per-CTA column sums match the tensor-core kernel's layout.
 __global__ void __launch_bounds__(128) k_row_epilogue(const float *C, int epi, EpiArgs e) {
-    extern __shared__ float cs[];
+    extern __shared__ float cs[];   // four slots of N column partials
     const int tid = threadIdx.x;
-    for (int n = tid; n < e.N; n += 128) cs[n] = 0.0f;
+    for (int n = tid; n < 4 * e.N; n += 128) cs[n] = 0.0f;
     __syncthreads();
     const int m = blockIdx.x * 128 + tid;
     float loss_acc = 0.0f;
@@ -642,7 +648,8 @@ __global__ void __launch_bounds__(128) k_row_epilogue(const float *C, int epi, E
     if ((tid & 31) == 0) s_loss[tid >> 5] = loss_acc;
     __syncthreads();
     if (e.colsum)
-        for (int n = tid; n < e.N; n += 128) e.colsum[(size_t)blockIdx.x * e.N + n] = cs[n];
+        for (int n = tid; n < e.N; n += 128)
+            e.colsum[(size_t)blockIdx.x * e.N + n] = ((cs[n] + cs[e.N + n]) + cs[2 * e.N + n]) + cs[3 * e.N + n];
     if (e.loss && tid == 0) e.loss[blockIdx.x] = s_loss[0] + s_loss[1] + s_loss[2] + s_loss[3];
 }
 
@@ -994,7 +1001,7 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
     k_gemm_f32<<<dim3(mt, (N + 127) / 128, splits), 256, 0, st>>>(static_cast<const float *>(a.p), a.pitch,
                                                                    static_cast<const float *>(b.p), b.pitch, dst, M, N, K,
                                                                    per, ldc);
-    if (epi != EPI_F32) k_row_epilogue<<<mt, 128, N * sizeof(float), st>>>(t->C, epi, e);
+    if (epi != EPI_F32) k_row_epilogue<<<mt, 128, 4 * N * sizeof(float), st>>>(t->C, epi, e);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "fp32 gemm launch");
 }
