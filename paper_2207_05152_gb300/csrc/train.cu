@@ -46,7 +46,9 @@ struct EpiArgs {
     float *c;                   // EPI_F32: output (+ blockIdx.z * M * ldc)
     const float *bias;          // BIAS_RELU, SOFTMAX
     void *out, *outT;           // row-major [M][N] and transposed [N][M] outputs (bf16 or fp32)
-    const void *act;            // RELU_GRAD: activation [M][N] whose sign masks the gradient
+    const void *act;            // RELU_GRAD (FP32 path): activation [M][N] whose sign masks the gradient
+    const uint16_t *mask;       // RELU_GRAD (BF16 paths): that sign as bits, [M][N / 16] words
+    uint16_t *mask_out;         // BIAS_RELU (BF16 paths): the output's sign bits, [M][N / 16] words
     const uint8_t *tgt;         // SOFTMAX: targets
     float inv_batch_ln2;        // SOFTMAX: 1 / (B ln 2)
     float *colsum;              // per-CTA column sums [gridDim.x][N] (db), or null
@@ -304,12 +306,22 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return d;
 }
 
+// bf16 > 0 for the two halves of a packed pair, as bits 0 and 1.
+__device__ __forceinline__ uint32_t bf16x2_positive(uint32_t p) {
+    const uint32_t lo = p & 0xFFFFu, hi = p >> 16;
+    return (uint32_t)(lo != 0u && (lo & 0x8000u) == 0u) | ((uint32_t)(hi != 0u && (hi & 0x8000u) == 0u) << 1);
+}
+
 // 16 consecutive values of row m as bf16 (and, in split mode, the low plane
-// bf16(v - hi)) with two 16-byte stores per plane.
-__device__ __forceinline__ void store_row16(const EpiArgs &e, const float (&v)[16], int m, int n0) {
+// bf16(v - hi)) with two 16-byte stores per plane.  Returns which of the
+// stored (high-plane) values are positive, bit j for value j.
+__device__ __forceinline__ uint32_t store_row16(const EpiArgs &e, const float (&v)[16], int m, int n0) {
     uint32_t hi[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) hi[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+    uint32_t pos = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) pos |= bf16x2_positive(hi[j]) << (2 * j);
     uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(e.out) + (size_t)m * e.N + n0);
     o[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     o[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
@@ -322,6 +334,7 @@ __device__ __forceinline__ void store_row16(const EpiArgs &e, const float (&v)[1
         ol[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         ol[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
     }
+    return pos;
 }
 
 // Walks this thread's 16-column chunks [n_lo, n_hi) of its tensor-memory row,
@@ -407,9 +420,9 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         // producer; first the activation rows that will mask this tile's
         // gradient are pulled into L2 (one contiguous block)
         if (epi == EPI_RELU_GRAD && m0 < e.M) {
-            const uint32_t bytes = (uint32_t)(min(128, e.M - m0) * N * 2);
-            const void *src = static_cast<const uint16_t *>(e.act) + (size_t)m0 * N;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+            const uint32_t bytes = (uint32_t)(min(128, e.M - m0) * (N / 16) * 2);
+            const void *src = e.mask + (size_t)m0 * (N / 16);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((bytes + 15u) & ~15u) : "memory");
         }
         for (int i = 0; i < nkb; i++) {
             const int s = i % NS;
@@ -493,28 +506,21 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
             for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) v[j] = fmaxf(v[j] + s_bias[n0 + j], 0.0f);
-                if (valid) store_row16(e, v, m, n0);
+                if (valid) {
+                    const uint32_t pos = store_row16(e, v, m, n0);
+                    if (e.mask_out) e.mask_out[(size_t)m * (N / 16) + n0 / 16] = (uint16_t)pos;
+                }
             });
         } else if (epi == EPI_RELU_GRAD) {
-            // the activation that masks the gradient, one chunk ahead
-            const uint4 *ap = reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(e.act) + (size_t)m * N);
-            uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0;
-            if (valid && n_lo < n_hi) {
-                a0 = ap[n_lo / 8];
-                a1 = ap[n_lo / 8 + 1];
-            }
+            // the sign bits of the activation that masks the gradient (written
+            // by its forward epilogue), one chunk ahead
+            const uint16_t *mp = e.mask + (size_t)m * (N / 16);
+            uint32_t mb = valid && n_lo < n_hi ? mp[n_lo / 16] : 0u;
             for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
-                const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                if (valid && n0 + 16 < n_hi) {
-                    a0 = ap[n0 / 8 + 2];
-                    a1 = ap[n0 / 8 + 3];
-                }
+                const uint32_t bits = mb;
+                if (valid && n0 + 16 < n_hi) mb = mp[n0 / 16 + 1];
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const uint32_t bits = (aw[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                    const bool pos = bits != 0 && (bits & 0x8000u) == 0;   // bf16 > 0
-                    v[j] = pos ? v[j] : 0.0f;
-                }
+                for (int j = 0; j < 16; j++) v[j] = (bits >> j) & 1u ? v[j] : 0.0f;
                 if (valid) store_row16(e, v, m, n0);
                 if (e.colsum) colsum_add(cs + n0, q, 256, v);
             });
@@ -717,7 +723,7 @@ __global__ void k_features(const uint8_t *ctx, int B, int n_in, int k1, int ldT,
 constexpr int kL1Ctx = 32;
 template <int NMAX>
 __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n_in, const float *W1, const float *b1,
-                                                int h1, uint16_t *H1, size_t p1) {
+                                                int h1, uint16_t *H1, size_t p1, uint16_t *M1) {
     __shared__ __align__(16) uint16_t thi[kL1Ctx * kMaxHidden];
     __shared__ __align__(16) uint16_t tlo[kL1Ctx * kMaxHidden];
     __shared__ float xs[kL1Ctx][NMAX];
@@ -752,6 +758,18 @@ __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n
     if (p1) {
         uint4 *dl = reinterpret_cast<uint4 *>(H1 + p1 + (size_t)b0 * h1);
         for (int i = tid; i < n16; i += 256) dl[i] = reinterpret_cast<const uint4 *>(tlo)[i];
+    }
+    // the sign bits of the stored values: bit j of word (row, g) = unit 16 g + j > 0
+    const int g16 = h1 / 16;
+    for (int i = tid; i < rows * g16; i += 256) {
+        const int r = i / g16, g = i % g16;
+        uint32_t pos = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const uint32_t pair = (uint32_t)thi[r * h1 + 16 * g + j] | ((uint32_t)thi[r * h1 + 16 * g + j + 1] << 16);
+            pos |= bf16x2_positive(pair) << j;
+        }
+        M1[(size_t)(b0 + r) * g16 + g] = (uint16_t)pos;
     }
 }
 
@@ -885,6 +903,7 @@ struct dlic_trainer {
     float *params, *grads, *mom, *vel;           // FP32 master state
     void *w1, *w2, *w3, *w2t, *w3t;              // operand copies (bf16 or fp32)
     void *X, *H1, *H2, *DZ, *DA2, *DA1;          // row-major [batch][features]
+    uint16_t *M1, *M2;                           // BF16 modes: sign bits of H1, H2 [batch][h / 16]
     void *XT, *H1T, *H2T, *DZT, *DA2T, *DA1T;    // FP32 path: transposed [features][batch]
     float *C, *part, *colsum, *losspart;
     int *err;
@@ -1057,17 +1076,18 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
         const int nb = (B + kL1Ctx - 1) / kL1Ctx;
         uint16_t *H1 = static_cast<uint16_t *>(t->H1);
         if (n_in <= 16)
-            k_layer1<16><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+            k_layer1<16><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
         else if (n_in <= 32)
-            k_layer1<32><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+            k_layer1<32><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
         else if (n_in <= 64)
-            k_layer1<64><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+            k_layer1<64><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
         else
-            k_layer1<96><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1);
+            k_layer1<96><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
     } else if ((s = gemm(t, rowmaj(t->X, k1), wmat(t->w1, h1, k1), B, h1, k1, EPI_BIAS_RELU, e, 1, st))) {
         return s;
     }
     e = EpiArgs{}; e.bias = p.b2; e.out = t->H2; e.outT = t->H2T; e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
+    e.mask_out = bf ? t->M2 : nullptr;
     if ((s = gemm(t, rowmaj(t->H1, h1), wmat(t->w2, h2, h1), B, h2, h1, EPI_BIAS_RELU, e, 1, st))) return s;
     // layer 3 + softmax cross-entropy: loss partials, dz, db3 partials
     e = EpiArgs{}; e.bias = p.b3; e.out = t->DZ; e.outT = t->DZT; e.tgt = tgt;
@@ -1083,13 +1103,13 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     }
     reduce_parts(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f, 0, 0, st);
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
-    e = EpiArgs{}; e.act = t->H2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
+    e = EpiArgs{}; e.act = t->H2; e.mask = t->M2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
     if ((s = gemm(t, rowmaj(t->DZ, kSymbols), wmat(t->w3t, h2, kSymbols), B, h2, kSymbols, EPI_RELU_GRAD, e, 1, st)))
         return s;
     reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, 0, st);
     // dh1 = da2 W2, da1 = dh1 * [h1 > 0]; db1
-    e = EpiArgs{}; e.act = t->H1; e.out = bf ? t->DA1 : nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
+    e = EpiArgs{}; e.act = t->H1; e.mask = t->M1; e.out = bf ? t->DA1 : nullptr; e.outT = t->DA1T; e.colsum = t->colsum;
     e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
     reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, 0, st);
@@ -1173,6 +1193,8 @@ extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, i
     t->DA2 = A(es * Bm * h2);
     if (t->bf) {
         t->DA1 = A(es * Bm * h1);
+        t->M1 = (uint16_t *)A(2 * Bm * (h1 / 16) + 16);   // (+16: the L2 prefetch rounds up)
+        t->M2 = (uint16_t *)A(2 * Bm * (h2 / 16) + 16);
     } else {
         t->XT = A(es * t->k1 * Bm);
         t->H1T = A(es * h1 * Bm);
