@@ -363,14 +363,14 @@ __device__ __forceinline__ void for_chunks(uint32_t taddr, int n_lo, int n_hi, F
 // SPLIT: operands come as high and low bf16 planes (x = hi + lo) and every K
 // step issues hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits of
 // each operand.
-template <bool SPLIT>
-__global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
+template <bool SPLIT, bool PERSIST>
+__global__ void __launch_bounds__(kGemmThreads, SPLIT || PERSIST ? 1 : 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapAl, const __grid_constant__ CUtensorMap mapBl, int K,
               int kb_per_split, int epi, GemmCfg g, EpiArgs e, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[kGemmMaxStages], empty[kGemmMaxStages], accum;
+    __shared__ uint64_t full[kGemmMaxStages], empty[kGemmMaxStages], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ float cs[4 * 256];   // column partials, one slot per lane quarter
@@ -382,10 +382,11 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     const uint32_t a_bytes = 128 * 128, b_bytes = (uint32_t)g.n_mma * 128;
     const uint32_t b_al = (b_bytes + 1023) & ~1023u;
     const uint32_t stage_bytes = SPLIT ? 2 * (a_bytes + b_al) : a_bytes + b_al;
-    const int m0 = blockIdx.x * 128;
-    // bytes a stage's loads deliver (whole boxes past the extent are skipped)
-    const int a_boxes = m0 + 64 < e.M ? 2 : 1;
-    const uint32_t a_load = g.a_mn ? 8192u * a_boxes : a_bytes;
+    // tiles of this CTA: m-tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+    // with two accumulators the epilogue of one tile overlaps the loads and
+    // MMAs of the next
+    const int mt = (e.M + 127) / 128, nacc = PERSIST ? 2 : 1;
+    const int ntiles = !PERSIST ? 1 : (int)blockIdx.x < mt ? (mt - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t b_load = g.b_mn ? 8192u * g.b_boxes : b_bytes;
     const int nkb_total = (K + 63) / 64;
     const int kb0 = blockIdx.z * kb_per_split;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     const int nkb = max(0, kb1 - kb0);
 
     if (warp == 0) {
-        tc::tmem_alloc(&tmem_base, 256);
+        tc::tmem_alloc(&tmem_base, 256 * nacc);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -401,7 +402,10 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(&accum, 1);
+        for (int a = 0; a < 2; a++) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], kEpiThreads / 32);   // one arrival per epilogue warp
+        }
         tc::fence_mbar_init();
         s_fail = 0;
     }
@@ -417,32 +421,40 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
     const uint32_t tm = tmem_base;
 
     if (warp == 0 && lane == 0) {
-        // producer; first the activation rows that will mask this tile's
-        // gradient are pulled into L2 (one contiguous block)
-        if (epi == EPI_RELU_GRAD && m0 < e.M) {
-            const uint32_t bytes = (uint32_t)(min(128, e.M - m0) * (N / 16) * 2);
-            const void *src = e.mask + (size_t)m0 * (N / 16);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((bytes + 15u) & ~15u) : "memory");
-        }
-        for (int i = 0; i < nkb; i++) {
-            const int s = i % NS;
-            if (!tc::mbar_wait(&empty[s], ((i / NS) & 1) ^ 1, kGemmWaitLimit)) { s_fail = 1; break; }
-            uint8_t *st = smem + s * stage_bytes;
-            const int k = (kb0 + i) * 64;
-            const uint32_t bar = tc::smem_addr(&full[s]);
-            mbar_expect_tx(&full[s], SPLIT ? 2 * (a_load + b_load) : a_load + b_load);
+        // producer: every K block of every tile through the NS stages
+        int it = 0;
+        for (int j = 0; j < ntiles && !*reinterpret_cast<volatile int *>(&s_fail); j++) {
+            const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * 128;
+            // bytes a stage's loads deliver (whole boxes past the extent are skipped)
+            const int a_boxes = m0 + 64 < e.M ? 2 : 1;
+            const uint32_t a_load = g.a_mn ? 8192u * a_boxes : a_bytes;
+            // the sign bits that will mask this tile's gradient, pulled into L2
+            if (epi == EPI_RELU_GRAD) {
+                const uint32_t bytes = (uint32_t)(min(128, e.M - m0) * (N / 16) * 2);
+                const void *src = e.mask + (size_t)m0 * (N / 16);
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((bytes + 15u) & ~15u)
+                             : "memory");
+            }
+            for (int i = 0; i < nkb; i++, it++) {
+                const int s = it % NS;
+                if (!tc::mbar_wait(&empty[s], ((it / NS) & 1) ^ 1, kGemmWaitLimit)) { s_fail = 1; break; }
+                uint8_t *st = smem + s * stage_bytes;
+                const int k = (kb0 + i) * 64;
+                const uint32_t bar = tc::smem_addr(&full[s]);
+                mbar_expect_tx(&full[s], SPLIT ? 2 * (a_load + b_load) : a_load + b_load);
 #pragma unroll 1
-            for (int pl = 0; pl < (SPLIT ? 2 : 1); pl++) {
-                const CUtensorMap *ma = pl ? &mapAl : &mapA, *mb = pl ? &mapBl : &mapB;
-                uint8_t *sa = st + pl * (a_bytes + b_al), *sb = sa + a_bytes;
-                if (g.a_mn)
-                    for (int h = 0; h < a_boxes; h++) tma_load_2d(tc::smem_addr(sa + 8192 * h), ma, m0 + 64 * h, k, bar);
-                else
-                    tma_load_2d(tc::smem_addr(sa), ma, k, m0, bar);
-                if (g.b_mn)
-                    for (int h = 0; h < g.b_boxes; h++) tma_load_2d(tc::smem_addr(sb + 8192 * h), mb, 64 * h, k, bar);
-                else
-                    tma_load_2d(tc::smem_addr(sb), mb, k, 0, bar);
+                for (int pl = 0; pl < (SPLIT ? 2 : 1); pl++) {
+                    const CUtensorMap *ma = pl ? &mapAl : &mapA, *mb = pl ? &mapBl : &mapB;
+                    uint8_t *sa = st + pl * (a_bytes + b_al), *sb = sa + a_bytes;
+                    if (g.a_mn)
+                        for (int h = 0; h < a_boxes; h++) tma_load_2d(tc::smem_addr(sa + 8192 * h), ma, m0 + 64 * h, k, bar);
+                    else
+                        tma_load_2d(tc::smem_addr(sa), ma, k, m0, bar);
+                    if (g.b_mn)
+                        for (int h = 0; h < g.b_boxes; h++) tma_load_2d(tc::smem_addr(sb + 8192 * h), mb, 64 * h, k, bar);
+                    else
+                        tma_load_2d(tc::smem_addr(sb), mb, k, 0, bar);
+                }
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -450,37 +462,46 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         const uint32_t idesc = tc::idesc_bf16_f32(128, g.n_mma) | ((uint32_t)g.a_mn << 15) | ((uint32_t)g.b_mn << 16);
         // start-address step per K = 16 (descriptor units of 16 bytes)
         const uint32_t astep = g.a_mn ? 128u : 2u, bstep = g.b_mn ? 128u : 2u;
-        for (int i = 0; i < nkb; i++) {
-            const int s = i % NS;
-            if (!tc::mbar_wait(&full[s], (i / NS) & 1, kGemmWaitLimit)) { s_fail = 1; break; }
+        int it = 0;
+        for (int j = 0; j < ntiles && !*reinterpret_cast<volatile int *>(&s_fail); j++) {
+            const int acc = j % nacc;
+            const uint32_t tma = tm + 256u * (uint32_t)acc;
+            // the epilogue of the tile that last used this accumulator is done
+            if (j >= nacc && !tc::mbar_wait(&tempty[acc], ((j / nacc) - 1) & 1, kGemmWaitLimit)) { s_fail = 1; break; }
             tc::fence_after_sync();
-            uint8_t *st = smem + s * stage_bytes;
-            auto dA = [&](uint8_t *p) { return g.a_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
-            auto dB = [&](uint8_t *p) { return g.b_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
-            const uint64_t da = dA(st), db = dB(st + a_bytes);
+            for (int i = 0; i < nkb; i++, it++) {
+                const int s = it % NS;
+                if (!tc::mbar_wait(&full[s], (it / NS) & 1, kGemmWaitLimit)) { s_fail = 1; break; }
+                tc::fence_after_sync();
+                uint8_t *st = smem + s * stage_bytes;
+                auto dA = [&](uint8_t *p) { return g.a_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
+                auto dB = [&](uint8_t *p) { return g.b_mn ? desc_mn128(tc::smem_addr(p)) : desc_k128(tc::smem_addr(p)); };
+                const uint64_t da = dA(st), db = dB(st + a_bytes);
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++) tc::mma_bf16(tm, da + astep * ks, db + bstep * ks, idesc, (i | ks) != 0);
-            if (SPLIT) {
-                const uint64_t dal = dA(st + a_bytes + b_al), dbl = dB(st + 2 * a_bytes + b_al);
+                for (int ks = 0; ks < 4; ks++) tc::mma_bf16(tma, da + astep * ks, db + bstep * ks, idesc, (i | ks) != 0);
+                if (SPLIT) {
+                    const uint64_t dal = dA(st + a_bytes + b_al), dbl = dB(st + 2 * a_bytes + b_al);
 #pragma unroll
-                for (int ks = 0; ks < 4; ks++) {
-                    tc::mma_bf16(tm, dal + astep * ks, db + bstep * ks, idesc, 1u);
-                    tc::mma_bf16(tm, da + astep * ks, dbl + bstep * ks, idesc, 1u);
+                    for (int ks = 0; ks < 4; ks++) {
+                        tc::mma_bf16(tma, dal + astep * ks, db + bstep * ks, idesc, 1u);
+                        tc::mma_bf16(tma, da + astep * ks, dbl + bstep * ks, idesc, 1u);
+                    }
                 }
+                tc::mma_commit(&empty[s]);
             }
-            tc::mma_commit(&empty[s]);
+            tc::mma_commit(&tfull[acc]);
         }
-        tc::mma_commit(&accum);
     } else if (warp >= 2) {
-        if (lane == 0 && !tc::mbar_wait(&accum, 0, kGemmWaitLimit)) s_fail = 1;
+      const int etid = tid - 64;   // epilogue thread 0 .. kEpiThreads - 1
+      for (int j = 0; j < ntiles; j++) {
+        const int acc = j % nacc, tile = (int)blockIdx.x + j * (int)gridDim.x, m0 = tile * 128;
+        if (lane == 0 && !*reinterpret_cast<volatile int *>(&s_fail) &&
+            !tc::mbar_wait(&tfull[acc], (j / nacc) & 1, kGemmWaitLimit))
+            s_fail = 1;
         __syncwarp();
-        tc::mbar_wait(&accum, 0, 1000);   // every lane observes the completed phase
+        if (!*reinterpret_cast<volatile int *>(&s_fail)) tc::mbar_wait(&tfull[acc], (j / nacc) & 1, 1000);   // every lane observes the completed phase
         tc::fence_after_sync();
-    }
-    __syncwarp();
-    asm volatile("bar.sync 1, %0;" ::"r"(kGemmThreads) : "memory");
-    float loss_acc = 0.0f;
-    if (warp >= 2) {
+        float loss_acc = 0.0f;
         const int q = warp & 3, hf = (warp - 2) >> 2;
         const int row = 32 * q + lane, m = m0 + row;
         const bool valid = m < e.M;
@@ -488,7 +509,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
         const int nch = N / 16, first = (nch + 1) / 2;
         int n_lo = hf ? 16 * first : 0, n_hi = hf ? N : 16 * first;
         if (s_fail) n_hi = n_lo;
-        const uint32_t taddr = tm + ((uint32_t)(32 * q) << 16);
+        const uint32_t taddr = tm + 256u * (uint32_t)acc + ((uint32_t)(32 * q) << 16);
         if (epi == EPI_F32) {
             float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
             if (nkb == 0) {
@@ -570,23 +591,28 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT ? 1 : 2)
                 if (e.colsum) colsum_add(cs + n0, q, 256, v);
             });
         }
+        for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+        if (lane == 0) s_loss[warp] = loss_acc;
+        tc::fence_before_sync();
+        epi_sync();   // the tile's accumulator is read out, its column and loss partials are in place
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&tempty[acc])) : "memory");
+        if (e.colsum)
+            for (int n = etid; n < N; n += kEpiThreads)
+                e.colsum[(size_t)tile * N + n] = ((cs[n] + cs[256 + n]) + cs[512 + n]) + cs[768 + n];
+        if (e.loss && etid == 0) {
+            float t = 0.0f;
+            for (int w = 2; w < kGemmThreads / 32; w++) t += s_loss[w];
+            e.loss[tile] = t;
+        }
+        epi_sync();   // (the next tile overwrites the partials)
+      }
     }
-    for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-    if (lane == 0) s_loss[warp] = loss_acc;
     tc::fence_before_sync();
     __syncthreads();
-    if (e.colsum)
-        for (int n = tid; n < N; n += kGemmThreads)
-            e.colsum[(size_t)blockIdx.x * N + n] = ((cs[n] + cs[256 + n]) + cs[512 + n]) + cs[768 + n];
-    if (e.loss && tid == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < kGemmThreads / 32; w++) t += s_loss[w];
-        e.loss[blockIdx.x] = t;
-    }
     if (tid == 0 && s_fail) atomicExch(err, DLIC_ERR_TIMEOUT);
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tm, 256);
+        tc::tmem_dealloc(tm, 256 * nacc);
     }
 }
 
@@ -983,8 +1009,15 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
         g.b_mn = b.mn;
         g.n_mma = b.mn ? (N + 63) / 64 * 64 : (N + 15) / 16 * 16;
         g.b_boxes = (N + 63) / 64;
-        // K blocks of 64: a deeper pipeline for the long-K weight gradients
-        // (one CTA per SM); two stages elsewhere (two CTAs per SM in BF16)
+        // Split mode: the activation GEMMs (M = batch) run persistent, one
+        // CTA per SM over the m-tiles with two accumulators, so that a tile's
+        // epilogue overlaps the next tile's loads and MMAs (its stages are
+        // twice as large, so only one CTA fits an SM anyway).  Plain BF16:
+        // one tile per CTA and two CTAs per SM (two stages each), whose
+        // epilogues run side by side; measured faster than one persistent
+        // CTA.  The weight gradients (M = 256 or h, K = batch) take one tile
+        // per CTA with split-K over gridDim.z and a deeper pipeline.
+        const bool persist = t->split && epi != EPI_F32;
         g.stages = epi == EPI_F32 && !t->split ? 4 : 2;
         CUtensorMap ma, mb, mal, mbl;
         const uint16_t *A16 = static_cast<const uint16_t *>(a.p), *B16 = static_cast<const uint16_t *>(b.p);
@@ -1001,13 +1034,17 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
         const int per = (nkb + splits - 1) / splits;
         const uint32_t stage = 128 * 128 + ((uint32_t)g.n_mma * 128 + 1023) / 1024 * 1024;
         const size_t smem = (size_t)g.stages * (t->split ? 2 : 1) * stage + 1024;
-        if (t->split) {
-            cudaFuncSetAttribute(k_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gemm_tc<true><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
-        } else {
-            cudaFuncSetAttribute(k_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_gemm_tc<false><<<dim3(mt, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
-        }
+        const int gx = persist ? min(mt, t->num_sms) : mt;
+        auto launch = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<dim3(gx, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
+        };
+        if (persist)
+            launch(k_gemm_tc<true, true>);
+        else if (t->split)
+            launch(k_gemm_tc<true, false>);
+        else
+            launch(k_gemm_tc<false, false>);
         cudaError_t ce = cudaGetLastError();
         if (ce != cudaSuccess) return cuda_fail(ce, "k_gemm_tc launch");
         return DLIC_OK;
