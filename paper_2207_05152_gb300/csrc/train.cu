@@ -753,27 +753,46 @@ __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n
     __shared__ __align__(16) uint16_t thi[kL1Ctx * kMaxHidden];
     __shared__ __align__(16) uint16_t tlo[kL1Ctx * kMaxHidden];
     __shared__ float xs[kL1Ctx][NMAX];
-    const int tid = threadIdx.x, b0 = blockIdx.x * kL1Ctx;
+    __shared__ uint16_t smask[kL1Ctx][kMaxHidden / 16];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, b0 = blockIdx.x * kL1Ctx;
     for (int i = tid; i < kL1Ctx * NMAX; i += 256) {
         const int r = i / NMAX, k = i % NMAX;
         xs[r][k] = b0 + r < B && k < n_in ? (float)ctx[(size_t)(b0 + r) * n_in + k] * 0.0078125f - 1.0f : 0.0f;
     }
     __syncthreads();
-    if (tid < h1) {
-        const int j = tid;
-        float w[NMAX];
+    // every thread runs the loop (the sign ballots need whole warps); units
+    // j >= h1 have zero weights and store nothing
+    const int j = tid;
+    const bool unit = j < h1;
+    float w[NMAX];
 #pragma unroll
-        for (int k = 0; k < NMAX; k++) w[k] = k < n_in ? W1[j * n_in + k] : 0.0f;
-        const float bj = b1[j];
-        for (int r = 0; r < kL1Ctx; r++) {
-            float acc = bj;
-            // (the zero weights past n_in add exact zeros)
+    for (int k = 0; k < NMAX; k++) w[k] = unit && k < n_in ? W1[j * n_in + k] : 0.0f;
+    const float bj = unit ? b1[j] : 0.0f;
+    for (int r = 0; r < kL1Ctx; r += 2) {
+        // two contexts at a time: two independent fma chains
+        float acc0 = bj, acc1 = bj;
+        // (the zero weights past n_in add exact zeros)
 #pragma unroll
-            for (int k = 0; k < NMAX; k++) acc = fmaf(xs[r][k], w[k], acc);
-            const float v = fmaxf(acc, 0.0f);
-            const uint16_t hi = f2bf(v);
-            thi[r * h1 + j] = hi;
-            if (p1) tlo[r * h1 + j] = f2bf(v - bf2f(hi));
+        for (int k = 0; k < NMAX; k++) {
+            acc0 = fmaf(xs[r][k], w[k], acc0);
+            acc1 = fmaf(xs[r + 1][k], w[k], acc1);
+        }
+        const float v0 = fmaxf(acc0, 0.0f), v1 = fmaxf(acc1, 0.0f);
+        const uint16_t hi0 = f2bf(v0), hi1 = f2bf(v1);
+        // the sign bits of the stored values, 32 units per ballot
+        const uint32_t pos0 = __ballot_sync(0xffffffffu, unit && hi0 != 0 && (hi0 & 0x8000u) == 0);
+        const uint32_t pos1 = __ballot_sync(0xffffffffu, unit && hi1 != 0 && (hi1 & 0x8000u) == 0);
+        if (unit) {
+            thi[r * h1 + j] = hi0;
+            thi[(r + 1) * h1 + j] = hi1;
+            if (p1) {
+                tlo[r * h1 + j] = f2bf(v0 - bf2f(hi0));
+                tlo[(r + 1) * h1 + j] = f2bf(v1 - bf2f(hi1));
+            }
+        }
+        if (lane < 2 && 32 * warp + 16 * lane < h1) {
+            smask[r][2 * warp + lane] = (uint16_t)(pos0 >> (16 * lane));
+            smask[r + 1][2 * warp + lane] = (uint16_t)(pos1 >> (16 * lane));
         }
     }
     __syncthreads();
@@ -785,18 +804,9 @@ __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n
         uint4 *dl = reinterpret_cast<uint4 *>(H1 + p1 + (size_t)b0 * h1);
         for (int i = tid; i < n16; i += 256) dl[i] = reinterpret_cast<const uint4 *>(tlo)[i];
     }
-    // the sign bits of the stored values: bit j of word (row, g) = unit 16 g + j > 0
+    // the sign bits: word (row, g) holds units 16 g .. 16 g + 15
     const int g16 = h1 / 16;
-    for (int i = tid; i < rows * g16; i += 256) {
-        const int r = i / g16, g = i % g16;
-        uint32_t pos = 0;
-#pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-            const uint32_t pair = (uint32_t)thi[r * h1 + 16 * g + j] | ((uint32_t)thi[r * h1 + 16 * g + j + 1] << 16);
-            pos |= bf16x2_positive(pair) << j;
-        }
-        M1[(size_t)(b0 + r) * g16 + g] = (uint16_t)pos;
-    }
+    for (int i = tid; i < rows * g16; i += 256) M1[(size_t)(b0 + i / g16) * g16 + i % g16] = smask[i / g16][i % g16];
 }
 
 // out[i] = scale * sum_z part[z * stride + i]: 32 columns per block, the
@@ -1112,7 +1122,9 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     if (bf) {
         const int nb = (B + kL1Ctx - 1) / kL1Ctx;
         uint16_t *H1 = static_cast<uint16_t *>(t->H1);
-        if (n_in <= 16)
+        if (n_in <= 12)
+            k_layer1<12><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+        else if (n_in <= 16)
             k_layer1<16><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
         else if (n_in <= 32)
             k_layer1<32><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
