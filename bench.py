@@ -148,6 +148,43 @@ def _profiled_traffic(kernel: str):
         return None
 
 
+def _profiled_instructions(kernel: str):
+    """Warp instructions per launch from the committed ncu summary of
+    `kernel`, or None when its source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        prof, src = PROFILES[kernel]
+        text = open(os.path.join(ROOT, prof)).read()
+        digest = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+        if f"sha256 prefix {digest}" not in text:
+            return None
+        m = re.search(r"instructions \(warp\) \(`smsp__inst_executed.sum`\) \| ([0-9.]+) inst", text)
+        return float(m.group(1)) if m else None
+    except (OSError, KeyError):
+        return None
+
+
+def measure_predict(codec, dev_img, flush, steps):
+    """CUDA-event time of dlic_predict (the encoder's prediction kernel alone:
+    network and frequency table of every pixel) on the image, L2 flushed
+    before every call."""
+    import torch
+    out = codec.predict([dev_img])
+    stream = torch.cuda.current_stream()
+    ts = []
+    for it in range(steps + 2):
+        flush.fill_(it & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        codec.predict([dev_img], out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 2:
+            ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -214,6 +251,9 @@ def run_ours(args):
                     clocks=sampler.summary() if sampler else None)
 
     r8 = measure(blob8, args.steps, args.warmup, clocks=True)
+    pcodec = Codec(blob8)
+    pred_ms = measure_predict(pcodec, dev_img, flush, max(3, args.steps))
+    pcodec.close()
     r32 = measure(blob32, max(2, args.steps // 3), 2)
     # the same image with the 9 x 9 causal window of Fig. 6 (78 priors)
     from paper_2207_05152_gb300 import model as M, workloads
@@ -308,6 +348,7 @@ def run_ours(args):
         "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
+        "roofline_encode": _encode_roofline(pred_ms, ops_per_px * N, bf16_peak, r8["clocks"]),
         "train": train,
         "batch": batch,
         "volume": volume,
@@ -324,6 +365,25 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _encode_roofline(ms, ops, bf16_peak, clocks):
+    """The encoder's prediction kernel (k_encode_tc) against both of its
+    ceilings: the tensor pipe (the network's multiply-adds as bf16 MMAs) and
+    instruction issue (152 SMs x 4 schedulers x 32 lanes per cycle; the
+    frequency table is plain ALU work), the latter from the committed ncu
+    instruction count of the same source."""
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    issue_peak = 152 * 4 * 32 * mhz * 1e6 / 1e12   # T lane-instructions/s
+    inst = _profiled_instructions("encode")
+    alu = inst * 32 / (ms * 1e-3) / 1e12 if inst else None
+    tens = ops / (ms * 1e-3) / 1e12
+    return {"kernel": "k_encode_tc (via dlic_predict)", "ms": round(ms, 4), "bound": "alu",
+            "achieved": round(alu, 3) if alu else None, "peak": round(issue_peak, 2), "unit": "T lane-instr/s",
+            "frac": round(alu / issue_peak, 4) if alu else None,
+            "tensor": {"achieved": round(tens, 2), "peak": bf16_peak, "unit": "TFLOP/s",
+                       "frac": round(tens / bf16_peak, 4)},
+            "peak_source": "issue peak from unit counts and the max SM clock; bf16 burst measured"}
 
 
 def measure_batch(args):

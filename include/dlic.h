@@ -227,6 +227,25 @@ DLIC_API dlic_status dlic_encode(const dlic_model *model, const dlic_image *h_im
                                  uint64_t *d_out_offsets, int32_t *d_status, void *d_workspace,
                                  size_t workspace_bytes, void *stream);
 
+/* The model's prediction for every pixel, without coding: the frequency-
+ * table entry of the pixel's own value, f | c << 16 (uint32; f the
+ * frequency, c the cumulative frequency below the value, the table summing
+ * to 2^16), computed by the same kernels and bits as dlic_encode (Sec. II-B:
+ * the network predicts a PDF per pixel, which is quantised to the table the
+ * rANS coder uses; Eq. 1).  The ideal code length of an image is the sum of
+ * -log2(f / 2^16) over its pixels, the "bits per pixel" a trained model is
+ * judged by (Sec. III-A).
+ *  d_fc:        device, image i's H_i x W_i entries in raster order at
+ *               element offset sum_{j<i} H_j W_j; 4-byte aligned.
+ *  d_status:    one int32 on the device, or NULL; DLIC_OK, DLIC_ERR_TIMEOUT
+ *               (a tensor-core wait ran out) or DLIC_ERR_INVALID (a 12-bit
+ *               sample above 4095).
+ *  d_workspace: when d_status is NULL, at least 4 bytes of device memory for
+ *               the status word; otherwise unused (may be NULL).
+ * Models with a 3D window are refused (DLIC_ERR_INVALID). */
+DLIC_API dlic_status dlic_predict(const dlic_model *model, const dlic_image *h_images, int n, uint32_t *d_fc,
+                                  int32_t *d_status, void *d_workspace, size_t workspace_bytes, void *stream);
+
 /* Size of the fixed scratch block of dlic_encode_noalloc (16 MiB). */
 #define DLIC_NOALLOC_SCRATCH_BYTES (16u << 20)
 

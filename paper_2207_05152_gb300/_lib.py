@@ -55,6 +55,7 @@ SIGNATURES = {
     "dlic_encode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_I), C.POINTER(_SZ)]),
     "dlic_encode": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _VP, _SZ, _VP]),
     "dlic_encode_noalloc": (_I, [_VP, _IMGP, _I, C.POINTER(_I), _VP, _SZ, _VP, _VP, _VP]),
+    "dlic_predict": (_I, [_VP, _IMGP, _I, _VP, _VP, _VP, _SZ, _VP]),
     "dlic_read_header": (_I, [_VP, _SZ, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                               C.POINTER(C.c_uint64)]),
     "dlic_decode_workspace_size": (_I, [_VP, _IMGP, _I, C.POINTER(_SZ)]),
@@ -166,6 +167,12 @@ def dlic_encode(model: int, images, streams, d_out: int, out_capacity: int, d_ou
     arr, n = images_array(images)
     check(lib().dlic_encode(model, arr, n, int_array(streams), d_out, out_capacity, d_out_offsets,
                             d_status or None, d_ws, ws_bytes, stream or None))
+
+
+def dlic_predict(model: int, images, d_fc: int, d_status: int = 0, d_ws: int = 0, ws_bytes: int = 0,
+                 stream: int = 0):
+    arr, n = images_array(images)
+    check(lib().dlic_predict(model, arr, n, d_fc, d_status or None, d_ws or None, ws_bytes, stream or None))
 
 
 def dlic_encode_noalloc(model: int, images, streams, d_out: int, out_capacity: int,

@@ -84,6 +84,19 @@ class Codec:
                          _stream_handle(stream))
         return out, offsets
 
+    def predict(self, images, out=None, status=None, stream=None):
+        """Per-pixel (f | c << 16) of every pixel's own value, raster order,
+        images back to back (uint32 as an int32 CUDA tensor); `status`, if
+        given, is a 1-element int32 CUDA tensor for the device status."""
+        desc = self._desc(images)
+        npx = sum(d[1] * d[2] for d in desc)
+        if out is None or out.numel() < npx:
+            out = torch.empty(max(npx, 1), dtype=torch.int32, device="cuda")
+        ws = self._workspace(256)
+        _lib.dlic_predict(self.handle, desc, out.data_ptr(), status.data_ptr() if status is not None else 0,
+                          ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return out
+
     def encode_to_bytes(self, images, streams=None):
         """Host bytes of each image's bitstream (synchronises)."""
         status = torch.zeros(1, dtype=torch.int32, device="cuda")

@@ -504,6 +504,58 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
     return DLIC_OK;
 }
 
+extern "C" dlic_status dlic_predict(const dlic_model *m, const dlic_image *im, int n, uint32_t *d_fc, int32_t *d_status,
+                                    void *d_ws, size_t ws_bytes, void *stream) {
+    if (!m) return fail(DLIC_ERR_INVALID, "null model");
+    if (m->dev.vol) return fail(DLIC_ERR_INVALID, "the model has a 3D window: its priors span slices");
+    dlic_status st = check_images(im, n, nullptr, false, m->dev.bits == 12 ? 2 : 1);
+    if (st) return st;
+    if (n == 0) return DLIC_OK;
+    if (!d_fc) return fail(DLIC_ERR_INVALID, "null output");
+    if (!d_status && (!d_ws || ws_bytes < 4)) return fail(DLIC_ERR_INVALID, "a status word or 4 bytes of workspace is needed");
+    if (reinterpret_cast<uintptr_t>(d_fc) & 3) return fail(DLIC_ERR_INVALID, "d_fc must be 4-byte aligned");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    int32_t *err = d_status ? d_status : static_cast<int32_t *>(d_ws);
+    {
+        cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    }
+    const bool use_tc = m->dev.nl == 3 && m->dev.bits == 8 && tc_supported(m->dev);
+    const int tile_px = use_tc ? 128 : kPredictTile;
+    uint64_t px0 = 0;   // element offset of the chunk's first image in d_fc
+    for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
+        const int cn = n - c0 < kMaxBatch ? n - c0 : kMaxBatch;
+        EncBatch *b = new EncBatch();
+        b->n = cn;
+        b->ws = reinterpret_cast<uint8_t *>(d_fc);
+        b->chunk_start = c0;
+        b->tile_px = tile_px;
+        b->raster = 1;
+        int tiles = 0;
+        for (int k = 0; k < cn; k++) {
+            const dlic_image &g = im[c0 + k];
+            EncImage &e = b->img[k];
+            e.pixels = g.pixels;
+            e.pitch = g.pitch;
+            e.H = g.height;
+            e.W = g.width;
+            e.S = g.height;
+            e.tile_begin = tiles;
+            const size_t N = (size_t)e.H * e.W;
+            tiles += (int)((N + tile_px - 1) / tile_px);
+            e.fc_off = 4 * px0;
+            px0 += N;
+        }
+        b->total_tiles = tiles;
+        cudaError_t e = use_tc                  ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
+                        : m->dev.bits == 12 ? launch_predict12(m->dev, *b, err, cs)
+                                            : launch_predict_cc(m->dev, *b, cs);
+        delete b;
+        if (e != cudaSuccess) return cuda_fail(e, "predict launch");
+    }
+    return DLIC_OK;
+}
+
 extern "C" dlic_status dlic_encode(const dlic_model *m, const dlic_image *im, int n, const int *streams,
                                    void *d_out, size_t out_capacity, uint64_t *d_out_offsets,
                                    int32_t *d_status, void *d_ws, size_t ws_bytes, void *stream) {

@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b
             const uint32_t c_lo = sym[p] + (uint32_t)((Ps * Q) >> 32);
             const uint32_t c_hi =
                 sym[p] == kSymbols12 - 1 ? kTotal : sym[p] + 1u + (uint32_t)(((Ps + Wsym) * Q) >> 32);
-            fc[stream_index(im.H, im.W, im.S, rr[p], cc[p])] = (c_hi - c_lo) | (c_lo << 16);
+            fc[b.raster ? (int64_t)rr[p] * im.W + cc[p] : stream_index(im.H, im.W, im.S, rr[p], cc[p])] =
+                (c_hi - c_lo) | (c_lo << 16);
         }
     }
 }

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kCH) k_predict_cc(DevModel m, EncBatch b) {
     const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
     const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
     uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
-    fc[stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
+    fc[b.raster ? (int64_t)r * im.W + c : stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kF32Threads, 2) k_predict_f32(DevModel m, EncB
             const uint32_t Q = table_q(W);
             const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
             const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
-            fc[stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
+            fc[b.raster ? (int64_t)r * im.W + c : stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
         }
     }
 }

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_encode_tc(DevModel m, EncBatc
             const uint32_t c_lo = (uint32_t)sym + __umulhi(Ps, Q);
             const uint32_t c_hi = sym == kSymbols - 1 ? kTotal : (uint32_t)sym + 1u + __umulhi(Ps + ws, Q);
             uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
-            fc[stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
+            fc[b.raster ? (int64_t)r * im.W + c : stream_index(im.H, im.W, im.S, r, c)] = (c_hi - c_lo) | (c_lo << 16);
         }
         tc::fence_before_sync();   // tensor-memory reads done before the next tile's MMAs
     }

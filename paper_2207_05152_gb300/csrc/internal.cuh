@@ -94,6 +94,7 @@ struct EncBatch {
     int total_tiles;
     uint8_t *ws;                  // workspace base
     uint64_t *sizes;              // per image bitstream bytes (in workspace)
+    int raster;                   // 1: (f, c) per pixel in raster order (dlic_predict), else stream order
     EncImage img[kMaxBatch];
 };
 
