@@ -9,6 +9,13 @@ gradient is the textbook adjoint of that expression: dL/dz = (softmax(z) -
 onehot(y)) / (B ln 2), then the dense-layer and ReLU adjoints.  Adam (Kingma
 and Ba 2015) with bias correction is the optimiser reading.  Everything here
 is float64 numpy; matrix products use numpy's matmul as a library primitive.
+
+The frequency-weighted loss (Sec. IV "Color Frequencies": the loss weighted
+by value frequency, so that rare values count more) takes a weight w_v per
+target value v: L = sum_b w_{y_b} * -log2 softmax(z_b)[y_b] / sum_b w_{y_b}.
+Its gradient replaces 1/B by w_{y_b} / sum w.  With every w_v = 1 it is the
+plain loss, and an integer weight k on a context is the same as k copies of
+it in the batch.
 """
 from __future__ import annotations
 
@@ -21,9 +28,18 @@ def features(ctx_u8: np.ndarray) -> np.ndarray:
     return ctx_u8.astype(np.float64) / 128.0 - 1.0
 
 
-def forward(params, ctx_u8, tgt):
-    """params: [(W1, b1), (W2, b2), (W3, b3)] (any float dtype).
-    Returns (loss_bits, cache)."""
+def _row_weights(tgt, weights):
+    """Per-context loss weights w_{y_b} / sum_b w_{y_b} (1/B unweighted)."""
+    y = np.asarray(tgt, np.int64)
+    if weights is None:
+        return np.full(y.size, 1.0 / y.size)
+    w = np.asarray(weights, np.float64)[y]
+    return w / w.sum()
+
+
+def forward(params, ctx_u8, tgt, weights=None):
+    """params: [(W1, b1), (W2, b2), (W3, b3)] (any float dtype); weights:
+    None, or one loss weight per target value.  Returns (loss_bits, cache)."""
     (w1, b1), (w2, b2), (w3, b3) = [(np.asarray(w, np.float64), np.asarray(b, np.float64))
                                     for w, b in params]
     x = features(ctx_u8)
@@ -36,19 +52,22 @@ def forward(params, ctx_u8, tgt):
     lse = zm[:, 0] + np.log(np.exp(z - zm).sum(axis=1))
     B = z.shape[0]
     nll = lse - z[np.arange(B), np.asarray(tgt, np.int64)]
-    loss = nll.mean() / LN2
+    loss = nll.mean() / LN2 if weights is None else float((_row_weights(tgt, weights) * nll).sum()) / LN2
     return loss, (x, a1, h1, a2, h2, z, lse)
 
 
-def gradient(params, ctx_u8, tgt):
+def gradient(params, ctx_u8, tgt, weights=None):
     """Analytic FP64 gradient: [(dW1, db1), (dW2, db2), (dW3, db3)], loss."""
-    loss, (x, a1, h1, a2, h2, z, lse) = forward(params, ctx_u8, tgt)
+    loss, (x, a1, h1, a2, h2, z, lse) = forward(params, ctx_u8, tgt, weights)
     w1, w2, w3 = [np.asarray(p[0], np.float64) for p in params]
     B = z.shape[0]
     p = np.exp(z - lse[:, None])
     dz = p
     dz[np.arange(B), np.asarray(tgt, np.int64)] -= 1.0
-    dz /= B * LN2
+    if weights is None:
+        dz /= B * LN2
+    else:
+        dz *= (_row_weights(tgt, weights) / LN2)[:, None]
     dw3 = dz.T @ h2
     db3 = dz.sum(axis=0)
     dh2 = dz @ w3
@@ -62,14 +81,14 @@ def gradient(params, ctx_u8, tgt):
     return [(dw1, db1), (dw2, db2), (dw3, db3)], loss
 
 
-def finite_difference(params, ctx_u8, tgt, layer: int, which: int, index, h: float):
+def finite_difference(params, ctx_u8, tgt, layer: int, which: int, index, h: float, weights=None):
     """Central difference (L(theta + h e) - L(theta - h e)) / 2h for one
     parameter (layer 0..2, which 0 = weight / 1 = bias, flat index)."""
     def loss_with(delta):
         ps = [[np.array(w, np.float64, copy=True), np.array(b, np.float64, copy=True)]
               for w, b in params]
         ps[layer][which].reshape(-1)[index] += delta
-        return forward([tuple(q) for q in ps], ctx_u8, tgt)[0]
+        return forward([tuple(q) for q in ps], ctx_u8, tgt, weights)[0]
     return (loss_with(h) - loss_with(-h)) / (2.0 * h)
 
 

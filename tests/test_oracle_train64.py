@@ -121,3 +121,42 @@ def test_gradient_vs_central_differences_cfg3_widths():
                 assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (layer, which, i, fd, g[i])
                 checked += 1
     assert checked >= 16
+
+
+def test_weighted_loss_pins():
+    # the frequency-weighted loss (Sec. IV "Color Frequencies"): unit weights
+    # give the plain loss; an integer weight k on a value is k copies of
+    # every context with that target; central differences agree
+    ctx, tgt = _batch(300, 31)
+    params = _params([12, 24, 24, 256], 32, gain=2.0)
+    ones = np.ones(256)
+    l0, _ = train64.forward(params, ctx, tgt)
+    l1, _ = train64.forward(params, ctx, tgt, ones)
+    assert abs(l0 - l1) <= 1e-13 * l0
+    g0, _ = train64.gradient(params, ctx, tgt)
+    g1, _ = train64.gradient(params, ctx, tgt, ones)
+    for a, b in zip(g0, g1):
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=1e-12, atol=1e-15)
+    w = np.ones(256)
+    w[np.unique(tgt)[::3]] = 3.0               # every third present value counts three times
+    rep = np.concatenate([np.arange(tgt.size)] + [np.nonzero(w[tgt] == 3.0)[0]] * 2)
+    lw, _ = train64.forward(params, ctx, tgt, w)
+    lr, _ = train64.forward(params, ctx[rep], tgt[rep])
+    assert abs(lw - lr) <= 1e-12 * lr
+    gw, _ = train64.gradient(params, ctx, tgt, w)
+    gr, _ = train64.gradient(params, ctx[rep], tgt[rep])
+    for a, b in zip(gw, gr):
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=1e-9, atol=1e-14)
+    _, (x, a1, h1, a2, h2, z, lse) = train64.forward(params, ctx, tgt, w)
+    for layer, which in [(0, 1), (1, 0), (2, 0), (2, 1)]:
+        g = gw[layer][which].reshape(-1)
+        for i in np.argsort(-np.abs(g))[:2]:
+            i = int(i)
+            theta = params[layer][which].reshape(-1)[i]
+            h = 1e-6 * max(1.0, abs(theta))
+            if not _kink_free(params, x, a1, h1, a2, layer, which, i, 2.0 * h):
+                continue
+            fd = train64.finite_difference(params, ctx, tgt, layer, which, i, h, w)
+            assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9
