@@ -388,10 +388,25 @@ DLIC_API size_t dlic_train_param_count(int n_in, int h1, int h2);
  * tensor-core operand as two bf16 planes (x = hi + lo) and accumulates
  * hi*hi + lo*hi + hi*lo (about 16 significant bits per operand, three times
  * the MMAs); DLIC_TRAIN_FP32 runs every product in FP32 on the CUDA cores.
- * Allocates its device memory here and frees it in dlic_trainer_destroy. */
+ * Allocates its device memory here and frees it in dlic_trainer_destroy.
+ * The calls below take any batch B >= 1: a batch above max_batch runs in
+ * chunks of max_batch contexts (each chunk's forward and backward on its
+ * own, the chunks' mean losses and gradients added with weights B_c / B),
+ * so the activations held at any time are one chunk's whatever B is; the
+ * result equals the one-pass result up to FP32 rounding of the sums. */
 DLIC_API dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, int max_batch, const float *h_params,
                                          dlic_trainer **out);
 DLIC_API dlic_status dlic_trainer_destroy(dlic_trainer *trainer);
+
+/* The frequency-weighted loss (Sec. IV "Color Frequencies": the loss is
+ * weighted by value frequency so that rare values count more): h_weights
+ * (host, 256 floats, finite, >= 0, not all zero) gives each target value v a
+ * weight w_v, and every later loss and gradient of this trainer become
+ *     sum_b w_{y_b} * -log2 softmax(z_b)[y_b] / sum_b w_{y_b},
+ * the plain mean when every w_v is 1; an integer weight k counts a context
+ * like k copies of it.  A batch must hold a context whose value has a
+ * positive weight.  h_weights NULL restores the plain loss. */
+DLIC_API dlic_status dlic_trainer_set_value_weights(dlic_trainer *trainer, const float *h_weights);
 
 /* Loss of a batch: d_ctx holds B x n_in u8 causal priors (the window's
  * order, as the coder gathers them), d_tgt B u8 target pixels; *d_loss_bits (device float)

@@ -71,6 +71,7 @@ SIGNATURES = {
     "dlic_train_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP]),
     "dlic_train_step": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "dlic_train_apply": (_I, [_VP, _VP, _VP]),
+    "dlic_trainer_set_value_weights": (_I, [_VP, _VP]),
     "dlic_trainer_params": (_I, [_VP, _VP, _I, _VP]),
     "dlic_trainer_status": (_I, [_VP, C.POINTER(C.c_int32)]),
 }
@@ -271,6 +272,17 @@ def dlic_train_backward(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: in
 
 def dlic_train_step(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, stream: int = 0):
     check(lib().dlic_train_step(trainer, d_ctx, d_tgt, B, d_loss, stream or None))
+
+
+def dlic_trainer_set_value_weights(trainer: int, weights=None):
+    if weights is None:
+        check(lib().dlic_trainer_set_value_weights(trainer, None))
+        return
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
+    if w.size != 256:
+        raise ValueError("one weight per 8-bit value (256)")
+    check(lib().dlic_trainer_set_value_weights(trainer, w.ctypes.data))
 
 
 def dlic_train_apply(trainer: int, d_grads: int, stream: int = 0):

@@ -51,6 +51,8 @@ struct EpiArgs {
     uint16_t *mask_out;         // BIAS_RELU (BF16 paths): the output's sign bits, [M][N / 16] words
     const uint8_t *tgt;         // SOFTMAX: targets
     float inv_batch_ln2;        // SOFTMAX: 1 / (B ln 2)
+    const float *vw;            // SOFTMAX: loss weight per target value (frequency-weighted loss), or null
+    const float *wnorm;         // SOFTMAX with vw: device {1 / (W ln 2), 1 / W}, W = sum_b vw[y_b]
     float *colsum;              // per-CTA column sums [gridDim.x][N] (db), or null
     float *loss;                // SOFTMAX: per-CTA loss sums [gridDim.x]
     int bf16;                   // outputs (and act) are bf16, else fp32
@@ -201,6 +203,10 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
     const float lse = mx + logf(se);
     const int y = valid ? e.tgt[m] : 0;
     const float inv = 1.0f / se;
+    // the row's gradient scale and loss weight: 1 / (B ln 2) and 1, or with
+    // value weights w_y / (W ln 2) and w_y / W
+    const float rw = e.vw ? e.vw[y] : 1.0f;
+    const float gscale = e.vw ? rw * e.wnorm[0] : e.inv_batch_ln2, lw = e.vw ? rw * e.wnorm[1] : 1.0f;
     for (int n0 = 0; n0 < N; n0 += 16) {
         float v[16];
         row.load16(n0, v);
@@ -218,9 +224,9 @@ __device__ void row_epilogue(int epi, const EpiArgs &e, const Row &row, int m, b
             float g = expf(zz - mx) * inv;
             if (n0 + j == y) {
                 g -= 1.0f;
-                *loss_acc += (lse - zz) / kLn2;
+                *loss_acc += lw * ((lse - zz) / kLn2);
             }
-            g *= e.inv_batch_ln2;
+            g *= gscale;
             store_val(e, e.out, (size_t)m * N + n0 + j, g, e.out_plane);
             store_val(e, e.outT, (size_t)(n0 + j) * e.ldT + m, g, e.outT_plane);
             v[j] = g;
@@ -570,22 +576,26 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT || PERSIST ? 1 : 2)
             const float mx = fmaxf(ma, mb);
             const float se = red[1][0][row] * fast_exp2(ma - mx) + red[1][1][row] * fast_exp2(mb - mx);
             const float lse2 = mx + log2f(se);
-            const float scale = valid ? e.inv_batch_ln2 / se : 0.0f;
             const int y = valid ? e.tgt[m] : -1;
+            // the row's gradient scale and loss weight: 1 / (B ln 2) and 1,
+            // or with value weights w_y / (W ln 2) and w_y / W
+            const float rw = e.vw && valid ? e.vw[y] : 1.0f;
+            const float rs = e.vw ? rw * e.wnorm[0] : e.inv_batch_ln2, lw = e.vw ? rw * e.wnorm[1] : 1.0f;
+            const float scale = valid ? rs / se : 0.0f;
             for_chunks(taddr, n_lo, n_hi, [&](int n0, float (&v)[16]) {
                 const bool has_y = (y & ~15) == n0;
                 if (has_y) {
                     // -log2 p_y = lse2 - z2_y
 #pragma unroll
                     for (int j = 0; j < 16; j++)
-                        if (n0 + j == y) loss_acc += lse2 - fmaf(v[j], kLog2e, s_bias[n0 + j]);
+                        if (n0 + j == y) loss_acc += lw * (lse2 - fmaf(v[j], kLog2e, s_bias[n0 + j]));
                 }
 #pragma unroll
                 for (int j = 0; j < 16; j++) v[j] = fast_exp2(fmaf(v[j], kLog2e, s_bias[n0 + j]) - mx) * scale;
                 if (has_y) {
 #pragma unroll
                     for (int j = 0; j < 16; j++)
-                        if (n0 + j == y) v[j] -= e.inv_batch_ln2;
+                        if (n0 + j == y) v[j] -= rs;
                 }
                 if (valid) store_row16(e, v, m, n0);
                 if (e.colsum) colsum_add(cs + n0, q, 256, v);
@@ -942,6 +952,9 @@ struct dlic_trainer {
     uint16_t *M1, *M2;                           // BF16 modes: sign bits of H1, H2 [batch][h / 16]
     void *XT, *H1T, *H2T, *DZT, *DA2T, *DA1T;    // FP32 path: transposed [features][batch]
     float *C, *part, *colsum, *losspart;
+    float *gacc, *closs, *lacc;   // batches above max_batch: gradient and loss sums over chunks
+    int weighted;                 // the frequency-weighted loss is on
+    float *vw, *wnorm;            // its weights per target value (256) and {1 / (W ln 2), 1 / W}
     int *err;
     std::vector<void *> allocs;
 };
@@ -1096,8 +1109,26 @@ dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
 // every activation row-major [batch][features] and read the weight-gradient
 // factors MN-major; the FP32 path also keeps transposed copies [features]
 // [batch] for its K-major CUDA-core GEMM.
+// W = sum_b vw[tgt[b]] in a fixed order (one CTA), and {1 / (W ln 2), 1 / W}.
+__global__ void __launch_bounds__(1024) k_wsum(const uint8_t *tgt, int B, const float *vw, float *wnorm) {
+    __shared__ float red[1024];
+    const int tid = threadIdx.x;
+    float s = 0.0f;
+    for (int b = tid; b < B; b += 1024) s += vw[tgt[b]];
+    red[tid] = s;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if (tid < off) red[tid] += red[tid + off];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        wnorm[0] = 1.0f / (red[0] * kLn2);
+        wnorm[1] = 1.0f / red[0];
+    }
+}
+
 dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss, bool backward,
-                cudaStream_t st) {
+                cudaStream_t st, bool wnorm_ready = false) {
     const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128, n_in = t->n_in, k1 = t->k1;
     const int bf = t->bf;
     ParamView p = view(t->params, n_in, h1, h2);
@@ -1142,10 +1173,16 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     e = EpiArgs{}; e.bias = p.b3; e.out = t->DZ; e.outT = t->DZT; e.tgt = tgt;
     e.out_plane = Bm * kSymbols; e.outT_plane = (size_t)kSymbols * Bm;
     e.inv_batch_ln2 = 1.0f / ((float)B * kLn2);
+    if (t->weighted) {
+        // the frequency-weighted loss: the batch's weight total first
+        if (!wnorm_ready) k_wsum<<<1, 1024, 0, st>>>(tgt, B, t->vw, t->wnorm);
+        e.vw = t->vw;
+        e.wnorm = t->wnorm;
+    }
     e.colsum = t->colsum; e.loss = t->losspart;
     if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, kSymbols, h2), B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
         return s;
-    reduce_parts(t->losspart, mt, 1, 1, d_loss, 1.0f / (float)B, 0, 0, st);
+    reduce_parts(t->losspart, mt, 1, 1, d_loss, t->weighted ? 1.0f : 1.0f / (float)B, 0, 0, st);
     if (!backward) {
         cudaError_t ce = cudaGetLastError();
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
@@ -1255,8 +1292,13 @@ extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, i
     }
     // split-K partials: up to one split per SM (BF16) or 64 (FP32)
     t->part = (float *)A(4 * (size_t)(t->num_sms > 64 ? t->num_sms : 64) * kSymbols * hmax);
-    t->colsum = (float *)A(4 * (Bm / 128) * kSymbols);
-    t->losspart = (float *)A(4 * (Bm / 128));
+    t->colsum = (float *)A(4 * ((Bm + 127) / 128) * kSymbols);   // one row per m-tile, the last one ragged
+    t->losspart = (float *)A(4 * ((Bm + 127) / 128));
+    t->gacc = (float *)A(4 * t->nparams);
+    t->vw = (float *)A(4 * kSymbols);
+    t->wnorm = (float *)A(8);
+    t->closs = (float *)A(8);
+    t->lacc = (float *)A(8);
     t->err = (int *)A(4);
     if (!ok) {
         dlic_trainer_destroy(t);
@@ -1286,8 +1328,45 @@ extern "C" dlic_status dlic_trainer_destroy(dlic_trainer *t) {
 static dlic_status check_batch(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B) {
     if (!t) return fail(DLIC_ERR_INVALID, "null trainer");
     if (!ctx || !tgt) return fail(DLIC_ERR_INVALID, "null batch");
-    if (B < 1 || B > t->max_batch) return fail(DLIC_ERR_CAPACITY, "batch %d outside [1, %d]", B, t->max_batch);
+    if (B < 1) return fail(DLIC_ERR_CAPACITY, "batch %d < 1", B);
     return DLIC_OK;
+}
+
+// acc = w g (first) or acc + w g, element by element.
+__global__ void k_accum(float *acc, const float *g, int n, float w, int first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) acc[i] = first ? w * g[i] : fmaf(w, g[i], acc[i]);
+}
+
+// A batch larger than the trainer's capacity, in chunks of max_batch
+// contexts: each chunk's forward (and backward) runs on its own, and its
+// mean loss (and gradient) is added with weight B_c / B, so that the
+// activations held at any time are one chunk's, whatever the batch.  The
+// result lands where the one-pass run puts it (d_loss, t->grads).
+static dlic_status run_chunked(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss,
+                               bool backward, cudaStream_t st) {
+    const int n = (int)t->nparams, nb = (n + 255) / 256;
+    // with value weights every chunk's terms are normalised by the whole
+    // batch's weight total, and the chunks simply add up
+    if (t->weighted) k_wsum<<<1, 1024, 0, st>>>(tgt, B, t->vw, t->wnorm);
+    for (int c0 = 0; c0 < B; c0 += t->max_batch) {
+        const int bc = min(t->max_batch, B - c0);
+        dlic_status s = run(t, ctx + (size_t)c0 * t->n_in, tgt + c0, bc, t->closs, backward, st, t->weighted);
+        if (s) return s;
+        const float w = t->weighted ? 1.0f : (float)bc / (float)B;
+        k_accum<<<1, 32, 0, st>>>(t->lacc, t->closs, 1, w, c0 == 0);
+        if (backward) k_accum<<<nb, 256, 0, st>>>(t->gacc, t->grads, n, w, c0 == 0);
+    }
+    cudaError_t ce = cudaMemcpyAsync(d_loss, t->lacc, 4, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess && backward)
+        ce = cudaMemcpyAsync(t->grads, t->gacc, 4ull * n, cudaMemcpyDeviceToDevice, st);
+    return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "chunk sums");
+}
+
+static dlic_status run_any(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss,
+                           bool backward, cudaStream_t st) {
+    return B <= t->max_batch ? run(t, ctx, tgt, B, d_loss, backward, st)
+                             : run_chunked(t, ctx, tgt, B, d_loss, backward, st);
 }
 
 extern "C" dlic_status dlic_train_forward(dlic_trainer *t, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
@@ -1295,7 +1374,7 @@ extern "C" dlic_status dlic_train_forward(dlic_trainer *t, const uint8_t *d_ctx,
     dlic_status s = check_batch(t, d_ctx, d_tgt, B);
     if (s) return s;
     if (!d_loss_bits) return fail(DLIC_ERR_INVALID, "null loss output");
-    return run(t, d_ctx, d_tgt, B, d_loss_bits, false, static_cast<cudaStream_t>(stream));
+    return run_any(t, d_ctx, d_tgt, B, d_loss_bits, false, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" dlic_status dlic_train_backward(dlic_trainer *t, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
@@ -1304,7 +1383,7 @@ extern "C" dlic_status dlic_train_backward(dlic_trainer *t, const uint8_t *d_ctx
     if (s) return s;
     if (!d_loss_bits) return fail(DLIC_ERR_INVALID, "null loss output");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    s = run(t, d_ctx, d_tgt, B, d_loss_bits, true, st);
+    s = run_any(t, d_ctx, d_tgt, B, d_loss_bits, true, st);
     if (s) return s;
     if (d_grads) {
         cudaError_t ce = cudaMemcpyAsync(d_grads, t->grads, 4 * t->nparams, cudaMemcpyDeviceToDevice, st);
@@ -1319,7 +1398,7 @@ extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, co
     if (s) return s;
     if (!d_loss_bits) return fail(DLIC_ERR_INVALID, "null loss output");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    s = run(t, d_ctx, d_tgt, B, d_loss_bits, true, st);
+    s = run_any(t, d_ctx, d_tgt, B, d_loss_bits, true, st);
     if (s) return s;
     t->step += 1;
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
@@ -1340,6 +1419,25 @@ extern "C" dlic_status dlic_train_apply(dlic_trainer *t, const float *d_grads, v
                                                              t->beta1, t->beta2, t->eps, c1, c2, sa);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "adam launch");
+}
+
+extern "C" dlic_status dlic_trainer_set_value_weights(dlic_trainer *t, const float *h_weights) {
+    if (!t) return fail(DLIC_ERR_INVALID, "null trainer");
+    if (!h_weights) {
+        t->weighted = 0;
+        return DLIC_OK;
+    }
+    double total = 0.0;
+    for (int v = 0; v < kSymbols; v++) {
+        if (!(h_weights[v] >= 0.0f) || !isfinite(h_weights[v]))
+            return fail(DLIC_ERR_INVALID, "value weight %d is negative or not finite", v);
+        total += h_weights[v];
+    }
+    if (!(total > 0.0)) return fail(DLIC_ERR_INVALID, "every value weight is zero");
+    cudaError_t ce = cudaMemcpy(t->vw, h_weights, 4 * kSymbols, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "value weights");
+    t->weighted = 1;
+    return DLIC_OK;
 }
 
 extern "C" dlic_status dlic_trainer_params(dlic_trainer *t, float *d_params, int write, void *stream) {

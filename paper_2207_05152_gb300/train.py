@@ -107,6 +107,19 @@ def sample_upsampled_contexts(images, count: int, seed: int, window=M.DEFAULT_WI
     return np.concatenate([ctx, c2]), np.concatenate([tgt, t2])
 
 
+def frequency_weights(images, alpha: float = 1.0):
+    """Loss weights per value, hist(v)^-alpha normalised to mean 1 over the
+    values present (absent values get 0): the frequency-weighted loss of
+    Sec. IV "Color Frequencies", the counterpart of rare_value_positions."""
+    flat = np.concatenate([im.reshape(-1) for im in images])
+    hist = np.bincount(flat, minlength=256).astype(np.float64)
+    w = np.zeros(256)
+    present = hist > 0
+    w[present] = hist[present] ** -float(alpha)
+    w[present] /= w[present].mean()
+    return w.astype(np.float32)
+
+
 def _contexts_at(images, idx, rr, cc, window):
     count = idx.size
     offs = M.window_offsets3(window)
@@ -174,6 +187,11 @@ class Trainer:
         _lib.dlic_train_step(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
                              self.loss.data_ptr(), self._stream())
         return self.loss
+
+    def set_value_weights(self, weights=None):
+        """The frequency-weighted loss (Sec. IV "Color Frequencies"): one loss
+        weight per target value (256), or None for the plain loss."""
+        _lib.dlic_trainer_set_value_weights(self.handle, weights)
 
     def apply(self, grads: torch.Tensor):
         """One Adam update with the given gradient (device float32, the

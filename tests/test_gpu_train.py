@@ -228,3 +228,75 @@ def test_apply_of_own_gradient_is_the_step(T, mode):
     assert a.status() == 0 and b.status() == 0
     for tr in (a, b, d.trainer):
         tr.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("fp32", 2e-4), ("bf16x3", 1e-3)])
+def test_batches_above_capacity_run_in_chunks(T, mode, tol):
+    # 2500 contexts through a trainer sized for 1000: chunks of 1000, 1000
+    # and 500 (a ragged last chunk, a ragged last tile in each); loss and
+    # gradient against the whole batch's FP64 reference, and a step taken
+    # from the chunk sums matches Adam on that gradient
+    layers, ctx, tgt = _data(T, 2500, 29, widths=(12, 64, 48, 256))
+    tr = T.Trainer(layers, mode, max_batch=1000)
+    c = torch.from_numpy(ctx).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    loss, g = tr.backward(c, t)
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    ref, loss64 = train64.gradient(layers, ctx, tgt)
+    assert abs(float(loss.item()) - loss64) <= 1e-3 * loss64
+    for (gw, gb), (rw, rb) in zip(T.unflatten(g.cpu().numpy(), 64, 48, 12), ref):
+        assert _rel(gw, rw) < tol and _rel(gb, rb) < tol
+    p0 = tr.params().cpu().numpy().astype(np.float64)
+    tr.step(c, t)
+    p1 = tr.params().cpu().numpy().astype(np.float64)
+    want, _, _ = train64.adam_step(p0, g.cpu().numpy().astype(np.float64), np.zeros_like(p0), np.zeros_like(p0), 1)
+    assert np.allclose(p1, want, rtol=1e-5, atol=1e-6)
+    # the forward alone gives the same chunked loss
+    l2 = float(tr.forward(c, t).item())
+    assert abs(l2 - loss64) <= 1e-3 * loss64
+    tr.close()
+
+
+@pytest.mark.parametrize("mode,tol", [("fp32", 2e-4), ("bf16x3", 1e-3)])
+def test_frequency_weighted_loss(T, mode, tol):
+    # weights hist(v)^-1 over the batch's values (Sec. IV "Color
+    # Frequencies"): loss and gradient against the FP64 weighted reference,
+    # in one pass and in chunks above the trainer's capacity; unit weights
+    # give the plain loss; clearing the weights restores it
+    imgs = [synth.phantom_image(64, 64, 40 + i) for i in range(3)]
+    ctx, tgt = T.sample_contexts(imgs, 2000, 41)
+    layers = synth.xavier_mlp([12, 64, 64, 256], 42)
+    w = T.frequency_weights(imgs)
+    c, t = torch.from_numpy(ctx).cuda(), torch.from_numpy(tgt).cuda()
+    ref, loss64 = train64.gradient(layers, ctx, tgt, w.astype(np.float64))
+    plain, plain64 = train64.gradient(layers, ctx, tgt)
+    for cap in (2000, 700):
+        tr = T.Trainer(layers, mode, max_batch=cap)
+        tr.set_value_weights(w)
+        loss, g = tr.backward(c, t)
+        torch.cuda.synchronize()
+        assert tr.status() == 0
+        assert abs(float(loss.item()) - loss64) <= 1e-3 * loss64
+        for (gw, gb), (rw, rb) in zip(T.unflatten(g.cpu().numpy(), 64, 64, 12), ref):
+            assert _rel(gw, rw) < tol and _rel(gb, rb) < tol
+        tr.set_value_weights(np.ones(256, np.float32))
+        loss1, g1 = tr.backward(c, t)
+        tr.set_value_weights(None)
+        loss0, g0 = tr.backward(c, t)
+        torch.cuda.synchronize()
+        assert abs(float(loss1.item()) - plain64) <= 1e-3 * plain64
+        assert abs(float(loss0.item()) - plain64) <= 1e-3 * plain64
+        for (gw, gb), (rw, rb) in zip(T.unflatten(g0.cpu().numpy(), 64, 64, 12), plain):
+            assert _rel(gw, rw) < tol and _rel(gb, rb) < tol
+        assert torch.allclose(g1, g0, rtol=1e-4, atol=1e-7)
+        tr.close()
+    from paper_2207_05152_gb300 import _lib
+    tr = T.Trainer(layers, mode, max_batch=16)
+    with pytest.raises(_lib.DlicError):
+        tr.set_value_weights(np.zeros(256, np.float32))
+    bad = np.ones(256, np.float32)
+    bad[3] = -1.0
+    with pytest.raises(_lib.DlicError):
+        tr.set_value_weights(bad)
+    tr.close()

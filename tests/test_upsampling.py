@@ -80,3 +80,21 @@ def test_seeded():
     b = T.sample_upsampled_contexts(imgs, 1000, 3)
     c = T.sample_upsampled_contexts(imgs, 1000, 4)
     assert np.array_equal(a[0], b[0]) and not np.array_equal(a[0], c[0])
+
+
+def test_frequency_weights():
+    # hist(v)^-alpha over the values present, mean 1, absent values 0: over
+    # the images' own pixels, alpha = 1 gives every present value the same
+    # total weight, alpha = 0 weight 1 per pixel (the plain loss)
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.phantom_image(48, 40, 60 + i) for i in range(2)]
+    flat = np.concatenate([im.reshape(-1) for im in imgs])
+    hist = np.bincount(flat, minlength=256)
+    w = T.frequency_weights(imgs, 1.0).astype(np.float64)
+    present = hist > 0
+    assert np.all(w[~present] == 0) and np.all(w[present] > 0)
+    assert abs(w[present].mean() - 1.0) < 1e-6
+    totals = (hist * w)[present]
+    assert np.allclose(totals, totals[0], rtol=1e-5)
+    w0 = T.frequency_weights(imgs, 0.0)
+    assert np.all(w0[present] == 1.0) and np.all(w0[~present] == 0)
