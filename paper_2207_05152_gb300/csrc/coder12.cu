@@ -23,8 +23,6 @@ static_assert(k12Tile == kPredictTile, "the encoder plans CUDA-core tiles of kPr
 constexpr uint64_t k12Slack = kTotal - kSymbols12;     // 2^16 - 4096: the table's free mass
 constexpr int k12InPitch = 16;                         // encoder: floats per pixel of the input rows
 constexpr int k12PerLane = kSymbols12 / 32;            // decoder: consecutive values each lane searches
-constexpr int k12Chains = 8;                           // decoder: logits each lane computes side by side
-static_assert(kSymbols12 % (32 * k12Chains) == 0, "the logit loop covers the values in whole steps");
 
 __device__ __forceinline__ uint32_t px12(const uint8_t *img, int64_t pitch, int r, int c) {
     return *reinterpret_cast<const uint16_t *>(img + (int64_t)r * pitch + 2 * (int64_t)c);
@@ -201,173 +199,239 @@ __global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b
 }
 
 // ---------------------------------------------------------------------------
-// Wavefront decoder (Sec. II-B "Preprocessor"): one CTA of 8 warps per
-// image.  The pixels of wave t = 3r + c go to the warps in chunks of 8, one
-// pixel per warp: the warp computes its network (lanes over units and
-// values), keeps the 4096 logits in shared memory, turns them into weights
-// in place, and each lane sums the weights of 128 consecutive values; a
-// 64-bit warp scan gives the cumulative mass at every lane's first value.
-// The rANS step then needs one lane: the one whose value range holds the
-// slot walks its 128 values.  Pixels that share a stream (rows S apart) take
-// their rANS steps in row order (rounds of the chunk, a CTA barrier each).
-// Shared memory per warp: the table [4096] (logits, then weights) and two
-// activation buffers [hmax].
+// Wavefront decoder (Sec. II-B "Preprocessor"): one cluster of P CTAs per
+// image.  CTA k owns the rows whose stream (r mod S) is k mod P, so every
+// stream's state stays in one CTA.  Per wave t = 3r + c each CTA takes its
+// pixels in chunks of 8 in row order: the priors come back from the output
+// image through L2 (other CTAs decoded them in earlier waves; one cluster
+// barrier per wave orders those stores before these loads), the hidden
+// layers run with thread = unit and the chunk's 8 pixels in registers, and
+// the 4096 logits with thread = value, so that every weight load of the
+// 4096 x h output layer (the bulk of the work) feeds 8 FMAs; each unit and
+// value accumulates from its bias in the fixed k order of the encoder.  One
+// warp per pixel then turns its 4096 logits into weights in place, each lane
+// summing 128 consecutive values, a 64-bit warp scan gives every lane's
+// cumulative mass, and the lane whose value range holds the slot walks it.
+// Pixels of one stream in one wave (S below the wave's length) take their
+// rANS steps in row order.
+// Shared memory: the chunk's logits, then weights [8][4096], and two
+// activation buffers [hmax][8] (unit-major, a unit's 8 pixels as two
+// 16-byte vectors).
 // ---------------------------------------------------------------------------
-__host__ __device__ inline size_t decode12_warp_bytes(int hmax) { return 4ull * kSymbols12 + 8ull * hmax; }
+constexpr int k12DecThreads = 256, k12DecWarps = k12DecThreads / 32, k12DecPix = 8;
+static_assert(k12DecWarps == k12DecPix, "one table warp per pixel of a chunk");
+__host__ __device__ inline size_t decode12_smem_bytes(int hmax) {
+    return 4ull * k12DecPix * kSymbols12 + 2ull * 4 * k12DecPix * (size_t)hmax + 4ull * k12DecPix * 16;
+}
 
-__global__ void __launch_bounds__(k12Threads) k_decode12(DevModel m, DecBatch b) {
+__device__ __forceinline__ uint32_t px12_cg(const uint8_t *img, int64_t pitch, int r, int c) {
+    return __ldcg(reinterpret_cast<const unsigned short *>(img + (int64_t)r * pitch + 2 * (int64_t)c));
+}
+
+__global__ void __launch_bounds__(k12DecThreads, 1) k_decode12(DevModel m, DecBatch b, int P) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t lut2[kTableSteps];
-    __shared__ int s_err;
+    __shared__ int s_err, s_n;
+    __shared__ int s_rows[k12DecPix * 32];   // this CTA's rows of the wave (a slice of them)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const DecImage &im = b.img[blockIdx.x];
-    expand_lut(m.lut, lut2, tid, k12Threads);
+    uint32_t k = 0;
+    if (P > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(k));
+    const DecImage &im = b.img[blockIdx.x / P];
+    expand_lut(m.lut, lut2, tid, k12DecThreads);
     if (tid == 0) s_err = 0;
     StreamState *st = reinterpret_cast<StreamState *>(b.ws + im.st_off);
     const uint8_t *in = b.in + im.in_off;
     int S;
     const uint16_t *pay;
-    if (!decode_setup(m, im, in, st, &S, &pay)) {   // its barriers also publish lut2 and s_err
-        if (tid == 0) b.status[im.sidx] = DLIC_ERR_CORRUPT;
-        return;
+    // every CTA parses the same header; the cluster barrier after it keeps
+    // the set-up writes of the stream states ahead of every update
+    const bool ok = decode_setup(m, im, in, st, &S, &pay);   // its barriers also publish lut2 and s_err
+    if (P > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    if (!ok) {
+        if (tid == 0 && k == 0) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
+        return;   // uniform: every CTA read the same header
     }
     const int hmax = m.hmax;
-    uint8_t *wbase = smem + (size_t)warp * decode12_warp_bytes(hmax);
-    float *zs = reinterpret_cast<float *>(wbase);         // logits, then (as u32) the weights
-    uint32_t *wts = reinterpret_cast<uint32_t *>(wbase);
-    float *hA = reinterpret_cast<float *>(wbase + 4ull * kSymbols12);
-    float *hB = hA + hmax;
+    float *zs = reinterpret_cast<float *>(smem);                                   // [8][4096]
+    float *hA = zs + (size_t)k12DecPix * kSymbols12, *hB = hA + (size_t)k12DecPix * hmax;   // [hmax][8]
+    float *xin = hB + (size_t)k12DecPix * hmax;                                    // [8][16]
     const int L = m.nl - 1;
     const DevLayer lo = m.layers[L];
     const float *wo = static_cast<const float *>(lo.w);
+    const int hl = lo.n_in;
     const int H = im.H, W = im.W;
     const int T = 3 * (H - 1) + W;
     for (int t = 0; t < T; t++) {
-        if (s_err) break;
         const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
         const int r_hi = min(H - 1, t / 3);
-        const int n_t = r_hi - r_lo + 1;
-        for (int base = 0; base < n_t; base += k12Warps) {
-            const int pix = base + warp;
-            const bool active = pix < n_t;   // uniform over the warp
-            const int r = r_lo + pix, c = t - 3 * r;
-            uint64_t Q = 0, P0 = 0;
-            uint32_t lsum = 0;
-            if (active) {
-                // hidden layers: layer 0 from the window in registers
-                float x[kPriors];
-#pragma unroll
-                for (int k = 0; k < kPriors; k++) x[k] = input12(im.pixels, im.pitch, H, W, r, c, k);
-                const float *hin = nullptr;
-                float *hout = hA;
+        const bool repeats = r_hi - r_lo + 1 > S;   // two rows of one stream on this wave
+        // this CTA's rows of the wave, k8 * 32 of them at a time, in row order
+        for (int seg = r_lo; seg <= r_hi; seg += k12DecPix * 32) {
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+            if (warp == 0) {
+                int n = 0;
+                for (int g = 0; g < k12DecPix; g++) {
+                    const int r = seg + 32 * g + lane;
+                    const bool own = r <= r_hi && (P == 1 || ((r % S) & (P - 1)) == (int)k);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, own);
+                    if (own) s_rows[n + __popc(bal & ((1u << lane) - 1u))] = r;
+                    n += __popc(bal);
+                }
+                if (lane == 0) s_n = n;
+            }
+            __syncthreads();
+            const int nk = s_n;
+            for (int base = 0; base < nk; base += k12DecPix) {
+                const int np = min(k12DecPix, nk - base);
+                // priors of the chunk's pixels (pixels past np repeat the first)
+                for (int i = tid; i < k12DecPix * kPriors; i += k12DecThreads) {
+                    const int p = i / kPriors, q = i % kPriors;
+                    const int r = s_rows[base + (p < np ? p : 0)], c = t - 3 * r;
+                    const int dr = q < 5 ? -2 : (q < 10 ? -1 : 0);
+                    const int dc = q < 5 ? q - 2 : (q < 10 ? q - 7 : q - 12);
+                    const int rr = r + dr, cc = c + dc;
+                    const uint32_t v = (rr >= 0 && rr < H && cc >= 0 && cc < W) ? px12_cg(im.pixels, im.pitch, rr, cc) : 0u;
+                    xin[p * 16 + q] = __fmaf_rn((float)v, 0.00048828125f, -1.0f);   // v / 2048 - 1
+                }
+                __syncthreads();
+                // hidden layers: thread = unit, the chunk's 8 pixels side by side
+                float *hin = nullptr, *hout = hA;
                 for (int l = 0; l < L; l++) {
                     const DevLayer ly = m.layers[l];
                     const float *wt = static_cast<const float *>(ly.w);
-                    for (int u = lane; u < ly.n_out; u += 32) {
-                        float acc = __ldg(ly.a + u);
-                        if (l == 0) {
+                    for (int u = tid; u < ly.n_out; u += k12DecThreads) {
+                        float acc[k12DecPix];
+                        const float bias = __ldg(ly.a + u);
 #pragma unroll
-                            for (int k = 0; k < kPriors; k++) acc = __fmaf_rn(x[k], __ldg(wt + (size_t)k * ly.n_out + u), acc);
-                        } else {
-                            for (int k = 0; k < ly.n_in; k++)
-                                acc = __fmaf_rn(hin[k], __ldg(wt + (size_t)k * ly.n_out + u), acc);
+                        for (int p = 0; p < k12DecPix; p++) acc[p] = bias;
+                        for (int kk = 0; kk < ly.n_in; kk++) {
+                            const float w = __ldg(wt + (size_t)kk * ly.n_out + u);
+                            if (l == 0) {
+#pragma unroll
+                                for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(xin[p * 16 + kk], w, acc[p]);
+                            } else {
+                                const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix);
+                                const float4 bq = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4);
+                                const float x[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+                                for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(x[p], w, acc[p]);
+                            }
                         }
-                        hout[u] = acc > 0.0f ? acc : 0.0f;
+                        float4 o0, o1;
+                        o0.x = acc[0] > 0.0f ? acc[0] : 0.0f; o0.y = acc[1] > 0.0f ? acc[1] : 0.0f;
+                        o0.z = acc[2] > 0.0f ? acc[2] : 0.0f; o0.w = acc[3] > 0.0f ? acc[3] : 0.0f;
+                        o1.x = acc[4] > 0.0f ? acc[4] : 0.0f; o1.y = acc[5] > 0.0f ? acc[5] : 0.0f;
+                        o1.z = acc[6] > 0.0f ? acc[6] : 0.0f; o1.w = acc[7] > 0.0f ? acc[7] : 0.0f;
+                        *reinterpret_cast<float4 *>(hout + u * k12DecPix) = o0;
+                        *reinterpret_cast<float4 *>(hout + u * k12DecPix + 4) = o1;
                     }
-                    __syncwarp();
+                    __syncthreads();
                     hin = hout;
                     hout = hout == hA ? hB : hA;
                 }
-                // logits and their maximum: each lane runs eight values'
-                // chains side by side (values i, i + 32, ..., i + 224)
-                float mx = -INFINITY;
-                for (int i = lane; i < kSymbols12; i += 32 * k12Chains) {
-                    float acc[k12Chains];
+                // logits: thread = value, one weight load for the 8 pixels
+                for (int j = tid; j < kSymbols12; j += k12DecThreads) {
+                    float acc[k12DecPix];
+                    const float bias = __ldg(lo.a + j);
 #pragma unroll
-                    for (int j = 0; j < k12Chains; j++) acc[j] = __ldg(lo.a + i + 32 * j);
-                    for (int k = 0; k < lo.n_in; k++) {
-                        const float hk = hin[k];
-                        const float *wk = wo + (size_t)k * kSymbols12 + i;
+                    for (int p = 0; p < k12DecPix; p++) acc[p] = bias;
+                    for (int kk = 0; kk < hl; kk++) {
+                        const float w = __ldg(wo + (size_t)kk * kSymbols12 + j);
+                        const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix);
+                        const float4 bq = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4);
+                        const float x[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
 #pragma unroll
-                        for (int j = 0; j < k12Chains; j++) acc[j] = __fmaf_rn(hk, __ldg(wk + 32 * j), acc[j]);
+                        for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(x[p], w, acc[p]);
                     }
 #pragma unroll
-                    for (int j = 0; j < k12Chains; j++) {
-                        zs[i + 32 * j] = acc[j];
-                        mx = acc[j] > mx ? acc[j] : mx;
-                    }
-                }
-                mx = warp_max(mx);
-                __syncwarp();
-                // weights in place over the lane's consecutive values, and their sum
-                const int i0 = k12PerLane * lane;
-                for (int i = i0; i < i0 + k12PerLane; i++) {
-                    const uint32_t w = table_weight2(mx, zs[i], m.tscale, lut2);
-                    wts[i] = w;
-                    lsum += w;
-                }
-                // inclusive scan of the lane sums: the mass below each lane's first value
-                uint64_t incl = lsum;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint64_t o = __shfl_up_sync(0xffffffffu, incl, off);
-                    if (lane >= off) incl += o;
-                }
-                P0 = incl - lsum;
-                Q = table_q12(__shfl_sync(0xffffffffu, incl, 31));
-            }
-            const int rounds = (min(k12Warps, n_t - base) + S - 1) / S;
-            for (int rnd = 0; rnd < rounds; rnd++) {
-                if (active && warp / S == rnd) {
-                    StreamState q = st[r % S];
-                    const uint32_t slot = q.x & 0xFFFFu;
-                    const int i0 = k12PerLane * lane;
-                    const uint32_t c0 = (uint32_t)i0 + (uint32_t)((P0 * Q) >> 32);
-                    const uint32_t c1 = lane == 31 ? kTotal
-                                                   : (uint32_t)(i0 + k12PerLane) + (uint32_t)(((P0 + lsum) * Q) >> 32);
-                    if (c0 <= slot && slot < c1) {   // exactly one lane: the ranges tile [0, 2^16)
-                        uint64_t P = P0;
-                        uint32_t c_lo = c0, f = 1;
-                        int sym = i0 + k12PerLane - 1;
-                        for (int i = i0; i < i0 + k12PerLane; i++) {
-                            const uint32_t w = wts[i];
-                            const uint32_t lo_i = (uint32_t)i + (uint32_t)((P * Q) >> 32);
-                            const uint32_t hi_i =
-                                i == kSymbols12 - 1 ? kTotal : (uint32_t)i + 1u + (uint32_t)(((P + w) * Q) >> 32);
-                            if (hi_i > slot) {
-                                sym = i;
-                                c_lo = lo_i;
-                                f = hi_i - lo_i;
-                                break;
-                            }
-                            P += w;
-                        }
-                        q.x = f * (q.x >> 16) + slot - c_lo;
-                        if (q.x < kRansL) {
-                            if (q.pos < q.end) {
-                                q.x = (q.x << 16) | pay[q.pos];
-                                q.pos++;
-                            } else {
-                                s_err = 1;
-                            }
-                        }
-                        st[r % S] = q;
-                        *reinterpret_cast<uint16_t *>(im.pixels + (int64_t)r * im.pitch + 2 * (int64_t)c) =
-                            (uint16_t)sym;
-                    }
+                    for (int p = 0; p < k12DecPix; p++) zs[(size_t)p * kSymbols12 + j] = acc[p];
                 }
                 __syncthreads();
+                // tables, one warp per pixel: maximum, weights in place, lane sums
+                uint64_t Q = 0, P0 = 0;
+                uint32_t lsum = 0;
+                const int i0 = k12PerLane * lane;
+                float *zw = zs + (size_t)warp * kSymbols12;
+                uint32_t *wts = reinterpret_cast<uint32_t *>(zw);
+                if (warp < np) {
+                    float mx = -INFINITY;
+                    for (int i = lane; i < kSymbols12; i += 32) mx = zw[i] > mx ? zw[i] : mx;
+                    mx = warp_max(mx);
+                    __syncwarp();
+                    for (int i = i0; i < i0 + k12PerLane; i++) {
+                        const uint32_t w = table_weight2(mx, zw[i], m.tscale, lut2);
+                        wts[i] = w;
+                        lsum += w;
+                    }
+                    // inclusive scan of the lane sums: the mass below each lane's first value
+                    uint64_t incl = lsum;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const uint64_t o = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += o;
+                    }
+                    P0 = incl - lsum;
+                    Q = table_q12(__shfl_sync(0xffffffffu, incl, 31));
+                }
+                // rANS steps: all at once, or in row order when a stream repeats
+                for (int rnd = 0; rnd < (repeats ? np : 1); rnd++) {
+                    if (warp < np && (!repeats || warp == rnd)) {
+                        const int r = s_rows[base + warp], c = t - 3 * r;
+                        const int s = r % S;
+                        StreamState q = st[s];
+                        const uint32_t slot = q.x & 0xFFFFu;
+                        const uint32_t c0 = (uint32_t)i0 + (uint32_t)((P0 * Q) >> 32);
+                        const uint32_t c1 =
+                            lane == 31 ? kTotal : (uint32_t)(i0 + k12PerLane) + (uint32_t)(((P0 + lsum) * Q) >> 32);
+                        if (c0 <= slot && slot < c1) {   // exactly one lane: the ranges tile [0, 2^16)
+                            uint64_t Pc = P0;
+                            uint32_t c_lo = c0, f = 1;
+                            int sym = i0 + k12PerLane - 1;
+                            for (int i = i0; i < i0 + k12PerLane; i++) {
+                                const uint32_t w = wts[i];
+                                const uint32_t lo_i = (uint32_t)i + (uint32_t)((Pc * Q) >> 32);
+                                const uint32_t hi_i =
+                                    i == kSymbols12 - 1 ? kTotal : (uint32_t)i + 1u + (uint32_t)(((Pc + w) * Q) >> 32);
+                                if (hi_i > slot) {
+                                    sym = i;
+                                    c_lo = lo_i;
+                                    f = hi_i - lo_i;
+                                    break;
+                                }
+                                Pc += w;
+                            }
+                            q.x = f * (q.x >> 16) + slot - c_lo;
+                            if (q.x < kRansL) {
+                                if (q.pos < q.end) {
+                                    q.x = (q.x << 16) | pay[q.pos];
+                                    q.pos++;
+                                } else {
+                                    s_err = 1;
+                                }
+                            }
+                            st[s] = q;
+                            *reinterpret_cast<uint16_t *>(im.pixels + (int64_t)r * im.pitch + 2 * (int64_t)c) =
+                                (uint16_t)sym;
+                        }
+                    }
+                    if (repeats) __syncthreads();
+                }
+                __syncthreads();   // the logits and activations are free again
             }
         }
+        // this wave's pixels in the image before any CTA's next gather
+        if (P > 1) asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        else __syncthreads();
     }
+    // the final states of this CTA's streams must be back at L with every word read
+    for (int s = tid; s < S; s += k12DecThreads)
+        if (P == 1 || (s & (P - 1)) == (int)k) {
+            const StreamState q = st[s];
+            if (q.x != kRansL || q.pos != q.end) s_err = 1;
+        }
     __syncthreads();
-    // final states must be back at the initial value L with every word read
-    for (int s = tid; s < S && !s_err; s += k12Threads) {
-        const StreamState q = st[s];
-        if (q.x != kRansL || q.pos != q.end) s_err = 1;
-    }
-    __syncthreads();
-    if (tid == 0) b.status[im.sidx] = s_err ? DLIC_ERR_CORRUPT : DLIC_OK;
+    if (tid == 0) atomicMax(b.status + im.sidx, s_err ? (int)DLIC_ERR_CORRUPT : (int)DLIC_OK);
 }
 
 cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cudaStream_t st) {
@@ -383,11 +447,36 @@ cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cud
 cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t st) {
     if (b.n == 0) return cudaSuccess;
     if (m.bits != 12 || m.precision != DLIC_FP32 || !default_window(m) || !m.layers) return cudaErrorNotSupported;
-    const size_t sm = (size_t)k12Warps * decode12_warp_bytes(m.hmax);
+    const size_t sm = decode12_smem_bytes(m.hmax);
     cudaError_t e = cudaFuncSetAttribute(k_decode12, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_decode12<<<b.n, k12Threads, sm, st>>>(m, b);
-    return cudaGetLastError();
+    e = cudaFuncSetAttribute(k_decode12, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    // cluster size: about 8 pixels of the longest wave per CTA, at most 16
+    int wave = 1;
+    for (int i = 0; i < b.n; i++) wave = max(wave, min(b.img[i].H, (b.img[i].W + 2) / 3));
+    int P = 1;
+    while (P < 16 && P * k12DecPix < wave) P <<= 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(k12DecThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (;;) {
+        attr[0].val.clusterDim.x = (unsigned)P;
+        cfg.gridDim = dim3((unsigned)(b.n * P));
+        int nclusters = 0;
+        if (P == 1 || (cudaOccupancyMaxActiveClusters(&nclusters, k_decode12, &cfg) == cudaSuccess && nclusters > 0))
+            break;
+        cudaGetLastError();
+        P >>= 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k_decode12, m, b, P);
 }
 
 }  // namespace dlic
