@@ -205,6 +205,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     size_t offs[3 * kMaxLayers + 1] = {0};
     const int kTcImage = 3 * kMaxLayers;
     const size_t off_table = deep ? put(std::vector<DevLayer>(nl).data(), sizeof(DevLayer) * nl) : 0;
+    size_t off_w3tiles = 0;   // 12-bit: the output layer tiled for the decoder
     const uint8_t *p = b + hdr;
     if (prec == DLIC_FP32) {
         for (int l = 0; l < nl; l++) {
@@ -216,6 +217,20 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             p += 4ull * dout[l];
             offs[3 * l] = put(wt.data(), wt.size() * 4);
             offs[3 * l + 1] = put(bias.data(), bias.size() * 4);
+            if (twelve && l == nl - 1) {
+                // the 12-bit decoder's copy of the output layer in 16 x 256
+                // tiles (block q of 256 values, k tile kt of 16 rows, rows past
+                // the layer's inputs zero), one bulk copy each
+                const int KT = (din[l] + 15) / 16;
+                std::vector<float> tiles((size_t)kSymbols12 * 16 * KT, 0.0f);
+                for (int q = 0; q < kSymbols12 / 256; q++)
+                    for (int kt = 0; kt < KT; kt++)
+                        for (int r = 0; r < 16 && 16 * kt + r < din[l]; r++)
+                            for (int j = 0; j < 256; j++)
+                                tiles[(((size_t)q * KT + kt) * 16 + r) * 256 + j] =
+                                    wt[(size_t)(16 * kt + r) * dout[l] + 256 * q + j];
+                off_w3tiles = put(tiles.data(), tiles.size() * 4);
+            }
         }
     } else {
         const int8_t *raw[kMaxLayers];
@@ -288,7 +303,9 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     }
     d.lut = reinterpret_cast<const uint32_t *>(base + off_lut);
     if (deep) {
-        // the kernels read the layer table only
+        // the kernels read the layer table only (and the 12-bit decoder the
+        // tiled output layer)
+        if (twelve) d.w3t = reinterpret_cast<const float *>(base + off_w3tiles);
     } else if (prec == DLIC_FP32) {
         d.w1t = reinterpret_cast<const float *>(base + offs[0]);
         d.b1 = reinterpret_cast<const float *>(base + offs[1]);

@@ -13,6 +13,7 @@
 // encoder and the decoder compute the same logits bit for bit.
 #include "coder_device.cuh"
 #include "decode_setup.cuh"
+#include "tc.cuh"
 
 namespace dlic {
 
@@ -218,10 +219,16 @@ __global__ void __launch_bounds__(k12Threads) k_predict12(DevModel m, EncBatch b
 // activation buffers [hmax][8] (unit-major, a unit's 8 pixels as two
 // 16-byte vectors).
 // ---------------------------------------------------------------------------
-constexpr int k12DecThreads = 256, k12DecWarps = k12DecThreads / 32, k12DecPix = 8;
-static_assert(k12DecWarps == k12DecPix, "one table warp per pixel of a chunk");
+constexpr int k12DecThreads = 512, k12DecWarps = k12DecThreads / 32, k12DecPix = 8;
+static_assert(k12DecWarps >= k12DecPix, "one table warp per pixel of a chunk");
+// The output layer streams through two stages of two 16 x 256 weight tiles
+// (the model's tiled copy: tile (block q, k tile kt) holds rows 16 kt ..
+// 16 kt + 15 of W^T at values 256 q .. 256 q + 255, 16 KB).
+constexpr int k12TileRows = 16, k12TileFloats = k12TileRows * 256, k12StageFloats = 2 * k12TileFloats;
+constexpr long long k12CopyWaitLimit = 4000000000LL;   // clock cycles (about 2 s); a copy from L2 always lands
 __host__ __device__ inline size_t decode12_smem_bytes(int hmax) {
-    return 4ull * k12DecPix * kSymbols12 + 2ull * 4 * k12DecPix * (size_t)hmax + 4ull * k12DecPix * 16;
+    return 4ull * k12DecPix * kSymbols12 + 2ull * 4 * k12StageFloats + 2ull * 4 * k12DecPix * (size_t)hmax +
+           4ull * k12DecPix * 16;
 }
 
 __device__ __forceinline__ uint32_t px12_cg(const uint8_t *img, int64_t pitch, int r, int c) {
@@ -233,12 +240,20 @@ __global__ void __launch_bounds__(k12DecThreads, 1) k_decode12(DevModel m, DecBa
     __shared__ uint32_t lut2[kTableSteps];
     __shared__ int s_err, s_n;
     __shared__ int s_rows[k12DecPix * 32];   // this CTA's rows of the wave (a slice of them)
+    __shared__ uint64_t wbar[2];             // output-layer stages filled
+    __shared__ int s_cfail;                  // a stage's copy did not land: no further copies
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t k = 0;
     if (P > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(k));
     const DecImage &im = b.img[blockIdx.x / P];
     expand_lut(m.lut, lut2, tid, k12DecThreads);
-    if (tid == 0) s_err = 0;
+    if (tid == 0) {
+        s_err = 0;
+        s_cfail = 0;
+        tc::mbar_init(&wbar[0], 1);
+        tc::mbar_init(&wbar[1], 1);
+        tc::fence_mbar_init();
+    }
     StreamState *st = reinterpret_cast<StreamState *>(b.ws + im.st_off);
     const uint8_t *in = b.in + im.in_off;
     int S;
@@ -253,7 +268,8 @@ __global__ void __launch_bounds__(k12DecThreads, 1) k_decode12(DevModel m, DecBa
     }
     const int hmax = m.hmax;
     float *zs = reinterpret_cast<float *>(smem);                                   // [8][4096]
-    float *hA = zs + (size_t)k12DecPix * kSymbols12, *hB = hA + (size_t)k12DecPix * hmax;   // [hmax][8]
+    float *wstage = zs + (size_t)k12DecPix * kSymbols12;                           // [2][2 tiles]
+    float *hA = wstage + 2 * k12StageFloats, *hB = hA + (size_t)k12DecPix * hmax;  // [hmax][8]
     float *xin = hB + (size_t)k12DecPix * hmax;                                    // [8][16]
     const int L = m.nl - 1;
     const DevLayer lo = m.layers[L];
@@ -261,6 +277,22 @@ __global__ void __launch_bounds__(k12DecThreads, 1) k_decode12(DevModel m, DecBa
     const int hl = lo.n_in;
     const int H = im.H, W = im.W;
     const int T = 3 * (H - 1) + W;
+    const int KT = (hl + k12TileRows - 1) / k12TileRows;   // k tiles of the output layer
+    const int nstage = (kSymbols12 / 512) * KT;            // stages per chunk: 8 value-block pairs x KT
+    long long g0 = 0;                                      // stages issued and consumed so far
+    // stage g: blocks 2 qp, 2 qp + 1 at k tile kt (g - g0 = qp KT + kt)
+    auto issue = [&](long long g) {
+        const int loc = (int)(g - g0), qp = loc / KT, kt = loc % KT, stg = (int)(g & 1);
+        const uint32_t bar_a = tc::smem_addr(&wbar[stg]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(4u * k12StageFloats)
+                     : "memory");
+        for (int h = 0; h < 2; h++)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tc::smem_addr(wstage + stg * k12StageFloats + h * k12TileFloats)),
+                         "l"(m.w3t + ((size_t)(2 * qp + h) * KT + kt) * k12TileFloats), "r"(4u * k12TileFloats),
+                         "r"(bar_a)
+                         : "memory");
+    };
     for (int t = 0; t < T; t++) {
         const int r_lo = t - W + 1 > 0 ? (t - W + 3) / 3 : 0;
         const int r_hi = min(H - 1, t / 3);
@@ -300,52 +332,82 @@ __global__ void __launch_bounds__(k12DecThreads, 1) k_decode12(DevModel m, DecBa
                 for (int l = 0; l < L; l++) {
                     const DevLayer ly = m.layers[l];
                     const float *wt = static_cast<const float *>(ly.w);
-                    for (int u = tid; u < ly.n_out; u += k12DecThreads) {
-                        float acc[k12DecPix];
+                    const int ph = tid >> 8;   // pixels 4 ph .. 4 ph + 3
+                    for (int u = tid & 255; u < ly.n_out; u += 256) {
+                        float acc[4];
                         const float bias = __ldg(ly.a + u);
 #pragma unroll
-                        for (int p = 0; p < k12DecPix; p++) acc[p] = bias;
+                        for (int p = 0; p < 4; p++) acc[p] = bias;
                         for (int kk = 0; kk < ly.n_in; kk++) {
                             const float w = __ldg(wt + (size_t)kk * ly.n_out + u);
                             if (l == 0) {
 #pragma unroll
-                                for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(xin[p * 16 + kk], w, acc[p]);
+                                for (int p = 0; p < 4; p++) acc[p] = __fmaf_rn(xin[(4 * ph + p) * 16 + kk], w, acc[p]);
                             } else {
-                                const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix);
-                                const float4 bq = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4);
-                                const float x[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+                                const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4 * ph);
+                                const float x[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                                for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(x[p], w, acc[p]);
+                                for (int p = 0; p < 4; p++) acc[p] = __fmaf_rn(x[p], w, acc[p]);
                             }
                         }
-                        float4 o0, o1;
+                        float4 o0;
                         o0.x = acc[0] > 0.0f ? acc[0] : 0.0f; o0.y = acc[1] > 0.0f ? acc[1] : 0.0f;
                         o0.z = acc[2] > 0.0f ? acc[2] : 0.0f; o0.w = acc[3] > 0.0f ? acc[3] : 0.0f;
-                        o1.x = acc[4] > 0.0f ? acc[4] : 0.0f; o1.y = acc[5] > 0.0f ? acc[5] : 0.0f;
-                        o1.z = acc[6] > 0.0f ? acc[6] : 0.0f; o1.w = acc[7] > 0.0f ? acc[7] : 0.0f;
-                        *reinterpret_cast<float4 *>(hout + u * k12DecPix) = o0;
-                        *reinterpret_cast<float4 *>(hout + u * k12DecPix + 4) = o1;
+                        *reinterpret_cast<float4 *>(hout + u * k12DecPix + 4 * ph) = o0;
                     }
                     __syncthreads();
                     hin = hout;
                     hout = hout == hA ? hB : hA;
                 }
                 // logits: thread = value, one weight load for the 8 pixels
-                for (int j = tid; j < kSymbols12; j += k12DecThreads) {
-                    float acc[k12DecPix];
-                    const float bias = __ldg(lo.a + j);
+                // logits: two value blocks of 256 at a time, their weights
+                // through the stages; thread = (block hh, value pair jp, pixel
+                // quad pq): per k row one 8-byte weight load and one 16-byte
+                // activation load feed 8 FMAs
+                {
+                    const int hh = tid >> 8, jp = tid & 127, pq = (tid >> 7) & 1;
+                    if (tid == 0 && !s_cfail)
+                        for (int q = 0; q < 2 && q < nstage; q++) issue(g0 + q);
+                    for (int qp = 0; qp < kSymbols12 / 512; qp++) {
+                        const int j0 = 256 * (2 * qp + hh) + 2 * jp;
+                        float acc[2][4];
+                        const float b0v = __ldg(lo.a + j0), b1v = __ldg(lo.a + j0 + 1);
 #pragma unroll
-                    for (int p = 0; p < k12DecPix; p++) acc[p] = bias;
-                    for (int kk = 0; kk < hl; kk++) {
-                        const float w = __ldg(wo + (size_t)kk * kSymbols12 + j);
-                        const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix);
-                        const float4 bq = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4);
-                        const float x[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+                        for (int p = 0; p < 4; p++) {
+                            acc[0][p] = b0v;
+                            acc[1][p] = b1v;
+                        }
+                        for (int kt = 0; kt < KT; kt++) {
+                            const long long g = g0 + (long long)qp * KT + kt;
+                            const int stg = (int)(g & 1);
+                            if (!*reinterpret_cast<volatile int *>(&s_cfail) &&
+                                !tc::mbar_wait(&wbar[stg], (uint32_t)((g >> 1) & 1), k12CopyWaitLimit)) {
+                                s_cfail = 1;
+                                s_err = 1;
+                            }
+                            const float *tile = wstage + stg * k12StageFloats + hh * k12TileFloats;
+                            const int rows = min(k12TileRows, hl - k12TileRows * kt);
+                            for (int rr = 0; rr < rows; rr++) {
+                                const int kk = k12TileRows * kt + rr;
+                                const float2 w = *reinterpret_cast<const float2 *>(tile + rr * 256 + 2 * jp);
+                                const float4 a = *reinterpret_cast<const float4 *>(hin + kk * k12DecPix + 4 * pq);
+                                const float x[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                        for (int p = 0; p < k12DecPix; p++) acc[p] = __fmaf_rn(x[p], w, acc[p]);
+                                for (int p = 0; p < 4; p++) {
+                                    acc[0][p] = __fmaf_rn(x[p], w.x, acc[0][p]);
+                                    acc[1][p] = __fmaf_rn(x[p], w.y, acc[1][p]);
+                                }
+                            }
+                            __syncthreads();   // every reader is done with this stage
+                            if (tid == 0 && !s_cfail && g + 2 < g0 + nstage) issue(g + 2);
+                        }
+#pragma unroll
+                        for (int p = 0; p < 4; p++) {
+                            zs[(size_t)(4 * pq + p) * kSymbols12 + j0] = acc[0][p];
+                            zs[(size_t)(4 * pq + p) * kSymbols12 + j0 + 1] = acc[1][p];
+                        }
                     }
-#pragma unroll
-                    for (int p = 0; p < k12DecPix; p++) zs[(size_t)p * kSymbols12 + j] = acc[p];
+                    g0 += nstage;
                 }
                 __syncthreads();
                 // tables, one warp per pixel: maximum, weights in place, lane sums

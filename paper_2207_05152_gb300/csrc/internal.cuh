@@ -47,7 +47,8 @@ struct DevModel {
     int vol, pu, pd, pl, pr, n2;
     float tscale;
     const uint32_t *lut;          // 64 entries
-    // FP32 network, transposed: WkT[k * out + j] = W[j][k]
+    // FP32 network, transposed: WkT[k * out + j] = W[j][k] (a 12-bit model
+    // keeps here its output layer in the decoder's 16 x 256 tiles)
     const float *w1t, *b1, *w2t, *b2, *w3t, *b3;
     // INT8 network, packed 4 inputs per u32 and transposed:
     // QkT[k4 * out + j] = bytes W[j][4*k4 .. 4*k4+3]
