@@ -4,7 +4,10 @@ The paper trains the density-estimation network with categorical
 cross-entropy reported in bits per pixel (Sec. III-A, Table I: "vloss in
 bpp").  Reading: for a batch of B (context, target) pairs the loss is
     L = (1/B) * sum_b -log2 softmax(z_b)[y_b],
-with z = W3 relu(W2 relu(W1 x + b1) + b2) + b3 and x = v/128 - 1.  The
+with z = W3 relu(W2 relu(W1 x + b1) + b2) + b3 and x = v/128 - 1 for 8-bit
+samples (256 outputs).  For 12-bit samples (Sec. IV "Higher Bit Depth": one
+12-bit channel, 4096 output neurons) the same expression runs with
+x = v/2048 - 1 and 4096 outputs; the output count is W3's row count.  The
 gradient is the textbook adjoint of that expression: dL/dz = (softmax(z) -
 onehot(y)) / (B ln 2), then the dense-layer and ReLU adjoints.  Adam (Kingma
 and Ba 2015) with bias correction is the optimiser reading.  Everything here
@@ -24,8 +27,10 @@ import numpy as np
 LN2 = np.log(2.0)
 
 
-def features(ctx_u8: np.ndarray) -> np.ndarray:
-    return ctx_u8.astype(np.float64) / 128.0 - 1.0
+def features(ctx, bits: int = 8) -> np.ndarray:
+    """Network inputs v / 2^(bits-1) - 1: v/128 - 1 for 8-bit samples,
+    v/2048 - 1 for 12-bit ones."""
+    return np.asarray(ctx).astype(np.float64) / float(1 << (bits - 1)) - 1.0
 
 
 def _row_weights(tgt, weights):
@@ -37,12 +42,13 @@ def _row_weights(tgt, weights):
     return w / w.sum()
 
 
-def forward(params, ctx_u8, tgt, weights=None):
+def forward(params, ctx_u8, tgt, weights=None, bits: int = 8):
     """params: [(W1, b1), (W2, b2), (W3, b3)] (any float dtype); weights:
-    None, or one loss weight per target value.  Returns (loss_bits, cache)."""
+    None, or one loss weight per target value; bits: the sample depth of the
+    contexts (8 or 12).  Returns (loss_bits, cache)."""
     (w1, b1), (w2, b2), (w3, b3) = [(np.asarray(w, np.float64), np.asarray(b, np.float64))
                                     for w, b in params]
-    x = features(ctx_u8)
+    x = features(ctx_u8, bits)
     a1 = x @ w1.T + b1
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ w2.T + b2
@@ -56,9 +62,9 @@ def forward(params, ctx_u8, tgt, weights=None):
     return loss, (x, a1, h1, a2, h2, z, lse)
 
 
-def gradient(params, ctx_u8, tgt, weights=None):
+def gradient(params, ctx_u8, tgt, weights=None, bits: int = 8):
     """Analytic FP64 gradient: [(dW1, db1), (dW2, db2), (dW3, db3)], loss."""
-    loss, (x, a1, h1, a2, h2, z, lse) = forward(params, ctx_u8, tgt, weights)
+    loss, (x, a1, h1, a2, h2, z, lse) = forward(params, ctx_u8, tgt, weights, bits)
     w1, w2, w3 = [np.asarray(p[0], np.float64) for p in params]
     B = z.shape[0]
     p = np.exp(z - lse[:, None])
@@ -81,14 +87,14 @@ def gradient(params, ctx_u8, tgt, weights=None):
     return [(dw1, db1), (dw2, db2), (dw3, db3)], loss
 
 
-def finite_difference(params, ctx_u8, tgt, layer: int, which: int, index, h: float, weights=None):
+def finite_difference(params, ctx_u8, tgt, layer: int, which: int, index, h: float, weights=None, bits: int = 8):
     """Central difference (L(theta + h e) - L(theta - h e)) / 2h for one
     parameter (layer 0..2, which 0 = weight / 1 = bias, flat index)."""
     def loss_with(delta):
         ps = [[np.array(w, np.float64, copy=True), np.array(b, np.float64, copy=True)]
               for w, b in params]
         ps[layer][which].reshape(-1)[index] += delta
-        return forward([tuple(q) for q in ps], ctx_u8, tgt, weights)[0]
+        return forward([tuple(q) for q in ps], ctx_u8, tgt, weights, bits)[0]
     return (loss_with(h) - loss_with(-h)) / (2.0 * h)
 
 

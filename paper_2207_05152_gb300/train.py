@@ -35,21 +35,31 @@ def unflatten(vec, h1: int, h2: int, n_in: int = 12):
     return [(out[0], out[1]), (out[2], out[3]), (out[4], out[5])]
 
 
+def _sample_dtype(images):
+    """u16 for 12-bit images (Sec. IV "Higher Bit Depth"), else u8."""
+    return np.uint16 if any(np.asarray(im).dtype == np.uint16 for im in images) else np.uint8
+
+
+def _levels(images):
+    return 4096 if _sample_dtype(images) == np.uint16 else 256
+
+
 def sample_contexts(images, count: int, seed: int):
-    """(ctx u8 [count, 12], tgt u8 [count]) at pixel positions drawn uniformly
+    """(ctx [count, 12], tgt [count]) at pixel positions drawn uniformly
     over the images; priors outside an image are 0 (the coder's window).
-    Training-data preparation on the host; the coding path gathers on the
-    device."""
+    u8 for 8-bit images, u16 for 12-bit ones.  Training-data preparation on
+    the host; the coding path gathers on the device."""
     import synth
     idx, rr, cc = synth.sample_positions(images, count, seed)
-    ctx = np.zeros((count, 12), np.uint8)
-    tgt = np.zeros(count, np.uint8)
+    dt = _sample_dtype(images)
+    ctx = np.zeros((count, 12), dt)
+    tgt = np.zeros(count, dt)
     for i, img in enumerate(images):
         sel = np.nonzero(idx == i)[0]
         if sel.size == 0:
             continue
         H, W = img.shape
-        pad = np.zeros((H + 2, W + 4), np.uint8)
+        pad = np.zeros((H + 2, W + 4), dt)
         pad[2:, 2:W + 2] = img
         r, c = rr[sel], cc[sel]
         ctx[sel] = pad[r[:, None] + 2 + _DR[None, :], c[:, None] + 2 + _DC[None, :]]
@@ -76,7 +86,7 @@ def rare_value_positions(images, count: int, seed: int, alpha: float = 1.0):
     alpha = 0 is the uniform draw over pixels."""
     import synth
     flat = np.concatenate([im.reshape(-1) for im in images])
-    hist = np.bincount(flat, minlength=256).astype(np.float64)
+    hist = np.bincount(flat, minlength=_levels(images)).astype(np.float64)
     w = hist[flat] ** -float(alpha)
     cum = np.cumsum(w)
     u = synth.Rng(seed).uniform(count) * cum[-1]
@@ -110,10 +120,12 @@ def sample_upsampled_contexts(images, count: int, seed: int, window=M.DEFAULT_WI
 def frequency_weights(images, alpha: float = 1.0):
     """Loss weights per value, hist(v)^-alpha normalised to mean 1 over the
     values present (absent values get 0): the frequency-weighted loss of
-    Sec. IV "Color Frequencies", the counterpart of rare_value_positions."""
+    Sec. IV "Color Frequencies", the counterpart of rare_value_positions.
+    256 weights for 8-bit images, 4096 for 12-bit ones."""
     flat = np.concatenate([im.reshape(-1) for im in images])
-    hist = np.bincount(flat, minlength=256).astype(np.float64)
-    w = np.zeros(256)
+    L = _levels(images)
+    hist = np.bincount(flat, minlength=L).astype(np.float64)
+    w = np.zeros(L)
     present = hist > 0
     w[present] = hist[present] ** -float(alpha)
     w[present] /= w[present].mean()
@@ -123,8 +135,9 @@ def frequency_weights(images, alpha: float = 1.0):
 def _contexts_at(images, idx, rr, cc, window):
     count = idx.size
     offs = M.window_offsets3(window)
-    ctx = np.zeros((count, len(offs)), np.uint8)
-    tgt = np.zeros(count, np.uint8)
+    dt = _sample_dtype(images)
+    ctx = np.zeros((count, len(offs)), dt)
+    tgt = np.zeros(count, dt)
     for i, img in enumerate(images):
         sel = np.nonzero(idx == i)[0]
         if sel.size == 0:

@@ -160,3 +160,81 @@ def test_weighted_loss_pins():
                 continue
             fd = train64.finite_difference(params, ctx, tgt, layer, which, i, h, w)
             assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9
+
+
+# --- 12-bit samples (Sec. IV "Higher Bit Depth": 4096 output neurons) -----
+
+def _batch12(n, seed):
+    from paper_2207_05152_gb300 import train as T
+    imgs = [synth.phantom_image12(48, 40, seed + i) for i in range(2)]
+    return T.sample_contexts(imgs, n, seed)
+
+
+def test_twelve_bit_flat_network_costs_twelve_bits():
+    ctx, tgt = _batch12(96, 51)
+    assert ctx.dtype == np.uint16 and tgt.max() > 255
+    params = _params([12, 16, 16, 4096], 52)
+    params[2] = (np.zeros((4096, 16)), np.zeros(4096))
+    loss, _ = train64.forward(params, ctx, tgt, bits=12)
+    assert abs(loss - 12.0) < 1e-12
+    grads, _ = train64.gradient(params, ctx, tgt, bits=12)
+    counts = np.bincount(tgt, minlength=4096)
+    want = (1.0 / 4096.0 - counts / len(tgt)) / np.log(2.0)
+    assert np.allclose(grads[2][1], want, atol=1e-15)
+    # a zero output layer passes no gradient to the hidden layers
+    assert not np.any(grads[0][0]) and not np.any(grads[1][0]) and np.any(grads[2][0])
+
+
+def test_twelve_bit_inputs_are_v_over_2048_minus_1():
+    # a 12-bit context of multiples of 16 (16 u) is the 8-bit context u on
+    # the input side: 16 u / 2048 - 1 = u / 128 - 1 exactly
+    rng = synth.Rng(53)
+    ctx8 = rng.integers(64 * 12, 0, 255).reshape(64, 12).astype(np.uint8)
+    tgt = rng.integers(64, 0, 4095)
+    ctx12 = ctx8.astype(np.uint16) * 16
+    params = _params([12, 16, 16, 4096], 54, gain=2.0)
+    l8, c8 = train64.forward(params, ctx8, tgt, bits=8)
+    l12, c12 = train64.forward(params, ctx12, tgt, bits=12)
+    assert l8 == l12 and np.array_equal(c8[0], c12[0])
+    g8, _ = train64.gradient(params, ctx8, tgt, bits=8)
+    g12, _ = train64.gradient(params, ctx12, tgt, bits=12)
+    for a, b in zip(g8, g12):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    # the 8-bit scale on 12-bit samples is a different network input
+    l_wrong, _ = train64.forward(params, ctx12, tgt, bits=8)
+    assert abs(l_wrong - l12) > 1e-3
+
+
+def test_twelve_bit_logits_match_the_coder():
+    # the trained network is the one the 12-bit coder evaluates: the FP64
+    # logits equal the oracle coder's FP32 logits of the same weights
+    import oracle
+    from paper_2207_05152_gb300 import model as M
+    ctx, tgt = _batch12(200, 55)
+    layers = synth.xavier_mlp([12, 32, 32, 4096], 56)
+    _, cache = train64.forward(layers, ctx, tgt, bits=12)
+    z64 = cache[5]
+    z32 = oracle.logits(M.fp32_blob12(layers), ctx).astype(np.float64)
+    assert np.max(np.abs(z64 - z32)) <= 2e-5 * max(1.0, np.max(np.abs(z64)))
+
+
+@pytest.mark.parametrize("layer,which", [(0, 0), (1, 1), (2, 0), (2, 1)])
+def test_twelve_bit_gradient_vs_central_differences(layer, which):
+    ctx, tgt = _batch12(128, 57)
+    params = _params([12, 16, 16, 4096], 58, gain=2.0)
+    grads, _ = train64.gradient(params, ctx, tgt, bits=12)
+    _, (x, a1, h1, a2, h2, z, lse) = train64.forward(params, ctx, tgt, bits=12)
+    g = grads[layer][which].reshape(-1)
+    picks = list(np.argsort(-np.abs(g))[:3]) + list(synth.Rng(60 + layer).integers(3, 0, g.size - 1))
+    checked = 0
+    for i in picks:
+        i = int(i)
+        theta = params[layer][which].reshape(-1)[i]
+        h = 1e-6 * max(1.0, abs(theta))
+        if not _kink_free(params, x, a1, h1, a2, layer, which, i, 2.0 * h):
+            continue
+        fd = train64.finite_difference(params, ctx, tgt, layer, which, i, h, bits=12)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-9, (i, fd, g[i])
+        checked += 1
+    assert checked >= 3
