@@ -379,6 +379,11 @@ enum { DLIC_TRAIN_BF16 = 0, DLIC_TRAIN_FP32 = 1, DLIC_TRAIN_BF16X3 = 2 };
  * layer order of an FP32 model blob). */
 DLIC_API size_t dlic_train_param_count(int n_in, int h1, int h2);
 
+/* The same for an n_in -> h1 -> h2 -> n_out network: n_out = 256 for 8-bit
+ * samples, 4096 for 12-bit ones (Sec. IV "Higher Bit Depth": one output
+ * neuron per value); W3 is [n_out][h2] and b3 [n_out]. */
+DLIC_API size_t dlic_train_param_count_k(int n_in, int h1, int h2, int n_out);
+
 /* Creates a trainer: FP32 master weights (copied from h_params, host),
  * Adam moments (lr 1e-3, betas 0.9 / 0.999, eps 1e-8, bias-corrected) and
  * device buffers for batches of up to max_batch contexts.  mode
@@ -396,11 +401,25 @@ DLIC_API size_t dlic_train_param_count(int n_in, int h1, int h2);
  * result equals the one-pass result up to FP32 rounding of the sums. */
 DLIC_API dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, int max_batch, const float *h_params,
                                          dlic_trainer **out);
+
+/* dlic_trainer_create for n_out outputs: 256 (the call above; batches of u8
+ * samples, inputs v/128 - 1) or 4096 (12-bit samples, Sec. IV "Higher Bit
+ * Depth": batches of u16 samples 0..4095, inputs v/2048 - 1, the 4096-way
+ * cross-entropy in bits).  With 4096 outputs the output layer's products
+ * go to an FP32 buffer of max_batch x 4096 (16 KB per context, allocated
+ * here) and a row-wise kernel takes the softmax; every mode is available.
+ * A 12-bit sample or target above 4095 sets DLIC_ERR_INVALID in the
+ * trainer's device status (dlic_trainer_status, which keeps it for the
+ * trainer's life); that call's loss and gradient are then meaningless.
+ * Any other n_out is DLIC_ERR_INVALID. */
+DLIC_API dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out, int mode, int max_batch,
+                                           const float *h_params, dlic_trainer **out);
 DLIC_API dlic_status dlic_trainer_destroy(dlic_trainer *trainer);
 
 /* The frequency-weighted loss (Sec. IV "Color Frequencies": the loss is
  * weighted by value frequency so that rare values count more): h_weights
- * (host, 256 floats, finite, >= 0, not all zero) gives each target value v a
+ * (host, n_out floats: 256, or 4096 for 12-bit samples; finite, >= 0, not
+ * all zero) gives each target value v a
  * weight w_v, and every later loss and gradient of this trainer become
  *     sum_b w_{y_b} * -log2 softmax(z_b)[y_b] / sum_b w_{y_b},
  * the plain mean when every w_v is 1; an integer weight k counts a context
@@ -408,10 +427,11 @@ DLIC_API dlic_status dlic_trainer_destroy(dlic_trainer *trainer);
  * positive weight.  h_weights NULL restores the plain loss. */
 DLIC_API dlic_status dlic_trainer_set_value_weights(dlic_trainer *trainer, const float *h_weights);
 
-/* Loss of a batch: d_ctx holds B x n_in u8 causal priors (the window's
- * order, as the coder gathers them), d_tgt B u8 target pixels; *d_loss_bits (device float)
+/* Loss of a batch: d_ctx holds B x n_in causal priors (the window's order,
+ * as the coder gathers them), d_tgt B target pixels, both u8 for a trainer
+ * of 256 outputs and u16 for one of 4096; *d_loss_bits (device float)
  * receives mean_b -log2 softmax(z_b)[y_b]. */
-DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const void *d_ctx, const void *d_tgt, int B,
                                         float *d_loss_bits, void *stream);
 
 /* Loss and its gradient with respect to every parameter (the adjoint of the
@@ -419,11 +439,11 @@ DLIC_API dlic_status dlic_train_forward(dlic_trainer *trainer, const uint8_t *d_
  * is kept from an earlier dlic_train_forward.  d_grads (device,
  * dlic_train_param_count floats, may be NULL) receives the gradient in the
  * parameter layout. */
-DLIC_API dlic_status dlic_train_backward(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+DLIC_API dlic_status dlic_train_backward(dlic_trainer *trainer, const void *d_ctx, const void *d_tgt, int B,
                                          float *d_loss_bits, float *d_grads, void *stream);
 
 /* Forward, backward and one Adam update of the master weights. */
-DLIC_API dlic_status dlic_train_step(dlic_trainer *trainer, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+DLIC_API dlic_status dlic_train_step(dlic_trainer *trainer, const void *d_ctx, const void *d_tgt, int B,
                                      float *d_loss_bits, void *stream);
 
 /* One Adam update of the master weights (and their bf16 operand copies)
@@ -442,8 +462,9 @@ DLIC_API dlic_status dlic_train_apply(dlic_trainer *trainer, const float *d_grad
  * trainer; d_params is a device buffer of dlic_train_param_count floats. */
 DLIC_API dlic_status dlic_trainer_params(dlic_trainer *trainer, float *d_params, int write, void *stream);
 
-/* Device status of the trainer's kernels (DLIC_OK or DLIC_ERR_TIMEOUT when a
- * tensor-core wait ran out); synchronises with the device. */
+/* Device status of the trainer's kernels (DLIC_OK, DLIC_ERR_TIMEOUT when a
+ * tensor-core wait ran out, DLIC_ERR_INVALID after a 12-bit sample above
+ * 4095); synchronises with the device. */
 DLIC_API dlic_status dlic_trainer_status(dlic_trainer *trainer, int32_t *h_status);
 
 #ifdef __cplusplus

@@ -66,6 +66,8 @@ SIGNATURES = {
     "dlic_decode_volume": (_I, [_VP, _VP, C.POINTER(C.c_uint64), _I, _VOLP, _VP, _VP, _SZ, _VP]),
     "dlic_train_param_count": (_SZ, [_I, _I, _I]),
     "dlic_trainer_create": (_I, [_I, _I, _I, _I, _I, _VP, C.POINTER(_VP)]),
+    "dlic_train_param_count_k": (_SZ, [_I, _I, _I, _I]),
+    "dlic_trainer_create_k": (_I, [_I, _I, _I, _I, _I, _I, _VP, C.POINTER(_VP)]),
     "dlic_trainer_destroy": (_I, [_VP]),
     "dlic_train_forward": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "dlic_train_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP]),
@@ -257,6 +259,17 @@ def dlic_trainer_create(n_in: int, h1: int, h2: int, mode: int, max_batch: int, 
     return h.value
 
 
+def dlic_train_param_count_k(n_in: int, h1: int, h2: int, n_out: int) -> int:
+    return int(lib().dlic_train_param_count_k(n_in, h1, h2, n_out))
+
+
+def dlic_trainer_create_k(n_in: int, h1: int, h2: int, n_out: int, mode: int, max_batch: int, h_params) -> int:
+    """h_params: contiguous float32 numpy array of dlic_train_param_count_k values."""
+    h = _VP()
+    check(lib().dlic_trainer_create_k(n_in, h1, h2, n_out, mode, max_batch, h_params.ctypes.data, C.byref(h)))
+    return h.value
+
+
 def dlic_trainer_destroy(trainer: int):
     check(lib().dlic_trainer_destroy(trainer))
 
@@ -274,14 +287,16 @@ def dlic_train_step(trainer: int, d_ctx: int, d_tgt: int, B: int, d_loss: int, s
     check(lib().dlic_train_step(trainer, d_ctx, d_tgt, B, d_loss, stream or None))
 
 
-def dlic_trainer_set_value_weights(trainer: int, weights=None):
+def dlic_trainer_set_value_weights(trainer: int, weights=None, n_out: int = 256):
+    """weights: one per target value, n_out of them (256, or 4096 for a
+    12-bit trainer), or None for the plain loss."""
     if weights is None:
         check(lib().dlic_trainer_set_value_weights(trainer, None))
         return
     import numpy as np
     w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
-    if w.size != 256:
-        raise ValueError("one weight per 8-bit value (256)")
+    if w.size != n_out:
+        raise ValueError(f"one weight per value ({n_out})")
     check(lib().dlic_trainer_set_value_weights(trainer, w.ctypes.data))
 
 

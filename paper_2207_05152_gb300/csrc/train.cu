@@ -698,28 +698,42 @@ __global__ void __launch_bounds__(128) k_row_epilogue(const float *C, int epi, E
 // ---------------------------------------------------------------------------
 // Small kernels: features, reductions, Adam, weight shadows.
 // ---------------------------------------------------------------------------
-// v / 128 - 1 has at most 8 significant bits: exact in bf16, low plane 0.
-// Network inputs x/128 - 1 (exact in bf16 and FP32) of n_in priors per
-// context, K padded to k1 (a multiple of 16); the transposed copy XT
-// [k1][ldT] only for the FP32 path (XT non-null).  BF16: one context per
-// thread; the 12-prior window reads three words and writes two 16-byte rows
-// (plus a zero low plane in split mode).
-__global__ void k_features(const uint8_t *ctx, int B, int n_in, int k1, int ldT, void *X, void *XT, int bf16,
-                           size_t xplane) {
+// One network input: v / 128 - 1 for an 8-bit sample (u8 contexts), v /
+// 2048 - 1 for a 12-bit one (u16 contexts, Sec. IV "Higher Bit Depth"); both
+// exact in FP32.  A 12-bit sample above 4095 sets DLIC_ERR_INVALID.
+__device__ __forceinline__ float ctx_input(const void *ctx, int wide, size_t i, int *err) {
+    if (!wide) return (float)static_cast<const uint8_t *>(ctx)[i] * 0.0078125f - 1.0f;
+    const uint32_t v = static_cast<const uint16_t *>(ctx)[i];
+    if (v > 4095u) atomicExch(err, (int)DLIC_ERR_INVALID);
+    return (float)v * 0.00048828125f - 1.0f;
+}
+
+// v / 128 - 1 has at most 8 significant bits: exact in bf16, low plane 0;
+// v / 2048 - 1 has up to 12, and its low plane carries the rest.
+// Network inputs of n_in priors per context, K padded to k1 (a multiple of
+// 16); the transposed copy XT [k1][ldT] only for the FP32 path (XT
+// non-null).  BF16: one context per thread; the 12-prior window of u8
+// contexts reads three words and writes two 16-byte rows (plus a zero low
+// plane in split mode).
+__global__ void k_features(const void *ctx, int wide, int B, int n_in, int k1, int ldT, void *X, void *XT, int bf16,
+                           size_t xplane, int *err) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    if (bf16 && n_in != kPriors) {
+    if (bf16 && (n_in != kPriors || wide)) {
         uint16_t *o = static_cast<uint16_t *>(X) + (size_t)b * k1;
         for (int k = 0; k < k1; k += 2) {
-            const float x0 = k < n_in ? (float)ctx[(size_t)b * n_in + k] * 0.0078125f - 1.0f : 0.0f;
-            const float x1 = k + 1 < n_in ? (float)ctx[(size_t)b * n_in + k + 1] * 0.0078125f - 1.0f : 0.0f;
-            reinterpret_cast<uint32_t *>(o)[k / 2] = pack_bf16x2(x0, x1);
-            if (xplane) reinterpret_cast<uint32_t *>(o + xplane)[k / 2] = 0u;
+            const float x0 = k < n_in ? ctx_input(ctx, wide, (size_t)b * n_in + k, err) : 0.0f;
+            const float x1 = k + 1 < n_in ? ctx_input(ctx, wide, (size_t)b * n_in + k + 1, err) : 0.0f;
+            const uint32_t hi = pack_bf16x2(x0, x1);
+            reinterpret_cast<uint32_t *>(o)[k / 2] = hi;
+            if (xplane)
+                reinterpret_cast<uint32_t *>(o + xplane)[k / 2] =
+                    pack_bf16x2(x0 - bf2f((uint16_t)(hi & 0xFFFFu)), x1 - bf2f((uint16_t)(hi >> 16)));
         }
         return;
     }
     if (bf16) {
-        const uint8_t *c = ctx + (size_t)b * kPriors;
+        const uint8_t *c = static_cast<const uint8_t *>(ctx) + (size_t)b * kPriors;
         const bool al4 = (reinterpret_cast<uintptr_t>(c) & 3u) == 0;
         uint32_t w[8];
 #pragma unroll
@@ -744,7 +758,7 @@ __global__ void k_features(const uint8_t *ctx, int B, int n_in, int k1, int ldT,
         return;
     }
     for (int k = 0; k < k1; k++) {
-        const float x = k < n_in ? (float)ctx[(size_t)b * n_in + k] * 0.0078125f - 1.0f : 0.0f;
+        const float x = k < n_in ? ctx_input(ctx, wide, (size_t)b * n_in + k, err) : 0.0f;
         reinterpret_cast<float *>(X)[(size_t)b * k1 + k] = x;
         reinterpret_cast<float *>(XT)[(size_t)k * ldT + b] = x;
     }
@@ -758,8 +772,8 @@ __global__ void k_features(const uint8_t *ctx, int B, int n_in, int k1, int ldT,
 // leaves as 16-byte rows.
 constexpr int kL1Ctx = 32;
 template <int NMAX>
-__global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n_in, const float *W1, const float *b1,
-                                                int h1, uint16_t *H1, size_t p1, uint16_t *M1) {
+__global__ void __launch_bounds__(256) k_layer1(const void *ctx, int wide, int B, int n_in, const float *W1,
+                                                const float *b1, int h1, uint16_t *H1, size_t p1, uint16_t *M1, int *err) {
     __shared__ __align__(16) uint16_t thi[kL1Ctx * kMaxHidden];
     __shared__ __align__(16) uint16_t tlo[kL1Ctx * kMaxHidden];
     __shared__ float xs[kL1Ctx][NMAX];
@@ -767,7 +781,7 @@ __global__ void __launch_bounds__(256) k_layer1(const uint8_t *ctx, int B, int n
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, b0 = blockIdx.x * kL1Ctx;
     for (int i = tid; i < kL1Ctx * NMAX; i += 256) {
         const int r = i / NMAX, k = i % NMAX;
-        xs[r][k] = b0 + r < B && k < n_in ? (float)ctx[(size_t)(b0 + r) * n_in + k] * 0.0078125f - 1.0f : 0.0f;
+        xs[r][k] = b0 + r < B && k < n_in ? ctx_input(ctx, wide, (size_t)(b0 + r) * n_in + k, err) : 0.0f;
     }
     __syncthreads();
     // every thread runs the loop (the sign ballots need whole warps); units
@@ -885,7 +899,7 @@ __device__ __forceinline__ void shadow_put(void *Wd, size_t idx, size_t plane, f
 // updated weights written straight into the GEMM operand copies (row-major
 // and transposed).  The zero padding of the W1 copy is never touched.
 struct ShadowArgs {
-    int n_in, k1, h1, h2, bf16, split;
+    int n_in, k1, h1, h2, n_out, bf16, split;
     void *w1, *w2, *w3, *w2t, *w3t;
 };
 __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, float lr, float b1, float b2, float eps,
@@ -907,10 +921,10 @@ __global__ void k_adam(float *p, const float *g, float *mo, float *ve, int n, fl
         const int j = i - oW2, o = j / h1, k = j % h1;
         shadow_put(sa.w2, j, (size_t)h2 * h1, w, sa.bf16, sa.split);
         shadow_put(sa.w2t, (size_t)k * h2 + o, (size_t)h1 * h2, w, sa.bf16, sa.split);
-    } else if (i >= oW3 && i < oW3 + kSymbols * h2) {
+    } else if (i >= oW3 && i < oW3 + sa.n_out * h2) {
         const int j = i - oW3, o = j / h2, k = j % h2;
-        shadow_put(sa.w3, j, (size_t)kSymbols * h2, w, sa.bf16, sa.split);
-        shadow_put(sa.w3t, (size_t)k * kSymbols + o, (size_t)h2 * kSymbols, w, sa.bf16, sa.split);
+        shadow_put(sa.w3, j, (size_t)sa.n_out * h2, w, sa.bf16, sa.split);
+        shadow_put(sa.w3t, (size_t)k * sa.n_out + o, (size_t)h2 * sa.n_out, w, sa.bf16, sa.split);
     }
 }
 __global__ void k_shadow(const float *W, int out, int in, int in_pad, void *Wd, void *WTd, int bf16, int split) {
@@ -942,6 +956,8 @@ using namespace dlic;
 struct dlic_trainer {
     int n_in, k1;                                // network inputs (the window's priors), padded to 16
     int h1, h2, mode, max_batch, num_sms;
+    int n_out;                                   // 256 (8-bit samples, u8 batches) or 4096 (12-bit, u16)
+    int wide;                                    // n_out = 4096
     int bf, split;                               // bf16 operands; hi + lo planes
     size_t nparams;
     int step;
@@ -952,30 +968,32 @@ struct dlic_trainer {
     uint16_t *M1, *M2;                           // BF16 modes: sign bits of H1, H2 [batch][h / 16]
     void *XT, *H1T, *H2T, *DZT, *DA2T, *DA1T;    // FP32 path: transposed [features][batch]
     float *C, *part, *colsum, *losspart;
+    float *Z;                     // 4096 outputs: the output layer's products [batch][n_out] (FP32)
+    size_t part_floats;           // capacity of the split-K partials
     float *gacc, *closs, *lacc;   // batches above max_batch: gradient and loss sums over chunks
     int weighted;                 // the frequency-weighted loss is on
-    float *vw, *wnorm;            // its weights per target value (256) and {1 / (W ln 2), 1 / W}
+    float *vw, *wnorm;            // its weights per target value (n_out) and {1 / (W ln 2), 1 / W}
     int *err;
     std::vector<void *> allocs;
 };
 
 namespace {
 
-size_t param_count(int n_in, int h1, int h2) {
-    return (size_t)h1 * n_in + h1 + (size_t)h2 * h1 + h2 + (size_t)kSymbols * h2 + kSymbols;
+size_t param_count(int n_in, int h1, int h2, int n_out) {
+    return (size_t)h1 * n_in + h1 + (size_t)h2 * h1 + h2 + (size_t)n_out * h2 + n_out;
 }
 
 struct ParamView {
     float *W1, *b1, *W2, *b2, *W3, *b3;
 };
-ParamView view(float *p, int n_in, int h1, int h2) {
+ParamView view(float *p, int n_in, int h1, int h2, int n_out) {
     ParamView v;
     v.W1 = p;
     v.b1 = v.W1 + (size_t)h1 * n_in;
     v.W2 = v.b1 + h1;
     v.b2 = v.W2 + (size_t)h2 * h1;
     v.W3 = v.b2 + h2;
-    v.b3 = v.W3 + (size_t)kSymbols * h2;
+    v.b3 = v.W3 + (size_t)n_out * h2;
     return v;
 }
 
@@ -1096,11 +1114,11 @@ void reduce_parts(const float *part, int nparts, size_t stride, int n, float *ou
 }
 
 dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
-    ParamView p = view(t->params, t->n_in, t->h1, t->h2);
+    ParamView p = view(t->params, t->n_in, t->h1, t->h2, t->n_out);
     const int bf = t->bf, sp = t->split;
     k_shadow<<<(t->h1 * t->k1 + 255) / 256, 256, 0, st>>>(p.W1, t->h1, t->n_in, t->k1, t->w1, nullptr, bf, sp);
     k_shadow<<<(t->h2 * t->h1 + 255) / 256, 256, 0, st>>>(p.W2, t->h2, t->h1, t->h1, t->w2, t->w2t, bf, sp);
-    k_shadow<<<(kSymbols * t->h2 + 255) / 256, 256, 0, st>>>(p.W3, kSymbols, t->h2, t->h2, t->w3, t->w3t, bf, sp);
+    k_shadow<<<(t->n_out * t->h2 + 255) / 256, 256, 0, st>>>(p.W3, t->n_out, t->h2, t->h2, t->w3, t->w3t, bf, sp);
     cudaError_t ce = cudaGetLastError();
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "shadow launch");
 }
@@ -1109,12 +1127,22 @@ dlic_status refresh_shadows(dlic_trainer *t, cudaStream_t st) {
 // every activation row-major [batch][features] and read the weight-gradient
 // factors MN-major; the FP32 path also keeps transposed copies [features]
 // [batch] for its K-major CUDA-core GEMM.
+// Target value b of a batch: u8, or u16 for 12-bit samples; a value past
+// the n_out outputs sets DLIC_ERR_INVALID and reads as 0.
+__device__ __forceinline__ int batch_target(const void *tgt, int wide, int b, int n_out, int *err) {
+    const int y = wide ? (int)static_cast<const uint16_t *>(tgt)[b] : (int)static_cast<const uint8_t *>(tgt)[b];
+    if (y < n_out) return y;
+    atomicExch(err, (int)DLIC_ERR_INVALID);
+    return 0;
+}
+
 // W = sum_b vw[tgt[b]] in a fixed order (one CTA), and {1 / (W ln 2), 1 / W}.
-__global__ void __launch_bounds__(1024) k_wsum(const uint8_t *tgt, int B, const float *vw, float *wnorm) {
+__global__ void __launch_bounds__(1024) k_wsum(const void *tgt, int wide, int B, int n_out, const float *vw,
+                                               float *wnorm, int *err) {
     __shared__ float red[1024];
     const int tid = threadIdx.x;
     float s = 0.0f;
-    for (int b = tid; b < B; b += 1024) s += vw[tgt[b]];
+    for (int b = tid; b < B; b += 1024) s += vw[batch_target(tgt, wide, b, n_out, err)];
     red[tid] = s;
     __syncthreads();
     for (int off = 512; off > 0; off >>= 1) {
@@ -1127,12 +1155,159 @@ __global__ void __launch_bounds__(1024) k_wsum(const uint8_t *tgt, int B, const 
     }
 }
 
-dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss, bool backward,
+// Softmax cross-entropy over the 4096 outputs of a 12-bit network (Sec. IV
+// "Higher Bit Depth"), a row too long for one tensor-memory tile: the output
+// layer's GEMMs first write z - b3 to Z [B][4096] (FP32), then this kernel
+// does what the fused epilogue of the 256-output layer does (maximum, sum
+// of expf, lse = m + logf(sum), loss (lse - z_y) / ln 2 weighted as there,
+// dz = (softmax - onehot) * scale) with every logit read from HBM once.
+// One CTA of 512 threads per 128-row tile; thread t owns the columns 4t ..
+// 4t + 3 and 2048 + 4t .. 2048 + 4t + 3 of every row, so that a row's loads
+// are two fully coalesced 8 KB sweeps; rows go four at a time through two
+// block reductions (warp trees, then the 16 warp values in a fixed order),
+// so every sum has the same order on every run.  The thread keeps its
+// columns' dz sums over the tile (the db3 partials) in registers; the
+// tile's loss and column partials are added in a fixed order afterwards.
+constexpr int kWideOut = 4096, kWideRows = 128, kWideThreads = 512, kWideGroup = 4;
+__global__ void __launch_bounds__(kWideThreads) k_softmax_wide(const float *Z, const float *b3, const uint16_t *tgt,
+                                                               int B, float inv_batch_ln2, const float *vw,
+                                                               const float *wnorm, void *DZ, size_t dz_plane, int bf16,
+                                                               int split, float *colsum, float *losspart, int *err) {
+    __shared__ float s_max[kWideGroup][kWideThreads / 32], s_sum[kWideGroup][kWideThreads / 32];
+    __shared__ float s_loss[kWideThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = blockIdx.x * kWideRows;
+    const int cA = 4 * tid, cB = kWideOut / 2 + 4 * tid;
+    const float4 bA = *reinterpret_cast<const float4 *>(b3 + cA), bB = *reinterpret_cast<const float4 *>(b3 + cB);
+    const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
+    float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float loss_acc = 0.0f;
+    for (int g0 = 0; g0 < kWideRows; g0 += kWideGroup) {
+        float zb[kWideGroup][8], mx[kWideGroup];
+#pragma unroll
+        for (int i = 0; i < kWideGroup; i++) {
+            const int row = r0 + g0 + i;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+            if (row < B) {
+                const float *z = Z + (size_t)row * kWideOut;
+                a = *reinterpret_cast<const float4 *>(z + cA);
+                c = *reinterpret_cast<const float4 *>(z + cB);
+            }
+            const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+            mx[i] = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                zb[i][q] = v[q] + bias[q];
+                mx[i] = fmaxf(mx[i], zb[i][q]);
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], off));
+            if (lane == 0) s_max[i][warp] = mx[i];
+        }
+        __syncthreads();
+        float ex[kWideGroup][8], se[kWideGroup];
+#pragma unroll
+        for (int i = 0; i < kWideGroup; i++) {
+            float m = s_max[i][0];
+#pragma unroll
+            for (int w = 1; w < kWideThreads / 32; w++) m = fmaxf(m, s_max[i][w]);
+            mx[i] = m;
+            float l = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                ex[i][q] = expf(zb[i][q] - m);
+                l += ex[i][q];
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
+            if (lane == 0) s_sum[i][warp] = l;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kWideGroup; i++) {
+            const int row = r0 + g0 + i;
+            float sum = s_sum[i][0];
+#pragma unroll
+            for (int w = 1; w < kWideThreads / 32; w++) sum += s_sum[i][w];
+            se[i] = sum;
+            if (row >= B) continue;
+            int y = tgt[row];
+            if (y >= kWideOut) {
+                atomicExch(err, (int)DLIC_ERR_INVALID);
+                y = 0;
+            }
+            const float lse = mx[i] + logf(se[i]), inv = 1.0f / se[i];
+            const float rw = vw ? vw[y] : 1.0f;
+            const float gscale = vw ? rw * wnorm[0] : inv_batch_ln2, lw = vw ? rw * wnorm[1] : 1.0f;
+            float g[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int col = (q < 4 ? cA : cB - 4) + q;
+                g[q] = ex[i][q] * inv;
+                if (col == y) {
+                    g[q] -= 1.0f;
+                    loss_acc += lw * ((lse - zb[i][q]) / kLn2);
+                }
+                g[q] *= gscale;
+                cs[q] += g[q];
+            }
+            const size_t o = (size_t)row * kWideOut;
+            if (bf16) {
+                uint16_t *d = static_cast<uint16_t *>(DZ);
+                const uint2 hA = make_uint2(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]));
+                const uint2 hB = make_uint2(pack_bf16x2(g[4], g[5]), pack_bf16x2(g[6], g[7]));
+                *reinterpret_cast<uint2 *>(d + o + cA) = hA;
+                *reinterpret_cast<uint2 *>(d + o + cB) = hB;
+                if (split) {
+                    const uint32_t h[4] = {hA.x, hA.y, hB.x, hB.y};
+                    uint32_t lo[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        lo[k] = pack_bf16x2(g[2 * k] - __uint_as_float(h[k] << 16),
+                                            g[2 * k + 1] - __uint_as_float(h[k] & 0xFFFF0000u));
+                    *reinterpret_cast<uint2 *>(d + dz_plane + o + cA) = make_uint2(lo[0], lo[1]);
+                    *reinterpret_cast<uint2 *>(d + dz_plane + o + cB) = make_uint2(lo[2], lo[3]);
+                }
+            } else {
+                float *d = static_cast<float *>(DZ);
+                *reinterpret_cast<float4 *>(d + o + cA) = make_float4(g[0], g[1], g[2], g[3]);
+                *reinterpret_cast<float4 *>(d + o + cB) = make_float4(g[4], g[5], g[6], g[7]);
+            }
+        }
+    }
+    float *cp = colsum + (size_t)blockIdx.x * kWideOut;
+    *reinterpret_cast<float4 *>(cp + cA) = make_float4(cs[0], cs[1], cs[2], cs[3]);
+    *reinterpret_cast<float4 *>(cp + cB) = make_float4(cs[4], cs[5], cs[6], cs[7]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) loss_acc += __shfl_down_sync(0xffffffffu, loss_acc, off);
+    if (lane == 0) s_loss[warp] = loss_acc;
+    __syncthreads();
+    if (tid == 0) {
+        float l = 0.0f;
+        for (int w = 0; w < kWideThreads / 32; w++) l += s_loss[w];
+        losspart[blockIdx.x] = l;
+    }
+}
+
+// out[c][r] = in[r][c] for an R x Cn FP32 array (row pitch Cn; out pitch
+// ldo): 32 x 32 tiles through shared memory, both sides coalesced.
+__global__ void k_transpose_f32(const float *in, int R, int Cn, float *out, int ldo) {
+    __shared__ float tile[32][33];
+    const int x = threadIdx.x, y = threadIdx.y;   // 32 x 8
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = y; k < 32; k += 8)
+        if (r0 + k < R && c0 + x < Cn) tile[k][x] = in[(size_t)(r0 + k) * Cn + c0 + x];
+    __syncthreads();
+    for (int k = y; k < 32; k += 8)
+        if (c0 + k < Cn && r0 + x < R) out[(size_t)(c0 + k) * ldo + r0 + x] = tile[x][k];
+}
+
+dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float *d_loss, bool backward,
                 cudaStream_t st, bool wnorm_ready = false) {
-    const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128, n_in = t->n_in, k1 = t->k1;
+    const int h1 = t->h1, h2 = t->h2, mt = (B + 127) / 128, n_in = t->n_in, k1 = t->k1, n_out = t->n_out;
     const int bf = t->bf;
-    ParamView p = view(t->params, n_in, h1, h2);
-    ParamView g = view(t->grads, n_in, h1, h2);
+    ParamView p = view(t->params, n_in, h1, h2, n_out);
+    ParamView g = view(t->grads, n_in, h1, h2, n_out);
     const int P = t->max_batch;   // capacity: pitch of the transposed arrays, offset of the low planes
     const size_t Bm = (size_t)P;
     const size_t sp = t->split ? 1 : 0;
@@ -1145,7 +1320,8 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     auto wgrad = [&](const void *rm, const void *tr, int n) {
         return bf ? Operand{rm, B, n, n, Bm * n, 1} : Operand{tr, n, B, P, (size_t)n * Bm, 0};
     };
-    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, B, n_in, k1, P, t->X, bf ? nullptr : t->XT, bf, sp * Bm * k1);
+    k_features<<<(B + 255) / 256, 256, 0, st>>>(ctx, t->wide, B, n_in, k1, P, t->X, bf ? nullptr : t->XT, bf,
+                                                sp * Bm * k1, t->err);
     EpiArgs e{};
     // layer 1, 2: bias + ReLU
     e.bias = p.b1; e.out = t->H1; e.outT = t->H1T; e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
@@ -1154,15 +1330,15 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
         const int nb = (B + kL1Ctx - 1) / kL1Ctx;
         uint16_t *H1 = static_cast<uint16_t *>(t->H1);
         if (n_in <= 12)
-            k_layer1<12><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+            k_layer1<12><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
         else if (n_in <= 16)
-            k_layer1<16><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+            k_layer1<16><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
         else if (n_in <= 32)
-            k_layer1<32><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+            k_layer1<32><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
         else if (n_in <= 64)
-            k_layer1<64><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+            k_layer1<64><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
         else
-            k_layer1<96><<<nb, 256, 0, st>>>(ctx, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1);
+            k_layer1<96><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
     } else if ((s = gemm(t, rowmaj(t->X, k1), wmat(t->w1, h1, k1), B, h1, k1, EPI_BIAS_RELU, e, 1, st))) {
         return s;
     }
@@ -1170,28 +1346,55 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     e.mask_out = bf ? t->M2 : nullptr;
     if ((s = gemm(t, rowmaj(t->H1, h1), wmat(t->w2, h2, h1), B, h2, h1, EPI_BIAS_RELU, e, 1, st))) return s;
     // layer 3 + softmax cross-entropy: loss partials, dz, db3 partials
-    e = EpiArgs{}; e.bias = p.b3; e.out = t->DZ; e.outT = t->DZT; e.tgt = tgt;
-    e.out_plane = Bm * kSymbols; e.outT_plane = (size_t)kSymbols * Bm;
-    e.inv_batch_ln2 = 1.0f / ((float)B * kLn2);
-    if (t->weighted) {
-        // the frequency-weighted loss: the batch's weight total first
-        if (!wnorm_ready) k_wsum<<<1, 1024, 0, st>>>(tgt, B, t->vw, t->wnorm);
-        e.vw = t->vw;
-        e.wnorm = t->wnorm;
+    // the frequency-weighted loss: the batch's weight total first
+    if (t->weighted && !wnorm_ready) k_wsum<<<1, 1024, 0, st>>>(tgt, t->wide, B, n_out, t->vw, t->wnorm, t->err);
+    if (!t->wide) {
+        // 256 outputs: one tensor-memory tile per row, softmax fused into the
+        // GEMM's epilogue
+        e = EpiArgs{}; e.bias = p.b3; e.out = t->DZ; e.outT = t->DZT; e.tgt = static_cast<const uint8_t *>(tgt);
+        e.out_plane = Bm * n_out; e.outT_plane = (size_t)n_out * Bm;
+        e.inv_batch_ln2 = 1.0f / ((float)B * kLn2);
+        if (t->weighted) {
+            e.vw = t->vw;
+            e.wnorm = t->wnorm;
+        }
+        e.colsum = t->colsum; e.loss = t->losspart;
+        if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, n_out, h2), B, n_out, h2, EPI_SOFTMAX, e, 1, st)))
+            return s;
+    } else {
+        // 4096 outputs: the products z - b3 to Z (the tensor-core GEMM takes
+        // 256 columns, one accumulator tile, per launch), then the row-wise
+        // softmax kernel
+        e = EpiArgs{}; e.c = t->Z; e.ldc = n_out;
+        if (bf) {
+            for (int j = 0; j < n_out / 256; j++) {
+                EpiArgs ej = e;
+                ej.c = t->Z + 256 * j;
+                const Operand w3j{static_cast<const uint16_t *>(t->w3) + (size_t)256 * j * h2, 256, h2, h2,
+                                  (size_t)n_out * h2, 0};
+                if ((s = gemm(t, rowmaj(t->H2, h2), w3j, B, 256, h2, EPI_F32, ej, 1, st))) return s;
+            }
+        } else if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, n_out, h2), B, n_out, h2, EPI_F32, e, 1, st))) {
+            return s;
+        }
+        k_softmax_wide<<<mt, kWideThreads, 0, st>>>(t->Z, p.b3, static_cast<const uint16_t *>(tgt), B,
+                                                    1.0f / ((float)B * kLn2), t->weighted ? t->vw : nullptr,
+                                                    t->wnorm, t->DZ, Bm * n_out, bf, t->split, t->colsum,
+                                                    t->losspart, t->err);
+        if (!bf && backward)
+            k_transpose_f32<<<dim3(n_out / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
+                static_cast<const float *>(t->DZ), B, n_out, static_cast<float *>(t->DZT), P);
     }
-    e.colsum = t->colsum; e.loss = t->losspart;
-    if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, kSymbols, h2), B, kSymbols, h2, EPI_SOFTMAX, e, 1, st)))
-        return s;
     reduce_parts(t->losspart, mt, 1, 1, d_loss, t->weighted ? 1.0f : 1.0f / (float)B, 0, 0, st);
     if (!backward) {
         cudaError_t ce = cudaGetLastError();
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
     }
-    reduce_parts(t->colsum, mt, kSymbols, kSymbols, g.b3, 1.0f, 0, 0, st);
+    reduce_parts(t->colsum, mt, n_out, n_out, g.b3, 1.0f, 0, 0, st);
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.mask = t->M2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
-    if ((s = gemm(t, rowmaj(t->DZ, kSymbols), wmat(t->w3t, h2, kSymbols), B, h2, kSymbols, EPI_RELU_GRAD, e, 1, st)))
+    if ((s = gemm(t, rowmaj(t->DZ, n_out), wmat(t->w3t, h2, n_out), B, h2, n_out, EPI_RELU_GRAD, e, 1, st)))
         return s;
     reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, 0, st);
     // dh1 = da2 W2, da1 = dh1 * [h1 > 0]; db1
@@ -1200,23 +1403,25 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
     if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
     reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, 0, st);
     // weight gradients dW = dY^T X: K = batch, split-K partials summed in a
-    // fixed order; enough splits to cover every SM
-    auto splits_for = [&](int M) {
+    // fixed order; enough splits to cover every SM, as many as the partial
+    // buffer holds
+    auto splits_for = [&](int M, int N) {
         const int nkb = (B + 63) / 64;
-        const int want = bf ? max(1, t->num_sms / ((M + 127) / 128)) : max(1, min(64, (B + 1023) / 1024));
+        int want = bf ? max(1, t->num_sms / ((M + 127) / 128)) : max(1, min(64, (B + 1023) / 1024));
+        want = max(1, min(want, (int)(t->part_floats / ((size_t)M * N))));
         const int per = (nkb + min(want, nkb) - 1) / min(want, nkb);
         return (nkb + per - 1) / per;
     };
-    int sk = splits_for(kSymbols);
+    int sk = splits_for(n_out, h2);
     e = EpiArgs{}; e.c = t->part; e.ldc = h2;
-    if ((s = gemm(t, wgrad(t->DZ, t->DZT, kSymbols), wgrad(t->H2, t->H2T, h2), kSymbols, h2, B, EPI_F32, e, sk, st)))
+    if ((s = gemm(t, wgrad(t->DZ, t->DZT, n_out), wgrad(t->H2, t->H2T, h2), n_out, h2, B, EPI_F32, e, sk, st)))
         return s;
-    reduce_parts(t->part, sk, (size_t)kSymbols * h2, kSymbols * h2, g.W3, 1.0f, 0, 0, st);
-    sk = splits_for(h2);
+    reduce_parts(t->part, sk, (size_t)n_out * h2, n_out * h2, g.W3, 1.0f, 0, 0, st);
+    sk = splits_for(h2, h1);
     e = EpiArgs{}; e.c = t->part; e.ldc = h1;
     if ((s = gemm(t, wgrad(t->DA2, t->DA2T, h2), wgrad(t->H1, t->H1T, h1), h2, h1, B, EPI_F32, e, sk, st))) return s;
     reduce_parts(t->part, sk, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, 0, st);
-    sk = splits_for(h1);
+    sk = splits_for(h1, k1);
     e = EpiArgs{}; e.c = t->part; e.ldc = k1;
     if ((s = gemm(t, wgrad(t->DA1, t->DA1T, h1), wgrad(t->X, t->XT, k1), h1, k1, B, EPI_F32, e, sk, st))) return s;
     reduce_parts(t->part, sk, (size_t)h1 * k1, h1 * k1, g.W1, 1.0f, k1, n_in, st);
@@ -1226,12 +1431,23 @@ dlic_status run(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, 
 
 }  // namespace
 
-extern "C" size_t dlic_train_param_count(int n_in, int h1, int h2) { return param_count(n_in, h1, h2); }
+extern "C" size_t dlic_train_param_count(int n_in, int h1, int h2) { return param_count(n_in, h1, h2, kSymbols); }
+
+extern "C" size_t dlic_train_param_count_k(int n_in, int h1, int h2, int n_out) {
+    return param_count(n_in, h1, h2, n_out);
+}
 
 extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, int max_batch, const float *h_params,
                                            dlic_trainer **out) {
+    return dlic_trainer_create_k(n_in, h1, h2, kSymbols, mode, max_batch, h_params, out);
+}
+
+extern "C" dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out, int mode, int max_batch,
+                                             const float *h_params, dlic_trainer **out) {
     if (!out) return fail(DLIC_ERR_INVALID, "null output");
     *out = nullptr;
+    if (n_out != kSymbols && n_out != kWideOut)
+        return fail(DLIC_ERR_INVALID, "n_out must be 256 (8-bit samples) or 4096 (12-bit samples)");
     if (n_in < 1 || n_in > kMaxPriors) return fail(DLIC_ERR_INVALID, "network inputs must be in [1, %d]", kMaxPriors);
     if (h1 < 16 || h1 > 256 || h1 % 16 || h2 < 16 || h2 > 256 || h2 % 16)
         return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
@@ -1243,10 +1459,12 @@ extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, i
     t->n_in = n_in;
     t->k1 = (n_in + 15) / 16 * 16;
     t->h1 = h1; t->h2 = h2; t->mode = mode;
+    t->n_out = n_out;
+    t->wide = n_out == kWideOut;
     t->bf = mode != DLIC_TRAIN_FP32;
     t->split = mode == DLIC_TRAIN_BF16X3;
     t->max_batch = (max_batch + 127) / 128 * 128;
-    t->nparams = param_count(n_in, h1, h2);
+    t->nparams = param_count(n_in, h1, h2, n_out);
     t->step = 0;
     t->lr = 1e-3f; t->beta1 = 0.9f; t->beta2 = 0.999f; t->eps = 1e-8f;
     int dev = 0;
@@ -1269,13 +1487,14 @@ extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, i
     t->vel = (float *)A(4 * t->nparams);
     t->w1 = A(es * h1 * t->k1);
     t->w2 = A(es * h2 * h1);
-    t->w3 = A(es * kSymbols * h2);
+    t->w3 = A(es * n_out * h2);
     t->w2t = A(es * h1 * h2);
-    t->w3t = A(es * h2 * kSymbols);
+    t->w3t = A(es * h2 * n_out);
     t->X = A(es * Bm * t->k1);
     t->H1 = A(es * Bm * h1);
     t->H2 = A(es * Bm * h2);
-    t->DZ = A(es * Bm * kSymbols);
+    t->DZ = A(es * Bm * n_out);
+    if (t->wide) t->Z = (float *)A(4 * Bm * n_out);
     t->DA2 = A(es * Bm * h2);
     if (t->bf) {
         t->DA1 = A(es * Bm * h1);
@@ -1285,17 +1504,18 @@ extern "C" dlic_status dlic_trainer_create(int n_in, int h1, int h2, int mode, i
         t->XT = A(es * t->k1 * Bm);
         t->H1T = A(es * h1 * Bm);
         t->H2T = A(es * h2 * Bm);
-        t->DZT = A(es * kSymbols * Bm);
+        t->DZT = A(es * n_out * Bm);
         t->DA2T = A(es * h2 * Bm);
         t->DA1T = A(es * h1 * Bm);
         t->C = (float *)A(4 * Bm * kSymbols);
     }
     // split-K partials: up to one split per SM (BF16) or 64 (FP32)
-    t->part = (float *)A(4 * (size_t)(t->num_sms > 64 ? t->num_sms : 64) * kSymbols * hmax);
-    t->colsum = (float *)A(4 * ((Bm + 127) / 128) * kSymbols);   // one row per m-tile, the last one ragged
+    t->part_floats = (size_t)(t->num_sms > 64 ? t->num_sms : 64) * kSymbols * hmax;
+    t->part = (float *)A(4 * t->part_floats);
+    t->colsum = (float *)A(4 * ((Bm + 127) / 128) * n_out);   // one row per m-tile, the last one ragged
     t->losspart = (float *)A(4 * ((Bm + 127) / 128));
     t->gacc = (float *)A(4 * t->nparams);
-    t->vw = (float *)A(4 * kSymbols);
+    t->vw = (float *)A(4 * (size_t)n_out);
     t->wnorm = (float *)A(8);
     t->closs = (float *)A(8);
     t->lacc = (float *)A(8);
@@ -1325,7 +1545,7 @@ extern "C" dlic_status dlic_trainer_destroy(dlic_trainer *t) {
     return DLIC_OK;
 }
 
-static dlic_status check_batch(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B) {
+static dlic_status check_batch(dlic_trainer *t, const void *ctx, const void *tgt, int B) {
     if (!t) return fail(DLIC_ERR_INVALID, "null trainer");
     if (!ctx || !tgt) return fail(DLIC_ERR_INVALID, "null batch");
     if (B < 1) return fail(DLIC_ERR_CAPACITY, "batch %d < 1", B);
@@ -1343,15 +1563,17 @@ __global__ void k_accum(float *acc, const float *g, int n, float w, int first) {
 // mean loss (and gradient) is added with weight B_c / B, so that the
 // activations held at any time are one chunk's, whatever the batch.  The
 // result lands where the one-pass run puts it (d_loss, t->grads).
-static dlic_status run_chunked(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss,
+static dlic_status run_chunked(dlic_trainer *t, const void *ctx, const void *tgt, int B, float *d_loss,
                                bool backward, cudaStream_t st) {
     const int n = (int)t->nparams, nb = (n + 255) / 256;
+    const size_t es = t->wide ? 2 : 1;   // bytes per sample
     // with value weights every chunk's terms are normalised by the whole
     // batch's weight total, and the chunks simply add up
-    if (t->weighted) k_wsum<<<1, 1024, 0, st>>>(tgt, B, t->vw, t->wnorm);
+    if (t->weighted) k_wsum<<<1, 1024, 0, st>>>(tgt, t->wide, B, t->n_out, t->vw, t->wnorm, t->err);
     for (int c0 = 0; c0 < B; c0 += t->max_batch) {
         const int bc = min(t->max_batch, B - c0);
-        dlic_status s = run(t, ctx + (size_t)c0 * t->n_in, tgt + c0, bc, t->closs, backward, st, t->weighted);
+        dlic_status s = run(t, static_cast<const char *>(ctx) + (size_t)c0 * t->n_in * es,
+                            static_cast<const char *>(tgt) + (size_t)c0 * es, bc, t->closs, backward, st, t->weighted);
         if (s) return s;
         const float w = t->weighted ? 1.0f : (float)bc / (float)B;
         k_accum<<<1, 32, 0, st>>>(t->lacc, t->closs, 1, w, c0 == 0);
@@ -1363,13 +1585,13 @@ static dlic_status run_chunked(dlic_trainer *t, const uint8_t *ctx, const uint8_
     return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "chunk sums");
 }
 
-static dlic_status run_any(dlic_trainer *t, const uint8_t *ctx, const uint8_t *tgt, int B, float *d_loss,
+static dlic_status run_any(dlic_trainer *t, const void *ctx, const void *tgt, int B, float *d_loss,
                            bool backward, cudaStream_t st) {
     return B <= t->max_batch ? run(t, ctx, tgt, B, d_loss, backward, st)
                              : run_chunked(t, ctx, tgt, B, d_loss, backward, st);
 }
 
-extern "C" dlic_status dlic_train_forward(dlic_trainer *t, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+extern "C" dlic_status dlic_train_forward(dlic_trainer *t, const void *d_ctx, const void *d_tgt, int B,
                                           float *d_loss_bits, void *stream) {
     dlic_status s = check_batch(t, d_ctx, d_tgt, B);
     if (s) return s;
@@ -1377,7 +1599,7 @@ extern "C" dlic_status dlic_train_forward(dlic_trainer *t, const uint8_t *d_ctx,
     return run_any(t, d_ctx, d_tgt, B, d_loss_bits, false, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" dlic_status dlic_train_backward(dlic_trainer *t, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+extern "C" dlic_status dlic_train_backward(dlic_trainer *t, const void *d_ctx, const void *d_tgt, int B,
                                            float *d_loss_bits, float *d_grads, void *stream) {
     dlic_status s = check_batch(t, d_ctx, d_tgt, B);
     if (s) return s;
@@ -1392,7 +1614,7 @@ extern "C" dlic_status dlic_train_backward(dlic_trainer *t, const uint8_t *d_ctx
     return DLIC_OK;
 }
 
-extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, const uint8_t *d_tgt, int B,
+extern "C" dlic_status dlic_train_step(dlic_trainer *t, const void *d_ctx, const void *d_tgt, int B,
                                        float *d_loss_bits, void *stream) {
     dlic_status s = check_batch(t, d_ctx, d_tgt, B);
     if (s) return s;
@@ -1402,7 +1624,7 @@ extern "C" dlic_status dlic_train_step(dlic_trainer *t, const uint8_t *d_ctx, co
     if (s) return s;
     t->step += 1;
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
-    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
+    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->n_out, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
     k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, t->grads, t->mom, t->vel, (int)t->nparams, t->lr,
                                                              t->beta1, t->beta2, t->eps, c1, c2, sa);
     cudaError_t ce = cudaGetLastError();
@@ -1414,7 +1636,7 @@ extern "C" dlic_status dlic_train_apply(dlic_trainer *t, const float *d_grads, v
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     t->step += 1;
     const float c1 = 1.0f - powf(t->beta1, (float)t->step), c2 = 1.0f - powf(t->beta2, (float)t->step);
-    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
+    const ShadowArgs sa{t->n_in, t->k1, t->h1, t->h2, t->n_out, t->bf, t->split, t->w1, t->w2, t->w3, t->w2t, t->w3t};
     k_adam<<<(int)((t->nparams + 255) / 256), 256, 0, st>>>(t->params, d_grads, t->mom, t->vel, (int)t->nparams, t->lr,
                                                              t->beta1, t->beta2, t->eps, c1, c2, sa);
     cudaError_t ce = cudaGetLastError();
@@ -1428,13 +1650,13 @@ extern "C" dlic_status dlic_trainer_set_value_weights(dlic_trainer *t, const flo
         return DLIC_OK;
     }
     double total = 0.0;
-    for (int v = 0; v < kSymbols; v++) {
+    for (int v = 0; v < t->n_out; v++) {
         if (!(h_weights[v] >= 0.0f) || !isfinite(h_weights[v]))
             return fail(DLIC_ERR_INVALID, "value weight %d is negative or not finite", v);
         total += h_weights[v];
     }
     if (!(total > 0.0)) return fail(DLIC_ERR_INVALID, "every value weight is zero");
-    cudaError_t ce = cudaMemcpy(t->vw, h_weights, 4 * kSymbols, cudaMemcpyHostToDevice);
+    cudaError_t ce = cudaMemcpy(t->vw, h_weights, 4 * (size_t)t->n_out, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return cuda_fail(ce, "value weights");
     t->weighted = 1;
     return DLIC_OK;

@@ -24,9 +24,9 @@ def flatten(layers) -> np.ndarray:
     return np.concatenate([np.asarray(a, np.float32).reshape(-1) for wb in layers for a in wb])
 
 
-def unflatten(vec, h1: int, h2: int, n_in: int = 12):
+def unflatten(vec, h1: int, h2: int, n_in: int = 12, n_out: int = 256):
     v = np.asarray(vec, np.float32)
-    shapes = [(h1, n_in), (h1,), (h2, h1), (h2,), (256, h2), (256,)]
+    shapes = [(h1, n_in), (h1,), (h2, h1), (h2,), (n_out, h2), (n_out,)]
     out, off = [], 0
     for s in shapes:
         n = int(np.prod(s))
@@ -156,18 +156,32 @@ def _contexts_at(images, idx, rr, cc, window):
 
 
 class Trainer:
-    """FP32 master weights + Adam on the current CUDA device."""
+    """FP32 master weights + Adam on the current CUDA device.  A network of
+    4096 outputs (12-bit samples, Sec. IV "Higher Bit Depth") trains on u16
+    contexts and targets; one of 256 on u8."""
 
     def __init__(self, layers, mode: str = "bf16", max_batch: int = 65536):
         self.n_in = layers[0][0].shape[1]   # the window's priors
         self.h1 = layers[0][0].shape[0]
         self.h2 = layers[1][0].shape[0]
+        self.n_out = layers[2][0].shape[0]
         self.mode = mode
-        self.nparams = _lib.dlic_train_param_count(self.n_in, self.h1, self.h2)
+        self.nparams = _lib.dlic_train_param_count_k(self.n_in, self.h1, self.h2, self.n_out)
         flat = np.ascontiguousarray(flatten(layers))
         assert flat.size == self.nparams
-        self.handle = _lib.dlic_trainer_create(self.n_in, self.h1, self.h2, MODES[mode], max_batch, flat)
+        self.handle = _lib.dlic_trainer_create_k(self.n_in, self.h1, self.h2, self.n_out, MODES[mode], max_batch,
+                                                 flat)
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def _check(self, ctx: torch.Tensor, tgt: torch.Tensor):
+        want = torch.int16 if self.n_out == M.N_OUT_12 else torch.uint8
+        for t in (ctx, tgt):
+            if not (t.is_cuda and t.is_contiguous() and (t.dtype == want or (want == torch.int16 and
+                                                                               t.dtype == torch.uint16))):
+                raise ValueError(f"contexts and targets must be contiguous device tensors of "
+                                 f"{'u16 samples' if want == torch.int16 else 'uint8'}")
+        if ctx.numel() != tgt.numel() * self.n_in:
+            raise ValueError("one context of n_in priors per target")
 
     def close(self):
         if self.handle:
@@ -185,6 +199,7 @@ class Trainer:
         return int(torch.cuda.current_stream().cuda_stream)
 
     def forward(self, ctx: torch.Tensor, tgt: torch.Tensor) -> torch.Tensor:
+        self._check(ctx, tgt)
         _lib.dlic_train_forward(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
                                 self.loss.data_ptr(), self._stream())
         return self.loss
@@ -192,19 +207,22 @@ class Trainer:
     def backward(self, ctx: torch.Tensor, tgt: torch.Tensor, grads: torch.Tensor | None = None):
         if grads is None:
             grads = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        self._check(ctx, tgt)
         _lib.dlic_train_backward(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
                                  self.loss.data_ptr(), grads.data_ptr(), self._stream())
         return self.loss, grads
 
     def step(self, ctx: torch.Tensor, tgt: torch.Tensor) -> torch.Tensor:
+        self._check(ctx, tgt)
         _lib.dlic_train_step(self.handle, ctx.data_ptr(), tgt.data_ptr(), tgt.numel(),
                              self.loss.data_ptr(), self._stream())
         return self.loss
 
     def set_value_weights(self, weights=None):
         """The frequency-weighted loss (Sec. IV "Color Frequencies"): one loss
-        weight per target value (256), or None for the plain loss."""
-        _lib.dlic_trainer_set_value_weights(self.handle, weights)
+        weight per target value (256, or 4096 for 12-bit samples), or None
+        for the plain loss."""
+        _lib.dlic_trainer_set_value_weights(self.handle, weights, self.n_out)
 
     def apply(self, grads: torch.Tensor):
         """One Adam update with the given gradient (device float32, the
@@ -224,11 +242,14 @@ class Trainer:
         _lib.dlic_trainer_params(self.handle, flat.data_ptr(), True, self._stream())
 
     def layers(self):
-        return unflatten(self.params().cpu().numpy(), self.h1, self.h2, self.n_in)
+        return unflatten(self.params().cpu().numpy(), self.h1, self.h2, self.n_in, self.n_out)
 
     def fp32_blob(self, window=M.DEFAULT_WINDOW) -> bytes:
         """The trained network as an FP32 model blob for `window` (whose
-        prior count is the trainer's n_in)."""
+        prior count is the trainer's n_in); a 12-bit network (4096
+        outputs) takes the default window."""
+        if self.n_out == M.N_OUT_12:
+            return M.fp32_blob12(self.layers())
         return M.fp32_blob(self.layers(), window)
 
     def status(self) -> int:
