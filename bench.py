@@ -516,9 +516,84 @@ def measure_12bit(args):
         return {"workload": "one 256x256 12-bit MRI-like slice (phantom, seed 12), FP32 12-128-128-4096, "
                             "96 streams", "enc_mpix_s": round(img.size / te / 1e3, 3),
                 "dec_mpix_s": round(img.size / td / 1e3, 4), "bpp": round(8.0 * nbytes / img.size, 4),
-                "roundtrip_bit_exact": ok}
+                "roundtrip_bit_exact": ok, "training": measure_12bit_training(args, img, S)}
     except Exception as e:   # recorded, so that the rest of the line stands
         return {"error": f"{type(e).__name__}: {e}"}
+
+
+TRAIN12_WIDTHS = [12, 128, 128, 4096]
+TRAIN12_BATCH = 16384
+# forward 2 (12*128 + 128*128 + 128*4096) flop, backward twice that without
+# the first layer's input gradient
+TRAIN12_FLOP_PER_CTX = 3 * 2 * (12 * 128 + 128 * 128 + 128 * 4096) - 2 * 12 * 128
+
+
+def measure_12bit_training(args, img, S, steps: int = 400):
+    """12-bit training (Sec. IV "Higher Bit Depth", the 4096-way loss):
+    12-128-128-4096 from Xavier weights on contexts of 12 other 256x256
+    12-bit phantom slices, batch 16384; ms per step in each mode (CUDA
+    events after warm-up), then `steps` split-BF16 steps and the bench's
+    slice coded with the untrained and the trained FP32 networks."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2207_05152_gb300 import model as M, train as T
+    from paper_2207_05152_gb300.codec import Codec
+    imgs = [synth.phantom_image12(256, 256, 1200 + i) for i in range(12)]
+    ctx, tgt = T.sample_contexts(imgs, TRAIN12_BATCH * steps, 1212)
+    c = torch.from_numpy(ctx.view(np.int16)).cuda()
+    t = torch.from_numpy(tgt.view(np.int16)).cuda()
+    layers = synth.xavier_mlp(TRAIN12_WIDTHS, 1213)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "12-128-128-4096 on 12-bit phantom contexts, batch 16384, forward + backward + Adam",
+           "flop_per_ctx": TRAIN12_FLOP_PER_CTX}
+    _, bf16_peak, _ = _peaks()
+    B = TRAIN12_BATCH
+
+    def batch(k):
+        k %= steps
+        return c[k * B:(k + 1) * B], t[k * B:(k + 1) * B]
+
+    for mode in ("bf16x3", "bf16", "fp32"):
+        tr = T.Trainer(layers, mode, max_batch=B)
+        for k in range(args.warmup):
+            tr.step(*batch(k))
+        n = args.steps if mode != "fp32" else max(3, args.steps // 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n):
+            tr.step(*batch(k))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        assert tr.status() == 0
+        tr.close()
+        tfl = TRAIN12_FLOP_PER_CTX * B / (ms * 1e-3) / 1e12
+        out[mode] = {"ms_per_step": round(ms, 4), "ctx_s": round(B / (ms * 1e-3), 1), "tflops": round(tfl, 2),
+                     "roofline_frac": round(tfl / bf16_peak, 4)}
+    tr = T.Trainer(layers, "bf16x3", max_batch=B)
+    losses = []
+    for k in range(steps):
+        losses.append(tr.step(*batch(k)).clone())
+    torch.cuda.synchronize()
+    assert tr.status() == 0
+    res = {}
+    for name, blob in (("untrained", M.fp32_blob12(layers)), ("trained", tr.fp32_blob())):
+        codec = Codec(blob)
+        x = torch.from_numpy(img.astype(np.int16)).cuda()
+        o, offs = codec.encode([x], [S])
+        nbytes = int(offs[1].item())
+        dec, st = codec.decode(o, [0, nbytes], [img.shape])
+        torch.cuda.synchronize()
+        res[name] = {"bpp": round(8.0 * nbytes / img.size, 4),
+                     "roundtrip_bit_exact": int(st[0].item()) == 0 and bool(torch.equal(dec[0], x))}
+        codec.close()
+    tr.close()
+    out["split_bf16_steps"] = steps
+    out["loss_bits_first_last"] = [round(float(losses[0].item()), 4), round(float(losses[-1].item()), 4)]
+    out.update(res)
+    return out
 
 
 def measure_volume(args):

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT || PERSIST ? 1 : 2)
                     if (g.b_mn)
                         for (int h = 0; h < g.b_boxes; h++) tma_load_2d(tc::smem_addr(sb + 8192 * h), mb, 64 * h, k, bar);
                     else
-                        tma_load_2d(tc::smem_addr(sb), mb, k, 0, bar);
+                        tma_load_2d(tc::smem_addr(sb), mb, k, (int)blockIdx.y * N, bar);   // n-block of a wide B
                 }
             }
         }
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kGemmThreads, SPLIT || PERSIST ? 1 : 2)
         if (s_fail) n_hi = n_lo;
         const uint32_t taddr = tm + 256u * (uint32_t)acc + ((uint32_t)(32 * q) << 16);
         if (epi == EPI_F32) {
-            float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc;
+            float *c = e.c + (size_t)blockIdx.z * e.M * e.ldc + (size_t)m * e.ldc + (size_t)blockIdx.y * N;
             if (nkb == 0) {
                 if (valid)
                     for (int n0 = n_lo; n0 < n_hi; n0 += 4) *reinterpret_cast<float4 *>(c + n0) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1035,9 +1035,11 @@ struct Operand {
     int mn;
 };
 
-// C = A[M x K] B[N x K]^T with the given epilogue.
+// C = A[M x K] B[N x K]^T with the given epilogue.  nblk > 1 (EPI_F32, K-major
+// B of nblk * N rows, tensor-core path): nblk column blocks of N, one per
+// gridDim.y, C's columns offset by the block.
 dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int N, int K, int epi, EpiArgs e,
-                 int splits, cudaStream_t st) {
+                 int splits, cudaStream_t st, int nblk = 1) {
     e.M = M;
     e.N = N;
     e.ldT = t->max_batch;
@@ -1058,6 +1060,7 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
         // epilogues run side by side; measured faster than one persistent
         // CTA.  The weight gradients (M = 256 or h, K = batch) take one tile
         // per CTA with split-K over gridDim.z and a deeper pipeline.
+        if (nblk > 1 && (epi != EPI_F32 || b.mn)) return fail(DLIC_ERR_INVALID, "column blocks need EPI_F32, K-major B");
         const bool persist = t->split && epi != EPI_F32;
         g.stages = epi == EPI_F32 && !t->split ? 4 : 2;
         CUtensorMap ma, mb, mal, mbl;
@@ -1078,7 +1081,7 @@ dlic_status gemm(dlic_trainer *t, const Operand &a, const Operand &b, int M, int
         const int gx = persist ? min(mt, t->num_sms) : mt;
         auto launch = [&](auto kern) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            kern<<<dim3(gx, 1, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
+            kern<<<dim3(gx, nblk, splits), kGemmThreads, smem, st>>>(ma, mb, mal, mbl, K, per, epi, g, e, t->err);
         };
         if (persist)
             launch(k_gemm_tc<true, true>);
@@ -1157,55 +1160,65 @@ __global__ void __launch_bounds__(1024) k_wsum(const void *tgt, int wide, int B,
 
 // Softmax cross-entropy over the 4096 outputs of a 12-bit network (Sec. IV
 // "Higher Bit Depth"), a row too long for one tensor-memory tile: the output
-// layer's GEMMs first write z - b3 to Z [B][4096] (FP32), then this kernel
+// layer's GEMM first writes z - b3 to Z [B][4096] (FP32), then this kernel
 // does what the fused epilogue of the 256-output layer does (maximum, sum
 // of expf, lse = m + logf(sum), loss (lse - z_y) / ln 2 weighted as there,
 // dz = (softmax - onehot) * scale) with every logit read from HBM once.
-// One CTA of 512 threads per 128-row tile; thread t owns the columns 4t ..
-// 4t + 3 and 2048 + 4t .. 2048 + 4t + 3 of every row, so that a row's loads
-// are two fully coalesced 8 KB sweeps; rows go four at a time through two
-// block reductions (warp trees, then the 16 warp values in a fixed order),
-// so every sum has the same order on every run.  The thread keeps its
-// columns' dz sums over the tile (the db3 partials) in registers; the
-// tile's loss and column partials are added in a fixed order afterwards.
-constexpr int kWideOut = 4096, kWideRows = 128, kWideThreads = 512, kWideGroup = 4;
-__global__ void __launch_bounds__(kWideThreads) k_softmax_wide(const float *Z, const float *b3, const uint16_t *tgt,
-                                                               int B, float inv_batch_ln2, const float *vw,
-                                                               const float *wnorm, void *DZ, size_t dz_plane, int bf16,
-                                                               int split, float *colsum, float *losspart, int *err) {
+// One CTA of 512 threads per 32-row tile (two CTAs per SM); thread t owns
+// the columns 4t .. 4t + 3 and 2048 + 4t .. 2048 + 4t + 3 of every row, so
+// that a row's loads are two fully coalesced 8 KB sweeps; rows go four at a
+// time through two block reductions (warp trees, then the 16 warp values in
+// a fixed order), so every sum has the same order on every run.  The thread
+// keeps its columns' dz sums over the tile (the db3 partials) in registers;
+// the tiles' loss and column partials are added in a fixed order afterwards.
+constexpr int kWideOut = 4096, kWideRows = 32, kWideThreads = 512, kWideGroup = 2;
+__global__ void __launch_bounds__(kWideThreads, 2) k_softmax_wide(const float *Z, const float *b3, const uint16_t *tgt,
+                                                                  int B, float inv_batch_ln2, const float *vw,
+                                                                  const float *wnorm, void *DZ, size_t dz_plane,
+                                                                  int bf16, int split, float *colsum, float *losspart,
+                                                                  int *err) {
     __shared__ float s_max[kWideGroup][kWideThreads / 32], s_sum[kWideGroup][kWideThreads / 32];
     __shared__ float s_loss[kWideThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r0 = blockIdx.x * kWideRows;
     const int cA = 4 * tid, cB = kWideOut / 2 + 4 * tid;
-    const float4 bA = *reinterpret_cast<const float4 *>(b3 + cA), bB = *reinterpret_cast<const float4 *>(b3 + cB);
-    const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
     float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float loss_acc = 0.0f;
     for (int g0 = 0; g0 < kWideRows; g0 += kWideGroup) {
-        float zb[kWideGroup][8], mx[kWideGroup];
+        // v: the row's logits, then exp(z - m), then dz, in place
+        float v[kWideGroup][8], mx[kWideGroup], zy[kWideGroup];
+        int ys[kWideGroup];
 #pragma unroll
         for (int i = 0; i < kWideGroup; i++) {
             const int row = r0 + g0 + i;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+            int y = 0;
             if (row < B) {
                 const float *z = Z + (size_t)row * kWideOut;
                 a = *reinterpret_cast<const float4 *>(z + cA);
                 c = *reinterpret_cast<const float4 *>(z + cB);
+                y = tgt[row];
+                if (y >= kWideOut) {
+                    atomicExch(err, (int)DLIC_ERR_INVALID);
+                    y = 0;
+                }
             }
-            const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+            const float4 bA = *reinterpret_cast<const float4 *>(b3 + cA), bB = *reinterpret_cast<const float4 *>(b3 + cB);
+            v[i][0] = a.x + bA.x; v[i][1] = a.y + bA.y; v[i][2] = a.z + bA.z; v[i][3] = a.w + bA.w;
+            v[i][4] = c.x + bB.x; v[i][5] = c.y + bB.y; v[i][6] = c.z + bB.z; v[i][7] = c.w + bB.w;
+            ys[i] = y;
             mx[i] = -INFINITY;
+            zy[i] = 0.0f;
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                zb[i][q] = v[q] + bias[q];
-                mx[i] = fmaxf(mx[i], zb[i][q]);
+                mx[i] = fmaxf(mx[i], v[i][q]);
+                if ((q < 4 ? cA : cB - 4) + q == y) zy[i] = v[i][q];
             }
 #pragma unroll
             for (int off = 16; off; off >>= 1) mx[i] = fmaxf(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], off));
             if (lane == 0) s_max[i][warp] = mx[i];
         }
         __syncthreads();
-        float ex[kWideGroup][8], se[kWideGroup];
 #pragma unroll
         for (int i = 0; i < kWideGroup; i++) {
             float m = s_max[i][0];
@@ -1215,8 +1228,8 @@ __global__ void __launch_bounds__(kWideThreads) k_softmax_wide(const float *Z, c
             float l = 0.0f;
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                ex[i][q] = expf(zb[i][q] - m);
-                l += ex[i][q];
+                v[i][q] = expf(v[i][q] - m);
+                l += v[i][q];
             }
 #pragma unroll
             for (int off = 16; off; off >>= 1) l += __shfl_down_sync(0xffffffffu, l, off);
@@ -1226,36 +1239,30 @@ __global__ void __launch_bounds__(kWideThreads) k_softmax_wide(const float *Z, c
 #pragma unroll
         for (int i = 0; i < kWideGroup; i++) {
             const int row = r0 + g0 + i;
-            float sum = s_sum[i][0];
+            float se = s_sum[i][0];
 #pragma unroll
-            for (int w = 1; w < kWideThreads / 32; w++) sum += s_sum[i][w];
-            se[i] = sum;
+            for (int w = 1; w < kWideThreads / 32; w++) se += s_sum[i][w];
             if (row >= B) continue;
-            int y = tgt[row];
-            if (y >= kWideOut) {
-                atomicExch(err, (int)DLIC_ERR_INVALID);
-                y = 0;
-            }
-            const float lse = mx[i] + logf(se[i]), inv = 1.0f / se[i];
+            const int y = ys[i];
+            const float lse = mx[i] + logf(se), inv = 1.0f / se;
             const float rw = vw ? vw[y] : 1.0f;
             const float gscale = vw ? rw * wnorm[0] : inv_batch_ln2, lw = vw ? rw * wnorm[1] : 1.0f;
-            float g[8];
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const int col = (q < 4 ? cA : cB - 4) + q;
-                g[q] = ex[i][q] * inv;
-                if (col == y) {
-                    g[q] -= 1.0f;
-                    loss_acc += lw * ((lse - zb[i][q]) / kLn2);
+                float g = v[i][q] * inv;
+                if ((q < 4 ? cA : cB - 4) + q == y) {
+                    g -= 1.0f;
+                    loss_acc += lw * ((lse - zy[i]) / kLn2);
                 }
-                g[q] *= gscale;
-                cs[q] += g[q];
+                g *= gscale;
+                v[i][q] = g;
+                cs[q] += g;
             }
             const size_t o = (size_t)row * kWideOut;
             if (bf16) {
                 uint16_t *d = static_cast<uint16_t *>(DZ);
-                const uint2 hA = make_uint2(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]));
-                const uint2 hB = make_uint2(pack_bf16x2(g[4], g[5]), pack_bf16x2(g[6], g[7]));
+                const uint2 hA = make_uint2(pack_bf16x2(v[i][0], v[i][1]), pack_bf16x2(v[i][2], v[i][3]));
+                const uint2 hB = make_uint2(pack_bf16x2(v[i][4], v[i][5]), pack_bf16x2(v[i][6], v[i][7]));
                 *reinterpret_cast<uint2 *>(d + o + cA) = hA;
                 *reinterpret_cast<uint2 *>(d + o + cB) = hB;
                 if (split) {
@@ -1263,15 +1270,15 @@ __global__ void __launch_bounds__(kWideThreads) k_softmax_wide(const float *Z, c
                     uint32_t lo[4];
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        lo[k] = pack_bf16x2(g[2 * k] - __uint_as_float(h[k] << 16),
-                                            g[2 * k + 1] - __uint_as_float(h[k] & 0xFFFF0000u));
+                        lo[k] = pack_bf16x2(v[i][2 * k] - __uint_as_float(h[k] << 16),
+                                            v[i][2 * k + 1] - __uint_as_float(h[k] & 0xFFFF0000u));
                     *reinterpret_cast<uint2 *>(d + dz_plane + o + cA) = make_uint2(lo[0], lo[1]);
                     *reinterpret_cast<uint2 *>(d + dz_plane + o + cB) = make_uint2(lo[2], lo[3]);
                 }
             } else {
                 float *d = static_cast<float *>(DZ);
-                *reinterpret_cast<float4 *>(d + o + cA) = make_float4(g[0], g[1], g[2], g[3]);
-                *reinterpret_cast<float4 *>(d + o + cB) = make_float4(g[4], g[5], g[6], g[7]);
+                *reinterpret_cast<float4 *>(d + o + cA) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+                *reinterpret_cast<float4 *>(d + o + cB) = make_float4(v[i][4], v[i][5], v[i][6], v[i][7]);
             }
         }
     }
@@ -1367,30 +1374,25 @@ dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float 
         // softmax kernel
         e = EpiArgs{}; e.c = t->Z; e.ldc = n_out;
         if (bf) {
-            for (int j = 0; j < n_out / 256; j++) {
-                EpiArgs ej = e;
-                ej.c = t->Z + 256 * j;
-                const Operand w3j{static_cast<const uint16_t *>(t->w3) + (size_t)256 * j * h2, 256, h2, h2,
-                                  (size_t)n_out * h2, 0};
-                if ((s = gemm(t, rowmaj(t->H2, h2), w3j, B, 256, h2, EPI_F32, ej, 1, st))) return s;
-            }
+            if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, n_out, h2), B, 256, h2, EPI_F32, e, 1, st, n_out / 256)))
+                return s;
         } else if ((s = gemm(t, rowmaj(t->H2, h2), wmat(t->w3, n_out, h2), B, n_out, h2, EPI_F32, e, 1, st))) {
             return s;
         }
-        k_softmax_wide<<<mt, kWideThreads, 0, st>>>(t->Z, p.b3, static_cast<const uint16_t *>(tgt), B,
-                                                    1.0f / ((float)B * kLn2), t->weighted ? t->vw : nullptr,
-                                                    t->wnorm, t->DZ, Bm * n_out, bf, t->split, t->colsum,
-                                                    t->losspart, t->err);
+        k_softmax_wide<<<(B + kWideRows - 1) / kWideRows, kWideThreads, 0, st>>>(
+            t->Z, p.b3, static_cast<const uint16_t *>(tgt), B, 1.0f / ((float)B * kLn2),
+            t->weighted ? t->vw : nullptr, t->wnorm, t->DZ, Bm * n_out, bf, t->split, t->colsum, t->losspart, t->err);
         if (!bf && backward)
             k_transpose_f32<<<dim3(n_out / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
                 static_cast<const float *>(t->DZ), B, n_out, static_cast<float *>(t->DZT), P);
     }
-    reduce_parts(t->losspart, mt, 1, 1, d_loss, t->weighted ? 1.0f : 1.0f / (float)B, 0, 0, st);
+    const int lt = t->wide ? (B + kWideRows - 1) / kWideRows : mt;   // tiles of the loss and db3 partials
+    reduce_parts(t->losspart, lt, 1, 1, d_loss, t->weighted ? 1.0f : 1.0f / (float)B, 0, 0, st);
     if (!backward) {
         cudaError_t ce = cudaGetLastError();
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
     }
-    reduce_parts(t->colsum, mt, n_out, n_out, g.b3, 1.0f, 0, 0, st);
+    reduce_parts(t->colsum, lt, n_out, n_out, g.b3, 1.0f, 0, 0, st);
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.mask = t->M2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
@@ -1512,8 +1514,10 @@ extern "C" dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out
     // split-K partials: up to one split per SM (BF16) or 64 (FP32)
     t->part_floats = (size_t)(t->num_sms > 64 ? t->num_sms : 64) * kSymbols * hmax;
     t->part = (float *)A(4 * t->part_floats);
-    t->colsum = (float *)A(4 * ((Bm + 127) / 128) * n_out);   // one row per m-tile, the last one ragged
-    t->losspart = (float *)A(4 * ((Bm + 127) / 128));
+    // one row per m-tile (or per 32-row tile of the 4096-way softmax), the last one ragged
+    const size_t ntile = t->wide ? (Bm + kWideRows - 1) / kWideRows : (Bm + 127) / 128;
+    t->colsum = (float *)A(4 * ntile * n_out);
+    t->losspart = (float *)A(4 * ntile);
     t->gacc = (float *)A(4 * t->nparams);
     t->vw = (float *)A(4 * (size_t)n_out);
     t->wnorm = (float *)A(8);
