@@ -51,8 +51,10 @@ def test_identity_layers_code_like_the_shallow_network(orc, prec, extra):
     assert st == 0 and np.array_equal(dec, img)
 
 
-def test_deep_fp32_logits_against_float64(orc):
-    widths = [12, 64, 96, 48, 32, 80, 256]   # five hidden layers: six dense layers
+@pytest.mark.parametrize("widths", [[12, 64, 96, 48, 32, 80, 256],    # five hidden layers: six dense layers
+                                    [12, 1024, 320, 256],             # hidden layers wider than 256
+                                    [12, 4096, 256]])                 # the widest of Sec. II-B
+def test_deep_fp32_logits_against_float64(orc, widths):
     layers = _random_deep(widths, 21)
     blob = M.deep_fp32_blob(layers)
     pri = synth.voronoi_image(16, 16, 3).reshape(-1, 1)[:, [0] * 12] ^ np.arange(12, dtype=np.uint8)
@@ -65,8 +67,8 @@ def test_deep_fp32_logits_against_float64(orc):
     assert np.max(np.abs(z - x)) <= 1e-4 * max(1.0, np.abs(x).max())
 
 
-def test_deep_int8_logits_exact(orc):
-    widths = [12, 48, 32, 64, 40, 256]
+@pytest.mark.parametrize("widths", [[12, 48, 32, 64, 40, 256], [12, 1024, 2048, 256]])
+def test_deep_int8_logits_exact(orc, widths):
     layers = _random_deep(widths, 23)
     img = synth.voronoi_image(30, 30, 4)
     cal = calib_contexts([img])
@@ -79,11 +81,13 @@ def test_deep_int8_logits_exact(orc):
     for li, (wq, s, o) in enumerate(q):
         acc = a @ wq.astype(np.int64).T
         s32, o32 = s.astype(f32), o.astype(f32)
-        # fma(acc, s, o): float64 holds acc * s exactly (|acc| < 2^24, s
-        # float32); the float64 sum rounded to float32 differs from a single
-        # rounding only on an exact float32 midpoint, which these fixed
-        # inputs do not hit
-        v = (acc.astype(np.float64) * s32.astype(np.float64) + o32.astype(np.float64)).astype(f32)
+        # fma(float(acc), s, o): the integer rounded to float32 first (exact
+        # below 2^24; wide layers reach past it), then float64 holds the
+        # product with s exactly; the float64 sum rounded to float32 differs
+        # from a single rounding only on an exact float32 midpoint, which
+        # these fixed inputs do not hit
+        accf = acc.astype(f32).astype(np.float64)
+        v = (accf * s32.astype(np.float64) + o32.astype(np.float64)).astype(f32)
         if li < len(q) - 1:
             a = np.clip(np.rint(v), 0, 255).astype(np.int64)
         else:
