@@ -263,6 +263,10 @@ def run_ours(args):
     # six dense layers (five hidden, widths 128) on the CUDA-core coder
     deep8, _ = workloads.deep_models()
     rdeep = measure(deep8, 2, 2)
+    # two hidden layers of 4096 units (the widest of Sec. II-B) on the
+    # layer-at-a-time coder
+    wide8, wide32 = workloads.wide_models()
+    rwide, rwide32 = measure(wide8, 2, 1), measure(wide32, 1, 1)
 
     def leg(r):
         return {"enc_mpix_s": round(N / (statistics.mean(r["enc"]) * 1e-3) / 1e6, 3),
@@ -345,6 +349,14 @@ def run_ours(args):
                         "int8": leg(r6), "fp32": leg(r6f)},
         "deep_network": {"widths": [12, 128, 128, 128, 128, 128, 256], "precision": "int8",
                          "kernels": "CUDA-core encoder, unit-split wavefront decoder", **leg(rdeep)},
+        "wide_network": {"widths": [12, 4096, 4096, 256],
+                         "weights": "the predictive 12-64-64-256 network in 64 of each layer's 4096 units, "
+                                    "seeded random weights in the rest",
+                         "kernels": "layer-at-a-time: one GEMM-like kernel per dense layer over 4096-pixel "
+                                    "passes (encode) or one wave (decode)",
+                         "mac_per_px": WIDE_MAC_PER_PX, "int8": leg(rwide), "fp32": leg(rwide32),
+                         "int8_enc_tmac_s": round(WIDE_MAC_PER_PX * N / (statistics.mean(rwide["enc"]) * 1e-3) / 1e12, 2),
+                         "fp32_enc_tfma_s": round(WIDE_MAC_PER_PX * N / (statistics.mean(rwide32["enc"]) * 1e-3) / 1e12, 2)},
         "roofline": {"kernel": dominant, "bound": "tensor", "achieved": round(achieved, 4),
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(achieved / bf16_peak, 6),
                      "peak_source": f"bf16 burst, {peak_kind}", "traffic": _profiled_traffic(dominant)},
@@ -520,6 +532,8 @@ def measure_12bit(args):
     except Exception as e:   # recorded, so that the rest of the line stands
         return {"error": f"{type(e).__name__}: {e}"}
 
+
+WIDE_MAC_PER_PX = 12 * 4096 + 4096 * 4096 + 4096 * 256
 
 TRAIN12_WIDTHS = [12, 128, 128, 4096]
 TRAIN12_BATCH = 16384

@@ -63,6 +63,7 @@ struct dlic_model {
     cudaStream_t group_stream[kDecodeGroups] = {};
     cudaEvent_t fork_event = nullptr, join_event[kDecodeGroups] = {};
     int decode_plan = DLIC_PLAN_AUTO;
+    DevLayer hl[kMaxLayers] = {};   // host copy of the layer table (networks wider than 256)
 };
 
 extern "C" const char *dlic_last_error(void) { return g_err; }
@@ -103,7 +104,11 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     // 4096 outputs: 12-bit pixels (Sec. IV "Higher Bit Depth"), on the
     // layer-table FP32 kernels like networks of other depths
     const bool twelve = n_out == (uint32_t)kSymbols12;
-    const bool deep = L != 2 || twelve;   // the layer-table kernels
+    uint32_t wmax = 0;
+    for (int l = 0; l < L; l++) wmax = std::max(wmax, widths[l]);
+    // hidden layers wider than 256 (8-bit): one layer at a time (wide.cu)
+    const bool wide = !twelve && wmax > (uint32_t)kMaxHidden;
+    const bool deep = L != 2 || twelve || wide;   // the layer-table kernels
     if (prec > 1) return fail(DLIC_ERR_INVALID, "unknown precision %u", prec);
     // window field: 2 = the default radius-2 window, else 1 << 24 | u | l << 8 | r << 16,
     // or a 3D window 2 << 28 | u | l << 4 | r << 8 | pu << 10 | pd << 14 | pl << 18 | pr << 22
@@ -143,9 +148,11 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
     } else {
         for (int l = 0; l < L; l++)
-            if (widths[l] < 4 || widths[l] > kMaxHidden || widths[l] % 4)
-                return fail(DLIC_ERR_UNSUPPORTED, "hidden widths of a 12-bit network or of a network of %d hidden "
-                            "layers must be multiples of 4 in [4, 256]", L);
+            if (widths[l] < 4 || widths[l] > (twelve ? (uint32_t)kMaxHidden : 4096u) || widths[l] % 4)
+                return fail(DLIC_ERR_UNSUPPORTED, twelve ? "hidden widths of a 12-bit network must be multiples of 4 in "
+                                                           "[4, 256]"
+                                                         : "hidden widths of a network of %d hidden layers (or wider "
+                                                           "than 256) must be multiples of 4 in [4, 4096]", L);
         if (radius != 2)
             return fail(DLIC_ERR_UNSUPPORTED, "12-bit networks and networks of other than two hidden layers run with "
                                               "the default window only");
@@ -285,6 +292,7 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
         }
         memcpy(host.data() + off_table, table.data(), sizeof(DevLayer) * nl);
         d.layers = reinterpret_cast<const DevLayer *>(base + off_table);
+        for (int l = 0; l < nl; l++) m->hl[l] = table[l];
     }
     e = cudaMemcpy(m->mem, host.data(), host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -445,7 +453,7 @@ extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dli
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, streams, false, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
-    *bytes = enc_ws_bytes(image_items(im, n, streams));
+    *bytes = enc_ws_bytes(image_items(im, n, streams)) + wide_scratch_bytes(m->dev);
     return DLIC_OK;
 }
 
@@ -458,7 +466,7 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
     if (!d_out || !d_out_offsets || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(DLIC_ERR_INVALID, "workspace must be 256-byte aligned");
     size_t need_out = 0;
-    const size_t need_ws = enc_ws_bytes(it);
+    const size_t need_ws = enc_ws_bytes(it) + wide_scratch_bytes(m->dev);
     for (const EncItem &e : it) need_out += dlic_max_encoded_bytes(e.H, e.W, e.S);
     if (ws_bytes < need_ws) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need_ws);
     if (out_capacity < need_out) return fail(DLIC_ERR_CAPACITY, "output capacity %zu < %zu bytes", out_capacity, need_out);
@@ -510,9 +518,10 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
             off += align256(4ull * e.S);
         }
         b->total_tiles = tiles;
-        cudaError_t e = use_tc                  ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
-                        : m->dev.bits == 12 ? launch_predict12(m->dev, *b, err, cs)
-                                            : launch_predict_cc(m->dev, *b, cs);
+        cudaError_t e = use_tc                       ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
+                        : m->dev.bits == 12          ? launch_predict12(m->dev, *b, err, cs)
+                        : wide_supported(m->dev) ? launch_predict_wide(m->dev, m->hl, *b, ws + enc_ws_bytes(it), cs)
+                                                     : launch_predict_cc(m->dev, *b, cs);
         if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
         if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
         delete b;
@@ -529,6 +538,7 @@ extern "C" dlic_status dlic_predict(const dlic_model *m, const dlic_image *im, i
     if (st) return st;
     if (n == 0) return DLIC_OK;
     if (!d_fc) return fail(DLIC_ERR_INVALID, "null output");
+    if (wide_supported(m->dev)) return fail(DLIC_ERR_UNSUPPORTED, "dlic_predict takes hidden widths up to 256");
     if (!d_status && (!d_ws || ws_bytes < 4)) return fail(DLIC_ERR_INVALID, "a status word or 4 bytes of workspace is needed");
     if (reinterpret_cast<uintptr_t>(d_fc) & 3) return fail(DLIC_ERR_INVALID, "d_fc must be 4-byte aligned");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -693,7 +703,7 @@ extern "C" dlic_status dlic_decode_workspace_size(const dlic_model *m, const dli
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, nullptr, true, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
-    *bytes = dec_ws_bytes(dec_image_items(im, n));
+    *bytes = dec_ws_bytes(dec_image_items(im, n)) + wide_scratch_bytes(m->dev);
     return DLIC_OK;
 }
 
@@ -714,8 +724,10 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
     const int n = (int)it.size();
     if (n == 0) return DLIC_OK;
     if (!d_in || !h_in_offsets || !d_status || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
-    const size_t need = dec_ws_bytes(it);
+    const size_t need = dec_ws_bytes(it) + wide_scratch_bytes(m->dev);
     if (ws_bytes < need) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need);
+    // networks wider than 256: the layers' scratch after the stream states
+    uint8_t *wide_scratch = static_cast<uint8_t *>(d_ws) + dec_ws_bytes(it);
     for (int i = 0; i < n; i++) {
         if (h_in_offsets[i + 1] < h_in_offsets[i]) return fail(DLIC_ERR_INVALID, "offsets must not decrease");
         if (h_in_offsets[i] & 1) return fail(DLIC_ERR_INVALID, "bitstream %d starts at an odd offset", i);
@@ -874,6 +886,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
             for (int k = 0; k < cn; k++) fill(b->img[k], members[c0 + k]);
             cudaError_t e = use_wave              ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs)
                             : m->dev.bits == 12 ? launch_decode12(m->dev, *b, gs)
+                            : wide_supported(m->dev) ? launch_decode_wide(m->dev, m->hl, *b, wide_scratch, gs)
                                                 : launch_decode_cc(m->dev, *b, gs);
             delete b;
             if (e != cudaSuccess && err == DLIC_OK)

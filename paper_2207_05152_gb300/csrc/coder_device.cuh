@@ -194,6 +194,16 @@ __device__ __forceinline__ void expand_lut(const uint32_t *lut_g, uint32_t *lut2
     for (int u = tid; u < kTableSteps; u += nthreads) lut2_s[u] = __ldg(lut_g + (u & 63)) >> (u >> 6);
 }
 
+// Order-preserving map of a float to an unsigned integer (and back), so
+// that a warp-wide unsigned maximum finds the float maximum.
+__device__ __forceinline__ uint32_t float_key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
 __device__ __forceinline__ uint32_t table_q(uint32_t W) {
     return (uint32_t)((65280ull << 32) / (unsigned long long)W);
 }

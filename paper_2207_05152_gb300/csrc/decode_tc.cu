@@ -147,21 +147,6 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p) {
     return v;
 }
 
-// Grid decoder of a volume: the volume's state block in the workspace, at
-// im.st_off: a 256-byte header (stream count, ok flag, wave-barrier counter,
-// failure flag), then x, position and end of every stream (z S + s).
-struct VolState {
-    uint32_t *hdr, *x, *pos, *end;
-};
-__host__ __device__ inline size_t vol_state_bytes(int D, int S) { return 256 + 12ull * D * S; }
-__device__ __forceinline__ VolState vol_state(const DecBatch &b, const DecImage &im) {
-    VolState v;
-    v.hdr = reinterpret_cast<uint32_t *>(b.ws + im.st_off);
-    v.x = v.hdr + 64;
-    v.pos = v.x + (size_t)im.D * im.S;
-    v.end = v.pos + (size_t)im.D * im.S;
-    return v;
-}
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) {
     uint32_t v;
@@ -220,15 +205,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                  : "memory");
 }
 
-// Order-preserving map of a float to an unsigned integer (and back), so
-// that a warp-wide unsigned maximum finds the float maximum.
-__device__ __forceinline__ uint32_t float_key(float f) {
-    const uint32_t u = __float_as_uint(f);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float key_float(uint32_t k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
 
 // FP32 network helpers of the wavefront decoder.  Activations are stored
 // [unit][pitch PT] so that a k row of consecutive pixels is one broadcast
@@ -1807,6 +1783,17 @@ cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms
         k_volume_finish<<<1, kDecThreads, 0, st>>>(b);
     else
         k_batch_finish<<<b.n, kDecThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+// The grid decoder's set-up and final check of a 2D batch, for the other
+// decoders that keep their stream states in the workspace.
+cudaError_t launch_batch_setup(const DevModel &m, const DecBatch &b, cudaStream_t st) {
+    k_batch_setup<<<b.n, kDecThreads, 0, st>>>(m, b);
+    return cudaGetLastError();
+}
+cudaError_t launch_batch_finish(const DecBatch &b, cudaStream_t st) {
+    k_batch_finish<<<b.n, kDecThreads, 0, st>>>(b);
     return cudaGetLastError();
 }
 

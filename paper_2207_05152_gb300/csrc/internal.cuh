@@ -120,6 +120,23 @@ struct DecBatch {
     DecImage img[kMaxBatch];
 };
 
+// Stream states of a decode in the workspace, at im.st_off: a 256-byte
+// header (stream count, ok flag, wave-barrier counter, failure flag, whether
+// no wave holds two rows of one stream), then x, position (16-bit words from
+// the start of the input) and end of every stream (z S + s).
+struct VolState {
+    uint32_t *hdr, *x, *pos, *end;
+};
+__host__ __device__ inline size_t vol_state_bytes(int D, int S) { return 256 + 12ull * D * S; }
+__device__ __forceinline__ VolState vol_state(const DecBatch &b, const DecImage &im) {
+    VolState v;
+    v.hdr = reinterpret_cast<uint32_t *>(b.ws + im.st_off);
+    v.x = v.hdr + 64;
+    v.pos = v.x + (size_t)im.D * im.S;
+    v.end = v.pos + (size_t)im.D * im.S;
+    return v;
+}
+
 // Sets the thread-local error text and returns the code.
 dlic_status fail(dlic_status code, const char *fmt, ...);
 dlic_status cuda_fail(cudaError_t e, const char *what);
@@ -142,6 +159,18 @@ cudaError_t launch_decode_cc(const DevModel &m, const DecBatch &b, cudaStream_t 
 // 12-bit pixels (coder12.cu): warp-per-pixel FP32 kernels over the layer table
 cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cudaStream_t st);
 cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t st);
+// Networks with hidden layers wider than 256 (wide.cu): one layer at a time
+// over sets of pixels, activations in a workspace scratch of
+// wide_scratch_bytes; hl is the host copy of the layer table
+bool wide_supported(const DevModel &m);
+size_t wide_scratch_bytes(const DevModel &m);
+cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch,
+                                cudaStream_t st);
+cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecBatch &b, uint8_t *scratch,
+                               cudaStream_t st);
+// the grid decoder's stream-state set-up and final check (decode_tc.cu)
+cudaError_t launch_batch_setup(const DevModel &m, const DecBatch &b, cudaStream_t st);
+cudaError_t launch_batch_finish(const DecBatch &b, cudaStream_t st);
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
 bool wave_decode_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)

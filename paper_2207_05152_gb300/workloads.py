@@ -79,6 +79,31 @@ def deep_models(seed: int = 2, extra: int = 3, hidden: int = 128):
     return M.deep_int8_blob(deep, calibration_contexts()), M.deep_fp32_blob(deep)
 
 
+def wide_models(seed: int = 2, hidden: int = 4096):
+    """(INT8 blob, FP32 blob) of a network with two hidden layers of `hidden`
+    units (Sec. II-B: up to 4096 per hidden layer): the synthetic predictive
+    network 12-64-64-256 in the first 64 units of each hidden layer, the
+    other units with seeded random weights that the output layer does not
+    read (its weights from them are zero), so the tables are realistic and
+    every multiply-add of the dense layers is still done."""
+    (w1, b1), (w2, b2), (w3, b3) = synth.predictive_mlp([M.window_size(M.DEFAULT_WINDOW), 64, 64, 256], seed)
+    rng = synth.Rng(seed + 4096)
+    n = w1.shape[1]
+    W1 = (rng.normal(hidden * n).reshape(hidden, n) * np.sqrt(2.0 / n)).astype(np.float32)
+    W1[:64] = w1
+    B1 = (0.05 * rng.normal(hidden)).astype(np.float32)
+    B1[:64] = b1
+    W2 = (rng.normal(hidden * hidden).reshape(hidden, hidden) * np.sqrt(2.0 / hidden)).astype(np.float32)
+    W2[:64, :] = 0.0
+    W2[:64, :64] = w2
+    B2 = (0.05 * rng.normal(hidden)).astype(np.float32)
+    B2[:64] = b2
+    W3 = np.zeros((256, hidden), np.float32)
+    W3[:, :64] = w3
+    layers = [(W1, B1), (W2, B2), (W3, b3.astype(np.float32))]
+    return M.deep_int8_blob(layers, calibration_contexts()), M.deep_fp32_blob(layers)
+
+
 def cfg2_image() -> np.ndarray:
     return synth.config_image(2)
 

@@ -96,10 +96,14 @@ def test_deeper_network_blobs_are_checked_before_any_device_call(lib):
     cases = [
         (deep([32, 32, 32], window=(3, 3, 2)), lib.DLIC_ERR_UNSUPPORTED),   # three hidden layers, wider window
         (deep([32, 6, 32]), lib.DLIC_ERR_UNSUPPORTED),                      # width not a multiple of 4
-        (deep([32, 260, 32]), lib.DLIC_ERR_UNSUPPORTED),                    # width above 256
+        (deep([32, 258, 32]), lib.DLIC_ERR_UNSUPPORTED),                    # wider than 256, not a multiple of 4
+        (deep([300, 40], window=(3, 3, 2)), lib.DLIC_ERR_UNSUPPORTED),      # wider than 256, wider window
         (deep([24, 40]), lib.DLIC_ERR_UNSUPPORTED),                         # two hidden layers: multiples of 16
     ]
     good = deep([32, 48, 32])
+    too_wide = bytearray(good)
+    too_wide[20:24] = struct.pack("<I", 4100)                               # the second width above 4096
+    cases.append((bytes(too_wide), lib.DLIC_ERR_INVALID))
     bad_l = bytearray(good)
     bad_l[12:16] = struct.pack("<I", 0)                                      # no hidden layer
     cases.append((bytes(bad_l), lib.DLIC_ERR_INVALID))
