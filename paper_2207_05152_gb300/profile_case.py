@@ -5,6 +5,7 @@
     python -m paper_2207_05152_gb300.profile_case --case volume --iters 1
     python -m paper_2207_05152_gb300.profile_case --case deep --size 128 --iters 1
     python -m paper_2207_05152_gb300.profile_case --case twelve --size 64 --iters 1
+    python -m paper_2207_05152_gb300.profile_case --case wide --size 64 --iters 1
 
 Each iteration encodes and decodes the batch and checks the round trip.
 """
@@ -21,7 +22,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4", "volume", "deep", "twelve"])
+    ap.add_argument("--case", default="cfg2", choices=["cfg2", "cfg4", "volume", "deep", "twelve", "wide"])
     ap.add_argument("--size", type=int, default=128, help="deep / twelve: the square image's side")
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--count", type=int, default=8)
@@ -45,6 +46,21 @@ def main():
             torch.cuda.synchronize()
             assert int(status[0].item()) == 0 and torch.equal(dec[0], dv)
         print("ok volume", vol.shape)
+        return
+    if args.case == "wide":
+        # two hidden layers of 4096 units on a square crop of the cfg-2 image
+        import numpy as np
+        w8, w32 = workloads.wide_models()
+        codec = Codec(w8 if args.precision == "int8" else w32)
+        img = np.ascontiguousarray(workloads.cfg2_image()[:args.size, :args.size])
+        dv = torch.from_numpy(img).cuda()
+        for _ in range(args.iters):
+            out, offs = codec.encode([dv], [min(args.size, 64)])
+            o = offs.cpu().tolist()
+            dec, status = codec.decode(out, o, [img.shape])
+            torch.cuda.synchronize()
+            assert int(status[0].item()) == 0 and torch.equal(dec[0], dv)
+        print("ok wide", img.shape)
         return
     if args.case in ("deep", "twelve"):
         # six dense layers (five hidden, widths 128) on an 8-bit crop of the
