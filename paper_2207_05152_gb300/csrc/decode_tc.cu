@@ -31,6 +31,16 @@ constexpr int kDecThreads = 512;
 constexpr int kDecWarps = kDecThreads / 32;
 constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
+// The INT8 network's two wide layers (128 x 128 and 256 x 128 against at
+// most a chunk of pixels per wave) as warp-level bf16 MMAs (mma.sync
+// m16n8k16 with FP32 accumulation, exact for these integer-valued operands:
+// every partial sum is an integer below 2^23): a few tens of cycles per MMA
+// and the accumulators in registers, against a tcgen05 round trip (issue,
+// commit, mbarrier, tensor-memory load) of 0.7-1.0K cycles per layer.  The
+// operands sit row-major in shared memory with rows of kActPitch bf16, so
+// that every fragment load is free of bank conflicts.
+constexpr bool kDecSyncMma = true;
+constexpr int kActPitch = kDecHidden + 8;
 
 struct DecTcLayout {
     // INT8 network: bf16 operand tiles, s8 priors, bf16 activations
@@ -98,6 +108,12 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.h1t = base + xs_bytes;
         L.z = base;
         L.h2t = take(4u * h2 * (nt + 4));
+    } else if (kDecSyncMma) {
+        L.w1 = take((uint32_t)prm.k1 * kDecHidden);   // W1 as s8 words [k1 / 4][128] (the first layer runs as dp4a)
+        L.w2 = take(2u * kDecHidden * kActPitch);     // W2 [unit][k], bf16
+        L.w3 = take(2u * kSymbols * kActPitch);       // W3 [unit][k], bf16
+        L.pri = take((uint32_t)prm.k1 * nt);
+        L.b23 = take(2u * 2u * nt * kActPitch);       // the two hidden layers' outputs [pixel][unit], bf16
     } else {
         L.w1 = take((uint32_t)prm.k1 * kDecHidden);   // W1 as s8 words [k1 / 4][128] (the first layer runs as dp4a)
         L.w2 = take(2u * kDecHidden * kDecHidden);
@@ -522,6 +538,26 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             for (int i = tid; i < kSymbols; i += kDecThreads) wf[NPRI * h1 + h1 + h2 + i] = m.b3[i];
             for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
                 reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
+        } else if (kDecSyncMma) {
+            // W2, W3 as bf16 rows [unit][k] from the packed s8 words [k / 4][unit]
+            auto unpack = [&](const uint32_t *q, int units, uint16_t *dst) {
+                for (int i = tid; i < (kDecHidden / 4) * units; i += kDecThreads) {
+                    const int j = i % units, k4 = i / units;
+                    const uint32_t v = __ldg(q + i);
+                    uint32_t lo = 0, hi = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const uint32_t h = tc::bf16_of_int((int)(int8_t)(uint8_t)(v >> (8 * e)));
+                        if (e < 2) lo |= h << (16 * e); else hi |= h << (16 * (e - 2));
+                    }
+                    *reinterpret_cast<uint2 *>(dst + (size_t)j * kActPitch + 4 * k4) = make_uint2(lo, hi);
+                }
+            };
+            unpack(m.q2t, kDecHidden, reinterpret_cast<uint16_t *>(smem + L.w2));
+            unpack(m.q3t, kSymbols, reinterpret_cast<uint16_t *>(smem + L.w3));
+            uint32_t *w1q = reinterpret_cast<uint32_t *>(smem + L.w1);
+            for (int i = tid; i < (K1 / 4) * kDecHidden; i += kDecThreads)
+                w1q[i] = i < ((NPRI + 3) / 4) * kDecHidden ? __ldg(m.q1t + i) : 0u;
         } else {
             // W2 | W3 of the weight image (after the k1 x 128 bf16 W1 tile)
             const uint4 *src = reinterpret_cast<const uint4 *>(m.tc_w) + 16 * K1;
@@ -548,7 +584,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
         for (int i = tid; i < prm.tq * prm.tslots * prm.tcols; i += kDecThreads) tring[i] = 0u;
     }
-    if constexpr (!F32) {
+    if constexpr (!F32 && !kDecSyncMma) {
         if (warp == 0) {
             tc::tmem_alloc(&tmem_base, 256);
             tc::tmem_relinquish();
@@ -556,7 +592,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     }
     if (tid == 0) {
         if constexpr (!F32) {
-            tc::mbar_init(&bar, 1);
+            if (!kDecSyncMma) tc::mbar_init(&bar, 1);
         } else {
             for (int q = 0; q < kW3Stages; q++) tc::mbar_init(&w3bar[q], 1);
         }
@@ -711,7 +747,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // Every CTA of the cluster reads the same header, so this exit is uniform.
     if (!s_ok) {
         if (tid == 0 && k == 0) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
-        if constexpr (!F32) {
+        if constexpr (!F32 && !kDecSyncMma) {
             if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
         }
         return;
@@ -763,9 +799,16 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const int unit = 32 * q4 + lane;                          // hidden / output unit of this thread
     const uint32_t tm_q = tm + ((uint32_t)(32 * q4) << 16);
     float s1r = 0.f, o1r = 0.f, s2r = 0.f, o2r = 0.f, s3a = 0.f, o3a = 0.f, s3b = 0.f, o3b = 0.f;
+    // warp-level MMAs: the output units of this thread's accumulator rows,
+    // 16 w' + g and 16 w' + g + 8 (w' = warp mod 8 for layer 2, the warp for
+    // layer 3, g = lane / 4)
+    float s2lo = 0.f, o2lo = 0.f, s2hi = 0.f, o2hi = 0.f, s3lo = 0.f, o3lo = 0.f, s3hi = 0.f, o3hi = 0.f;
     if constexpr (!F32) {
         s1r = m.s1[unit]; o1r = m.o1[unit]; s2r = m.s2[unit]; o2r = m.o2[unit];
         s3a = m.s3[unit]; o3a = m.o3[unit]; s3b = m.s3[128 + unit]; o3b = m.o3[128 + unit];
+        const int u2 = 16 * (warp & 7) + (lane >> 2), u3 = 16 * warp + (lane >> 2);   // (layer 2: warps 0..7)
+        s2lo = m.s2[u2]; o2lo = m.o2[u2]; s2hi = m.s2[u2 + 8]; o2hi = m.o2[u2 + 8];
+        s3lo = m.s3[u3]; o3lo = m.o3[u3]; s3hi = m.s3[u3 + 8]; o3hi = m.o3[u3 + 8];
     }
     uint8_t *ring = smem + L.ring;
     const uint32_t ring_addr = tc::smem_addr(ring);
@@ -854,6 +897,95 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 if ((lane & 1) == 0)
                     *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(c0 + e, unit, kDecHidden)) = mine | (other << 16);
             }
+        }
+    };
+
+    // Warp-level MMAs of the two wide layers (kDecSyncMma).  A fragment rows
+    // are units (W [unit][k]), B fragment columns are pixels (the activations
+    // [pixel][k]); K = 128 in eight steps of 16.  Shared-memory bandwidth is
+    // what these layers spend (every fragment is a shared-memory read), so
+    // layer 3's weights, 16 units per warp, stay in registers across waves,
+    // and layer 2 runs on warps 0..7 (units 16 w .. 16 w + 15), each taking
+    // pixel octets in pairs so that one weight fragment feeds two MMAs.
+    // Activation fragments come in by ldmatrix (two 8 x 8 matrices: the
+    // octet's 8 pixel rows, k 0..7 and 8..15 of the step).
+    uint16_t *act1 = reinterpret_cast<uint16_t *>(b23), *act2 = act1 + (size_t)NT * kActPitch;
+    auto ld32 = [](const uint16_t *p) { return *reinterpret_cast<const uint32_t *>(p); };
+    auto ldsm2 = [](const uint16_t *row, uint32_t &r0, uint32_t &r1) {
+        asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
+                     : "=r"(r0), "=r"(r1) : "r"(tc::smem_addr(row)));
+    };
+    const int mg = lane >> 2, mt4 = lane & 3;
+    // this lane's row address within an 8-row ldmatrix block: row lane % 8,
+    // k half (lane / 8) & 1
+    const int lrow = lane & 7, lk = 8 * ((lane >> 3) & 1);
+    uint32_t w3f[kDecHidden / 16][4];
+    if constexpr (!F32 && kDecSyncMma) {
+        const uint16_t *W = reinterpret_cast<const uint16_t *>(smem + L.w3) + (size_t)(16 * warp + mg) * kActPitch + 2 * mt4;
+#pragma unroll
+        for (int ks = 0; ks < kDecHidden / 16; ks++) {
+            w3f[ks][0] = ld32(W + 16 * ks);
+            w3f[ks][1] = ld32(W + 8 * kActPitch + 16 * ks);
+            w3f[ks][2] = ld32(W + 16 * ks + 8);
+            w3f[ks][3] = ld32(W + 8 * kActPitch + 16 * ks + 8);
+        }
+    }
+    auto mma_layer2 = [&](int NP) {
+        if (warp >= 8) return;
+        const uint16_t *W = reinterpret_cast<const uint16_t *>(smem + L.w2);
+        const int u = 16 * warp + mg;
+        const uint16_t *wa = W + (size_t)u * kActPitch + 2 * mt4;
+        for (int n0 = 0; n0 < NP / 8; n0 += 2) {
+            const uint16_t *xa = act1 + (size_t)(8 * n0 + lrow) * kActPitch + lk, *xb = xa + 8 * kActPitch;
+            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < kDecHidden / 16; ks++) {
+                const uint32_t a0 = ld32(wa + 16 * ks), a1 = ld32(wa + 8 * kActPitch + 16 * ks),
+                               a2 = ld32(wa + 16 * ks + 8), a3 = ld32(wa + 8 * kActPitch + 16 * ks + 8);
+                uint32_t b0, b1, b2, b3;
+                ldsm2(xa + 16 * ks, b0, b1);
+                ldsm2(xb + 16 * ks, b2, b3);
+                tc::mma_sync_bf16(c0, a0, a1, a2, a3, b0, b1);
+                tc::mma_sync_bf16(c1, a0, a1, a2, a3, b2, b3);
+            }
+            auto q = [](float acc, float s, float o) {
+                float h = rintf(__fmaf_rn(acc, s, o));
+                h = fminf(fmaxf(h, 0.0f), 255.0f);
+                return (uint16_t)(__float_as_uint(h) >> 16);   // bf16 of the integer
+            };
+            const int p = 8 * n0 + 2 * mt4;
+            act2[(size_t)p * kActPitch + u] = q(c0[0], s2lo, o2lo);
+            act2[(size_t)(p + 1) * kActPitch + u] = q(c0[1], s2lo, o2lo);
+            act2[(size_t)p * kActPitch + u + 8] = q(c0[2], s2hi, o2hi);
+            act2[(size_t)(p + 1) * kActPitch + u + 8] = q(c0[3], s2hi, o2hi);
+            act2[(size_t)(p + 8) * kActPitch + u] = q(c1[0], s2lo, o2lo);
+            act2[(size_t)(p + 9) * kActPitch + u] = q(c1[1], s2lo, o2lo);
+            act2[(size_t)(p + 8) * kActPitch + u + 8] = q(c1[2], s2hi, o2hi);
+            act2[(size_t)(p + 9) * kActPitch + u + 8] = q(c1[3], s2hi, o2hi);
+        }
+    };
+    auto mma_layer3 = [&](int NP) {
+        const int u = 16 * warp + mg;
+        for (int n0 = 0; n0 < NP / 8; n0 += 2) {   // NP is a multiple of 16: octets in pairs
+            const uint16_t *xa = act2 + (size_t)(8 * n0 + lrow) * kActPitch + lk, *xb = xa + 8 * kActPitch;
+            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < kDecHidden / 16; ks++) {
+                uint32_t b0, b1, b2, b3;
+                ldsm2(xa + 16 * ks, b0, b1);
+                ldsm2(xb + 16 * ks, b2, b3);
+                tc::mma_sync_bf16(c0, w3f[ks][0], w3f[ks][1], w3f[ks][2], w3f[ks][3], b0, b1);
+                tc::mma_sync_bf16(c1, w3f[ks][0], w3f[ks][1], w3f[ks][2], w3f[ks][3], b2, b3);
+            }
+            const int p = 8 * n0 + 2 * mt4;
+            zb[(size_t)p * kSymbols + u] = __fmaf_rn(c0[0], s3lo, o3lo);
+            zb[(size_t)(p + 1) * kSymbols + u] = __fmaf_rn(c0[1], s3lo, o3lo);
+            zb[(size_t)p * kSymbols + u + 8] = __fmaf_rn(c0[2], s3hi, o3hi);
+            zb[(size_t)(p + 1) * kSymbols + u + 8] = __fmaf_rn(c0[3], s3hi, o3hi);
+            zb[(size_t)(p + 8) * kSymbols + u] = __fmaf_rn(c1[0], s3lo, o3lo);
+            zb[(size_t)(p + 9) * kSymbols + u] = __fmaf_rn(c1[1], s3lo, o3lo);
+            zb[(size_t)(p + 8) * kSymbols + u + 8] = __fmaf_rn(c1[2], s3hi, o3hi);
+            zb[(size_t)(p + 9) * kSymbols + u + 8] = __fmaf_rn(c1[3], s3hi, o3hi);
         }
     };
 
@@ -1248,11 +1380,23 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
                         const uint32_t other = __shfl_xor_sync(0xffffffffu, mine[j], 1);
-                        if ((lane & 1) == 0)
-                            *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(p0 + 4 * j, unit, kDecHidden)) =
-                                mine[j] | (other << 16);
+                        if ((lane & 1) == 0) {
+                            if (kDecSyncMma)
+                                *reinterpret_cast<uint32_t *>(act1 + (size_t)(p0 + 4 * j) * kActPitch + unit) =
+                                    mine[j] | (other << 16);
+                            else
+                                *reinterpret_cast<uint32_t *>(b23 + tc::kmajor_offset(p0 + 4 * j, unit, kDecHidden)) =
+                                    mine[j] | (other << 16);
+                        }
                     }
                 }
+                if (kDecSyncMma) {
+                    __syncthreads();   // the first layer's outputs are in place
+                    mma_layer2(NP);
+                    __syncthreads();
+                    mma_layer3(NP);
+                    __syncthreads();   // the logits are in place
+                } else {
                 run_layer(2, NP);
                 hidden_epilogue(NP, s2r, o2r, true);
                 run_layer(3, NP);
@@ -1273,6 +1417,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 }
                 tc::fence_before_sync();
                 __syncthreads();
+                }
             }
             // 3. tables and rANS steps, one warp per pixel; pixels that share a
             //    stream go to the same warp (by local stream index), in row
@@ -1454,7 +1599,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     __syncthreads();
     if (tid == 0 && (s_err || s_fail))
         atomicMax(b.status + im.sidx, s_fail ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
-    if constexpr (!F32) {
+    if constexpr (!F32 && !kDecSyncMma) {
         if (warp == 0) {
             tc::fence_after_sync();
             tc::tmem_dealloc(tm, 256);

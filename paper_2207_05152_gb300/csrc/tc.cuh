@@ -133,6 +133,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Warp-level D += A B, m16n8k16, bf16 operands, FP32 accumulators.  With
+// g = lane / 4, t = lane % 4: a0 = A[g][2t, 2t + 1], a1 = A[g + 8][2t, ..],
+// a2 = A[g][2t + 8, ..], a3 = A[g + 8][2t + 8, ..]; b0 = B[2t, 2t + 1][g],
+// b1 = B[2t + 8, 2t + 9][g]; d = D[g][2t], D[g][2t + 1], D[g + 8][2t],
+// D[g + 8][2t + 1].  Each register holds two bf16, the lower index in the
+// low half.
+__device__ __forceinline__ void mma_sync_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                              uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 // bf16 bit pattern of a small non-negative or negative integer |v| <= 256
 // (exact: bf16 holds 8 significant bits).
 __host__ __device__ __forceinline__ uint16_t bf16_of_int(int v) {
