@@ -41,6 +41,9 @@ constexpr long long kDecWaitLimit = 4000000000LL;
 // that every fragment load is free of bank conflicts.
 constexpr bool kDecSyncMma = true;
 constexpr int kActPitch = kDecHidden + 8;
+// Row pitch (floats) of the INT8 decoder's logits: the layer-3 fragments'
+// stores (four pixels x eight units per instruction) fall in distinct banks.
+constexpr int kZPitch = kSymbols + 4;
 
 struct DecTcLayout {
     // INT8 network: bf16 operand tiles, s8 priors, bf16 activations
@@ -121,7 +124,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.pri = take((uint32_t)prm.k1 * nt);
         L.b23 = take(2u * nt * kDecHidden);
     }
-    if (!f32) L.z = take(4u * nt * kSymbols);
+    if (!f32) L.z = take(4u * nt * (kDecSyncMma ? kZPitch : kSymbols));
     L.ring = take(prm.gimg ? 0u : (uint32_t)prm.rcols * rows);
     L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * prm.list_rows);
@@ -978,14 +981,14 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 tc::mma_sync_bf16(c1, w3f[ks][0], w3f[ks][1], w3f[ks][2], w3f[ks][3], b2, b3);
             }
             const int p = 8 * n0 + 2 * mt4;
-            zb[(size_t)p * kSymbols + u] = __fmaf_rn(c0[0], s3lo, o3lo);
-            zb[(size_t)(p + 1) * kSymbols + u] = __fmaf_rn(c0[1], s3lo, o3lo);
-            zb[(size_t)p * kSymbols + u + 8] = __fmaf_rn(c0[2], s3hi, o3hi);
-            zb[(size_t)(p + 1) * kSymbols + u + 8] = __fmaf_rn(c0[3], s3hi, o3hi);
-            zb[(size_t)(p + 8) * kSymbols + u] = __fmaf_rn(c1[0], s3lo, o3lo);
-            zb[(size_t)(p + 9) * kSymbols + u] = __fmaf_rn(c1[1], s3lo, o3lo);
-            zb[(size_t)(p + 8) * kSymbols + u + 8] = __fmaf_rn(c1[2], s3hi, o3hi);
-            zb[(size_t)(p + 9) * kSymbols + u + 8] = __fmaf_rn(c1[3], s3hi, o3hi);
+            zb[(size_t)p * kZPitch + u] = __fmaf_rn(c0[0], s3lo, o3lo);
+            zb[(size_t)(p + 1) * kZPitch + u] = __fmaf_rn(c0[1], s3lo, o3lo);
+            zb[(size_t)p * kZPitch + u + 8] = __fmaf_rn(c0[2], s3hi, o3hi);
+            zb[(size_t)(p + 1) * kZPitch + u + 8] = __fmaf_rn(c0[3], s3hi, o3hi);
+            zb[(size_t)(p + 8) * kZPitch + u] = __fmaf_rn(c1[0], s3lo, o3lo);
+            zb[(size_t)(p + 9) * kZPitch + u] = __fmaf_rn(c1[1], s3lo, o3lo);
+            zb[(size_t)(p + 8) * kZPitch + u + 8] = __fmaf_rn(c1[2], s3hi, o3hi);
+            zb[(size_t)(p + 9) * kZPitch + u + 8] = __fmaf_rn(c1[3], s3hi, o3hi);
         }
     };
 
@@ -1283,6 +1286,23 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     pri[K1 * px + q] = (uint8_t)(v ^ 0x80u);
             }
             __syncthreads();   // every prior of the chunk is in place
+            // the stream state (and the next payload word) of this warp's
+            // first pixel, read now rather than on the table's dependency
+            // chain (one pixel per stream in the wave: only this warp updates
+            // that state before its table step)
+            uint32_t pf_x = 0, pf_pos = 0, pf_end = 0, pf_word = 0;
+            int pf_i = -1;
+            if (!F32 && !GRID && spread && warp < nc) {   // (the FP32 decoder measured no gain)
+                const int pg = pixg[warp];
+                if ((pg >> 24) == warp) {
+                    const int g = pg & 0xFFFFFF;
+                    pf_x = st_x[g];
+                    pf_pos = st_pos[g];
+                    pf_end = st_end[g];
+                    pf_word = pf_pos < pf_end ? wsrc[pf_pos] : 0u;
+                    pf_i = warp;
+                }
+            }
             if constexpr (F32) {
                 // 2. the FP32 network on the CUDA cores, fixed order per unit:
                 //    bias first, then fma(x_k, w_jk, acc) for k ascending.
@@ -1439,12 +1459,15 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     se = vi.end;
                     gs = g & 0xFFFF;
                 }
-                const uint32_t x = GRID ? __ldcg(sx + gs) : sx[gs];
+                const bool pre = i == pf_i;
+                const uint32_t x = pre ? pf_x : GRID ? __ldcg(sx + gs) : sx[gs];
                 // the stream's next word, fetched before it is known to be needed
-                const uint32_t pos = GRID ? __ldcg(sp + gs) : sp[gs], pend = GRID ? __ldcg(se + gs) : se[gs];
-                const uint32_t next_word = pos < pend ? wsrc[pos] : 0u;
-                const float4 za = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane);
-                const float4 zc = *reinterpret_cast<const float4 *>(zb + i * kSymbols + 8 * lane + 4);
+                const uint32_t pos = pre ? pf_pos : GRID ? __ldcg(sp + gs) : sp[gs];
+                const uint32_t pend = pre ? pf_end : GRID ? __ldcg(se + gs) : se[gs];
+                const uint32_t next_word = pre ? pf_word : pos < pend ? wsrc[pos] : 0u;
+                const int zp = F32 || !kDecSyncMma ? kSymbols : kZPitch;
+                const float4 za = *reinterpret_cast<const float4 *>(zb + i * zp + 8 * lane);
+                const float4 zc = *reinterpret_cast<const float4 *>(zb + i * zp + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
                 // the lane's maximum, then the warp's through an order-preserving
                 // integer key (a zero maximum's sign changes no weight)
