@@ -124,7 +124,9 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.pri = take((uint32_t)prm.k1 * nt);
         L.b23 = take(2u * nt * kDecHidden);
     }
-    if (!f32) L.z = take(4u * nt * (kDecSyncMma ? kZPitch : kSymbols));
+    // warp-level MMAs: the logits overlay the W3 rows, which are read into
+    // registers before the first wave (4 nt 260 <= 2 x 256 x 136 for nt <= 64)
+    if (!f32) L.z = kDecSyncMma ? L.w3 : take(4u * nt * kSymbols);
     L.ring = take(prm.gimg ? 0u : (uint32_t)prm.rcols * rows);
     L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * prm.list_rows);
@@ -1780,7 +1782,7 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, ui
     // the expanded power-of-two table (6 KB) only where it costs no chunk size
     prm.lut2 = 1;
     if (size() > limit) prm.lut2 = 0;
-    while (!f32 && size() > limit && prm.nt > 16) prm.nt /= 2;
+    while (!f32 && size() > limit && prm.nt > 16) prm.nt -= 16;   // (chunks stay multiples of 16)
     if (size() > limit) prm.tq = 0;
     // volumes read every prior back from the output volume
     if (size() > limit || plan == DLIC_PLAN_IMAGE || m.vol) {
@@ -1905,7 +1907,7 @@ static bool plan_grid(const DevModel &m, const DecBatch &b, int NB, uint32_t lim
     prm.list_rows = (per_cta + designated + 15) & ~15;
     prm.lut2 = 1;
     if (dec_layout(prm, f32).total > limit) prm.lut2 = 0;
-    while (!f32 && dec_layout(prm, f32).total > limit && prm.nt > 16) prm.nt /= 2;
+    while (!f32 && dec_layout(prm, f32).total > limit && prm.nt > 16) prm.nt -= 16;   // (multiples of 16)
     return dec_layout(prm, f32).total <= limit;
 }
 
