@@ -31,15 +31,19 @@ constexpr int kDecThreads = 512;
 constexpr int kDecWarps = kDecThreads / 32;
 constexpr int kDecHidden = 128;
 constexpr long long kDecWaitLimit = 4000000000LL;
-// The INT8 network's two wide layers (128 x 128 and 256 x 128 against at
-// most a chunk of pixels per wave) as warp-level bf16 MMAs (mma.sync
-// m16n8k16 with FP32 accumulation, exact for these integer-valued operands:
-// every partial sum is an integer below 2^23): a few tens of cycles per MMA
-// and the accumulators in registers, against a tcgen05 round trip (issue,
-// commit, mbarrier, tensor-memory load) of 0.7-1.0K cycles per layer.  The
-// operands sit row-major in shared memory with rows of kActPitch bf16, so
-// that every fragment load is free of bank conflicts.
-constexpr bool kDecSyncMma = true;
+// The INT8 network's two wide layers (128 x 128 and 256 x 128 against a
+// chunk of pixels per wave) run either as tcgen05 MMAs (weights = A, the
+// chunk's pixels = B, accumulators in tensor memory) or, for chunks of up to
+// kSmmaMaxChunk pixels, as warp-level bf16 MMAs (mma.sync m16n8k16 with FP32
+// accumulation, exact for these integer-valued operands: every partial sum
+// is an integer below 2^23): a few tens of cycles per MMA with the
+// accumulators in registers, against a tcgen05 round trip (issue, commit,
+// mbarrier, tensor-memory load) of 0.7-1.0K cycles per layer; past about 32
+// pixels the warp MMAs' rate (about 0.32 per cycle per SM) loses to the
+// tensor core.  The warp MMAs' operands sit row-major in shared memory with
+// rows of kActPitch bf16, so that every fragment load is free of bank
+// conflicts.
+constexpr int kSmmaMaxChunk = 32;
 constexpr int kActPitch = kDecHidden + 8;
 // Row pitch (floats) of the INT8 decoder's logits: the layer-3 fragments'
 // stores (four pixels x eight units per instruction) fall in distinct banks.
@@ -74,6 +78,7 @@ struct DecTcParams {
                       // for a batch, of the per-image stream count, flags and wave count)
     int T;            // grid decoder of a batch: waves of the longest image
     int lut2;         // 1: the table's powers of two expanded to kTableSteps entries
+    int smma;         // INT8: 1 = the wide layers as warp-level MMAs, 0 = tcgen05
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -111,7 +116,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.h1t = base + xs_bytes;
         L.z = base;
         L.h2t = take(4u * h2 * (nt + 4));
-    } else if (kDecSyncMma) {
+    } else if (prm.smma) {
         L.w1 = take((uint32_t)prm.k1 * kDecHidden);   // W1 as s8 words [k1 / 4][128] (the first layer runs as dp4a)
         L.w2 = take(2u * kDecHidden * kActPitch);     // W2 [unit][k], bf16
         L.w3 = take(2u * kSymbols * kActPitch);       // W3 [unit][k], bf16
@@ -126,7 +131,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
     }
     // warp-level MMAs: the logits overlay the W3 rows, which are read into
     // registers before the first wave (4 nt 260 <= 2 x 256 x 136 for nt <= 64)
-    if (!f32) L.z = kDecSyncMma ? L.w3 : take(4u * nt * kSymbols);
+    if (!f32) L.z = prm.smma ? L.w3 : take(4u * nt * kSymbols);
     L.ring = take(prm.gimg ? 0u : (uint32_t)prm.rcols * rows);
     L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * prm.list_rows);
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(kDecThreads) k_batch_finish(DecBatch b) {
 // decodes one volume with every CTA of a cooperative grid (no cluster):
 // each wave's pixels are split evenly over the CTAs, stream states live in
 // the workspace and the waves are separated by a grid-wide barrier.
-template <bool F32, bool DEF, bool GRID>
+template <bool F32, bool DEF, bool GRID, bool SMMA>
 __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b, const DecTcParams &prm) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
@@ -529,7 +534,10 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     const uint8_t *in = b.in + im.in_off;
     const int H = im.H, W = im.W;
     const int h1 = prm.h1, h2 = prm.h2;
-    const DecTcLayout L = dec_layout(prm, F32);
+    // (the layout with this instance's MMA kind as a constant)
+    DecTcParams pl = prm;
+    pl.smma = SMMA ? 1 : 0;
+    const DecTcLayout L = dec_layout(pl, F32);
     const int K1 = DEF ? 16 : prm.k1, NPRI = DEF ? kPriors : m.n_in;
     const int TSLOTS = DEF ? 3 : prm.tslots, TCOLS = DEF ? 32 : prm.tcols, RCOLS = DEF ? 16 : prm.rcols;
 
@@ -543,7 +551,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             for (int i = tid; i < kSymbols; i += kDecThreads) wf[NPRI * h1 + h1 + h2 + i] = m.b3[i];
             for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
                 reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
-        } else if (kDecSyncMma) {
+        } else if (SMMA) {
             // W2, W3 as bf16 rows [unit][k] from the packed s8 words [k / 4][unit]
             auto unpack = [&](const uint32_t *q, int units, uint16_t *dst) {
                 for (int i = tid; i < (kDecHidden / 4) * units; i += kDecThreads) {
@@ -589,7 +597,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         uint32_t *tring = reinterpret_cast<uint32_t *>(smem + L.tring);
         for (int i = tid; i < prm.tq * prm.tslots * prm.tcols; i += kDecThreads) tring[i] = 0u;
     }
-    if constexpr (!F32 && !kDecSyncMma) {
+    if constexpr (!F32 && !SMMA) {
         if (warp == 0) {
             tc::tmem_alloc(&tmem_base, 256);
             tc::tmem_relinquish();
@@ -597,7 +605,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     }
     if (tid == 0) {
         if constexpr (!F32) {
-            if (!kDecSyncMma) tc::mbar_init(&bar, 1);
+            if (!SMMA) tc::mbar_init(&bar, 1);
         } else {
             for (int q = 0; q < kW3Stages; q++) tc::mbar_init(&w3bar[q], 1);
         }
@@ -752,7 +760,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // Every CTA of the cluster reads the same header, so this exit is uniform.
     if (!s_ok) {
         if (tid == 0 && k == 0) atomicMax(b.status + im.sidx, (int)DLIC_ERR_CORRUPT);
-        if constexpr (!F32 && !kDecSyncMma) {
+        if constexpr (!F32 && !SMMA) {
             if (warp == 0) tc::tmem_dealloc(tmem_base, 256);
         }
         return;
@@ -905,7 +913,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
         }
     };
 
-    // Warp-level MMAs of the two wide layers (kDecSyncMma).  A fragment rows
+    // Warp-level MMAs of the two wide layers (SMMA).  A fragment rows
     // are units (W [unit][k]), B fragment columns are pixels (the activations
     // [pixel][k]); K = 128 in eight steps of 16.  Shared-memory bandwidth is
     // what these layers spend (every fragment is a shared-memory read), so
@@ -925,7 +933,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // k half (lane / 8) & 1
     const int lrow = lane & 7, lk = 8 * ((lane >> 3) & 1);
     uint32_t w3f[kDecHidden / 16][4];
-    if constexpr (!F32 && kDecSyncMma) {
+    if constexpr (!F32 && SMMA) {
         const uint16_t *W = reinterpret_cast<const uint16_t *>(smem + L.w3) + (size_t)(16 * warp + mg) * kActPitch + 2 * mt4;
 #pragma unroll
         for (int ks = 0; ks < kDecHidden / 16; ks++) {
@@ -1403,7 +1411,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                     for (int j = 0; j < 4; j++) {
                         const uint32_t other = __shfl_xor_sync(0xffffffffu, mine[j], 1);
                         if ((lane & 1) == 0) {
-                            if (kDecSyncMma)
+                            if (SMMA)
                                 *reinterpret_cast<uint32_t *>(act1 + (size_t)(p0 + 4 * j) * kActPitch + unit) =
                                     mine[j] | (other << 16);
                             else
@@ -1412,7 +1420,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         }
                     }
                 }
-                if (kDecSyncMma) {
+                if (SMMA) {
                     __syncthreads();   // the first layer's outputs are in place
                     mma_layer2(NP);
                     __syncthreads();
@@ -1467,7 +1475,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                 const uint32_t pos = pre ? pf_pos : GRID ? __ldcg(sp + gs) : sp[gs];
                 const uint32_t pend = pre ? pf_end : GRID ? __ldcg(se + gs) : se[gs];
                 const uint32_t next_word = pre ? pf_word : pos < pend ? wsrc[pos] : 0u;
-                const int zp = F32 || !kDecSyncMma ? kSymbols : kZPitch;
+                const int zp = F32 || !SMMA ? kSymbols : kZPitch;
                 const float4 za = *reinterpret_cast<const float4 *>(zb + i * zp + 8 * lane);
                 const float4 zc = *reinterpret_cast<const float4 *>(zb + i * zp + 8 * lane + 4);
                 const float z[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
@@ -1624,7 +1632,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     __syncthreads();
     if (tid == 0 && (s_err || s_fail))
         atomicMax(b.status + im.sidx, s_fail ? (int)DLIC_ERR_TIMEOUT : (int)DLIC_ERR_CORRUPT);
-    if constexpr (!F32 && !kDecSyncMma) {
+    if constexpr (!F32 && !SMMA) {
         if (warp == 0) {
             tc::fence_after_sync();
             tc::tmem_dealloc(tm, 256);
@@ -1633,21 +1641,28 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     if (P > 1) cluster_sync_all();   // no CTA leaves while others may still write its ring
 }
 
-template <bool DEF>
+template <bool DEF, bool SMMA>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<false, DEF, false>(m, b, prm);
+    decode_wave<false, DEF, false, SMMA>(m, b, prm);
 }
 template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<true, DEF, false>(m, b, prm);
+    decode_wave<true, DEF, false, false>(m, b, prm);
 }
 // one volume over a cooperative grid
+template <bool SMMA>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_grid_tc(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<false, false, true>(m, b, prm);
+    decode_wave<false, false, true, SMMA>(m, b, prm);
 }
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_grid_f32(DevModel m, DecBatch b, DecTcParams prm) {
-    decode_wave<true, false, true>(m, b, prm);
+    decode_wave<true, false, true, false>(m, b, prm);
 }
+
+// Chunks of up to kSmmaMaxChunk pixels take the warp-level MMAs (INT8).
+static inline bool smma_chunk(const DevModel &m, int per_cta) {
+    return m.precision == DLIC_INT8 && min(64, (per_cta + 15) & ~15) <= kSmmaMaxChunk;
+}
+static inline int wave_per_cta(int maxH, int maxW, int P) { return (min(maxH, (maxW + 2) / 3) + P - 1) / P + 1; }
 
 // Cluster sizes for a batch (the decode autotuner).  A wave of an image
 // whose CTAs hold p pixels costs about kWaveFixed cycles (gather, MMA round
@@ -1712,11 +1727,12 @@ bool wave_decode_supported(const DevModel &m) {
            m.h2 % 4 == 0;
 }
 
-static void (*wave_kernel(const DevModel &m))(DevModel, DecBatch, DecTcParams) {
+static void (*wave_kernel(const DevModel &m, bool smma))(DevModel, DecBatch, DecTcParams) {
     // the default window runs the instance with its sizes as constants
     const bool def = default_window(m);
     if (m.precision == DLIC_FP32) return def ? k_decode_f32<true> : k_decode_f32<false>;
-    return def ? k_decode_tc<true> : k_decode_tc<false>;
+    if (smma) return def ? k_decode_tc<true, true> : k_decode_tc<false, true>;
+    return def ? k_decode_tc<true, false> : k_decode_tc<false, false>;
 }
 
 // Dynamic shared memory a CTA of the kernel may take next to its static arrays.
@@ -1746,6 +1762,7 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, ui
     prm.h1 = m.h1;
     prm.h2 = m.h2;
     prm.nt = f32 ? 12 : min(64, (per_cta + 15) & ~15);
+    prm.smma = smma_chunk(m, per_cta) ? 1 : 0;
     prm.k1 = (m.n_in + 15) / 16 * 16;
     prm.tslots = m.wu + 1;
     // ring columns kept per row: an entry must outlive its last reader,
@@ -1802,7 +1819,8 @@ bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan) {
     if (m.precision == DLIC_FP32 && default_window(m)) return true;   // the one-CTA decoder takes the rest
     uint32_t limit = 0;
     DecTcParams prm;
-    return smem_limit(wave_kernel(m), limit) == cudaSuccess && plan_wave(m, H, W, D, P, limit, plan, prm);
+    return smem_limit(wave_kernel(m, smma_chunk(m, wave_per_cta(H, W, P))), limit) == cudaSuccess &&
+           plan_wave(m, H, W, D, P, limit, plan, prm);
 }
 
 // Launches one cluster of `cluster` CTAs per image of the batch (stepping
@@ -1810,7 +1828,6 @@ bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan) {
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan,
                              cudaStream_t st) {
     const bool f32 = m.precision == DLIC_FP32;
-    void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m);
     if (b.n == 0) return cudaSuccess;
     int maxH = 1, maxW = 1, maxD = 1;
     for (int i = 0; i < b.n; i++) {
@@ -1819,6 +1836,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         maxD = max(maxD, b.img[i].D);
     }
     int P = cluster > 0 ? cluster : 1;
+    void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m, smma_chunk(m, wave_per_cta(maxH, maxW, P)));
     uint32_t limit = 0;
     cudaError_t e = smem_limit(kern, limit);
     if (e != cudaSuccess) return e;
@@ -1904,6 +1922,7 @@ static bool plan_grid(const DevModel &m, const DecBatch &b, int NB, uint32_t lim
     }
     const int per_cta = (int)((wave + NB - 1) / NB);
     prm.nt = f32 ? 12 : min(64, max(16, (per_cta + 15) & ~15));
+    prm.smma = smma_chunk(m, per_cta) ? 1 : 0;
     prm.list_rows = (per_cta + designated + 15) & ~15;
     prm.lut2 = 1;
     if (dec_layout(prm, f32).total > limit) prm.lut2 = 0;
@@ -1911,25 +1930,27 @@ static bool plan_grid(const DevModel &m, const DecBatch &b, int NB, uint32_t lim
     return dec_layout(prm, f32).total <= limit;
 }
 
-static void (*grid_kernel(const DevModel &m))(DevModel, DecBatch, DecTcParams) {
-    return m.precision == DLIC_FP32 ? k_decode_grid_f32 : k_decode_grid_tc;
+// (both INT8 instances have the same static shared memory, so the plan is
+// made against either's limit and then picks the instance)
+static void (*grid_kernel(const DevModel &m, bool smma))(DevModel, DecBatch, DecTcParams) {
+    return m.precision == DLIC_FP32 ? k_decode_grid_f32 : smma ? k_decode_grid_tc<true> : k_decode_grid_tc<false>;
 }
 
 bool grid_decode_fits(const DevModel &m, const DecBatch &b, int num_sms) {
     uint32_t limit = 0;
     DecTcParams prm;
-    return wave_decode_supported(m) && smem_limit(grid_kernel(m), limit) == cudaSuccess &&
+    return wave_decode_supported(m) && smem_limit(grid_kernel(m, true), limit) == cudaSuccess &&
            plan_grid(m, b, num_sms, limit, prm);
 }
 
 cudaError_t launch_decode_grid(const DevModel &m, const DecBatch &b, int num_sms, cudaStream_t st) {
-    void (*kern)(DevModel, DecBatch, DecTcParams) = grid_kernel(m);
     uint32_t limit = 0;
-    cudaError_t e = smem_limit(kern, limit);
+    cudaError_t e = smem_limit(grid_kernel(m, true), limit);
     if (e != cudaSuccess) return e;
     const int NB = num_sms;
     DecTcParams prm;
     if (!plan_grid(m, b, NB, limit, prm)) return cudaErrorNotSupported;
+    void (*kern)(DevModel, DecBatch, DecTcParams) = grid_kernel(m, prm.smma != 0);
     const DecTcLayout L = dec_layout(prm, m.precision == DLIC_FP32);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
