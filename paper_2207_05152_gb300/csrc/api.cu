@@ -851,6 +851,8 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
                 break;
             }
     const bool fork = groups_used > 1;
+    int cluster_ctas = 0;   // CTAs of every cluster of the call
+    for (int i = 0; i < n; i++) cluster_ctas += P[i];
     if (fork) {
         cudaError_t e = cudaEventRecord(m->fork_event, cs);
         if (e != cudaSuccess) return cuda_fail(e, "fork event");
@@ -884,7 +886,8 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
             b->ws = static_cast<uint8_t *>(d_ws);
             b->status = d_status;
             for (int k = 0; k < cn; k++) fill(b->img[k], members[c0 + k]);
-            cudaError_t e = use_wave              ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs)
+            cudaError_t e = use_wave              ? launch_decode_tc(m->dev, *b, cluster, m->num_sms, m->decode_plan, gs,
+                                                                  2 * cluster_ctas <= m->num_sms)
                             : m->dev.bits == 12 ? launch_decode12(m->dev, *b, gs)
                             : wide_supported(m->dev) ? launch_decode_wide(m->dev, m->hl, *b, wide_scratch, gs)
                                                 : launch_decode_cc(m->dev, *b, gs);

@@ -1753,7 +1753,7 @@ static cudaError_t smem_limit(void (*kern)(DevModel, DecBatch, DecTcParams), uin
 // smaller pixel chunks; the byte ring with one cluster barrier per wave;
 // priors read back from the output image.  False when none fits.
 static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, uint32_t limit, int plan,
-                      DecTcParams &prm) {
+                      DecTcParams &prm, bool smma_ok = true) {
     const bool f32 = m.precision == DLIC_FP32;
     const int wave_px = min(maxH, (maxW + 2) / 3);   // rows of the longest wave (per slice)
     const int per_cta = (wave_px + P - 1) / P + 1;
@@ -1762,7 +1762,7 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, ui
     prm.h1 = m.h1;
     prm.h2 = m.h2;
     prm.nt = f32 ? 12 : min(64, (per_cta + 15) & ~15);
-    prm.smma = smma_chunk(m, per_cta) ? 1 : 0;
+    prm.smma = smma_ok && smma_chunk(m, per_cta) ? 1 : 0;
     prm.k1 = (m.n_in + 15) / 16 * 16;
     prm.tslots = m.wu + 1;
     // ring columns kept per row: an entry must outlive its last reader,
@@ -1819,14 +1819,14 @@ bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan) {
     if (m.precision == DLIC_FP32 && default_window(m)) return true;   // the one-CTA decoder takes the rest
     uint32_t limit = 0;
     DecTcParams prm;
-    return smem_limit(wave_kernel(m, smma_chunk(m, wave_per_cta(H, W, P))), limit) == cudaSuccess &&
-           plan_wave(m, H, W, D, P, limit, plan, prm);
+    // (the tcgen05 layout is the larger one, so it decides for both instances)
+    return smem_limit(wave_kernel(m, false), limit) == cudaSuccess && plan_wave(m, H, W, D, P, limit, plan, prm, false);
 }
 
 // Launches one cluster of `cluster` CTAs per image of the batch (stepping
 // down when a cluster that large cannot be scheduled).
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool latency) {
     const bool f32 = m.precision == DLIC_FP32;
     if (b.n == 0) return cudaSuccess;
     int maxH = 1, maxW = 1, maxD = 1;
@@ -1836,12 +1836,16 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
         maxD = max(maxD, b.img[i].D);
     }
     int P = cluster > 0 ? cluster : 1;
-    void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m, smma_chunk(m, wave_per_cta(maxH, maxW, P)));
+    // Warp-level MMAs when the call's clusters leave most SMs idle (a wave's
+    // latency decides); when they fill the GPU, every SM's throughput does
+    // and the tensor core's MMAs win at any chunk size.
+    const bool smma = latency && smma_chunk(m, wave_per_cta(maxH, maxW, P));
+    void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m, smma);
     uint32_t limit = 0;
     cudaError_t e = smem_limit(kern, limit);
     if (e != cudaSuccess) return e;
     DecTcParams prm;
-    if (!plan_wave(m, maxH, maxW, maxD, P, limit, plan, prm))
+    if (!plan_wave(m, maxH, maxW, maxD, P, limit, plan, prm, smma))
         return f32 && default_window(m) ? launch_decode_cc(m, b, st) : cudaErrorNotSupported;
     const DecTcLayout L = dec_layout(prm, f32);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
@@ -1871,7 +1875,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     }
     if (P != prm.P) {
         // smaller clusters hold more streams and pixels per CTA
-        return launch_decode_tc(m, b, P, num_sms, plan, st);
+        return launch_decode_tc(m, b, P, num_sms, plan, st, latency);
     }
     return cudaLaunchKernelEx(&cfg, kern, m, b, prm);
 }

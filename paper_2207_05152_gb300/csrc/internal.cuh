@@ -171,7 +171,9 @@ cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecB
 // the grid decoder's stream-state set-up and final check (decode_tc.cu)
 cudaError_t launch_batch_setup(const DevModel &m, const DecBatch &b, cudaStream_t st);
 cudaError_t launch_batch_finish(const DecBatch &b, cudaStream_t st);
-cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st);
+// latency: the call's clusters leave most SMs idle (warp-level MMAs for small chunks)
+cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st,
+                             bool latency);
 bool wave_decode_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)
 bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan);
