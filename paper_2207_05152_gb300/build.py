@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")] + ARCH
 # translation units whose arithmetic must stay exactly as written
-EXACT = {"coder_cc.cu", "coder_tc.cu", "decode_tc.cu", "coder12.cu", "wide.cu"}
+EXACT = {"coder_cc.cu", "coder_tc.cu", "decode_tc.cu", "coder12.cu", "wide.cu", "wide_tc.cu"}
 
 
 def sources():

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace dlic {
 
@@ -213,6 +214,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
     const int kTcImage = 3 * kMaxLayers;
     const size_t off_table = deep ? put(std::vector<DevLayer>(nl).data(), sizeof(DevLayer) * nl) : 0;
     size_t off_w3tiles = 0;   // 12-bit: the output layer tiled for the decoder
+    size_t off_wtc[kMaxLayers] = {0};   // wide INT8: bf16 weight rows of the tensor-core layers
+    int wtc_pitch[kMaxLayers] = {0};
     const uint8_t *p = b + hdr;
     if (prec == DLIC_FP32) {
         for (int l = 0; l < nl; l++) {
@@ -268,6 +271,18 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             offs[3 * l + 1] = put(s.data(), s.size() * 4);
             offs[3 * l + 2] = put(o.data(), o.size() * 4);
         }
+        // a wide network's layers after the first (inputs: u8 units) also as
+        // bf16 rows [n_out][K padded to 64] for the tensor-core encoder; the
+        // integer weights are exact in bf16
+        if (wide)
+            for (int l = 1; l < nl; l++) {
+                const int kp = (din[l] + 63) / 64 * 64;
+                std::vector<uint16_t> wb((size_t)dout[l] * kp, 0);
+                for (int j = 0; j < dout[l]; j++)
+                    for (int k = 0; k < din[l]; k++) wb[(size_t)j * kp + k] = tc::bf16_of_int(raw[l][(size_t)j * din[l] + k]);
+                off_wtc[l] = put(wb.data(), wb.size() * 2);
+                wtc_pitch[l] = kp;
+            }
     }
     host.resize(align256(host.size()));
     dlic_model *m = new dlic_model();
@@ -289,6 +304,8 @@ extern "C" dlic_status dlic_model_create(const void *h_blob, size_t n, dlic_mode
             table[l].o = prec == DLIC_INT8 ? reinterpret_cast<const float *>(base + offs[3 * l + 2]) : nullptr;
             table[l].n_in = din[l];
             table[l].n_out = dout[l];
+            table[l].wtc = wtc_pitch[l] ? reinterpret_cast<const uint16_t *>(base + off_wtc[l]) : nullptr;
+            table[l].wtc_pitch = wtc_pitch[l];
         }
         memcpy(host.data() + off_table, table.data(), sizeof(DevLayer) * nl);
         d.layers = reinterpret_cast<const DevLayer *>(base + off_table);
@@ -453,7 +470,7 @@ extern "C" dlic_status dlic_encode_workspace_size(const dlic_model *m, const dli
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, streams, false, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
-    *bytes = enc_ws_bytes(image_items(im, n, streams)) + wide_scratch_bytes(m->dev);
+    *bytes = enc_ws_bytes(image_items(im, n, streams)) + wide_scratch_bytes(m->dev, true);
     return DLIC_OK;
 }
 
@@ -466,7 +483,7 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
     if (!d_out || !d_out_offsets || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
     if (reinterpret_cast<uintptr_t>(d_ws) & 255) return fail(DLIC_ERR_INVALID, "workspace must be 256-byte aligned");
     size_t need_out = 0;
-    const size_t need_ws = enc_ws_bytes(it) + wide_scratch_bytes(m->dev);
+    const size_t need_ws = enc_ws_bytes(it) + wide_scratch_bytes(m->dev, true);
     for (const EncItem &e : it) need_out += dlic_max_encoded_bytes(e.H, e.W, e.S);
     if (ws_bytes < need_ws) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need_ws);
     if (out_capacity < need_out) return fail(DLIC_ERR_CAPACITY, "output capacity %zu < %zu bytes", out_capacity, need_out);
@@ -520,7 +537,7 @@ static dlic_status encode_items(const dlic_model *m, const std::vector<EncItem> 
         b->total_tiles = tiles;
         cudaError_t e = use_tc                       ? launch_predict_tc(m->dev, *b, err, m->num_sms, cs)
                         : m->dev.bits == 12          ? launch_predict12(m->dev, *b, err, cs)
-                        : wide_supported(m->dev) ? launch_predict_wide(m->dev, m->hl, *b, ws + enc_ws_bytes(it), cs)
+                        : wide_supported(m->dev) ? launch_predict_wide(m->dev, m->hl, *b, ws + enc_ws_bytes(it), err, cs)
                                                      : launch_predict_cc(m->dev, *b, cs);
         if (e == cudaSuccess) e = launch_rans_encode(*b, total_streams, cs);
         if (e == cudaSuccess) e = launch_pack(m->dev, *b, out, d_out_offsets + c0, cs);
@@ -703,7 +720,7 @@ extern "C" dlic_status dlic_decode_workspace_size(const dlic_model *m, const dli
     if (!m || !bytes) return fail(DLIC_ERR_INVALID, "null argument");
     dlic_status st = check_images(im, n, nullptr, true, m->dev.bits == 12 ? 2 : 1);
     if (st) return st;
-    *bytes = dec_ws_bytes(dec_image_items(im, n)) + wide_scratch_bytes(m->dev);
+    *bytes = dec_ws_bytes(dec_image_items(im, n)) + wide_scratch_bytes(m->dev, false);
     return DLIC_OK;
 }
 
@@ -724,7 +741,7 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
     const int n = (int)it.size();
     if (n == 0) return DLIC_OK;
     if (!d_in || !h_in_offsets || !d_status || !d_ws) return fail(DLIC_ERR_INVALID, "null buffer");
-    const size_t need = dec_ws_bytes(it) + wide_scratch_bytes(m->dev);
+    const size_t need = dec_ws_bytes(it) + wide_scratch_bytes(m->dev, false);
     if (ws_bytes < need) return fail(DLIC_ERR_CAPACITY, "workspace %zu < %zu bytes", ws_bytes, need);
     // networks wider than 256: the layers' scratch after the stream states
     uint8_t *wide_scratch = static_cast<uint8_t *>(d_ws) + dec_ws_bytes(it);

@@ -27,6 +27,10 @@ struct DevLayer {
     const void *w;
     const float *a, *o;
     int32_t n_in, n_out;
+    // wide INT8 networks, layers after the first: the weights as bf16
+    // [n_out][wtc_pitch] for the tensor-core encoder (wide_tc.cu), else null
+    const uint16_t *wtc;
+    int32_t wtc_pitch;
 };
 constexpr int kMaxLayers = 9;     // deeper networks: up to 8 hidden layers and the output layer
 
@@ -161,11 +165,16 @@ cudaError_t launch_predict12(const DevModel &m, const EncBatch &b, int *err, cud
 cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t st);
 // Networks with hidden layers wider than 256 (wide.cu): one layer at a time
 // over sets of pixels, activations in a workspace scratch of
-// wide_scratch_bytes; hl is the host copy of the layer table
+// wide_scratch_bytes (encode: INT8 activations as the tensor-core layers'
+// bf16 planes); hl is the host copy of the layer table
 bool wide_supported(const DevModel &m);
-size_t wide_scratch_bytes(const DevModel &m);
+size_t wide_scratch_bytes(const DevModel &m, bool encode);
 cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch,
-                                cudaStream_t st);
+                                int *err, cudaStream_t st);
+// one INT8 layer of a wide network's encode pass on the tensor cores
+// (wide_tc.cu): X as bf16 hi / lo planes [np][ldx], plane_in elements apart
+cudaError_t launch_wide_tc(const DevLayer &ly, const uint16_t *X, int ldx, size_t plane_in, int np, void *Y,
+                           int ldy, size_t plane_out, bool logits, int *err, cudaStream_t st);
 cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecBatch &b, uint8_t *scratch,
                                cudaStream_t st);
 // the grid decoder's stream-state set-up and final check (decode_tc.cu)

@@ -130,10 +130,13 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_f32(const float *X, int l
 // One INT8 dense layer: acc_j = sum_k x_k q_jk exactly (dp4a over the packed
 // weights Q[k4][j]; signed inputs for the first layer, u8 units after), then
 // the requantised u8 unit (hidden) or the logit fma(acc, s, o) (output, FP32
-// into Y).  X and hidden Y are bytes [np][ld], ld a multiple of 4.
+// into Y).  X and hidden Y are bytes [np][ld], ld a multiple of 4; with
+// plane > 0 a hidden unit u goes out as the tensor-core layers' input
+// planes instead: bf16(u >> 4) at Y[p][j] and bf16(u & 15) plane elements
+// further (Y as uint16 [np][ldy]).
 __global__ void __launch_bounds__(kWideThreads) k_wide_i8(const uint8_t *X, int ldx, int K4, const uint32_t *Q,
                                                           const float *s, const float *o, int N, void *Y, int ldy,
-                                                          int np, int first, int logits) {
+                                                          int np, int first, int logits, size_t plane) {
     __shared__ uint32_t xs[kWideKC][kWideTileP + 4];
     __shared__ __align__(16) uint32_t ws[kWideKC][kWideTileU];
     const int tid = threadIdx.x, tc = tid % 16, tr = tid / 16;
@@ -180,6 +183,17 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_i8(const uint8_t *X, int 
 #pragma unroll
             for (int u = 0; u < 4; u++) z[u] = __fmaf_rn(__int2float_rn(acc[p][u]), sj[u], oj[u]);
             *reinterpret_cast<float4 *>(static_cast<float *>(Y) + (size_t)pp * ldy + j) = make_float4(z[0], z[1], z[2], z[3]);
+        } else if (plane) {
+            uint32_t hi[2] = {0u, 0u}, lo[2] = {0u, 0u};
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const uint32_t v = requant_u8(acc[p][u], sj[u], oj[u]);
+                hi[u >> 1] |= (uint32_t)(__float_as_uint((float)(v >> 4)) >> 16) << (16 * (u & 1));
+                lo[u >> 1] |= (uint32_t)(__float_as_uint((float)(v & 15u)) >> 16) << (16 * (u & 1));
+            }
+            uint16_t *yh = static_cast<uint16_t *>(Y) + (size_t)pp * ldy + j;
+            *reinterpret_cast<uint2 *>(yh) = make_uint2(hi[0], hi[1]);
+            *reinterpret_cast<uint2 *>(yh + plane) = make_uint2(lo[0], lo[1]);
         } else {
             uint32_t packed = 0;
 #pragma unroll
@@ -326,16 +340,24 @@ bool wide_supported(const DevModel &m) { return m.bits == 8 && m.hmax > kMaxHidd
 namespace {
 
 // The scratch of one pass (kWideChunk pixels): two activation buffers of
-// hmax units, the logits Z [pixel][256] (FP32) and the inputs X.
+// hmax units, the logits Z [pixel][256] (FP32) and the inputs X.  With
+// planes (the INT8 encoder) an activation buffer holds the two bf16 planes
+// [kWideChunk][hpad] of the tensor-core layers' inputs, plane elements apart.
 struct WideScratch {
     uint8_t *A, *B, *X;
     float *Z;
     size_t bytes;
+    int hpad;
+    size_t plane;
 };
-WideScratch wide_scratch(const DevModel &m, uint8_t *base) {
+WideScratch wide_scratch(const DevModel &m, uint8_t *base, bool planes) {
     auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t act = a256((size_t)kWideChunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
+    const int hpad = (m.hmax + 63) / 64 * 64;
+    const size_t act = planes ? a256((size_t)kWideChunk * hpad * 4)
+                              : a256((size_t)kWideChunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
     WideScratch w;
+    w.hpad = hpad;
+    w.plane = (size_t)kWideChunk * hpad;
     w.A = base;
     w.B = base + act;
     w.Z = reinterpret_cast<float *>(base + 2 * act);
@@ -345,12 +367,30 @@ WideScratch wide_scratch(const DevModel &m, uint8_t *base) {
 }
 
 // Inputs and every layer of the network over one set (np <= kWideChunk);
-// the logits land in Z.
-cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q, uint8_t *scratch, cudaStream_t st) {
-    const WideScratch w = wide_scratch(m, scratch);
+// the logits land in Z.  tc (INT8, encode): the layers after the first on
+// the tensor cores (wide_tc.cu), their inputs as bf16 planes.
+cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q, uint8_t *scratch, bool tc,
+                         int *err, cudaStream_t st) {
+    const WideScratch w = wide_scratch(m, scratch, tc);
     uint8_t *A = w.A, *B = w.B, *X = w.X;
     float *Z = w.Z;
     k_wide_inputs<<<(q.np * kPriors + 255) / 256, 256, 0, st>>>(q, m.precision, X);
+    if (tc) {
+        // the first layer (signed priors, K = 12) by dp4a into A's planes,
+        // then every later layer on the tensor cores, A and B in turn
+        const DevLayer &l0 = hl[0];
+        const dim3 grid((q.np + kWideTileP - 1) / kWideTileP, (l0.n_out + kWideTileU - 1) / kWideTileU);
+        k_wide_i8<<<grid, kWideThreads, 0, st>>>(X, kPriors, (l0.n_in + 3) / 4, static_cast<const uint32_t *>(l0.w),
+                                                 l0.a, l0.o, l0.n_out, A, w.hpad, q.np, 1, 0, w.plane);
+        cudaError_t e = cudaGetLastError();
+        for (int l = 1; l < m.nl && e == cudaSuccess; l++) {
+            const bool last = l == m.nl - 1;
+            const uint16_t *in = reinterpret_cast<const uint16_t *>(l & 1 ? A : B);
+            void *out = last ? static_cast<void *>(Z) : static_cast<void *>(l & 1 ? B : A);
+            e = launch_wide_tc(hl[l], in, w.hpad, w.plane, q.np, out, last ? kSymbols : w.hpad, w.plane, last, err, st);
+        }
+        return e;
+    }
     const uint8_t *in = X;
     int ldin = kPriors;
     for (int l = 0; l < m.nl; l++) {
@@ -364,7 +404,7 @@ cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q
                                                       reinterpret_cast<float *>(out), ly.n_out, q.np, !last);
         else
             k_wide_i8<<<grid, kWideThreads, 0, st>>>(in, ldin, (ly.n_in + 3) / 4, static_cast<const uint32_t *>(ly.w),
-                                                     ly.a, ly.o, ly.n_out, out, ly.n_out, q.np, l == 0, last);
+                                                     ly.a, ly.o, ly.n_out, out, ly.n_out, q.np, l == 0, last, 0);
         in = out;
         ldin = ly.n_out;
     }
@@ -373,19 +413,31 @@ cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q
 
 }  // namespace
 
-size_t wide_scratch_bytes(const DevModel &m) { return wide_supported(m) ? wide_scratch(m, nullptr).bytes : 0; }
+// whether the encoder runs the layers after the first on the tensor cores
+static bool wide_tc_encode(const DevModel &m, const DevLayer *hl) {
+    if (m.precision != DLIC_INT8) return false;
+    for (int l = 1; l < m.nl; l++)
+        if (!hl || !hl[l].wtc) return false;
+    return true;
+}
 
-cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch,
+size_t wide_scratch_bytes(const DevModel &m, bool encode) {
+    return wide_supported(m) ? wide_scratch(m, nullptr, encode && m.precision == DLIC_INT8).bytes : 0;
+}
+
+cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch, int *err,
                                 cudaStream_t st) {
+    // (the workspace holds the planes whenever the network is INT8)
+    const bool tc = wide_tc_encode(m, hl);
     for (int k = 0; k < b.n; k++) {
         const EncImage &im = b.img[k];
         const int64_t N = (int64_t)im.H * im.W;
         uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
         for (int64_t p0 = 0; p0 < N; p0 += kWideChunk) {
             const WideSet q{im.pixels, im.pitch, im.H, im.W, 0, p0, 0, 0, (int)std::min<int64_t>(kWideChunk, N - p0)};
-            cudaError_t e = wide_network(m, hl, q, scratch, st);
+            cudaError_t e = wide_network(m, hl, q, scratch, tc, err, st);
             if (e != cudaSuccess) return e;
-            k_wide_table_enc<<<(q.np + 7) / 8, kWideThreads, 0, st>>>(m, q, wide_scratch(m, scratch).Z, fc, im.S,
+            k_wide_table_enc<<<(q.np + 7) / 8, kWideThreads, 0, st>>>(m, q, wide_scratch(m, scratch, tc).Z, fc, im.S,
                                                                        b.raster);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
@@ -398,7 +450,7 @@ cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecB
                                cudaStream_t st) {
     cudaError_t e = launch_batch_setup(m, b, st);
     if (e != cudaSuccess) return e;
-    const float *Z = wide_scratch(m, scratch).Z;
+    const float *Z = wide_scratch(m, scratch, false).Z;
     for (int k = 0; k < b.n && e == cudaSuccess; k++) {
         const DecImage &im = b.img[k];
         WideDecState d;
@@ -417,7 +469,7 @@ cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecB
             for (int r0 = r_lo; r0 <= r_hi && e == cudaSuccess; r0 += kWideChunk) {
                 const int np = std::min(kWideChunk, r_hi - r0 + 1);
                 const WideSet q{im.pixels, im.pitch, H, W, 1, 0, t, r0, np};
-                e = wide_network(m, hl, q, scratch, st);
+                e = wide_network(m, hl, q, scratch, false, nullptr, st);
                 if (e != cudaSuccess) break;
                 // one warp per stream of the pass (at most H streams)
                 const int warps = std::min(np, H);
