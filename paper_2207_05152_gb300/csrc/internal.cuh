@@ -166,15 +166,15 @@ cudaError_t launch_decode12(const DevModel &m, const DecBatch &b, cudaStream_t s
 // Networks with hidden layers wider than 256 (wide.cu): one layer at a time
 // over sets of pixels, activations in a workspace scratch of
 // wide_scratch_bytes (encode: INT8 activations as the tensor-core layers'
-// bf16 planes); hl is the host copy of the layer table
+// bf16 inputs); hl is the host copy of the layer table
 bool wide_supported(const DevModel &m);
 size_t wide_scratch_bytes(const DevModel &m, bool encode);
 cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch,
                                 int *err, cudaStream_t st);
 // one INT8 layer of a wide network's encode pass on the tensor cores
-// (wide_tc.cu): X as bf16 hi / lo planes [np][ldx], plane_in elements apart
-cudaError_t launch_wide_tc(const DevLayer &ly, const uint16_t *X, int ldx, size_t plane_in, int np, void *Y,
-                           int ldy, size_t plane_out, bool logits, int *err, cudaStream_t st);
+// (wide_tc.cu): X the previous layer's u8 units as bf16 [np][ldx]
+cudaError_t launch_wide_tc(const DevLayer &ly, const uint16_t *X, int ldx, int np, void *Y, int ldy, bool logits,
+                           int num_sms, int *err, cudaStream_t st);
 cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecBatch &b, uint8_t *scratch,
                                cudaStream_t st);
 // the grid decoder's stream-state set-up and final check (decode_tc.cu)

@@ -131,12 +131,11 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_f32(const float *X, int l
 // weights Q[k4][j]; signed inputs for the first layer, u8 units after), then
 // the requantised u8 unit (hidden) or the logit fma(acc, s, o) (output, FP32
 // into Y).  X and hidden Y are bytes [np][ld], ld a multiple of 4; with
-// plane > 0 a hidden unit u goes out as the tensor-core layers' input
-// planes instead: bf16(u >> 4) at Y[p][j] and bf16(u & 15) plane elements
-// further (Y as uint16 [np][ldy]).
+// bf16out a hidden unit u goes out as the tensor-core layers' input, the
+// exact bf16(u) (Y as uint16 [np][ldy]).
 __global__ void __launch_bounds__(kWideThreads) k_wide_i8(const uint8_t *X, int ldx, int K4, const uint32_t *Q,
                                                           const float *s, const float *o, int N, void *Y, int ldy,
-                                                          int np, int first, int logits, size_t plane) {
+                                                          int np, int first, int logits, int bf16out) {
     __shared__ uint32_t xs[kWideKC][kWideTileP + 4];
     __shared__ __align__(16) uint32_t ws[kWideKC][kWideTileU];
     const int tid = threadIdx.x, tc = tid % 16, tr = tid / 16;
@@ -183,17 +182,12 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_i8(const uint8_t *X, int 
 #pragma unroll
             for (int u = 0; u < 4; u++) z[u] = __fmaf_rn(__int2float_rn(acc[p][u]), sj[u], oj[u]);
             *reinterpret_cast<float4 *>(static_cast<float *>(Y) + (size_t)pp * ldy + j) = make_float4(z[0], z[1], z[2], z[3]);
-        } else if (plane) {
-            uint32_t hi[2] = {0u, 0u}, lo[2] = {0u, 0u};
+        } else if (bf16out) {
+            uint32_t pk[2] = {0u, 0u};
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const uint32_t v = requant_u8(acc[p][u], sj[u], oj[u]);
-                hi[u >> 1] |= (uint32_t)(__float_as_uint((float)(v >> 4)) >> 16) << (16 * (u & 1));
-                lo[u >> 1] |= (uint32_t)(__float_as_uint((float)(v & 15u)) >> 16) << (16 * (u & 1));
-            }
-            uint16_t *yh = static_cast<uint16_t *>(Y) + (size_t)pp * ldy + j;
-            *reinterpret_cast<uint2 *>(yh) = make_uint2(hi[0], hi[1]);
-            *reinterpret_cast<uint2 *>(yh + plane) = make_uint2(lo[0], lo[1]);
+            for (int u = 0; u < 4; u++)
+                pk[u >> 1] |= (__float_as_uint((float)requant_u8(acc[p][u], sj[u], oj[u])) >> 16) << (16 * (u & 1));
+            *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(Y) + (size_t)pp * ldy + j) = make_uint2(pk[0], pk[1]);
         } else {
             uint32_t packed = 0;
 #pragma unroll
@@ -341,23 +335,21 @@ namespace {
 
 // The scratch of one pass (kWideChunk pixels): two activation buffers of
 // hmax units, the logits Z [pixel][256] (FP32) and the inputs X.  With
-// planes (the INT8 encoder) an activation buffer holds the two bf16 planes
-// [kWideChunk][hpad] of the tensor-core layers' inputs, plane elements apart.
+// bf16 (the INT8 encoder) an activation buffer holds the tensor-core
+// layers' bf16 inputs [kWideChunk][hpad].
 struct WideScratch {
     uint8_t *A, *B, *X;
     float *Z;
     size_t bytes;
     int hpad;
-    size_t plane;
 };
-WideScratch wide_scratch(const DevModel &m, uint8_t *base, bool planes) {
+WideScratch wide_scratch(const DevModel &m, uint8_t *base, bool bf16) {
     auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const int hpad = (m.hmax + 63) / 64 * 64;
-    const size_t act = planes ? a256((size_t)kWideChunk * hpad * 4)
-                              : a256((size_t)kWideChunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
+    const size_t act = bf16 ? a256((size_t)kWideChunk * hpad * 2)
+                            : a256((size_t)kWideChunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
     WideScratch w;
     w.hpad = hpad;
-    w.plane = (size_t)kWideChunk * hpad;
     w.A = base;
     w.B = base + act;
     w.Z = reinterpret_cast<float *>(base + 2 * act);
@@ -368,7 +360,7 @@ WideScratch wide_scratch(const DevModel &m, uint8_t *base, bool planes) {
 
 // Inputs and every layer of the network over one set (np <= kWideChunk);
 // the logits land in Z.  tc (INT8, encode): the layers after the first on
-// the tensor cores (wide_tc.cu), their inputs as bf16 planes.
+// the tensor cores (wide_tc.cu), their inputs as bf16.
 cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q, uint8_t *scratch, bool tc,
                          int *err, cudaStream_t st) {
     const WideScratch w = wide_scratch(m, scratch, tc);
@@ -376,18 +368,21 @@ cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q
     float *Z = w.Z;
     k_wide_inputs<<<(q.np * kPriors + 255) / 256, 256, 0, st>>>(q, m.precision, X);
     if (tc) {
-        // the first layer (signed priors, K = 12) by dp4a into A's planes,
+        // the first layer (signed priors, K = 12) by dp4a into A as bf16,
         // then every later layer on the tensor cores, A and B in turn
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const DevLayer &l0 = hl[0];
         const dim3 grid((q.np + kWideTileP - 1) / kWideTileP, (l0.n_out + kWideTileU - 1) / kWideTileU);
         k_wide_i8<<<grid, kWideThreads, 0, st>>>(X, kPriors, (l0.n_in + 3) / 4, static_cast<const uint32_t *>(l0.w),
-                                                 l0.a, l0.o, l0.n_out, A, w.hpad, q.np, 1, 0, w.plane);
+                                                 l0.a, l0.o, l0.n_out, A, w.hpad, q.np, 1, 0, 1);
         cudaError_t e = cudaGetLastError();
         for (int l = 1; l < m.nl && e == cudaSuccess; l++) {
             const bool last = l == m.nl - 1;
             const uint16_t *in = reinterpret_cast<const uint16_t *>(l & 1 ? A : B);
             void *out = last ? static_cast<void *>(Z) : static_cast<void *>(l & 1 ? B : A);
-            e = launch_wide_tc(hl[l], in, w.hpad, w.plane, q.np, out, last ? kSymbols : w.hpad, w.plane, last, err, st);
+            e = launch_wide_tc(hl[l], in, w.hpad, q.np, out, last ? kSymbols : w.hpad, last, sms, err, st);
         }
         return e;
     }
@@ -427,7 +422,7 @@ size_t wide_scratch_bytes(const DevModel &m, bool encode) {
 
 cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch, int *err,
                                 cudaStream_t st) {
-    // (the workspace holds the planes whenever the network is INT8)
+    // (the workspace holds bf16 activations whenever the network is INT8)
     const bool tc = wide_tc_encode(m, hl);
     for (int k = 0; k < b.n; k++) {
         const EncImage &im = b.img[k];
