@@ -27,6 +27,9 @@
 namespace dlic {
 
 constexpr int kWideChunk = 4096;     // pixels per pass through the layers
+// (the INT8 encoder's tensor-core passes: 1024 tiles of its 4096 x 4096
+// layers, enough to spread evenly over the SMs)
+constexpr int kWideChunkTc = 8192;
 constexpr int kWideTileP = 128, kWideTileU = 64, kWideKC = 32, kWideThreads = 256;
 
 // The pixels of one pass: np pixels in raster order from p0 (encode), or the
@@ -53,7 +56,7 @@ __device__ __forceinline__ void wide_pixel(const WideSet &q, int i, int &r, int 
 
 // Network inputs of the set's pixels, [np][kPriors]: the default window's
 // priors (two rows above at columns c-2..c+2, then (r, c-2), (r, c-1); 0
-// outside the image) as v/128 - 1 (FP32) or v - 128 as signed bytes (INT8).
+// outside the image) as v/128 - 1 (FP32) or v - 128 as signed bytes (INT8);
 __global__ void k_wide_inputs(WideSet q, int prec, void *X) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= q.np * kPriors) return;
@@ -346,19 +349,20 @@ struct WideScratch {
 WideScratch wide_scratch(const DevModel &m, uint8_t *base, bool bf16) {
     auto a256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const int hpad = (m.hmax + 63) / 64 * 64;
-    const size_t act = bf16 ? a256((size_t)kWideChunk * hpad * 2)
-                            : a256((size_t)kWideChunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
+    const size_t chunk = bf16 ? kWideChunkTc : kWideChunk;
+    const size_t act = bf16 ? a256(chunk * hpad * 2) : a256(chunk * m.hmax * (m.precision == DLIC_FP32 ? 4 : 1));
     WideScratch w;
     w.hpad = hpad;
     w.A = base;
     w.B = base + act;
     w.Z = reinterpret_cast<float *>(base + 2 * act);
-    w.X = base + 2 * act + a256((size_t)kWideChunk * kSymbols * 4);
-    w.bytes = 2 * act + a256((size_t)kWideChunk * kSymbols * 4) + a256((size_t)kWideChunk * kPriors * 4);
+    w.X = base + 2 * act + a256(chunk * kSymbols * 4);
+    w.bytes = 2 * act + a256(chunk * kSymbols * 4) + a256(chunk * kPriors * 4);
     return w;
 }
 
-// Inputs and every layer of the network over one set (np <= kWideChunk);
+// Inputs and every layer of the network over one set (np <= kWideChunk, or
+// kWideChunkTc with tc);
 // the logits land in Z.  tc (INT8, encode): the layers after the first on
 // the tensor cores (wide_tc.cu), their inputs as bf16.
 cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q, uint8_t *scratch, bool tc,
@@ -368,8 +372,9 @@ cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q
     float *Z = w.Z;
     k_wide_inputs<<<(q.np * kPriors + 255) / 256, 256, 0, st>>>(q, m.precision, X);
     if (tc) {
-        // the first layer (signed priors, K = 12) by dp4a into A as bf16,
-        // then every later layer on the tensor cores, A and B in turn
+        // the first layer (K = the 12 signed priors: too short a contraction
+        // for the tensor cores to gain) by dp4a into A as bf16, then every
+        // later layer on the tensor cores, B and A in turn, the logits into Z
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -428,8 +433,9 @@ cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const Enc
         const EncImage &im = b.img[k];
         const int64_t N = (int64_t)im.H * im.W;
         uint32_t *fc = reinterpret_cast<uint32_t *>(b.ws + im.fc_off);
-        for (int64_t p0 = 0; p0 < N; p0 += kWideChunk) {
-            const WideSet q{im.pixels, im.pitch, im.H, im.W, 0, p0, 0, 0, (int)std::min<int64_t>(kWideChunk, N - p0)};
+        const int64_t chunk = tc ? kWideChunkTc : kWideChunk;
+        for (int64_t p0 = 0; p0 < N; p0 += chunk) {
+            const WideSet q{im.pixels, im.pitch, im.H, im.W, 0, p0, 0, 0, (int)std::min<int64_t>(chunk, N - p0)};
             cudaError_t e = wide_network(m, hl, q, scratch, tc, err, st);
             if (e != cudaSuccess) return e;
             k_wide_table_enc<<<(q.np + 7) / 8, kWideThreads, 0, st>>>(m, q, wide_scratch(m, scratch, tc).Z, fc, im.S,

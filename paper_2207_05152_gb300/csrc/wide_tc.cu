@@ -14,12 +14,15 @@
 // next layer) or its logit map (output layer), exactly as the CUDA-core
 // kernels do, so the bitstreams do not change.
 //
-// Persistent CTAs over 128-pixel x 128-unit tiles: warp 0 issues the TMA
+// Persistent CTAs over 128-pixel x 256-unit tiles: warp 0 issues the TMA
 // loads of the activations and the weight rows (128-byte swizzle, K blocks
 // of 64) through a ring of stages, warp 1 issues the MMAs of each chunk into
 // one of two tensor-memory accumulators, and warps 2..9 drain the other one
 // into int32 sums held in registers, so the MMAs never wait for the
-// epilogue.
+// epilogue.  The tile is as wide as one MMA allows (N = 256), so that every
+// byte the loads bring from L2 feeds as many multiply-adds as the tensor
+// memory's two accumulators permit: the feed from L2 into shared memory,
+// not the tensor pipe, is what bounds narrower tiles.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -32,13 +35,19 @@ namespace dlic {
 
 constexpr int kWtThreads = 320;
 constexpr int kWtEpiWarps = 8;
-constexpr int kWtStages = 6;
-constexpr int kWtM = 128, kWtN = 128, kWtKB = 64;
+constexpr int kWtM = 128, kWtKB = 64;
 constexpr int kWtChunkKB = 4;                           // K blocks per exact chunk (K = 256)
 constexpr uint32_t kWtABytes = kWtM * kWtKB * 2;        // 16 KB: the activations' K block
-constexpr uint32_t kWtBBytes = kWtN * kWtKB * 2;        // 16 KB: the tile's weight rows, one K block
-constexpr uint32_t kWtStageBytes = kWtABytes + kWtBBytes;
 constexpr long long kWtWaitLimit = 4000000000LL;
+// Tiles of TN units (256, or 128 for a layer whose 256-wide tiles would
+// leave most SMs idle): the weight rows of a K block and the stage count
+// that fills about 192 KB of shared memory.
+template <int TN>
+struct WtShape {
+    static constexpr uint32_t kBBytes = TN * kWtKB * 2;
+    static constexpr uint32_t kStageBytes = kWtABytes + kBBytes;
+    static constexpr int kStages = TN == 256 ? 4 : 6;
+};
 
 // K-major operand tile with 128-byte swizzle as TMA writes it: 8-row groups
 // 1024 bytes apart; a K step of 16 advances the start address by 32 bytes.
@@ -63,18 +72,23 @@ __device__ __forceinline__ void wt_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
 }
 
-// Y = layer(X) for np pixels: X bf16 [np][K] at mapX (the previous layer's
-// u8 units as exact bf16), W bf16 [N][K] at mapW.  Hidden layer (logits ==
-// 0): Y[p * ldy + j] = bf16(requant(acc)) (uint16).  Output layer:
-// Y[p * ldy + j] = fma(float(acc), s_j, o_j) (FP32).
+// Y = layer(X) for np pixels: X bf16 [np][K] at mapX (the first layer's
+// priors v - 128, or the previous layer's u8 units, all exact in bf16), W
+// bf16 [N][K] at mapW.  Hidden layer (logits == 0): Y[p * ldy + j] =
+// bf16(requant(acc)) (uint16).  Output layer: Y[p * ldy + j] =
+// fma(float(acc), s_j, o_j) (FP32).
+template <int TN>
 __global__ void __launch_bounds__(kWtThreads, 1)
     k_wide_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW, int K, int N, int np,
               const float *__restrict__ s, const float *__restrict__ o, void *Y, int ldy, int logits, int *err) {
+    constexpr int kWtN = TN, kWtStages = WtShape<TN>::kStages;
+    constexpr uint32_t kWtStageBytes = WtShape<TN>::kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full[kWtStages], empty[kWtStages], cfull[2], cempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
+    __shared__ __align__(16) float s_so[kWtEpiWarps][2][128];   // an epilogue warp's scales and offsets
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = (np + kWtM - 1) / kWtM, tiles = mt * ((N + kWtN - 1) / kWtN);
     const int nkb = (K + kWtKB - 1) / kWtKB, nch = (nkb + kWtChunkKB - 1) / kWtChunkKB;
@@ -155,14 +169,24 @@ __global__ void __launch_bounds__(kWtThreads, 1)
         }
     } else if (warp >= 2) {
         // epilogue: warp w reads lanes 32 (w mod 4) .. + 31 (one pixel per
-        // thread); the two warps of a lane quarter take 64 columns each
+        // thread); the two warps of a lane quarter take half the columns each
+        constexpr int kHalf = kWtN / 2;
         const int qd = warp & 3, hf = (warp - 2) >> 2;
         const uint32_t lanes = (uint32_t)(32 * qd) << 16;
-        const int cb = 64 * hf;
+        const int cb = kHalf * hf;
+        float *sw = s_so[warp - 2][0], *ow = s_so[warp - 2][1];
         int g = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
             const int m0 = (t % mt) * kWtM, n0 = (t / mt) * kWtN;
-            int R[64];
+            // this tile's scales and offsets of the warp's columns (its last
+            // reads of the previous tile's are done: same warp)
+            for (int i = lane; i < kHalf; i += 32) {
+                const int j = n0 + cb + i;
+                sw[i] = j < N ? s[j] : 0.0f;
+                ow[i] = j < N ? o[j] : 0.0f;
+            }
+            __syncwarp();
+            int R[kHalf];
             bool ok = true;
             for (int c = 0; c < nch; c++, g++) {
                 const int b = g & 1;
@@ -174,7 +198,7 @@ __global__ void __launch_bounds__(kWtThreads, 1)
                 tc::mbar_wait(&cfull[b], (g >> 1) & 1, 1000);   // every lane observes the phase
                 tc::fence_after_sync();
 #pragma unroll
-                for (int h = 0; h < 4; h++) {
+                for (int h = 0; h < kHalf / 16; h++) {
                     uint32_t v[16];
                     tc::tmem_ld16(tm + lanes + (uint32_t)(kWtN * b + cb + 16 * h), v);
                     tc::tmem_wait_ld();
@@ -192,29 +216,40 @@ __global__ void __launch_bounds__(kWtThreads, 1)
             const int p = m0 + 32 * qd + lane;
             if (p >= np) continue;
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
+            for (int h = 0; h < kHalf / 16; h++) {
                 const int j0 = n0 + cb + 16 * h;   // N is a multiple of 4
                 if (j0 >= N) break;
                 const int nv = min(16, N - j0);
+                float sv[16], ov[16];
+#pragma unroll
+                for (int e = 0; e < 16; e += 4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(sw + 16 * h + e);
+                    const float4 c = *reinterpret_cast<const float4 *>(ow + 16 * h + e);
+                    sv[e] = a.x; sv[e + 1] = a.y; sv[e + 2] = a.z; sv[e + 3] = a.w;
+                    ov[e] = c.x; ov[e + 1] = c.y; ov[e + 2] = c.z; ov[e + 3] = c.w;
+                }
                 if (logits) {
                     float *z = static_cast<float *>(Y) + (size_t)p * ldy + j0;
 #pragma unroll
                     for (int e = 0; e < 16; e += 4)
                         if (e < nv)
-                            *reinterpret_cast<float4 *>(z + e) = make_float4(
-                                __fmaf_rn(__int2float_rn(R[16 * h + e]), __ldg(s + j0 + e), __ldg(o + j0 + e)),
-                                __fmaf_rn(__int2float_rn(R[16 * h + e + 1]), __ldg(s + j0 + e + 1), __ldg(o + j0 + e + 1)),
-                                __fmaf_rn(__int2float_rn(R[16 * h + e + 2]), __ldg(s + j0 + e + 2), __ldg(o + j0 + e + 2)),
-                                __fmaf_rn(__int2float_rn(R[16 * h + e + 3]), __ldg(s + j0 + e + 3), __ldg(o + j0 + e + 3)));
+                            *reinterpret_cast<float4 *>(z + e) =
+                                make_float4(__fmaf_rn(__int2float_rn(R[16 * h + e]), sv[e], ov[e]),
+                                            __fmaf_rn(__int2float_rn(R[16 * h + e + 1]), sv[e + 1], ov[e + 1]),
+                                            __fmaf_rn(__int2float_rn(R[16 * h + e + 2]), sv[e + 2], ov[e + 2]),
+                                            __fmaf_rn(__int2float_rn(R[16 * h + e + 3]), sv[e + 3], ov[e + 3]));
                 } else {
+                    // u = clamp(rint(fma(acc, s, o)), 0, 255) in the float
+                    // domain (the same value as the integer requantisation),
+                    // then its bf16 bits
                     uint32_t pk[8];
 #pragma unroll
                     for (int e = 0; e < 8; e++) {
-                        const bool in = 2 * e < nv;
-                        const uint32_t u0 = in ? requant_u8(R[16 * h + 2 * e], __ldg(s + j0 + 2 * e), __ldg(o + j0 + 2 * e)) : 0u;
-                        const uint32_t u1 =
-                            in ? requant_u8(R[16 * h + 2 * e + 1], __ldg(s + j0 + 2 * e + 1), __ldg(o + j0 + 2 * e + 1)) : 0u;
-                        pk[e] = (uint32_t)tc::bf16_of_int((int)u0) | ((uint32_t)tc::bf16_of_int((int)u1) << 16);
+                        float u0 = rintf(__fmaf_rn(__int2float_rn(R[16 * h + 2 * e]), sv[2 * e], ov[2 * e]));
+                        float u1 = rintf(__fmaf_rn(__int2float_rn(R[16 * h + 2 * e + 1]), sv[2 * e + 1], ov[2 * e + 1]));
+                        u0 = fminf(fmaxf(u0, 0.0f), 255.0f);
+                        u1 = fminf(fmaxf(u1, 0.0f), 255.0f);
+                        pk[e] = __byte_perm(__float_as_uint(u0), __float_as_uint(u1), 0x7632);
                     }
                     uint16_t *y = static_cast<uint16_t *>(Y) + (size_t)p * ldy + j0;
                     if (nv == 16) {
@@ -261,22 +296,32 @@ static CUresult wide_map(CUtensorMap *map, const void *g, int rows, int cols, in
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
+template <int TN>
+static cudaError_t launch_tn(const DevLayer &ly, const uint16_t *X, int ldx, int np, void *Y, int ldy, bool logits,
+                             int num_sms, int *err, cudaStream_t st) {
+    CUtensorMap mx, mw;
+    if (wide_map(&mx, X, np, ly.n_in, ldx, kWtM) != CUDA_SUCCESS ||
+        wide_map(&mw, ly.wtc, ly.n_out, ly.n_in, ly.wtc_pitch, TN) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)WtShape<TN>::kStages * WtShape<TN>::kStageBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_wide_tc<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((np + kWtM - 1) / kWtM) * ((ly.n_out + TN - 1) / TN);
+    k_wide_tc<TN><<<std::min(tiles, std::max(1, num_sms)), kWtThreads, smem, st>>>(mx, mw, ly.n_in, ly.n_out, np, ly.a,
+                                                                                    ly.o, Y, ldy, logits ? 1 : 0, err);
+    return cudaGetLastError();
+}
+
 // One layer of a pass: X bf16 [np][ldx], the layer's bf16 weights
 // [n_out][wtc_pitch]; one persistent CTA per SM (or per tile, if fewer).
+// Tiles are 256 units wide unless that leaves more than half the SMs
+// without a tile (the 256 logits of a pass, say).
 cudaError_t launch_wide_tc(const DevLayer &ly, const uint16_t *X, int ldx, int np, void *Y, int ldy, bool logits,
                            int num_sms, int *err, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
-    CUtensorMap mx, mw;
-    if (wide_map(&mx, X, np, ly.n_in, ldx, kWtM) != CUDA_SUCCESS ||
-        wide_map(&mw, ly.wtc, ly.n_out, ly.n_in, ly.wtc_pitch, kWtN) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kWtStages * kWtStageBytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_wide_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int tiles = ((np + kWtM - 1) / kWtM) * ((ly.n_out + kWtN - 1) / kWtN);
-    k_wide_tc<<<std::min(tiles, std::max(1, num_sms)), kWtThreads, smem, st>>>(mx, mw, ly.n_in, ly.n_out, np, ly.a,
-                                                                                ly.o, Y, ldy, logits ? 1 : 0, err);
-    return cudaGetLastError();
+    const int wide_tiles = ((np + kWtM - 1) / kWtM) * ((ly.n_out + 255) / 256);
+    return 2 * wide_tiles >= num_sms ? launch_tn<256>(ly, X, ldx, np, Y, ldy, logits, num_sms, err, st)
+                                     : launch_tn<128>(ly, X, ldx, np, Y, ldy, logits, num_sms, err, st);
 }
 
 }  // namespace dlic

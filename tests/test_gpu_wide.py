@@ -89,7 +89,8 @@ def test_4096_wide_layer(Codec, orc, prec):
 
 
 def test_more_pixels_than_one_pass(Codec, orc):
-    # 96 x 100 pixels: the encoder's passes of 4096 pixels end mid-image
+    # 96 x 100 pixels: the encoder's passes (4096 pixels, 8192 on the tensor
+    # cores) end mid-image
     img = synth.value_noise_image(96, 100, 7)
     _check(Codec, orc, _blob(_random_layers([12, 288, 256], 35), "int8", [img]), [img], [34])
 
