@@ -90,7 +90,10 @@ __global__ void __launch_bounds__(kWtThreads, 1)
     __shared__ int s_fail;
     __shared__ __align__(16) float s_so[kWtEpiWarps][2][128];   // an epilogue warp's scales and offsets
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int mt = (np + kWtM - 1) / kWtM, tiles = mt * ((N + kWtN - 1) / kWtN);
+    // tile t: n-tile t mod nt, m-tile t / nt, so that the CTAs resident at
+    // one time share their activation tiles (each read from DRAM once) and
+    // the weights stay in L2
+    const int nt = (N + kWtN - 1) / kWtN, tiles = nt * ((np + kWtM - 1) / kWtM);
     const int nkb = (K + kWtKB - 1) / kWtKB, nch = (nkb + kWtChunkKB - 1) / kWtChunkKB;
 
     if (warp == 0) {
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(kWtThreads, 1)
         // and still deliver their full size)
         int it = 0;
         for (int t = blockIdx.x; t < tiles && !failed(); t += gridDim.x) {
-            const int m0 = (t % mt) * kWtM, n0 = (t / mt) * kWtN;
+            const int m0 = (t / nt) * kWtM, n0 = (t % nt) * kWtN;
             for (int i = 0; i < nkb; i++, it++) {
                 const int q = it % kWtStages;
                 if (!tc::mbar_wait(&empty[q], ((it / kWtStages) & 1) ^ 1, kWtWaitLimit)) {
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kWtThreads, 1)
         float *sw = s_so[warp - 2][0], *ow = s_so[warp - 2][1];
         int g = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-            const int m0 = (t % mt) * kWtM, n0 = (t / mt) * kWtN;
+            const int m0 = (t / nt) * kWtM, n0 = (t % nt) * kWtN;
             // this tile's scales and offsets of the warp's columns (its last
             // reads of the previous tile's are done: same warp)
             for (int i = lane; i < kHalf; i += 32) {
