@@ -348,7 +348,8 @@ def run_ours(args):
                         "widths": [M.window_size(M.FIG6_WINDOW), 128, 128, 256],
                         "int8": leg(r6), "fp32": leg(r6f)},
         "deep_network": {"widths": [12, 128, 128, 128, 128, 128, 256], "precision": "int8",
-                         "kernels": "CUDA-core encoder, unit-split wavefront decoder", **leg(rdeep)},
+                         "kernels": "CUDA-core encoder; cluster wavefront decoder with the warp-level MMAs "
+                                    "chained over the layer table", **leg(rdeep)},
         "wide_network": {"widths": [12, 4096, 4096, 256],
                          "weights": "the predictive 12-64-64-256 network in 64 of each layer's 4096 units, "
                                     "seeded random weights in the rest",

@@ -754,7 +754,8 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
         return fail(DLIC_ERR_INVALID, "input of %llu bytes: at most 8 GiB per decode call",
                     (unsigned long long)h_in_offsets[n]);
     const bool vol = m->dev.vol != 0;
-    const bool use_wave = m->dev.nl == 3 && m->dev.bits == 8 && wave_decode_supported(m->dev);
+    const bool deep_wave = deep_wave_supported(m->dev);
+    const bool use_wave = (m->dev.nl == 3 && m->dev.bits == 8 && wave_decode_supported(m->dev)) || deep_wave;
     if (vol && !use_wave) return fail(DLIC_ERR_UNSUPPORTED, "volumes decode on the cluster wavefront kernels only");
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     {
@@ -824,8 +825,9 @@ static dlic_status decode_items(const dlic_model *m, const void *d_in, const uin
                 used += P[i];
                 per = std::max(per, (std::min(it[i].H, (it[i].W + 2) / 3) + P[i] - 1) / P[i]);
             }
-            bool grid = plan == DLIC_PLAN_GRID ||
-                        (plan == DLIC_PLAN_AUTO && 2 * used <= m->num_sms && per > kGridMinChunkPixels);
+            // (deeper networks decode on clusters only)
+            bool grid = !deep_wave && (plan == DLIC_PLAN_GRID ||
+                                       (plan == DLIC_PLAN_AUTO && 2 * used <= m->num_sms && per > kGridMinChunkPixels));
             for (int c0 = 0; grid && c0 < n; c0 += kMaxBatch) {
                 DecBatch *b = new_batch();
                 b->n = std::min(kMaxBatch, n - c0);

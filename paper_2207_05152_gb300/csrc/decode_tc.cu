@@ -51,7 +51,7 @@ constexpr int kZPitch = kSymbols + 4;
 
 struct DecTcLayout {
     // INT8 network: bf16 operand tiles, s8 priors, bf16 activations
-    uint32_t w1, w2, w3, pri, b23;
+    uint32_t w1, w2, w3, pri, b23, shid;
     // FP32 network: W1^T | b1 | b2 | b3, W2^T, the W3^T staging ring, FP32
     // inputs and activations (the logits z overlay xs and h1t)
     uint32_t wf, w2f, w3s, xs, h1t, h2t;
@@ -79,6 +79,9 @@ struct DecTcParams {
     int T;            // grid decoder of a batch: waves of the longest image
     int lut2;         // 1: the table's powers of two expanded to kTableSteps entries
     int smma;         // INT8: 1 = the wide layers as warp-level MMAs, 0 = tcgen05
+    int deep;         // INT8 networks of 1..5 hidden layers of widths up to 128 from the
+                      // layer table (warp-level MMAs, every layer zero-padded to 128 units)
+    int nhh;          // deep: hidden-to-hidden layers (the hidden layers less one)
 };
 
 // FP32 network parameters kept in shared memory (floats): W1^T [12][h1],
@@ -116,6 +119,14 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
         L.h1t = base + xs_bytes;
         L.z = base;
         L.h2t = take(4u * h2 * (nt + 4));
+    } else if (prm.smma && prm.deep) {
+        // deep: W1 words, nhh hidden-to-hidden layers [unit][k] bf16 with their
+        // scales and offsets; the output layer's weights live in registers
+        L.w1 = take((uint32_t)prm.k1 * kDecHidden);
+        L.w2 = take(2u * kDecHidden * kActPitch * (uint32_t)prm.nhh);
+        L.shid = take(4u * 2u * kDecHidden * (uint32_t)prm.nhh);
+        L.pri = take((uint32_t)prm.k1 * nt);
+        L.b23 = take(2u * 2u * nt * kActPitch);
     } else if (prm.smma) {
         L.w1 = take((uint32_t)prm.k1 * kDecHidden);   // W1 as s8 words [k1 / 4][128] (the first layer runs as dp4a)
         L.w2 = take(2u * kDecHidden * kActPitch);     // W2 [unit][k], bf16
@@ -131,7 +142,7 @@ __host__ __device__ inline DecTcLayout dec_layout(const DecTcParams &prm, bool f
     }
     // warp-level MMAs: the logits overlay the W3 rows, which are read into
     // registers before the first wave (4 nt 260 <= 2 x 256 x 136 for nt <= 64)
-    if (!f32) L.z = prm.smma ? L.w3 : take(4u * nt * kSymbols);
+    if (!f32) L.z = prm.smma && !prm.deep ? L.w3 : take(4u * nt * (prm.smma ? kZPitch : kSymbols));
     L.ring = take(prm.gimg ? 0u : (uint32_t)prm.rcols * rows);
     L.tring = take(prm.gimg ? 0u : 4u * prm.tcols * prm.tslots * prm.tq);
     L.rows = take(4u * prm.list_rows);
@@ -512,7 +523,11 @@ __global__ void __launch_bounds__(kDecThreads) k_batch_finish(DecBatch b) {
 // decodes one volume with every CTA of a cooperative grid (no cluster):
 // each wave's pixels are split evenly over the CTAs, stream states live in
 // the workspace and the waves are separated by a grid-wide barrier.
-template <bool F32, bool DEF, bool GRID, bool SMMA>
+// DEEP (with SMMA, 2D, default window): an INT8 network of 1..5 hidden
+// layers of widths up to 128 from the layer table, each layer zero-padded to
+// 128 units (a padded unit has zero weights in and out and requantises to 0,
+// so the sums are those of the unpadded network).
+template <bool F32, bool DEF, bool GRID, bool SMMA, bool DEEP = false>
 __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b, const DecTcParams &prm) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bar;
@@ -537,6 +552,7 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // (the layout with this instance's MMA kind as a constant)
     DecTcParams pl = prm;
     pl.smma = SMMA ? 1 : 0;
+    pl.deep = DEEP ? 1 : 0;
     const DecTcLayout L = dec_layout(pl, F32);
     const int K1 = DEF ? 16 : prm.k1, NPRI = DEF ? kPriors : m.n_in;
     const int TSLOTS = DEF ? 3 : prm.tslots, TCOLS = DEF ? 32 : prm.tcols, RCOLS = DEF ? 16 : prm.rcols;
@@ -551,6 +567,40 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             for (int i = tid; i < kSymbols; i += kDecThreads) wf[NPRI * h1 + h1 + h2 + i] = m.b3[i];
             for (int i = tid; i < h1 * h2 / 4; i += kDecThreads)
                 reinterpret_cast<float4 *>(smem + L.w2f)[i] = __ldg(reinterpret_cast<const float4 *>(m.w2t) + i);
+        } else if (DEEP) {
+            // the hidden-to-hidden layers as bf16 rows [unit][k] (128 x 128,
+            // zero-padded) from their packed s8 words [k / 4][n_out], with
+            // their scales and offsets (0 for padded units); W1 as s8 words
+            // [k1 / 4][128]
+            uint16_t *w2s = reinterpret_cast<uint16_t *>(smem + L.w2);
+            float *sh = reinterpret_cast<float *>(smem + L.shid);
+            for (int l = 0; l < prm.nhh; l++) {
+                const DevLayer ly = m.layers[1 + l];
+                const uint32_t *q = static_cast<const uint32_t *>(ly.w);
+                const int k4n = (ly.n_in + 3) / 4;
+                for (int i = tid; i < (kDecHidden / 4) * kDecHidden; i += kDecThreads) {
+                    const int j = i % kDecHidden, k4 = i / kDecHidden;
+                    const uint32_t v = j < ly.n_out && k4 < k4n ? __ldg(q + k4 * ly.n_out + j) : 0u;
+                    uint32_t lo = 0, hi = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const uint32_t h = tc::bf16_of_int((int)(int8_t)(uint8_t)(v >> (8 * e)));
+                        if (e < 2) lo |= h << (16 * e); else hi |= h << (16 * (e - 2));
+                    }
+                    *reinterpret_cast<uint2 *>(w2s + ((size_t)l * kDecHidden + j) * kActPitch + 4 * k4) = make_uint2(lo, hi);
+                }
+                for (int j = tid; j < kDecHidden; j += kDecThreads) {
+                    sh[(2 * l) * kDecHidden + j] = j < ly.n_out ? ly.a[j] : 0.0f;
+                    sh[(2 * l + 1) * kDecHidden + j] = j < ly.n_out ? ly.o[j] : 0.0f;
+                }
+            }
+            const DevLayer l0 = m.layers[0];
+            const uint32_t *q0 = static_cast<const uint32_t *>(l0.w);
+            uint32_t *w1q = reinterpret_cast<uint32_t *>(smem + L.w1);
+            for (int i = tid; i < (K1 / 4) * kDecHidden; i += kDecThreads) {
+                const int j = i % kDecHidden, k4 = i / kDecHidden;
+                w1q[i] = j < l0.n_out && k4 < (l0.n_in + 3) / 4 ? __ldg(q0 + k4 * l0.n_out + j) : 0u;
+            }
         } else if (SMMA) {
             // W2, W3 as bf16 rows [unit][k] from the packed s8 words [k / 4][unit]
             auto unpack = [&](const uint32_t *q, int units, uint16_t *dst) {
@@ -816,7 +866,15 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // 16 w' + g and 16 w' + g + 8 (w' = warp mod 8 for layer 2, the warp for
     // layer 3, g = lane / 4)
     float s2lo = 0.f, o2lo = 0.f, s2hi = 0.f, o2hi = 0.f, s3lo = 0.f, o3lo = 0.f, s3hi = 0.f, o3hi = 0.f;
-    if constexpr (!F32) {
+    if constexpr (DEEP) {
+        // the first layer's unit `unit` (0 past its width) and the output
+        // layer's units 16 warp + g and 16 warp + g + 8
+        const DevLayer l0 = m.layers[0], lo = m.layers[m.nl - 1];
+        s1r = unit < l0.n_out ? l0.a[unit] : 0.0f;
+        o1r = unit < l0.n_out ? l0.o[unit] : 0.0f;
+        const int u3 = 16 * warp + (lane >> 2);
+        s3lo = lo.a[u3]; o3lo = lo.o[u3]; s3hi = lo.a[u3 + 8]; o3hi = lo.o[u3 + 8];
+    } else if constexpr (!F32) {
         s1r = m.s1[unit]; o1r = m.o1[unit]; s2r = m.s2[unit]; o2r = m.o2[unit];
         s3a = m.s3[unit]; o3a = m.o3[unit]; s3b = m.s3[128 + unit]; o3b = m.o3[128 + unit];
         const int u2 = 16 * (warp & 7) + (lane >> 2), u3 = 16 * warp + (lane >> 2);   // (layer 2: warps 0..7)
@@ -933,7 +991,26 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
     // k half (lane / 8) & 1
     const int lrow = lane & 7, lk = 8 * ((lane >> 3) & 1);
     uint32_t w3f[kDecHidden / 16][4];
-    if constexpr (!F32 && SMMA) {
+    if constexpr (DEEP) {
+        // the output layer's fragments straight from its packed s8 words
+        // [k / 4][256]: W[u][k], W[u][k + 1] for even k (0 past its inputs)
+        const DevLayer lo = m.layers[m.nl - 1];
+        const uint32_t *q = static_cast<const uint32_t *>(lo.w);
+        auto pair = [&](int u, int k) -> uint32_t {
+            if (k >= lo.n_in) return 0u;
+            const uint32_t v = __ldg(q + (k >> 2) * kSymbols + u) >> (8 * (k & 3));
+            return (uint32_t)tc::bf16_of_int((int)(int8_t)(uint8_t)v) |
+                   ((uint32_t)tc::bf16_of_int((int)(int8_t)(uint8_t)(v >> 8)) << 16);
+        };
+        const int u = 16 * warp + mg;
+#pragma unroll
+        for (int ks = 0; ks < kDecHidden / 16; ks++) {
+            w3f[ks][0] = pair(u, 16 * ks + 2 * mt4);
+            w3f[ks][1] = pair(u + 8, 16 * ks + 2 * mt4);
+            w3f[ks][2] = pair(u, 16 * ks + 2 * mt4 + 8);
+            w3f[ks][3] = pair(u + 8, 16 * ks + 2 * mt4 + 8);
+        }
+    } else if constexpr (!F32 && SMMA) {
         const uint16_t *W = reinterpret_cast<const uint16_t *>(smem + L.w3) + (size_t)(16 * warp + mg) * kActPitch + 2 * mt4;
 #pragma unroll
         for (int ks = 0; ks < kDecHidden / 16; ks++) {
@@ -977,10 +1054,48 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
             act2[(size_t)(p + 9) * kActPitch + u + 8] = q(c1[3], s2hi, o2hi);
         }
     };
-    auto mma_layer3 = [&](int NP) {
+    // DEEP: hidden-to-hidden layer l (weights and scales in shared memory)
+    // from activations `in` to `out`, as mma_layer2 does for the fixed network
+    auto mma_hidden = [&](int NP, int l, const uint16_t *in, uint16_t *out) {
+        if (warp >= 8) return;
+        const uint16_t *W = reinterpret_cast<const uint16_t *>(smem + L.w2) + (size_t)l * kDecHidden * kActPitch;
+        const float *sh = reinterpret_cast<const float *>(smem + L.shid) + (size_t)(2 * l) * kDecHidden;
+        const int u = 16 * warp + mg;
+        const float slo = sh[u], shi = sh[u + 8], olo = sh[kDecHidden + u], ohi = sh[kDecHidden + u + 8];
+        const uint16_t *wa = W + (size_t)u * kActPitch + 2 * mt4;
+        for (int n0 = 0; n0 < NP / 8; n0 += 2) {
+            const uint16_t *xa = in + (size_t)(8 * n0 + lrow) * kActPitch + lk, *xb = xa + 8 * kActPitch;
+            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < kDecHidden / 16; ks++) {
+                const uint32_t a0 = ld32(wa + 16 * ks), a1 = ld32(wa + 8 * kActPitch + 16 * ks),
+                               a2 = ld32(wa + 16 * ks + 8), a3 = ld32(wa + 8 * kActPitch + 16 * ks + 8);
+                uint32_t b0, b1, b2, b3;
+                ldsm2(xa + 16 * ks, b0, b1);
+                ldsm2(xb + 16 * ks, b2, b3);
+                tc::mma_sync_bf16(c0, a0, a1, a2, a3, b0, b1);
+                tc::mma_sync_bf16(c1, a0, a1, a2, a3, b2, b3);
+            }
+            auto q = [](float acc, float sc, float of) {
+                float h = rintf(__fmaf_rn(acc, sc, of));
+                h = fminf(fmaxf(h, 0.0f), 255.0f);
+                return (uint16_t)(__float_as_uint(h) >> 16);   // bf16 of the integer
+            };
+            const int p = 8 * n0 + 2 * mt4;
+            out[(size_t)p * kActPitch + u] = q(c0[0], slo, olo);
+            out[(size_t)(p + 1) * kActPitch + u] = q(c0[1], slo, olo);
+            out[(size_t)p * kActPitch + u + 8] = q(c0[2], shi, ohi);
+            out[(size_t)(p + 1) * kActPitch + u + 8] = q(c0[3], shi, ohi);
+            out[(size_t)(p + 8) * kActPitch + u] = q(c1[0], slo, olo);
+            out[(size_t)(p + 9) * kActPitch + u] = q(c1[1], slo, olo);
+            out[(size_t)(p + 8) * kActPitch + u + 8] = q(c1[2], shi, ohi);
+            out[(size_t)(p + 9) * kActPitch + u + 8] = q(c1[3], shi, ohi);
+        }
+    };
+    auto mma_layer3 = [&](int NP, const uint16_t *act_in) {
         const int u = 16 * warp + mg;
         for (int n0 = 0; n0 < NP / 8; n0 += 2) {   // NP is a multiple of 16: octets in pairs
-            const uint16_t *xa = act2 + (size_t)(8 * n0 + lrow) * kActPitch + lk, *xb = xa + 8 * kActPitch;
+            const uint16_t *xa = act_in + (size_t)(8 * n0 + lrow) * kActPitch + lk, *xb = xa + 8 * kActPitch;
             float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int ks = 0; ks < kDecHidden / 16; ks++) {
@@ -1420,11 +1535,25 @@ __device__ __forceinline__ void decode_wave(const DevModel &m, const DecBatch &b
                         }
                     }
                 }
-                if (SMMA) {
+                if (DEEP) {
+                    // the hidden-to-hidden layers, act1 and act2 in turn, then
+                    // the output layer from the last of them
+                    uint16_t *ain = act1, *aout = act2;
+                    for (int l = 0; l < prm.nhh; l++) {
+                        __syncthreads();   // the previous layer's outputs are in place
+                        mma_hidden(NP, l, ain, aout);
+                        uint16_t *tsw = ain;
+                        ain = aout;
+                        aout = tsw;
+                    }
+                    __syncthreads();
+                    mma_layer3(NP, ain);
+                    __syncthreads();   // the logits are in place
+                } else if (SMMA) {
                     __syncthreads();   // the first layer's outputs are in place
                     mma_layer2(NP);
                     __syncthreads();
-                    mma_layer3(NP);
+                    mma_layer3(NP, act2);
                     __syncthreads();   // the logits are in place
                 } else {
                 run_layer(2, NP);
@@ -1645,6 +1774,10 @@ template <bool DEF, bool SMMA>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc(DevModel m, DecBatch b, DecTcParams prm) {
     decode_wave<false, DEF, false, SMMA>(m, b, prm);
 }
+// INT8 networks of 1..5 hidden layers of widths up to 128 (the default window)
+__global__ void __launch_bounds__(kDecThreads, 1) k_decode_tc_deep(DevModel m, DecBatch b, DecTcParams prm) {
+    decode_wave<false, true, false, true, true>(m, b, prm);
+}
 template <bool DEF>
 __global__ void __launch_bounds__(kDecThreads, 1) k_decode_f32(DevModel m, DecBatch b, DecTcParams prm) {
     decode_wave<true, DEF, false, false>(m, b, prm);
@@ -1727,7 +1860,17 @@ bool wave_decode_supported(const DevModel &m) {
            m.h2 % 4 == 0;
 }
 
+// INT8 networks of 1..5 hidden layers (other than two) of widths up to 128
+// with the default 2D window: the cluster wavefront decoder's warp-level
+// MMAs chained over the layer table (each layer padded to 128 units); the
+// hidden-to-hidden layers' weights fill up to 139 KB of shared memory.
+bool deep_wave_supported(const DevModel &m) {
+    return m.precision == DLIC_INT8 && m.bits == 8 && m.layers != nullptr && !m.vol && default_window(m) &&
+           m.nl != 3 && m.nl >= 2 && m.nl <= 6 && m.hmax <= kDecHidden;
+}
+
 static void (*wave_kernel(const DevModel &m, bool smma))(DevModel, DecBatch, DecTcParams) {
+    if (deep_wave_supported(m)) return k_decode_tc_deep;
     // the default window runs the instance with its sizes as constants
     const bool def = default_window(m);
     if (m.precision == DLIC_FP32) return def ? k_decode_f32<true> : k_decode_f32<false>;
@@ -1763,6 +1906,13 @@ static bool plan_wave(const DevModel &m, int maxH, int maxW, int maxD, int P, ui
     prm.h2 = m.h2;
     prm.nt = f32 ? 12 : min(64, (per_cta + 15) & ~15);
     prm.smma = smma_ok && smma_chunk(m, per_cta) ? 1 : 0;
+    if (deep_wave_supported(m)) {
+        // (warp-level MMAs only, on chunks of up to kSmmaMaxChunk pixels)
+        prm.deep = 1;
+        prm.nhh = m.nl - 2;
+        prm.smma = 1;
+        prm.nt = min(kSmmaMaxChunk, prm.nt);
+    }
     prm.k1 = (m.n_in + 15) / 16 * 16;
     prm.tslots = m.wu + 1;
     // ring columns kept per row: an entry must outlive its last reader,
@@ -1839,7 +1989,7 @@ cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, 
     // Warp-level MMAs when the call's clusters leave most SMs idle (a wave's
     // latency decides); when they fill the GPU, every SM's throughput does
     // and the tensor core's MMAs win at any chunk size.
-    const bool smma = latency && smma_chunk(m, wave_per_cta(maxH, maxW, P));
+    const bool smma = deep_wave_supported(m) || (latency && smma_chunk(m, wave_per_cta(maxH, maxW, P)));
     void (*kern)(DevModel, DecBatch, DecTcParams) = wave_kernel(m, smma);
     uint32_t limit = 0;
     cudaError_t e = smem_limit(kern, limit);

@@ -184,6 +184,8 @@ cudaError_t launch_batch_finish(const DecBatch &b, cudaStream_t st);
 cudaError_t launch_decode_tc(const DevModel &m, const DecBatch &b, int cluster, int num_sms, int plan, cudaStream_t st,
                              bool latency);
 bool wave_decode_supported(const DevModel &m);
+// INT8 networks of 1..5 hidden layers of widths up to 128 on the same decoder
+bool deep_wave_supported(const DevModel &m);
 // whether an H x W image decodes in clusters of P CTAs (some shared-memory plan fits)
 bool wave_decode_fits(const DevModel &m, int H, int W, int D, int P, int plan);
 // a volume on every SM at once (cooperative grid) instead of one cluster

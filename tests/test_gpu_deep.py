@@ -1,7 +1,9 @@
 """GPU parity for networks of other than two hidden layers (Sec. II-B
 "Neural Network Architecture": six dense layers): the "DLM2" blob on the
-one-pixel-per-thread CUDA-core encoder and decoder, bit for bit against the
-oracle on the same seeded inputs.
+one-pixel-per-thread CUDA-core encoder, the cluster wavefront decoder's
+warp-level MMA chain (INT8, 1..5 hidden layers of widths up to 128) and the
+unit-split CUDA-core decoder (the rest), bit for bit against the oracle on
+the same seeded inputs.
 
 Networks: a predictive two-hidden-layer network with hidden identity layers
 inserted (realistic, peaked tables), seeded random networks of five hidden
@@ -109,6 +111,23 @@ def test_two_hidden_layers_in_either_format(Codec, orc, prec):
     g1 = _check(Codec, orc, b1, [img], [32])[0]
     g2 = _check(Codec, orc, b2, [img], [32])[0]
     assert g1[:16] == g2[:16] and g1[24:] == g2[24:] and g1[16:24] != g2[16:24]
+
+
+def test_width_128_on_clusters(Codec, orc):
+    # six dense layers of 128 units on images large enough for clusters of
+    # several CTAs and waves of several pixel chunks per CTA, in one call
+    imgs = [synth.voronoi_image(192, 256, 12), synth.value_noise_image(40, 400, 13), synth.value_noise_image(3, 700, 14)]
+    layers = _random_layers([12, 128, 128, 128, 128, 128, 256], 61)
+    _check(Codec, orc, _blob(layers, "int8", imgs), imgs, [64, 40, 3])
+
+
+def test_predictive_six_layers(Codec, orc):
+    # the bench's six-layer network (the predictive network with three
+    # identity layers) on a 128 x 160 crop of the bench image: peaked tables
+    from paper_2207_05152_gb300 import workloads
+    img = np.ascontiguousarray(workloads.cfg2_image()[:128, :160])
+    got = _check(Codec, orc, workloads.deep_models()[0], [img], [32])
+    assert 8.0 * len(got[0]) / img.size < 7.0
 
 
 def test_corrupt_stream_is_reported(Codec, orc):
