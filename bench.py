@@ -831,6 +831,21 @@ def measure_train(args):
     ms_chunk = e0.elapsed_time(e1) / max(3, args.steps // 2)
     assert tr.status() == 0
     tr.close()
+    # activations recomputed rather than stored: two activation buffers, the
+    # first hidden layer recomputed in the backward pass (split mode)
+    tr = T.Trainer(layers, "bf16x3", max_batch=TRAIN_BATCH, recompute=True)
+    for _ in range(args.warmup):
+        tr.step(c, t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tr.step(c, t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_rec = e0.elapsed_time(e1) / args.steps
+    assert tr.status() == 0
+    tr.close()
     _, bf16_peak, _ = _peaks()
     # the BF16 number is the split mode (hi + lo bf16 planes, three MMAs per
     # K step): the one whose gradients are within 1e-3 of FP64 (tested); plain
@@ -848,6 +863,14 @@ def measure_train(args):
                            "ctx_s": round(TRAIN_BATCH / (ms_chunk * 1e-3), 1),
                            "cost_vs_one_pass": round(ms_chunk / out["bf16"]["ms_per_step"], 3),
                            "mode": "split bf16, batch 65536 as 8 chunks of 8192 (one chunk's activations held)"}
+    h1, h2, n_out = TRAIN_WIDTHS[1], TRAIN_WIDTHS[2], TRAIN_WIDTHS[3]
+    plane_bytes = 4   # split mode: hi + lo bf16 planes per element
+    out["bf16_recompute"] = {"ms_per_step": round(ms_rec, 4), "ctx_s": round(TRAIN_BATCH / (ms_rec * 1e-3), 1),
+                             "cost_vs_stored": round(ms_rec / out["bf16"]["ms_per_step"], 3),
+                             "activation_bytes": plane_bytes * TRAIN_BATCH * (max(h1, n_out) + h2),
+                             "activation_bytes_stored": plane_bytes * TRAIN_BATCH * (2 * h1 + 2 * h2 + n_out),
+                             "mode": "split bf16, batch 65536, two activation buffers, the first hidden layer "
+                                     "recomputed in the backward pass (bit-identical to the stored mode)"}
     return out
 
 

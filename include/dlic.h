@@ -372,6 +372,15 @@ DLIC_API dlic_status dlic_decode_volume(const dlic_model *model, const void *d_i
 /* ---------------------------------------------------------------------- */
 
 enum { DLIC_TRAIN_BF16 = 0, DLIC_TRAIN_FP32 = 1, DLIC_TRAIN_BF16X3 = 2 };
+/* OR'ed into a BF16 mode at dlic_trainer_create(_k): activations recomputed
+ * rather than stored.  The trainer then holds two activation buffers of
+ * max_batch rows instead of five: the first hidden layer's output is
+ * recomputed from the batch in the backward pass (one more first-layer
+ * launch per step) and every gradient buffer reuses the memory of an
+ * activation that is no longer needed.  Losses, gradients and updates are
+ * bit for bit those of the mode without it.  With DLIC_TRAIN_FP32 the call
+ * returns DLIC_ERR_INVALID. */
+enum { DLIC_TRAIN_RECOMPUTE = 0x100 };
 
 /* Number of FP32 parameters of an n_in -> h1 -> h2 -> 256 network (n_in:
  * the priors of the model's window, 12 for the default window), laid out as

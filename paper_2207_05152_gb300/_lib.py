@@ -17,6 +17,7 @@ DLIC_OK, DLIC_ERR_INVALID, DLIC_ERR_CAPACITY, DLIC_ERR_CORRUPT = 0, 1, 2, 3
 DLIC_ERR_TIMEOUT, DLIC_ERR_CUDA, DLIC_ERR_UNSUPPORTED = 4, 5, 6
 DLIC_FP32, DLIC_INT8 = 0, 1
 DLIC_TRAIN_BF16, DLIC_TRAIN_FP32, DLIC_TRAIN_BF16X3 = 0, 1, 2
+DLIC_TRAIN_RECOMPUTE = 0x100
 DLIC_PLAN_AUTO, DLIC_PLAN_BYTE_RING, DLIC_PLAN_IMAGE, DLIC_PLAN_GRID = 0, 1, 2, 3
 
 

@@ -959,6 +959,7 @@ struct dlic_trainer {
     int n_out;                                   // 256 (8-bit samples, u8 batches) or 4096 (12-bit, u16)
     int wide;                                    // n_out = 4096
     int bf, split;                               // bf16 operands; hi + lo planes
+    int recompute;                               // two activation buffers, h1 recomputed in the backward
     size_t nparams;
     int step;
     float lr, beta1, beta2, eps;
@@ -1333,7 +1334,8 @@ dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float 
     // layer 1, 2: bias + ReLU
     e.bias = p.b1; e.out = t->H1; e.outT = t->H1T; e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     dlic_status s = DLIC_OK;
-    if (bf) {
+    // the first layer on the CUDA cores (BF16 modes): h1 rows and their sign bits
+    auto layer1 = [&]() {
         const int nb = (B + kL1Ctx - 1) / kL1Ctx;
         uint16_t *H1 = static_cast<uint16_t *>(t->H1);
         if (n_in <= 12)
@@ -1346,6 +1348,9 @@ dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float 
             k_layer1<64><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
         else
             k_layer1<96><<<nb, 256, 0, st>>>(ctx, t->wide, B, n_in, p.W1, p.b1, h1, H1, sp * Bm * h1, t->M1, t->err);
+    };
+    if (bf) {
+        layer1();
     } else if ((s = gemm(t, rowmaj(t->X, k1), wmat(t->w1, h1, k1), B, h1, k1, EPI_BIAS_RELU, e, 1, st))) {
         return s;
     }
@@ -1393,6 +1398,50 @@ dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float 
         return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "forward launch");
     }
     reduce_parts(t->colsum, lt, n_out, n_out, g.b3, 1.0f, 0, 0, st);
+    // weight gradients dW = dY^T X: K = batch, split-K partials summed in a
+    // fixed order; enough splits to cover every SM, as many as the partial
+    // buffer holds
+    auto splits_for = [&](int M, int N) {
+        const int nkb = (B + 63) / 64;
+        int want = bf ? max(1, t->num_sms / ((M + 127) / 128)) : max(1, min(64, (B + 1023) / 1024));
+        want = max(1, min(want, (int)(t->part_floats / ((size_t)M * N))));
+        const int per = (nkb + min(want, nkb) - 1) / min(want, nkb);
+        return (nkb + per - 1) / per;
+    };
+    int sk = 0;
+    if (t->recompute) {
+        // Two activation buffers: A held h1, then dz (the layer-3 GEMM
+        // overwrote h1, which it no longer needs); B holds h2.  Each buffer
+        // is reused once its contents are dead: dW3 = dz^T h2 first, da2
+        // into B (over h2), then h1 recomputed from the batch into A (over
+        // dz), dW2 = da2^T h1, da1 into A (over h1), dW1 = da1^T x.  The
+        // same kernels in the same arithmetic: the gradient equals the
+        // stored-activation one bit for bit.
+        sk = splits_for(n_out, h2);
+        e = EpiArgs{}; e.c = t->part; e.ldc = h2;
+        if ((s = gemm(t, wgrad(t->DZ, t->DZT, n_out), wgrad(t->H2, t->H2T, h2), n_out, h2, B, EPI_F32, e, sk, st)))
+            return s;
+        reduce_parts(t->part, sk, (size_t)n_out * h2, n_out * h2, g.W3, 1.0f, 0, 0, st);
+        e = EpiArgs{}; e.mask = t->M2; e.out = t->DA2; e.colsum = t->colsum; e.out_plane = Bm * h2;
+        if ((s = gemm(t, rowmaj(t->DZ, n_out), wmat(t->w3t, h2, n_out), B, h2, n_out, EPI_RELU_GRAD, e, 1, st)))
+            return s;
+        reduce_parts(t->colsum, mt, h2, h2, g.b2, 1.0f, 0, 0, st);
+        layer1();
+        sk = splits_for(h2, h1);
+        e = EpiArgs{}; e.c = t->part; e.ldc = h1;
+        if ((s = gemm(t, wgrad(t->DA2, t->DA2T, h2), wgrad(t->H1, t->H1T, h1), h2, h1, B, EPI_F32, e, sk, st)))
+            return s;
+        reduce_parts(t->part, sk, (size_t)h2 * h1, h2 * h1, g.W2, 1.0f, 0, 0, st);
+        e = EpiArgs{}; e.mask = t->M1; e.out = t->DA1; e.colsum = t->colsum; e.out_plane = Bm * h1;
+        if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
+        reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, 0, st);
+        sk = splits_for(h1, k1);
+        e = EpiArgs{}; e.c = t->part; e.ldc = k1;
+        if ((s = gemm(t, wgrad(t->DA1, t->DA1T, h1), wgrad(t->X, t->XT, k1), h1, k1, B, EPI_F32, e, sk, st))) return s;
+        reduce_parts(t->part, sk, (size_t)h1 * k1, h1 * k1, g.W1, 1.0f, k1, n_in, st);
+        cudaError_t ce = cudaGetLastError();
+        return ce == cudaSuccess ? DLIC_OK : cuda_fail(ce, "backward launch");
+    }
     // dh2 = dz W3 (B operand W3^T), da2 = dh2 * [h2 > 0]; db2
     e = EpiArgs{}; e.act = t->H2; e.mask = t->M2; e.out = t->DA2; e.outT = t->DA2T; e.colsum = t->colsum;
     e.out_plane = Bm * h2; e.outT_plane = (size_t)h2 * Bm;
@@ -1404,17 +1453,7 @@ dlic_status run(dlic_trainer *t, const void *ctx, const void *tgt, int B, float 
     e.out_plane = Bm * h1; e.outT_plane = (size_t)h1 * Bm;
     if ((s = gemm(t, rowmaj(t->DA2, h2), wmat(t->w2t, h1, h2), B, h1, h2, EPI_RELU_GRAD, e, 1, st))) return s;
     reduce_parts(t->colsum, mt, h1, h1, g.b1, 1.0f, 0, 0, st);
-    // weight gradients dW = dY^T X: K = batch, split-K partials summed in a
-    // fixed order; enough splits to cover every SM, as many as the partial
-    // buffer holds
-    auto splits_for = [&](int M, int N) {
-        const int nkb = (B + 63) / 64;
-        int want = bf ? max(1, t->num_sms / ((M + 127) / 128)) : max(1, min(64, (B + 1023) / 1024));
-        want = max(1, min(want, (int)(t->part_floats / ((size_t)M * N))));
-        const int per = (nkb + min(want, nkb) - 1) / min(want, nkb);
-        return (nkb + per - 1) / per;
-    };
-    int sk = splits_for(n_out, h2);
+    sk = splits_for(n_out, h2);
     e = EpiArgs{}; e.c = t->part; e.ldc = h2;
     if ((s = gemm(t, wgrad(t->DZ, t->DZT, n_out), wgrad(t->H2, t->H2T, h2), n_out, h2, B, EPI_F32, e, sk, st)))
         return s;
@@ -1453,8 +1492,12 @@ extern "C" dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out
     if (n_in < 1 || n_in > kMaxPriors) return fail(DLIC_ERR_INVALID, "network inputs must be in [1, %d]", kMaxPriors);
     if (h1 < 16 || h1 > 256 || h1 % 16 || h2 < 16 || h2 > 256 || h2 % 16)
         return fail(DLIC_ERR_UNSUPPORTED, "hidden widths must be multiples of 16 in [16, 256]");
+    const int recompute = (mode & DLIC_TRAIN_RECOMPUTE) != 0;
+    mode &= ~DLIC_TRAIN_RECOMPUTE;
     if (mode != DLIC_TRAIN_BF16 && mode != DLIC_TRAIN_FP32 && mode != DLIC_TRAIN_BF16X3)
         return fail(DLIC_ERR_INVALID, "unknown training mode %d", mode);
+    if (recompute && mode == DLIC_TRAIN_FP32)
+        return fail(DLIC_ERR_INVALID, "DLIC_TRAIN_RECOMPUTE takes a BF16 mode");
     if (max_batch < 1 || max_batch > (1 << 22)) return fail(DLIC_ERR_INVALID, "max_batch must be in [1, 2^22]");
     if (!h_params) return fail(DLIC_ERR_INVALID, "null initial parameters");
     dlic_trainer *t = new dlic_trainer();
@@ -1465,6 +1508,7 @@ extern "C" dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out
     t->wide = n_out == kWideOut;
     t->bf = mode != DLIC_TRAIN_FP32;
     t->split = mode == DLIC_TRAIN_BF16X3;
+    t->recompute = recompute;
     t->max_batch = (max_batch + 127) / 128 * 128;
     t->nparams = param_count(n_in, h1, h2, n_out);
     t->step = 0;
@@ -1493,13 +1537,19 @@ extern "C" dlic_status dlic_trainer_create_k(int n_in, int h1, int h2, int n_out
     t->w2t = A(es * h1 * h2);
     t->w3t = A(es * h2 * n_out);
     t->X = A(es * Bm * t->k1);
-    t->H1 = A(es * Bm * h1);
-    t->H2 = A(es * Bm * h2);
-    t->DZ = A(es * Bm * n_out);
+    if (recompute) {
+        // two activation buffers (h1, dz, h1 again, da1 in turn; h2, da2)
+        t->H1 = t->DZ = t->DA1 = A(es * Bm * (n_out > h1 ? n_out : h1));
+        t->H2 = t->DA2 = A(es * Bm * h2);
+    } else {
+        t->H1 = A(es * Bm * h1);
+        t->H2 = A(es * Bm * h2);
+        t->DZ = A(es * Bm * n_out);
+        t->DA2 = A(es * Bm * h2);
+    }
     if (t->wide) t->Z = (float *)A(4 * Bm * n_out);
-    t->DA2 = A(es * Bm * h2);
     if (t->bf) {
-        t->DA1 = A(es * Bm * h1);
+        if (!recompute) t->DA1 = A(es * Bm * h1);
         t->M1 = (uint16_t *)A(2 * Bm * (h1 / 16) + 16);   // (+16: the L2 prefetch rounds up)
         t->M2 = (uint16_t *)A(2 * Bm * (h2 / 16) + 16);
     } else {

@@ -158,9 +158,11 @@ def _contexts_at(images, idx, rr, cc, window):
 class Trainer:
     """FP32 master weights + Adam on the current CUDA device.  A network of
     4096 outputs (12-bit samples, Sec. IV "Higher Bit Depth") trains on u16
-    contexts and targets; one of 256 on u8."""
+    contexts and targets; one of 256 on u8.  recompute (BF16 modes): two
+    activation buffers instead of five, the first hidden layer recomputed in
+    the backward pass; the results are bit for bit those without it."""
 
-    def __init__(self, layers, mode: str = "bf16", max_batch: int = 65536):
+    def __init__(self, layers, mode: str = "bf16", max_batch: int = 65536, recompute: bool = False):
         self.n_in = layers[0][0].shape[1]   # the window's priors
         self.h1 = layers[0][0].shape[0]
         self.h2 = layers[1][0].shape[0]
@@ -169,8 +171,9 @@ class Trainer:
         self.nparams = _lib.dlic_train_param_count_k(self.n_in, self.h1, self.h2, self.n_out)
         flat = np.ascontiguousarray(flatten(layers))
         assert flat.size == self.nparams
-        self.handle = _lib.dlic_trainer_create_k(self.n_in, self.h1, self.h2, self.n_out, MODES[mode], max_batch,
-                                                 flat)
+        flags = _lib.DLIC_TRAIN_RECOMPUTE if recompute else 0
+        self.handle = _lib.dlic_trainer_create_k(self.n_in, self.h1, self.h2, self.n_out, MODES[mode] | flags,
+                                                 max_batch, flat)
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
     def _check(self, ctx: torch.Tensor, tgt: torch.Tensor):

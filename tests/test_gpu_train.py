@@ -300,3 +300,46 @@ def test_frequency_weighted_loss(T, mode, tol):
     with pytest.raises(_lib.DlicError):
         tr.set_value_weights(bad)
     tr.close()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("widths,n,cap", [((12, 256, 256, 256), 4100, 4100), ((12, 64, 48, 256), 2500, 1000),
+                                          ((12, 128, 128, 4096), 700, 700)])
+def test_recompute_equals_stored_activations(T, mode, widths, n, cap):
+    # DLIC_TRAIN_RECOMPUTE: two activation buffers, the first hidden layer
+    # recomputed in the backward pass; loss, gradient and three Adam steps
+    # must be those of the trainer that stores every activation, bit for bit
+    # (256 and 4096 outputs, a ragged last tile, batches in chunks)
+    if widths[-1] == 4096:
+        # 12-bit phantoms (u16 samples travel as int16 bits)
+        imgs = [synth.phantom_image12(64, 72, 5 + i) for i in range(2)]
+        ctx, tgt = T.sample_contexts(imgs, n, 7)
+        layers = synth.xavier_mlp(list(widths), 7)
+        c = torch.from_numpy(np.ascontiguousarray(ctx).view(np.int16)).cuda()
+        t = torch.from_numpy(np.ascontiguousarray(tgt).view(np.int16)).cuda()
+    else:
+        layers, ctx, tgt = _data(T, n, 37, widths=widths)
+        c = torch.from_numpy(ctx).cuda()
+        t = torch.from_numpy(tgt).cuda()
+    a = T.Trainer(layers, mode, max_batch=cap)
+    b = T.Trainer(layers, mode, max_batch=cap, recompute=True)
+    la, ga = a.backward(c, t)
+    lb, gb = b.backward(c, t)
+    torch.cuda.synchronize()
+    assert torch.equal(la, lb) and torch.equal(ga, gb)
+    for _ in range(3):
+        a.step(c, t)
+        b.step(c, t)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params(), b.params()) and torch.equal(a.loss, b.loss)
+    assert a.status() == 0 and b.status() == 0
+    a.close()
+    b.close()
+
+
+def test_recompute_needs_a_bf16_mode(T):
+    from paper_2207_05152_gb300 import _lib
+    layers = synth.xavier_mlp([12, 32, 32, 256], 3)
+    with pytest.raises(Exception):
+        T.Trainer(layers, "fp32", max_batch=256, recompute=True)
+    assert _lib.DLIC_TRAIN_RECOMPUTE == 0x100
