@@ -354,9 +354,9 @@ def run_ours(args):
                          "weights": "the predictive 12-64-64-256 network in 64 of each layer's 4096 units, "
                                     "seeded random weights in the rest",
                          "kernels": "layer-at-a-time: one kernel per dense layer over a set of pixels; INT8 "
-                                    "encode: the first layer by dp4a, the 4096x4096 and 4096x256 layers on the "
-                                    "tensor cores (k_wide_tc, 8192-pixel passes, exact chunks of K = 256); "
-                                    "FP32 and decode (one wave per set) on the CUDA cores",
+                                    "encode (8192-pixel passes) and decode (one wave per set): the first layer by dp4a, "
+                                    "the 4096x4096 and 4096x256 layers on the tensor cores (k_wide_tc, exact "
+                                    "chunks of K = 256); FP32 on the CUDA cores",
                          "mac_per_px": WIDE_MAC_PER_PX, "int8": leg(rwide), "fp32": leg(rwide32),
                          "int8_enc_tmac_s": round(WIDE_MAC_PER_PX * N / (statistics.mean(rwide["enc"]) * 1e-3) / 1e12, 2),
                          # the whole INT8 encode's multiply-adds (2 int ops each) against the bf16 peak

@@ -413,8 +413,8 @@ cudaError_t wide_network(const DevModel &m, const DevLayer *hl, const WideSet &q
 
 }  // namespace
 
-// whether the encoder runs the layers after the first on the tensor cores
-static bool wide_tc_encode(const DevModel &m, const DevLayer *hl) {
+// whether the layers after the first run on the tensor cores (INT8)
+static bool wide_tc_layers(const DevModel &m, const DevLayer *hl) {
     if (m.precision != DLIC_INT8) return false;
     for (int l = 1; l < m.nl; l++)
         if (!hl || !hl[l].wtc) return false;
@@ -422,13 +422,14 @@ static bool wide_tc_encode(const DevModel &m, const DevLayer *hl) {
 }
 
 size_t wide_scratch_bytes(const DevModel &m, bool encode) {
-    return wide_supported(m) ? wide_scratch(m, nullptr, encode && m.precision == DLIC_INT8).bytes : 0;
+    (void)encode;   // INT8 networks run their wide layers on the tensor cores in both directions
+    return wide_supported(m) ? wide_scratch(m, nullptr, m.precision == DLIC_INT8).bytes : 0;
 }
 
 cudaError_t launch_predict_wide(const DevModel &m, const DevLayer *hl, const EncBatch &b, uint8_t *scratch, int *err,
                                 cudaStream_t st) {
     // (the workspace holds bf16 activations whenever the network is INT8)
-    const bool tc = wide_tc_encode(m, hl);
+    const bool tc = wide_tc_layers(m, hl);
     for (int k = 0; k < b.n; k++) {
         const EncImage &im = b.img[k];
         const int64_t N = (int64_t)im.H * im.W;
@@ -451,7 +452,10 @@ cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecB
                                cudaStream_t st) {
     cudaError_t e = launch_batch_setup(m, b, st);
     if (e != cudaSuccess) return e;
-    const float *Z = wide_scratch(m, scratch, false).Z;
+    // INT8: the layers after the first on the tensor cores, as in the encoder
+    // (the same exact integer sums, so the same tables)
+    const bool tc = wide_tc_layers(m, hl);
+    const float *Z = wide_scratch(m, scratch, tc).Z;
     for (int k = 0; k < b.n && e == cudaSuccess; k++) {
         const DecImage &im = b.img[k];
         WideDecState d;
@@ -470,7 +474,7 @@ cudaError_t launch_decode_wide(const DevModel &m, const DevLayer *hl, const DecB
             for (int r0 = r_lo; r0 <= r_hi && e == cudaSuccess; r0 += kWideChunk) {
                 const int np = std::min(kWideChunk, r_hi - r0 + 1);
                 const WideSet q{im.pixels, im.pitch, H, W, 1, 0, t, r0, np};
-                e = wide_network(m, hl, q, scratch, false, nullptr, st);
+                e = wide_network(m, hl, q, scratch, tc, b.status + im.sidx, st);
                 if (e != cudaSuccess) break;
                 // one warp per stream of the pass (at most H streams)
                 const int warps = std::min(np, H);
