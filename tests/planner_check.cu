@@ -80,6 +80,25 @@ int main() {
         show("grid_batch_64x1536x2048", ok, p, false);
         delete b;
     }
+    // INT8 networks of 1..5 hidden layers up to 128 wide (the deep instance:
+    // up to four 128 x 128 bf16 hidden-to-hidden layers in shared memory)
+    {
+        static DevLayer table[kMaxLayers];   // (the planner reads only whether there is a table)
+        struct D { const char *name; int nl, H, W, P; } ds[] = {
+            {"six_layers_512", 6, 512, 512, 16}, {"six_layers_512_one_cta", 6, 512, 512, 1},
+            {"one_hidden_512", 2, 512, 512, 16}, {"six_layers_4096x12288", 6, 4096, 12288, 16},
+        };
+        for (const D &d : ds) {
+            DevModel m = model(DLIC_INT8, 2, 2, 2, 0, 0, 0, 0, 0, 128);
+            m.bits = 8;
+            m.nl = d.nl;
+            m.layers = table;
+            DecTcParams p{};
+            const bool ok = deep_wave_supported(m) && plan_wave(m, d.H, d.W, 1, d.P, limit, DLIC_PLAN_AUTO, p);
+            printf("deep %s %d %d %d %d %d %d %u\n", d.name, ok ? 1 : 0, p.deep, p.nhh, p.smma, p.nt, p.gimg,
+                   ok ? dec_layout(p, false).total : 0u);
+        }
+    }
     // the decode autotuner: cluster sizes for a few batches
     {
         const int H1[1] = {512}, W1[1] = {512};

@@ -31,6 +31,10 @@ def plans():
         if name == "clusters":
             res["clusters_" + v[0]] = [int(x) for x in v[1:]]
             continue
+        if name == "deep":
+            ok, deep, nhh, smma, nt, gimg, total = map(int, v[1:])
+            res["deep_" + v[0]] = dict(ok=ok, deep=deep, nhh=nhh, smma=smma, nt=nt, gimg=gimg, total=total)
+            continue
         ok, nt, tq, gimg, ring_rows, list_rows, lut2, total = map(int, v)
         res[name] = dict(ok=ok, nt=nt, tq=tq, gimg=gimg, ring_rows=ring_rows, list_rows=list_rows, lut2=lut2,
                          total=total)
@@ -80,3 +84,16 @@ def test_autotuner_cluster_sizes(plans):
     ps = plans["clusters_batch64"]
     assert all(p in (1, 2, 4, 8, 16) for p in ps) and sum(ps) <= 152 and max(ps) > 1
     assert plans["clusters_tiny200"] == [1, 1]
+
+
+def test_deeper_networks_take_the_warp_mma_chain(plans):
+    # six dense layers (four hidden-to-hidden layers of 128 units in shared
+    # memory) and a single hidden layer: warp-level MMAs on chunks of at most
+    # 32 pixels, every plan within the shared memory, the long waves of a
+    # 4096 x 12288 image reading their priors back from the image
+    for name in ("six_layers_512", "six_layers_512_one_cta", "one_hidden_512", "six_layers_4096x12288"):
+        p = plans["deep_" + name]
+        assert p["ok"] and p["deep"] == 1 and p["smma"] == 1 and 16 <= p["nt"] <= 32, name
+        assert 0 < p["total"] <= LIMIT, name
+    assert plans["deep_six_layers_512"]["nhh"] == 4 and plans["deep_one_hidden_512"]["nhh"] == 0
+    assert plans["deep_six_layers_512"]["gimg"] == 0 and plans["deep_six_layers_4096x12288"]["gimg"] == 1
