@@ -2,6 +2,7 @@
 
     python -m paper_2207_05152_gb300.profile_train --mode bf16 --batch 65536 --steps 2
     python -m paper_2207_05152_gb300.profile_train --bits 12 --mode bf16x3 --batch 16384 --steps 2
+    python -m paper_2207_05152_gb300.profile_train --mode bf16x3 --steps 2 --recompute
 
 8-bit: 12-256-256-256 on contexts of eight 512 x 512 synthetic images;
 12-bit: 12-128-128-4096 on contexts of twelve 256 x 256 12-bit phantoms.
@@ -23,6 +24,7 @@ def main():
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--bits", type=int, default=8, choices=[8, 12])
+    ap.add_argument("--recompute", action="store_true", help="activations recomputed rather than stored (BF16 modes)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -37,7 +39,7 @@ def main():
     ctx, tgt = T.sample_contexts(imgs, args.batch, 3000)
     if args.bits == 12:
         ctx, tgt = ctx.view(np.int16), tgt.view(np.int16)
-    tr = T.Trainer(synth.xavier_mlp(widths, 3), args.mode, max_batch=args.batch)
+    tr = T.Trainer(synth.xavier_mlp(widths, 3), args.mode, max_batch=args.batch, recompute=args.recompute)
     c, t = torch.from_numpy(ctx).cuda(), torch.from_numpy(tgt).cuda()
     for _ in range(args.steps):
         tr.step(c, t)
