@@ -165,3 +165,13 @@ def test_read_header_of_a_twelve_bit_container(lib, orc):
     with pytest.raises(lib.DlicError) as e:
         lib.dlic_read_header(b"DLC2" + data[4:])
     assert e.value.code == lib.DLIC_ERR_CORRUPT
+
+
+def test_trainer_modes_are_checked_before_any_device_call(lib):
+    # DLIC_TRAIN_RECOMPUTE takes a BF16 mode; unknown modes are refused; the
+    # checks run before the trainer allocates anything (no GPU here)
+    params = np.zeros(lib.dlic_train_param_count(12, 32, 32), np.float32)
+    for mode in (lib.DLIC_TRAIN_FP32 | lib.DLIC_TRAIN_RECOMPUTE, 7, 7 | lib.DLIC_TRAIN_RECOMPUTE):
+        with pytest.raises(Exception) as e:
+            lib.dlic_trainer_create_k(12, 32, 32, 256, mode, 256, params)
+        assert "mode" in str(e.value).lower() or "recompute" in str(e.value).lower()
